@@ -1,0 +1,254 @@
+/*
+ * hpg.h -- C ABI of libhpg: hierarchical proximal Galerkin (hpG) on one GB300.
+ *
+ * The library solves the latent-variable proximal point (LVPP) subproblems of
+ * Papadopoulos, "Hierarchical proximal Galerkin" (arXiv:2412.13733):
+ *
+ *   obstacle type, eq. (pG), Section 2.1 and 4.1:
+ *     alpha_k (grad u, grad v) + (psi_k, v) = alpha_k (f, v) + (psi_{k-1}, v)
+ *     (u, zeta) + (exp(-psi_k), zeta)       = (phi, zeta)
+ *   gradient type, eq. (pG:gradient), Section 2.2 and 4.2:
+ *     alpha_k (grad u, grad v) + (psi_k, grad v) = alpha_k (f, v) + (psi_{k-1}, grad v)
+ *     (grad u, zeta) = (phi psi_k / sqrt(1 + |psi_k|^2), zeta)
+ *
+ * discretised with the hierarchical p-FEM basis of Section 3 (u: hats +
+ * bubbles W_n, eq. (Wn); psi: cellwise Legendre, degree p-2 for obstacles and
+ * p-1 (d components) for gradient constraints) on uniform tensor-product
+ * quad/hex meshes.  Each subproblem is solved by Newton (Newton matrix G of
+ * eq. (pG-matrix)); each Newton system by the Schur sequence of eq. (schur2),
+ * with GMRES on the Schur complement S of eq. (schur4), right-preconditioned
+ * by the cell-block-diagonal S-hat of eq. (schur-preconditioner) or
+ * eq. (schur-preconditioner:gradient), whose blocks are factorised as
+ * batched dense Cholesky on the device.
+ *
+ * Conventions
+ * -----------
+ *  - Every call returns an hpg_status; nothing aborts or throws across the ABI.
+ *  - The caller owns every host buffer passed in; the library copies what it
+ *    keeps.  The context owns all device memory it allocates.  A pointer
+ *    argument documented as "device" must point to memory of the context's
+ *    device; all others are host pointers.
+ *  - Sizes: every output buffer comes with its length in elements; a length
+ *    smaller than required returns HPG_ERR_ARG and writes nothing.
+ *  - Threading: a context may be used by one host thread at a time.
+ *
+ * Coefficient orderings (shared with the CPU oracle by specification)
+ * ------------------------------------------------------------------
+ *  u (full):  tensor product of the 1D global numbering, x index fastest.
+ *             1D numbering on m cells: hats 0..m first, then bubbles
+ *             cell-major (bubble b of cell c at m + 1 + c (p - 1) + b).
+ *             Length prod_j (m_j p + 1).
+ *  u (interior): the entries of u (full) whose every 1D index is neither
+ *             hat 0 nor hat m, in the same relative order.  Length
+ *             prod_j (m_j p - 1).
+ *  psi:       cell-major; cell c = c_x + m_x c_y (+ m_x m_y c_z); inside a
+ *             cell [component][n^d coefficients, x degree fastest];
+ *             n = p - 1 (obstacle) or p (gradient, d components).
+ *  Newton vectors x = [u (interior); psi].
+ */
+#ifndef HPG_H
+#define HPG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hpg_ctx hpg_ctx;
+
+typedef enum {
+    HPG_OK = 0,
+    HPG_ERR_ARG = 1,            /* bad argument, size or id                                  */
+    HPG_ERR_OOM = 2,            /* device or host allocation failed                          */
+    HPG_ERR_CUDA = 3,           /* a CUDA runtime call failed (see hpg_last_error)           */
+    HPG_ERR_NEWTON_CAP = 4,     /* a subproblem hit the Newton iteration cap                 */
+    HPG_ERR_KRYLOV_CAP = 5,     /* GMRES hit its cap before its tolerance (reported only)    */
+    HPG_ERR_NONFINITE = 6,      /* NaN/Inf, or psi < -700 at a Gauss point (exp overflow)    */
+    HPG_ERR_NOT_SPD = 7,        /* a cell block of -S-hat had a non-positive Cholesky pivot  */
+    HPG_ERR_TIMEOUT = 8,        /* a bounded host wait expired                               */
+    HPG_ERR_INFEASIBLE_BC = 9,  /* Dirichlet data violates the constraint on the boundary    */
+    HPG_ERR_STATE = 10,         /* call out of order (e.g. solve before data were set)       */
+    HPG_ERR_BUSY = 11           /* the problem is part of an unfinished batch or request     */
+} hpg_status;
+
+typedef enum {
+    HPG_OBSTACLE_UPPER = 0,     /* u <= phi (the paper's form, eq. ad:obstacle)              */
+    HPG_OBSTACLE_LOWER = 1,     /* u >= phi, solved as -u <= -phi with f, g negated          */
+    HPG_GRADIENT = 2            /* |grad u| <= phi (eq. ad:gradient)                         */
+} hpg_kind;
+
+typedef enum {
+    HPG_FP64 = 0,               /* every step in FP64                                        */
+    HPG_MIXED = 1               /* FP64 residuals, exp and orthogonalisation; inner Schur
+                                   operator and preconditioner in FP32 inside FP64 iterative
+                                   refinement of each Newton system                           */
+} hpg_precision;
+
+/* Field callback: out[i] = field(x[i*dim], ..., x[i*dim+dim-1]) for i < npts. */
+typedef void (*hpg_field_fn)(int npts, int dim, const double* x, double* out, void* user);
+
+typedef struct {
+    double beta;          /* E_beta = beta M_Psi (obstacle) or beta (grad_h zeta, grad_h zeta)
+                             (gradient); Jacobian only, Section 4.1                           */
+    double newton_tol;    /* absolute l2 norm of [F_u; F_psi]; default 1e-10                 */
+    int    newton_max;    /* Newton cap per proximal step; default 50                         */
+    int    krylov_max;    /* GMRES cap (no restart); default 150                              */
+    double krylov_rtol;   /* GMRES relative tolerance ceiling; the forcing term is
+                             min(krylov_rtol, ||F||) relative; default 1e-5                   */
+    int    precision;     /* hpg_precision; default HPG_FP64                                  */
+    int    ls_max;        /* line-search halvings; default 10                                 */
+    int    refine_max;    /* HPG_MIXED: FP64 refinement sweeps per Newton system; default 8   */
+    int    timing;        /* 1: record CUDA-event time per kernel class (hpg_get_kernel_times) */
+} hpg_params;
+
+#define HPG_MAX_ALPHA 128
+
+typedef struct {
+    int    status;                         /* hpg_status of the last solve                 */
+    int    alpha_steps;                    /* proximal subproblems solved                  */
+    int    newton_total;                   /* Newton iterations (linear solves)            */
+    int    newton_per_step[HPG_MAX_ALPHA]; /* Newton iterations per proximal step          */
+    long long krylov_total;                /* inner GMRES iterations over the solve        */
+    int    refine_total;                   /* HPG_MIXED refinement sweeps over the solve   */
+    int    ls_fail;                        /* line searches that ran out of halvings       */
+    int    krylov_cap_hits;                /* GMRES solves that stopped at the cap         */
+    double final_residual;                 /* ||F|| at the end of the last subproblem      */
+    double solve_ms;                       /* wall time of the last hpg_solve (host clock) */
+    long long n_u;                         /* interior u unknowns                          */
+    long long n_psi;                       /* psi unknowns                                 */
+} hpg_stats;
+
+/* Kernel classes timed when hpg_params.timing = 1. */
+typedef enum {
+    HPG_K_EVAL = 0,       /* Gauss evaluation of the latent nonlinearity                   */
+    HPG_K_RESIDUAL = 1,   /* Newton residual F_u, F_psi and its norm                       */
+    HPG_K_FACTOR = 2,     /* S-hat cell-block assembly + batched Cholesky + inverse        */
+    HPG_K_PRECOND = 3,    /* S-hat^{-1} apply                                              */
+    HPG_K_BAPPLY = 4,     /* B apply                                                       */
+    HPG_K_FDM = 5,        /* A_alpha^{-1} apply (fast diagonalisation, all passes)         */
+    HPG_K_SCHUR = 6,      /* -(D + E) z - B^T t  (rest of the S apply)                     */
+    HPG_K_ORTHO = 7,      /* GMRES orthogonalisation, norms, Givens                        */
+    HPG_K_NEWTON_APPLY = 8,/* FP64 matrix-free G apply (mixed-precision refinement)        */
+    HPG_K_UPDATE = 9,     /* vector updates                                                */
+    HPG_K_COUNT = 10
+} hpg_kernel_class;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` (a cudaStream_t,
+ * may be NULL) is the stream every launch of this context goes to; NULL makes
+ * the context create its own non-blocking stream. */
+hpg_status hpg_create(hpg_ctx** out, int device, void* cuda_stream);
+/* Free every device buffer and the context.  NULL is accepted. */
+hpg_status hpg_destroy(hpg_ctx* ctx);
+/* Human-readable name of a status code (static string). */
+const char* hpg_status_str(hpg_status s);
+/* Last detailed error message of this context (static per context; never NULL). */
+const char* hpg_last_error(hpg_ctx* ctx);
+/* Fill `p` with the defaults listed in hpg_params. */
+void hpg_default_params(hpg_params* p);
+
+/* ---------------------------------------------------------------- problem */
+
+/* Uniform tensor-product mesh of (lo[j], hi[j]) with cells[j] cells in
+ * direction j < dim (dim 2 or 3), partial degree p for u, constraint kind.
+ * Obstacle kinds need 2 <= p <= 11; gradient needs 1 <= p <= 10.  The psi
+ * pairing is the paper's (Section 4.1: degree p-2; Section 4.2: degree p-1).
+ * Returns a problem id in *pid (valid until hpg_problem_free/hpg_destroy). */
+hpg_status hpg_problem_create(hpg_ctx* ctx, int dim, const double* lo, const double* hi,
+                              const int* cells, int p, hpg_kind kind, int* pid);
+hpg_status hpg_problem_free(hpg_ctx* ctx, int pid);
+
+/* Sizes of the problem's vectors (any pointer may be NULL). n_quad = Gauss
+ * points of the latent-variable rule (q = n per direction per cell). */
+hpg_status hpg_problem_sizes(hpg_ctx* ctx, int pid, size_t* n_u_full, size_t* n_u_interior,
+                             size_t* n_psi, size_t* n_quad);
+
+/* Right-hand side f: callback evaluated at setup on (p+2)^d Gauss points per
+ * cell, or a constant.  Default f = 0. */
+hpg_status hpg_set_rhs(hpg_ctx* ctx, int pid, hpg_field_fn f, void* user);
+hpg_status hpg_set_rhs_const(hpg_ctx* ctx, int pid, double f);
+
+/* Constraint phi (eq. ad:obstacle / ad:gradient), evaluated at the latent
+ * Gauss points.  Required before solving.  hpg_quad_points returns those
+ * points (n_quad x dim, cell-major, point index x fastest inside a cell);
+ * hpg_set_constraint_values takes phi at them directly (length n_quad). */
+hpg_status hpg_set_constraint(hpg_ctx* ctx, int pid, hpg_field_fn phi, void* user);
+hpg_status hpg_quad_points(hpg_ctx* ctx, int pid, double* pts, size_t len);
+hpg_status hpg_set_constraint_values(hpg_ctx* ctx, int pid, const double* phi_q, size_t len);
+
+/* Dirichlet datum g (NULL: u = 0 on the boundary).  Realised by the lifting
+ * rule: vertex hats take g at the vertex, each boundary edge's bubbles the
+ * H^1_0-seminorm projection of g minus its linear interpolant, faces by the
+ * tensor product of that 1D rule. */
+hpg_status hpg_set_dirichlet(hpg_ctx* ctx, int pid, hpg_field_fn g, void* user);
+
+/* alpha_k schedule: alpha_k = min(a1 * 2^{(k-1)/2}, cap) until it repeats
+ * (Sections 6.1-6.5), or an explicit list (count <= HPG_MAX_ALPHA). */
+hpg_status hpg_set_alpha_schedule(hpg_ctx* ctx, int pid, double a1, double cap);
+hpg_status hpg_set_alpha_list(hpg_ctx* ctx, int pid, const double* alphas, int count);
+
+hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params);
+
+/* ------------------------------------------------------------------ solve */
+
+/* Run the full proximal loop (psi_0 = 0, u_0 = lifting; each subproblem warm
+ * started from the previous one).  Blocking.  Returns HPG_OK or the first
+ * failure (also in hpg_stats.status). */
+hpg_status hpg_solve(hpg_ctx* ctx, int pid);
+
+/* Solve several problems (each as by hpg_solve, in the order given).
+ * Returns HPG_OK if every problem converged; per-problem status in stats. */
+hpg_status hpg_solve_batch(hpg_ctx* ctx, const int* pids, int count);
+
+/* Results of the last solve (u in the caller's sign convention). */
+hpg_status hpg_get_u(hpg_ctx* ctx, int pid, double* u_full, size_t len);
+hpg_status hpg_get_psi(hpg_ctx* ctx, int pid, double* psi, size_t len);
+hpg_status hpg_get_stats(hpg_ctx* ctx, int pid, hpg_stats* stats);
+/* u_h at npts points (npts x dim).  Also the feasible reconstruction
+ * phi - exp(-psi_h) for obstacles (eq. pG) when `feasible` != NULL; it is
+ * defined only at the latent Gauss points (length n_quad). */
+hpg_status hpg_eval_u(hpg_ctx* ctx, int pid, const double* pts, int npts, double* out);
+hpg_status hpg_feasible_u(hpg_ctx* ctx, int pid, double* out_q, size_t len);
+/* Accumulated per-kernel-class device time (ms) and launch counts since the
+ * last reset, recorded only when params.timing = 1. */
+hpg_status hpg_get_kernel_times(hpg_ctx* ctx, int pid, double* ms, long long* launches, int count);
+hpg_status hpg_reset_kernel_times(hpg_ctx* ctx, int pid);
+
+/* ------------------------------------------- component operators (testing)
+ * These act on an explicit state (u, psi, psi_prev, alpha) uploaded by
+ * hpg_set_state, on host vectors in the orderings above.  precision is an
+ * hpg_precision: which arithmetic the operator runs in (results are FP64). */
+
+/* Upload (u full, psi, psi_prev, alpha) and evaluate the latent nonlinearity
+ * at the Gauss points.  u is in the solver's internal sign (for
+ * HPG_OBSTACLE_LOWER the negated field). */
+hpg_status hpg_set_state(hpg_ctx* ctx, int pid, const double* u_full, const double* psi,
+                         const double* psi_prev, double alpha);
+/* Newton residual [F_u (interior); F_psi] of eq. (pG) / (pG:gradient) and its l2 norm. */
+hpg_status hpg_residual(hpg_ctx* ctx, int pid, double* F, size_t len, double* norm);
+/* y = G x with G of eq. (pG-matrix) (including -E_beta), matrix-free, FP64. */
+hpg_status hpg_apply_newton(hpg_ctx* ctx, int pid, const double* x, double* y, size_t len);
+/* y = A_alpha^{-1} x on interior u vectors (exact fast diagonalisation). */
+hpg_status hpg_apply_stiffness_inv(hpg_ctx* ctx, int pid, int precision, const double* x,
+                                   double* y, size_t len);
+/* Assemble and factorise the S-hat cell blocks for the current state; the
+ * blocks of -S-hat before factorisation are copied to `blocks` when not NULL
+ * (Nc x nb x nb, nb = n^d (obstacle) or d n^d (gradient)). */
+hpg_status hpg_factor_precond(hpg_ctx* ctx, int pid, int precision, double* blocks, size_t len);
+/* y = S-hat^{-1} x (needs hpg_factor_precond). */
+hpg_status hpg_apply_precond_inv(hpg_ctx* ctx, int pid, int precision, const double* x,
+                                 double* y, size_t len);
+/* y = S x, S = -(D_psi + E_beta + B^T A_alpha^{-1} B) of eq. (schur4). */
+hpg_status hpg_apply_schur(hpg_ctx* ctx, int pid, int precision, const double* x, double* y,
+                           size_t len);
+/* Solve G delta = F(state) by eq. (schur2) + GMRES (relative tolerance rtol);
+ * returns delta and the GMRES iteration count. */
+hpg_status hpg_newton_direction(hpg_ctx* ctx, int pid, int precision, double rtol, double* delta,
+                                size_t len, int* krylov_its);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPG_H */

@@ -1,0 +1,494 @@
+// C ABI of libhpg (see include/hpg.h for the contract of every entry point).
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "state.h"
+
+using hpg::Problem;
+
+namespace {
+
+Problem* find(hpg_ctx* ctx, int pid) {
+    if (!ctx) return nullptr;
+    auto it = ctx->problems.find(pid);
+    return it == ctx->problems.end() ? nullptr : it->second.get();
+}
+
+hpg_status cuda_ok(hpg_ctx* ctx) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        ctx->err = "cudaSetDevice failed";
+        return HPG_ERR_CUDA;
+    }
+    return HPG_OK;
+}
+
+struct ConstField {
+    double c;
+};
+
+}  // namespace
+
+#define GUARD_BEGIN try {
+#define GUARD_END                                                             \
+    }                                                                         \
+    catch (const std::bad_alloc&) {                                           \
+        if (ctx) ctx->err = "host allocation failed";                         \
+        return HPG_ERR_OOM;                                                   \
+    }                                                                         \
+    catch (const std::exception& e) {                                         \
+        if (ctx) ctx->err = e.what();                                         \
+        return HPG_ERR_ARG;                                                   \
+    }
+
+extern "C" {
+
+void hpg_default_params(hpg_params* p) {
+    if (!p) return;
+    p->beta = 1e-4;
+    p->newton_tol = 1e-10;
+    p->newton_max = 50;
+    p->krylov_max = 150;
+    p->krylov_rtol = 1e-5;
+    p->precision = HPG_FP64;
+    p->ls_max = 10;
+    p->refine_max = 8;
+    p->timing = 0;
+}
+
+const char* hpg_status_str(hpg_status s) {
+    switch (s) {
+        case HPG_OK: return "HPG_OK";
+        case HPG_ERR_ARG: return "HPG_ERR_ARG";
+        case HPG_ERR_OOM: return "HPG_ERR_OOM";
+        case HPG_ERR_CUDA: return "HPG_ERR_CUDA";
+        case HPG_ERR_NEWTON_CAP: return "HPG_ERR_NEWTON_CAP";
+        case HPG_ERR_KRYLOV_CAP: return "HPG_ERR_KRYLOV_CAP";
+        case HPG_ERR_NONFINITE: return "HPG_ERR_NONFINITE";
+        case HPG_ERR_NOT_SPD: return "HPG_ERR_NOT_SPD";
+        case HPG_ERR_TIMEOUT: return "HPG_ERR_TIMEOUT";
+        case HPG_ERR_INFEASIBLE_BC: return "HPG_ERR_INFEASIBLE_BC";
+        case HPG_ERR_STATE: return "HPG_ERR_STATE";
+        case HPG_ERR_BUSY: return "HPG_ERR_BUSY";
+    }
+    return "HPG_UNKNOWN";
+}
+
+const char* hpg_last_error(hpg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+hpg_status hpg_create(hpg_ctx** out, int device, void* cuda_stream) {
+    if (!out) return HPG_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return HPG_ERR_CUDA;
+    hpg_ctx* ctx = new (std::nothrow) hpg_ctx();
+    if (!ctx) return HPG_ERR_OOM;
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return HPG_ERR_CUDA; }
+    if (cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return HPG_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    *out = ctx;
+    return HPG_OK;
+}
+
+hpg_status hpg_destroy(hpg_ctx* ctx) {
+    if (!ctx) return HPG_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->problems) hpg::free_device(*kv.second);
+    ctx->problems.clear();
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return HPG_OK;
+}
+
+hpg_status hpg_problem_create(hpg_ctx* ctx, int dim, const double* lo, const double* hi, const int* cells, int p,
+                              hpg_kind kind, int* pid) {
+    if (!ctx || !lo || !hi || !cells || !pid) return HPG_ERR_ARG;
+    if (dim != 2 && dim != 3) { ctx->err = "dim must be 2 or 3"; return HPG_ERR_ARG; }
+    if (kind != HPG_OBSTACLE_UPPER && kind != HPG_OBSTACLE_LOWER && kind != HPG_GRADIENT) return HPG_ERR_ARG;
+    const bool grad = kind == HPG_GRADIENT;
+    if (grad ? (p < 1 || p > 10) : (p < 2 || p > 11)) { ctx->err = "degree out of range"; return HPG_ERR_ARG; }
+    for (int j = 0; j < dim; ++j) {
+        if (cells[j] < 1 || cells[j] > 4096 || !(hi[j] > lo[j])) { ctx->err = "bad mesh"; return HPG_ERR_ARG; }
+        if (cells[j] * p - 1 < 1) { ctx->err = "no interior dofs"; return HPG_ERR_ARG; }
+    }
+    GUARD_BEGIN
+    auto P = std::make_unique<Problem>();
+    hpg::HostProblem& H = P->H;
+    H.d = dim;
+    H.p = p;
+    H.n = grad ? p : p - 1;
+    H.kind = kind;
+    H.sign = (kind == HPG_OBSTACLE_LOWER) ? -1.0 : 1.0;
+    for (int j = 0; j < dim; ++j) { H.m[j] = cells[j]; H.lo[j] = lo[j]; H.hi[j] = hi[j]; }
+    hpg::build_problem_constants(H);
+    hpg_default_params(&P->params);
+    P->id = ctx->next_id++;
+    *pid = P->id;
+    ctx->problems[P->id] = std::move(P);
+    return HPG_OK;
+    GUARD_END
+}
+
+hpg_status hpg_problem_free(hpg_ctx* ctx, int pid) {
+    Problem* P = find(ctx, pid);
+    if (!P) return HPG_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    hpg::free_device(*P);
+    ctx->problems.erase(pid);
+    return HPG_OK;
+}
+
+hpg_status hpg_problem_sizes(hpg_ctx* ctx, int pid, size_t* n_u_full, size_t* n_u_interior, size_t* n_psi,
+                             size_t* n_quad) {
+    Problem* P = find(ctx, pid);
+    if (!P) return HPG_ERR_ARG;
+    if (n_u_full) *n_u_full = P->H.Nu_full;
+    if (n_u_interior) *n_u_interior = P->H.Nu0;
+    if (n_psi) *n_psi = P->H.Npsi;
+    if (n_quad) *n_quad = P->H.Nq;
+    return HPG_OK;
+}
+
+hpg_status hpg_set_rhs(hpg_ctx* ctx, int pid, hpg_field_fn f, void* user) {
+    Problem* P = find(ctx, pid);
+    if (!P || !f) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    hpg::compute_rhs(P->H, f, user, false, 0.0);
+    return HPG_OK;
+    GUARD_END
+}
+
+hpg_status hpg_set_rhs_const(hpg_ctx* ctx, int pid, double f) {
+    Problem* P = find(ctx, pid);
+    if (!P || !std::isfinite(f)) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    hpg::compute_rhs(P->H, nullptr, nullptr, true, f);
+    return HPG_OK;
+    GUARD_END
+}
+
+hpg_status hpg_quad_points(hpg_ctx* ctx, int pid, double* pts, size_t len) {
+    Problem* P = find(ctx, pid);
+    if (!P || !pts) return HPG_ERR_ARG;
+    if (len < P->H.Nq * P->H.d) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    std::vector<double> v;
+    hpg::latent_points(P->H, v);
+    std::memcpy(pts, v.data(), v.size() * sizeof(double));
+    return HPG_OK;
+    GUARD_END
+}
+
+hpg_status hpg_set_constraint_values(hpg_ctx* ctx, int pid, const double* phi_q, size_t len) {
+    Problem* P = find(ctx, pid);
+    if (!P || !phi_q) return HPG_ERR_ARG;
+    if (len < P->H.Nq) return HPG_ERR_ARG;
+    for (size_t i = 0; i < P->H.Nq; ++i)
+        if (!std::isfinite(phi_q[i])) { ctx->err = "non-finite constraint value"; return HPG_ERR_NONFINITE; }
+    if (P->H.kind == HPG_GRADIENT)
+        for (size_t i = 0; i < P->H.Nq; ++i)
+            if (!(phi_q[i] > 0.0)) { ctx->err = "gradient constraint must be positive"; return HPG_ERR_ARG; }
+    GUARD_BEGIN
+    hpg::compute_phi(P->H, phi_q);
+    return HPG_OK;
+    GUARD_END
+}
+
+hpg_status hpg_set_constraint(hpg_ctx* ctx, int pid, hpg_field_fn phi, void* user) {
+    Problem* P = find(ctx, pid);
+    if (!P || !phi) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    std::vector<double> pts, vals(P->H.Nq);
+    hpg::latent_points(P->H, pts);
+    phi((int)P->H.Nq, P->H.d, pts.data(), vals.data(), user);
+    return hpg_set_constraint_values(ctx, pid, vals.data(), vals.size());
+    GUARD_END
+}
+
+hpg_status hpg_set_dirichlet(hpg_ctx* ctx, int pid, hpg_field_fn g, void* user) {
+    Problem* P = find(ctx, pid);
+    if (!P) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    hpg::compute_lifting(P->H, g, user);
+    for (double v : P->H.ulift)
+        if (!std::isfinite(v)) { ctx->err = "non-finite Dirichlet data"; return HPG_ERR_NONFINITE; }
+    P->dirichlet_set = g != nullptr;
+    return HPG_OK;
+    GUARD_END
+}
+
+hpg_status hpg_set_alpha_schedule(hpg_ctx* ctx, int pid, double a1, double cap) {
+    Problem* P = find(ctx, pid);
+    if (!P || !(a1 > 0.0) || !(cap > 0.0)) return HPG_ERR_ARG;
+    std::vector<double> al;
+    for (int k = 1; k <= HPG_MAX_ALPHA; ++k) {
+        const double a = std::min(a1 * std::pow(2.0, 0.5 * (k - 1)), cap);
+        al.push_back(a);
+        if (al.size() >= 2 && al[al.size() - 1] == al[al.size() - 2]) break;
+    }
+    P->H.alphas = al;
+    return HPG_OK;
+}
+
+hpg_status hpg_set_alpha_list(hpg_ctx* ctx, int pid, const double* alphas, int count) {
+    Problem* P = find(ctx, pid);
+    if (!P || !alphas || count < 1 || count > HPG_MAX_ALPHA) return HPG_ERR_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!(alphas[i] > 0.0) || !std::isfinite(alphas[i])) return HPG_ERR_ARG;
+    P->H.alphas.assign(alphas, alphas + count);
+    return HPG_OK;
+}
+
+hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params) {
+    Problem* P = find(ctx, pid);
+    if (!P || !params) return HPG_ERR_ARG;
+    if (params->krylov_max < 1 || params->krylov_max > 1000 || params->newton_max < 0 ||
+        !(params->newton_tol > 0.0) || !(params->krylov_rtol > 0.0) || params->beta < 0.0 ||
+        (params->precision != HPG_FP64 && params->precision != HPG_MIXED) || params->ls_max < 0)
+        return HPG_ERR_ARG;
+    const bool realloc = P->alloc_done && params->krylov_max != P->params.krylov_max;
+    if (realloc) hpg::free_device(*P);
+    P->params = *params;
+    return HPG_OK;
+}
+
+static hpg_status ready(hpg_ctx* ctx, Problem* P) {
+    if (!P->H.has_phi) { ctx->err = "constraint not set"; return HPG_ERR_STATE; }
+    if (P->H.alphas.empty()) { ctx->err = "alpha schedule not set"; return HPG_ERR_STATE; }
+    if (P->H.kind != HPG_GRADIENT && P->dirichlet_set) {
+        // the lifting must satisfy the constraint at the boundary Gauss points of the data
+        // (checked against phi at boundary-adjacent latent points is not meaningful; the
+        // paper requires phi >= g on the boundary, which the caller guarantees)
+    }
+    hpg_status s = hpg::alloc_device(ctx, *P);
+    if (s != HPG_OK) return s;
+    return hpg::upload_data(ctx, *P);
+}
+
+hpg_status hpg_solve(hpg_ctx* ctx, int pid) {
+    Problem* P = find(ctx, pid);
+    if (!P) return HPG_ERR_ARG;
+    hpg_status s = cuda_ok(ctx);
+    if (s != HPG_OK) return s;
+    GUARD_BEGIN
+    s = ready(ctx, P);
+    if (s != HPG_OK) return s;
+    return hpg::solve_problem(ctx, *P);
+    GUARD_END
+}
+
+hpg_status hpg_solve_batch(hpg_ctx* ctx, const int* pids, int count) {
+    if (!ctx || !pids || count < 1) return HPG_ERR_ARG;
+    hpg_status s = cuda_ok(ctx);
+    if (s != HPG_OK) return s;
+    GUARD_BEGIN
+    std::vector<Problem*> ps;
+    for (int i = 0; i < count; ++i) {
+        Problem* P = find(ctx, pids[i]);
+        if (!P) return HPG_ERR_ARG;
+        s = ready(ctx, P);
+        if (s != HPG_OK) return s;
+        ps.push_back(P);
+    }
+    return hpg::solve_batch(ctx, ps);
+    GUARD_END
+}
+
+hpg_status hpg_get_u(hpg_ctx* ctx, int pid, double* u_full, size_t len) {
+    Problem* P = find(ctx, pid);
+    if (!P || !u_full) return HPG_ERR_ARG;
+    if (len < P->H.Nu_full) return HPG_ERR_ARG;
+    if (!P->solved) return HPG_ERR_STATE;
+    hpg::HostProblem& H = P->H;
+    std::vector<double> u0(H.Nu0);
+    if (cudaMemcpy(u0.data(), P->D.x, H.Nu0 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HPG_ERR_CUDA;
+    for (size_t i = 0; i < H.Nu_full; ++i) u_full[i] = H.sign * H.ulift[i];
+    for (size_t I = 0; I < H.Nu0; ++I) {
+        size_t ii = I, full = 0, stride = 1;
+        for (int j = 0; j < H.d; ++j) {
+            full += (size_t)H.dir[j].glob_of_int((int)(ii % H.dir[j].n1)) * stride;
+            ii /= H.dir[j].n1;
+            stride *= H.dir[j].N1;
+        }
+        u_full[full] = H.sign * u0[I];
+    }
+    return HPG_OK;
+}
+
+hpg_status hpg_get_psi(hpg_ctx* ctx, int pid, double* psi, size_t len) {
+    Problem* P = find(ctx, pid);
+    if (!P || !psi) return HPG_ERR_ARG;
+    if (len < P->H.Npsi) return HPG_ERR_ARG;
+    if (!P->solved) return HPG_ERR_STATE;
+    if (cudaMemcpy(psi, P->D.x + P->H.Nu0, P->H.Npsi * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HPG_ERR_CUDA;
+    return HPG_OK;
+}
+
+hpg_status hpg_get_stats(hpg_ctx* ctx, int pid, hpg_stats* stats) {
+    Problem* P = find(ctx, pid);
+    if (!P || !stats) return HPG_ERR_ARG;
+    *stats = P->stats;
+    return HPG_OK;
+}
+
+hpg_status hpg_eval_u(hpg_ctx* ctx, int pid, const double* pts, int npts, double* out) {
+    Problem* P = find(ctx, pid);
+    if (!P || !pts || !out || npts < 0) return HPG_ERR_ARG;
+    if (!P->solved) return HPG_ERR_STATE;
+    GUARD_BEGIN
+    std::vector<double> u(P->H.Nu_full);
+    hpg_status s = hpg_get_u(ctx, pid, u.data(), u.size());
+    if (s != HPG_OK) return s;
+    for (int i = 0; i < npts; ++i) out[i] = hpg::eval_u_point(P->H, u, pts + (size_t)i * P->H.d);
+    return HPG_OK;
+    GUARD_END
+}
+
+hpg_status hpg_feasible_u(hpg_ctx* ctx, int pid, double* out_q, size_t len) {
+    Problem* P = find(ctx, pid);
+    if (!P || !out_q) return HPG_ERR_ARG;
+    if (P->H.kind == HPG_GRADIENT) return HPG_ERR_ARG;
+    if (len < P->H.Nq) return HPG_ERR_ARG;
+    if (!P->solved) return HPG_ERR_STATE;
+    // u~ = phi - exp(-psi) at the latent Gauss points (eq. pG), in the caller's sign
+    hpg::HostProblem& H = P->H;
+    std::vector<double> psi(H.Npsi);
+    if (cudaMemcpy(psi.data(), P->D.x + H.Nu0, H.Npsi * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HPG_ERR_CUDA;
+    const int n = H.n;
+    for (size_t c = 0; c < H.Nc; ++c)
+        for (size_t q = 0; q < H.nloc; ++q) {
+            double v = 0.0;
+            for (size_t k = 0; k < H.nloc; ++k) {
+                size_t qq = q, kk = k;
+                double w = 1.0;
+                for (int j = 0; j < H.d; ++j) {
+                    w *= H.Vq[(qq % n) * n + (kk % n)];
+                    qq /= n;
+                    kk /= n;
+                }
+                v += w * psi[c * H.nloc + k];
+            }
+            out_q[c * H.nloc + q] = H.sign * (H.phiq[c * H.nloc + q] - std::exp(-v));
+        }
+    return HPG_OK;
+}
+
+hpg_status hpg_get_kernel_times(hpg_ctx* ctx, int pid, double* ms, long long* launches, int count) {
+    Problem* P = find(ctx, pid);
+    if (!P || count < 0) return HPG_ERR_ARG;
+    for (int i = 0; i < count && i < HPG_K_COUNT; ++i) {
+        if (ms) ms[i] = P->timer.ms[i];
+        if (launches) launches[i] = P->timer.launches[i];
+    }
+    return HPG_OK;
+}
+
+hpg_status hpg_reset_kernel_times(hpg_ctx* ctx, int pid) {
+    Problem* P = find(ctx, pid);
+    if (!P) return HPG_ERR_ARG;
+    for (int i = 0; i < HPG_K_COUNT; ++i) { P->timer.ms[i] = 0.0; P->timer.launches[i] = 0; }
+    return HPG_OK;
+}
+
+// ------------------------------------------------------------ component operators
+static hpg_status op_ready(hpg_ctx* ctx, Problem* P) {
+    hpg_status s = cuda_ok(ctx);
+    if (s != HPG_OK) return s;
+    return ready(ctx, P);
+}
+
+hpg_status hpg_set_state(hpg_ctx* ctx, int pid, const double* u_full, const double* psi, const double* psi_prev,
+                         double alpha) {
+    Problem* P = find(ctx, pid);
+    if (!P || !u_full || !psi || !psi_prev || !(alpha > 0.0)) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    hpg_status s = op_ready(ctx, P);
+    if (s != HPG_OK) return s;
+    return hpg::op_set_state(ctx, *P, u_full, psi, psi_prev, alpha);
+    GUARD_END
+}
+
+#define OP_PROLOGUE(need)                                        \
+    Problem* P = find(ctx, pid);                                 \
+    if (!P) return HPG_ERR_ARG;                                  \
+    if (!P->alloc_done || P->state_alpha <= 0.0) return HPG_ERR_STATE; \
+    if (len < (need)) return HPG_ERR_ARG;                        \
+    if (cuda_ok(ctx) != HPG_OK) return HPG_ERR_CUDA;
+
+hpg_status hpg_residual(hpg_ctx* ctx, int pid, double* F, size_t len, double* norm) {
+    OP_PROLOGUE(P->H.Nu0 + P->H.Npsi)
+    if (!F) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    return hpg::op_residual(ctx, *P, F, norm);
+    GUARD_END
+}
+
+hpg_status hpg_apply_newton(hpg_ctx* ctx, int pid, const double* x, double* y, size_t len) {
+    OP_PROLOGUE(P->H.Nu0 + P->H.Npsi)
+    if (!x || !y) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    return hpg::op_apply_newton(ctx, *P, x, y);
+    GUARD_END
+}
+
+hpg_status hpg_apply_stiffness_inv(hpg_ctx* ctx, int pid, int precision, const double* x, double* y, size_t len) {
+    OP_PROLOGUE(P->H.Nu0)
+    if (!x || !y) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    return hpg::op_stiffness_inv(ctx, *P, precision, x, y);
+    GUARD_END
+}
+
+hpg_status hpg_factor_precond(hpg_ctx* ctx, int pid, int precision, double* blocks, size_t len) {
+    Problem* P = find(ctx, pid);
+    if (!P) return HPG_ERR_ARG;
+    if (!P->alloc_done || P->state_alpha <= 0.0) return HPG_ERR_STATE;
+    if (blocks && len < P->H.Nc * P->H.nb * P->H.nb) return HPG_ERR_ARG;
+    if (cuda_ok(ctx) != HPG_OK) return HPG_ERR_CUDA;
+    GUARD_BEGIN
+    return hpg::op_factor(ctx, *P, precision, blocks);
+    GUARD_END
+}
+
+hpg_status hpg_apply_precond_inv(hpg_ctx* ctx, int pid, int precision, const double* x, double* y, size_t len) {
+    OP_PROLOGUE(P->H.Npsi)
+    if (!x || !y) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    return hpg::op_precond_inv(ctx, *P, precision, x, y);
+    GUARD_END
+}
+
+hpg_status hpg_apply_schur(hpg_ctx* ctx, int pid, int precision, const double* x, double* y, size_t len) {
+    OP_PROLOGUE(P->H.Npsi)
+    if (!x || !y) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    return hpg::op_schur(ctx, *P, precision, x, y);
+    GUARD_END
+}
+
+hpg_status hpg_newton_direction(hpg_ctx* ctx, int pid, int precision, double rtol, double* delta, size_t len,
+                                int* krylov_its) {
+    OP_PROLOGUE(P->H.Nu0 + P->H.Npsi)
+    if (!delta || !(rtol > 0.0)) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    return hpg::op_newton_direction(ctx, *P, precision, rtol, delta, krylov_its);
+    GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Device-side views of a problem and the kernel launchers of libhpg.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hpg_internal.h"
+
+namespace hpg {
+
+// A 1D operator in padded-ELL form (kEll entries per row; cnt[r] used).
+// For Gram operators the column packs (cell << 8) | k.
+template <typename T>
+struct Sten {
+    const int* cnt;
+    const int* col;
+    const T* val;
+};
+
+// Everything a kernel needs to know about one problem, for compute type T.
+template <typename T>
+struct Geo {
+    int d, n, ncomp, kind;
+    int m[kMaxDim], n1[kMaxDim];
+    long long Nu0, Nc, nloc, nb, Npsi;
+    Sten<T> A[kMaxDim], M[kMaxDim];          // interior x interior
+    Sten<T> B[kMaxDim], BT[kMaxDim];         // interior -> psi-1D, psi-1D -> interior
+    Sten<T> Bd[kMaxDim], BdT[kMaxDim];       // derivative Gram (gradient kind)
+    const T* Vq;                              // n x n : P_k(y_q)
+    const T* wq;                              // n
+    T detJ;
+    const T* Mpsi;                            // nloc (one component)
+    const T* Kpsi;                            // nloc x nloc (gradient E_beta)
+    const T* C;                               // nloc x nloc (obstacle S-hat constant part)
+    const T* V[kMaxDim];                      // n1 x n1 fast-diagonalisation eigenvectors
+    const T* lam[kMaxDim];                    // n1 eigenvalues
+};
+
+// Number of values stored per Gauss point by the evaluation kernel:
+// obstacle: 1 (w |J| exp(-psi)); gradient: packed symmetric d x d Jacobian * w|J|.
+inline int gauss_stride(int kind, int d) { return kind == HPG_GRADIENT ? d * (d + 1) / 2 : 1; }
+
+// ------------------------------------------------------------ launchers
+// Each launcher enqueues on `s` and returns the CUDA error of the launch.
+
+// Latent nonlinearity at Gauss points: gw (FP64, Nc*nloc*gstride), gwf (FP32
+// copy, may be null), eg = projection onto zeta (FP64, Npsi), flag |= 1 on
+// psi < -700 (obstacle) or non-finite values.
+cudaError_t launch_eval(const Geo<double>& g, const double* psi, const double* phiq, double* gw, float* gwf,
+                        double* eg, int* flag, cudaStream_t s);
+
+// F_u = alpha A u + alpha rA + B (psi - psi_prev) - alpha bf;  F_psi = B^T u + rB + sgn*eg - phiz.
+// Writes F (Nu0 + Npsi) and block partial sums of squares into part (see n_res_partials).
+cudaError_t launch_residual(const Geo<double>& g, const double* u, const double* psi, const double* psi_prev,
+                            const double* eg, const double* rA, const double* rB, const double* bf,
+                            const double* phiz, double alpha, double* F, double* part, cudaStream_t s);
+int n_res_partials(const Geo<double>& g);
+
+// Deterministic reduction of `count` partials into out[0] (one block).
+cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaStream_t s);
+
+// Assemble -S-hat cell blocks, Cholesky, invert: Sinv (Nc x nb x nb, precision T)
+// holds (-S-hat)^{-1}.  If `dump` is non-null the assembled -S-hat blocks are written there.
+template <typename T>
+cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double beta, T* Sinv, double* dump,
+                          int* flag, cudaStream_t s);
+size_t factor_smem_bytes(int nb, int elem);
+
+// z = -Sinv v (per cell), in/out precision mixing: v (Tin), z (Tout).
+template <typename T, typename Tin, typename Tout>
+cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s);
+
+// y = B z  (psi -> interior u);  Tin/Tout storage, T compute.
+template <typename T, typename Tin, typename Tout>
+cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s);
+
+// y = B^T x (interior u -> psi).
+template <typename T, typename Tin, typename Tout>
+cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t s);
+
+// y = A_alpha^{-1} x (interior) by fast diagonalisation; work1/work2 scratch of Nu0.
+template <typename T>
+cudaError_t launch_fdm(const Geo<T>& g, double alpha, const T* x, T* y, T* work1, T* work2, cudaStream_t s);
+
+// w = -(D z + E z + B^T t)  (per cell), D from gw.  z, t in T; w in Tout.
+template <typename T, typename Tout>
+cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T* z, const T* t, Tout* w,
+                              cudaStream_t s);
+
+// FP64 matrix-free Newton apply y = G x (eq. pG-matrix) split in two kernels.
+cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
+                                const double* x, double* y, cudaStream_t s);
+
+// y = A x (interior), FP64 (used by tests of the stiffness inverse).
+cudaError_t launch_aapply(const Geo<double>& g, const double* x, double* y, cudaStream_t s);
+
+// ---- vector helpers (FP64 unless typed)
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const Tin* x, Tout* y, long long n, cudaStream_t s);
+// y = a*x + b*y
+cudaError_t launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s);
+// y = x - b*z  (elementwise, z of precision T)
+template <typename T>
+cudaError_t launch_sub_scaled(const double* x, double b, const T* z, double* y, long long n, cudaStream_t s);
+// trial state: xt = x - lam * dx
+cudaError_t launch_trial(const double* x, const double* dx, double lam, double* xt, long long n, cudaStream_t s);
+// partial sums of squares of x into part (returns number of partials through nparts)
+cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts, cudaStream_t s);
+
+// ---- GMRES (right-preconditioned, unrestarted), all state on the device.
+struct GmresDev {
+    double* Vb;       // (kmax+1) x N basis
+    double* H;        // kmax columns of (kmax+1)
+    double* cs;       // kmax
+    double* sn;       // kmax
+    double* gv;       // kmax+1
+    double* part;     // partial sums scratch (>= blocks * (kmax+1))
+    double* scal;     // [0] beta0, [1] resid estimate, [2] tol*beta0, [3] h_{j+1,j}
+    int* iflag;       // [0] converged flag, [1] last completed iteration count, [2] breakdown
+    unsigned int* counter;  // block-completion counter for last-block reductions
+    double* y;        // kmax coefficients
+    int kmax;
+    long long N;
+    int blocks;       // blocks used by the dot/update kernels
+};
+// r0 = b: beta0 = ||b||, V_0 = b / beta0, g = beta0 e_1, tol*beta0 stored.
+cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s);
+// After w (= S Shat^{-1} V_j) has been written into Vb[j+1]: CGS2 orthogonalise,
+// normalise, Givens update and convergence flag.  Skipped on device if converged.
+cudaError_t gmres_arnoldi(GmresDev& G, int j, cudaStream_t s);
+// Solve H y = g for k columns and form x = sum_i y_i V_i (x of length N).
+cudaError_t gmres_finish(GmresDev& G, int k, double* x, cudaStream_t s);
+
+}  // namespace hpg

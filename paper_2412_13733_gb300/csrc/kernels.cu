@@ -1,0 +1,1107 @@
+// CUDA kernels of libhpg (sm_103a).  Every step of the hpG Newton--Krylov path
+// runs here: Gauss evaluation of the latent nonlinearity, residuals, the
+// matrix-free Newton and Schur operators by sum factorisation and sparse
+// Kronecker stencils, the S-hat cell-block factorisation, the fast-diagonalisation
+// inverse of A_alpha, and GMRES.
+#include <cfloat>
+#include <cmath>
+
+#include "device.h"
+
+namespace hpg {
+
+namespace {
+
+constexpr int kRedThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+    // deterministic block reduction (fixed tree)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+
+__device__ __forceinline__ void decompose(long long i, int d, const int* n1, int* ix) {
+    for (int j = 0; j < d; ++j) { ix[j] = (int)(i % n1[j]); i /= n1[j]; }
+}
+
+// sum over the tensor stencil of prod_j S_j[r_j] applied to an interior-u vector
+template <int D, typename T, typename Tx>
+__device__ __forceinline__ T gather_u(const Sten<T>* const* S, const int* r, const int* n1, const Tx* x) {
+    T s = T(0);
+    if (D == 2) {
+        const int c0 = S[0]->cnt[r[0]], c1 = S[1]->cnt[r[1]];
+        const int* col0 = S[0]->col + (size_t)r[0] * kEll;
+        const T* val0 = S[0]->val + (size_t)r[0] * kEll;
+        for (int e1 = 0; e1 < c1; ++e1) {
+            const long long base = (long long)S[1]->col[(size_t)r[1] * kEll + e1] * n1[0];
+            T t = T(0);
+            for (int e0 = 0; e0 < c0; ++e0) t += val0[e0] * (T)x[base + col0[e0]];
+            s += S[1]->val[(size_t)r[1] * kEll + e1] * t;
+        }
+    } else {
+        const int c0 = S[0]->cnt[r[0]], c1 = S[1]->cnt[r[1]], c2 = S[2]->cnt[r[2]];
+        const int* col0 = S[0]->col + (size_t)r[0] * kEll;
+        const T* val0 = S[0]->val + (size_t)r[0] * kEll;
+        for (int e2 = 0; e2 < c2; ++e2) {
+            const long long b2 = (long long)S[2]->col[(size_t)r[2] * kEll + e2] * n1[1];
+            T t2 = T(0);
+            for (int e1 = 0; e1 < c1; ++e1) {
+                const long long base = (b2 + S[1]->col[(size_t)r[1] * kEll + e1]) * n1[0];
+                T t = T(0);
+                for (int e0 = 0; e0 < c0; ++e0) t += val0[e0] * (T)x[base + col0[e0]];
+                t2 += S[1]->val[(size_t)r[1] * kEll + e1] * t;
+            }
+            s += S[2]->val[(size_t)r[2] * kEll + e2] * t2;
+        }
+    }
+    return s;
+}
+
+// (A x)[r] with A = sum_k (x)_j (j == k ? A_j : M_j)
+template <int D, typename T, typename Tx>
+__device__ __forceinline__ T apply_A_row(const Geo<T>& g, const int* r, const Tx* x) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const Sten<T>* S[kMaxDim];
+#pragma unroll
+        for (int j = 0; j < D; ++j) S[j] = (j == k) ? &g.A[j] : &g.M[j];
+        s += gather_u<D, T, Tx>(S, r, g.n1, x);
+    }
+    return s;
+}
+
+// (B z)[r] (psi -> interior u).  Column packing: (cell << 8) | k.
+// If z2 != nullptr the input is z - z2 (used for psi - psi_prev).
+template <int D, typename T, typename Tz>
+__device__ __forceinline__ T apply_B_row(const Geo<T>& g, const int* r, const Tz* z, const Tz* z2) {
+    T s = T(0);
+    const int n = g.n;
+    for (int comp = 0; comp < g.ncomp; ++comp) {
+        const Sten<T>* S[kMaxDim];
+#pragma unroll
+        for (int j = 0; j < D; ++j) S[j] = (g.kind == HPG_GRADIENT && j == comp) ? &g.Bd[j] : &g.B[j];
+        int cnt[kMaxDim];
+#pragma unroll
+        for (int j = 0; j < D; ++j) cnt[j] = S[j]->cnt[r[j]];
+        if (D == 2) {
+            for (int e1 = 0; e1 < cnt[1]; ++e1) {
+                const int p1 = S[1]->col[(size_t)r[1] * kEll + e1];
+                const T v1 = S[1]->val[(size_t)r[1] * kEll + e1];
+                const int c1 = p1 >> 8, k1 = p1 & 255;
+                T t = T(0);
+                for (int e0 = 0; e0 < cnt[0]; ++e0) {
+                    const int p0 = S[0]->col[(size_t)r[0] * kEll + e0];
+                    const int c0 = p0 >> 8, k0 = p0 & 255;
+                    const long long cell = c0 + (long long)g.m[0] * c1;
+                    const long long idx = (cell * g.ncomp + comp) * g.nloc + k0 + n * k1;
+                    T zv = (T)z[idx];
+                    if (z2) zv -= (T)z2[idx];
+                    t += S[0]->val[(size_t)r[0] * kEll + e0] * zv;
+                }
+                s += v1 * t;
+            }
+        } else {
+            for (int e2 = 0; e2 < cnt[2]; ++e2) {
+                const int p2 = S[2]->col[(size_t)r[2] * kEll + e2];
+                const T v2 = S[2]->val[(size_t)r[2] * kEll + e2];
+                const int c2 = p2 >> 8, k2 = p2 & 255;
+                T t2 = T(0);
+                for (int e1 = 0; e1 < cnt[1]; ++e1) {
+                    const int p1 = S[1]->col[(size_t)r[1] * kEll + e1];
+                    const T v1 = S[1]->val[(size_t)r[1] * kEll + e1];
+                    const int c1 = p1 >> 8, k1 = p1 & 255;
+                    T t = T(0);
+                    for (int e0 = 0; e0 < cnt[0]; ++e0) {
+                        const int p0 = S[0]->col[(size_t)r[0] * kEll + e0];
+                        const int c0 = p0 >> 8, k0 = p0 & 255;
+                        const long long cell = c0 + (long long)g.m[0] * (c1 + (long long)g.m[1] * c2);
+                        const long long idx = (cell * g.ncomp + comp) * g.nloc + k0 + n * (k1 + n * k2);
+                        T zv = (T)z[idx];
+                        if (z2) zv -= (T)z2[idx];
+                        t += S[0]->val[(size_t)r[0] * kEll + e0] * zv;
+                    }
+                    t2 += v1 * t;
+                }
+                s += v2 * t2;
+            }
+        }
+    }
+    return s;
+}
+
+// (B^T x)[cell, comp, k] (interior u -> psi)
+template <int D, typename T, typename Tx>
+__device__ __forceinline__ T apply_BT_entry(const Geo<T>& g, const int* cm, int comp, const int* km, const Tx* x) {
+    const Sten<T>* S[kMaxDim];
+    int r[kMaxDim];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        S[j] = (g.kind == HPG_GRADIENT && j == comp) ? &g.BdT[j] : &g.BT[j];
+        r[j] = cm[j] * g.n + km[j];
+    }
+    return gather_u<D, T, Tx>(S, r, g.n1, x);
+}
+
+template <typename T>
+__device__ __forceinline__ void cell_multi(const Geo<T>& g, long long c, int* cm) {
+    for (int j = 0; j < g.d; ++j) { cm[j] = (int)(c % g.m[j]); c /= g.m[j]; }
+}
+
+// One sum-factorisation pass along axis `ax` over `cnt` tensors of n^d each:
+// out[.., a, ..] = sum_k M(a, k) in[.., k, ..] with M(a,k) = mat[a*n+k] (or mat[k*n+a] if transp)
+template <typename T>
+__device__ __forceinline__ void sf_pass(const T* in, T* out, const T* mat, bool transp, int n, int nloc, int cnt,
+                                        int stride) {
+    for (int i = threadIdx.x; i < nloc * cnt; i += blockDim.x) {
+        const int t = i / nloc, li = i - t * nloc;
+        const int a = (li / stride) % n;
+        const int base = t * nloc + li - a * stride;
+        T s = T(0);
+        if (!transp)
+            for (int k = 0; k < n; ++k) s += mat[a * n + k] * in[base + k * stride];
+        else
+            for (int k = 0; k < n; ++k) s += mat[k * n + a] * in[base + k * stride];
+        out[i] = s;
+    }
+}
+
+}  // namespace
+
+// ====================================================================== eval
+// Obstacle: g_q = w_q |J| exp(-psi(x_q)), eg = V^T g per cell (Section 5, Quadrature).
+// Gradient: psi_q (d comps), s = 1 + |psi_q|^2, G = phi psi / sqrt(s) projected into eg,
+// Jacobian J_ab = phi (s d_ab - psi_a psi_b) s^{-3/2} (times w|J|) packed into gw.
+__global__ void k_eval(Geo<double> g, const double* __restrict__ psi, const double* __restrict__ phiq,
+                       double* __restrict__ gw, float* __restrict__ gwf, double* __restrict__ eg,
+                       int* __restrict__ flag) {
+    extern __shared__ double sm[];
+    const int n = g.n, nloc = (int)g.nloc, nc = g.ncomp;
+    double* a = sm;
+    double* b = sm + nc * nloc;
+    double* Vq = sm + 2 * nc * nloc;
+    const long long c = blockIdx.x;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Vq[i] = g.Vq[i];
+    for (int i = threadIdx.x; i < nc * nloc; i += blockDim.x) a[i] = psi[c * nc * nloc + i];
+    __syncthreads();
+    double *in = a, *out = b;
+    int stride = 1;
+    for (int ax = 0; ax < g.d; ++ax) {
+        sf_pass(in, out, Vq, false, n, nloc, nc, stride);
+        __syncthreads();
+        double* t = in; in = out; out = t;
+        stride *= n;
+    }
+    // in: Gauss values per component
+    const int gs = (g.kind == HPG_GRADIENT) ? g.d * (g.d + 1) / 2 : 1;
+    for (int q = threadIdx.x; q < nloc; q += blockDim.x) {
+        double w = g.detJ;
+        int qq = q;
+        for (int ax = 0; ax < g.d; ++ax) { w *= g.wq[qq % n]; qq /= n; }
+        const long long gq = c * nloc + q;
+        if (g.kind != HPG_GRADIENT) {
+            const double pv = in[q];
+            if (!(pv >= -700.0) || !isfinite(pv)) atomicOr(flag, 1);
+            const double v = w * exp(-pv);
+            out[q] = v;
+            gw[gq] = v;
+            if (gwf) gwf[gq] = (float)v;
+        } else {
+            double pv[kMaxDim];
+            double s = 1.0;
+            for (int k = 0; k < nc; ++k) { pv[k] = in[k * nloc + q]; s += pv[k] * pv[k]; }
+            if (!isfinite(s)) atomicOr(flag, 1);
+            const double ph = phiq[gq];
+            const double rs = 1.0 / sqrt(s);
+            const double r3 = rs * rs * rs;
+            for (int k = 0; k < nc; ++k) out[k * nloc + q] = w * ph * pv[k] * rs;
+            int e = 0;
+            for (int k = 0; k < nc; ++k)
+                for (int l = k; l < nc; ++l, ++e) {
+                    const double jv = w * ph * ((k == l ? s : 0.0) - pv[k] * pv[l]) * r3;
+                    gw[gq * gs + e] = jv;
+                    if (gwf) gwf[gq * gs + e] = (float)jv;
+                }
+        }
+    }
+    __syncthreads();
+    { double* t = in; in = out; out = t; }
+    stride = 1;
+    for (int ax = 0; ax < g.d; ++ax) {
+        sf_pass(in, out, Vq, true, n, nloc, nc, stride);
+        __syncthreads();
+        double* t = in; in = out; out = t;
+        stride *= n;
+    }
+    for (int i = threadIdx.x; i < nc * nloc; i += blockDim.x) eg[c * nc * nloc + i] = in[i];
+}
+
+cudaError_t launch_eval(const Geo<double>& g, const double* psi, const double* phiq, double* gw, float* gwf,
+                        double* eg, int* flag, cudaStream_t s) {
+    const size_t smem = (size_t)(2 * g.ncomp * g.nloc + g.n * g.n) * sizeof(double);
+    const int threads = g.nloc * g.ncomp >= 256 ? 256 : 128;
+    k_eval<<<(unsigned)g.Nc, threads, smem, s>>>(g, psi, phiq, gw, gwf, eg, flag);
+    return cudaGetLastError();
+}
+
+// ================================================================== residual
+template <int D>
+__global__ void k_residual_u(Geo<double> g, const double* __restrict__ u, const double* __restrict__ psi,
+                             const double* __restrict__ psi_prev, const double* __restrict__ rA,
+                             const double* __restrict__ bf, double alpha, double* __restrict__ F,
+                             double* __restrict__ part) {
+    __shared__ double sh[32];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < g.Nu0) {
+        int r[kMaxDim];
+        decompose(i, D, g.n1, r);
+        const double Au = apply_A_row<D, double, double>(g, r, u);
+        const double Bp = apply_B_row<D, double, double>(g, r, psi, psi_prev);
+        v = alpha * (Au + rA[i] - bf[i]) + Bp;
+        F[i] = v;
+    }
+    v = block_sum(v * v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+template <int D>
+__global__ void k_residual_psi(Geo<double> g, const double* __restrict__ u, const double* __restrict__ eg,
+                               const double* __restrict__ rB, const double* __restrict__ phiz,
+                               double* __restrict__ F, double* __restrict__ part) {
+    __shared__ double sh[32];
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (j < g.Npsi) {
+        const long long cell = j / g.nb;
+        const int rem = (int)(j - cell * g.nb);
+        const int comp = rem / (int)g.nloc;
+        int km[kMaxDim], cm[kMaxDim];
+        int kk = rem - comp * (int)g.nloc;
+        for (int t = 0; t < D; ++t) { km[t] = kk % g.n; kk /= g.n; }
+        cell_multi(g, cell, cm);
+        const double bt = apply_BT_entry<D, double, double>(g, cm, comp, km, u);
+        if (g.kind == HPG_GRADIENT) v = bt + rB[j] - eg[j];
+        else v = bt + rB[j] + eg[j] - phiz[j];
+        F[j] = v;
+    }
+    v = block_sum(v * v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+int n_res_partials(const Geo<double>& g) {
+    return (int)((g.Nu0 + 255) / 256 + (g.Npsi + 255) / 256);
+}
+
+cudaError_t launch_residual(const Geo<double>& g, const double* u, const double* psi, const double* psi_prev,
+                            const double* eg, const double* rA, const double* rB, const double* bf,
+                            const double* phiz, double alpha, double* F, double* part, cudaStream_t s) {
+    const int bu = (int)((g.Nu0 + 255) / 256), bp = (int)((g.Npsi + 255) / 256);
+    if (g.d == 2) {
+        k_residual_u<2><<<bu, 256, 0, s>>>(g, u, psi, psi_prev, rA, bf, alpha, F, part);
+        k_residual_psi<2><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
+    } else {
+        k_residual_u<3><<<bu, 256, 0, s>>>(g, u, psi, psi_prev, rA, bf, alpha, F, part);
+        k_residual_psi<3><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void k_reduce_sum(const double* __restrict__ part, int count, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) v += part[i];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) out[0] = v;
+}
+
+cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaStream_t s) {
+    k_reduce_sum<<<1, 1024, 0, s>>>(part, count, out);
+    return cudaGetLastError();
+}
+
+// ==================================================================== factor
+// Assemble -S-hat_K = D_K + beta M_K + C/alpha (obstacle) or D_K + beta K_K (gradient)
+// by sum factorisation over the Gauss points, factor it (Cholesky, L L^T), invert
+// L (X = L^{-1}, kept transposed in the upper triangle), and write (-S-hat_K)^{-1} = X^T X.
+template <typename T>
+__device__ void assemble_D_block(const Geo<T>& g, const T* __restrict__ gw, long long cell, int gs, int ge,
+                                 const T* Vq, T* bufA, T* bufB) {
+    // stage 0: X0[q] = gw[q]; stage s contracts q_{d-s-1}; final X_d = D (nloc x nloc) in bufA
+    const int n = g.n, d = g.d, nloc = (int)g.nloc;
+    T* cur = ((d % 2) == 0) ? bufA : bufB;
+    for (int q = threadIdx.x; q < nloc; q += blockDim.x) cur[q] = gw[(cell * nloc + q) * gs + ge];
+    __syncthreads();
+    int nq_out = nloc;      // n^{d-s}
+    int ns = 1;             // n^s
+    for (int st = 0; st < d; ++st) {
+        T* nxt = (((d - st - 1) % 2) == 0) ? bufA : bufB;
+        const int nq_new = nq_out / n;          // n^{d-s-1}
+        const int ns_new = ns * n;
+        const int total = nq_new * ns_new * ns_new;
+        for (int o = threadIdx.x; o < total; o += blockDim.x) {
+            const int J = o % ns_new;
+            const int rest = o / ns_new;
+            const int I = rest % ns_new;
+            const int Qp = rest / ns_new;
+            const int i = I % n, Is = I / n;
+            const int j = J % n, Js = J / n;
+            T s = T(0);
+            for (int q = 0; q < n; ++q) {
+                const T w = Vq[q * n + i] * Vq[q * n + j];
+                s += w * cur[(((long long)(Qp + nq_new * q) * ns + Is) * ns) + Js];
+            }
+            nxt[o] = s;
+        }
+        __syncthreads();
+        cur = nxt;
+        nq_out = nq_new;
+        ns = ns_new;
+    }
+}
+
+template <typename T>
+__global__ void k_factor(Geo<T> g, const T* __restrict__ gw, T alpha_inv, T beta, T* __restrict__ Sinv,
+                         double* __restrict__ dump, int* __restrict__ flag, T* __restrict__ gwork, int use_smem) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = g.n, nloc = (int)g.nloc, nb = (int)g.nb, nc = g.ncomp;
+    const long long cell = blockIdx.x;
+    // workspace layout: A (nb^2) | bufA (nloc^2, gradient only) | bufB (n^{2d-1}) | Vq (n^2) | ldiag (nb)
+    size_t nbuf_b = 1;
+    for (int t = 0; t < 2 * g.d - 1; ++t) nbuf_b *= n;
+    T* base = use_smem ? sm : gwork + cell * ((size_t)nb * nb + (nc > 1 ? (size_t)nloc * nloc : 0) + nbuf_b + n * n + nb);
+    T* A = base;
+    T* bufA = (nc > 1) ? A + (size_t)nb * nb : A;
+    T* bufB = bufA + (nc > 1 ? (size_t)nloc * nloc : (size_t)nb * nb);
+    T* Vq = bufB + nbuf_b;
+    T* ldiag = Vq + n * n;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Vq[i] = g.Vq[i];
+    __syncthreads();
+    const int gs = (g.kind == HPG_GRADIENT) ? g.d * (g.d + 1) / 2 : 1;
+    if (nc == 1) {
+        assemble_D_block(g, gw, cell, 1, 0, Vq, A, bufB);
+        for (int o = threadIdx.x; o < nloc * nloc; o += blockDim.x) {
+            const int I = o / nloc, J = o % nloc;
+            T v = A[o] + g.C[o] * alpha_inv;
+            if (I == J) v += beta * g.Mpsi[I];
+            A[o] = v;
+        }
+    } else {
+        int e = 0;
+        for (int ca = 0; ca < nc; ++ca)
+            for (int cb = ca; cb < nc; ++cb, ++e) {
+                assemble_D_block(g, gw, cell, gs, e, Vq, bufA, bufB);
+                for (int o = threadIdx.x; o < nloc * nloc; o += blockDim.x) {
+                    const int I = o / nloc, J = o % nloc;
+                    T v = bufA[o];
+                    if (ca == cb) v += beta * g.Kpsi[o];
+                    A[(size_t)(ca * nloc + I) * nb + cb * nloc + J] = v;
+                    A[(size_t)(cb * nloc + J) * nb + ca * nloc + I] = v;
+                }
+                __syncthreads();
+            }
+    }
+    __syncthreads();
+    if (dump)
+        for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) dump[cell * nb * nb + o] = (double)A[o];
+    // Cholesky (right-looking), lower triangle
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < nb; ++k) {
+        if (threadIdx.x == 0) {
+            T pv = A[(size_t)k * nb + k];
+            if (!(pv > T(0))) { bad = 1; pv = T(1); }
+            A[(size_t)k * nb + k] = sqrt(pv);
+        }
+        __syncthreads();
+        const T lkk = A[(size_t)k * nb + k];
+        for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) A[(size_t)i * nb + k] /= lkk;
+        __syncthreads();
+        const int rem = nb - k - 1;
+        for (int o = threadIdx.x; o < rem * rem; o += blockDim.x) {
+            const int i = k + 1 + o / rem, j = k + 1 + o % rem;
+            if (j <= i) A[(size_t)i * nb + j] -= A[(size_t)i * nb + k] * A[(size_t)j * nb + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && bad) atomicOr(flag, 2);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) ldiag[i] = A[(size_t)i * nb + i];
+    __syncthreads();
+    // X = L^{-1}, column j per thread; X[i][j] stored at A[j][i] (i >= j)
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        A[(size_t)j * nb + j] = T(1) / ldiag[j];
+        for (int i = j + 1; i < nb; ++i) {
+            T s = T(0);
+            for (int k = j; k < i; ++k) s += A[(size_t)i * nb + k] * A[(size_t)j * nb + k];
+            A[(size_t)j * nb + i] = -s / ldiag[i];
+        }
+    }
+    __syncthreads();
+    // Sinv[i][j] = sum_{k >= max(i,j)} X[k][i] X[k][j] = sum_k A[i][k] A[j][k]
+    T* out = Sinv + cell * (long long)nb * nb;
+    for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
+        const int i = o / nb, j = o % nb;
+        const int k0 = i > j ? i : j;
+        T s = T(0);
+        for (int k = k0; k < nb; ++k) s += A[(size_t)i * nb + k] * A[(size_t)j * nb + k];
+        out[o] = s;
+    }
+}
+
+static size_t factor_ws_elems(int n, int d, int nb, int nc) {
+    size_t nloc = 1, nbuf_b = 1;
+    for (int t = 0; t < d; ++t) nloc *= n;
+    for (int t = 0; t < 2 * d - 1; ++t) nbuf_b *= n;
+    return (size_t)nb * nb + (nc > 1 ? nloc * nloc : 0) + nbuf_b + (size_t)n * n + nb;
+}
+
+size_t factor_smem_bytes(int nb, int elem) { return (size_t)nb * nb * elem; }
+
+template <typename T>
+cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double beta, T* Sinv, double* dump,
+                          int* flag, cudaStream_t s) {
+    const size_t elems = factor_ws_elems(g.n, g.d, (int)g.nb, g.ncomp);
+    const size_t bytes = elems * sizeof(T);
+    static T* gwork = nullptr;
+    static size_t gwork_elems = 0;
+    int use_smem = bytes <= 200 * 1024;
+    if (use_smem) {
+        cudaFuncSetAttribute(k_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    } else {
+        const size_t need = elems * (size_t)g.Nc;
+        if (need > gwork_elems) {
+            if (gwork) cudaFree(gwork);
+            if (cudaMalloc(&gwork, need * sizeof(T)) != cudaSuccess) { gwork = nullptr; gwork_elems = 0; return cudaErrorMemoryAllocation; }
+            gwork_elems = need;
+        }
+    }
+    k_factor<T><<<(unsigned)g.Nc, 256, use_smem ? bytes : 0, s>>>(g, gw, (T)(1.0 / alpha), (T)beta, Sinv, dump,
+                                                                 flag, gwork, use_smem);
+    return cudaGetLastError();
+}
+
+// =================================================================== precond
+template <typename T, typename Tin, typename Tout>
+__global__ void k_precond(Geo<T> g, const T* __restrict__ Sinv, const Tin* __restrict__ v, Tout* __restrict__ z) {
+    extern __shared__ unsigned char smraw[];
+    T* vs = reinterpret_cast<T*>(smraw);
+    const int nb = (int)g.nb;
+    const long long cell = blockIdx.x;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) vs[i] = (T)v[cell * nb + i];
+    __syncthreads();
+    const T* S = Sinv + cell * (long long)nb * nb;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        T s = T(0);
+        for (int k = 0; k < nb; ++k) s += S[(size_t)k * nb + i] * vs[k];
+        z[cell * nb + i] = (Tout)(-s);
+    }
+}
+
+template <typename T, typename Tin, typename Tout>
+cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s) {
+    const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
+    k_precond<T, Tin, Tout><<<(unsigned)g.Nc, threads, g.nb * sizeof(T), s>>>(g, Sinv, v, z);
+    return cudaGetLastError();
+}
+
+// ==================================================================== B, B^T
+template <int D, typename T, typename Tin, typename Tout>
+__global__ void k_bapply(Geo<T> g, const Tin* __restrict__ z, Tout* __restrict__ y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.Nu0) return;
+    int r[kMaxDim];
+    decompose(i, D, g.n1, r);
+    y[i] = (Tout)apply_B_row<D, T, Tin>(g, r, z, (const Tin*)nullptr);
+}
+
+template <typename T, typename Tin, typename Tout>
+cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s) {
+    const unsigned b = (unsigned)((g.Nu0 + 255) / 256);
+    if (g.d == 2) k_bapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y);
+    else k_bapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y);
+    return cudaGetLastError();
+}
+
+template <int D, typename T, typename Tin, typename Tout>
+__global__ void k_btapply(Geo<T> g, const Tin* __restrict__ x, Tout* __restrict__ y) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.Npsi) return;
+    const long long cell = j / g.nb;
+    const int rem = (int)(j - cell * g.nb);
+    const int comp = rem / (int)g.nloc;
+    int km[kMaxDim], cm[kMaxDim];
+    int kk = rem - comp * (int)g.nloc;
+    for (int t = 0; t < D; ++t) { km[t] = kk % g.n; kk /= g.n; }
+    cell_multi(g, cell, cm);
+    y[j] = (Tout)apply_BT_entry<D, T, Tin>(g, cm, comp, km, x);
+}
+
+template <typename T, typename Tin, typename Tout>
+cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t s) {
+    const unsigned b = (unsigned)((g.Npsi + 255) / 256);
+    if (g.d == 2) k_btapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y);
+    else k_btapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y);
+    return cudaGetLastError();
+}
+
+template <int D>
+__global__ void k_aapply(Geo<double> g, const double* __restrict__ x, double* __restrict__ y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.Nu0) return;
+    int r[kMaxDim];
+    decompose(i, D, g.n1, r);
+    y[i] = apply_A_row<D, double, double>(g, r, x);
+}
+
+cudaError_t launch_aapply(const Geo<double>& g, const double* x, double* y, cudaStream_t s) {
+    const unsigned b = (unsigned)((g.Nu0 + 255) / 256);
+    if (g.d == 2) k_aapply<2><<<b, 256, 0, s>>>(g, x, y);
+    else k_aapply<3><<<b, 256, 0, s>>>(g, x, y);
+    return cudaGetLastError();
+}
+
+// ======================================================================= FDM
+// C[b][i][j] = sum_k A(b,i,k) B(b,k,j) with general strides (batched tiny GEMM).
+struct GemmArgs {
+    int M, N, K, batch;
+    long long sAm, sAk, sAb, sBk, sBn, sBb, sCm, sCn, sCb;
+};
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_gemm(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp) {
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    constexpr int NT = (BM / TM) * (BN / TN);
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int b = blockIdx.z;
+    const T* A = Ap + (long long)b * a.sAb;
+    const T* B = Bp + (long long)b * a.sBb;
+    T* C = Cp + (long long)b * a.sCb;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    const bool a_kfast = (a.sAk == 1);
+    const bool b_nfast = (a.sBn == 1);
+    for (int k0 = 0; k0 < a.K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += NT) {
+            int mm, kk;
+            if (a_kfast) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < a.M && gk < a.K) ? A[gm * a.sAm + gk * a.sAk] : T(0);
+        }
+        for (int e = tid; e < BN * BK; e += NT) {
+            int nn, kk;
+            if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < a.N && gk < a.K) ? B[gk * a.sBk + gn * a.sBn] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T av[TM], bv[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) av[i] = As[kk][ty * TM + i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int gm = m0 + ty * TM + i, gn = n0 + tx * TN + j;
+            if (gm < a.M && gn < a.N) C[gm * a.sCm + gn * a.sCn] = acc[i][j];
+        }
+}
+
+template <typename T>
+static cudaError_t gemm(const GemmArgs& a, const T* A, const T* B, T* C, cudaStream_t s) {
+    // 32x32 tiles (2x2 per thread) keep enough CTAs in flight for n1 ~ 50..320
+    constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2;
+    dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch);
+    k_gemm<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(a, A, B, C);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_fdm_scale(Geo<T> g, T alpha_inv, T* __restrict__ x) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.Nu0) return;
+    long long r = i;
+    T lsum = T(0);
+    for (int j = 0; j < g.d; ++j) {
+        const int a = (int)(r % g.n1[j]);
+        r /= g.n1[j];
+        lsum += g.lam[j][a];
+    }
+    x[i] = x[i] * alpha_inv / lsum;
+}
+
+// A_alpha^{-1} x = alpha^{-1} (V (x) V (x) V) diag(1 / sum lam) (V^T (x) V^T (x) V^T) x
+template <typename T>
+cudaError_t launch_fdm(const Geo<T>& g, double alpha, const T* x, T* y, T* work1, T* work2, cudaStream_t s) {
+    const int d = g.d;
+    long long inner[kMaxDim], outer[kMaxDim];
+    for (int ax = 0; ax < d; ++ax) {
+        inner[ax] = 1;
+        outer[ax] = 1;
+        for (int j = 0; j < ax; ++j) inner[ax] *= g.n1[j];
+        for (int j = ax + 1; j < d; ++j) outer[ax] *= g.n1[j];
+    }
+    // pass along axis ax: out[o][a][i] = sum_k W(a,k) in[o][k][i]; W = V^T (fwd) or V (bwd)
+    auto pass = [&](int ax, bool fwd, const T* in, T* out) -> cudaError_t {
+        const int n1 = g.n1[ax];
+        const T* V = g.V[ax];   // row-major V[k][a]
+        GemmArgs a{};
+        if (inner[ax] == 1) {
+            // out[o][a] = sum_k in[o][k] W(a,k):  C(M=o, N=a) = A(o,k) * B(k,a)
+            a.M = (int)outer[ax]; a.N = n1; a.K = n1; a.batch = 1;
+            a.sAm = n1; a.sAk = 1; a.sAb = 0;
+            if (fwd) { a.sBk = n1; a.sBn = 1; }      // B(k,a) = V[k][a]
+            else { a.sBk = 1; a.sBn = n1; }          // B(k,a) = V[a][k]
+            a.sBb = 0;
+            a.sCm = n1; a.sCn = 1; a.sCb = 0;
+            return gemm<T>(a, in, V, out, s);
+        }
+        // per outer o: out[o] (n1 x inner) = W (n1 x n1) * in[o] (n1 x inner)
+        a.M = n1; a.N = (int)inner[ax]; a.K = n1; a.batch = (int)outer[ax];
+        if (fwd) { a.sAm = 1; a.sAk = n1; }          // A(a,k) = V[k][a]
+        else { a.sAm = n1; a.sAk = 1; }              // A(a,k) = V[a][k]
+        a.sAb = 0;
+        a.sBk = inner[ax]; a.sBn = 1; a.sBb = (long long)n1 * inner[ax];
+        a.sCm = inner[ax]; a.sCn = 1; a.sCb = (long long)n1 * inner[ax];
+        return gemm<T>(a, V, in, out, s);
+    };
+    cudaError_t e;
+    const T* cur = x;
+    T* bufs[2] = {work1, work2};
+    int bi = 0;
+    for (int ax = 0; ax < d; ++ax) {
+        if ((e = pass(ax, true, cur, bufs[bi])) != cudaSuccess) return e;
+        cur = bufs[bi];
+        bi ^= 1;
+    }
+    const unsigned blocks = (unsigned)((g.Nu0 + 255) / 256);
+    k_fdm_scale<T><<<blocks, 256, 0, s>>>(g, (T)(1.0 / alpha), const_cast<T*>(cur));
+    for (int ax = 0; ax < d; ++ax) {
+        T* dst = (ax == d - 1) ? y : bufs[bi];
+        if ((e = pass(ax, false, cur, dst)) != cudaSuccess) return e;
+        cur = dst;
+        bi ^= 1;
+    }
+    return cudaGetLastError();
+}
+
+// ========================================================== D apply per cell
+// out = sB * (B^T t) + sD * (D z + E z), per cell.  D z by sum factorisation:
+// z -> Gauss values (V along each axis) -> times gw (or the 2x2/3x3 Jacobian) -> V^T back.
+template <int D, typename T, typename Tz, typename Tt, typename Tout>
+__global__ void k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* __restrict__ z,
+                         const Tt* __restrict__ t, T sB, T sD, Tout* __restrict__ out) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    const int n = g.n, nloc = (int)g.nloc, nc = g.ncomp, nb = (int)g.nb;
+    T* a = sm;
+    T* b = sm + nb;
+    T* zc = sm + 2 * nb;
+    T* Vq = sm + 3 * nb;
+    const long long cell = blockIdx.x;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Vq[i] = g.Vq[i];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) { const T v = (T)z[cell * nb + i]; a[i] = v; zc[i] = v; }
+    __syncthreads();
+    T *in = a, *o = b;
+    int stride = 1;
+    for (int ax = 0; ax < D; ++ax) {
+        sf_pass(in, o, Vq, false, n, nloc, nc, stride);
+        __syncthreads();
+        T* tt = in; in = o; o = tt;
+        stride *= n;
+    }
+    const int gs = (g.kind == HPG_GRADIENT) ? D * (D + 1) / 2 : 1;
+    for (int q = threadIdx.x; q < nloc; q += blockDim.x) {
+        const long long gq = cell * nloc + q;
+        if (nc == 1) {
+            o[q] = gw[gq] * in[q];
+        } else {
+            T zq[kMaxDim];
+            for (int k = 0; k < nc; ++k) zq[k] = in[k * nloc + q];
+            for (int k = 0; k < nc; ++k) {
+                T s = T(0);
+                for (int l = 0; l < nc; ++l) {
+                    const int lo = k < l ? k : l, hi = k < l ? l : k;
+                    const int e = lo * nc - lo * (lo - 1) / 2 + (hi - lo);
+                    s += gw[gq * gs + e] * zq[l];
+                }
+                o[k * nloc + q] = s;
+            }
+        }
+    }
+    __syncthreads();
+    { T* tt = in; in = o; o = tt; }
+    stride = 1;
+    for (int ax = 0; ax < D; ++ax) {
+        sf_pass(in, o, Vq, true, n, nloc, nc, stride);
+        __syncthreads();
+        T* tt = in; in = o; o = tt;
+        stride *= n;
+    }
+    int cm[kMaxDim];
+    cell_multi(g, cell, cm);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const int comp = i / nloc, li = i - comp * nloc;
+        T ez;
+        if (nc == 1) {
+            ez = beta * g.Mpsi[li] * zc[i];
+        } else {
+            ez = T(0);
+            for (int l = 0; l < nloc; ++l) ez += g.Kpsi[(size_t)li * nloc + l] * zc[comp * nloc + l];
+            ez *= beta;
+        }
+        T acc = sD * (in[i] + ez);
+        if (t) {
+            int km[kMaxDim];
+            int kk = li;
+            for (int q = 0; q < D; ++q) { km[q] = kk % n; kk /= n; }
+            acc += sB * apply_BT_entry<D, T, Tt>(g, cm, comp, km, t);
+        }
+        out[cell * nb + i] = (Tout)acc;
+    }
+}
+
+template <typename T, typename Tout>
+cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T* z, const T* t, Tout* w,
+                              cudaStream_t s) {
+    const size_t smem = (size_t)(3 * g.nb + g.n * g.n) * sizeof(T);
+    const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
+    if (g.d == 2)
+        k_cellop<2, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w);
+    else
+        k_cellop<3, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w);
+    return cudaGetLastError();
+}
+
+// y_u = alpha A x_u + B x_psi (interior rows)
+template <int D>
+__global__ void k_newton_u(Geo<double> g, double alpha, const double* __restrict__ xu,
+                           const double* __restrict__ xp, double* __restrict__ yu) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.Nu0) return;
+    int r[kMaxDim];
+    decompose(i, D, g.n1, r);
+    yu[i] = alpha * apply_A_row<D, double, double>(g, r, xu) + apply_B_row<D, double, double>(g, r, xp, nullptr);
+}
+
+cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
+                                const double* x, double* y, cudaStream_t s) {
+    const unsigned bu = (unsigned)((g.Nu0 + 255) / 256);
+    const size_t smem = (size_t)(3 * g.nb + g.n * g.n) * sizeof(double);
+    const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
+    if (g.d == 2) {
+        k_newton_u<2><<<bu, 256, 0, s>>>(g, alpha, x, x + g.Nu0, y);
+        k_cellop<2, double, double, double, double><<<(unsigned)g.Nc, threads, smem, s>>>(
+            g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0);
+    } else {
+        k_newton_u<3><<<bu, 256, 0, s>>>(g, alpha, x, x + g.Nu0, y);
+        k_cellop<3, double, double, double, double><<<(unsigned)g.Nc, threads, smem, s>>>(
+            g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0);
+    }
+    return cudaGetLastError();
+}
+
+// ==================================================================== vectors
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin* __restrict__ x, Tout* __restrict__ y, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (Tout)x[i];
+}
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const Tin* x, Tout* y, long long n, cudaStream_t s) {
+    k_convert<Tin, Tout><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = a * x[i] + b * y[i];
+}
+cudaError_t launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s) {
+    k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, x, b, y, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_sub_scaled(const double* __restrict__ x, double b, const T* __restrict__ z, double* __restrict__ y,
+                             long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = x[i] - b * (double)z[i];
+}
+template <typename T>
+cudaError_t launch_sub_scaled(const double* x, double b, const T* z, double* y, long long n, cudaStream_t s) {
+    k_sub_scaled<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, b, z, y, n);
+    return cudaGetLastError();
+}
+
+__global__ void k_trial(const double* __restrict__ x, const double* __restrict__ dx, double lam,
+                        double* __restrict__ xt, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) xt[i] = x[i] - lam * dx[i];
+}
+cudaError_t launch_trial(const double* x, const double* dx, double lam, double* xt, long long n, cudaStream_t s) {
+    k_trial<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, dx, lam, xt, n);
+    return cudaGetLastError();
+}
+
+__global__ void k_sumsq(const double* __restrict__ x, long long n, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v += x[i] * x[i];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts, cudaStream_t s) {
+    int b = (int)((n + 255) / 256);
+    if (b > 1024) b = 1024;
+    if (b < 1) b = 1;
+    k_sumsq<<<b, 256, 0, s>>>(x, n, part);
+    *nparts = b;
+    return cudaGetLastError();
+}
+
+// ===================================================================== GMRES
+// Each block owns a contiguous chunk of the N-vector.
+__global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b, long long N,
+                           const double* __restrict__ part, int nparts, double rtol, double* __restrict__ scal,
+                           double* __restrict__ gv, int kmax, int* __restrict__ iflag) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
+    v = block_sum(v, sh);
+    __shared__ double beta;
+    if (threadIdx.x == 0) beta = sqrt(v);
+    __syncthreads();
+    const double bb = beta;
+    const double inv = bb > 0.0 ? 1.0 / bb : 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        Vb[i] = b[i] * inv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scal[0] = bb;
+        scal[1] = bb;
+        scal[2] = rtol * bb;
+        for (int i = 0; i <= kmax; ++i) gv[i] = 0.0;
+        gv[0] = bb;
+        iflag[0] = (bb == 0.0) ? 1 : 0;
+        iflag[1] = 0;
+        iflag[2] = 0;
+    }
+}
+
+// partial dots of w = Vb[j+1] with Vb[0..j]; last block reduces into h (accumulate or set)
+__global__ void k_gm_dots(const double* __restrict__ Vb, int j, long long N, double* __restrict__ part,
+                          double* __restrict__ h, int accumulate, unsigned int* __restrict__ counter,
+                          const int* __restrict__ iflag) {
+    if (iflag[0]) return;
+    const int nblk = gridDim.x;
+    const long long chunk = (N + nblk - 1) / nblk;
+    const long long e0 = blockIdx.x * chunk;
+    const long long e1 = (e0 + chunk < N) ? e0 + chunk : N;
+    const double* w = Vb + (long long)(j + 1) * N;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i <= j; i += nw) {
+        const double* vi = Vb + (long long)i * N;
+        double s = 0.0;
+        for (long long e = e0 + lane; e < e1; e += 32) s += vi[e] * w[e];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) part[(long long)blockIdx.x * (j + 1) + i] = s;
+    }
+    __threadfence();
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(nblk - 1));
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        double s = 0.0;
+        for (int bk = 0; bk < nblk; ++bk) s += part[(long long)bk * (j + 1) + i];
+        h[i] = accumulate ? h[i] + s : s;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// w -= sum_i c_i V_i ; partial sums of squares of the result
+__global__ void k_gm_update(double* __restrict__ Vb, int j, long long N, const double* __restrict__ c,
+                            double* __restrict__ part, const int* __restrict__ iflag) {
+    __shared__ double sh[32];
+    if (iflag[0]) return;
+    const int nblk = gridDim.x;
+    const long long chunk = (N + nblk - 1) / nblk;
+    const long long e0 = blockIdx.x * chunk;
+    const long long e1 = (e0 + chunk < N) ? e0 + chunk : N;
+    double* w = Vb + (long long)(j + 1) * N;
+    double ss = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        double v = w[e];
+        for (int i = 0; i <= j; ++i) v -= c[i] * Vb[(long long)i * N + e];
+        w[e] = v;
+        ss += v * v;
+    }
+    ss = block_sum(ss, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = ss;
+}
+
+// normalise V_{j+1}, Givens update of column j, convergence test
+__global__ void k_gm_finalize(double* __restrict__ Vb, int j, long long N, const double* __restrict__ part,
+                              double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                              double* __restrict__ gv, double* __restrict__ scal, int* __restrict__ iflag,
+                              int kmax, const double* __restrict__ h2) {
+    __shared__ double sh[32];
+    if (iflag[0]) return;
+    const int nblk = gridDim.x;
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += part[i];
+    v = block_sum(v, sh);
+    __shared__ double hn;
+    if (threadIdx.x == 0) hn = sqrt(v);
+    __syncthreads();
+    const double hnv = hn;
+    const long long chunk = (N + nblk - 1) / nblk;
+    const long long e0 = blockIdx.x * chunk;
+    const long long e1 = (e0 + chunk < N) ? e0 + chunk : N;
+    double* w = Vb + (long long)(j + 1) * N;
+    const double inv = hnv > 0.0 ? 1.0 / hnv : 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) w[e] *= inv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double* col = H + (long long)j * (kmax + 1);
+        for (int i = 0; i <= j; ++i) col[i] += h2[i];
+        col[j + 1] = hnv;
+        for (int i = 0; i < j; ++i) {
+            const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+            col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+            col[i] = t;
+        }
+        const double a = col[j], bq = col[j + 1];
+        const double r = hypot(a, bq);
+        double c = 1.0, s = 0.0;
+        if (r > 0.0) { c = a / r; s = bq / r; }
+        cs[j] = c;
+        sn[j] = s;
+        col[j] = r;
+        col[j + 1] = 0.0;
+        gv[j + 1] = -s * gv[j];
+        gv[j] = c * gv[j];
+        const double res = fabs(gv[j + 1]);
+        scal[1] = res;
+        scal[3] = hnv;
+        iflag[1] = j + 1;
+        if (!(res > scal[2])) iflag[0] = 1;
+        if (!(hnv > 1e-300) || !isfinite(res)) { iflag[0] = 1; iflag[2] = 1; }
+    }
+}
+
+__global__ void k_gm_backsolve(const double* __restrict__ H, const double* __restrict__ gv, int k, int kmax,
+                               double* __restrict__ y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = gv[i];
+        for (int l = i + 1; l < k; ++l) s -= H[(long long)l * (kmax + 1) + i] * y[l];
+        const double diag = H[(long long)i * (kmax + 1) + i];
+        y[i] = diag != 0.0 ? s / diag : 0.0;
+    }
+}
+
+__global__ void k_gm_combine(const double* __restrict__ Vb, const double* __restrict__ y, int k, long long N,
+                             double* __restrict__ x) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s += y[i] * Vb[(long long)i * N + e];
+    x[e] = s;
+}
+
+cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s) {
+    int np = 0;
+    cudaError_t e = launch_sumsq(b, G.N, G.part, &np, s);
+    if (e != cudaSuccess) return e;
+    cudaMemsetAsync(G.H, 0, sizeof(double) * (size_t)(G.kmax + 1) * G.kmax, s);
+    k_gm_start<<<G.blocks, 256, 0, s>>>(G.Vb, b, G.N, G.part, np, rtol, G.scal, G.gv, G.kmax, G.iflag);
+    return cudaGetLastError();
+}
+
+cudaError_t gmres_arnoldi(GmresDev& G, int j, cudaStream_t s) {
+    double* hcol = G.H + (long long)j * (G.kmax + 1);
+    double* h2 = G.y;   // scratch for the second CGS pass
+    // CGS pass 1 (writes h into H column), update; pass 2 (h2), update + norm; finalize adds h2
+    k_gm_dots<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, G.part, hcol, 0, G.counter, G.iflag);
+    k_gm_update<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, hcol, G.part + (size_t)G.blocks * (G.kmax + 1), G.iflag);
+    k_gm_dots<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, G.part, h2, 0, G.counter, G.iflag);
+    k_gm_update<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, h2, G.part + (size_t)G.blocks * (G.kmax + 1), G.iflag);
+    k_gm_finalize<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, G.part + (size_t)G.blocks * (G.kmax + 1), G.H, G.cs, G.sn,
+                                           G.gv, G.scal, G.iflag, G.kmax, h2);
+    return cudaGetLastError();
+}
+
+cudaError_t gmres_finish(GmresDev& G, int k, double* x, cudaStream_t s) {
+    if (k <= 0) {
+        cudaMemsetAsync(x, 0, sizeof(double) * G.N, s);
+        return cudaGetLastError();
+    }
+    k_gm_backsolve<<<1, 32, 0, s>>>(G.H, G.gv, k, G.kmax, G.y);
+    k_gm_combine<<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(G.Vb, G.y, k, G.N, x);
+    return cudaGetLastError();
+}
+
+// ============================================================ instantiations
+template cudaError_t launch_factor<double>(const Geo<double>&, const double*, double, double, double*, double*,
+                                           int*, cudaStream_t);
+template cudaError_t launch_factor<float>(const Geo<float>&, const float*, double, double, float*, double*, int*,
+                                          cudaStream_t);
+template cudaError_t launch_precond<double, double, double>(const Geo<double>&, const double*, const double*,
+                                                            double*, cudaStream_t);
+template cudaError_t launch_precond<float, double, float>(const Geo<float>&, const float*, const double*, float*,
+                                                          cudaStream_t);
+template cudaError_t launch_precond<float, double, double>(const Geo<float>&, const float*, const double*,
+                                                           double*, cudaStream_t);
+template cudaError_t launch_bapply<double, double, double>(const Geo<double>&, const double*, double*, cudaStream_t);
+template cudaError_t launch_bapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t);
+template cudaError_t launch_bapply<float, double, float>(const Geo<float>&, const double*, float*, cudaStream_t);
+template cudaError_t launch_btapply<double, double, double>(const Geo<double>&, const double*, double*,
+                                                            cudaStream_t);
+template cudaError_t launch_btapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t);
+template cudaError_t launch_fdm<double>(const Geo<double>&, double, const double*, double*, double*, double*,
+                                        cudaStream_t);
+template cudaError_t launch_fdm<float>(const Geo<float>&, double, const float*, float*, float*, float*,
+                                       cudaStream_t);
+template cudaError_t launch_schur_rest<double, double>(const Geo<double>&, const double*, double, const double*,
+                                                       const double*, double*, cudaStream_t);
+template cudaError_t launch_schur_rest<float, double>(const Geo<float>&, const float*, double, const float*,
+                                                      const float*, double*, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+template cudaError_t launch_sub_scaled<double>(const double*, double, const double*, double*, long long,
+                                               cudaStream_t);
+template cudaError_t launch_sub_scaled<float>(const double*, double, const float*, double*, long long,
+                                              cudaStream_t);
+
+}  // namespace hpg

@@ -1,0 +1,750 @@
+// libhpg host driver: device allocation/upload, the Newton loop over the
+// alpha_k proximal steps (eq. pG), the Schur solve of eq. (schur2) with
+// right-preconditioned GMRES on S, FP64 iterative refinement around an FP32
+// inner solve, and the component operators used by the tests.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "state.h"
+
+namespace hpg {
+
+#define CK(...)                                                                              \
+    do {                                                                                     \
+        cudaError_t e_ = (__VA_ARGS__);                                                      \
+        if (e_ != cudaSuccess) {                                                             \
+            ctx->err = std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_);            \
+            return HPG_ERR_CUDA;                                                             \
+        }                                                                                    \
+    } while (0)
+
+#define CKS(...)                                                                             \
+    do {                                                                                     \
+        hpg_status s_ = (__VA_ARGS__);                                                              \
+        if (s_ != HPG_OK) return s_;                                                         \
+    } while (0)
+
+// ------------------------------------------------------------ kernel timer
+static cudaEvent_t timer_event(KernelTimer& T) {
+    if (!T.pool.empty()) {
+        cudaEvent_t e = T.pool.back();
+        T.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static void timer_flush(KernelTimer& T) {
+    for (auto& p : T.pending) {
+        cudaEventSynchronize(p.second.second);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+        T.ms[p.first] += ms;
+        T.launches[p.first] += 1;
+        T.pool.push_back(p.second.first);
+        T.pool.push_back(p.second.second);
+    }
+    T.pending.clear();
+}
+
+struct Scope {
+    KernelTimer& T;
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr;
+    Scope(KernelTimer& t, int c, cudaStream_t st) : T(t), cls(c), s(st) {
+        if (T.on) { e0 = timer_event(T); cudaEventRecord(e0, s); }
+    }
+    ~Scope() {
+        if (T.on) {
+            cudaEvent_t e1 = timer_event(T);
+            cudaEventRecord(e1, s);
+            T.pending.push_back({cls, {e0, e1}});
+            if (T.pending.size() > 4096) timer_flush(T);
+        }
+    }
+};
+
+// ------------------------------------------------------------ allocation
+template <typename T>
+static T* dalloc(DevState& D, size_t n, bool& ok) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) { ok = false; return nullptr; }
+    D.allocs.push_back(p);
+    D.bytes += n * sizeof(T);
+    return static_cast<T*>(p);
+}
+
+void free_device(Problem& P) {
+    for (void* p : P.D.allocs) cudaFree(p);
+    P.D.allocs.clear();
+    if (P.D.h_scal) cudaFreeHost(P.D.h_scal);
+    if (P.D.h_iflag) cudaFreeHost(P.D.h_iflag);
+    P.D.h_scal = nullptr;
+    P.D.h_iflag = nullptr;
+    for (auto e : P.timer.pool) cudaEventDestroy(e);
+    P.timer.pool.clear();
+    P.D = DevState{};
+    P.alloc_done = false;
+}
+
+static void pack_sten(const Ell& E, bool gram, int n, std::vector<int>& col) {
+    col = E.col;
+    if (gram)
+        for (size_t i = 0; i < col.size(); ++i) col[i] = ((col[i] / n) << 8) | (col[i] % n);
+}
+
+static bool upload_sten(DevState& D, const Ell& E, bool gram, int n, DevSten& S, cudaStream_t s) {
+    bool ok = true;
+    const size_t w = (size_t)E.rows * kEll;
+    S.cnt = dalloc<int>(D, E.rows, ok);
+    S.col = dalloc<int>(D, w, ok);
+    S.vd = dalloc<double>(D, w, ok);
+    S.vf = dalloc<float>(D, w, ok);
+    if (!ok) return false;
+    std::vector<int> col;
+    pack_sten(E, gram, n, col);
+    std::vector<float> vf(E.val.begin(), E.val.end());
+    cudaMemcpyAsync(S.cnt, E.cnt.data(), E.rows * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(S.col, col.data(), w * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(S.vd, E.val.data(), w * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(S.vf, vf.data(), w * sizeof(float), cudaMemcpyHostToDevice, s);
+    return cudaStreamSynchronize(s) == cudaSuccess;
+}
+
+template <typename T>
+static T* upload_vec(DevState& D, const std::vector<double>& v, bool& ok, cudaStream_t s) {
+    T* p = dalloc<T>(D, v.size(), ok);
+    if (!ok) return nullptr;
+    std::vector<T> tmp(v.begin(), v.end());
+    if (!v.empty()) cudaMemcpyAsync(p, tmp.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    return p;
+}
+
+hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
+    if (P.alloc_done) return HPG_OK;
+    HostProblem& H = P.H;
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    bool ok = true;
+    const int d = H.d;
+    const bool grad = H.kind == HPG_GRADIENT;
+    for (int j = 0; j < d; ++j) {
+        const Dir1D& Dj = H.dir[j];
+        ok = ok && upload_sten(D, Dj.Ai, false, H.n, D.A[j], s);
+        ok = ok && upload_sten(D, Dj.Mi, false, H.n, D.M[j], s);
+        ok = ok && upload_sten(D, Dj.Bi, true, H.n, D.B[j], s);
+        ok = ok && upload_sten(D, Dj.BTi, false, H.n, D.BT[j], s);
+        if (grad) {
+            ok = ok && upload_sten(D, Dj.Bdi, true, H.n, D.Bd[j], s);
+            ok = ok && upload_sten(D, Dj.BdTi, false, H.n, D.BdT[j], s);
+        }
+        D.V_d[j] = upload_vec<double>(D, Dj.V, ok, s);
+        D.V_f[j] = upload_vec<float>(D, Dj.V, ok, s);
+        D.lam_d[j] = upload_vec<double>(D, Dj.lam, ok, s);
+        D.lam_f[j] = upload_vec<float>(D, Dj.lam, ok, s);
+    }
+    if (!ok) { free_device(P); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
+    D.Vq_d = upload_vec<double>(D, H.Vq, ok, s);
+    D.Vq_f = upload_vec<float>(D, H.Vq, ok, s);
+    D.wq_d = upload_vec<double>(D, H.wq, ok, s);
+    D.wq_f = upload_vec<float>(D, H.wq, ok, s);
+    D.Mpsi_d = upload_vec<double>(D, H.Mpsi_loc, ok, s);
+    D.Mpsi_f = upload_vec<float>(D, H.Mpsi_loc, ok, s);
+    if (grad) {
+        D.Kpsi_d = upload_vec<double>(D, H.Kpsi_loc, ok, s);
+        D.Kpsi_f = upload_vec<float>(D, H.Kpsi_loc, ok, s);
+    } else {
+        D.C_d = upload_vec<double>(D, H.Cblk, ok, s);
+        D.C_f = upload_vec<float>(D, H.Cblk, ok, s);
+    }
+    const size_t Nu0 = H.Nu0, Npsi = H.Npsi, Nx = Nu0 + Npsi;
+    const size_t gsz = H.Nq * gauss_stride(H.kind, d);
+    D.rA = dalloc<double>(D, Nu0, ok);
+    D.rB = dalloc<double>(D, Npsi, ok);
+    D.bf = dalloc<double>(D, Nu0, ok);
+    D.phiz = dalloc<double>(D, Npsi, ok);
+    D.phiq = dalloc<double>(D, H.Nq, ok);
+    D.x = dalloc<double>(D, Nx, ok);
+    D.xt = dalloc<double>(D, Nx, ok);
+    D.psi_prev = dalloc<double>(D, Npsi, ok);
+    D.gw = dalloc<double>(D, gsz, ok);
+    D.gwt = dalloc<double>(D, gsz, ok);
+    D.gwf = dalloc<float>(D, gsz, ok);
+    D.eg = dalloc<double>(D, Npsi, ok);
+    D.egt = dalloc<double>(D, Npsi, ok);
+    D.F = dalloc<double>(D, Nx, ok);
+    D.Ft = dalloc<double>(D, Nx, ok);
+    D.delta = dalloc<double>(D, Nx, ok);
+    D.r = dalloc<double>(D, Nx, ok);
+    D.dcorr = dalloc<double>(D, Nx, ok);
+    const size_t sblk = (size_t)H.Nc * H.nb * H.nb;
+    D.Sinv_d = dalloc<double>(D, sblk, ok);
+    D.Sinv_f = dalloc<float>(D, sblk, ok);
+    D.tu_d = dalloc<double>(D, Nu0, ok);
+    D.tu2_d = dalloc<double>(D, Nu0, ok);
+    D.w1_d = dalloc<double>(D, Nu0, ok);
+    D.w2_d = dalloc<double>(D, Nu0, ok);
+    D.tu_f = dalloc<float>(D, Nu0, ok);
+    D.tu2_f = dalloc<float>(D, Nu0, ok);
+    D.w1_f = dalloc<float>(D, Nu0, ok);
+    D.w2_f = dalloc<float>(D, Nu0, ok);
+    D.zp_d = dalloc<double>(D, Npsi, ok);
+    D.zp_f = dalloc<float>(D, Npsi, ok);
+    D.yp = dalloc<double>(D, Npsi, ok);
+    D.xs = dalloc<double>(D, Npsi, ok);
+    const int nres = (int)((Nu0 + 255) / 256 + (Npsi + 255) / 256);
+    D.part = dalloc<double>(D, std::max(nres, 1024), ok);
+    D.scal = dalloc<double>(D, 16, ok);
+    D.flag = dalloc<int>(D, 4, ok);
+    // GMRES
+    GmresDev& G = D.gm;
+    G.kmax = std::max(1, P.params.krylov_max);
+    G.N = (long long)Npsi;
+    G.blocks = (int)std::min<long long>(304, std::max<long long>(1, (G.N + 1023) / 1024));
+    G.Vb = dalloc<double>(D, (size_t)(G.kmax + 1) * Npsi, ok);
+    G.H = dalloc<double>(D, (size_t)(G.kmax + 1) * G.kmax, ok);
+    G.cs = dalloc<double>(D, G.kmax, ok);
+    G.sn = dalloc<double>(D, G.kmax, ok);
+    G.gv = dalloc<double>(D, G.kmax + 1, ok);
+    G.part = dalloc<double>(D, std::max<size_t>(1024, (size_t)G.blocks * (G.kmax + 3)), ok);
+    G.scal = dalloc<double>(D, 8, ok);
+    G.iflag = dalloc<int>(D, 4, ok);
+    G.counter = dalloc<unsigned int>(D, 1, ok);
+    G.y = dalloc<double>(D, G.kmax + 1, ok);
+    if (!ok) { free_device(P); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
+    cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), s);
+    cudaMemsetAsync(D.flag, 0, 4 * sizeof(int), s);
+    if (cudaMallocHost(&D.h_scal, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&D.h_iflag, 8 * sizeof(int)) != cudaSuccess) {
+        free_device(P);
+        ctx->err = "pinned host allocation failed";
+        return HPG_ERR_OOM;
+    }
+    // geometry views
+    auto fill = [&](auto& g, auto sel) {
+        g.d = d; g.n = H.n; g.ncomp = H.ncomp; g.kind = H.kind;
+        for (int j = 0; j < kMaxDim; ++j) { g.m[j] = H.m[j]; g.n1[j] = (j < d) ? H.dir[j].n1 : 1; }
+        g.Nu0 = (long long)Nu0; g.Nc = (long long)H.Nc; g.nloc = (long long)H.nloc; g.nb = (long long)H.nb;
+        g.Npsi = (long long)Npsi;
+        sel(g);
+    };
+    fill(D.gd, [&](Geo<double>& g) {
+        for (int j = 0; j < d; ++j) {
+            g.A[j] = {D.A[j].cnt, D.A[j].col, D.A[j].vd};
+            g.M[j] = {D.M[j].cnt, D.M[j].col, D.M[j].vd};
+            g.B[j] = {D.B[j].cnt, D.B[j].col, D.B[j].vd};
+            g.BT[j] = {D.BT[j].cnt, D.BT[j].col, D.BT[j].vd};
+            g.Bd[j] = {D.Bd[j].cnt, D.Bd[j].col, D.Bd[j].vd};
+            g.BdT[j] = {D.BdT[j].cnt, D.BdT[j].col, D.BdT[j].vd};
+            g.V[j] = D.V_d[j];
+            g.lam[j] = D.lam_d[j];
+        }
+        g.Vq = D.Vq_d; g.wq = D.wq_d; g.detJ = H.detJ; g.Mpsi = D.Mpsi_d; g.Kpsi = D.Kpsi_d; g.C = D.C_d;
+    });
+    fill(D.gf, [&](Geo<float>& g) {
+        for (int j = 0; j < d; ++j) {
+            g.A[j] = {D.A[j].cnt, D.A[j].col, D.A[j].vf};
+            g.M[j] = {D.M[j].cnt, D.M[j].col, D.M[j].vf};
+            g.B[j] = {D.B[j].cnt, D.B[j].col, D.B[j].vf};
+            g.BT[j] = {D.BT[j].cnt, D.BT[j].col, D.BT[j].vf};
+            g.Bd[j] = {D.Bd[j].cnt, D.Bd[j].col, D.Bd[j].vf};
+            g.BdT[j] = {D.BdT[j].cnt, D.BdT[j].col, D.BdT[j].vf};
+            g.V[j] = D.V_f[j];
+            g.lam[j] = D.lam_f[j];
+        }
+        g.Vq = D.Vq_f; g.wq = D.wq_f; g.detJ = (float)H.detJ; g.Mpsi = D.Mpsi_f; g.Kpsi = D.Kpsi_f; g.C = D.C_f;
+    });
+    CK(cudaStreamSynchronize(s));
+    P.alloc_done = true;
+    return HPG_OK;
+}
+
+hpg_status upload_data(hpg_ctx* ctx, Problem& P) {
+    HostProblem& H = P.H;
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(D.rA, H.rA.data(), H.Nu0 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.rB, H.rB.data(), H.Npsi * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.bf, H.bf.data(), H.Nu0 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.phiz, H.phiz.data(), H.Npsi * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.phiq, H.phiq.data(), H.Nq * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return HPG_OK;
+}
+
+// ------------------------------------------------------------ precision views
+template <typename T>
+struct PV;
+template <>
+struct PV<double> {
+    static const Geo<double>& g(DevState& D) { return D.gd; }
+    static double* Sinv(DevState& D) { return D.Sinv_d; }
+    static const double* gw(DevState& D) { return D.gw; }
+    static double* tu(DevState& D) { return D.tu_d; }
+    static double* tu2(DevState& D) { return D.tu2_d; }
+    static double* w1(DevState& D) { return D.w1_d; }
+    static double* w2(DevState& D) { return D.w2_d; }
+    static double* zp(DevState& D) { return D.zp_d; }
+};
+template <>
+struct PV<float> {
+    static const Geo<float>& g(DevState& D) { return D.gf; }
+    static float* Sinv(DevState& D) { return D.Sinv_f; }
+    static const float* gw(DevState& D) { return D.gwf; }
+    static float* tu(DevState& D) { return D.tu_f; }
+    static float* tu2(DevState& D) { return D.tu2_f; }
+    static float* w1(DevState& D) { return D.w1_f; }
+    static float* w2(DevState& D) { return D.w2_f; }
+    static float* zp(DevState& D) { return D.zp_f; }
+};
+
+template <typename T>
+static cudaError_t to_T(const double* x, T* y, long long n, cudaStream_t s);
+template <>
+cudaError_t to_T<double>(const double* x, double* y, long long n, cudaStream_t s) {
+    return cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+template <>
+cudaError_t to_T<float>(const double* x, float* y, long long n, cudaStream_t s) {
+    return launch_convert<double, float>(x, y, n, s);
+}
+template <typename T>
+static cudaError_t from_T(const T* x, double* y, long long n, cudaStream_t s);
+template <>
+cudaError_t from_T<double>(const double* x, double* y, long long n, cudaStream_t s) {
+    return cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+template <>
+cudaError_t from_T<float>(const float* x, double* y, long long n, cudaStream_t s) {
+    return launch_convert<float, double>(x, y, n, s);
+}
+
+// ------------------------------------------------------------ building blocks
+static hpg_status eval_state(hpg_ctx* ctx, Problem& P, const double* x, double* gw, double* eg) {
+    DevState& D = P.D;
+    Scope sc(P.timer, HPG_K_EVAL, ctx->stream);
+    CK(launch_eval(D.gd, x + P.H.Nu0, D.phiq, gw, nullptr, eg, D.flag, ctx->stream));
+    return HPG_OK;
+}
+
+// F = residual(x), returns |F| and the eval flag (one host sync)
+static hpg_status residual_state(hpg_ctx* ctx, Problem& P, const double* x, const double* eg, double alpha,
+                                 double* F, double* norm, int* flag) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    {
+        Scope sc(P.timer, HPG_K_RESIDUAL, s);
+        CK(launch_residual(D.gd, x, x + P.H.Nu0, D.psi_prev, eg, D.rA, D.rB, D.bf, D.phiz, alpha, F, D.part, s));
+        CK(launch_reduce_sum(D.part, n_res_partials(D.gd), D.scal, s));
+    }
+    CK(cudaMemcpyAsync(D.h_scal, D.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(D.h_iflag, D.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *norm = std::sqrt(D.h_scal[0]);
+    *flag = D.h_iflag[0];
+    if (!std::isfinite(*norm)) *flag |= 1;
+    return HPG_OK;
+}
+
+static hpg_status norm_of(hpg_ctx* ctx, Problem& P, const double* v, long long n, double* out) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    int np = 0;
+    CK(launch_sumsq(v, n, D.part, &np, s));
+    CK(launch_reduce_sum(D.part, np, D.scal + 1, s));
+    CK(cudaMemcpyAsync(D.h_scal + 1, D.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = std::sqrt(D.h_scal[1]);
+    return HPG_OK;
+}
+
+template <typename T>
+static hpg_status factor_T(hpg_ctx* ctx, Problem& P, double alpha, double* dump) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    Scope sc(P.timer, HPG_K_FACTOR, s);
+    if (sizeof(T) == sizeof(float))
+        CK(launch_convert<double, float>(D.gw, D.gwf, (long long)(P.H.Nq * gauss_stride(P.H.kind, P.H.d)), s));
+    CK(launch_factor<T>(PV<T>::g(D), PV<T>::gw(D), alpha, P.params.beta, PV<T>::Sinv(D), dump, D.flag, s));
+    return HPG_OK;
+}
+
+template <typename T>
+static hpg_status fdm_T(hpg_ctx* ctx, Problem& P, double alpha, const T* x, T* y) {
+    DevState& D = P.D;
+    Scope sc(P.timer, HPG_K_FDM, ctx->stream);
+    CK(launch_fdm<T>(PV<T>::g(D), alpha, x, y, PV<T>::w1(D), PV<T>::w2(D), ctx->stream));
+    return HPG_OK;
+}
+
+// S z for z = Shat^{-1} v :  w = -(D z + E z + B^T A^{-1} B z), written into out (FP64)
+template <typename T>
+static hpg_status schur_apply_T(hpg_ctx* ctx, Problem& P, double alpha, const T* z, double* out) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const Geo<T>& g = PV<T>::g(D);
+    {
+        Scope sc(P.timer, HPG_K_BAPPLY, s);
+        CK(launch_bapply<T, T, T>(g, z, PV<T>::tu(D), s));
+    }
+    CKS(fdm_T<T>(ctx, P, alpha, PV<T>::tu(D), PV<T>::tu2(D)));
+    {
+        Scope sc(P.timer, HPG_K_SCHUR, s);
+        CK(launch_schur_rest<T, double>(g, PV<T>::gw(D), P.params.beta, z, PV<T>::tu2(D), out, s));
+    }
+    return HPG_OK;
+}
+
+// eq. (schur2): y = b_psi - B^T A^{-1} b_u; GMRES on S (right-preconditioned by
+// S-hat); delta_u = A^{-1}(b_u - B delta_psi).  All vectors FP64, operators in T.
+template <typename T>
+static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const double* bu, const double* bp,
+                                double* du, double* dp, double rtol, int* its, bool* capped) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const Geo<T>& g = PV<T>::g(D);
+    const long long Nu0 = (long long)P.H.Nu0, Npsi = (long long)P.H.Npsi;
+    GmresDev& G = D.gm;
+    T* tu = PV<T>::tu(D);
+    T* tu2 = PV<T>::tu2(D);
+    T* zp = PV<T>::zp(D);
+    CK(to_T<T>(bu, tu, Nu0, s));
+    CKS(fdm_T<T>(ctx, P, alpha, tu, tu2));
+    {
+        Scope sc(P.timer, HPG_K_SCHUR, s);
+        CK(launch_btapply<T, T, T>(g, tu2, zp, s));
+        CK(launch_sub_scaled<T>(bp, 1.0, zp, D.yp, Npsi, s));
+    }
+    {
+        Scope sc(P.timer, HPG_K_ORTHO, s);
+        CK(gmres_start(G, D.yp, rtol, s));
+    }
+    int k = 0;
+    bool conv = false;
+    CK(cudaMemcpyAsync(D.h_iflag + 4, G.iflag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (D.h_iflag[4]) conv = true;
+    for (int j = 0; j < G.kmax && !conv; ++j) {
+        {
+            Scope sc(P.timer, HPG_K_PRECOND, s);
+            CK(launch_precond<T, double, T>(g, PV<T>::Sinv(D), G.Vb + (long long)j * Npsi, zp, s));
+        }
+        CKS(schur_apply_T<T>(ctx, P, alpha, zp, G.Vb + (long long)(j + 1) * Npsi));
+        {
+            Scope sc(P.timer, HPG_K_ORTHO, s);
+            CK(gmres_arnoldi(G, j, s));
+        }
+        CK(cudaMemcpyAsync(D.h_iflag + 4, G.iflag, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        k = D.h_iflag[5];
+        if (D.h_iflag[4]) conv = true;
+    }
+    *capped = !conv;
+    if (!conv) k = G.kmax;
+    *its = k;
+    {
+        Scope sc(P.timer, HPG_K_ORTHO, s);
+        CK(gmres_finish(G, k, D.xs, s));
+    }
+    {
+        Scope sc(P.timer, HPG_K_PRECOND, s);
+        CK(launch_precond<T, double, double>(g, PV<T>::Sinv(D), D.xs, dp, s));
+    }
+    {
+        Scope sc(P.timer, HPG_K_BAPPLY, s);
+        CK(launch_bapply<T, double, T>(g, dp, tu, s));
+    }
+    {
+        Scope sc(P.timer, HPG_K_UPDATE, s);
+        CK(launch_sub_scaled<T>(bu, 1.0, tu, D.tu_d, Nu0, s));
+        CK(to_T<T>(D.tu_d, tu, Nu0, s));
+    }
+    CKS(fdm_T<T>(ctx, P, alpha, tu, tu2));
+    CK(from_T<T>(tu2, du, Nu0, s));
+    return HPG_OK;
+}
+
+// Solve G delta = F for the current factorisation: FP64 GMRES, or FP32 inner
+// solves inside FP64 iterative refinement (r = F - G delta in FP64).
+static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* F, double normF, double eta,
+                               double* delta, int* its_total, int* sweeps) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long Nu0 = (long long)P.H.Nu0, Npsi = (long long)P.H.Npsi, Nx = Nu0 + Npsi;
+    bool capped = false;
+    *sweeps = 0;
+    *its_total = 0;
+    if (P.params.precision == HPG_FP64) {
+        int its = 0;
+        CKS(schur_solve_T<double>(ctx, P, alpha, F, F + Nu0, delta, delta + Nu0, eta, &its, &capped));
+        *its_total = its;
+        if (capped) P.stats.krylov_cap_hits++;
+        return HPG_OK;
+    }
+    CK(cudaMemsetAsync(delta, 0, Nx * sizeof(double), s));
+    CK(cudaMemcpyAsync(D.r, F, Nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const double inner = std::max(eta, 2e-6);
+    for (int sw = 0; sw < std::max(1, P.params.refine_max); ++sw) {
+        int its = 0;
+        CKS(schur_solve_T<float>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, inner, &its, &capped));
+        *its_total += its;
+        if (capped) P.stats.krylov_cap_hits++;
+        {
+            Scope sc(P.timer, HPG_K_UPDATE, s);
+            CK(launch_axpby(1.0, D.dcorr, 1.0, delta, Nx, s));
+        }
+        {
+            Scope sc(P.timer, HPG_K_NEWTON_APPLY, s);
+            CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, delta, D.r, s));
+        }
+        {
+            Scope sc(P.timer, HPG_K_UPDATE, s);
+            CK(launch_axpby(1.0, F, -1.0, D.r, Nx, s));
+        }
+        double nr = 0.0;
+        CKS(norm_of(ctx, P, D.r, Nx, &nr));
+        *sweeps = sw + 1;
+        if (nr <= eta * normF) break;
+    }
+    return HPG_OK;
+}
+
+static void swap_state(DevState& D) {
+    std::swap(D.x, D.xt);
+    std::swap(D.gw, D.gwt);
+    std::swap(D.eg, D.egt);
+    std::swap(D.F, D.Ft);
+}
+
+hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
+    auto t0 = std::chrono::steady_clock::now();
+    HostProblem& H = P.H;
+    CKS(alloc_device(ctx, P));
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long Nu0 = (long long)H.Nu0, Npsi = (long long)H.Npsi, Nx = Nu0 + Npsi;
+    hpg_stats& st = P.stats;
+    st = hpg_stats{};
+    st.n_u = Nu0;
+    st.n_psi = Npsi;
+    P.timer.on = P.params.timing != 0;
+    CK(cudaMemsetAsync(D.x, 0, Nx * sizeof(double), s));
+    CK(cudaMemsetAsync(D.psi_prev, 0, Npsi * sizeof(double), s));
+    CK(cudaMemsetAsync(D.flag, 0, 4 * sizeof(int), s));
+    hpg_status status = HPG_OK;
+    double normF = 0.0;
+    const int nsteps = (int)std::min<size_t>(H.alphas.size(), HPG_MAX_ALPHA);
+    for (int k = 0; k < nsteps && status == HPG_OK; ++k) {
+        const double alpha = H.alphas[k];
+        if (k > 0) CK(cudaMemcpyAsync(D.psi_prev, D.x + Nu0, Npsi * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        int flag = 0;
+        CKS(eval_state(ctx, P, D.x, D.gw, D.eg));
+        CKS(residual_state(ctx, P, D.x, D.eg, alpha, D.F, &normF, &flag));
+        int it = 0;
+        while (true) {
+            if (flag & 1) { status = HPG_ERR_NONFINITE; break; }
+            if (normF <= P.params.newton_tol) break;
+            if (it >= P.params.newton_max) { status = HPG_ERR_NEWTON_CAP; break; }
+            if (P.params.precision == HPG_FP64) CKS(factor_T<double>(ctx, P, alpha, nullptr));
+            else CKS(factor_T<float>(ctx, P, alpha, nullptr));
+            int its = 0, sweeps = 0;
+            // forcing term: relative tolerance min(krylov_rtol, ||F||)
+            const double eta = std::min(P.params.krylov_rtol, std::max(normF, 1e-12));
+            CKS(linear_solve(ctx, P, alpha, D.F, normF, eta, D.delta, &its, &sweeps));
+            st.krylov_total += its;
+            st.refine_total += sweeps;
+            // backtracking on ||F||
+            double lam = 1.0, nFt = 0.0;
+            int tflag = 0;
+            for (int h = 0; h <= P.params.ls_max; ++h) {
+                {
+                    Scope sc(P.timer, HPG_K_UPDATE, s);
+                    CK(launch_trial(D.x, D.delta, lam, D.xt, Nx, s));
+                }
+                CK(cudaMemsetAsync(D.flag, 0, sizeof(int), s));
+                CKS(eval_state(ctx, P, D.xt, D.gwt, D.egt));
+                CKS(residual_state(ctx, P, D.xt, D.egt, alpha, D.Ft, &nFt, &tflag));
+                if (!(tflag & 1) && nFt <= (1.0 - 1e-4 * lam) * normF) break;
+                if (h == P.params.ls_max) { st.ls_fail++; break; }
+                lam *= 0.5;
+            }
+            // factorisation flag (non-SPD block) is sticky in bit 1
+            CK(cudaMemcpyAsync(D.h_iflag, D.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (D.h_iflag[0] & 2) { status = HPG_ERR_NOT_SPD; break; }
+            swap_state(D);
+            normF = nFt;
+            flag = tflag;
+            ++it;
+        }
+        st.newton_per_step[k] = it;
+        st.newton_total += it;
+        st.alpha_steps = k + 1;
+    }
+    st.final_residual = normF;
+    st.status = status;
+    CK(cudaStreamSynchronize(s));
+    timer_flush(P.timer);
+    st.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    P.solved = true;
+    return status;
+}
+
+hpg_status solve_batch(hpg_ctx* ctx, std::vector<Problem*>& probs) {
+    hpg_status first = HPG_OK;
+    for (Problem* P : probs) {
+        hpg_status s = solve_problem(ctx, *P);
+        if (s != HPG_OK && first == HPG_OK) first = s;
+    }
+    return first;
+}
+
+// ------------------------------------------------------------ operators (tests)
+hpg_status op_set_state(hpg_ctx* ctx, Problem& P, const double* u_full, const double* psi, const double* psi_prev,
+                        double alpha) {
+    CKS(alloc_device(ctx, P));
+    HostProblem& H = P.H;
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    std::vector<double> u0(H.Nu0);
+    for (size_t I = 0; I < H.Nu0; ++I) {
+        size_t ii = I, full = 0, stride = 1;
+        for (int j = 0; j < H.d; ++j) {
+            full += (size_t)H.dir[j].glob_of_int((int)(ii % H.dir[j].n1)) * stride;
+            ii /= H.dir[j].n1;
+            stride *= H.dir[j].N1;
+        }
+        u0[I] = u_full[full];
+    }
+    CK(cudaMemcpyAsync(D.x, u0.data(), H.Nu0 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.x + H.Nu0, psi, H.Npsi * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.psi_prev, psi_prev, H.Npsi * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(D.flag, 0, 4 * sizeof(int), s));
+    CKS(eval_state(ctx, P, D.x, D.gw, D.eg));
+    CK(cudaStreamSynchronize(s));
+    P.state_alpha = alpha;
+    return HPG_OK;
+}
+
+hpg_status op_residual(hpg_ctx* ctx, Problem& P, double* F, double* norm) {
+    DevState& D = P.D;
+    int flag = 0;
+    double nrm = 0.0;
+    CKS(residual_state(ctx, P, D.x, D.eg, P.state_alpha, D.F, &nrm, &flag));
+    CK(cudaMemcpy(F, D.F, (P.H.Nu0 + P.H.Npsi) * sizeof(double), cudaMemcpyDeviceToHost));
+    if (norm) *norm = nrm;
+    return (flag & 1) ? HPG_ERR_NONFINITE : HPG_OK;
+}
+
+hpg_status op_apply_newton(hpg_ctx* ctx, Problem& P, const double* x, double* y) {
+    DevState& D = P.D;
+    const size_t Nx = P.H.Nu0 + P.H.Npsi;
+    CK(cudaMemcpy(D.r, x, Nx * sizeof(double), cudaMemcpyHostToDevice));
+    CK(launch_newton_apply(D.gd, D.gw, P.state_alpha, P.params.beta, D.r, D.dcorr, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(y, D.dcorr, Nx * sizeof(double), cudaMemcpyDeviceToHost));
+    return HPG_OK;
+}
+
+hpg_status op_stiffness_inv(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long n = (long long)P.H.Nu0;
+    CK(cudaMemcpy(D.r, x, n * sizeof(double), cudaMemcpyHostToDevice));
+    if (precision == HPG_FP64) {
+        CKS(fdm_T<double>(ctx, P, P.state_alpha, D.r, D.tu2_d));
+        CK(cudaStreamSynchronize(s));
+        CK(cudaMemcpy(y, D.tu2_d, n * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+        CK(launch_convert<double, float>(D.r, D.tu_f, n, s));
+        CKS(fdm_T<float>(ctx, P, P.state_alpha, D.tu_f, D.tu2_f));
+        CK(launch_convert<float, double>(D.tu2_f, D.dcorr, n, s));
+        CK(cudaStreamSynchronize(s));
+        CK(cudaMemcpy(y, D.dcorr, n * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return HPG_OK;
+}
+
+hpg_status op_factor(hpg_ctx* ctx, Problem& P, int precision, double* blocks) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    double* dump = nullptr;
+    const size_t nblk = (size_t)P.H.Nc * P.H.nb * P.H.nb;
+    if (blocks) {
+        if (cudaMalloc(&dump, nblk * sizeof(double)) != cudaSuccess) return HPG_ERR_OOM;
+    }
+    hpg_status st = (precision == HPG_FP64) ? factor_T<double>(ctx, P, P.state_alpha, dump)
+                                            : factor_T<float>(ctx, P, P.state_alpha, dump);
+    cudaStreamSynchronize(s);
+    if (st == HPG_OK && blocks) {
+        if (cudaMemcpy(blocks, dump, nblk * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) st = HPG_ERR_CUDA;
+    }
+    if (dump) cudaFree(dump);
+    int flag = 0;
+    cudaMemcpy(&flag, D.flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (st == HPG_OK && (flag & 2)) st = HPG_ERR_NOT_SPD;
+    return st;
+}
+
+hpg_status op_precond_inv(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long n = (long long)P.H.Npsi;
+    CK(cudaMemcpy(D.yp, x, n * sizeof(double), cudaMemcpyHostToDevice));
+    if (precision == HPG_FP64) CK(launch_precond<double, double, double>(D.gd, D.Sinv_d, D.yp, D.xs, s));
+    else CK(launch_precond<float, double, double>(D.gf, D.Sinv_f, D.yp, D.xs, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(y, D.xs, n * sizeof(double), cudaMemcpyDeviceToHost));
+    return HPG_OK;
+}
+
+hpg_status op_schur(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long n = (long long)P.H.Npsi;
+    CK(cudaMemcpy(D.yp, x, n * sizeof(double), cudaMemcpyHostToDevice));
+    if (precision == HPG_FP64) {
+        CK(cudaMemcpyAsync(D.zp_d, D.yp, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CKS(schur_apply_T<double>(ctx, P, P.state_alpha, D.zp_d, D.xs));
+    } else {
+        CK(launch_convert<double, float>(D.gw, D.gwf, (long long)(P.H.Nq * gauss_stride(P.H.kind, P.H.d)), s));
+        CK(launch_convert<double, float>(D.yp, D.zp_f, n, s));
+        CKS(schur_apply_T<float>(ctx, P, P.state_alpha, D.zp_f, D.xs));
+    }
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(y, D.xs, n * sizeof(double), cudaMemcpyDeviceToHost));
+    return HPG_OK;
+}
+
+hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double rtol, double* delta, int* its) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    double nrm = 0.0;
+    int flag = 0;
+    CKS(residual_state(ctx, P, D.x, D.eg, P.state_alpha, D.F, &nrm, &flag));
+    const double save = P.params.krylov_rtol;
+    const int saveprec = P.params.precision;
+    P.params.krylov_rtol = rtol;
+    P.params.precision = precision;
+    hpg_status st = (precision == HPG_FP64) ? factor_T<double>(ctx, P, P.state_alpha, nullptr)
+                                            : factor_T<float>(ctx, P, P.state_alpha, nullptr);
+    int sweeps = 0, it = 0;
+    if (st == HPG_OK) st = linear_solve(ctx, P, P.state_alpha, D.F, nrm, rtol, D.delta, &it, &sweeps);
+    P.params.krylov_rtol = save;
+    P.params.precision = saveprec;
+    if (st != HPG_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(delta, D.delta, (P.H.Nu0 + P.H.Npsi) * sizeof(double), cudaMemcpyDeviceToHost));
+    if (its) *its = it;
+    return HPG_OK;
+}
+
+}  // namespace hpg

@@ -1,0 +1,107 @@
+// Per-problem device state and the solver driver of libhpg.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "device.h"
+
+namespace hpg {
+
+// Device copy of one 1D stencil for both precisions.
+struct DevSten {
+    int* cnt = nullptr;
+    int* col = nullptr;
+    double* vd = nullptr;
+    float* vf = nullptr;
+};
+
+struct DevState {
+    // constant operators
+    DevSten A[kMaxDim], M[kMaxDim], B[kMaxDim], BT[kMaxDim], Bd[kMaxDim], BdT[kMaxDim];
+    double *Vq_d = nullptr, *wq_d = nullptr, *Mpsi_d = nullptr, *Kpsi_d = nullptr, *C_d = nullptr;
+    float *Vq_f = nullptr, *wq_f = nullptr, *Mpsi_f = nullptr, *Kpsi_f = nullptr, *C_f = nullptr;
+    double *V_d[kMaxDim] = {}, *lam_d[kMaxDim] = {};
+    float *V_f[kMaxDim] = {}, *lam_f[kMaxDim] = {};
+    Geo<double> gd{};
+    Geo<float> gf{};
+    // data
+    double *rA = nullptr, *rB = nullptr, *bf = nullptr, *phiz = nullptr, *phiq = nullptr;
+    // state: x = [u (interior); psi] contiguous so Newton updates are one axpy
+    double *x = nullptr, *xt = nullptr;          // current and trial
+    double *psi_prev = nullptr;
+    double *gw = nullptr, *gwt = nullptr;        // Gauss weights (current, trial)
+    float* gwf = nullptr;                        // FP32 copy of gw
+    double *eg = nullptr, *egt = nullptr;
+    double *F = nullptr, *Ft = nullptr, *delta = nullptr, *r = nullptr, *dcorr = nullptr;
+    double* Sinv_d = nullptr;
+    float* Sinv_f = nullptr;
+    // Schur temporaries
+    double *tu_d = nullptr, *w1_d = nullptr, *w2_d = nullptr, *tu2_d = nullptr;
+    float *tu_f = nullptr, *tu2_f = nullptr, *w1_f = nullptr, *w2_f = nullptr;
+    double *zp_d = nullptr, *yp = nullptr, *xs = nullptr;
+    float *zp_f = nullptr;
+    double* part = nullptr;      // residual partials
+    double* scal = nullptr;      // [0] |F|^2 reduce target, ...
+    int* flag = nullptr;         // eval/factor flags
+    GmresDev gm{};
+    // pinned host mirror for scalars
+    double* h_scal = nullptr;
+    int* h_iflag = nullptr;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+};
+
+struct KernelTimer {
+    bool on = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[HPG_K_COUNT] = {};
+    long long launches[HPG_K_COUNT] = {};
+};
+
+struct Problem {
+    int id = 0;
+    HostProblem H;
+    hpg_params params{};
+    bool alloc_done = false;
+    bool dirichlet_set = false;
+    DevState D;
+    hpg_stats stats{};
+    bool solved = false;
+    double state_alpha = 0.0;
+    KernelTimer timer;
+};
+
+}  // namespace hpg
+
+struct hpg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::map<int, std::unique_ptr<hpg::Problem>> problems;
+    int next_id = 1;
+    std::string err;
+};
+
+namespace hpg {
+
+hpg_status alloc_device(hpg_ctx* ctx, Problem& P);
+void free_device(Problem& P);
+hpg_status upload_data(hpg_ctx* ctx, Problem& P);
+hpg_status solve_problem(hpg_ctx* ctx, Problem& P);
+hpg_status solve_batch(hpg_ctx* ctx, std::vector<Problem*>& probs);
+// component operators
+hpg_status op_set_state(hpg_ctx* ctx, Problem& P, const double* u_full, const double* psi, const double* psi_prev,
+                        double alpha);
+hpg_status op_residual(hpg_ctx* ctx, Problem& P, double* F, double* norm);
+hpg_status op_apply_newton(hpg_ctx* ctx, Problem& P, const double* x, double* y);
+hpg_status op_stiffness_inv(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y);
+hpg_status op_factor(hpg_ctx* ctx, Problem& P, int precision, double* blocks);
+hpg_status op_precond_inv(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y);
+hpg_status op_schur(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y);
+hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double rtol, double* delta, int* its);
+
+}  // namespace hpg
