@@ -117,6 +117,8 @@ typedef struct {
     double solve_ms;                       /* wall time of the last hpg_solve (host clock) */
     long long n_u;                         /* interior u unknowns                          */
     long long n_psi;                       /* psi unknowns                                 */
+    long long kernel_launches;             /* libhpg kernels launched by the last solve    */
+    long long h2d_bytes;                   /* problem data copied host->device by it       */
 } hpg_stats;
 
 /* Kernel classes timed when hpg_params.timing = 1. */

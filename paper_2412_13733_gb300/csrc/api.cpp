@@ -167,6 +167,7 @@ hpg_status hpg_set_rhs(hpg_ctx* ctx, int pid, hpg_field_fn f, void* user) {
     if (!P || !f) return HPG_ERR_ARG;
     GUARD_BEGIN
     hpg::compute_rhs(P->H, f, user, false, 0.0);
+    P->data_dirty = true;
     return HPG_OK;
     GUARD_END
 }
@@ -176,6 +177,7 @@ hpg_status hpg_set_rhs_const(hpg_ctx* ctx, int pid, double f) {
     if (!P || !std::isfinite(f)) return HPG_ERR_ARG;
     GUARD_BEGIN
     hpg::compute_rhs(P->H, nullptr, nullptr, true, f);
+    P->data_dirty = true;
     return HPG_OK;
     GUARD_END
 }
@@ -203,6 +205,7 @@ hpg_status hpg_set_constraint_values(hpg_ctx* ctx, int pid, const double* phi_q,
             if (!(phi_q[i] > 0.0)) { ctx->err = "gradient constraint must be positive"; return HPG_ERR_ARG; }
     GUARD_BEGIN
     hpg::compute_phi(P->H, phi_q);
+    P->phi_dirty = true;
     return HPG_OK;
     GUARD_END
 }
@@ -226,6 +229,7 @@ hpg_status hpg_set_dirichlet(hpg_ctx* ctx, int pid, hpg_field_fn g, void* user) 
     for (double v : P->H.ulift)
         if (!std::isfinite(v)) { ctx->err = "non-finite Dirichlet data"; return HPG_ERR_NONFINITE; }
     P->dirichlet_set = g != nullptr;
+    P->data_dirty = true;
     return HPG_OK;
     GUARD_END
 }
@@ -260,7 +264,10 @@ hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params) {
         (params->precision != HPG_FP64 && params->precision != HPG_MIXED) || params->ls_max < 0)
         return HPG_ERR_ARG;
     const bool realloc = P->alloc_done && params->krylov_max != P->params.krylov_max;
-    if (realloc) hpg::free_device(*P);
+    if (realloc) {
+        hpg::free_device(*P);
+        P->data_dirty = P->phi_dirty = true;
+    }
     P->params = *params;
     return HPG_OK;
 }

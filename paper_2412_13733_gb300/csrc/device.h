@@ -48,6 +48,11 @@ inline int gauss_stride(int kind, int d) { return kind == HPG_GRADIENT ? d * (d 
 cudaError_t launch_eval(const Geo<double>& g, const double* psi, const double* phiq, double* gw, float* gwf,
                         double* eg, int* flag, cudaStream_t s);
 
+// phiz = (phi, zeta) from phi at the latent Gauss points (obstacle kinds).
+cudaError_t launch_project(const Geo<double>& g, const double* phiq, double* phiz, cudaStream_t s);
+// Number of kernels launched by this library since load.
+long long kernel_launch_count();
+
 // F_u = alpha A u + alpha rA + B (psi - psi_prev) - alpha bf;  F_psi = B^T u + rB + sgn*eg - phiz.
 // Writes F (Nu0 + Npsi) and block partial sums of squares into part (see n_res_partials).
 cudaError_t launch_residual(const Geo<double>& g, const double* u, const double* psi, const double* psi_prev,

@@ -3,6 +3,7 @@
 // matrix-free Newton and Schur operators by sum factorisation and sparse
 // Kronecker stencils, the S-hat cell-block factorisation, the fast-diagonalisation
 // inverse of A_alpha, and GMRES.
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 
@@ -12,7 +13,8 @@ namespace hpg {
 
 namespace {
 
-constexpr int kRedThreads = 256;
+std::atomic<long long> g_launches{0};
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* sh) {
@@ -177,6 +179,8 @@ __device__ __forceinline__ void sf_pass(const T* in, T* out, const T* mat, bool 
 
 }  // namespace
 
+long long kernel_launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 // ====================================================================== eval
 // Obstacle: g_q = w_q |J| exp(-psi(x_q)), eg = V^T g per cell (Section 5, Quadrature).
 // Gradient: psi_q (d comps), s = 1 + |psi_q|^2, G = phi psi / sqrt(s) projected into eg,
@@ -250,6 +254,41 @@ cudaError_t launch_eval(const Geo<double>& g, const double* psi, const double* p
     const size_t smem = (size_t)(2 * g.ncomp * g.nloc + g.n * g.n) * sizeof(double);
     const int threads = g.nloc * g.ncomp >= 256 ? 256 : 128;
     k_eval<<<(unsigned)g.Nc, threads, smem, s>>>(g, psi, phiq, gw, gwf, eg, flag);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// (phi, zeta) = V^T (w |J| phi_q) per cell (the same Gauss rule as the latent terms)
+__global__ void k_project(Geo<double> g, const double* __restrict__ phiq, double* __restrict__ phiz) {
+    extern __shared__ double sm[];
+    const int n = g.n, nloc = (int)g.nloc;
+    double* a = sm;
+    double* b = sm + nloc;
+    double* Vq = sm + 2 * nloc;
+    const long long c = blockIdx.x;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Vq[i] = g.Vq[i];
+    for (int q = threadIdx.x; q < nloc; q += blockDim.x) {
+        double w = g.detJ;
+        int qq = q;
+        for (int ax = 0; ax < g.d; ++ax) { w *= g.wq[qq % n]; qq /= n; }
+        a[q] = w * phiq[c * nloc + q];
+    }
+    __syncthreads();
+    double *in = a, *out = b;
+    int stride = 1;
+    for (int ax = 0; ax < g.d; ++ax) {
+        sf_pass(in, out, Vq, true, n, nloc, 1, stride);
+        __syncthreads();
+        double* t = in; in = out; out = t;
+        stride *= n;
+    }
+    for (int i = threadIdx.x; i < nloc; i += blockDim.x) phiz[c * nloc + i] = in[i];
+}
+
+cudaError_t launch_project(const Geo<double>& g, const double* phiq, double* phiz, cudaStream_t s) {
+    const size_t smem = (size_t)(2 * g.nloc + g.n * g.n) * sizeof(double);
+    k_project<<<(unsigned)g.Nc, 128, smem, s>>>(g, phiq, phiz);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -308,10 +347,14 @@ cudaError_t launch_residual(const Geo<double>& g, const double* u, const double*
     const int bu = (int)((g.Nu0 + 255) / 256), bp = (int)((g.Npsi + 255) / 256);
     if (g.d == 2) {
         k_residual_u<2><<<bu, 256, 0, s>>>(g, u, psi, psi_prev, rA, bf, alpha, F, part);
+        note_launch();
         k_residual_psi<2><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
+        note_launch();
     } else {
         k_residual_u<3><<<bu, 256, 0, s>>>(g, u, psi, psi_prev, rA, bf, alpha, F, part);
+        note_launch();
         k_residual_psi<3><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
+        note_launch();
     }
     return cudaGetLastError();
 }
@@ -326,6 +369,7 @@ __global__ void k_reduce_sum(const double* __restrict__ part, int count, double*
 
 cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaStream_t s) {
     k_reduce_sum<<<1, 1024, 0, s>>>(part, count, out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -488,6 +532,7 @@ cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double bet
     }
     k_factor<T><<<(unsigned)g.Nc, 256, use_smem ? bytes : 0, s>>>(g, gw, (T)(1.0 / alpha), (T)beta, Sinv, dump,
                                                                  flag, gwork, use_smem);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -512,6 +557,7 @@ template <typename T, typename Tin, typename Tout>
 cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s) {
     const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
     k_precond<T, Tin, Tout><<<(unsigned)g.Nc, threads, g.nb * sizeof(T), s>>>(g, Sinv, v, z);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -530,6 +576,7 @@ cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s
     const unsigned b = (unsigned)((g.Nu0 + 255) / 256);
     if (g.d == 2) k_bapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y);
     else k_bapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -552,6 +599,7 @@ cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t 
     const unsigned b = (unsigned)((g.Npsi + 255) / 256);
     if (g.d == 2) k_btapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y);
     else k_btapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -568,6 +616,7 @@ cudaError_t launch_aapply(const Geo<double>& g, const double* x, double* y, cuda
     const unsigned b = (unsigned)((g.Nu0 + 255) / 256);
     if (g.d == 2) k_aapply<2><<<b, 256, 0, s>>>(g, x, y);
     else k_aapply<3><<<b, 256, 0, s>>>(g, x, y);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -641,6 +690,7 @@ static cudaError_t gemm(const GemmArgs& a, const T* A, const T* B, T* C, cudaStr
     constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2;
     dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch);
     k_gemm<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(a, A, B, C);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -704,6 +754,7 @@ cudaError_t launch_fdm(const Geo<T>& g, double alpha, const T* x, T* y, T* work1
     }
     const unsigned blocks = (unsigned)((g.Nu0 + 255) / 256);
     k_fdm_scale<T><<<blocks, 256, 0, s>>>(g, (T)(1.0 / alpha), const_cast<T*>(cur));
+    note_launch();
     for (int ax = 0; ax < d; ++ax) {
         T* dst = (ax == d - 1) ? y : bufs[bi];
         if ((e = pass(ax, false, cur, dst)) != cudaSuccess) return e;
@@ -798,6 +849,7 @@ cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T
         k_cellop<2, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w);
     else
         k_cellop<3, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -819,12 +871,16 @@ cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double a
     const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
     if (g.d == 2) {
         k_newton_u<2><<<bu, 256, 0, s>>>(g, alpha, x, x + g.Nu0, y);
+        note_launch();
         k_cellop<2, double, double, double, double><<<(unsigned)g.Nc, threads, smem, s>>>(
             g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0);
+        note_launch();
     } else {
         k_newton_u<3><<<bu, 256, 0, s>>>(g, alpha, x, x + g.Nu0, y);
+        note_launch();
         k_cellop<3, double, double, double, double><<<(unsigned)g.Nc, threads, smem, s>>>(
             g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0);
+        note_launch();
     }
     return cudaGetLastError();
 }
@@ -838,6 +894,7 @@ __global__ void k_convert(const Tin* __restrict__ x, Tout* __restrict__ y, long 
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin* x, Tout* y, long long n, cudaStream_t s) {
     k_convert<Tin, Tout><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -847,6 +904,7 @@ __global__ void k_axpby(double a, const double* __restrict__ x, double b, double
 }
 cudaError_t launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s) {
     k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, x, b, y, n);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -859,6 +917,7 @@ __global__ void k_sub_scaled(const double* __restrict__ x, double b, const T* __
 template <typename T>
 cudaError_t launch_sub_scaled(const double* x, double b, const T* z, double* y, long long n, cudaStream_t s) {
     k_sub_scaled<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, b, z, y, n);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -869,6 +928,7 @@ __global__ void k_trial(const double* __restrict__ x, const double* __restrict__
 }
 cudaError_t launch_trial(const double* x, const double* dx, double lam, double* xt, long long n, cudaStream_t s) {
     k_trial<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, dx, lam, xt, n);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -885,6 +945,7 @@ cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts
     if (b > 1024) b = 1024;
     if (b < 1) b = 1;
     k_sumsq<<<b, 256, 0, s>>>(x, n, part);
+    note_launch();
     *nparts = b;
     return cudaGetLastError();
 }
@@ -1046,6 +1107,7 @@ cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t 
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(G.H, 0, sizeof(double) * (size_t)(G.kmax + 1) * G.kmax, s);
     k_gm_start<<<G.blocks, 256, 0, s>>>(G.Vb, b, G.N, G.part, np, rtol, G.scal, G.gv, G.kmax, G.iflag);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1054,11 +1116,16 @@ cudaError_t gmres_arnoldi(GmresDev& G, int j, cudaStream_t s) {
     double* h2 = G.y;   // scratch for the second CGS pass
     // CGS pass 1 (writes h into H column), update; pass 2 (h2), update + norm; finalize adds h2
     k_gm_dots<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, G.part, hcol, 0, G.counter, G.iflag);
+    note_launch();
     k_gm_update<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, hcol, G.part + (size_t)G.blocks * (G.kmax + 1), G.iflag);
+    note_launch();
     k_gm_dots<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, G.part, h2, 0, G.counter, G.iflag);
+    note_launch();
     k_gm_update<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, h2, G.part + (size_t)G.blocks * (G.kmax + 1), G.iflag);
+    note_launch();
     k_gm_finalize<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, G.part + (size_t)G.blocks * (G.kmax + 1), G.H, G.cs, G.sn,
                                            G.gv, G.scal, G.iflag, G.kmax, h2);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1068,7 +1135,9 @@ cudaError_t gmres_finish(GmresDev& G, int k, double* x, cudaStream_t s) {
         return cudaGetLastError();
     }
     k_gm_backsolve<<<1, 32, 0, s>>>(G.H, G.gv, k, G.kmax, G.y);
+    note_launch();
     k_gm_combine<<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(G.Vb, G.y, k, G.N, x);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -557,28 +557,9 @@ void compute_rhs(HostProblem& P, hpg_field_fn f, void* user, bool is_const, doub
     }
 }
 
-// (phi, zeta) by the q = n Gauss rule from phi at the latent points.
+// phi at the latent Gauss points (sign applied); (phi, zeta) is formed on the device.
 void compute_phi(HostProblem& P, const double* phi_q) {
-    const int d = P.d, n = P.n;
     for (size_t i = 0; i < P.Nq; ++i) P.phiq[i] = P.sign * phi_q[i];
-    std::fill(P.phiz.begin(), P.phiz.end(), 0.0);
-    if (P.kind == HPG_GRADIENT) { P.has_phi = true; return; }
-    for (size_t c = 0; c < P.Nc; ++c)
-        for (size_t k = 0; k < P.nloc; ++k) {
-            double s = 0.0;
-            for (size_t q = 0; q < P.nloc; ++q) {
-                size_t qq = q, kk = k;
-                double v = P.detJ;
-                for (int j = 0; j < d; ++j) {
-                    int qi = (int)(qq % n), ki = (int)(kk % n);
-                    qq /= n;
-                    kk /= n;
-                    v *= P.wq[qi] * P.Vq[(size_t)qi * n + ki];
-                }
-                s += v * P.phiq[c * P.nloc + q];
-            }
-            P.phiz[c * P.nloc + k] = s;
-        }
     P.has_phi = true;
 }
 

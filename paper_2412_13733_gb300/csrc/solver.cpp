@@ -271,11 +271,20 @@ hpg_status upload_data(hpg_ctx* ctx, Problem& P) {
     HostProblem& H = P.H;
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
-    CK(cudaMemcpyAsync(D.rA, H.rA.data(), H.Nu0 * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(D.rB, H.rB.data(), H.Npsi * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(D.bf, H.bf.data(), H.Nu0 * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(D.phiz, H.phiz.data(), H.Npsi * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(D.phiq, H.phiq.data(), H.Nq * sizeof(double), cudaMemcpyHostToDevice, s));
+    P.h2d_bytes = 0;
+    if (P.data_dirty) {
+        CK(cudaMemcpyAsync(D.rA, H.rA.data(), H.Nu0 * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(D.rB, H.rB.data(), H.Npsi * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(D.bf, H.bf.data(), H.Nu0 * sizeof(double), cudaMemcpyHostToDevice, s));
+        P.h2d_bytes += (long long)(2 * H.Nu0 + H.Npsi) * (long long)sizeof(double);
+        P.data_dirty = false;
+    }
+    if (P.phi_dirty) {
+        CK(cudaMemcpyAsync(D.phiq, H.phiq.data(), H.Nq * sizeof(double), cudaMemcpyHostToDevice, s));
+        P.h2d_bytes += (long long)H.Nq * (long long)sizeof(double);
+        if (H.kind != HPG_GRADIENT) CK(launch_project(D.gd, D.phiq, D.phiz, s));
+        P.phi_dirty = false;
+    }
     CK(cudaStreamSynchronize(s));
     return HPG_OK;
 }
@@ -526,6 +535,7 @@ static void swap_state(DevState& D) {
 
 hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
     auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = kernel_launch_count();
     HostProblem& H = P.H;
     CKS(alloc_device(ctx, P));
     DevState& D = P.D;
@@ -591,6 +601,8 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
     }
     st.final_residual = normF;
     st.status = status;
+    st.kernel_launches = kernel_launch_count() - launches0;
+    st.h2d_bytes = P.h2d_bytes;
     CK(cudaStreamSynchronize(s));
     timer_flush(P.timer);
     st.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

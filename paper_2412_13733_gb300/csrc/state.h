@@ -68,6 +68,9 @@ struct Problem {
     hpg_params params{};
     bool alloc_done = false;
     bool dirichlet_set = false;
+    bool data_dirty = true;      // f load / lifting terms changed since the last upload
+    bool phi_dirty = true;       // constraint values changed since the last upload
+    long long h2d_bytes = 0;     // bytes uploaded by the last upload_data
     DevState D;
     hpg_stats stats{};
     bool solved = false;
