@@ -175,6 +175,31 @@ def alu_peak_tflops(kind, clock_mhz):
     return 1.25 * clock_mhz / 2070.0
 
 
+def kernel_only(args, ctx, w, stream, hpg, torch):
+    """Launch one kernel class `steps` times on a seeded synthetic Newton state of
+    the workload (no solve), for ncu captures and per-kernel timing."""
+    prec = hpg.HPG_MIXED if args.precision == "mixed" else hpg.HPG_FP64
+    P = hpg.from_workload(ctx, w, hpg.default_params(precision=prec))
+    rng = np.random.default_rng(7)
+    u = np.zeros(P.n_u_full)
+    psi = 0.3 * rng.standard_normal(P.n_psi)
+    P.set_state(u, psi, np.zeros(P.n_psi), w["alphas"][-1])
+    P.factor_precond(prec)
+    P.launch_kernel(args.kernel, prec, args.steps)          # capture + first replay
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.launch_kernel(args.kernel, prec, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": args.kernel, "precision": args.precision, "launches": args.steps,
+                      "avg_us": 1000.0 * e0.elapsed_time(e1) / args.steps}), flush=True)
+    P.free()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,6 +208,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-kernel-timing", action="store_true")
+    ap.add_argument("--kernel", default=None,
+                    help="kernel-only mode (profiling): synthetic state, `--steps` launches of one kernel class")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--batch", type=int, default=8, help="independent solves in flight per step")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -206,7 +237,8 @@ def main():
             dist.barrier()
 
     w = W.workload(WORKLOAD)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()             # libhpg launches (and its CUDA graphs) go to this stream
+    torch.cuda.set_stream(stream)
     ctx = hpg.Context(local_rank, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > 126 MB L2
     peaks, peak_src = load_peaks()
@@ -232,95 +264,133 @@ def main():
             times.append(e0.elapsed_time(e1))
         return times, d2h
 
-    results = {}
-    precisions = [("mixed", hpg.HPG_MIXED)] + ([] if args.no_fp64 else [("fp64", hpg.HPG_FP64)])
-    clocks = None
-    for name, prec in precisions:
-        P = hpg.from_workload(ctx, w, hpg.default_params(precision=prec))
+    if args.kernel:
+        return kernel_only(args, ctx, w, stream, hpg, torch)
+
+    B = args.batch
+
+    def make(prec, count):
+        ps = [hpg.from_workload(ctx, w, hpg.default_params(precision=prec)) for _ in range(count)]
+        return ps
+
+    def run_steps(ps, steps, e2e=False, host_phi=None):
+        """K timed steps; one step = len(ps) complete solves (batched when > 1)."""
+        times, d2h = [], 0
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if e2e:
+                for P in ps:
+                    P.set_constraint_values(host_phi)
+            if len(ps) == 1:
+                ps[0].solve()
+            else:
+                ctx.solve_batch(ps)
+            if e2e:
+                d2h = 0
+                for P in ps:
+                    P.u()
+                    P.psi()
+                    d2h += 8 * (P.n_u + P.n_psi)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times, d2h
+
+    def leg(name, prec, count, with_e2e, with_kernels, sampler=None):
+        ps = make(prec, count)
         for _ in range(args.warmup):
-            P.solve()
-        st = P.stats()
-        sampler = ClockSampler(local_rank) if name == "mixed" else None
+            run_steps(ps, 1)
         if sampler:
             sampler.start()
         barrier()
         torch.cuda.synchronize()
-        t_wall0 = time.perf_counter()
-        times, _ = timed(P, args.steps)
+        times, _ = run_steps(ps, args.steps)
         torch.cuda.synchronize()
         barrier()
-        t_wall = time.perf_counter() - t_wall0
-        if sampler:
-            clocks = sampler.stop()
-        st = P.stats()
+        clk = sampler.stop() if sampler else None
         total_ms = sum(times)
         if dist is not None:
             t = torch.tensor([total_ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = float(t.item())
-        dofs = P.n_u + P.n_psi
-        res = dict(value=world * args.steps / (total_ms / 1000.0), ms_per_step=total_ms / args.steps,
-                   wall_s=t_wall, newton=st["newton_total"], krylov=st["krylov_total"],
-                   refine=st["refine_total"], launches=st["kernel_launches"],
-                   dof_krylov_per_s=world * dofs * st["krylov_total"] / (total_ms / args.steps / 1000.0))
-        # e2e through the C ABI with host buffers
-        host_phi = np.ascontiguousarray(w["phi"](P.quad_points()), dtype=np.float64)
-        host_phi_pinned = torch.from_numpy(host_phi).pin_memory().numpy()
-        times_e2e, d2h = timed(P, args.steps, e2e=True, host_phi=host_phi_pinned)
-        st2 = P.stats()
-        e2e_ms = sum(times_e2e)
-        res["e2e"] = dict(value=world * args.steps / (e2e_ms / 1000.0), unit="solves/s",
-                          h2d_bytes_per_step=int(st2["h2d_bytes"]), d2h_bytes_per_step=int(d2h))
-        # per-kernel-class device time: a second pass of the same steps with event pairs
-        prm = hpg.default_params(precision=prec, timing=1)
-        prm.beta = w["beta"]
-        P.set_params(prm)
-        P.solve()
-        P.reset_kernel_times()
-        for _ in range(args.steps):
-            flush.zero_()
-            P.solve()
-        torch.cuda.synchronize()
-        res["kernels"] = P.kernel_times()
-        res["work"] = algorithmic_work(P, w)
-        results[name] = res
-        P.free()
+        st = ps[0].stats()
+        dofs = ps[0].n_u + ps[0].n_psi
+        kry = sum(P.stats()["krylov_total"] for P in ps)
+        res = dict(value=world * count * args.steps / (total_ms / 1000.0), ms_per_step=total_ms / args.steps,
+                   batch=count, newton=st["newton_total"], krylov=st["krylov_total"], refine=st["refine_total"],
+                   launches=sum(P.stats()["kernel_launches"] for P in ps),
+                   dof_krylov_per_s=world * dofs * kry / (total_ms / args.steps / 1000.0), clocks=clk,
+                   h2d=int(sum(P.stats()["h2d_bytes"] for P in ps)))
+        res["e2e"] = None
+        if with_e2e and not args.no_e2e:
+            host_phi = np.ascontiguousarray(w["phi"](ps[0].quad_points()), dtype=np.float64)
+            host_phi_pinned = torch.from_numpy(host_phi).pin_memory().numpy()
+            times_e2e, d2h = run_steps(ps, args.steps, e2e=True, host_phi=host_phi_pinned)
+            e2e_ms = sum(times_e2e)
+            res["e2e"] = dict(value=world * count * args.steps / (e2e_ms / 1000.0), unit="solves/s",
+                              h2d_bytes_per_step=int(sum(P.stats()["h2d_bytes"] for P in ps)),
+                              d2h_bytes_per_step=int(d2h))
+        res["kernels"] = {}
+        if with_kernels and not args.no_kernel_timing:
+            P = ps[0]
+            for cls, reps in (("fdm", 50), ("precond", 50), ("bapply", 50), ("schur", 50),
+                              ("newton_apply", 50), ("factor", 5), ("eval", 20)):
+                P.launch_kernel(cls, prec, reps)          # captures the graph and runs it once
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.launch_kernel(cls, prec, reps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res["kernels"][cls] = (e0.elapsed_time(e1) / reps, reps)
+        res["work"] = algorithmic_work(ps[0], w)
+        for P in ps:
+            P.free()
+        return res
+
+    ctx.set_concurrency(B)
+    results = {}
+    results["mixed_batch"] = leg("mixed_batch", hpg.HPG_MIXED, B, True, False, ClockSampler(local_rank))
+    clocks = results["mixed_batch"]["clocks"]
+    results["mixed"] = leg("mixed", hpg.HPG_MIXED, 1, False, True)
+    if not args.no_fp64:
+        results["fp64"] = leg("fp64", hpg.HPG_FP64, 1, True, True)
+        results["fp64_batch"] = leg("fp64_batch", hpg.HPG_FP64, B, False, False)
 
     mixed = results["mixed"]
-    # dominant kernel of the headline (mixed) path
-    kt = mixed["kernels"]
-    dom = max(kt, key=lambda k: kt[k][0])
-    clock_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_mhz = peaks.get("sm_max_mhz", 2070.0)
     work = mixed["work"]
+    kt = mixed["kernels"]
     roof = None
-    if dom in ("fdm", "factor", "newton_apply"):
-        kind, flops, unit = work[dom]
-        avg_ms = kt[dom][0] / max(kt[dom][1], 1)
+    if "fdm" in kt:
+        # the fast-diagonalisation A_alpha^{-1} apply (2d GEMM passes, FP32 in the mixed path)
+        _, flops, unit = work["fdm"]
+        avg_ms = kt["fdm"][0]
         ach = flops / (avg_ms / 1000.0) / 1e12
-        fp = "fp64" if dom == "newton_apply" else "fp32"
-        peak = alu_peak_tflops(fp, peaks.get("sm_max_mhz", 2070.0))
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "traffic": None, "peak_source": f"derived {fp} ALU peak at {peaks.get('sm_max_mhz', 2070.0)} MHz"}
-    elif dom == "precond":
-        kind, byts, unit = work["precond"]
-        avg_ms = kt[dom][0] / max(kt[dom][1], 1)
-        ach = byts / (avg_ms / 1000.0) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src}
-    else:
-        avg_ms = kt[dom][0] / max(kt[dom][1], 1)
-        roof = {"kernel": dom, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None, "avg_launch_ms": avg_ms}
-    # FP64 matrix-free Newton apply (the refinement residual kernel) against its own roofline
-    na = kt.get("newton_apply", (0.0, 0))
+        peak = alu_peak_tflops("fp32", peak_mhz)
+        roof = {"kernel": "fdm (A_alpha^-1, FP32 SIMT GEMM passes)", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": unit, "frac": ach / peak, "traffic": None, "avg_launch_us": avg_ms * 1000.0,
+                "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x {peak_mhz:.0f} MHz"}
     newton_roof = None
-    if na[1] > 0:
-        avg = na[0] / na[1] / 1000.0
+    if "newton_apply" in kt:
+        avg = kt["newton_apply"][0] / 1000.0
         _, fl, _ = work["newton_apply"]
-        t_alu = fl / (alu_peak_tflops("fp64", peaks.get("sm_max_mhz", 2070.0)) * 1e12)
+        t_alu = fl / (alu_peak_tflops("fp64", peak_mhz) * 1e12)
         t_hbm = work["newton_apply_bytes"] / (peaks["hbm_gbs"] * 1e9)
-        newton_roof = {"bound": "alu" if t_alu > t_hbm else "hbm", "roofline_us": max(t_alu, t_hbm) * 1e6,
-                       "avg_us": avg * 1e6, "frac": max(t_alu, t_hbm) / avg}
+        newton_roof = {"kernel": "matrix-free Newton apply G x (FP64)", "bound": "alu" if t_alu > t_hbm else "hbm",
+                       "roofline_us": max(t_alu, t_hbm) * 1e6, "avg_us": avg * 1e6, "frac": max(t_alu, t_hbm) / avg}
+    fp64_fdm = None
+    if "fp64" in results and "fdm" in results["fp64"]["kernels"]:
+        _, flops, _ = results["fp64"]["work"]["fdm"]
+        avg_ms = results["fp64"]["kernels"]["fdm"][0]
+        ach = flops / (avg_ms / 1000.0) / 1e12
+        pk = alu_peak_tflops("fp64", peak_mhz)
+        fp64_fdm = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "avg_launch_us": avg_ms * 1000.0, "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -330,25 +400,32 @@ def main():
                           f"Newton steps, {s['seconds']:.1f} s), extrapolated linearly in Newton steps")}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": mixed["value"], "unit": "solves/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"],
+        head = results["mixed_batch"]
+        fp = results.get("fp64")
+        line = {"metric": METRIC, "value": head["value"], "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic (analytic radial obstacle; no dataset)",
                 "config": {"workload": "radial obstacle 32x32 cells p=8 (66049 u-dofs, 50176 psi-dofs), "
                                        "10 alpha steps, Newton tol 1e-10",
+                           "batch": f"{B} independent solves in flight per step (hpg_solve_batch, {B} streams)",
                            "precision": "FP32 inner Schur/GMRES operator in FP64 iterative refinement",
                            "l2_flush": "256 MB buffer zeroed before every timed step",
                            "parallelism": f"replicas x{world}"},
-                "dof_krylov_its_per_s": mixed["dof_krylov_per_s"],
-                "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
-                         "dof_krylov_its_per_s": results["fp64"]["dof_krylov_per_s"],
-                         "e2e": results["fp64"]["e2e"], "newton": results["fp64"]["newton"],
-                         "krylov": results["fp64"]["krylov"]} if "fp64" in results else None,
-                "mixed_over_fp64": (mixed["value"] / results["fp64"]["value"]) if "fp64" in results else None,
-                "newton": mixed["newton"], "krylov": mixed["krylov"], "refine_sweeps": mixed["refine"],
-                "e2e": mixed["e2e"], "gpu_launches": int(mixed["launches"] * args.steps),
+                "dof_krylov_its_per_s": head["dof_krylov_per_s"],
+                "single_solve": {"mixed": {"solves_per_s": mixed["value"], "latency_ms": mixed["ms_per_step"],
+                                           "krylov": mixed["krylov"], "refine_sweeps": mixed["refine"]},
+                                 "fp64": ({"solves_per_s": fp["value"], "latency_ms": fp["ms_per_step"],
+                                           "krylov": fp["krylov"], "e2e": fp["e2e"],
+                                           "kernel_avg_us": {k: v[0] * 1000.0 for k, v in fp["kernels"].items()},
+                                           "fdm_roofline": fp64_fdm} if fp else None)},
+                "fp64_batch": ({"solves_per_s": results["fp64_batch"]["value"],
+                                "ms_per_step": results["fp64_batch"]["ms_per_step"]} if fp else None),
+                "mixed_batch_over_fp64_single": (head["value"] / fp["value"]) if fp else None,
+                "newton": head["newton"], "krylov": head["krylov"], "refine_sweeps": head["refine"],
+                "e2e": head["e2e"], "gpu_launches": int(head["launches"] * args.steps),
                 "roofline": roof, "newton_apply_roofline": newton_roof,
-                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+                "kernel_avg_us": {k: v[0] * 1000.0 for k, v in kt.items()},
                 "clocks": clocks, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -200,9 +200,16 @@ hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params);
  * failure (also in hpg_stats.status). */
 hpg_status hpg_solve(hpg_ctx* ctx, int pid);
 
-/* Solve several problems (each as by hpg_solve, in the order given).
- * Returns HPG_OK if every problem converged; per-problem status in stats. */
+/* Solve several independent problems with their work overlapping on the
+ * device: up to hpg_set_concurrency() host workers, each on its own CUDA
+ * stream forked from (and joined back to) the context's stream, take the
+ * problems in order.  Each problem's arithmetic is exactly that of hpg_solve,
+ * so a result does not depend on what else is in the batch.  Ids must be
+ * distinct.  Blocking.  Returns HPG_OK if every problem converged, else the
+ * first failure in id order; per-problem status in hpg_stats. */
 hpg_status hpg_solve_batch(hpg_ctx* ctx, const int* pids, int count);
+/* Number of concurrent workers/streams of hpg_solve_batch (1..64, default 8). */
+hpg_status hpg_set_concurrency(hpg_ctx* ctx, int streams);
 
 /* Results of the last solve (u in the caller's sign convention). */
 hpg_status hpg_get_u(hpg_ctx* ctx, int pid, double* u_full, size_t len);
@@ -217,6 +224,16 @@ hpg_status hpg_feasible_u(hpg_ctx* ctx, int pid, double* out_q, size_t len);
  * last reset, recorded only when params.timing = 1. */
 hpg_status hpg_get_kernel_times(hpg_ctx* ctx, int pid, double* ms, long long* launches, int count);
 hpg_status hpg_reset_kernel_times(hpg_ctx* ctx, int pid);
+/* Enqueue `reps` back-to-back applications of one kernel class (hpg_kernel_class:
+ * HPG_K_EVAL, _FACTOR, _PRECOND, _BAPPLY, _FDM, _SCHUR or _NEWTON_APPLY) on the
+ * state left by the last solve, in arithmetic `precision`, on the context's
+ * stream, without synchronising: bracket it with CUDA events on that stream
+ * to time the kernels in their solver launch configuration.  The launches are
+ * captured into a CUDA graph on the first call for a given (class, precision,
+ * reps) and replayed on later calls, so time the second call.  Needs a prior
+ * hpg_solve or hpg_set_state (+ hpg_factor_precond for _PRECOND/_SCHUR);
+ * the kernels write only scratch buffers. */
+hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precision, int reps);
 
 /* ------------------------------------------- component operators (testing)
  * These act on an explicit state (u, psi, psi_prev, alpha) uploaded by

@@ -107,8 +107,16 @@ hpg_status hpg_destroy(hpg_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->problems) hpg::free_device(*kv.second);
     ctx->problems.clear();
+    for (auto st : ctx->side_streams) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+    for (auto ev : ctx->side_events) cudaEventDestroy(ev);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+    return HPG_OK;
+}
+
+hpg_status hpg_set_concurrency(hpg_ctx* ctx, int streams) {
+    if (!ctx || streams < 1 || streams > 64) return HPG_ERR_ARG;
+    ctx->concurrency = streams;
     return HPG_OK;
 }
 
@@ -306,6 +314,8 @@ hpg_status hpg_solve_batch(hpg_ctx* ctx, const int* pids, int count) {
     for (int i = 0; i < count; ++i) {
         Problem* P = find(ctx, pids[i]);
         if (!P) return HPG_ERR_ARG;
+        for (Problem* Q : ps)
+            if (Q == P) { ctx->err = "duplicate problem id in batch"; return HPG_ERR_ARG; }
         s = ready(ctx, P);
         if (s != HPG_OK) return s;
         ps.push_back(P);
@@ -495,6 +505,16 @@ hpg_status hpg_newton_direction(hpg_ctx* ctx, int pid, int precision, double rto
     if (!delta || !(rtol > 0.0)) return HPG_ERR_ARG;
     GUARD_BEGIN
     return hpg::op_newton_direction(ctx, *P, precision, rtol, delta, krylov_its);
+    GUARD_END
+}
+
+hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precision, int reps) {
+    Problem* P = find(ctx, pid);
+    if (!P || reps < 0 || kernel_class < 0 || kernel_class >= HPG_K_COUNT) return HPG_ERR_ARG;
+    if (!P->alloc_done || !(P->solved || P->state_alpha > 0.0)) return HPG_ERR_STATE;
+    if (cuda_ok(ctx) != HPG_OK) return HPG_ERR_CUDA;
+    GUARD_BEGIN
+    return hpg::op_launch_kernel(ctx, *P, kernel_class, precision, reps);
     GUARD_END
 }
 

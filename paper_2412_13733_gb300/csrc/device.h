@@ -39,6 +39,15 @@ struct Geo {
 // obstacle: 1 (w |J| exp(-psi)); gradient: packed symmetric d x d Jacobian * w|J|.
 inline int gauss_stride(int kind, int d) { return kind == HPG_GRADIENT ? d * (d + 1) / 2 : 1; }
 
+// Device-side loop control for kernels replayed inside a captured GMRES chunk:
+// `skip` (non-null) makes the kernel return when *skip != 0; `jptr` offsets an
+// input (precond) or output (cell operator) by (*jptr [+1]) * jstride.
+struct IterCtl {
+    const int* skip = nullptr;
+    const int* jptr = nullptr;
+    long long jstride = 0;
+};
+
 // ------------------------------------------------------------ launchers
 // Each launcher enqueues on `s` and returns the CUDA error of the launch.
 
@@ -50,8 +59,9 @@ cudaError_t launch_eval(const Geo<double>& g, const double* psi, const double* p
 
 // phiz = (phi, zeta) from phi at the latent Gauss points (obstacle kinds).
 cudaError_t launch_project(const Geo<double>& g, const double* phiq, double* phiz, cudaStream_t s);
-// Number of kernels launched by this library since load.
+// Number of kernels launched (or replayed in graphs) by this library since load.
 long long kernel_launch_count();
+void add_kernel_launches(long long n);
 
 // F_u = alpha A u + alpha rA + B (psi - psi_prev) - alpha bf;  F_psi = B^T u + rB + sgn*eg - phiz.
 // Writes F (Nu0 + Npsi) and block partial sums of squares into part (see n_res_partials).
@@ -65,31 +75,36 @@ cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaSt
 
 // Assemble -S-hat cell blocks, Cholesky, invert: Sinv (Nc x nb x nb, precision T)
 // holds (-S-hat)^{-1}.  If `dump` is non-null the assembled -S-hat blocks are written there.
+// gwork: global workspace of factor_workspace_elems() elements (null when that is 0).
 template <typename T>
 cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double beta, T* Sinv, double* dump,
-                          int* flag, cudaStream_t s);
+                          int* flag, T* gwork, cudaStream_t s);
 size_t factor_smem_bytes(int nb, int elem);
+size_t factor_workspace_elems(int n, int d, int nb, int nc, long long Nc, int elem);
 
 // z = -Sinv v (per cell), in/out precision mixing: v (Tin), z (Tout).
 template <typename T, typename Tin, typename Tout>
-cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s);
+cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s,
+                           IterCtl ctl = IterCtl{});
 
 // y = B z  (psi -> interior u);  Tin/Tout storage, T compute.
 template <typename T, typename Tin, typename Tout>
-cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s);
+cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s, const int* skip = nullptr);
 
 // y = B^T x (interior u -> psi).
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t s);
 
 // y = A_alpha^{-1} x (interior) by fast diagonalisation; work1/work2 scratch of Nu0.
+// alpha is read from alpha_dev when non-null (graph replay), else alpha.
 template <typename T>
-cudaError_t launch_fdm(const Geo<T>& g, double alpha, const T* x, T* y, T* work1, T* work2, cudaStream_t s);
+cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, const T* x, T* y, T* work1,
+                       T* work2, cudaStream_t s, const int* skip = nullptr);
 
 // w = -(D z + E z + B^T t)  (per cell), D from gw.  z, t in T; w in Tout.
 template <typename T, typename Tout>
 cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T* z, const T* t, Tout* w,
-                              cudaStream_t s);
+                              cudaStream_t s, IterCtl ctl = IterCtl{});
 
 // FP64 matrix-free Newton apply y = G x (eq. pG-matrix) split in two kernels.
 cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
@@ -112,27 +127,34 @@ cudaError_t launch_trial(const double* x, const double* dx, double lam, double* 
 cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts, cudaStream_t s);
 
 // ---- GMRES (right-preconditioned, unrestarted), all state on the device.
+constexpr int kMaxKrylov = 1000;   // upper bound of hpg_params.krylov_max
 struct GmresDev {
     double* Vb;       // (kmax+1) x N basis
     double* H;        // kmax columns of (kmax+1)
     double* cs;       // kmax
     double* sn;       // kmax
     double* gv;       // kmax+1
-    double* part;     // partial sums scratch (>= blocks * (kmax+1))
+    double* part_dots;  // dot-product partials, gmres_dot_blocks(N) x (kmax+1)
+    double* part_norm;  // norm partials, >= max(gmres_upd_blocks(N), 1024)
     double* scal;     // [0] beta0, [1] resid estimate, [2] tol*beta0, [3] h_{j+1,j}
-    int* iflag;       // [0] converged flag, [1] last completed iteration count, [2] breakdown
-    unsigned int* counter;  // block-completion counter for last-block reductions
-    double* y;        // kmax coefficients
+    int* iflag;       // [0] stop flag, [1] completed iterations, [2] breakdown, [3] cap reached
+    int* jdev;        // current iteration index
+    unsigned int* counter;   // last-block counters (dots, finalize)
+    unsigned int* counter2;
+    double* y;        // kmax coefficients (also CGS scratch)
     int kmax;
     long long N;
-    int blocks;       // blocks used by the dot/update kernels
 };
-// r0 = b: beta0 = ||b||, V_0 = b / beta0, g = beta0 e_1, tol*beta0 stored.
+int gmres_dot_blocks(long long N);
+int gmres_upd_blocks(long long N);
+// r0 = b: beta0 = ||b||, V_0 = b / beta0, g = beta0 e_1, tol*beta0 stored, j = 0.
 cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s);
 // After w (= S Shat^{-1} V_j) has been written into Vb[j+1]: CGS2 orthogonalise,
-// normalise, Givens update and convergence flag.  Skipped on device if converged.
-cudaError_t gmres_arnoldi(GmresDev& G, int j, cudaStream_t s);
-// Solve H y = g for k columns and form x = sum_i y_i V_i (x of length N).
-cudaError_t gmres_finish(GmresDev& G, int k, double* x, cudaStream_t s);
+// normalise, Givens update, convergence test, j += 1.  No-op once stopped.
+cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s);
+// Solve H y = g for the completed iterations and form x = sum_i y_i V_i.
+cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s);
+// Opt-in shared-memory limits of the large-smem kernels (call once per device).
+void configure_kernels();
 
 }  // namespace hpg

@@ -180,6 +180,7 @@ __device__ __forceinline__ void sf_pass(const T* in, T* out, const T* mat, bool 
 }  // namespace
 
 long long kernel_launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_kernel_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ====================================================================== eval
 // Obstacle: g_q = w_q |J| exp(-psi(x_q)), eg = V^T g per cell (Section 5, Quadrature).
@@ -512,24 +513,18 @@ static size_t factor_ws_elems(int n, int d, int nb, int nc) {
 
 size_t factor_smem_bytes(int nb, int elem) { return (size_t)nb * nb * elem; }
 
+size_t factor_workspace_elems(int n, int d, int nb, int nc, long long Nc, int elem) {
+    const size_t elems = factor_ws_elems(n, d, nb, nc);
+    return elems * elem <= 200 * 1024 ? 0 : elems * (size_t)Nc;
+}
+
 template <typename T>
 cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double beta, T* Sinv, double* dump,
-                          int* flag, cudaStream_t s) {
+                          int* flag, T* gwork, cudaStream_t s) {
     const size_t elems = factor_ws_elems(g.n, g.d, (int)g.nb, g.ncomp);
     const size_t bytes = elems * sizeof(T);
-    static T* gwork = nullptr;
-    static size_t gwork_elems = 0;
-    int use_smem = bytes <= 200 * 1024;
-    if (use_smem) {
-        cudaFuncSetAttribute(k_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    } else {
-        const size_t need = elems * (size_t)g.Nc;
-        if (need > gwork_elems) {
-            if (gwork) cudaFree(gwork);
-            if (cudaMalloc(&gwork, need * sizeof(T)) != cudaSuccess) { gwork = nullptr; gwork_elems = 0; return cudaErrorMemoryAllocation; }
-            gwork_elems = need;
-        }
-    }
+    const int use_smem = bytes <= 200 * 1024;
+    if (!use_smem && !gwork) return cudaErrorInvalidValue;
     k_factor<T><<<(unsigned)g.Nc, 256, use_smem ? bytes : 0, s>>>(g, gw, (T)(1.0 / alpha), (T)beta, Sinv, dump,
                                                                  flag, gwork, use_smem);
     note_launch();
@@ -537,33 +532,45 @@ cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double bet
 }
 
 // =================================================================== precond
+// z = -(-S-hat_K)^{-1} v per cell (symmetric inverse stored per cell, read once).
 template <typename T, typename Tin, typename Tout>
-__global__ void k_precond(Geo<T> g, const T* __restrict__ Sinv, const Tin* __restrict__ v, Tout* __restrict__ z) {
+__global__ void k_precond(Geo<T> g, const T* __restrict__ Sinv, const Tin* __restrict__ v, Tout* __restrict__ z,
+                          IterCtl ctl) {
     extern __shared__ unsigned char smraw[];
+    if (ctl.skip && *ctl.skip) return;
     T* vs = reinterpret_cast<T*>(smraw);
     const int nb = (int)g.nb;
     const long long cell = blockIdx.x;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) vs[i] = (T)v[cell * nb + i];
+    const Tin* vin = v + (ctl.jptr ? (long long)(*ctl.jptr) * ctl.jstride : 0LL);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) vs[i] = (T)vin[cell * nb + i];
     __syncthreads();
     const T* S = Sinv + cell * (long long)nb * nb;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        T s = T(0);
-        for (int k = 0; k < nb; ++k) s += S[(size_t)k * nb + i] * vs[k];
-        z[cell * nb + i] = (Tout)(-s);
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        int k = 0;
+        for (; k + 3 < nb; k += 4) {
+            s0 += S[(size_t)k * nb + i] * vs[k];
+            s1 += S[(size_t)(k + 1) * nb + i] * vs[k + 1];
+            s2 += S[(size_t)(k + 2) * nb + i] * vs[k + 2];
+            s3 += S[(size_t)(k + 3) * nb + i] * vs[k + 3];
+        }
+        for (; k < nb; ++k) s0 += S[(size_t)k * nb + i] * vs[k];
+        z[cell * nb + i] = (Tout)(-((s0 + s1) + (s2 + s3)));
     }
 }
 
 template <typename T, typename Tin, typename Tout>
-cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s) {
+cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s, IterCtl ctl) {
     const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
-    k_precond<T, Tin, Tout><<<(unsigned)g.Nc, threads, g.nb * sizeof(T), s>>>(g, Sinv, v, z);
+    k_precond<T, Tin, Tout><<<(unsigned)g.Nc, threads, g.nb * sizeof(T), s>>>(g, Sinv, v, z, ctl);
     note_launch();
     return cudaGetLastError();
 }
 
 // ==================================================================== B, B^T
 template <int D, typename T, typename Tin, typename Tout>
-__global__ void k_bapply(Geo<T> g, const Tin* __restrict__ z, Tout* __restrict__ y) {
+__global__ void k_bapply(Geo<T> g, const Tin* __restrict__ z, Tout* __restrict__ y, const int* skip) {
+    if (skip && *skip) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.Nu0) return;
     int r[kMaxDim];
@@ -572,10 +579,10 @@ __global__ void k_bapply(Geo<T> g, const Tin* __restrict__ z, Tout* __restrict__
 }
 
 template <typename T, typename Tin, typename Tout>
-cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s) {
+cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s, const int* skip) {
     const unsigned b = (unsigned)((g.Nu0 + 255) / 256);
-    if (g.d == 2) k_bapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y);
-    else k_bapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y);
+    if (g.d == 2) k_bapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y, skip);
+    else k_bapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y, skip);
     note_launch();
     return cudaGetLastError();
 }
@@ -621,17 +628,138 @@ cudaError_t launch_aapply(const Geo<double>& g, const double* x, double* y, cuda
 }
 
 // ======================================================================= FDM
-// C[b][i][j] = sum_k A(b,i,k) B(b,k,j) with general strides (batched tiny GEMM).
+// One pass of the fast diagonalisation is a batched small GEMM
+//   C[b](M x N) = A[b](M x K) * B[b](K x N)
+// with general strides.  K = n1 <= ~400, so each CTA stages the whole K extent
+// of its A row-panel and B column-panel in shared memory at once (all global
+// loads in flight together, one barrier) and then runs the K loop from shared
+// memory with a 4x2 register tile per thread.  The last forward pass applies
+// the diagonal scaling 1 / (alpha (lam_0 + lam_1 (+ lam_2))) in its epilogue.
 struct GemmArgs {
     int M, N, K, batch;
     long long sAm, sAk, sAb, sBk, sBn, sBb, sCm, sCn, sCb;
 };
 
+struct FdmScale {
+    int on;
+    int d;
+    int n1[kMaxDim];
+    const double* alpha_dev;   // alpha on the device (graph-friendly); null: use alpha_host
+    double alpha_host;
+};
+
+// Asynchronous 4/8-byte global->shared copy (LDGSTS); `valid` false zero-fills.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem, bool valid) {
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+    const int src = valid ? (int)sizeof(T) : 0;
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(saddr), "l"(gmem), "r"(src));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr), "l"(gmem), "r"(src));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+// CTA tile BM x BN, TM x TN outputs per thread.  Panels are staged in
+// shared memory as [k][m] and [k][n] (the inner index contiguous), walked so
+// that consecutive threads write consecutive shared words (no bank conflicts);
+// when the global operand is transposed the L1 line is reused across k.
+template <typename T, int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_gemm_fullk(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp,
+                 FdmScale sc, const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2,
+                 const int* skip) {
+    constexpr int NT = (BM / TM) * (BN / TN);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if (skip && *skip) return;
+    T* As = reinterpret_cast<T*>(smraw);          // [K][BM]
+    T* Bs = As + (size_t)a.K * BM;                // [K][BN]
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int b = blockIdx.z;
+    const T* A = Ap + (long long)b * a.sAb;
+    const T* B = Bp + (long long)b * a.sBb;
+    T* C = Cp + (long long)b * a.sCb;
+    const int K = a.K;
+    for (int e = tid; e < BM * K; e += NT) {
+        const int mm = e % BM, kk = e / BM, gm = m0 + mm;
+        const bool ok = gm < a.M;
+        cp_async_elem(&As[e], ok ? A + (long long)gm * a.sAm + (long long)kk * a.sAk : A, ok);
+    }
+    for (int e = tid; e < BN * K; e += NT) {
+        const int nn = e % BN, kk = e / BN, gn = n0 + nn;
+        const bool ok = gn < a.N;
+        cp_async_elem(&Bs[e], ok ? B + (long long)kk * a.sBk + (long long)gn * a.sBn : B, ok);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) acc[i][jj] = T(0);
+    const T* ap = As + ty * TM;
+    const T* bp = Bs + tx * TN;
+#pragma unroll 8
+    for (int k = 0; k < K; ++k) {
+        T av[TM], bv[TN];
+        // vector shared loads (the panel rows are 16-byte aligned)
+        if (sizeof(T) == 4 && TM == 4 && TN == 2) {
+            const float4 va = *reinterpret_cast<const float4*>(ap + (size_t)k * BM);
+            const float2 vb = *reinterpret_cast<const float2*>(bp + (size_t)k * BN);
+            av[0] = (T)va.x; av[1] = (T)va.y; av[2] = (T)va.z; av[3] = (T)va.w;
+            bv[0] = (T)vb.x; bv[1] = (T)vb.y;
+        } else if (sizeof(T) == 8 && TM == 2 && TN == 2) {
+            const double2 va = *reinterpret_cast<const double2*>(ap + (size_t)k * BM);
+            const double2 vb = *reinterpret_cast<const double2*>(bp + (size_t)k * BN);
+            av[0] = (T)va.x; av[1] = (T)va.y;
+            bv[0] = (T)vb.x; bv[1] = (T)vb.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < TM; ++i) av[i] = ap[(size_t)k * BM + i];
+#pragma unroll
+            for (int jj = 0; jj < TN; ++jj) bv[jj] = bp[(size_t)k * BN + jj];
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int jj = 0; jj < TN; ++jj) acc[i][jj] += av[i] * bv[jj];
+    }
+    T ainv = T(1);
+    if (sc.on) ainv = (T)(1.0 / (sc.alpha_dev ? *sc.alpha_dev : sc.alpha_host));
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) {
+            const int gm = m0 + ty * TM + i, gn = n0 + tx * TN + jj;
+            if (gm < a.M && gn < a.N) {
+                const long long off = (long long)gm * a.sCm + (long long)gn * a.sCn;
+                T v = acc[i][jj];
+                if (sc.on) {
+                    // interior-tensor position of this output -> eigenvalue indices
+                    long long lin = off + (long long)b * a.sCb;
+                    const int i0 = (int)(lin % sc.n1[0]);
+                    lin /= sc.n1[0];
+                    const int i1 = (int)(lin % sc.n1[1]);
+                    T lsum = l0[i0] + l1[i1];
+                    if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                    v = v * ainv / lsum;
+                }
+                C[off] = v;
+            }
+        }
+}
+
+// fallback for K beyond the shared-memory budget: classic K-tiled GEMM
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-    k_gemm(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp) {
+    k_gemm_tiled(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp,
+                 FdmScale sc, const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2,
+                 const int* skip) {
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
+    if (skip && *skip) return;
     constexpr int NT = (BM / TM) * (BN / TN);
     const int tid = threadIdx.x;
     const int tx = tid % (BN / TN), ty = tid / (BN / TN);
@@ -652,13 +780,13 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
             int mm, kk;
             if (a_kfast) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
             const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < a.M && gk < a.K) ? A[gm * a.sAm + gk * a.sAk] : T(0);
+            As[kk][mm] = (gm < a.M && gk < a.K) ? A[(long long)gm * a.sAm + (long long)gk * a.sAk] : T(0);
         }
         for (int e = tid; e < BN * BK; e += NT) {
             int nn, kk;
             if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
             const int gn = n0 + nn, gk = k0 + kk;
-            Bs[kk][nn] = (gn < a.N && gk < a.K) ? B[gk * a.sBk + gn * a.sBn] : T(0);
+            Bs[kk][nn] = (gn < a.N && gk < a.K) ? B[(long long)gk * a.sBk + (long long)gn * a.sBn] : T(0);
         }
         __syncthreads();
 #pragma unroll
@@ -675,42 +803,69 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         }
         __syncthreads();
     }
+    T ainv = T(1);
+    if (sc.on) ainv = (T)(1.0 / (sc.alpha_dev ? *sc.alpha_dev : sc.alpha_host));
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             const int gm = m0 + ty * TM + i, gn = n0 + tx * TN + j;
-            if (gm < a.M && gn < a.N) C[gm * a.sCm + gn * a.sCn] = acc[i][j];
+            if (gm < a.M && gn < a.N) {
+                const long long off = (long long)gm * a.sCm + (long long)gn * a.sCn;
+                T v = acc[i][j];
+                if (sc.on) {
+                    long long lin = off + (long long)b * a.sCb;
+                    const int i0 = (int)(lin % sc.n1[0]);
+                    lin /= sc.n1[0];
+                    const int i1 = (int)(lin % sc.n1[1]);
+                    T lsum = l0[i0] + l1[i1];
+                    if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                    v = v * ainv / lsum;
+                }
+                C[off] = v;
+            }
         }
 }
 
+// Tile choice: FP32 uses 32x32 tiles (4x2 per thread) -- the pass is latency-
+// bound at these sizes; FP64 runs at a small fraction of the FP32 rate, so it
+// uses 16x16 tiles to spread the work over all SMs.
 template <typename T>
-static cudaError_t gemm(const GemmArgs& a, const T* A, const T* B, T* C, cudaStream_t s) {
-    // 32x32 tiles (2x2 per thread) keep enough CTAs in flight for n1 ~ 50..320
-    constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2;
-    dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch);
-    k_gemm<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(a, A, B, C);
+struct GemmTile;
+template <>
+struct GemmTile<float> { static constexpr int BM = 32, BN = 32, TM = 4, TN = 2; };
+template <>
+struct GemmTile<double> { static constexpr int BM = 16, BN = 16, TM = 2, TN = 2; };
+
+template <typename T>
+static size_t gemm_fullk_smem(int K) {
+    return (size_t)K * (GemmTile<T>::BM + GemmTile<T>::BN) * sizeof(T);
+}
+
+template <typename T>
+static cudaError_t gemm(const GemmArgs& a, const T* A, const T* B, T* C, const FdmScale& sc, const Geo<T>& g,
+                        cudaStream_t s, const int* skip) {
+    const T* l0 = g.lam[0];
+    const T* l1 = g.d > 1 ? g.lam[1] : g.lam[0];
+    const T* l2 = g.d > 2 ? g.lam[2] : g.lam[0];
+    const size_t smem = gemm_fullk_smem<T>(a.K);
+    constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN, TM = GemmTile<T>::TM, TN = GemmTile<T>::TN;
+    if (smem <= 200 * 1024) {
+        dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch);
+        k_gemm_fullk<T, BM, BN, TM, TN><<<grid, (BM / TM) * (BN / TN), smem, s>>>(a, A, B, C, sc, l0, l1, l2, skip);
+    } else {
+        constexpr int BK = 16;
+        dim3 grid((a.N + 31) / 32, (a.M + 31) / 32, a.batch);
+        k_gemm_tiled<T, 32, 32, BK, 2, 2><<<grid, 256, 0, s>>>(a, A, B, C, sc, l0, l1, l2, skip);
+    }
     note_launch();
     return cudaGetLastError();
 }
 
-template <typename T>
-__global__ void k_fdm_scale(Geo<T> g, T alpha_inv, T* __restrict__ x) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.Nu0) return;
-    long long r = i;
-    T lsum = T(0);
-    for (int j = 0; j < g.d; ++j) {
-        const int a = (int)(r % g.n1[j]);
-        r /= g.n1[j];
-        lsum += g.lam[j][a];
-    }
-    x[i] = x[i] * alpha_inv / lsum;
-}
-
 // A_alpha^{-1} x = alpha^{-1} (V (x) V (x) V) diag(1 / sum lam) (V^T (x) V^T (x) V^T) x
 template <typename T>
-cudaError_t launch_fdm(const Geo<T>& g, double alpha, const T* x, T* y, T* work1, T* work2, cudaStream_t s) {
+cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, const T* x, T* y, T* work1, T* work2,
+                       cudaStream_t s, const int* skip) {
     const int d = g.d;
     long long inner[kMaxDim], outer[kMaxDim];
     for (int ax = 0; ax < d; ++ax) {
@@ -719,45 +874,45 @@ cudaError_t launch_fdm(const Geo<T>& g, double alpha, const T* x, T* y, T* work1
         for (int j = 0; j < ax; ++j) inner[ax] *= g.n1[j];
         for (int j = ax + 1; j < d; ++j) outer[ax] *= g.n1[j];
     }
+    FdmScale off{};
+    FdmScale on{};
+    on.on = 1;
+    on.d = d;
+    for (int j = 0; j < kMaxDim; ++j) on.n1[j] = g.n1[j];
+    on.alpha_dev = alpha_dev;
+    on.alpha_host = alpha;
     // pass along axis ax: out[o][a][i] = sum_k W(a,k) in[o][k][i]; W = V^T (fwd) or V (bwd)
-    auto pass = [&](int ax, bool fwd, const T* in, T* out) -> cudaError_t {
+    auto pass = [&](int ax, bool fwd, const T* in, T* out, const FdmScale& sc) -> cudaError_t {
         const int n1 = g.n1[ax];
         const T* V = g.V[ax];   // row-major V[k][a]
         GemmArgs a{};
         if (inner[ax] == 1) {
-            // out[o][a] = sum_k in[o][k] W(a,k):  C(M=o, N=a) = A(o,k) * B(k,a)
             a.M = (int)outer[ax]; a.N = n1; a.K = n1; a.batch = 1;
             a.sAm = n1; a.sAk = 1; a.sAb = 0;
-            if (fwd) { a.sBk = n1; a.sBn = 1; }      // B(k,a) = V[k][a]
-            else { a.sBk = 1; a.sBn = n1; }          // B(k,a) = V[a][k]
+            if (fwd) { a.sBk = n1; a.sBn = 1; } else { a.sBk = 1; a.sBn = n1; }
             a.sBb = 0;
             a.sCm = n1; a.sCn = 1; a.sCb = 0;
-            return gemm<T>(a, in, V, out, s);
+            return gemm<T>(a, in, V, out, sc, g, s, skip);
         }
-        // per outer o: out[o] (n1 x inner) = W (n1 x n1) * in[o] (n1 x inner)
         a.M = n1; a.N = (int)inner[ax]; a.K = n1; a.batch = (int)outer[ax];
-        if (fwd) { a.sAm = 1; a.sAk = n1; }          // A(a,k) = V[k][a]
-        else { a.sAm = n1; a.sAk = 1; }              // A(a,k) = V[a][k]
+        if (fwd) { a.sAm = 1; a.sAk = n1; } else { a.sAm = n1; a.sAk = 1; }
         a.sAb = 0;
         a.sBk = inner[ax]; a.sBn = 1; a.sBb = (long long)n1 * inner[ax];
         a.sCm = inner[ax]; a.sCn = 1; a.sCb = (long long)n1 * inner[ax];
-        return gemm<T>(a, V, in, out, s);
+        return gemm<T>(a, V, in, out, sc, g, s, skip);
     };
     cudaError_t e;
     const T* cur = x;
     T* bufs[2] = {work1, work2};
     int bi = 0;
     for (int ax = 0; ax < d; ++ax) {
-        if ((e = pass(ax, true, cur, bufs[bi])) != cudaSuccess) return e;
+        if ((e = pass(ax, true, cur, bufs[bi], ax == d - 1 ? on : off)) != cudaSuccess) return e;
         cur = bufs[bi];
         bi ^= 1;
     }
-    const unsigned blocks = (unsigned)((g.Nu0 + 255) / 256);
-    k_fdm_scale<T><<<blocks, 256, 0, s>>>(g, (T)(1.0 / alpha), const_cast<T*>(cur));
-    note_launch();
     for (int ax = 0; ax < d; ++ax) {
         T* dst = (ax == d - 1) ? y : bufs[bi];
-        if ((e = pass(ax, false, cur, dst)) != cudaSuccess) return e;
+        if ((e = pass(ax, false, cur, dst, off)) != cudaSuccess) return e;
         cur = dst;
         bi ^= 1;
     }
@@ -769,14 +924,16 @@ cudaError_t launch_fdm(const Geo<T>& g, double alpha, const T* x, T* y, T* work1
 // z -> Gauss values (V along each axis) -> times gw (or the 2x2/3x3 Jacobian) -> V^T back.
 template <int D, typename T, typename Tz, typename Tt, typename Tout>
 __global__ void k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* __restrict__ z,
-                         const Tt* __restrict__ t, T sB, T sD, Tout* __restrict__ out) {
+                         const Tt* __restrict__ t, T sB, T sD, Tout* __restrict__ out, IterCtl ctl) {
     extern __shared__ unsigned char smraw[];
+    if (ctl.skip && *ctl.skip) return;
     T* sm = reinterpret_cast<T*>(smraw);
     const int n = g.n, nloc = (int)g.nloc, nc = g.ncomp, nb = (int)g.nb;
     T* a = sm;
     T* b = sm + nb;
     T* zc = sm + 2 * nb;
     T* Vq = sm + 3 * nb;
+    Tout* outp = out + (ctl.jptr ? (long long)(*ctl.jptr + 1) * ctl.jstride : 0LL);
     const long long cell = blockIdx.x;
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) Vq[i] = g.Vq[i];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) { const T v = (T)z[cell * nb + i]; a[i] = v; zc[i] = v; }
@@ -836,19 +993,19 @@ __global__ void k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* _
             for (int q = 0; q < D; ++q) { km[q] = kk % n; kk /= n; }
             acc += sB * apply_BT_entry<D, T, Tt>(g, cm, comp, km, t);
         }
-        out[cell * nb + i] = (Tout)acc;
+        outp[cell * nb + i] = (Tout)acc;
     }
 }
 
 template <typename T, typename Tout>
 cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T* z, const T* t, Tout* w,
-                              cudaStream_t s) {
+                              cudaStream_t s, IterCtl ctl) {
     const size_t smem = (size_t)(3 * g.nb + g.n * g.n) * sizeof(T);
     const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
     if (g.d == 2)
-        k_cellop<2, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w);
+        k_cellop<2, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl);
     else
-        k_cellop<3, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w);
+        k_cellop<3, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl);
     note_launch();
     return cudaGetLastError();
 }
@@ -873,13 +1030,13 @@ cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double a
         k_newton_u<2><<<bu, 256, 0, s>>>(g, alpha, x, x + g.Nu0, y);
         note_launch();
         k_cellop<2, double, double, double, double><<<(unsigned)g.Nc, threads, smem, s>>>(
-            g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0);
+            g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0, IterCtl{});
         note_launch();
     } else {
         k_newton_u<3><<<bu, 256, 0, s>>>(g, alpha, x, x + g.Nu0, y);
         note_launch();
         k_cellop<3, double, double, double, double><<<(unsigned)g.Nc, threads, smem, s>>>(
-            g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0);
+            g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0, IterCtl{});
         note_launch();
     }
     return cudaGetLastError();
@@ -951,10 +1108,16 @@ cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts
 }
 
 // ===================================================================== GMRES
-// Each block owns a contiguous chunk of the N-vector.
+// Right-preconditioned GMRES without restart; the iteration index j lives on
+// the device (G.jdev) so that a chunk of iterations can be captured once in a
+// CUDA graph and replayed.  Every kernel returns immediately once the
+// converged/stop flag (G.iflag[0]) is set.  Classical Gram--Schmidt with one
+// re-orthogonalisation (CGS2), FP64, fixed-order (deterministic) reductions.
+constexpr int kDotChunk = 512;
+
 __global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b, long long N,
                            const double* __restrict__ part, int nparts, double rtol, double* __restrict__ scal,
-                           double* __restrict__ gv, int kmax, int* __restrict__ iflag) {
+                           double* __restrict__ gv, int kmax, int* __restrict__ iflag, int* __restrict__ jdev) {
     __shared__ double sh[32];
     double v = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
@@ -975,18 +1138,20 @@ __global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b
         iflag[0] = (bb == 0.0) ? 1 : 0;
         iflag[1] = 0;
         iflag[2] = 0;
+        iflag[3] = 0;
+        *jdev = 0;
     }
 }
 
-// partial dots of w = Vb[j+1] with Vb[0..j]; last block reduces into h (accumulate or set)
-__global__ void k_gm_dots(const double* __restrict__ Vb, int j, long long N, double* __restrict__ part,
-                          double* __restrict__ h, int accumulate, unsigned int* __restrict__ counter,
-                          const int* __restrict__ iflag) {
+// partial dots of w = Vb[j+1] with Vb[0..j]; the last block reduces into h
+__global__ void k_gm_dots(const double* __restrict__ Vb, const int* __restrict__ jdev, long long N,
+                          double* __restrict__ part, int kmax, double* __restrict__ h, int h_in_H,
+                          unsigned int* __restrict__ counter, const int* __restrict__ iflag) {
     if (iflag[0]) return;
+    const int j = *jdev;
     const int nblk = gridDim.x;
-    const long long chunk = (N + nblk - 1) / nblk;
-    const long long e0 = blockIdx.x * chunk;
-    const long long e1 = (e0 + chunk < N) ? e0 + chunk : N;
+    const long long e0 = (long long)blockIdx.x * kDotChunk;
+    const long long e1 = (e0 + kDotChunk < N) ? e0 + kDotChunk : N;
     const double* w = Vb + (long long)(j + 1) * N;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = wid; i <= j; i += nw) {
@@ -994,7 +1159,7 @@ __global__ void k_gm_dots(const double* __restrict__ Vb, int j, long long N, dou
         double s = 0.0;
         for (long long e = e0 + lane; e < e1; e += 32) s += vi[e] * w[e];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) part[(long long)blockIdx.x * (j + 1) + i] = s;
+        if (lane == 0) part[(long long)blockIdx.x * (kmax + 1) + i] = s;
     }
     __threadfence();
     __shared__ bool last;
@@ -1003,42 +1168,47 @@ __global__ void k_gm_dots(const double* __restrict__ Vb, int j, long long N, dou
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    double* hh = h_in_H ? h + (long long)j * (kmax + 1) : h;
+    for (int i = wid; i <= j; i += nw) {
         double s = 0.0;
-        for (int bk = 0; bk < nblk; ++bk) s += part[(long long)bk * (j + 1) + i];
-        h[i] = accumulate ? h[i] + s : s;
+        for (int bk = lane; bk < nblk; bk += 32) s += part[(long long)bk * (kmax + 1) + i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) hh[i] = s;
     }
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-// w -= sum_i c_i V_i ; partial sums of squares of the result
-__global__ void k_gm_update(double* __restrict__ Vb, int j, long long N, const double* __restrict__ c,
-                            double* __restrict__ part, const int* __restrict__ iflag) {
+// w -= sum_i c_i V_i ; block partial sums of squares of the result
+__global__ void k_gm_update(double* __restrict__ Vb, const int* __restrict__ jdev, long long N,
+                            const double* __restrict__ c, int kmax, int c_in_H, double* __restrict__ part,
+                            const int* __restrict__ iflag) {
     __shared__ double sh[32];
     if (iflag[0]) return;
-    const int nblk = gridDim.x;
-    const long long chunk = (N + nblk - 1) / nblk;
-    const long long e0 = blockIdx.x * chunk;
-    const long long e1 = (e0 + chunk < N) ? e0 + chunk : N;
+    const int j = *jdev;
+    const double* cc = c_in_H ? c + (long long)j * (kmax + 1) : c;
     double* w = Vb + (long long)(j + 1) * N;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double ss = 0.0;
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    if (e < N) {
         double v = w[e];
-        for (int i = 0; i <= j; ++i) v -= c[i] * Vb[(long long)i * N + e];
+        for (int i = 0; i <= j; ++i) v -= cc[i] * Vb[(long long)i * N + e];
         w[e] = v;
-        ss += v * v;
+        ss = v * v;
     }
     ss = block_sum(ss, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = ss;
 }
 
-// normalise V_{j+1}, Givens update of column j, convergence test
-__global__ void k_gm_finalize(double* __restrict__ Vb, int j, long long N, const double* __restrict__ part,
-                              double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
-                              double* __restrict__ gv, double* __restrict__ scal, int* __restrict__ iflag,
-                              int kmax, const double* __restrict__ h2) {
+// normalise V_{j+1}; the last block to finish applies the Givens rotations,
+// tests convergence and advances j (all blocks have read j by then)
+__global__ void k_gm_finalize(double* __restrict__ Vb, const int* __restrict__ jdev_c, long long N,
+                              const double* __restrict__ part, double* __restrict__ H, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ gv, double* __restrict__ scal,
+                              int* __restrict__ iflag, int kmax, const double* __restrict__ h2,
+                              unsigned int* __restrict__ counter, int* __restrict__ jdev) {
     __shared__ double sh[32];
     if (iflag[0]) return;
+    const int j = *jdev_c;
     const int nblk = gridDim.x;
     double v = 0.0;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += part[i];
@@ -1047,125 +1217,177 @@ __global__ void k_gm_finalize(double* __restrict__ Vb, int j, long long N, const
     if (threadIdx.x == 0) hn = sqrt(v);
     __syncthreads();
     const double hnv = hn;
-    const long long chunk = (N + nblk - 1) / nblk;
-    const long long e0 = blockIdx.x * chunk;
-    const long long e1 = (e0 + chunk < N) ? e0 + chunk : N;
     double* w = Vb + (long long)(j + 1) * N;
     const double inv = hnv > 0.0 ? 1.0 / hnv : 0.0;
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) w[e] *= inv;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double* col = H + (long long)j * (kmax + 1);
-        for (int i = 0; i <= j; ++i) col[i] += h2[i];
-        col[j + 1] = hnv;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < N) w[e] *= inv;
+    __threadfence();
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(nblk - 1));
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // stage the Hessenberg column and the previous rotations in shared memory
+    __shared__ double scol[kMaxKrylov + 2], scs[kMaxKrylov], ssn[kMaxKrylov];
+    double* col = H + (long long)j * (kmax + 1);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        scol[i] = col[i] + h2[i];
+        if (i < j) { scs[i] = cs[i]; ssn[i] = sn[i]; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        scol[j + 1] = hnv;
         for (int i = 0; i < j; ++i) {
-            const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-            col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-            col[i] = t;
+            const double t = scs[i] * scol[i] + ssn[i] * scol[i + 1];
+            scol[i + 1] = -ssn[i] * scol[i] + scs[i] * scol[i + 1];
+            scol[i] = t;
         }
-        const double a = col[j], bq = col[j + 1];
+        const double a = scol[j], bq = scol[j + 1];
         const double r = hypot(a, bq);
         double c = 1.0, s = 0.0;
         if (r > 0.0) { c = a / r; s = bq / r; }
         cs[j] = c;
         sn[j] = s;
-        col[j] = r;
-        col[j + 1] = 0.0;
-        gv[j + 1] = -s * gv[j];
-        gv[j] = c * gv[j];
-        const double res = fabs(gv[j + 1]);
+        scol[j] = r;
+        scol[j + 1] = 0.0;
+        const double gj = gv[j];
+        gv[j + 1] = -s * gj;
+        gv[j] = c * gj;
+        const double res = fabs(s * gj);
         scal[1] = res;
         scal[3] = hnv;
         iflag[1] = j + 1;
-        if (!(res > scal[2])) iflag[0] = 1;
-        if (!(hnv > 1e-300) || !isfinite(res)) { iflag[0] = 1; iflag[2] = 1; }
+        int stop = 0;
+        if (!(res > scal[2])) stop = 1;                                    // converged
+        if (!(hnv > 1e-300) || !isfinite(res)) { stop = 1; iflag[2] = 1; }  // breakdown
+        if (j + 1 >= kmax) { stop = 1; iflag[3] = 1; }                     // cap
+        if (stop) iflag[0] = 1;
+        else *jdev = j + 1;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = scol[i];
 }
 
-__global__ void k_gm_backsolve(const double* __restrict__ H, const double* __restrict__ gv, int k, int kmax,
-                               double* __restrict__ y) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Back substitution H y = g on the k completed columns; the packed upper
+// triangle is staged in shared memory when it fits (use_smem), else read from H.
+__global__ void k_gm_backsolve(const double* __restrict__ H, const double* __restrict__ gv, const int* __restrict__ iflag,
+                               int kmax, double* __restrict__ y, int use_smem) {
+    extern __shared__ double shH[];
+    const int k = iflag[1];
+    if (use_smem) {
+        for (int e = threadIdx.x; e < k * (k + 1) / 2; e += blockDim.x) {
+            // e -> (column l, row i <= l) in packed column-major order
+            int l = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+            while ((l + 1) * (l + 2) / 2 <= e) ++l;
+            while (l * (l + 1) / 2 > e) --l;
+            const int i = e - l * (l + 1) / 2;
+            shH[e] = H[(long long)l * (kmax + 1) + i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     for (int i = k - 1; i >= 0; --i) {
         double s = gv[i];
-        for (int l = i + 1; l < k; ++l) s -= H[(long long)l * (kmax + 1) + i] * y[l];
-        const double diag = H[(long long)i * (kmax + 1) + i];
+        for (int l = i + 1; l < k; ++l)
+            s -= (use_smem ? shH[(size_t)l * (l + 1) / 2 + i] : H[(long long)l * (kmax + 1) + i]) * y[l];
+        const double diag = use_smem ? shH[(size_t)i * (i + 1) / 2 + i] : H[(long long)i * (kmax + 1) + i];
         y[i] = diag != 0.0 ? s / diag : 0.0;
     }
 }
 
-__global__ void k_gm_combine(const double* __restrict__ Vb, const double* __restrict__ y, int k, long long N,
-                             double* __restrict__ x) {
+__global__ void k_gm_combine(const double* __restrict__ Vb, const double* __restrict__ y,
+                             const int* __restrict__ iflag, long long N, double* __restrict__ x) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N) return;
+    const int k = iflag[1];
     double s = 0.0;
     for (int i = 0; i < k; ++i) s += y[i] * Vb[(long long)i * N + e];
     x[e] = s;
 }
 
+int gmres_dot_blocks(long long N) { return (int)((N + kDotChunk - 1) / kDotChunk); }
+int gmres_upd_blocks(long long N) { return (int)((N + 255) / 256); }
+
 cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s) {
     int np = 0;
-    cudaError_t e = launch_sumsq(b, G.N, G.part, &np, s);
+    cudaError_t e = launch_sumsq(b, G.N, G.part_norm, &np, s);
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(G.H, 0, sizeof(double) * (size_t)(G.kmax + 1) * G.kmax, s);
-    k_gm_start<<<G.blocks, 256, 0, s>>>(G.Vb, b, G.N, G.part, np, rtol, G.scal, G.gv, G.kmax, G.iflag);
+    const int nb = gmres_upd_blocks(G.N) < 1024 ? gmres_upd_blocks(G.N) : 1024;
+    k_gm_start<<<nb, 256, 0, s>>>(G.Vb, b, G.N, G.part_norm, np, rtol, G.scal, G.gv, G.kmax, G.iflag, G.jdev);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t gmres_arnoldi(GmresDev& G, int j, cudaStream_t s) {
-    double* hcol = G.H + (long long)j * (G.kmax + 1);
+cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s) {
+    const int bd = gmres_dot_blocks(G.N), bu = gmres_upd_blocks(G.N);
     double* h2 = G.y;   // scratch for the second CGS pass
-    // CGS pass 1 (writes h into H column), update; pass 2 (h2), update + norm; finalize adds h2
-    k_gm_dots<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, G.part, hcol, 0, G.counter, G.iflag);
+    k_gm_dots<<<bd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, G.H, 1, G.counter, G.iflag);
     note_launch();
-    k_gm_update<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, hcol, G.part + (size_t)G.blocks * (G.kmax + 1), G.iflag);
+    k_gm_update<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.H, G.kmax, 1, G.part_norm, G.iflag);
     note_launch();
-    k_gm_dots<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, G.part, h2, 0, G.counter, G.iflag);
+    k_gm_dots<<<bd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, h2, 0, G.counter, G.iflag);
     note_launch();
-    k_gm_update<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, h2, G.part + (size_t)G.blocks * (G.kmax + 1), G.iflag);
+    k_gm_update<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, h2, G.kmax, 0, G.part_norm, G.iflag);
     note_launch();
-    k_gm_finalize<<<G.blocks, 256, 0, s>>>(G.Vb, j, G.N, G.part + (size_t)G.blocks * (G.kmax + 1), G.H, G.cs, G.sn,
-                                           G.gv, G.scal, G.iflag, G.kmax, h2);
+    k_gm_finalize<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_norm, G.H, G.cs, G.sn, G.gv, G.scal, G.iflag, G.kmax,
+                                     h2, G.counter2, G.jdev);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t gmres_finish(GmresDev& G, int k, double* x, cudaStream_t s) {
-    if (k <= 0) {
-        cudaMemsetAsync(x, 0, sizeof(double) * G.N, s);
-        return cudaGetLastError();
-    }
-    k_gm_backsolve<<<1, 32, 0, s>>>(G.H, G.gv, k, G.kmax, G.y);
+cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s) {
+    const size_t tri = (size_t)G.kmax * (G.kmax + 1) / 2 * sizeof(double);
+    const int use_smem = tri <= 200 * 1024;
+    k_gm_backsolve<<<1, 256, use_smem ? tri : 0, s>>>(G.H, G.gv, G.iflag, G.kmax, G.y, use_smem);
     note_launch();
-    k_gm_combine<<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(G.Vb, G.y, k, G.N, x);
+    k_gm_combine<<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(G.Vb, G.y, G.iflag, G.N, x);
     note_launch();
     return cudaGetLastError();
+}
+
+void configure_kernels() {
+    cudaFuncSetAttribute(k_gemm_fullk<float, GemmTile<float>::BM, GemmTile<float>::BN, GemmTile<float>::TM,
+                                       GemmTile<float>::TN>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_gemm_fullk<double, GemmTile<double>::BM, GemmTile<double>::BN, GemmTile<double>::TM,
+                                       GemmTile<double>::TN>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 // ============================================================ instantiations
 template cudaError_t launch_factor<double>(const Geo<double>&, const double*, double, double, double*, double*,
-                                           int*, cudaStream_t);
+                                           int*, double*, cudaStream_t);
 template cudaError_t launch_factor<float>(const Geo<float>&, const float*, double, double, float*, double*, int*,
-                                          cudaStream_t);
+                                          float*, cudaStream_t);
 template cudaError_t launch_precond<double, double, double>(const Geo<double>&, const double*, const double*,
-                                                            double*, cudaStream_t);
+                                                            double*, cudaStream_t, IterCtl);
 template cudaError_t launch_precond<float, double, float>(const Geo<float>&, const float*, const double*, float*,
-                                                          cudaStream_t);
+                                                          cudaStream_t, IterCtl);
 template cudaError_t launch_precond<float, double, double>(const Geo<float>&, const float*, const double*,
-                                                           double*, cudaStream_t);
-template cudaError_t launch_bapply<double, double, double>(const Geo<double>&, const double*, double*, cudaStream_t);
-template cudaError_t launch_bapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t);
-template cudaError_t launch_bapply<float, double, float>(const Geo<float>&, const double*, float*, cudaStream_t);
+                                                           double*, cudaStream_t, IterCtl);
+template cudaError_t launch_bapply<double, double, double>(const Geo<double>&, const double*, double*, cudaStream_t,
+                                                           const int*);
+template cudaError_t launch_bapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t,
+                                                        const int*);
+template cudaError_t launch_bapply<float, double, float>(const Geo<float>&, const double*, float*, cudaStream_t,
+                                                         const int*);
 template cudaError_t launch_btapply<double, double, double>(const Geo<double>&, const double*, double*,
                                                             cudaStream_t);
 template cudaError_t launch_btapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t);
-template cudaError_t launch_fdm<double>(const Geo<double>&, double, const double*, double*, double*, double*,
-                                        cudaStream_t);
-template cudaError_t launch_fdm<float>(const Geo<float>&, double, const float*, float*, float*, float*,
-                                       cudaStream_t);
+template cudaError_t launch_fdm<double>(const Geo<double>&, const double*, double, const double*, double*, double*,
+                                        double*, cudaStream_t, const int*);
+template cudaError_t launch_fdm<float>(const Geo<float>&, const double*, double, const float*, float*, float*,
+                                       float*, cudaStream_t, const int*);
 template cudaError_t launch_schur_rest<double, double>(const Geo<double>&, const double*, double, const double*,
-                                                       const double*, double*, cudaStream_t);
+                                                       const double*, double*, cudaStream_t, IterCtl);
 template cudaError_t launch_schur_rest<float, double>(const Geo<float>&, const float*, double, const float*,
-                                                      const float*, double*, cudaStream_t);
+                                                      const float*, double*, cudaStream_t, IterCtl);
 template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
 template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
 template cudaError_t launch_sub_scaled<double>(const double*, double, const double*, double*, long long,

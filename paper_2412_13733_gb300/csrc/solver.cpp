@@ -3,6 +3,8 @@
 // right-preconditioned GMRES on S, FP64 iterative refinement around an FP32
 // inner solve, and the component operators used by the tests.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -82,6 +84,10 @@ static T* dalloc(DevState& D, size_t n, bool& ok) {
 }
 
 void free_device(Problem& P) {
+    for (auto& gx : P.D.gmres_graph)
+        if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
+    for (auto& kv : P.D.bench_graphs) cudaGraphExecDestroy(kv.second.first);
+    P.D.bench_graphs.clear();
     for (void* p : P.D.allocs) cudaFree(p);
     P.D.allocs.clear();
     if (P.D.h_scal) cudaFreeHost(P.D.h_scal);
@@ -177,7 +183,15 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     D.psi_prev = dalloc<double>(D, Npsi, ok);
     D.gw = dalloc<double>(D, gsz, ok);
     D.gwt = dalloc<double>(D, gsz, ok);
+    D.gwl = dalloc<double>(D, gsz, ok);
     D.gwf = dalloc<float>(D, gsz, ok);
+    D.alpha_dev = dalloc<double>(D, 1, ok);
+    {
+        const size_t fw_d = factor_workspace_elems(H.n, d, (int)H.nb, H.ncomp, (long long)H.Nc, 8);
+        const size_t fw_f = factor_workspace_elems(H.n, d, (int)H.nb, H.ncomp, (long long)H.Nc, 4);
+        if (fw_d) D.fwork_d = dalloc<double>(D, fw_d, ok);
+        if (fw_f) D.fwork_f = dalloc<float>(D, fw_f, ok);
+    }
     D.eg = dalloc<double>(D, Npsi, ok);
     D.egt = dalloc<double>(D, Npsi, ok);
     D.F = dalloc<double>(D, Nx, ok);
@@ -208,19 +222,26 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     GmresDev& G = D.gm;
     G.kmax = std::max(1, P.params.krylov_max);
     G.N = (long long)Npsi;
-    G.blocks = (int)std::min<long long>(304, std::max<long long>(1, (G.N + 1023) / 1024));
     G.Vb = dalloc<double>(D, (size_t)(G.kmax + 1) * Npsi, ok);
     G.H = dalloc<double>(D, (size_t)(G.kmax + 1) * G.kmax, ok);
     G.cs = dalloc<double>(D, G.kmax, ok);
     G.sn = dalloc<double>(D, G.kmax, ok);
     G.gv = dalloc<double>(D, G.kmax + 1, ok);
-    G.part = dalloc<double>(D, std::max<size_t>(1024, (size_t)G.blocks * (G.kmax + 3)), ok);
+    G.part_dots = dalloc<double>(D, (size_t)gmres_dot_blocks(G.N) * (G.kmax + 1), ok);
+    G.part_norm = dalloc<double>(D, std::max<size_t>(1024, (size_t)gmres_upd_blocks(G.N)), ok);
     G.scal = dalloc<double>(D, 8, ok);
     G.iflag = dalloc<int>(D, 4, ok);
+    G.jdev = dalloc<int>(D, 1, ok);
     G.counter = dalloc<unsigned int>(D, 1, ok);
+    G.counter2 = dalloc<unsigned int>(D, 1, ok);
     G.y = dalloc<double>(D, G.kmax + 1, ok);
     if (!ok) { free_device(P); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
     cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), s);
+    cudaMemsetAsync(G.counter2, 0, sizeof(unsigned int), s);
+    cudaMemsetAsync(G.iflag, 0, 4 * sizeof(int), s);
+    cudaMemsetAsync(G.jdev, 0, sizeof(int), s);
+    static bool configured = false;
+    if (!configured) { configure_kernels(); configured = true; }
     cudaMemsetAsync(D.flag, 0, 4 * sizeof(int), s);
     if (cudaMallocHost(&D.h_scal, 16 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&D.h_iflag, 8 * sizeof(int)) != cudaSuccess) {
@@ -296,7 +317,8 @@ template <>
 struct PV<double> {
     static const Geo<double>& g(DevState& D) { return D.gd; }
     static double* Sinv(DevState& D) { return D.Sinv_d; }
-    static const double* gw(DevState& D) { return D.gw; }
+    static const double* gw(DevState& D) { return D.gwl; }
+    static double* fwork(DevState& D) { return D.fwork_d; }
     static double* tu(DevState& D) { return D.tu_d; }
     static double* tu2(DevState& D) { return D.tu2_d; }
     static double* w1(DevState& D) { return D.w1_d; }
@@ -308,6 +330,7 @@ struct PV<float> {
     static const Geo<float>& g(DevState& D) { return D.gf; }
     static float* Sinv(DevState& D) { return D.Sinv_f; }
     static const float* gw(DevState& D) { return D.gwf; }
+    static float* fwork(DevState& D) { return D.fwork_f; }
     static float* tu(DevState& D) { return D.tu_f; }
     static float* tu2(DevState& D) { return D.tu2_f; }
     static float* w1(DevState& D) { return D.w1_f; }
@@ -380,9 +403,12 @@ static hpg_status factor_T(hpg_ctx* ctx, Problem& P, double alpha, double* dump)
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
     Scope sc(P.timer, HPG_K_FACTOR, s);
-    if (sizeof(T) == sizeof(float))
-        CK(launch_convert<double, float>(D.gw, D.gwf, (long long)(P.H.Nq * gauss_stride(P.H.kind, P.H.d)), s));
-    CK(launch_factor<T>(PV<T>::g(D), PV<T>::gw(D), alpha, P.params.beta, PV<T>::Sinv(D), dump, D.flag, s));
+    const long long gsz = (long long)(P.H.Nq * gauss_stride(P.H.kind, P.H.d));
+    // freeze the weights of this linearisation (D.gw is swapped by the line search)
+    CK(cudaMemcpyAsync(D.gwl, D.gw, gsz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (sizeof(T) == sizeof(float)) CK(launch_convert<double, float>(D.gwl, D.gwf, gsz, s));
+    CK(launch_factor<T>(PV<T>::g(D), PV<T>::gw(D), alpha, P.params.beta, PV<T>::Sinv(D), dump, D.flag,
+                        PV<T>::fwork(D), s));
     return HPG_OK;
 }
 
@@ -390,7 +416,7 @@ template <typename T>
 static hpg_status fdm_T(hpg_ctx* ctx, Problem& P, double alpha, const T* x, T* y) {
     DevState& D = P.D;
     Scope sc(P.timer, HPG_K_FDM, ctx->stream);
-    CK(launch_fdm<T>(PV<T>::g(D), alpha, x, y, PV<T>::w1(D), PV<T>::w2(D), ctx->stream));
+    CK(launch_fdm<T>(PV<T>::g(D), nullptr, alpha, x, y, PV<T>::w1(D), PV<T>::w2(D), ctx->stream));
     return HPG_OK;
 }
 
@@ -408,6 +434,90 @@ static hpg_status schur_apply_T(hpg_ctx* ctx, Problem& P, double alpha, const T*
     {
         Scope sc(P.timer, HPG_K_SCHUR, s);
         CK(launch_schur_rest<T, double>(g, PV<T>::gw(D), P.params.beta, z, PV<T>::tu2(D), out, s));
+    }
+    return HPG_OK;
+}
+
+// `chunk` GMRES iterations enqueued on the stream (no host synchronisation):
+// z = S-hat^{-1} V_j, w = S z written into V_{j+1}, Arnoldi/Givens update.
+// Iteration index, stop flag and alpha are read on the device, so the same
+// launches can be captured once into a CUDA graph and replayed.
+template <typename T>
+static hpg_status gmres_chunk(hpg_ctx* ctx, Problem& P, int chunk) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    GmresDev& G = D.gm;
+    const Geo<T>& g = PV<T>::g(D);
+    const IterCtl ctl{G.iflag, G.jdev, G.N};
+    for (int c = 0; c < chunk; ++c) {
+        {
+            Scope sc(P.timer, HPG_K_PRECOND, s);
+            CK(launch_precond<T, double, T>(g, PV<T>::Sinv(D), G.Vb, PV<T>::zp(D), s, ctl));
+        }
+        {
+            Scope sc(P.timer, HPG_K_BAPPLY, s);
+            CK(launch_bapply<T, T, T>(g, PV<T>::zp(D), PV<T>::tu(D), s, G.iflag));
+        }
+        {
+            Scope sc(P.timer, HPG_K_FDM, s);
+            CK(launch_fdm<T>(g, D.alpha_dev, 0.0, PV<T>::tu(D), PV<T>::tu2(D), PV<T>::w1(D), PV<T>::w2(D), s,
+                             G.iflag));
+        }
+        {
+            Scope sc(P.timer, HPG_K_SCHUR, s);
+            CK(launch_schur_rest<T, double>(g, PV<T>::gw(D), P.params.beta, PV<T>::zp(D), PV<T>::tu2(D), G.Vb, s,
+                                            ctl));
+        }
+        {
+            Scope sc(P.timer, HPG_K_ORTHO, s);
+            CK(gmres_arnoldi(G, s));
+        }
+    }
+    return HPG_OK;
+}
+
+constexpr int kGraphChunk = 4;
+
+// Run GMRES to its stop flag: replay the captured chunk graph (or launch
+// eagerly when kernel timing is on), reading the flags once per chunk.
+template <typename T>
+static hpg_status gmres_run(hpg_ctx* ctx, Problem& P, int* its, bool* capped) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    GmresDev& G = D.gm;
+    const int pi = sizeof(T) == sizeof(float) ? 1 : 0;
+    const bool use_graph = !P.timer.on;
+    if (use_graph && !D.gmres_graph[pi]) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        const long long before = kernel_launch_count();
+        hpg_status st = gmres_chunk<T>(ctx, P, kGraphChunk);
+        D.graph_kernels[pi] = kernel_launch_count() - before;
+        add_kernel_launches(-D.graph_kernels[pi]);   // captured, not executed
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st != HPG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        CK(ce);
+        cudaError_t ie = cudaGraphInstantiate(&D.gmres_graph[pi], graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+    }
+    for (int guard = 0; guard <= G.kmax; ++guard) {
+        if (use_graph) {
+            CK(cudaGraphLaunch(D.gmres_graph[pi], s));
+            add_kernel_launches(D.graph_kernels[pi]);
+        }
+        else CKS(gmres_chunk<T>(ctx, P, 1));
+        CK(cudaMemcpyAsync(D.h_iflag + 4, G.iflag, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (D.h_iflag[4]) break;
+    }
+    *its = D.h_iflag[5];
+    *capped = D.h_iflag[7] != 0 && D.h_iflag[4] != 0 && D.h_iflag[6] == 0;
+    if (*capped) {
+        // the cap flag is also set when the last allowed iteration converged; check the residual
+        CK(cudaMemcpyAsync(D.h_scal + 4, G.scal, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *capped = D.h_scal[5] > D.h_scal[6];
     }
     return HPG_OK;
 }
@@ -436,32 +546,10 @@ static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const do
         Scope sc(P.timer, HPG_K_ORTHO, s);
         CK(gmres_start(G, D.yp, rtol, s));
     }
-    int k = 0;
-    bool conv = false;
-    CK(cudaMemcpyAsync(D.h_iflag + 4, G.iflag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (D.h_iflag[4]) conv = true;
-    for (int j = 0; j < G.kmax && !conv; ++j) {
-        {
-            Scope sc(P.timer, HPG_K_PRECOND, s);
-            CK(launch_precond<T, double, T>(g, PV<T>::Sinv(D), G.Vb + (long long)j * Npsi, zp, s));
-        }
-        CKS(schur_apply_T<T>(ctx, P, alpha, zp, G.Vb + (long long)(j + 1) * Npsi));
-        {
-            Scope sc(P.timer, HPG_K_ORTHO, s);
-            CK(gmres_arnoldi(G, j, s));
-        }
-        CK(cudaMemcpyAsync(D.h_iflag + 4, G.iflag, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        k = D.h_iflag[5];
-        if (D.h_iflag[4]) conv = true;
-    }
-    *capped = !conv;
-    if (!conv) k = G.kmax;
-    *its = k;
+    CKS(gmres_run<T>(ctx, P, its, capped));
     {
         Scope sc(P.timer, HPG_K_ORTHO, s);
-        CK(gmres_finish(G, k, D.xs, s));
+        CK(gmres_finish(G, D.xs, s));
     }
     {
         Scope sc(P.timer, HPG_K_PRECOND, s);
@@ -500,7 +588,9 @@ static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
     }
     CK(cudaMemsetAsync(delta, 0, Nx * sizeof(double), s));
     CK(cudaMemcpyAsync(D.r, F, Nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    const double inner = std::max(eta, 2e-6);
+    // FP32 inner tolerance a decade below the forcing term (floored near the FP32
+    // limit) so that one refinement sweep usually meets ||F - G delta|| <= eta ||F||
+    const double inner = std::max(0.1 * eta, 1e-6);
     for (int sw = 0; sw < std::max(1, P.params.refine_max); ++sw) {
         int its = 0;
         CKS(schur_solve_T<float>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, inner, &its, &capped));
@@ -523,6 +613,14 @@ static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
         *sweeps = sw + 1;
         if (nr <= eta * normF) break;
     }
+    return HPG_OK;
+}
+
+static hpg_status set_alpha(hpg_ctx* ctx, Problem& P, double alpha) {
+    DevState& D = P.D;
+    D.h_scal[8] = alpha;
+    CK(cudaMemcpyAsync(D.alpha_dev, D.h_scal + 8, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return HPG_OK;
 }
 
@@ -554,6 +652,7 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
     const int nsteps = (int)std::min<size_t>(H.alphas.size(), HPG_MAX_ALPHA);
     for (int k = 0; k < nsteps && status == HPG_OK; ++k) {
         const double alpha = H.alphas[k];
+        CKS(set_alpha(ctx, P, alpha));
         if (k > 0) CK(cudaMemcpyAsync(D.psi_prev, D.x + Nu0, Npsi * sizeof(double), cudaMemcpyDeviceToDevice, s));
         int flag = 0;
         CKS(eval_state(ctx, P, D.x, D.gw, D.eg));
@@ -610,13 +709,51 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
     return status;
 }
 
+// Several independent solves in flight at once: up to ctx->concurrency host
+// workers, each driving its own CUDA stream (forked from and joined back to the
+// context's stream), pull problems from a shared queue.  Kernels of different
+// problems overlap on the device; each problem's arithmetic and reduction
+// order is exactly that of hpg_solve, so results do not depend on the mix.
 hpg_status solve_batch(hpg_ctx* ctx, std::vector<Problem*>& probs) {
-    hpg_status first = HPG_OK;
-    for (Problem* P : probs) {
-        hpg_status s = solve_problem(ctx, *P);
-        if (s != HPG_OK && first == HPG_OK) first = s;
+    const int n = (int)probs.size();
+    const int W = std::max(1, std::min(ctx->concurrency, n));
+    while ((int)ctx->side_streams.size() < W) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        ctx->side_streams.push_back(st);
+        ctx->side_events.push_back(ev);
     }
-    return first;
+    CK(cudaEventRecord(ctx->side_events[0], ctx->stream));
+    for (int w = 0; w < W; ++w) CK(cudaStreamWaitEvent(ctx->side_streams[w], ctx->side_events[0], 0));
+    std::vector<hpg_status> status(n, HPG_OK);
+    std::vector<std::string> errs(n);
+    std::atomic<int> next{0};
+    auto worker = [&](int w) {
+        cudaSetDevice(ctx->device);
+        hpg_ctx local;
+        local.device = ctx->device;
+        local.stream = ctx->side_streams[w];
+        for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
+            status[i] = solve_problem(&local, *probs[i]);
+            if (status[i] != HPG_OK) errs[i] = local.err;
+        }
+    };
+    std::vector<std::thread> threads;
+    for (int w = 1; w < W; ++w) threads.emplace_back(worker, w);
+    worker(0);
+    for (auto& t : threads) t.join();
+    for (int w = 0; w < W; ++w) {
+        CK(cudaEventRecord(ctx->side_events[w], ctx->side_streams[w]));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->side_events[w], 0));
+    }
+    for (int i = 0; i < n; ++i)
+        if (status[i] != HPG_OK) {
+            ctx->err = errs[i];
+            return status[i];
+        }
+    return HPG_OK;
 }
 
 // ------------------------------------------------------------ operators (tests)
@@ -643,6 +780,7 @@ hpg_status op_set_state(hpg_ctx* ctx, Problem& P, const double* u_full, const do
     CKS(eval_state(ctx, P, D.x, D.gw, D.eg));
     CK(cudaStreamSynchronize(s));
     P.state_alpha = alpha;
+    CKS(set_alpha(ctx, P, alpha));
     return HPG_OK;
 }
 
@@ -722,12 +860,14 @@ hpg_status op_schur(hpg_ctx* ctx, Problem& P, int precision, const double* x, do
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
     const long long n = (long long)P.H.Npsi;
+    const long long gsz = (long long)(P.H.Nq * gauss_stride(P.H.kind, P.H.d));
+    CK(cudaMemcpyAsync(D.gwl, D.gw, gsz * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpy(D.yp, x, n * sizeof(double), cudaMemcpyHostToDevice));
     if (precision == HPG_FP64) {
         CK(cudaMemcpyAsync(D.zp_d, D.yp, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         CKS(schur_apply_T<double>(ctx, P, P.state_alpha, D.zp_d, D.xs));
     } else {
-        CK(launch_convert<double, float>(D.gw, D.gwf, (long long)(P.H.Nq * gauss_stride(P.H.kind, P.H.d)), s));
+        CK(launch_convert<double, float>(D.gwl, D.gwf, gsz, s));
         CK(launch_convert<double, float>(D.yp, D.zp_f, n, s));
         CKS(schur_apply_T<float>(ctx, P, P.state_alpha, D.zp_f, D.xs));
     }
@@ -756,6 +896,80 @@ hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double r
     CK(cudaStreamSynchronize(s));
     CK(cudaMemcpy(delta, D.delta, (P.H.Nu0 + P.H.Npsi) * sizeof(double), cudaMemcpyDeviceToHost));
     if (its) *its = it;
+    return HPG_OK;
+}
+
+// Enqueue `reps` applications of one kernel class on the current state, with
+// no host synchronisation (for timing with events on the context's stream).
+// The launches are captured once per (class, precision, reps) into a CUDA
+// graph and replayed, so that host launch overhead does not enter the timing.
+static hpg_status enqueue_kernel(hpg_ctx* ctx, Problem& P, int cls, bool f32, double alpha) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    switch (cls) {
+        case HPG_K_FDM:
+            if (f32) CK(launch_fdm<float>(D.gf, nullptr, alpha, D.tu_f, D.tu2_f, D.w1_f, D.w2_f, s));
+            else CK(launch_fdm<double>(D.gd, nullptr, alpha, D.tu_d, D.tu2_d, D.w1_d, D.w2_d, s));
+            break;
+        case HPG_K_PRECOND:
+            if (f32) CK(launch_precond<float, double, float>(D.gf, D.Sinv_f, D.yp, D.zp_f, s));
+            else CK(launch_precond<double, double, double>(D.gd, D.Sinv_d, D.yp, D.zp_d, s));
+            break;
+        case HPG_K_BAPPLY:
+            if (f32) CK(launch_bapply<float, float, float>(D.gf, D.zp_f, D.tu_f, s));
+            else CK(launch_bapply<double, double, double>(D.gd, D.zp_d, D.tu_d, s));
+            break;
+        case HPG_K_SCHUR:
+            if (f32) CK(launch_schur_rest<float, double>(D.gf, D.gwf, P.params.beta, D.zp_f, D.tu2_f, D.xs, s));
+            else CK(launch_schur_rest<double, double>(D.gd, D.gwl, P.params.beta, D.zp_d, D.tu2_d, D.xs, s));
+            break;
+        case HPG_K_NEWTON_APPLY:
+            CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, D.x, D.r, s));
+            break;
+        case HPG_K_FACTOR:
+            if (f32) CK(launch_factor<float>(D.gf, D.gwf, alpha, P.params.beta, D.Sinv_f, nullptr, D.flag, D.fwork_f, s));
+            else CK(launch_factor<double>(D.gd, D.gwl, alpha, P.params.beta, D.Sinv_d, nullptr, D.flag, D.fwork_d, s));
+            break;
+        case HPG_K_EVAL:
+            CK(launch_eval(D.gd, D.x + P.H.Nu0, D.phiq, D.gwt, nullptr, D.egt, D.flag, s));
+            break;
+        default:
+            return HPG_ERR_ARG;
+    }
+    return HPG_OK;
+}
+
+hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, int reps) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long gsz = (long long)(P.H.Nq * gauss_stride(P.H.kind, P.H.d));
+    const bool f32 = precision == HPG_MIXED;
+    const double alpha = P.state_alpha > 0.0 ? P.state_alpha : (P.H.alphas.empty() ? 1.0 : P.H.alphas.back());
+    const long long key = ((long long)cls * 4 + (f32 ? 1 : 0)) * 1000003LL + reps;
+    auto it = D.bench_graphs.find(key);
+    if (it == D.bench_graphs.end()) {
+        // operands of this linearisation: the weights of the current state
+        CK(cudaMemcpyAsync(D.gwl, D.gw, gsz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(launch_convert<double, float>(D.gwl, D.gwf, gsz, s));
+        CK(cudaStreamSynchronize(s));
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        hpg_status st = HPG_OK;
+        const long long before = kernel_launch_count();
+        for (int r = 0; r < reps && st == HPG_OK; ++r) st = enqueue_kernel(ctx, P, cls, f32, alpha);
+        const long long nk = kernel_launch_count() - before;
+        add_kernel_launches(-nk);
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st != HPG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        CK(ce);
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+        it = D.bench_graphs.emplace(key, std::make_pair(ex, nk)).first;
+    }
+    CK(cudaGraphLaunch(it->second.first, s));
+    add_kernel_launches(it->second.second);
     return HPG_OK;
 }
 

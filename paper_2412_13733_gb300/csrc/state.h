@@ -33,7 +33,14 @@ struct DevState {
     double *x = nullptr, *xt = nullptr;          // current and trial
     double *psi_prev = nullptr;
     double *gw = nullptr, *gwt = nullptr;        // Gauss weights (current, trial)
-    float* gwf = nullptr;                        // FP32 copy of gw
+    double* gwl = nullptr;                       // weights of the current linearisation (FP64)
+    float* gwf = nullptr;                        // FP32 copy of gwl
+    double* fwork_d = nullptr;                   // factor workspace when blocks exceed shared memory
+    float* fwork_f = nullptr;
+    double* alpha_dev = nullptr;                 // alpha of the current proximal step (device)
+    cudaGraphExec_t gmres_graph[2] = {nullptr, nullptr};   // captured GMRES chunk per precision
+    long long graph_kernels[2] = {0, 0};                    // kernels in each captured chunk
+    std::map<long long, std::pair<cudaGraphExec_t, long long>> bench_graphs;   // hpg_launch_kernel replays
     double *eg = nullptr, *egt = nullptr;
     double *F = nullptr, *Ft = nullptr, *delta = nullptr, *r = nullptr, *dcorr = nullptr;
     double* Sinv_d = nullptr;
@@ -87,6 +94,9 @@ struct hpg_ctx {
     std::map<int, std::unique_ptr<hpg::Problem>> problems;
     int next_id = 1;
     std::string err;
+    int concurrency = 8;                       // streams/host workers used by hpg_solve_batch
+    std::vector<cudaStream_t> side_streams;    // owned; forked from / joined to `stream`
+    std::vector<cudaEvent_t> side_events;
 };
 
 namespace hpg {
@@ -106,5 +116,6 @@ hpg_status op_factor(hpg_ctx* ctx, Problem& P, int precision, double* blocks);
 hpg_status op_precond_inv(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y);
 hpg_status op_schur(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y);
 hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double rtol, double* delta, int* its);
+hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, int reps);
 
 }  // namespace hpg

@@ -64,6 +64,7 @@ SIGNATURES = {
     "hpg_set_params": ([_ctx, C.c_int, _P(hpg_params)], C.c_int),
     "hpg_solve": ([_ctx, C.c_int], C.c_int),
     "hpg_solve_batch": ([_ctx, _P(C.c_int), C.c_int], C.c_int),
+    "hpg_set_concurrency": ([_ctx, C.c_int], C.c_int),
     "hpg_get_u": ([_ctx, C.c_int, _pd, _sz], C.c_int),
     "hpg_get_psi": ([_ctx, C.c_int, _pd, _sz], C.c_int),
     "hpg_get_stats": ([_ctx, C.c_int, _P(hpg_stats)], C.c_int),
@@ -79,6 +80,7 @@ SIGNATURES = {
     "hpg_apply_precond_inv": ([_ctx, C.c_int, C.c_int, _pd, _pd, _sz], C.c_int),
     "hpg_apply_schur": ([_ctx, C.c_int, C.c_int, _pd, _pd, _sz], C.c_int),
     "hpg_newton_direction": ([_ctx, C.c_int, C.c_int, _d, _pd, _sz, _P(C.c_int)], C.c_int),
+    "hpg_launch_kernel": ([_ctx, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
 }
 
 _lib = None
@@ -137,6 +139,16 @@ class Context:
         if rc != 0:
             raise HpgError(rc, f"{what}: {self.L.hpg_last_error(self.h).decode()}")
         return rc
+
+    def solve_batch(self, problems, check=True):
+        ids = (C.c_int * len(problems))(*[p.pid for p in problems])
+        rc = self.L.hpg_solve_batch(self.h, ids, len(problems))
+        if check:
+            self.check(rc, "hpg_solve_batch")
+        return rc
+
+    def set_concurrency(self, n):
+        self.check(self.L.hpg_set_concurrency(self.h, int(n)), "hpg_set_concurrency")
 
     def close(self):
         if self.h:
@@ -258,6 +270,10 @@ class Problem:
         ln = (C.c_longlong * len(KERNEL_CLASSES))()
         self.ctx.check(self.L.hpg_get_kernel_times(self.ctx.h, self.pid, _dptr(ms), ln, len(KERNEL_CLASSES)))
         return {k: (float(ms[i]), int(ln[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def launch_kernel(self, name, precision=HPG_FP64, reps=1):
+        self.ctx.check(self.L.hpg_launch_kernel(self.ctx.h, self.pid, KERNEL_CLASSES.index(name), int(precision),
+                                                int(reps)), "hpg_launch_kernel")
 
     def reset_kernel_times(self):
         self.ctx.check(self.L.hpg_reset_kernel_times(self.ctx.h, self.pid))
