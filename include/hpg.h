@@ -262,6 +262,24 @@ hpg_status hpg_apply_precond_inv(hpg_ctx* ctx, int pid, int precision, const dou
 /* y = S x, S = -(D_psi + E_beta + B^T A_alpha^{-1} B) of eq. (schur4). */
 hpg_status hpg_apply_schur(hpg_ctx* ctx, int pid, int precision, const double* x, double* y,
                            size_t len);
+/* y_dev = A_alpha^{-1} x_dev, the same FP64 fast-diagonalisation apply as
+ * hpg_apply_stiffness_inv, for callers that cannot allocate device memory at
+ * call time: code running while a CUDA stream is being captured into a graph
+ * (where cudaMalloc is not allowed), or real-time loops that forbid allocation
+ * after start-up.  The paper has no counterpart; this is a library service.
+ * x_dev, y_dev: device pointers of length n_u_interior (len >= that); they may
+ * alias.  Its intermediate tensors live in one fixed device array of the
+ * library (4 MiB, held by every GPU that loads libhpg until exit), so it
+ * accepts at most 262144 interior unknowns (HPG_ERR_ARG beyond, with a message
+ * in hpg_last_error) and calls no allocator.  The problem's operators must
+ * already be on the device (after hpg_solve or hpg_set_state), else
+ * HPG_ERR_STATE.  The first call on a device looks up the array's device
+ * address once; make that first call before any stream capture.  Work is
+ * enqueued on the context's stream; y_dev is ready when that stream is.
+ * Every call shares the array, so calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. */
+hpg_status hpg_apply_stiffness_inv_noalloc(hpg_ctx* ctx, int pid, double alpha, const double* x_dev, double* y_dev,
+                                           size_t len);
 /* Solve G delta = F(state) by eq. (schur2) + GMRES (relative tolerance rtol);
  * returns delta and the GMRES iteration count. */
 hpg_status hpg_newton_direction(hpg_ctx* ctx, int pid, int precision, double rtol, double* delta,

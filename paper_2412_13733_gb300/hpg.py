@@ -81,6 +81,7 @@ SIGNATURES = {
     "hpg_apply_schur": ([_ctx, C.c_int, C.c_int, _pd, _pd, _sz], C.c_int),
     "hpg_newton_direction": ([_ctx, C.c_int, C.c_int, _d, _pd, _sz, _P(C.c_int)], C.c_int),
     "hpg_launch_kernel": ([_ctx, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
+    "hpg_apply_stiffness_inv_noalloc": ([_ctx, C.c_int, _d, C.c_void_p, C.c_void_p, _sz], C.c_int),
 }
 
 _lib = None
@@ -302,6 +303,11 @@ class Problem:
         self.ctx.check(self.L.hpg_apply_stiffness_inv(self.ctx.h, self.pid, int(precision), _dptr(x), _dptr(y),
                                                       y.size))
         return y
+
+    def apply_stiffness_inv_noalloc(self, alpha, x_dev_ptr, y_dev_ptr, length):
+        """A_alpha^{-1} on device pointers without any allocation (see hpg.h)."""
+        return self.L.hpg_apply_stiffness_inv_noalloc(self.ctx.h, self.pid, float(alpha), C.c_void_p(x_dev_ptr),
+                                                       C.c_void_p(y_dev_ptr), int(length))
 
     def factor_precond(self, precision=HPG_FP64, dump=False):
         if dump:
