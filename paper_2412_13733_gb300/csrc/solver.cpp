@@ -569,37 +569,39 @@ static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const do
     return HPG_OK;
 }
 
-// Solve G delta = F for the current factorisation: FP64 GMRES, or FP32 inner
-// solves inside FP64 iterative refinement (r = F - G delta in FP64).
+// Solve G delta = F for the current factorisation.  FP64: GMRES on S in FP64;
+// if it stops at its cap the FP64 residual r = F - G delta is formed and the
+// solve is repeated on r (a restart).  Mixed: FP32 inner solves inside FP64
+// iterative refinement until ||F - G delta|| <= eta ||F||.
 static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* F, double normF, double eta,
                                double* delta, int* its_total, int* sweeps) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
     const long long Nu0 = (long long)P.H.Nu0, Npsi = (long long)P.H.Npsi, Nx = Nu0 + Npsi;
-    bool capped = false;
+    const bool f64 = P.params.precision == HPG_FP64;
     *sweeps = 0;
     *its_total = 0;
-    if (P.params.precision == HPG_FP64) {
-        int its = 0;
-        CKS(schur_solve_T<double>(ctx, P, alpha, F, F + Nu0, delta, delta + Nu0, eta, &its, &capped));
-        *its_total = its;
-        if (capped) P.stats.krylov_cap_hits++;
-        return HPG_OK;
-    }
     CK(cudaMemsetAsync(delta, 0, Nx * sizeof(double), s));
     CK(cudaMemcpyAsync(D.r, F, Nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
     // FP32 inner tolerance a decade below the forcing term (floored near the FP32
     // limit) so that one refinement sweep usually meets ||F - G delta|| <= eta ||F||
-    const double inner = std::max(0.1 * eta, 1e-6);
+    const double inner = f64 ? eta : std::max(0.1 * eta, 1e-6);
+    double rnorm = normF;
     for (int sw = 0; sw < std::max(1, P.params.refine_max); ++sw) {
         int its = 0;
-        CKS(schur_solve_T<float>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, inner, &its, &capped));
+        bool capped = false;
+        // relative tolerance w.r.t. the current residual so that the target stays eta ||F||
+        const double rt = std::min(1.0, inner * normF / std::max(rnorm, 1e-300));
+        if (f64) CKS(schur_solve_T<double>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, rt, &its, &capped));
+        else CKS(schur_solve_T<float>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, rt, &its, &capped));
         *its_total += its;
+        *sweeps = sw + 1;
         if (capped) P.stats.krylov_cap_hits++;
         {
             Scope sc(P.timer, HPG_K_UPDATE, s);
             CK(launch_axpby(1.0, D.dcorr, 1.0, delta, Nx, s));
         }
+        if (f64 && !capped) break;      // FP64 GMRES residual is the true Newton-system residual
         {
             Scope sc(P.timer, HPG_K_NEWTON_APPLY, s);
             CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, delta, D.r, s));
@@ -608,10 +610,8 @@ static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
             Scope sc(P.timer, HPG_K_UPDATE, s);
             CK(launch_axpby(1.0, F, -1.0, D.r, Nx, s));
         }
-        double nr = 0.0;
-        CKS(norm_of(ctx, P, D.r, Nx, &nr));
-        *sweeps = sw + 1;
-        if (nr <= eta * normF) break;
+        CKS(norm_of(ctx, P, D.r, Nx, &rnorm));
+        if (rnorm <= eta * normF) break;
     }
     return HPG_OK;
 }
