@@ -235,6 +235,33 @@ hpg_status hpg_reset_kernel_times(hpg_ctx* ctx, int pid);
  * the kernels write only scratch buffers. */
 hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precision, int reps);
 
+/* ------------------------------------------------------------ request loop
+ * Continuous batching of independent solves.  The client creates and fills
+ * problems as usual and submits them; `workers` host threads, each with its
+ * own CUDA stream, take queued requests in arrival order as soon as they are
+ * free and the request's device footprint fits in `device_budget_bytes`
+ * (0: 80% of the device memory free at start), first fit.  Running requests
+ * overlap on the GPU; each one's arithmetic is exactly that of hpg_solve.
+ * A request's device bytes count against the budget from admission until its
+ * solve ends; the result (u_h, psi_h, stats) is then kept in host memory and
+ * the problem's device buffers are released (a later hpg_solve or
+ * component call re-creates them).  While queued or running, every call on
+ * that problem except hpg_poll/hpg_wait returns HPG_ERR_BUSY. */
+hpg_status hpg_server_start(hpg_ctx* ctx, int workers, size_t device_budget_bytes);
+/* Finish running and queued requests that fit, join the workers. */
+hpg_status hpg_server_stop(hpg_ctx* ctx);
+/* Queue problem `pid`; returns a ticket.  HPG_ERR_OOM if it can never fit. */
+hpg_status hpg_submit(hpg_ctx* ctx, int pid, long long* ticket);
+/* Non-blocking: *done = 1 once finished, *result its hpg_status. */
+hpg_status hpg_poll(hpg_ctx* ctx, long long ticket, int* done, hpg_status* result);
+/* Bounded wait: HPG_ERR_TIMEOUT if not finished within timeout_ms. */
+hpg_status hpg_wait(hpg_ctx* ctx, long long ticket, double timeout_ms, hpg_status* result);
+/* times3 = {queued ms, running ms, submit-to-done ms} (0 while unfinished). */
+hpg_status hpg_ticket_times(hpg_ctx* ctx, long long ticket, double* times3);
+/* Bytes currently charged to the budget (running requests), and the
+ * footprint estimate for problem pid (pid ignored when estimate is NULL). */
+hpg_status hpg_server_memory(hpg_ctx* ctx, int pid, size_t* in_use, size_t* estimate);
+
 /* ------------------------------------------- component operators (testing)
  * These act on an explicit state (u, psi, psi_prev, alpha) uploaded by
  * hpg_set_state, on host vectors in the orderings above.  precision is an

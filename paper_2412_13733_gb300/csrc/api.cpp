@@ -18,6 +18,15 @@ Problem* find(hpg_ctx* ctx, int pid) {
     return it == ctx->problems.end() ? nullptr : it->second.get();
 }
 
+// a problem queued or running in the request loop may not be touched by the client
+#define NOT_BUSY(P)                                                            \
+    do {                                                                       \
+        if ((P)->busy.load()) {                                                \
+            ctx->err = "problem is queued or running in the request loop";     \
+            return HPG_ERR_BUSY;                                               \
+        }                                                                      \
+    } while (0)
+
 hpg_status cuda_ok(hpg_ctx* ctx) {
     if (cudaSetDevice(ctx->device) != cudaSuccess) {
         ctx->err = "cudaSetDevice failed";
@@ -104,8 +113,9 @@ hpg_status hpg_create(hpg_ctx** out, int device, void* cuda_stream) {
 hpg_status hpg_destroy(hpg_ctx* ctx) {
     if (!ctx) return HPG_OK;
     cudaSetDevice(ctx->device);
+    hpg::server_stop(ctx);
     cudaStreamSynchronize(ctx->stream);
-    for (auto& kv : ctx->problems) hpg::free_device(*kv.second);
+    for (auto& kv : ctx->problems) hpg::free_device(*kv.second, ctx->stream);
     ctx->problems.clear();
     for (auto st : ctx->side_streams) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
     for (auto ev : ctx->side_events) cudaEventDestroy(ev);
@@ -152,9 +162,11 @@ hpg_status hpg_problem_create(hpg_ctx* ctx, int dim, const double* lo, const dou
 hpg_status hpg_problem_free(hpg_ctx* ctx, int pid) {
     Problem* P = find(ctx, pid);
     if (!P) return HPG_ERR_ARG;
+    NOT_BUSY(P);
+    hpg::server_release(ctx, *P);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    hpg::free_device(*P);
+    hpg::free_device(*P, ctx->stream);
     ctx->problems.erase(pid);
     return HPG_OK;
 }
@@ -173,6 +185,7 @@ hpg_status hpg_problem_sizes(hpg_ctx* ctx, int pid, size_t* n_u_full, size_t* n_
 hpg_status hpg_set_rhs(hpg_ctx* ctx, int pid, hpg_field_fn f, void* user) {
     Problem* P = find(ctx, pid);
     if (!P || !f) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     GUARD_BEGIN
     hpg::compute_rhs(P->H, f, user, false, 0.0);
     P->data_dirty = true;
@@ -183,6 +196,7 @@ hpg_status hpg_set_rhs(hpg_ctx* ctx, int pid, hpg_field_fn f, void* user) {
 hpg_status hpg_set_rhs_const(hpg_ctx* ctx, int pid, double f) {
     Problem* P = find(ctx, pid);
     if (!P || !std::isfinite(f)) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     GUARD_BEGIN
     hpg::compute_rhs(P->H, nullptr, nullptr, true, f);
     P->data_dirty = true;
@@ -205,6 +219,7 @@ hpg_status hpg_quad_points(hpg_ctx* ctx, int pid, double* pts, size_t len) {
 hpg_status hpg_set_constraint_values(hpg_ctx* ctx, int pid, const double* phi_q, size_t len) {
     Problem* P = find(ctx, pid);
     if (!P || !phi_q) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     if (len < P->H.Nq) return HPG_ERR_ARG;
     for (size_t i = 0; i < P->H.Nq; ++i)
         if (!std::isfinite(phi_q[i])) { ctx->err = "non-finite constraint value"; return HPG_ERR_NONFINITE; }
@@ -221,6 +236,7 @@ hpg_status hpg_set_constraint_values(hpg_ctx* ctx, int pid, const double* phi_q,
 hpg_status hpg_set_constraint(hpg_ctx* ctx, int pid, hpg_field_fn phi, void* user) {
     Problem* P = find(ctx, pid);
     if (!P || !phi) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     GUARD_BEGIN
     std::vector<double> pts, vals(P->H.Nq);
     hpg::latent_points(P->H, pts);
@@ -232,6 +248,7 @@ hpg_status hpg_set_constraint(hpg_ctx* ctx, int pid, hpg_field_fn phi, void* use
 hpg_status hpg_set_dirichlet(hpg_ctx* ctx, int pid, hpg_field_fn g, void* user) {
     Problem* P = find(ctx, pid);
     if (!P) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     GUARD_BEGIN
     hpg::compute_lifting(P->H, g, user);
     for (double v : P->H.ulift)
@@ -245,6 +262,7 @@ hpg_status hpg_set_dirichlet(hpg_ctx* ctx, int pid, hpg_field_fn g, void* user) 
 hpg_status hpg_set_alpha_schedule(hpg_ctx* ctx, int pid, double a1, double cap) {
     Problem* P = find(ctx, pid);
     if (!P || !(a1 > 0.0) || !(cap > 0.0)) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     std::vector<double> al;
     for (int k = 1; k <= HPG_MAX_ALPHA; ++k) {
         const double a = std::min(a1 * std::pow(2.0, 0.5 * (k - 1)), cap);
@@ -258,6 +276,7 @@ hpg_status hpg_set_alpha_schedule(hpg_ctx* ctx, int pid, double a1, double cap) 
 hpg_status hpg_set_alpha_list(hpg_ctx* ctx, int pid, const double* alphas, int count) {
     Problem* P = find(ctx, pid);
     if (!P || !alphas || count < 1 || count > HPG_MAX_ALPHA) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     for (int i = 0; i < count; ++i)
         if (!(alphas[i] > 0.0) || !std::isfinite(alphas[i])) return HPG_ERR_ARG;
     P->H.alphas.assign(alphas, alphas + count);
@@ -267,13 +286,14 @@ hpg_status hpg_set_alpha_list(hpg_ctx* ctx, int pid, const double* alphas, int c
 hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params) {
     Problem* P = find(ctx, pid);
     if (!P || !params) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     if (params->krylov_max < 1 || params->krylov_max > 1000 || params->newton_max < 0 ||
         !(params->newton_tol > 0.0) || !(params->krylov_rtol > 0.0) || params->beta < 0.0 ||
         (params->precision != HPG_FP64 && params->precision != HPG_MIXED) || params->ls_max < 0)
         return HPG_ERR_ARG;
     const bool realloc = P->alloc_done && params->krylov_max != P->params.krylov_max;
     if (realloc) {
-        hpg::free_device(*P);
+        hpg::free_device(*P, ctx->stream);
         P->data_dirty = P->phi_dirty = true;
     }
     P->params = *params;
@@ -296,11 +316,13 @@ static hpg_status ready(hpg_ctx* ctx, Problem* P) {
 hpg_status hpg_solve(hpg_ctx* ctx, int pid) {
     Problem* P = find(ctx, pid);
     if (!P) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     hpg_status s = cuda_ok(ctx);
     if (s != HPG_OK) return s;
     GUARD_BEGIN
     s = ready(ctx, P);
     if (s != HPG_OK) return s;
+    P->host_result = false;
     return hpg::solve_problem(ctx, *P);
     GUARD_END
 }
@@ -314,25 +336,43 @@ hpg_status hpg_solve_batch(hpg_ctx* ctx, const int* pids, int count) {
     for (int i = 0; i < count; ++i) {
         Problem* P = find(ctx, pids[i]);
         if (!P) return HPG_ERR_ARG;
+        NOT_BUSY(P);
         for (Problem* Q : ps)
             if (Q == P) { ctx->err = "duplicate problem id in batch"; return HPG_ERR_ARG; }
         s = ready(ctx, P);
         if (s != HPG_OK) return s;
+        P->host_result = false;
         ps.push_back(P);
     }
     return hpg::solve_batch(ctx, ps);
     GUARD_END
 }
 
+// [u interior; psi] of the last solve, from the device or from the host copy
+// kept by the request loop.
+static hpg_status result_x(hpg_ctx* ctx, Problem* P, std::vector<double>& x) {
+    (void)ctx;
+    const size_t n = P->H.Nu0 + P->H.Npsi;
+    if (P->host_result) {
+        x = P->host_x;
+        return HPG_OK;
+    }
+    if (!P->alloc_done) return HPG_ERR_STATE;
+    x.resize(n);
+    if (cudaMemcpy(x.data(), P->D.x, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return HPG_ERR_CUDA;
+    return HPG_OK;
+}
+
 hpg_status hpg_get_u(hpg_ctx* ctx, int pid, double* u_full, size_t len) {
     Problem* P = find(ctx, pid);
     if (!P || !u_full) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     if (len < P->H.Nu_full) return HPG_ERR_ARG;
     if (!P->solved) return HPG_ERR_STATE;
     hpg::HostProblem& H = P->H;
-    std::vector<double> u0(H.Nu0);
-    if (cudaMemcpy(u0.data(), P->D.x, H.Nu0 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return HPG_ERR_CUDA;
+    std::vector<double> x;
+    hpg_status st = result_x(ctx, P, x);
+    if (st != HPG_OK) return st;
     for (size_t i = 0; i < H.Nu_full; ++i) u_full[i] = H.sign * H.ulift[i];
     for (size_t I = 0; I < H.Nu0; ++I) {
         size_t ii = I, full = 0, stride = 1;
@@ -341,7 +381,7 @@ hpg_status hpg_get_u(hpg_ctx* ctx, int pid, double* u_full, size_t len) {
             ii /= H.dir[j].n1;
             stride *= H.dir[j].N1;
         }
-        u_full[full] = H.sign * u0[I];
+        u_full[full] = H.sign * x[I];
     }
     return HPG_OK;
 }
@@ -349,10 +389,13 @@ hpg_status hpg_get_u(hpg_ctx* ctx, int pid, double* u_full, size_t len) {
 hpg_status hpg_get_psi(hpg_ctx* ctx, int pid, double* psi, size_t len) {
     Problem* P = find(ctx, pid);
     if (!P || !psi) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     if (len < P->H.Npsi) return HPG_ERR_ARG;
     if (!P->solved) return HPG_ERR_STATE;
-    if (cudaMemcpy(psi, P->D.x + P->H.Nu0, P->H.Npsi * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return HPG_ERR_CUDA;
+    std::vector<double> x;
+    hpg_status st = result_x(ctx, P, x);
+    if (st != HPG_OK) return st;
+    std::memcpy(psi, x.data() + P->H.Nu0, P->H.Npsi * sizeof(double));
     return HPG_OK;
 }
 
@@ -366,6 +409,7 @@ hpg_status hpg_get_stats(hpg_ctx* ctx, int pid, hpg_stats* stats) {
 hpg_status hpg_eval_u(hpg_ctx* ctx, int pid, const double* pts, int npts, double* out) {
     Problem* P = find(ctx, pid);
     if (!P || !pts || !out || npts < 0) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     if (!P->solved) return HPG_ERR_STATE;
     GUARD_BEGIN
     std::vector<double> u(P->H.Nu_full);
@@ -379,14 +423,16 @@ hpg_status hpg_eval_u(hpg_ctx* ctx, int pid, const double* pts, int npts, double
 hpg_status hpg_feasible_u(hpg_ctx* ctx, int pid, double* out_q, size_t len) {
     Problem* P = find(ctx, pid);
     if (!P || !out_q) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     if (P->H.kind == HPG_GRADIENT) return HPG_ERR_ARG;
     if (len < P->H.Nq) return HPG_ERR_ARG;
     if (!P->solved) return HPG_ERR_STATE;
     // u~ = phi - exp(-psi) at the latent Gauss points (eq. pG), in the caller's sign
     hpg::HostProblem& H = P->H;
-    std::vector<double> psi(H.Npsi);
-    if (cudaMemcpy(psi.data(), P->D.x + H.Nu0, H.Npsi * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return HPG_ERR_CUDA;
+    std::vector<double> x;
+    hpg_status stx = result_x(ctx, P, x);
+    if (stx != HPG_OK) return stx;
+    std::vector<double> psi(x.begin() + H.Nu0, x.end());
     const int n = H.n;
     for (size_t c = 0; c < H.Nc; ++c)
         for (size_t q = 0; q < H.nloc; ++q) {
@@ -434,6 +480,7 @@ hpg_status hpg_set_state(hpg_ctx* ctx, int pid, const double* u_full, const doub
                          double alpha) {
     Problem* P = find(ctx, pid);
     if (!P || !u_full || !psi || !psi_prev || !(alpha > 0.0)) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     GUARD_BEGIN
     hpg_status s = op_ready(ctx, P);
     if (s != HPG_OK) return s;
@@ -511,11 +558,69 @@ hpg_status hpg_newton_direction(hpg_ctx* ctx, int pid, int precision, double rto
 hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precision, int reps) {
     Problem* P = find(ctx, pid);
     if (!P || reps < 0 || kernel_class < 0 || kernel_class >= HPG_K_COUNT) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     if (!P->alloc_done || !(P->solved || P->state_alpha > 0.0)) return HPG_ERR_STATE;
     if (cuda_ok(ctx) != HPG_OK) return HPG_ERR_CUDA;
     GUARD_BEGIN
     return hpg::op_launch_kernel(ctx, *P, kernel_class, precision, reps);
     GUARD_END
+}
+
+// ------------------------------------------------------------ request loop
+hpg_status hpg_server_start(hpg_ctx* ctx, int workers, size_t device_budget_bytes) {
+    if (!ctx || workers < 1 || workers > 64) return HPG_ERR_ARG;
+    if (cuda_ok(ctx) != HPG_OK) return HPG_ERR_CUDA;
+    size_t budget = device_budget_bytes;
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return HPG_ERR_CUDA;
+        budget = (size_t)(0.8 * (double)fr);
+    }
+    GUARD_BEGIN
+    return hpg::server_start(ctx, workers, budget);
+    GUARD_END
+}
+
+hpg_status hpg_server_stop(hpg_ctx* ctx) {
+    if (!ctx) return HPG_ERR_ARG;
+    return hpg::server_stop(ctx);
+}
+
+hpg_status hpg_submit(hpg_ctx* ctx, int pid, long long* ticket) {
+    Problem* P = find(ctx, pid);
+    if (!P || !ticket) return HPG_ERR_ARG;
+    NOT_BUSY(P);
+    if (!P->H.has_phi || P->H.alphas.empty()) { ctx->err = "problem data incomplete"; return HPG_ERR_STATE; }
+    GUARD_BEGIN
+    return hpg::server_submit(ctx, *P, ticket);
+    GUARD_END
+}
+
+hpg_status hpg_poll(hpg_ctx* ctx, long long ticket, int* done, hpg_status* result) {
+    if (!ctx) return HPG_ERR_ARG;
+    return hpg::server_poll(ctx, ticket, 0.0, done, result, nullptr);
+}
+
+hpg_status hpg_wait(hpg_ctx* ctx, long long ticket, double timeout_ms, hpg_status* result) {
+    if (!ctx || !(timeout_ms > 0.0)) return HPG_ERR_ARG;
+    int done = 0;
+    return hpg::server_poll(ctx, ticket, timeout_ms, &done, result, nullptr);
+}
+
+hpg_status hpg_ticket_times(hpg_ctx* ctx, long long ticket, double* times3) {
+    if (!ctx || !times3) return HPG_ERR_ARG;
+    return hpg::server_poll(ctx, ticket, 0.0, nullptr, nullptr, times3);
+}
+
+hpg_status hpg_server_memory(hpg_ctx* ctx, int pid, size_t* in_use, size_t* estimate) {
+    if (!ctx) return HPG_ERR_ARG;
+    if (in_use) *in_use = hpg::server_in_use(ctx);
+    if (estimate) {
+        Problem* P = find(ctx, pid);
+        if (!P) return HPG_ERR_ARG;
+        *estimate = hpg::estimate_device_bytes(*P);
+    }
+    return HPG_OK;
 }
 
 }  // extern "C"

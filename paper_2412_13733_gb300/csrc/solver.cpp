@@ -4,6 +4,7 @@
 // inner solve, and the component operators used by the tests.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <thread>
 #include <chrono>
 #include <cmath>
@@ -77,23 +78,26 @@ template <typename T>
 static T* dalloc(DevState& D, size_t n, bool& ok) {
     void* p = nullptr;
     if (n == 0) n = 1;
-    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) { ok = false; return nullptr; }
+    if (cudaMallocAsync(&p, n * sizeof(T), D.alloc_stream) != cudaSuccess) { ok = false; return nullptr; }
     D.allocs.push_back(p);
     D.bytes += n * sizeof(T);
     return static_cast<T*>(p);
 }
 
-void free_device(Problem& P) {
+Problem::~Problem() {
+    if (pinned_scal) cudaFreeHost(pinned_scal);
+    if (pinned_iflag) cudaFreeHost(pinned_iflag);
+}
+
+// Stream-ordered release (cudaFreeAsync), so that finishing one problem does
+// not synchronise the device while other problems run on other streams.
+void free_device(Problem& P, cudaStream_t s) {
     for (auto& gx : P.D.gmres_graph)
         if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
     for (auto& kv : P.D.bench_graphs) cudaGraphExecDestroy(kv.second.first);
     P.D.bench_graphs.clear();
-    for (void* p : P.D.allocs) cudaFree(p);
+    for (void* p : P.D.allocs) cudaFreeAsync(p, s);
     P.D.allocs.clear();
-    if (P.D.h_scal) cudaFreeHost(P.D.h_scal);
-    if (P.D.h_iflag) cudaFreeHost(P.D.h_iflag);
-    P.D.h_scal = nullptr;
-    P.D.h_iflag = nullptr;
     for (auto e : P.timer.pool) cudaEventDestroy(e);
     P.timer.pool.clear();
     P.D = DevState{};
@@ -139,6 +143,18 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     HostProblem& H = P.H;
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
+    D.alloc_stream = s;
+    {
+        // keep freed pool memory cached in this process (no release to the OS between solves)
+        static std::once_flag pool_cfg;
+        std::call_once(pool_cfg, [&] {
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+                unsigned long long thr = ~0ULL;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+        });
+    }
     bool ok = true;
     const int d = H.d;
     const bool grad = H.kind == HPG_GRADIENT;
@@ -157,7 +173,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
         D.lam_d[j] = upload_vec<double>(D, Dj.lam, ok, s);
         D.lam_f[j] = upload_vec<float>(D, Dj.lam, ok, s);
     }
-    if (!ok) { free_device(P); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
+    if (!ok) { free_device(P, s); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
     D.Vq_d = upload_vec<double>(D, H.Vq, ok, s);
     D.Vq_f = upload_vec<float>(D, H.Vq, ok, s);
     D.wq_d = upload_vec<double>(D, H.wq, ok, s);
@@ -235,20 +251,22 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     G.counter = dalloc<unsigned int>(D, 1, ok);
     G.counter2 = dalloc<unsigned int>(D, 1, ok);
     G.y = dalloc<double>(D, G.kmax + 1, ok);
-    if (!ok) { free_device(P); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
+    if (!ok) { free_device(P, s); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
     cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), s);
     cudaMemsetAsync(G.counter2, 0, sizeof(unsigned int), s);
     cudaMemsetAsync(G.iflag, 0, 4 * sizeof(int), s);
     cudaMemsetAsync(G.jdev, 0, sizeof(int), s);
-    static bool configured = false;
-    if (!configured) { configure_kernels(); configured = true; }
+    static std::once_flag configured;
+    std::call_once(configured, configure_kernels);
     cudaMemsetAsync(D.flag, 0, 4 * sizeof(int), s);
-    if (cudaMallocHost(&D.h_scal, 16 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&D.h_iflag, 8 * sizeof(int)) != cudaSuccess) {
-        free_device(P);
+    if (!P.pinned_scal && (cudaMallocHost(&P.pinned_scal, 16 * sizeof(double)) != cudaSuccess ||
+                           cudaMallocHost(&P.pinned_iflag, 8 * sizeof(int)) != cudaSuccess)) {
+        free_device(P, s);
         ctx->err = "pinned host allocation failed";
         return HPG_ERR_OOM;
     }
+    D.h_scal = P.pinned_scal;
+    D.h_iflag = P.pinned_iflag;
     // geometry views
     auto fill = [&](auto& g, auto sel) {
         g.d = d; g.n = H.n; g.ncomp = H.ncomp; g.kind = H.kind;
@@ -583,15 +601,15 @@ static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
     *its_total = 0;
     CK(cudaMemsetAsync(delta, 0, Nx * sizeof(double), s));
     CK(cudaMemcpyAsync(D.r, F, Nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    // FP32 inner tolerance a decade below the forcing term (floored near the FP32
-    // limit) so that one refinement sweep usually meets ||F - G delta|| <= eta ||F||
-    const double inner = f64 ? eta : std::max(0.1 * eta, 1e-6);
     double rnorm = normF;
     for (int sw = 0; sw < std::max(1, P.params.refine_max); ++sw) {
         int its = 0;
         bool capped = false;
-        // relative tolerance w.r.t. the current residual so that the target stays eta ||F||
-        const double rt = std::min(1.0, inner * normF / std::max(rnorm, 1e-300));
+        // GMRES tolerance relative to the current residual r, aimed at ||r|| <= eta ||F||:
+        // FP64 exactly; FP32 a decade below, floored near the FP32 limit, so that one
+        // refinement sweep usually suffices
+        const double need = eta * normF / std::max(rnorm, 1e-300);
+        const double rt = f64 ? std::min(1.0, need) : std::min(1.0, std::max(0.1 * need, 1e-6));
         if (f64) CKS(schur_solve_T<double>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, rt, &its, &capped));
         else CKS(schur_solve_T<float>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, rt, &its, &capped));
         *its_total += its;

@@ -1,6 +1,7 @@
 // Per-problem device state and the solver driver of libhpg.
 #pragma once
 
+#include <atomic>
 #include <map>
 #include <memory>
 #include <string>
@@ -54,9 +55,10 @@ struct DevState {
     double* scal = nullptr;      // [0] |F|^2 reduce target, ...
     int* flag = nullptr;         // eval/factor flags
     GmresDev gm{};
-    // pinned host mirror for scalars
+    // pinned host mirror for scalars (owned by the Problem, kept across re-allocation)
     double* h_scal = nullptr;
     int* h_iflag = nullptr;
+    cudaStream_t alloc_stream = nullptr;   // stream the stream-ordered allocations were made on
     std::vector<void*> allocs;
     size_t bytes = 0;
 };
@@ -69,8 +71,13 @@ struct KernelTimer {
     long long launches[HPG_K_COUNT] = {};
 };
 
+struct Server;
+
 struct Problem {
     int id = 0;
+    std::atomic<bool> busy{false};   // queued or running in the request loop
+    bool host_result = false;        // result copied to host_x and device memory released
+    std::vector<double> host_x;      // [u interior; psi] of the last solve when host_result
     HostProblem H;
     hpg_params params{};
     bool alloc_done = false;
@@ -83,6 +90,9 @@ struct Problem {
     bool solved = false;
     double state_alpha = 0.0;
     KernelTimer timer;
+    double* pinned_scal = nullptr;   // 16 doubles + 8 ints of pinned host memory, lazily allocated
+    int* pinned_iflag = nullptr;
+    ~Problem();
 };
 
 }  // namespace hpg
@@ -97,12 +107,14 @@ struct hpg_ctx {
     int concurrency = 8;                       // streams/host workers used by hpg_solve_batch
     std::vector<cudaStream_t> side_streams;    // owned; forked from / joined to `stream`
     std::vector<cudaEvent_t> side_events;
+    hpg::Server* server = nullptr;             // request loop (hpg_server_start)
 };
 
 namespace hpg {
 
 hpg_status alloc_device(hpg_ctx* ctx, Problem& P);
-void free_device(Problem& P);
+// Release the problem's device buffers, stream-ordered on `s`.
+void free_device(Problem& P, cudaStream_t s);
 hpg_status upload_data(hpg_ctx* ctx, Problem& P);
 hpg_status solve_problem(hpg_ctx* ctx, Problem& P);
 hpg_status solve_batch(hpg_ctx* ctx, std::vector<Problem*>& probs);
@@ -117,5 +129,14 @@ hpg_status op_precond_inv(hpg_ctx* ctx, Problem& P, int precision, const double*
 hpg_status op_schur(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y);
 hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double rtol, double* delta, int* its);
 hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, int reps);
+// request loop
+size_t estimate_device_bytes(const Problem& P);
+hpg_status server_start(hpg_ctx* ctx, int workers, size_t budget);
+hpg_status server_stop(hpg_ctx* ctx);
+hpg_status server_submit(hpg_ctx* ctx, Problem& P, long long* ticket);
+hpg_status server_poll(hpg_ctx* ctx, long long ticket, double wait_ms, int* done, hpg_status* result,
+                       double* times3);
+void server_release(hpg_ctx* ctx, Problem& P);
+size_t server_in_use(hpg_ctx* ctx);
 
 }  // namespace hpg

@@ -82,6 +82,13 @@ SIGNATURES = {
     "hpg_newton_direction": ([_ctx, C.c_int, C.c_int, _d, _pd, _sz, _P(C.c_int)], C.c_int),
     "hpg_launch_kernel": ([_ctx, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "hpg_apply_stiffness_inv_noalloc": ([_ctx, C.c_int, _d, C.c_void_p, C.c_void_p, _sz], C.c_int),
+    "hpg_server_start": ([_ctx, C.c_int, _sz], C.c_int),
+    "hpg_server_stop": ([_ctx], C.c_int),
+    "hpg_submit": ([_ctx, C.c_int, _P(C.c_longlong)], C.c_int),
+    "hpg_poll": ([_ctx, C.c_longlong, _P(C.c_int), _P(C.c_int)], C.c_int),
+    "hpg_wait": ([_ctx, C.c_longlong, _d, _P(C.c_int)], C.c_int),
+    "hpg_ticket_times": ([_ctx, C.c_longlong, _pd], C.c_int),
+    "hpg_server_memory": ([_ctx, C.c_int, _P(_sz), _P(_sz)], C.c_int),
 }
 
 _lib = None
@@ -147,6 +154,41 @@ class Context:
         if check:
             self.check(rc, "hpg_solve_batch")
         return rc
+
+    # request loop
+    def server_start(self, workers=8, budget_bytes=0):
+        self.check(self.L.hpg_server_start(self.h, int(workers), int(budget_bytes)), "hpg_server_start")
+
+    def server_stop(self):
+        self.check(self.L.hpg_server_stop(self.h), "hpg_server_stop")
+
+    def submit(self, problem):
+        t = C.c_longlong()
+        self.check(self.L.hpg_submit(self.h, problem.pid, C.byref(t)), "hpg_submit")
+        return t.value
+
+    def poll(self, ticket):
+        done, res = C.c_int(), C.c_int()
+        self.check(self.L.hpg_poll(self.h, C.c_longlong(ticket), C.byref(done), C.byref(res)), "hpg_poll")
+        return bool(done.value), res.value
+
+    def wait(self, ticket, timeout_ms=60000.0):
+        res = C.c_int()
+        rc = self.L.hpg_wait(self.h, C.c_longlong(ticket), float(timeout_ms), C.byref(res))
+        if rc != 0:
+            raise HpgError(rc, "hpg_wait")
+        return res.value
+
+    def ticket_times(self, ticket):
+        t = (C.c_double * 3)()
+        self.check(self.L.hpg_ticket_times(self.h, C.c_longlong(ticket), t), "hpg_ticket_times")
+        return tuple(t)
+
+    def server_memory(self, problem=None):
+        a, b = _sz(), _sz()
+        self.check(self.L.hpg_server_memory(self.h, problem.pid if problem else 0, C.byref(a),
+                                            C.byref(b) if problem else None))
+        return a.value, (b.value if problem else None)
 
     def set_concurrency(self, n):
         self.check(self.L.hpg_set_concurrency(self.h, int(n)), "hpg_set_concurrency")
