@@ -175,6 +175,54 @@ def alu_peak_tflops(kind, clock_mhz):
     return 1.25 * clock_mhz / 2070.0
 
 
+def serve_requests(ctx, hpg, W, prec, count, rate=None, workers=8):
+    """Serve `count` seeded 2D obstacle requests through the request loop.
+
+    rate None: saturated (all submitted at once).  Otherwise Poisson arrivals at
+    `rate` requests/s; each request's problem is set up (host) when it arrives
+    and submitted; latency = arrival -> result readable (set-up included).
+    Returns (solves/s, p50 ms, p99 ms, mean Newton, makespan s).
+    """
+    reqs = W.requests(count)
+    arr = W.arrivals(count, rate) if rate else np.zeros(count)
+    ctx.server_start(workers=workers)
+    t0 = time.perf_counter()
+    pending = {}
+    lat = []
+    newton = []
+    failed = 0
+    i = 0
+    done_t = 0.0
+    while i < count or pending:
+        now = time.perf_counter() - t0
+        while i < count and arr[i] <= now:
+            P = hpg.from_workload(ctx, reqs[i], hpg.default_params(precision=prec, newton_max=200))
+            pending[ctx.submit(P)] = (P, arr[i])
+            i += 1
+            now = time.perf_counter() - t0
+        for t in list(pending):
+            done, res = ctx.poll(t)
+            if done:
+                P, a = pending.pop(t)
+                if res != 0:
+                    failed += 1
+                else:
+                    P.u()                                 # result readable
+                end = time.perf_counter() - t0
+                lat.append(1000.0 * (end - a))
+                newton.append(P.stats()["newton_total"])
+                P.free()
+                done_t = end
+        if i < count and not pending:
+            time.sleep(max(0.0, min(0.002, arr[i] - (time.perf_counter() - t0))))
+        else:
+            time.sleep(0.0005)
+    ctx.server_stop()
+    lat = np.array(lat)
+    return (count / done_t, float(np.percentile(lat, 50)), float(np.percentile(lat, 99)), float(np.mean(newton)),
+            done_t, failed)
+
+
 def kernel_only(args, ctx, w, stream, hpg, torch):
     """Launch one kernel class `steps` times on a seeded synthetic Newton state of
     the workload (no solve), for ncu captures and per-kernel timing."""
@@ -214,6 +262,9 @@ def main():
                     help="kernel-only mode (profiling): synthetic state, `--steps` launches of one kernel class")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--batch", type=int, default=8, help="independent solves in flight per step")
+    ap.add_argument("--serve-requests", type=int, default=128,
+                    help="requests of the serving workload (0 = skip; 512 = the full stream)")
+    ap.add_argument("--serve-fp64", action="store_true", help="also serve with the FP64 path")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -392,6 +443,21 @@ def main():
         fp64_fdm = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                     "avg_launch_us": avg_ms * 1000.0, "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz"}
 
+    serving = None
+    if args.serve_requests > 0 and world == 1:
+        serving = {"requests": args.serve_requests, "workers": B,
+                   "workload": "seeded 2D obstacle requests (0,1)^2, f~U[1,50], phi=0.3+1..4 Gaussian bumps, "
+                               "m in 4..32, p in 2..10"}
+        for pname, prec in [("mixed", hpg.HPG_MIXED)] + ([("fp64", hpg.HPG_FP64)] if args.serve_fp64 else []):
+            thr, p50, p99, nmean, mk, nf = serve_requests(ctx, hpg, W, prec, args.serve_requests, None, B)
+            runs = {"saturated": {"solves_per_s": thr, "p50_ms": p50, "p99_ms": p99, "mean_newton": nmean,
+                                  "failed": nf}}
+            for f in (0.5, 0.9, 1.5):
+                t2, q50, q99, _, _, nf2 = serve_requests(ctx, hpg, W, prec, args.serve_requests, f * thr, B)
+                runs[f"poisson_{f}x"] = {"rate": f * thr, "solves_per_s": t2, "p50_ms": q50, "p99_ms": q99,
+                                         "failed": nf2}
+            serving[pname] = runs
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample()
@@ -426,7 +492,7 @@ def main():
                 "e2e": head["e2e"], "gpu_launches": int(head["launches"] * args.steps),
                 "roofline": roof, "newton_apply_roofline": newton_roof,
                 "kernel_avg_us": {k: v[0] * 1000.0 for k, v in kt.items()},
-                "clocks": clocks, "cpu_baseline": cpu}
+                "serving": serving, "clocks": clocks, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

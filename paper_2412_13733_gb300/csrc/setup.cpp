@@ -3,6 +3,9 @@
 // pencil, the constant part of the S-hat cell blocks (Section 4.5), data loads
 // and the Dirichlet lifting.  Everything here runs once per problem.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
@@ -194,7 +197,26 @@ static double yab_ref(int a, int b) {
     return 0.0;
 }
 
+static void build_dir1d_uncached(Dir1D& D, int m, int p, int n, double lo, double hi);
+
+// The 1D operators (and their fast-diagonalisation eigenpairs, the costly part)
+// depend only on (m, p, n, lo, hi); many problems share them, so keep a cache.
 void build_dir1d(Dir1D& D, int m, int p, int n, double lo, double hi) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, double, double>, Dir1D> cache;
+    const auto key = std::make_tuple(m, p, n, lo, hi);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) { D = it->second; return; }
+    }
+    build_dir1d_uncached(D, m, p, n, lo, hi);
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache.size() > 512) cache.clear();
+    cache.emplace(key, D);
+}
+
+static void build_dir1d_uncached(Dir1D& D, int m, int p, int n, double lo, double hi) {
     D.m = m; D.p = p; D.n = n;
     D.N1 = m * p + 1;
     D.n1 = m * p - 1;
