@@ -265,6 +265,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests of the serving workload (0 = skip; 512 = the full stream)")
     ap.add_argument("--serve-fp64", action="store_true", help="also serve with the FP64 path")
+    ap.add_argument("--no-others", action="store_true", help="skip the 4x4, 3D and torsion workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -443,6 +444,32 @@ def main():
         fp64_fdm = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                     "avg_launch_us": avg_ms * 1000.0, "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz"}
 
+    # the other configured workloads: single-solve latency and solves/s, both paths
+    others = {}
+    if not args.no_others:
+        for wname in ("radial4", "sine3d", "torsion"):
+            wo = W.workload(wname)
+            entry = {}
+            for pname, prec in (("mixed", hpg.HPG_MIXED), ("fp64", hpg.HPG_FP64)):
+                P = hpg.from_workload(ctx, wo, hpg.default_params(precision=prec))
+                P.solve()                                   # warm-up (set-up, graph capture)
+                ts = []
+                for _ in range(max(1, min(args.steps, 3))):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    P.solve()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                st = P.stats()
+                entry[pname] = {"solves_per_s": 1000.0 / statistics.median(ts), "latency_ms": statistics.median(ts),
+                                "newton": st["newton_total"], "krylov": st["krylov_total"],
+                                "n_u": P.n_u, "n_psi": P.n_psi}
+                P.free()
+            others[wname] = entry
+
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = {"requests": args.serve_requests, "workers": B,
@@ -492,7 +519,7 @@ def main():
                 "e2e": head["e2e"], "gpu_launches": int(head["launches"] * args.steps),
                 "roofline": roof, "newton_apply_roofline": newton_roof,
                 "kernel_avg_us": {k: v[0] * 1000.0 for k, v in kt.items()},
-                "serving": serving, "clocks": clocks, "cpu_baseline": cpu}
+                "other_workloads": others, "serving": serving, "clocks": clocks, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

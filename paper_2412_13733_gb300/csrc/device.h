@@ -69,6 +69,7 @@ cudaError_t launch_residual(const Geo<double>& g, const double* u, const double*
                             const double* eg, const double* rA, const double* rB, const double* bf,
                             const double* phiz, double alpha, double* F, double* part, cudaStream_t s);
 int n_res_partials(const Geo<double>& g);
+int n_res_partials_for(int d, const int* n1, long long Npsi);
 
 // Deterministic reduction of `count` partials into out[0] (one block).
 cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaStream_t s);
@@ -108,7 +109,8 @@ cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T
 
 // FP64 matrix-free Newton apply y = G x (eq. pG-matrix) split in two kernels.
 cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
-                                const double* x, double* y, cudaStream_t s);
+                                const double* x, double* y, cudaStream_t s, cudaStream_t s2 = nullptr,
+                                cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 
 // y = A x (interior), FP64 (used by tests of the stiffness inverse).
 cudaError_t launch_aapply(const Geo<double>& g, const double* x, double* y, cudaStream_t s);

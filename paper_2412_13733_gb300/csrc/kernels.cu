@@ -3,6 +3,7 @@
 // matrix-free Newton and Schur operators by sum factorisation and sparse
 // Kronecker stencils, the S-hat cell-block factorisation, the fast-diagonalisation
 // inverse of A_alpha, and GMRES.
+#include <algorithm>
 #include <atomic>
 #include <cfloat>
 #include <cmath>
@@ -163,8 +164,9 @@ __device__ __forceinline__ void cell_multi(const Geo<T>& g, long long c, int* cm
 // out[.., a, ..] = sum_k M(a, k) in[.., k, ..] with M(a,k) = mat[a*n+k] (or mat[k*n+a] if transp)
 template <typename T>
 __device__ __forceinline__ void sf_pass(const T* in, T* out, const T* mat, bool transp, int n, int nloc, int cnt,
-                                        int stride) {
-    for (int i = threadIdx.x; i < nloc * cnt; i += blockDim.x) {
+                                        int stride, int lt = -1, int nthr = 0) {
+    if (lt < 0) { lt = threadIdx.x; nthr = blockDim.x; }
+    for (int i = lt; i < nloc * cnt; i += nthr) {
         const int t = i / nloc, li = i - t * nloc;
         const int a = (li / stride) % n;
         const int base = t * nloc + li - a * stride;
@@ -180,6 +182,188 @@ __device__ __forceinline__ void sf_pass(const T* in, T* out, const T* mat, bool 
 }  // namespace
 
 long long kernel_launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// ============================================================ tiled u-row applies
+// y[i] over interior u-dofs i of  cA * (A x)[i] + cB * (B z)[i]  (+ residual terms),
+// with A = sum_k (x)_j (j == k ? A_j : M_j) and B = (x)_j B_j (gradient: component
+// c uses the derivative Gram Bd_c along axis c).  Each block owns a tile of the
+// tensor grid and first stages the 1D stencil rows of its tile ranges in shared
+// memory, so every term of the gather costs one independent global load.
+template <int D>
+struct UTile;
+template <>
+struct UTile<2> { static constexpr int T0 = 32, T1 = 8, T2 = 1; };
+template <>
+struct UTile<3> { static constexpr int T0 = 8, T1 = 8, T2 = 4; };
+
+enum { OP_A = 0, OP_M = 1, OP_B = 2, OP_BD = 3, NOPS = 4 };
+
+template <typename T, int TMAX>
+struct StenTile {
+    int cnt[NOPS][kMaxDim][TMAX];
+    int col[NOPS][kMaxDim][TMAX][kEll];
+    T val[NOPS][kMaxDim][TMAX][kEll];
+};
+
+template <typename T>
+__device__ __forceinline__ const Sten<T>& op_of(const Geo<T>& g, int op, int j) {
+    return op == OP_A ? g.A[j] : (op == OP_M ? g.M[j] : (op == OP_B ? g.B[j] : g.Bd[j]));
+}
+
+template <int D>
+struct UTileMax {
+    static constexpr int T0 = UTile<D>::T0, T1 = UTile<D>::T1, T2 = UTile<D>::T2;
+    static constexpr int v = T0 > T1 ? (T0 > T2 ? T0 : T2) : (T1 > T2 ? T1 : T2);
+};
+
+// Body of the tiled u-row apply for the tile with linear index `blin`
+// (x-tiles fastest); `stp` points to the block's shared StenTile.
+template <int D, typename T, typename Tx, typename Tz, bool HAS_A, bool HAS_B, bool RESID>
+__device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __restrict__ x, T cB,
+                                            const Tz* __restrict__ z, const Tz* __restrict__ z2,
+                                            const double* __restrict__ rA, const double* __restrict__ bf,
+                                            double* __restrict__ yres, double* __restrict__ part,
+                                            Tx* __restrict__ y, int blin, void* stp) {
+    constexpr int T0 = UTile<D>::T0, T1 = UTile<D>::T1, T2 = UTile<D>::T2;
+    constexpr int TMAX = UTileMax<D>::v;
+    StenTile<T, TMAX>& st = *reinterpret_cast<StenTile<T, TMAX>*>(stp);
+    __shared__ double sh[32];
+    const int tile[kMaxDim] = {T0, T1, T2};
+    const int gx = (g.n1[0] + T0 - 1) / T0, gy = (g.n1[1] + T1 - 1) / T1;
+    const int org[kMaxDim] = {(blin % gx) * T0, ((blin / gx) % gy) * T1, (blin / (gx * gy)) * T2};
+    const bool grad = g.kind == HPG_GRADIENT;
+    // stage the stencil rows of this tile
+    for (int op = 0; op < NOPS; ++op) {
+        if ((op == OP_A || op == OP_M) && !HAS_A) continue;
+        if (op == OP_B && !HAS_B) continue;
+        if (op == OP_BD && !(HAS_B && grad)) continue;
+        for (int j = 0; j < D; ++j) {
+            const Sten<T>& S = op_of(g, op, j);
+            for (int e = threadIdx.x; e < tile[j] * kEll; e += blockDim.x) {
+                const int l = e / kEll, k = e % kEll, r = org[j] + l;
+                if (r < g.n1[j]) {
+                    st.col[op][j][l][k] = S.col[(size_t)r * kEll + k];
+                    st.val[op][j][l][k] = S.val[(size_t)r * kEll + k];
+                    if (k == 0) st.cnt[op][j][l] = S.cnt[r];
+                } else if (k == 0) {
+                    st.cnt[op][j][l] = 0;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int l0 = threadIdx.x % T0, l1 = (threadIdx.x / T0) % T1, l2 = threadIdx.x / (T0 * T1);
+    const int r0 = org[0] + l0, r1 = org[1] + l1, r2 = (D == 3) ? org[2] + l2 : 0;
+    const bool inside = r0 < g.n1[0] && r1 < g.n1[1] && (D == 2 || r2 < g.n1[2]);
+    const int n1x = g.n1[0], n1y = g.n1[1];
+    double v = 0.0;
+    long long i = 0;
+    if (inside) {
+        i = r0 + (long long)n1x * (r1 + (long long)n1y * r2);
+        T acc = T(0);
+        if (HAS_A) {
+            T sa = T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const int o0 = (k == 0) ? OP_A : OP_M, o1 = (k == 1) ? OP_A : OP_M, o2 = (k == 2) ? OP_A : OP_M;
+                const int c0 = st.cnt[o0][0][l0], c1 = st.cnt[o1][1][l1];
+                if (D == 2) {
+                    for (int e1 = 0; e1 < c1; ++e1) {
+                        const long long base = (long long)st.col[o1][1][l1][e1] * n1x;
+                        T t = T(0);
+                        for (int e0 = 0; e0 < c0; ++e0) t += st.val[o0][0][l0][e0] * (T)x[base + st.col[o0][0][l0][e0]];
+                        sa += st.val[o1][1][l1][e1] * t;
+                    }
+                } else {
+                    const int c2 = st.cnt[o2][2][l2];
+                    for (int e2 = 0; e2 < c2; ++e2) {
+                        const long long b2 = (long long)st.col[o2][2][l2][e2] * n1y;
+                        T t2 = T(0);
+                        for (int e1 = 0; e1 < c1; ++e1) {
+                            const long long base = (b2 + st.col[o1][1][l1][e1]) * n1x;
+                            T t = T(0);
+                            for (int e0 = 0; e0 < c0; ++e0) t += st.val[o0][0][l0][e0] * (T)x[base + st.col[o0][0][l0][e0]];
+                            t2 += st.val[o1][1][l1][e1] * t;
+                        }
+                        sa += st.val[o2][2][l2][e2] * t2;
+                    }
+                }
+            }
+            acc += cA * sa;
+        }
+        if (HAS_B) {
+            T sb = T(0);
+            const int n = g.n;
+            for (int comp = 0; comp < g.ncomp; ++comp) {
+                const int o0 = (grad && comp == 0) ? OP_BD : OP_B, o1 = (grad && comp == 1) ? OP_BD : OP_B,
+                          o2 = (grad && comp == 2) ? OP_BD : OP_B;
+                const int c0 = st.cnt[o0][0][l0], c1 = st.cnt[o1][1][l1];
+                const int c2 = (D == 3) ? st.cnt[o2][2][l2] : 1;
+                for (int e2 = 0; e2 < c2; ++e2) {
+                    int cz = 0, kz = 0;
+                    T vz = T(1);
+                    if (D == 3) {
+                        const int p2 = st.col[o2][2][l2][e2];
+                        cz = p2 >> 8; kz = p2 & 255; vz = st.val[o2][2][l2][e2];
+                    }
+                    T t2 = T(0);
+                    for (int e1 = 0; e1 < c1; ++e1) {
+                        const int p1 = st.col[o1][1][l1][e1];
+                        const int cy = p1 >> 8, ky = p1 & 255;
+                        T t = T(0);
+                        for (int e0 = 0; e0 < c0; ++e0) {
+                            const int p0 = st.col[o0][0][l0][e0];
+                            const int cx = p0 >> 8, kx = p0 & 255;
+                            const long long cell = cx + (long long)g.m[0] * (cy + (long long)g.m[1] * cz);
+                            const long long idx = (cell * g.ncomp + comp) * g.nloc + kx + n * (ky + n * kz);
+                            T zv = (T)z[idx];
+                            if (z2) zv -= (T)z2[idx];
+                            t += st.val[o0][0][l0][e0] * zv;
+                        }
+                        t2 += st.val[o1][1][l1][e1] * t;
+                    }
+                    sb += vz * t2;
+                }
+            }
+            acc += cB * sb;
+        }
+        if (RESID) {
+            const double r = (double)acc + (double)cA * (rA[i] - bf[i]);
+            yres[i] = r;
+            v = r * r;
+        } else {
+            y[i] = (Tx)acc;
+        }
+    }
+    if (RESID) {
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) part[blin] = v;
+    }
+}
+
+template <int D, typename T, typename Tx, typename Tz, bool HAS_A, bool HAS_B, bool RESID>
+__global__ void __launch_bounds__(256)
+    k_urow(Geo<T> g, T cA, const Tx* __restrict__ x, T cB, const Tz* __restrict__ z, const Tz* __restrict__ z2,
+           const double* __restrict__ rA, const double* __restrict__ bf, double* __restrict__ yres,
+           double* __restrict__ part, Tx* __restrict__ y, const int* skip) {
+    __shared__ StenTile<T, UTileMax<D>::v> st;
+    if (skip && *skip) return;
+    const int blin = (int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+    k_urow_body<D, T, Tx, Tz, HAS_A, HAS_B, RESID>(g, cA, x, cB, z, z2, rA, bf, yres, part, y, blin, &st);
+}
+
+template <int D>
+static dim3 utile_grid(const int* n1) {
+    return dim3((n1[0] + UTile<D>::T0 - 1) / UTile<D>::T0, (n1[1] + UTile<D>::T1 - 1) / UTile<D>::T1,
+                D == 3 ? (n1[2] + UTile<D>::T2 - 1) / UTile<D>::T2 : 1);
+}
+
+static long long utile_blocks(int d, const int* n1) {
+    const dim3 gr = d == 2 ? utile_grid<2>(n1) : utile_grid<3>(n1);
+    return (long long)gr.x * gr.y * gr.z;
+}
+
+
 void add_kernel_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ====================================================================== eval
@@ -339,20 +523,26 @@ __global__ void k_residual_psi(Geo<double> g, const double* __restrict__ u, cons
 }
 
 int n_res_partials(const Geo<double>& g) {
-    return (int)((g.Nu0 + 255) / 256 + (g.Npsi + 255) / 256);
+    return (int)(utile_blocks(g.d, g.n1) + (g.Npsi + 255) / 256);
+}
+
+int n_res_partials_for(int d, const int* n1, long long Npsi) {
+    return (int)(utile_blocks(d, n1) + (Npsi + 255) / 256);
 }
 
 cudaError_t launch_residual(const Geo<double>& g, const double* u, const double* psi, const double* psi_prev,
                             const double* eg, const double* rA, const double* rB, const double* bf,
                             const double* phiz, double alpha, double* F, double* part, cudaStream_t s) {
-    const int bu = (int)((g.Nu0 + 255) / 256), bp = (int)((g.Npsi + 255) / 256);
+    const int bu = (int)utile_blocks(g.d, g.n1), bp = (int)((g.Npsi + 255) / 256);
     if (g.d == 2) {
-        k_residual_u<2><<<bu, 256, 0, s>>>(g, u, psi, psi_prev, rA, bf, alpha, F, part);
+        k_urow<2, double, double, double, true, true, true><<<utile_grid<2>(g.n1), 256, 0, s>>>(
+            g, alpha, u, 1.0, psi, psi_prev, rA, bf, F, part, nullptr, nullptr);
         note_launch();
         k_residual_psi<2><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
         note_launch();
     } else {
-        k_residual_u<3><<<bu, 256, 0, s>>>(g, u, psi, psi_prev, rA, bf, alpha, F, part);
+        k_urow<3, double, double, double, true, true, true><<<utile_grid<3>(g.n1), 256, 0, s>>>(
+            g, alpha, u, 1.0, psi, psi_prev, rA, bf, F, part, nullptr, nullptr);
         note_launch();
         k_residual_psi<3><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
         note_launch();
@@ -580,9 +770,12 @@ __global__ void k_bapply(Geo<T> g, const Tin* __restrict__ z, Tout* __restrict__
 
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s, const int* skip) {
-    const unsigned b = (unsigned)((g.Nu0 + 255) / 256);
-    if (g.d == 2) k_bapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y, skip);
-    else k_bapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, z, y, skip);
+    if (g.d == 2)
+        k_urow<2, T, Tout, Tin, false, true, false><<<utile_grid<2>(g.n1), 256, 0, s>>>(
+            g, T(0), (const Tout*)nullptr, T(1), z, (const Tin*)nullptr, nullptr, nullptr, nullptr, nullptr, y, skip);
+    else
+        k_urow<3, T, Tout, Tin, false, true, false><<<utile_grid<3>(g.n1), 256, 0, s>>>(
+            g, T(0), (const Tout*)nullptr, T(1), z, (const Tin*)nullptr, nullptr, nullptr, nullptr, nullptr, y, skip);
     note_launch();
     return cudaGetLastError();
 }
@@ -620,9 +813,12 @@ __global__ void k_aapply(Geo<double> g, const double* __restrict__ x, double* __
 }
 
 cudaError_t launch_aapply(const Geo<double>& g, const double* x, double* y, cudaStream_t s) {
-    const unsigned b = (unsigned)((g.Nu0 + 255) / 256);
-    if (g.d == 2) k_aapply<2><<<b, 256, 0, s>>>(g, x, y);
-    else k_aapply<3><<<b, 256, 0, s>>>(g, x, y);
+    if (g.d == 2)
+        k_urow<2, double, double, double, true, false, false><<<utile_grid<2>(g.n1), 256, 0, s>>>(
+            g, 1.0, x, 0.0, (const double*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, y, nullptr);
+    else
+        k_urow<3, double, double, double, true, false, false><<<utile_grid<3>(g.n1), 256, 0, s>>>(
+            g, 1.0, x, 0.0, (const double*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, y, nullptr);
     note_launch();
     return cudaGetLastError();
 }
@@ -660,16 +856,19 @@ __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem, bool valid
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
 
-// CTA tile BM x BN, TM x TN outputs per thread.  Panels are staged in
-// shared memory as [k][m] and [k][n] (the inner index contiguous), walked so
-// that consecutive threads write consecutive shared words (no bank conflicts);
-// when the global operand is transposed the L1 line is reused across k.
-template <typename T, int BM, int BN, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+// CTA tile BM x BN, TM x TN outputs per thread, KS warp groups splitting K.
+// Panels are staged in shared memory as [k][m] and [k][n] (the inner index
+// contiguous), walked so that consecutive threads write consecutive shared
+// words (no bank conflicts); when the global operand is transposed the L1 line
+// is reused across k.  Each of the KS groups runs a contiguous K range; the
+// partial tiles are summed in group order (deterministic) before the epilogue.
+template <typename T, int BM, int BN, int TM, int TN, int KS>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
     k_gemm_fullk(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp,
                  FdmScale sc, const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2,
                  const int* skip) {
-    constexpr int NT = (BM / TM) * (BN / TN);
+    constexpr int NG = (BM / TM) * (BN / TN);     // threads per group
+    constexpr int NT = NG * KS;
     extern __shared__ __align__(16) unsigned char smraw[];
     if (skip && *skip) return;
     T* As = reinterpret_cast<T*>(smraw);          // [K][BM]
@@ -693,7 +892,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     }
     cp_async_wait_all();
     __syncthreads();
-    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int grp = tid / NG, gt = tid % NG;
+    const int tx = gt % (BN / TN), ty = gt / (BN / TN);
+    const int kchunk = (K + KS - 1) / KS;
+    const int kb = grp * kchunk, ke = (kb + kchunk < K) ? kb + kchunk : K;
     T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -701,8 +903,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         for (int jj = 0; jj < TN; ++jj) acc[i][jj] = T(0);
     const T* ap = As + ty * TM;
     const T* bp = Bs + tx * TN;
-#pragma unroll 8
-    for (int k = 0; k < K; ++k) {
+#pragma unroll 4
+    for (int k = kb; k < ke; ++k) {
         T av[TM], bv[TN];
         // vector shared loads (the panel rows are 16-byte aligned)
         if (sizeof(T) == 4 && TM == 4 && TN == 2) {
@@ -725,6 +927,23 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         for (int i = 0; i < TM; ++i)
 #pragma unroll
             for (int jj = 0; jj < TN; ++jj) acc[i][jj] += av[i] * bv[jj];
+    }
+    if (KS > 1) {
+        // deterministic reduction of the group partials through shared memory
+        __syncthreads();
+        T* red = As;                               // (KS-1) x NG x TM*TN, reuses the panels
+        if (grp > 0)
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int jj = 0; jj < TN; ++jj) red[((size_t)(grp - 1) * NG + gt) * (TM * TN) + i * TN + jj] = acc[i][jj];
+        __syncthreads();
+        if (grp > 0) return;
+        for (int g2 = 1; g2 < KS; ++g2)
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int jj = 0; jj < TN; ++jj) acc[i][jj] += red[((size_t)(g2 - 1) * NG + gt) * (TM * TN) + i * TN + jj];
     }
     T ainv = T(1);
     if (sc.on) ainv = (T)(1.0 / (sc.alpha_dev ? *sc.alpha_dev : sc.alpha_host));
@@ -833,9 +1052,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 template <typename T>
 struct GemmTile;
 template <>
-struct GemmTile<float> { static constexpr int BM = 32, BN = 32, TM = 4, TN = 2; };
+struct GemmTile<float> { static constexpr int BM = 32, BN = 16, TM = 4, TN = 2, KS = 4; };
 template <>
-struct GemmTile<double> { static constexpr int BM = 16, BN = 16, TM = 2, TN = 2; };
+struct GemmTile<double> { static constexpr int BM = 16, BN = 16, TM = 2, TN = 2, KS = 1; };
 
 template <typename T>
 static size_t gemm_fullk_smem(int K) {
@@ -848,11 +1067,15 @@ static cudaError_t gemm(const GemmArgs& a, const T* A, const T* B, T* C, const F
     const T* l0 = g.lam[0];
     const T* l1 = g.d > 1 ? g.lam[1] : g.lam[0];
     const T* l2 = g.d > 2 ? g.lam[2] : g.lam[0];
-    const size_t smem = gemm_fullk_smem<T>(a.K);
     constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN, TM = GemmTile<T>::TM, TN = GemmTile<T>::TN;
+    constexpr int KS = GemmTile<T>::KS;
+    // shared memory: the two panels, and at least the split-K reduction buffer that reuses them
+    const size_t red = (size_t)(KS - 1) * (BM / TM) * (BN / TN) * TM * TN * sizeof(T);
+    const size_t smem = std::max(gemm_fullk_smem<T>(a.K), red);
     if (smem <= 200 * 1024) {
         dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch);
-        k_gemm_fullk<T, BM, BN, TM, TN><<<grid, (BM / TM) * (BN / TN), smem, s>>>(a, A, B, C, sc, l0, l1, l2, skip);
+        k_gemm_fullk<T, BM, BN, TM, TN, KS><<<grid, (BM / TM) * (BN / TN) * KS, smem, s>>>(a, A, B, C, sc, l0, l1, l2,
+                                                                                        skip);
     } else {
         constexpr int BK = 16;
         dim3 grid((a.N + 31) / 32, (a.M + 31) / 32, a.batch);
@@ -920,63 +1143,65 @@ cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, c
 }
 
 // ========================================================== D apply per cell
-// out = sB * (B^T t) + sD * (D z + E z), per cell.  D z by sum factorisation:
-// z -> Gauss values (V along each axis) -> times gw (or the 2x2/3x3 Jacobian) -> V^T back.
+// out = sB * (B^T t) + sD * (D z + E z) for one cell, by a group of `nthr`
+// threads (local id lt) with shared scratch `sm` of 3 nb + n^2 elements.  D z by
+// sum factorisation: z -> Gauss values (V along each axis) -> times gw (or the
+// 2x2/3x3 Jacobian) -> V^T back.  Every thread of the block must call this the
+// same number of times (it contains block-wide barriers).
 template <int D, typename T, typename Tz, typename Tt, typename Tout>
-__global__ void k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* __restrict__ z,
-                         const Tt* __restrict__ t, T sB, T sD, Tout* __restrict__ out, IterCtl ctl) {
-    extern __shared__ unsigned char smraw[];
-    if (ctl.skip && *ctl.skip) return;
-    T* sm = reinterpret_cast<T*>(smraw);
+__device__ __forceinline__ void cellop_body(const Geo<T>& g, const T* __restrict__ gw, T beta, const Tz* __restrict__ z,
+                                            const Tt* __restrict__ t, T sB, T sD, Tout* __restrict__ outp,
+                                            long long cell, bool active, int lt, int nthr, T* sm) {
     const int n = g.n, nloc = (int)g.nloc, nc = g.ncomp, nb = (int)g.nb;
     T* a = sm;
     T* b = sm + nb;
     T* zc = sm + 2 * nb;
     T* Vq = sm + 3 * nb;
-    Tout* outp = out + (ctl.jptr ? (long long)(*ctl.jptr + 1) * ctl.jstride : 0LL);
-    const long long cell = blockIdx.x;
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Vq[i] = g.Vq[i];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) { const T v = (T)z[cell * nb + i]; a[i] = v; zc[i] = v; }
+    for (int i = lt; i < n * n; i += nthr) Vq[i] = g.Vq[i];
+    if (active)
+        for (int i = lt; i < nb; i += nthr) { const T v = (T)z[cell * nb + i]; a[i] = v; zc[i] = v; }
     __syncthreads();
     T *in = a, *o = b;
     int stride = 1;
     for (int ax = 0; ax < D; ++ax) {
-        sf_pass(in, o, Vq, false, n, nloc, nc, stride);
+        if (active) sf_pass(in, o, Vq, false, n, nloc, nc, stride, lt, nthr);
         __syncthreads();
         T* tt = in; in = o; o = tt;
         stride *= n;
     }
     const int gs = (g.kind == HPG_GRADIENT) ? D * (D + 1) / 2 : 1;
-    for (int q = threadIdx.x; q < nloc; q += blockDim.x) {
-        const long long gq = cell * nloc + q;
-        if (nc == 1) {
-            o[q] = gw[gq] * in[q];
-        } else {
-            T zq[kMaxDim];
-            for (int k = 0; k < nc; ++k) zq[k] = in[k * nloc + q];
-            for (int k = 0; k < nc; ++k) {
-                T s = T(0);
-                for (int l = 0; l < nc; ++l) {
-                    const int lo = k < l ? k : l, hi = k < l ? l : k;
-                    const int e = lo * nc - lo * (lo - 1) / 2 + (hi - lo);
-                    s += gw[gq * gs + e] * zq[l];
+    if (active)
+        for (int q = lt; q < nloc; q += nthr) {
+            const long long gq = cell * nloc + q;
+            if (nc == 1) {
+                o[q] = gw[gq] * in[q];
+            } else {
+                T zq[kMaxDim];
+                for (int k = 0; k < nc; ++k) zq[k] = in[k * nloc + q];
+                for (int k = 0; k < nc; ++k) {
+                    T sacc = T(0);
+                    for (int l = 0; l < nc; ++l) {
+                        const int lo = k < l ? k : l, hi = k < l ? l : k;
+                        const int e = lo * nc - lo * (lo - 1) / 2 + (hi - lo);
+                        sacc += gw[gq * gs + e] * zq[l];
+                    }
+                    o[k * nloc + q] = sacc;
                 }
-                o[k * nloc + q] = s;
             }
         }
-    }
     __syncthreads();
     { T* tt = in; in = o; o = tt; }
     stride = 1;
     for (int ax = 0; ax < D; ++ax) {
-        sf_pass(in, o, Vq, true, n, nloc, nc, stride);
+        if (active) sf_pass(in, o, Vq, true, n, nloc, nc, stride, lt, nthr);
         __syncthreads();
         T* tt = in; in = o; o = tt;
         stride *= n;
     }
+    if (!active) return;
     int cm[kMaxDim];
     cell_multi(g, cell, cm);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    for (int i = lt; i < nb; i += nthr) {
         const int comp = i / nloc, li = i - comp * nloc;
         T ez;
         if (nc == 1) {
@@ -995,6 +1220,38 @@ __global__ void k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* _
         }
         outp[cell * nb + i] = (Tout)acc;
     }
+}
+
+template <int D, typename T, typename Tz, typename Tt, typename Tout>
+__global__ void k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* __restrict__ z,
+                         const Tt* __restrict__ t, T sB, T sD, Tout* __restrict__ out, IterCtl ctl) {
+    extern __shared__ unsigned char smraw[];
+    if (ctl.skip && *ctl.skip) return;
+    Tout* outp = out + (ctl.jptr ? (long long)(*ctl.jptr + 1) * ctl.jstride : 0LL);
+    cellop_body<D, T, Tz, Tt, Tout>(g, gw, beta, z, t, sB, sD, outp, blockIdx.x, true, threadIdx.x, blockDim.x,
+                                    reinterpret_cast<T*>(smraw));
+}
+
+// One launch for G x: blocks [0, nu) are u-row tiles (alpha A x_u + B x_psi),
+// the rest apply the psi rows B^T x_u - (D + E) x_psi to `cpb` cells each
+// (groups of 256 / cpb threads), so both FP64 workloads share the SMs.
+template <int D>
+__global__ void __launch_bounds__(256)
+    k_newton_fused(Geo<double> g, const double* __restrict__ gw, double alpha, double beta,
+                   const double* __restrict__ x, double* __restrict__ y, int nu, int cpb) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if ((int)blockIdx.x < nu) {
+        // u rows: reuse the tiled row kernel body through a grid-index remap
+        k_urow_body<D, double, double, double, true, true, false>(
+            g, alpha, x, 1.0, x + g.Nu0, nullptr, nullptr, nullptr, nullptr, nullptr, y, (int)blockIdx.x, smraw);
+        return;
+    }
+    const int grp = threadIdx.x / (256 / cpb), lt = threadIdx.x % (256 / cpb);
+    const long long cell = (long long)(blockIdx.x - nu) * cpb + grp;
+    const size_t per = (size_t)(3 * g.nb + g.n * g.n);
+    cellop_body<D, double, double, double, double>(g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0, cell,
+                                                   cell < g.Nc, lt, 256 / cpb,
+                                                   reinterpret_cast<double*>(smraw) + grp * per);
 }
 
 template <typename T, typename Tout>
@@ -1021,24 +1278,18 @@ __global__ void k_newton_u(Geo<double> g, double alpha, const double* __restrict
     yu[i] = alpha * apply_A_row<D, double, double>(g, r, xu) + apply_B_row<D, double, double>(g, r, xp, nullptr);
 }
 
+// G x (eq. pG-matrix) in one launch: u-row tiles and psi cells share the SMs.
 cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
-                                const double* x, double* y, cudaStream_t s) {
-    const unsigned bu = (unsigned)((g.Nu0 + 255) / 256);
-    const size_t smem = (size_t)(3 * g.nb + g.n * g.n) * sizeof(double);
-    const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
-    if (g.d == 2) {
-        k_newton_u<2><<<bu, 256, 0, s>>>(g, alpha, x, x + g.Nu0, y);
-        note_launch();
-        k_cellop<2, double, double, double, double><<<(unsigned)g.Nc, threads, smem, s>>>(
-            g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0, IterCtl{});
-        note_launch();
-    } else {
-        k_newton_u<3><<<bu, 256, 0, s>>>(g, alpha, x, x + g.Nu0, y);
-        note_launch();
-        k_cellop<3, double, double, double, double><<<(unsigned)g.Nc, threads, smem, s>>>(
-            g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0, IterCtl{});
-        note_launch();
-    }
+                                const double* x, double* y, cudaStream_t s, cudaStream_t, cudaEvent_t, cudaEvent_t) {
+    const int nu = (int)utile_blocks(g.d, g.n1);
+    const int cpb = g.nb <= 64 ? 4 : 1;
+    const int nc = (int)((g.Nc + cpb - 1) / cpb);
+    const size_t per = (size_t)(3 * g.nb + g.n * g.n) * sizeof(double);
+    const size_t st = g.d == 2 ? sizeof(StenTile<double, UTileMax<2>::v>) : sizeof(StenTile<double, UTileMax<3>::v>);
+    const size_t smem = std::max(st, cpb * per);
+    if (g.d == 2) k_newton_fused<2><<<nu + nc, 256, smem, s>>>(g, gw, alpha, beta, x, y, nu, cpb);
+    else k_newton_fused<3><<<nu + nc, 256, smem, s>>>(g, gw, alpha, beta, x, y, nu, cpb);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1350,14 +1601,16 @@ cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s) {
 
 void configure_kernels() {
     cudaFuncSetAttribute(k_gemm_fullk<float, GemmTile<float>::BM, GemmTile<float>::BN, GemmTile<float>::TM,
-                                       GemmTile<float>::TN>,
+                                       GemmTile<float>::TN, GemmTile<float>::KS>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_gemm_fullk<double, GemmTile<double>::BM, GemmTile<double>::BN, GemmTile<double>::TM,
-                                       GemmTile<double>::TN>,
+                                       GemmTile<double>::TN, GemmTile<double>::KS>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_newton_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_newton_fused<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 // ============================================================ instantiations
