@@ -154,6 +154,8 @@ cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t 
 // After w (= S Shat^{-1} V_j) has been written into Vb[j+1]: CGS2 orthogonalise,
 // normalise, Givens update, convergence test, j += 1.  No-op once stopped.
 cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s);
+// Set the WHILE condition of a device-side GMRES loop to "not stopped".
+cudaError_t launch_gm_setcond(cudaGraphConditionalHandle h, const int* iflag, cudaStream_t s);
 // Solve H y = g for the completed iterations and form x = sum_i y_i V_i.
 cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s);
 // Opt-in shared-memory limits of the large-smem kernels (call once per device).

@@ -1558,6 +1558,17 @@ __global__ void k_gm_combine(const double* __restrict__ Vb, const double* __rest
     x[e] = s;
 }
 
+// Body terminator of the device-side GMRES loop: keep looping while not stopped.
+__global__ void k_gm_setcond(cudaGraphConditionalHandle h, const int* __restrict__ iflag) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, iflag[0] ? 0u : 1u);
+}
+
+cudaError_t launch_gm_setcond(cudaGraphConditionalHandle h, const int* iflag, cudaStream_t s) {
+    k_gm_setcond<<<1, 32, 0, s>>>(h, iflag);
+    note_launch();
+    return cudaGetLastError();
+}
+
 int gmres_dot_blocks(long long N) { return (int)((N + kDotChunk - 1) / kDotChunk); }
 int gmres_upd_blocks(long long N) { return (int)((N + 255) / 256); }
 

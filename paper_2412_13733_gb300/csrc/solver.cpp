@@ -506,10 +506,53 @@ static hpg_status gmres_chunk(hpg_ctx* ctx, Problem& P, int chunk) {
     return HPG_OK;
 }
 
-constexpr int kGraphChunk = 4;
+constexpr int kGraphChunk = 2;
 
-// Run GMRES to its stop flag: replay the captured chunk graph (or launch
-// eagerly when kernel timing is on), reading the flags once per chunk.
+// Build the device-side GMRES loop: one CUDA graph holding a conditional WHILE
+// node whose body is `kGraphChunk` iterations followed by a kernel that sets
+// the loop condition from the stop flag.  One launch runs GMRES to its stop
+// flag with no host round trip.  Returns false if the runtime lacks support.
+template <typename T>
+static bool build_gmres_loop(hpg_ctx* ctx, Problem& P, cudaGraphExec_t* exec, long long* kernels_per_body) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return false;
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return false;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return false;
+    }
+    const long long before = kernel_launch_count();
+    hpg_status st = gmres_chunk<T>(ctx, P, kGraphChunk);
+    if (st == HPG_OK && launch_gm_setcond(h, D.gm.iflag, s) != cudaSuccess) st = HPG_ERR_CUDA;
+    *kernels_per_body = kernel_launch_count() - before;
+    add_kernel_launches(-*kernels_per_body);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &captured);
+    bool ok = st == HPG_OK && ce == cudaSuccess && cudaGraphInstantiate(exec, g, 0) == cudaSuccess;
+    cudaGraphDestroy(g);
+    if (!ok) cudaGetLastError();
+    return ok;
+}
+
+// Run GMRES to its stop flag: one launch of the device-side loop graph (or
+// eager launches when kernel timing is on), then one read of the flags.
 template <typename T>
 static hpg_status gmres_run(hpg_ctx* ctx, Problem& P, int* its, bool* capped) {
     DevState& D = P.D;
@@ -517,29 +560,28 @@ static hpg_status gmres_run(hpg_ctx* ctx, Problem& P, int* its, bool* capped) {
     GmresDev& G = D.gm;
     const int pi = sizeof(T) == sizeof(float) ? 1 : 0;
     const bool use_graph = !P.timer.on;
-    if (use_graph && !D.gmres_graph[pi]) {
-        cudaGraph_t graph = nullptr;
-        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-        const long long before = kernel_launch_count();
-        hpg_status st = gmres_chunk<T>(ctx, P, kGraphChunk);
-        D.graph_kernels[pi] = kernel_launch_count() - before;
-        add_kernel_launches(-D.graph_kernels[pi]);   // captured, not executed
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        if (st != HPG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
-        CK(ce);
-        cudaError_t ie = cudaGraphInstantiate(&D.gmres_graph[pi], graph, 0);
-        cudaGraphDestroy(graph);
-        CK(ie);
-    }
-    for (int guard = 0; guard <= G.kmax; ++guard) {
-        if (use_graph) {
-            CK(cudaGraphLaunch(D.gmres_graph[pi], s));
-            add_kernel_launches(D.graph_kernels[pi]);
+    if (use_graph && !D.gmres_graph[pi] && !D.gmres_graph_failed[pi]) {
+        long long nk = 0;
+        if (!build_gmres_loop<T>(ctx, P, &D.gmres_graph[pi], &nk)) {
+            D.gmres_graph[pi] = nullptr;
+            D.gmres_graph_failed[pi] = true;
+        } else {
+            D.graph_kernels[pi] = nk;
         }
-        else CKS(gmres_chunk<T>(ctx, P, 1));
+    }
+    if (use_graph && D.gmres_graph[pi]) {
+        CK(cudaGraphLaunch(D.gmres_graph[pi], s));
         CK(cudaMemcpyAsync(D.h_iflag + 4, G.iflag, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (D.h_iflag[4]) break;
+        // kernels executed: one body per kGraphChunk iterations (rounded up)
+        add_kernel_launches(D.graph_kernels[pi] * ((D.h_iflag[5] + kGraphChunk - 1) / kGraphChunk + 1));
+    } else {
+        for (int guard = 0; guard <= G.kmax; ++guard) {
+            CKS(gmres_chunk<T>(ctx, P, 1));
+            CK(cudaMemcpyAsync(D.h_iflag + 4, G.iflag, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (D.h_iflag[4]) break;
+        }
     }
     *its = D.h_iflag[5];
     *capped = D.h_iflag[7] != 0 && D.h_iflag[4] != 0 && D.h_iflag[6] == 0;

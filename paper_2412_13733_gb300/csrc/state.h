@@ -42,7 +42,8 @@ struct DevState {
     cudaStream_t aux = nullptr;                  // helper stream for concurrent halves of G x
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gmres_graph[2] = {nullptr, nullptr};   // captured GMRES chunk per precision
-    long long graph_kernels[2] = {0, 0};                    // kernels in each captured chunk
+    long long graph_kernels[2] = {0, 0};                    // kernels in one loop body
+    bool gmres_graph_failed[2] = {false, false};            // conditional graphs unsupported
     std::map<long long, std::pair<cudaGraphExec_t, long long>> bench_graphs;   // hpg_launch_kernel replays
     double *eg = nullptr, *egt = nullptr;
     double *F = nullptr, *Ft = nullptr, *delta = nullptr, *r = nullptr, *dcorr = nullptr;
