@@ -266,6 +266,8 @@ def main():
                     help="requests of the serving workload (0 = skip; 512 = the full stream)")
     ap.add_argument("--serve-fp64", action="store_true", help="also serve with the FP64 path")
     ap.add_argument("--no-others", action="store_true", help="skip the 4x4, 3D and torsion workloads")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="host-driven GMRES launches (profilers cannot trace conditional graph nodes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -322,7 +324,8 @@ def main():
     B = args.batch
 
     def make(prec, count):
-        ps = [hpg.from_workload(ctx, w, hpg.default_params(precision=prec)) for _ in range(count)]
+        ps = [hpg.from_workload(ctx, w, hpg.default_params(precision=prec, graphs=0 if args.no_graphs else 1))
+              for _ in range(count)]
         return ps
 
     def run_steps(ps, steps, e2e=False, host_phi=None):

@@ -100,6 +100,9 @@ typedef struct {
     int    ls_max;        /* line-search halvings; default 10                                 */
     int    refine_max;    /* HPG_MIXED: FP64 refinement sweeps per Newton system; default 8   */
     int    timing;        /* 1: record CUDA-event time per kernel class (hpg_get_kernel_times) */
+    int    graphs;        /* 1 (default): GMRES runs as a device-side loop in one CUDA graph;
+                             0: host-driven launches (for profilers that cannot trace
+                             conditional graph nodes)                                          */
 } hpg_params;
 
 #define HPG_MAX_ALPHA 128

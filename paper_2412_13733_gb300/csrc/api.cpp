@@ -66,6 +66,7 @@ void hpg_default_params(hpg_params* p) {
     p->ls_max = 10;
     p->refine_max = 8;
     p->timing = 0;
+    p->graphs = 1;
 }
 
 const char* hpg_status_str(hpg_status s) {

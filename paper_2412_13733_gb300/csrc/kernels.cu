@@ -1364,7 +1364,6 @@ cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts
 // CUDA graph and replayed.  Every kernel returns immediately once the
 // converged/stop flag (G.iflag[0]) is set.  Classical Gram--Schmidt with one
 // re-orthogonalisation (CGS2), FP64, fixed-order (deterministic) reductions.
-constexpr int kDotChunk = 512;
 
 __global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b, long long N,
                            const double* __restrict__ part, int nparts, double rtol, double* __restrict__ scal,
@@ -1394,102 +1393,114 @@ __global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b
     }
 }
 
-// partial dots of w = Vb[j+1] with Vb[0..j]; the last block reduces into h
-__global__ void k_gm_dots(const double* __restrict__ Vb, const int* __restrict__ jdev, long long N,
-                          double* __restrict__ part, int kmax, double* __restrict__ h, int h_in_H,
-                          unsigned int* __restrict__ counter, const int* __restrict__ iflag) {
+// ---- Arnoldi step (CGS2), four kernels, no atomics or fences on the data path:
+//   dots(pass 1):   partial h1_i = <V_i, w> per chunk           (grid: chunks x vector groups)
+//   update(pass 1): h1 = sum of partials; w1 = w - V h1; H(:,j) = h1
+//   dots(pass 2):   partial h2_i = <V_i, w1>, partial ||w1||^2
+//   update(pass 2): h2, ||w2||^2 = ||w1||^2 - ||h2||^2 (Pythagoras: V orthonormal),
+//                   V_{j+1} = (w1 - V h2)/||w2||; the last block to finish applies the
+//                   Givens rotations, tests convergence and advances j.
+// Partials are summed in chunk order (deterministic).
+constexpr int kDotChunk = 2048;
+constexpr int kDotWarps = 8;
+
+__global__ void __launch_bounds__(32 * kDotWarps)
+    k_gm_dots2(const double* __restrict__ Vb, const int* __restrict__ jdev, long long N, double* __restrict__ part,
+               int kmax, int with_norm, const int* __restrict__ iflag) {
     if (iflag[0]) return;
     const int j = *jdev;
-    const int nblk = gridDim.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i = blockIdx.y * kDotWarps + wid;          // vector handled by this warp
+    const int nvec = j + 1 + (with_norm ? 1 : 0);        // slot j+1 = ||w||^2
+    if (i >= nvec) return;
     const long long e0 = (long long)blockIdx.x * kDotChunk;
     const long long e1 = (e0 + kDotChunk < N) ? e0 + kDotChunk : N;
     const double* w = Vb + (long long)(j + 1) * N;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = wid; i <= j; i += nw) {
-        const double* vi = Vb + (long long)i * N;
-        double s = 0.0;
-        for (long long e = e0 + lane; e < e1; e += 32) s += vi[e] * w[e];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) part[(long long)blockIdx.x * (kmax + 1) + i] = s;
+    const double* vi = (i <= j) ? Vb + (long long)i * N : w;
+    double s0 = 0.0, s1 = 0.0;
+    long long e = e0 + lane;
+    for (; e + 32 < e1; e += 64) {
+        s0 += vi[e] * w[e];
+        s1 += vi[e + 32] * w[e + 32];
     }
-    __threadfence();
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(nblk - 1));
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double* hh = h_in_H ? h + (long long)j * (kmax + 1) : h;
-    for (int i = wid; i <= j; i += nw) {
-        double s = 0.0;
-        for (int bk = lane; bk < nblk; bk += 32) s += part[(long long)bk * (kmax + 1) + i];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) hh[i] = s;
-    }
-    if (threadIdx.x == 0) *counter = 0u;
+    if (e < e1) s0 += vi[e] * w[e];
+    double sacc = s0 + s1;
+    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+    if (lane == 0) part[(long long)blockIdx.x * (kmax + 2) + i] = sacc;
 }
 
-// w -= sum_i c_i V_i ; block partial sums of squares of the result
-__global__ void k_gm_update(double* __restrict__ Vb, const int* __restrict__ jdev, long long N,
-                            const double* __restrict__ c, int kmax, int c_in_H, double* __restrict__ part,
-                            const int* __restrict__ iflag) {
-    __shared__ double sh[32];
+// sum the chunk partials of vectors 0..nvec-1 into shared h[] (warp per vector)
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int nchunks, int kmax, int nvec,
+                                                double* h) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < nvec; i += nw) {
+        double sacc = 0.0;
+        for (int c = lane; c < nchunks; c += 32) sacc += part[(long long)c * (kmax + 2) + i];
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+        if (lane == 0) h[i] = sacc;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256)
+    k_gm_update1(double* __restrict__ Vb, const int* __restrict__ jdev, long long N, const double* __restrict__ part,
+                 int nchunks, int kmax, double* __restrict__ H, const int* __restrict__ iflag) {
+    __shared__ double h[kMaxKrylov + 2];
     if (iflag[0]) return;
     const int j = *jdev;
-    const double* cc = c_in_H ? c + (long long)j * (kmax + 1) : c;
-    double* w = Vb + (long long)(j + 1) * N;
+    reduce_partials(part, nchunks, kmax, j + 1, h);
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(long long)j * (kmax + 1) + i] = h[i];
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double ss = 0.0;
-    if (e < N) {
-        double v = w[e];
-        for (int i = 0; i <= j; ++i) v -= cc[i] * Vb[(long long)i * N + e];
-        w[e] = v;
-        ss = v * v;
-    }
-    ss = block_sum(ss, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = ss;
+    if (e >= N) return;
+    double* w = Vb + (long long)(j + 1) * N;
+    double v = w[e];
+    for (int i = 0; i <= j; ++i) v -= h[i] * Vb[(long long)i * N + e];
+    w[e] = v;
 }
 
-// normalise V_{j+1}; the last block to finish applies the Givens rotations,
-// tests convergence and advances j (all blocks have read j by then)
-__global__ void k_gm_finalize(double* __restrict__ Vb, const int* __restrict__ jdev_c, long long N,
-                              const double* __restrict__ part, double* __restrict__ H, double* __restrict__ cs,
-                              double* __restrict__ sn, double* __restrict__ gv, double* __restrict__ scal,
-                              int* __restrict__ iflag, int kmax, const double* __restrict__ h2,
-                              unsigned int* __restrict__ counter, int* __restrict__ jdev) {
-    __shared__ double sh[32];
+__global__ void __launch_bounds__(256)
+    k_gm_update2(double* __restrict__ Vb, const int* __restrict__ jdev_c, long long N, const double* __restrict__ part,
+                 int nchunks, int kmax, double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                 double* __restrict__ gv, double* __restrict__ scal, int* __restrict__ iflag,
+                 unsigned int* __restrict__ counter, int* __restrict__ jdev) {
+    __shared__ double h[kMaxKrylov + 2];
+    __shared__ double shn;
+    __shared__ bool last;
     if (iflag[0]) return;
     const int j = *jdev_c;
-    const int nblk = gridDim.x;
-    double v = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) v += part[i];
-    v = block_sum(v, sh);
-    __shared__ double hn;
-    if (threadIdx.x == 0) hn = sqrt(v);
+    reduce_partials(part, nchunks, kmax, j + 2, h);     // h2[0..j], ||w1||^2 in h[j+1]
+    if (threadIdx.x == 0) {
+        double q = 0.0;
+        for (int i = 0; i <= j; ++i) q += h[i] * h[i];
+        const double n2 = h[j + 1] - q;
+        shn = n2 > 0.0 ? sqrt(n2) : 0.0;
+    }
     __syncthreads();
-    const double hnv = hn;
-    double* w = Vb + (long long)(j + 1) * N;
-    const double inv = hnv > 0.0 ? 1.0 / hnv : 0.0;
+    const double hn = shn;
+    const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < N) w[e] *= inv;
-    __threadfence();
-    __shared__ bool last;
+    if (e < N) {
+        double* w = Vb + (long long)(j + 1) * N;
+        double v = w[e];
+        for (int i = 0; i <= j; ++i) v -= h[i] * Vb[(long long)i * N + e];
+        w[e] = v * inv;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(nblk - 1));
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(gridDim.x - 1));
     __syncthreads();
     if (!last) return;
-    __threadfence();
-    // stage the Hessenberg column and the previous rotations in shared memory
+    // the last block: every block has read j; H column, Givens, convergence, j += 1
     __shared__ double scol[kMaxKrylov + 2], scs[kMaxKrylov], ssn[kMaxKrylov];
     double* col = H + (long long)j * (kmax + 1);
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        scol[i] = col[i] + h2[i];
+        scol[i] = col[i] + h[i];
         if (i < j) { scs[i] = cs[i]; ssn[i] = sn[i]; }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         *counter = 0u;
-        scol[j + 1] = hnv;
+        scol[j + 1] = hn;
         for (int i = 0; i < j; ++i) {
             const double t = scs[i] * scol[i] + ssn[i] * scol[i + 1];
             scol[i + 1] = -ssn[i] * scol[i] + scs[i] * scol[i + 1];
@@ -1497,23 +1508,23 @@ __global__ void k_gm_finalize(double* __restrict__ Vb, const int* __restrict__ j
         }
         const double a = scol[j], bq = scol[j + 1];
         const double r = hypot(a, bq);
-        double c = 1.0, s = 0.0;
-        if (r > 0.0) { c = a / r; s = bq / r; }
+        double c = 1.0, sgv = 0.0;
+        if (r > 0.0) { c = a / r; sgv = bq / r; }
         cs[j] = c;
-        sn[j] = s;
+        sn[j] = sgv;
         scol[j] = r;
         scol[j + 1] = 0.0;
         const double gj = gv[j];
-        gv[j + 1] = -s * gj;
+        gv[j + 1] = -sgv * gj;
         gv[j] = c * gj;
-        const double res = fabs(s * gj);
+        const double res = fabs(sgv * gj);
         scal[1] = res;
-        scal[3] = hnv;
+        scal[3] = hn;
         iflag[1] = j + 1;
         int stop = 0;
-        if (!(res > scal[2])) stop = 1;                                    // converged
-        if (!(hnv > 1e-300) || !isfinite(res)) { stop = 1; iflag[2] = 1; }  // breakdown
-        if (j + 1 >= kmax) { stop = 1; iflag[3] = 1; }                     // cap
+        if (!(res > scal[2])) stop = 1;                                   // converged
+        if (!(hn > 1e-300) || !isfinite(res)) { stop = 1; iflag[2] = 1; }  // breakdown
+        if (j + 1 >= kmax) { stop = 1; iflag[3] = 1; }                    // cap
         if (stop) iflag[0] = 1;
         else *jdev = j + 1;
     }
@@ -1584,18 +1595,17 @@ cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t 
 }
 
 cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s) {
-    const int bd = gmres_dot_blocks(G.N), bu = gmres_upd_blocks(G.N);
-    double* h2 = G.y;   // scratch for the second CGS pass
-    k_gm_dots<<<bd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, G.H, 1, G.counter, G.iflag);
+    const int nch = gmres_dot_blocks(G.N), bu = gmres_upd_blocks(G.N);
+    const dim3 gd1(nch, (G.kmax + 1 + kDotWarps - 1) / kDotWarps);
+    const dim3 gd2(nch, (G.kmax + 2 + kDotWarps - 1) / kDotWarps);
+    k_gm_dots2<<<gd1, 32 * kDotWarps, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, 0, G.iflag);
     note_launch();
-    k_gm_update<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.H, G.kmax, 1, G.part_norm, G.iflag);
+    k_gm_update1<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, nch, G.kmax, G.H, G.iflag);
     note_launch();
-    k_gm_dots<<<bd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, h2, 0, G.counter, G.iflag);
+    k_gm_dots2<<<gd2, 32 * kDotWarps, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, 1, G.iflag);
     note_launch();
-    k_gm_update<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, h2, G.kmax, 0, G.part_norm, G.iflag);
-    note_launch();
-    k_gm_finalize<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_norm, G.H, G.cs, G.sn, G.gv, G.scal, G.iflag, G.kmax,
-                                     h2, G.counter2, G.jdev);
+    k_gm_update2<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, nch, G.kmax, G.H, G.cs, G.sn, G.gv, G.scal,
+                                    G.iflag, G.counter2, G.jdev);
     note_launch();
     return cudaGetLastError();
 }

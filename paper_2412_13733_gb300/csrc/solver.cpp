@@ -248,7 +248,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     G.cs = dalloc<double>(D, G.kmax, ok);
     G.sn = dalloc<double>(D, G.kmax, ok);
     G.gv = dalloc<double>(D, G.kmax + 1, ok);
-    G.part_dots = dalloc<double>(D, (size_t)gmres_dot_blocks(G.N) * (G.kmax + 1), ok);
+    G.part_dots = dalloc<double>(D, (size_t)gmres_dot_blocks(G.N) * (G.kmax + 2), ok);
     G.part_norm = dalloc<double>(D, std::max<size_t>(1024, (size_t)gmres_upd_blocks(G.N)), ok);
     G.scal = dalloc<double>(D, 8, ok);
     G.iflag = dalloc<int>(D, 4, ok);
@@ -559,7 +559,7 @@ static hpg_status gmres_run(hpg_ctx* ctx, Problem& P, int* its, bool* capped) {
     cudaStream_t s = ctx->stream;
     GmresDev& G = D.gm;
     const int pi = sizeof(T) == sizeof(float) ? 1 : 0;
-    const bool use_graph = !P.timer.on;
+    const bool use_graph = !P.timer.on && P.params.graphs != 0;
     if (use_graph && !D.gmres_graph[pi] && !D.gmres_graph_failed[pi]) {
         long long nk = 0;
         if (!build_gmres_loop<T>(ctx, P, &D.gmres_graph[pi], &nk)) {

@@ -25,7 +25,7 @@ STATUS = ["HPG_OK", "HPG_ERR_ARG", "HPG_ERR_OOM", "HPG_ERR_CUDA", "HPG_ERR_NEWTO
 class hpg_params(C.Structure):
     _fields_ = [("beta", C.c_double), ("newton_tol", C.c_double), ("newton_max", C.c_int),
                 ("krylov_max", C.c_int), ("krylov_rtol", C.c_double), ("precision", C.c_int),
-                ("ls_max", C.c_int), ("refine_max", C.c_int), ("timing", C.c_int)]
+                ("ls_max", C.c_int), ("refine_max", C.c_int), ("timing", C.c_int), ("graphs", C.c_int)]
 
 
 class hpg_stats(C.Structure):
