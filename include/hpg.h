@@ -122,6 +122,8 @@ typedef struct {
     long long n_psi;                       /* psi unknowns                                 */
     long long kernel_launches;             /* libhpg kernels launched by the last solve    */
     long long h2d_bytes;                   /* problem data copied host->device by it       */
+    int    fdm_tile_f32;                   /* FDM GEMM tile variant picked by the autotuner */
+    int    fdm_tile_f64;                   /*   (FP32 and FP64 passes)                      */
 } hpg_stats;
 
 /* Kernel classes timed when hpg_params.timing = 1. */

@@ -33,6 +33,7 @@ struct Geo {
     const T* C;                               // nloc x nloc (obstacle S-hat constant part)
     const T* V[kMaxDim];                      // n1 x n1 fast-diagonalisation eigenvectors
     const T* lam[kMaxDim];                    // n1 eigenvalues
+    int gemm_cfg;                             // tile variant of the FDM passes (autotuned)
 };
 
 // Number of values stored per Gauss point by the evaluation kernel:
@@ -158,6 +159,8 @@ cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s);
 cudaError_t launch_gm_setcond(cudaGraphConditionalHandle h, const int* iflag, cudaStream_t s);
 // Solve H y = g for the completed iterations and form x = sum_i y_i V_i.
 cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s);
+// Number of FDM GEMM tile variants for elements of `elem` bytes.
+int fdm_tile_count(int elem);
 // Opt-in shared-memory limits of the large-smem kernels (call once per device).
 void configure_kernels();
 

@@ -5,6 +5,7 @@
 // inverse of A_alpha, and GMRES.
 #include <algorithm>
 #include <atomic>
+#include <tuple>
 #include <cfloat>
 #include <cmath>
 
@@ -1049,16 +1050,66 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // Tile choice: FP32 uses 32x32 tiles (4x2 per thread) -- the pass is latency-
 // bound at these sizes; FP64 runs at a small fraction of the FP32 rate, so it
 // uses 16x16 tiles to spread the work over all SMs.
-template <typename T>
-struct GemmTile;
-template <>
-struct GemmTile<float> { static constexpr int BM = 32, BN = 16, TM = 4, TN = 2, KS = 4; };
-template <>
-struct GemmTile<double> { static constexpr int BM = 16, BN = 16, TM = 2, TN = 2, KS = 1; };
+// Tile variants of the fast-diagonalisation GEMM pass; which one runs for a
+// given (dim, n1, precision) is picked at set-up by timing them on the device
+// (autotune_fdm).  FP32 passes are latency-bound (few, short K loops), FP64
+// passes are FP64-ALU-bound (~1/64 of the FP32 rate), so the candidates differ.
+template <typename T, int BM_, int BN_, int TM_, int TN_, int KS_>
+struct Tile { static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, KS = KS_; };
 
+template <typename T, typename C>
+static cudaError_t launch_tile(const GemmArgs& a, const T* A, const T* B, T* Cp, const FdmScale& sc, const T* l0,
+                               const T* l1, const T* l2, cudaStream_t s, const int* skip) {
+    constexpr int BM = C::BM, BN = C::BN, TM = C::TM, TN = C::TN, KS = C::KS;
+    const size_t red = (size_t)(KS - 1) * (BM / TM) * (BN / TN) * TM * TN * sizeof(T);
+    const size_t smem = std::max((size_t)a.K * (BM + BN) * sizeof(T), red);
+    if (smem <= 200 * 1024) {
+        dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch);
+        k_gemm_fullk<T, BM, BN, TM, TN, KS><<<grid, (BM / TM) * (BN / TN) * KS, smem, s>>>(a, A, B, Cp, sc, l0, l1,
+                                                                                        l2, skip);
+    } else {
+        dim3 grid((a.N + 31) / 32, (a.M + 31) / 32, a.batch);
+        k_gemm_tiled<T, 32, 32, 16, 2, 2><<<grid, 256, 0, s>>>(a, A, B, Cp, sc, l0, l1, l2, skip);
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
+using F32Tiles = std::tuple<Tile<float, 32, 16, 4, 2, 4>, Tile<float, 32, 32, 4, 2, 2>, Tile<float, 32, 16, 4, 2, 2>,
+                            Tile<float, 16, 16, 2, 2, 4>, Tile<float, 32, 32, 4, 2, 4>>;
+using F64Tiles = std::tuple<Tile<double, 16, 16, 2, 2, 1>, Tile<double, 16, 16, 2, 2, 2>,
+                            Tile<double, 32, 16, 4, 2, 1>, Tile<double, 16, 8, 2, 2, 2>>;
 template <typename T>
-static size_t gemm_fullk_smem(int K) {
-    return (size_t)K * (GemmTile<T>::BM + GemmTile<T>::BN) * sizeof(T);
+struct TileSet;
+template <>
+struct TileSet<float> { using type = F32Tiles; };
+template <>
+struct TileSet<double> { using type = F64Tiles; };
+
+int fdm_tile_count(int elem) { return elem == 4 ? (int)std::tuple_size<F32Tiles>::value : (int)std::tuple_size<F64Tiles>::value; }
+
+template <typename T, size_t I = 0>
+static cudaError_t launch_tile_idx(int idx, const GemmArgs& a, const T* A, const T* B, T* Cp, const FdmScale& sc,
+                                   const T* l0, const T* l1, const T* l2, cudaStream_t s, const int* skip) {
+    using Set = typename TileSet<T>::type;
+    if constexpr (I < std::tuple_size<Set>::value) {
+        if (idx == (int)I)
+            return launch_tile<T, typename std::tuple_element<I, Set>::type>(a, A, B, Cp, sc, l0, l1, l2, s, skip);
+        return launch_tile_idx<T, I + 1>(idx, a, A, B, Cp, sc, l0, l1, l2, s, skip);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, size_t I = 0>
+static void configure_tiles() {
+    using Set = typename TileSet<T>::type;
+    if constexpr (I < std::tuple_size<Set>::value) {
+        using C = typename std::tuple_element<I, Set>::type;
+        cudaFuncSetAttribute(k_gemm_fullk<T, C::BM, C::BN, C::TM, C::TN, C::KS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        configure_tiles<T, I + 1>();
+    }
 }
 
 template <typename T>
@@ -1067,22 +1118,7 @@ static cudaError_t gemm(const GemmArgs& a, const T* A, const T* B, T* C, const F
     const T* l0 = g.lam[0];
     const T* l1 = g.d > 1 ? g.lam[1] : g.lam[0];
     const T* l2 = g.d > 2 ? g.lam[2] : g.lam[0];
-    constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN, TM = GemmTile<T>::TM, TN = GemmTile<T>::TN;
-    constexpr int KS = GemmTile<T>::KS;
-    // shared memory: the two panels, and at least the split-K reduction buffer that reuses them
-    const size_t red = (size_t)(KS - 1) * (BM / TM) * (BN / TN) * TM * TN * sizeof(T);
-    const size_t smem = std::max(gemm_fullk_smem<T>(a.K), red);
-    if (smem <= 200 * 1024) {
-        dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch);
-        k_gemm_fullk<T, BM, BN, TM, TN, KS><<<grid, (BM / TM) * (BN / TN) * KS, smem, s>>>(a, A, B, C, sc, l0, l1, l2,
-                                                                                        skip);
-    } else {
-        constexpr int BK = 16;
-        dim3 grid((a.N + 31) / 32, (a.M + 31) / 32, a.batch);
-        k_gemm_tiled<T, 32, 32, BK, 2, 2><<<grid, 256, 0, s>>>(a, A, B, C, sc, l0, l1, l2, skip);
-    }
-    note_launch();
-    return cudaGetLastError();
+    return launch_tile_idx<T>(g.gemm_cfg, a, A, B, C, sc, l0, l1, l2, s, skip);
 }
 
 // A_alpha^{-1} x = alpha^{-1} (V (x) V (x) V) diag(1 / sum lam) (V^T (x) V^T (x) V^T) x
@@ -1621,12 +1657,8 @@ cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s) {
 }
 
 void configure_kernels() {
-    cudaFuncSetAttribute(k_gemm_fullk<float, GemmTile<float>::BM, GemmTile<float>::BN, GemmTile<float>::TM,
-                                       GemmTile<float>::TN, GemmTile<float>::KS>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_gemm_fullk<double, GemmTile<double>::BM, GemmTile<double>::BN, GemmTile<double>::TM,
-                                       GemmTile<double>::TN, GemmTile<double>::KS>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    configure_tiles<float>();
+    configure_tiles<double>();
     cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -4,6 +4,8 @@
 // inner solve, and the component operators used by the tests.
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <thread>
 #include <chrono>
@@ -140,6 +142,9 @@ static T* upload_vec(DevState& D, const std::vector<double>& v, bool& ok, cudaSt
     cudaStreamSynchronize(s);
     return p;
 }
+
+template <typename T>
+static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, T* w1, T* w2);
 
 hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     if (P.alloc_done) return HPG_OK;
@@ -314,7 +319,50 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
         g.Vq = D.Vq_f; g.wq = D.wq_f; g.detJ = (float)H.detJ; g.Mpsi = D.Mpsi_f; g.Kpsi = D.Kpsi_f; g.C = D.C_f;
     });
     CK(cudaStreamSynchronize(s));
+    CKS(autotune_fdm<double>(ctx, P, D.gd, D.tu_d, D.tu2_d, D.w1_d, D.w2_d));
+    CKS(autotune_fdm<float>(ctx, P, D.gf, D.tu_f, D.tu2_f, D.w1_f, D.w2_f));
     P.alloc_done = true;
+    return HPG_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+// Pick the FDM GEMM tile variant for this (dim, n1, precision) by timing one
+// A_alpha^{-1} apply per variant on the device (after a warm-up apply); cached
+// per process, so each mesh shape is tuned once.
+template <typename T>
+static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, T* w1, T* w2) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int>, int> cache;
+    const auto key = std::make_tuple(g.d, g.n1[0], g.n1[1], g.d > 2 ? g.n1[2] : 1, (int)sizeof(T));
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) { g.gemm_cfg = it->second; return HPG_OK; }
+    }
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemsetAsync(x, 0, (size_t)g.Nu0 * sizeof(T), s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 1e30f;
+    const int ncfg = fdm_tile_count((int)sizeof(T));
+    for (int c = 0; c < ncfg; ++c) {
+        g.gemm_cfg = c;
+        if (launch_fdm<T>(g, nullptr, 1.0, x, y, w1, w2, s) != cudaSuccess) { cudaGetLastError(); continue; }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 5; ++r) launch_fdm<T>(g, nullptr, 1.0, x, y, w1, w2, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g.gemm_cfg = best;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best;
     return HPG_OK;
 }
 
@@ -773,6 +821,8 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
     st.final_residual = normF;
     st.status = status;
     st.kernel_launches = kernel_launch_count() - launches0;
+    st.fdm_tile_f32 = D.gf.gemm_cfg;
+    st.fdm_tile_f64 = D.gd.gemm_cfg;
     st.h2d_bytes = P.h2d_bytes;
     CK(cudaStreamSynchronize(s));
     timer_flush(P.timer);

@@ -33,7 +33,8 @@ class hpg_stats(C.Structure):
                 ("newton_per_step", C.c_int * HPG_MAX_ALPHA), ("krylov_total", C.c_longlong),
                 ("refine_total", C.c_int), ("ls_fail", C.c_int), ("krylov_cap_hits", C.c_int),
                 ("final_residual", C.c_double), ("solve_ms", C.c_double), ("n_u", C.c_longlong),
-                ("n_psi", C.c_longlong), ("kernel_launches", C.c_longlong), ("h2d_bytes", C.c_longlong)]
+                ("n_psi", C.c_longlong), ("kernel_launches", C.c_longlong), ("h2d_bytes", C.c_longlong),
+                ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int)]
 
 
 FIELD_FN = C.CFUNCTYPE(None, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
