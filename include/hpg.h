@@ -230,14 +230,16 @@ hpg_status hpg_feasible_u(hpg_ctx* ctx, int pid, double* out_q, size_t len);
 hpg_status hpg_get_kernel_times(hpg_ctx* ctx, int pid, double* ms, long long* launches, int count);
 hpg_status hpg_reset_kernel_times(hpg_ctx* ctx, int pid);
 /* Enqueue `reps` back-to-back applications of one kernel class (hpg_kernel_class:
- * HPG_K_EVAL, _FACTOR, _PRECOND, _BAPPLY, _FDM, _SCHUR or _NEWTON_APPLY) on the
- * state left by the last solve, in arithmetic `precision`, on the context's
+ * HPG_K_EVAL, _FACTOR, _PRECOND, _BAPPLY, _FDM, _SCHUR, _NEWTON_APPLY or _ORTHO) on
+ * the state left by the last solve, in arithmetic `precision`, on the context's
  * stream, without synchronising: bracket it with CUDA events on that stream
  * to time the kernels in their solver launch configuration.  The launches are
  * captured into a CUDA graph on the first call for a given (class, precision,
  * reps) and replayed on later calls, so time the second call.  Needs a prior
  * hpg_solve or hpg_set_state (+ hpg_factor_precond for _PRECOND/_SCHUR);
- * the kernels write only scratch buffers. */
+ * the kernels write only scratch buffers.  _ORTHO is one FP64 CGS2 Arnoldi
+ * step (two dot passes, two update passes, Givens) at j = krylov_max / 2 on the
+ * Krylov basis buffer, whose contents it overwrites. */
 hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precision, int reps);
 
 /* ------------------------------------------------------------ request loop

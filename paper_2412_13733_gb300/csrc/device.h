@@ -137,24 +137,29 @@ struct GmresDev {
     double* cs;       // kmax
     double* sn;       // kmax
     double* gv;       // kmax+1
-    double* part_dots;  // dot-product partials, gmres_dot_blocks(N) x (kmax+1)
+    double* part_dots;  // dot-product partials, gmres_dot_blocks(N) x (kmax+2)
     double* part_norm;  // norm partials, >= max(gmres_upd_blocks(N), 1024)
-    double* scal;     // [0] beta0, [1] resid estimate, [2] tol*beta0, [3] h_{j+1,j}
+    double* scal;     // [0] beta0, [1] resid estimate, [2] tol*beta0, [3] h_{j+1,j}, [4] ||w1||^2
     int* iflag;       // [0] stop flag, [1] completed iterations, [2] breakdown, [3] cap reached
     int* jdev;        // current iteration index
-    unsigned int* counter;   // last-block counters (dots, finalize)
+    double* hsum;     // final dot sums of the current pass, kmax+2
+    unsigned int* counter;   // last-block counters of the dot kernel, one per vector group
     unsigned int* counter2;
+    int* reo;         // 1: the current Arnoldi step takes a second Gram-Schmidt pass
     double* y;        // kmax coefficients (also CGS scratch)
     int kmax;
     long long N;
 };
 int gmres_dot_blocks(long long N);
+int gmres_dot_groups(int kmax);
 int gmres_upd_blocks(long long N);
 // r0 = b: beta0 = ||b||, V_0 = b / beta0, g = beta0 e_1, tol*beta0 stored, j = 0.
 cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s);
 // After w (= S Shat^{-1} V_j) has been written into Vb[j+1]: CGS2 orthogonalise,
 // normalise, Givens update, convergence test, j += 1.  No-op once stopped.
 cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s);
+// Timing aid: set j (and clear the stop flags), then one Arnoldi step.
+cudaError_t gmres_timed_step(GmresDev& G, int j, cudaStream_t s);
 // Set the WHILE condition of a device-side GMRES loop to "not stopped".
 cudaError_t launch_gm_setcond(cudaGraphConditionalHandle h, const int* iflag, cudaStream_t s);
 // Solve H y = g for the completed iterations and form x = sum_i y_i V_i.

@@ -723,21 +723,86 @@ cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double bet
 }
 
 // =================================================================== precond
-// z = -(-S-hat_K)^{-1} v per cell (symmetric inverse stored per cell, read once).
+// z = -(-S-hat_K)^{-1} v per cell.  The inverse is symmetric, so row i of the
+// stored block is also its column i: a warp takes four rows at a time and reads
+// them along k with coalesced loads (16 per lane in flight), then reduces each
+// row over its lanes (fixed shuffle tree, deterministic).  `rsplit` blocks share
+// a cell's rows when there are few cells.  The apply streams N_c nb^2 words and
+// is bandwidth-bound.
 template <typename T, typename Tin, typename Tout>
-__global__ void k_precond(Geo<T> g, const T* __restrict__ Sinv, const Tin* __restrict__ v, Tout* __restrict__ z,
-                          IterCtl ctl) {
-    extern __shared__ unsigned char smraw[];
+__global__ void __launch_bounds__(256)
+    k_precond(Geo<T> g, const T* __restrict__ Sinv, const Tin* __restrict__ v, Tout* __restrict__ z, IterCtl ctl,
+              int rsplit) {
+    extern __shared__ __align__(16) unsigned char smraw[];
     if (ctl.skip && *ctl.skip) return;
-    T* vs = reinterpret_cast<T*>(smraw);
     const int nb = (int)g.nb;
-    const long long cell = blockIdx.x;
+    T* vs = reinterpret_cast<T*>(smraw);      // nb
+    const long long cell = blockIdx.x / rsplit;
+    const int part = (int)(blockIdx.x - cell * rsplit);
     const Tin* vin = v + (ctl.jptr ? (long long)(*ctl.jptr) * ctl.jstride : 0LL);
     for (int i = threadIdx.x; i < nb; i += blockDim.x) vs[i] = (T)vin[cell * nb + i];
     __syncthreads();
     const T* S = Sinv + cell * (long long)nb * nb;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rc = (nb + rsplit - 1) / rsplit;
+    const int r0 = part * rc, r1 = (r0 + rc < nb) ? r0 + rc : nb;
+    for (int i0 = r0 + 4 * wid; i0 < r1; i0 += 4 * nw) {
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        const bool full_rows = i0 + 3 < r1;
+        for (int k0 = 0; k0 < nb; k0 += 128) {
+            T a[4][4];
+            if (full_rows && k0 + 128 <= nb) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) a[r][u] = S[(size_t)(i0 + r) * nb + k0 + lane + 32 * u];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[r] += a[r][u] * vs[k0 + lane + 32 * u];
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = k0 + lane + 32 * u;
+                        a[r][u] = (i0 + r < r1 && k < nb) ? S[(size_t)(i0 + r) * nb + k] : T(0);
+                    }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = k0 + lane + 32 * u;
+                        if (k < nb) acc[r] += a[r][u] * vs[k];
+                    }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            T t = acc[r];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0 && i0 + r < r1) z[cell * nb + i0 + r] = (Tout)(-t);
+        }
+    }
+}
+
+// FP64 variant: the FP64 pipe (1/64 of the FP32 rate) makes the padded lanes and
+// the shuffle reductions of the row form cost more than they save, so each
+// thread owns one row and walks k (exactly nb^2 FMAs per cell, no reduction).
+template <typename Tin, typename Tout>
+__global__ void k_precond_f64(Geo<double> g, const double* __restrict__ Sinv, const Tin* __restrict__ v,
+                              Tout* __restrict__ z, IterCtl ctl) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if (ctl.skip && *ctl.skip) return;
+    double* vs = reinterpret_cast<double*>(smraw);
+    const int nb = (int)g.nb;
+    const long long cell = blockIdx.x;
+    const Tin* vin = v + (ctl.jptr ? (long long)(*ctl.jptr) * ctl.jstride : 0LL);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) vs[i] = (double)vin[cell * nb + i];
+    __syncthreads();
+    const double* S = Sinv + cell * (long long)nb * nb;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int k = 0;
         for (; k + 3 < nb; k += 4) {
             s0 += S[(size_t)k * nb + i] * vs[k];
@@ -750,10 +815,24 @@ __global__ void k_precond(Geo<T> g, const T* __restrict__ Sinv, const Tin* __res
     }
 }
 
+// blocks per cell: enough blocks for two per SM when cells are few
+static int precond_rsplit(long long Nc, long long nb) {
+    int r = 1;
+    while (r < 8 && Nc * r < 304 && nb / (r * 2) >= 32) r *= 2;
+    return r;
+}
+
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s, IterCtl ctl) {
-    const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
-    k_precond<T, Tin, Tout><<<(unsigned)g.Nc, threads, g.nb * sizeof(T), s>>>(g, Sinv, v, z, ctl);
+    if constexpr (sizeof(T) == 8) {
+        const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
+        k_precond_f64<Tin, Tout><<<(unsigned)g.Nc, threads, g.nb * sizeof(double), s>>>(g, Sinv, v, z, ctl);
+        note_launch();
+        return cudaGetLastError();
+    }
+    const int rsplit = precond_rsplit(g.Nc, g.nb);
+    const size_t smem = (size_t)g.nb * sizeof(T);
+    k_precond<T, Tin, Tout><<<(unsigned)(g.Nc * rsplit), 256, smem, s>>>(g, Sinv, v, z, ctl, rsplit);
     note_launch();
     return cudaGetLastError();
 }
@@ -1429,87 +1508,169 @@ __global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b
     }
 }
 
-// ---- Arnoldi step (CGS2), four kernels, no atomics or fences on the data path:
-//   dots(pass 1):   partial h1_i = <V_i, w> per chunk           (grid: chunks x vector groups)
-//   update(pass 1): h1 = sum of partials; w1 = w - V h1; H(:,j) = h1
-//   dots(pass 2):   partial h2_i = <V_i, w1>, partial ||w1||^2
-//   update(pass 2): h2, ||w2||^2 = ||w1||^2 - ||h2||^2 (Pythagoras: V orthonormal),
-//                   V_{j+1} = (w1 - V h2)/||w2||; the last block to finish applies the
-//                   Givens rotations, tests convergence and advances j.
-// Partials are summed in chunk order (deterministic).
-constexpr int kDotChunk = 2048;
-constexpr int kDotWarps = 8;
+// ---- Arnoldi step: classical Gram-Schmidt with selective re-orthogonalisation
+// (the Daniel-Gragg-Kaufman-Stewart test: a second pass only when the first one
+// cancelled more than half of ||w||^2), four kernels:
+//   dots(pass 1):   h1_i = <V_i, w> (i <= j) and ||w||^2
+//   update(pass 1): w1 = w - V h1; H(:,j) = h1; ||w1||^2 = ||w||^2 - ||h1||^2
+//                   (Pythagoras, V orthonormal); re-orthogonalise iff
+//                   ||w1||^2 <= ||w||^2 / 2
+//   dots(pass 2):   h2_i = <V_i, w1> and ||w1||^2            (skipped if not)
+//   update(pass 2): V_{j+1} = (w1 - V h2) / ||w2||, ||w2||^2 = ||w1||^2 - ||h2||^2;
+//                   the last block to finish applies the Givens rotations, tests
+//                   convergence and advances j.
+// In FP64 on this GPU the passes are bound by the FP64 FMA rate (one FMA per
+// 8-byte basis word), so every kernel does (j+1) N FMAs and a few adds: a dot
+// work item is one (vector, 1024-element chunk) pair per warp, 32 FMAs per lane
+// before one shuffle reduction.  Chunk partials are summed in chunk order by the
+// last block of each vector group (deterministic).
+constexpr int kDotChunk = 1024;      // elements per warp work item (32 per lane)
+constexpr int kDotVec = 8;           // vectors per dot block (one per warp)
 
-__global__ void __launch_bounds__(32 * kDotWarps)
+__global__ void __launch_bounds__(256)
     k_gm_dots2(const double* __restrict__ Vb, const int* __restrict__ jdev, long long N, double* __restrict__ part,
-               int kmax, int with_norm, const int* __restrict__ iflag) {
+               int kmax, const int* __restrict__ iflag, const int* __restrict__ reo, double* __restrict__ hsum,
+               unsigned int* __restrict__ counter) {
+    __shared__ double ws[kDotChunk];
+    __shared__ bool last;
     if (iflag[0]) return;
+    if (reo && *reo == 0) return;                        // second pass not needed
     const int j = *jdev;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int i = blockIdx.y * kDotWarps + wid;          // vector handled by this warp
-    const int nvec = j + 1 + (with_norm ? 1 : 0);        // slot j+1 = ||w||^2
-    if (i >= nvec) return;
+    const int nvec = j + 2;                              // slot j+1 = ||w||^2
+    const int i0 = blockIdx.y * kDotVec;
+    if (i0 >= nvec) return;
     const long long e0 = (long long)blockIdx.x * kDotChunk;
-    const long long e1 = (e0 + kDotChunk < N) ? e0 + kDotChunk : N;
-    const double* w = Vb + (long long)(j + 1) * N;
-    const double* vi = (i <= j) ? Vb + (long long)i * N : w;
-    double s0 = 0.0, s1 = 0.0;
-    long long e = e0 + lane;
-    for (; e + 32 < e1; e += 64) {
-        s0 += vi[e] * w[e];
-        s1 += vi[e + 32] * w[e + 32];
+    const int len = (N - e0 < kDotChunk) ? (int)(N - e0) : kDotChunk;
+    const double* w = Vb + (long long)(j + 1) * N + e0;
+    for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) ws[t] = (t < len) ? w[t] : 0.0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i = i0 + wid;
+    const long long ld = kmax + 2;
+    if (i < nvec) {
+        const double* vi = (i <= j) ? Vb + (long long)i * N + e0 : nullptr;
+        double s0 = 0.0, s1 = 0.0;
+        if (vi && len == kDotChunk) {
+#pragma unroll
+            for (int q0 = 0; q0 < 32; q0 += 8) {
+                double a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = vi[lane + 32 * (q0 + u)];
+#pragma unroll
+                for (int u = 0; u < 8; u += 2) {
+                    s0 += a[u] * ws[lane + 32 * (q0 + u)];
+                    s1 += a[u + 1] * ws[lane + 32 * (q0 + u + 1)];
+                }
+            }
+        } else if (vi) {
+            for (int q = 0; q < 32; ++q) {
+                const int e = lane + 32 * q;
+                if (e < len) s0 += vi[e] * ws[e];
+            }
+        } else {
+#pragma unroll 8
+            for (int q = 0; q < 32; q += 2) {
+                const double x0 = ws[lane + 32 * q], x1 = ws[lane + 32 * (q + 1)];
+                s0 += x0 * x0;
+                s1 += x1 * x1;
+            }
+        }
+        double t = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) {
+            part[(long long)blockIdx.x * ld + i] = t;
+            __threadfence();
+        }
     }
-    if (e < e1) s0 += vi[e] * w[e];
-    double sacc = s0 + s1;
-    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
-    if (lane == 0) part[(long long)blockIdx.x * (kmax + 2) + i] = sacc;
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&counter[blockIdx.y], 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    // the last chunk block of this vector group: chunk partials in chunk order,
+    // one warp per vector, fixed shuffle tree
+    __threadfence();
+    if (i < nvec) {
+        double t = 0.0;
+        for (int c = lane; c < (int)gridDim.x; c += 32) t += __ldcg(&part[(long long)c * ld + i]);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) hsum[i] = t;
+    }
+    if (threadIdx.x == 0) counter[blockIdx.y] = 0u;
 }
 
-// sum the chunk partials of vectors 0..nvec-1 into shared h[] (warp per vector)
-__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int nchunks, int kmax, int nvec,
-                                                double* h) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = wid; i < nvec; i += nw) {
-        double sacc = 0.0;
-        for (int c = lane; c < nchunks; c += 32) sacc += part[(long long)c * (kmax + 2) + i];
-        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
-        if (lane == 0) h[i] = sacc;
-    }
+// the final dot sums of the pass (written by the dot kernel's last blocks)
+__device__ __forceinline__ void load_sums(const double* __restrict__ hsum, int nvec, double* h) {
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) h[i] = hsum[i];
     __syncthreads();
 }
 
+// v - sum_{i < nv} h[i] V_i[e], in order of i, sixteen basis loads in flight
+__device__ __forceinline__ double sub_basis(const double* __restrict__ Vb, long long N, long long e,
+                                            const double* h, int nv, double v) {
+    int i = 0;
+    for (; i + 16 <= nv; i += 16) {
+        double a[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) a[u] = Vb[(long long)(i + u) * N + e];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v -= h[i + u] * a[u];
+    }
+    for (; i < nv; ++i) v -= h[i] * Vb[(long long)i * N + e];
+    return v;
+}
+
 __global__ void __launch_bounds__(256)
-    k_gm_update1(double* __restrict__ Vb, const int* __restrict__ jdev, long long N, const double* __restrict__ part,
-                 int nchunks, int kmax, double* __restrict__ H, const int* __restrict__ iflag) {
+    k_gm_update1(double* __restrict__ Vb, const int* __restrict__ jdev, long long N, const double* __restrict__ hsum,
+                 int kmax, double* __restrict__ H, double* __restrict__ scal, int* __restrict__ reo,
+                 const int* __restrict__ iflag) {
     __shared__ double h[kMaxKrylov + 2];
     if (iflag[0]) return;
     const int j = *jdev;
-    reduce_partials(part, nchunks, kmax, j + 1, h);
+    load_sums(hsum, j + 2, h);                      // h1[0..j], ||w||^2 in h[j+1]
+    if (threadIdx.x == 0) {
+        double q = 0.0;
+        for (int i = 0; i <= j; ++i) q += h[i] * h[i];
+        const double n1 = h[j + 1] - q;             // ||w1||^2
+        const int r = !(n1 > 0.5 * h[j + 1]);
+        if (blockIdx.x == 0) {
+            *reo = r;
+            scal[4] = n1;
+        }
+    }
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(long long)j * (kmax + 1) + i] = h[i];
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N) return;
     double* w = Vb + (long long)(j + 1) * N;
-    double v = w[e];
-    for (int i = 0; i <= j; ++i) v -= h[i] * Vb[(long long)i * N + e];
-    w[e] = v;
+    w[e] = sub_basis(Vb, N, e, h, j + 1, w[e]);
 }
 
 __global__ void __launch_bounds__(256)
-    k_gm_update2(double* __restrict__ Vb, const int* __restrict__ jdev_c, long long N, const double* __restrict__ part,
-                 int nchunks, int kmax, double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+    k_gm_update2(double* __restrict__ Vb, const int* __restrict__ jdev_c, long long N, const double* __restrict__ hsum,
+                 int kmax, double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
                  double* __restrict__ gv, double* __restrict__ scal, int* __restrict__ iflag,
-                 unsigned int* __restrict__ counter, int* __restrict__ jdev) {
+                 const int* __restrict__ reo, unsigned int* __restrict__ counter, int* __restrict__ jdev) {
     __shared__ double h[kMaxKrylov + 2];
     __shared__ double shn;
     __shared__ bool last;
     if (iflag[0]) return;
     const int j = *jdev_c;
-    reduce_partials(part, nchunks, kmax, j + 2, h);     // h2[0..j], ||w1||^2 in h[j+1]
+    const bool second = *reo != 0;
+    if (second) {
+        load_sums(hsum, j + 2, h);                      // h2[0..j], ||w1||^2 in h[j+1]
+    } else {
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = 0.0;
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        double q = 0.0;
-        for (int i = 0; i <= j; ++i) q += h[i] * h[i];
-        const double n2 = h[j + 1] - q;
+        double n2;
+        if (second) {
+            double q = 0.0;
+            for (int i = 0; i <= j; ++i) q += h[i] * h[i];
+            n2 = h[j + 1] - q;
+        } else {
+            n2 = scal[4];
+        }
         shn = n2 > 0.0 ? sqrt(n2) : 0.0;
     }
     __syncthreads();
@@ -1518,9 +1679,7 @@ __global__ void __launch_bounds__(256)
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < N) {
         double* w = Vb + (long long)(j + 1) * N;
-        double v = w[e];
-        for (int i = 0; i <= j; ++i) v -= h[i] * Vb[(long long)i * N + e];
-        w[e] = v * inv;
+        w[e] = (second ? sub_basis(Vb, N, e, h, j + 1, w[e]) : w[e]) * inv;
     }
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(gridDim.x - 1));
@@ -1601,7 +1760,15 @@ __global__ void k_gm_combine(const double* __restrict__ Vb, const double* __rest
     if (e >= N) return;
     const int k = iflag[1];
     double s = 0.0;
-    for (int i = 0; i < k; ++i) s += y[i] * Vb[(long long)i * N + e];
+    int i = 0;
+    for (; i + 8 <= k; i += 8) {
+        double a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = Vb[(long long)(i + u) * N + e];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += y[i + u] * a[u];
+    }
+    for (; i < k; ++i) s += y[i] * Vb[(long long)i * N + e];
     x[e] = s;
 }
 
@@ -1617,6 +1784,7 @@ cudaError_t launch_gm_setcond(cudaGraphConditionalHandle h, const int* iflag, cu
 }
 
 int gmres_dot_blocks(long long N) { return (int)((N + kDotChunk - 1) / kDotChunk); }
+int gmres_dot_groups(int kmax) { return (kmax + 2 + kDotVec - 1) / kDotVec; }
 int gmres_upd_blocks(long long N) { return (int)((N + 255) / 256); }
 
 cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s) {
@@ -1632,18 +1800,32 @@ cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t 
 
 cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s) {
     const int nch = gmres_dot_blocks(G.N), bu = gmres_upd_blocks(G.N);
-    const dim3 gd1(nch, (G.kmax + 1 + kDotWarps - 1) / kDotWarps);
-    const dim3 gd2(nch, (G.kmax + 2 + kDotWarps - 1) / kDotWarps);
-    k_gm_dots2<<<gd1, 32 * kDotWarps, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, 0, G.iflag);
+    const dim3 gd(nch, gmres_dot_groups(G.kmax));
+    k_gm_dots2<<<gd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, nullptr, G.hsum, G.counter);
     note_launch();
-    k_gm_update1<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, nch, G.kmax, G.H, G.iflag);
+    k_gm_update1<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.hsum, G.kmax, G.H, G.scal, G.reo, G.iflag);
     note_launch();
-    k_gm_dots2<<<gd2, 32 * kDotWarps, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, 1, G.iflag);
+    k_gm_dots2<<<gd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, G.reo, G.hsum, G.counter);
     note_launch();
-    k_gm_update2<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, nch, G.kmax, G.H, G.cs, G.sn, G.gv, G.scal,
-                                    G.iflag, G.counter2, G.jdev);
+    k_gm_update2<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.hsum, G.kmax, G.H, G.cs, G.sn, G.gv, G.scal, G.iflag, G.reo,
+                                    G.counter2, G.jdev);
     note_launch();
     return cudaGetLastError();
+}
+
+__global__ void k_gm_setj(int* __restrict__ jdev, int* __restrict__ iflag, unsigned int* __restrict__ counter, int j) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *jdev = j;
+        iflag[0] = iflag[1] = iflag[2] = iflag[3] = 0;
+        *counter = 0u;
+    }
+}
+
+cudaError_t gmres_timed_step(GmresDev& G, int j, cudaStream_t s) {
+    if (j < 0 || j >= G.kmax) return cudaErrorInvalidValue;
+    k_gm_setj<<<1, 32, 0, s>>>(G.jdev, G.iflag, G.counter2, j);
+    note_launch();
+    return gmres_arnoldi(G, s);
 }
 
 cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s) {

@@ -74,7 +74,7 @@ size_t estimate_device_bytes(const Problem& P) {
     b += factor_workspace_elems(H.n, H.d, (int)H.nb, H.ncomp, (long long)H.Nc, 8) * 8;
     b += factor_workspace_elems(H.n, H.d, (int)H.nb, H.ncomp, (long long)H.Nc, 4) * 4;
     b += (kmax + 1) * Npsi * 8;                          // Krylov basis
-    b += (kmax + 1) * kmax * 8 + (size_t)gmres_dot_blocks((long long)Npsi) * (kmax + 2) * 8;
+    b += (kmax + 1) * kmax * 8 + (size_t)gmres_dot_blocks((long long)Npsi) * (kmax + 2) * 8 + (kmax + 2) * 8;
     return b + (1u << 20);
 }
 

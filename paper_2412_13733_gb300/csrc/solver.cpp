@@ -258,11 +258,13 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     G.scal = dalloc<double>(D, 8, ok);
     G.iflag = dalloc<int>(D, 4, ok);
     G.jdev = dalloc<int>(D, 1, ok);
-    G.counter = dalloc<unsigned int>(D, 1, ok);
+    G.hsum = dalloc<double>(D, G.kmax + 2, ok);
+    G.counter = dalloc<unsigned int>(D, gmres_dot_groups(G.kmax), ok);
     G.counter2 = dalloc<unsigned int>(D, 1, ok);
+    G.reo = dalloc<int>(D, 1, ok);
     G.y = dalloc<double>(D, G.kmax + 1, ok);
     if (!ok) { free_device(P, s); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
-    cudaMemsetAsync(G.counter, 0, sizeof(unsigned int), s);
+    cudaMemsetAsync(G.counter, 0, sizeof(unsigned int) * gmres_dot_groups(G.kmax), s);
     cudaMemsetAsync(G.counter2, 0, sizeof(unsigned int), s);
     cudaMemsetAsync(G.iflag, 0, 4 * sizeof(int), s);
     cudaMemsetAsync(G.jdev, 0, sizeof(int), s);
@@ -1055,6 +1057,10 @@ static hpg_status enqueue_kernel(hpg_ctx* ctx, Problem& P, int cls, bool f32, do
             break;
         case HPG_K_EVAL:
             CK(launch_eval(D.gd, D.x + P.H.Nu0, D.phiq, D.gwt, nullptr, D.egt, D.flag, s));
+            break;
+        case HPG_K_ORTHO:
+            // one CGS2 Arnoldi step at j = kmax / 2, the mean j of a full Krylov cycle
+            CK(gmres_timed_step(D.gm, D.gm.kmax / 2, s));
             break;
         default:
             return HPG_ERR_ARG;

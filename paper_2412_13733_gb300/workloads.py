@@ -120,6 +120,14 @@ def workload(name):
                     breakpoints=[uniform(0.0, 1.0, m)] * 2, m=m, p=p,
                     f=const_field(8.0), f_const=8.0, phi=torsion_phi, g=None,
                     alphas=alpha_list(2.0 ** -7, 4.0), beta=1e-14, tol=1e-10, exact=None)
+    if name.startswith("box3d_"):
+        # Section 6.5's 3D solver study: (0,1)^3, f = 40, phi = 1, alpha_1 = 2^-2, cap 2,
+        # beta = 1e-5; name "box3d_p{p}_m{m}" picks the degree and cells per side
+        p, m = (int(t[1:]) for t in name.split("_")[1:3])
+        return dict(name=name, kind="obstacle", lower=False, dim=3,
+                    breakpoints=[uniform(0.0, 1.0, m)] * 3, m=m, p=p,
+                    f=const_field(40.0), f_const=40.0, phi=const_field(1.0), g=None,
+                    alphas=alpha_list(2.0 ** -2, 2.0), beta=1e-5, tol=1e-6, exact=None)
     raise KeyError(name)
 
 

@@ -38,6 +38,10 @@ def case(name):
         w = W.workload("torsion_small")
         w.update(breakpoints=[W.uniform(0, 1, 3)] * 2, p=3)
         return w
+    if name.startswith("box3d_"):
+        w = W.workload(name)
+        w["tol"] = 1e-10          # parity gates at the usual Newton tolerance
+        return w
     raise KeyError(name)
 
 

@@ -58,7 +58,8 @@ def _check(o, r, u, psi, st, u_tol, psi_tol):
     assert st["final_residual"] <= 1e-10
 
 
-@pytest.mark.parametrize("name", ["radial4", "aniso_upper", "p2", "single_cell", "sine3d_small", "torsion_small"])
+@pytest.mark.parametrize("name", ["radial4", "aniso_upper", "p2", "single_cell", "sine3d_small", "torsion_small",
+                                  "box3d_p3_m4"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_full_solve_matches_oracle(ctx, name, precision):
     o, r = oracle_solution(name)
@@ -100,4 +101,23 @@ def test_radial32_full_size_against_stored_oracle(ctx, precision):
     err = np.sqrt(e @ (S.M @ e)) / np.sqrt(g["u"] @ (S.M @ g["u"]))
     assert err <= (1e-9 if precision == 0 else 1e-8), err
     assert rel(psi, g["psi"]) <= (1e-8 if precision == 0 else 1e-7)
+    P.free()
+
+
+@pytest.mark.parametrize("p,m", [(2, 4), (2, 8), (3, 4)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_box3d_paper_newton_counts(ctx, p, m, precision):
+    """Section 6.5's 3D example at the oracle's pinned tolerance: the GPU's Newton
+    counts equal the oracle's within 1 per proximal step, and the total lies in
+    the window around the paper's printed 16."""
+    from paper_2412_13733_gb300 import workloads as W
+    from oracle.hpg import ObstacleOracle
+    w = W.workload(f"box3d_p{p}_m{m}")
+    o = ObstacleOracle(w["breakpoints"], w["p"], w["f"], w["phi"], None, beta=w["beta"])
+    r = o.solve(w["alphas"], tol=w["tol"])
+    P, u, psi, st = gpu_solve(ctx, w, precision)
+    assert st["status"] == 0
+    for a, b in zip(st["newton_per_step"], r["newton"]):
+        assert abs(a - b) <= 1, (st["newton_per_step"], r["newton"])
+    assert 16 <= st["newton_total"] <= 22, st["newton_total"]
     P.free()

@@ -38,3 +38,22 @@ def test_oscillatory_obstacle_newton_totals():
     ref = printed("oscillatory_obstacle_2d")
     assert abs(totals[0] - totals[1]) <= 1, totals
     assert all(ref <= t <= ref + 6 for t in totals), (totals, ref)
+
+
+def test_box3d_newton_totals_independent_of_h_and_p():
+    """Section 6.5 (3D solver study): the paper prints 16 Newton steps for every
+    (p, N) it runs.  The literal alpha rule gives eight subproblems where the
+    paper counts six (each extra subproblem at alpha = 2 costs two steps at the
+    tolerance used here), so the printed value is pinned within [16, 22], and
+    the h- and p-independence within 2."""
+    ref = printed("obstacle_3d")
+    totals = {}
+    for p, m in ((2, 4), (2, 8), (3, 4)):
+        w = W.workload(f"box3d_p{p}_m{m}")
+        o = ObstacleOracle(w["breakpoints"], w["p"], w["f"], w["phi"], None, beta=w["beta"])
+        r = o.solve(w["alphas"], tol=w["tol"])
+        assert r["converged"]
+        assert len(r["newton"]) == 8
+        totals[(p, m)] = sum(r["newton"])
+    assert max(totals.values()) - min(totals.values()) <= 2, totals
+    assert all(ref <= t <= ref + 6 for t in totals.values()), (totals, ref)
