@@ -146,6 +146,7 @@ struct GmresDev {
     unsigned int* counter;   // last-block counters of the dot kernel, one per vector group
     unsigned int* counter2;
     int* reo;         // 1: the current Arnoldi step takes a second Gram-Schmidt pass
+    int* force;       // nonzero: every step takes the second pass (timing of the full step)
     double* y;        // kmax coefficients (also CGS scratch)
     int kmax;
     long long N;

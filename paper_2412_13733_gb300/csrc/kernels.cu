@@ -1355,14 +1355,21 @@ __global__ void __launch_bounds__(256)
     k_newton_fused(Geo<double> g, const double* __restrict__ gw, double alpha, double beta,
                    const double* __restrict__ x, double* __restrict__ y, int nu, int cpb) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    if ((int)blockIdx.x < nu) {
+    // u-row tiles and cell groups alternate in block order, so that the block
+    // scheduler hands every SM a similar mix of the two kinds of work
+    const int nc = (int)gridDim.x - nu;
+    const int mn = nu < nc ? nu : nc;
+    const int b = (int)blockIdx.x;
+    const bool is_u = b < 2 * mn ? (b & 1) == 0 : nu > nc;
+    const int idx = b < 2 * mn ? (b >> 1) : mn + (b - 2 * mn);
+    if (is_u) {
         // u rows: reuse the tiled row kernel body through a grid-index remap
         k_urow_body<D, double, double, double, true, true, false>(
-            g, alpha, x, 1.0, x + g.Nu0, nullptr, nullptr, nullptr, nullptr, nullptr, y, (int)blockIdx.x, smraw);
+            g, alpha, x, 1.0, x + g.Nu0, nullptr, nullptr, nullptr, nullptr, nullptr, y, idx, smraw);
         return;
     }
     const int grp = threadIdx.x / (256 / cpb), lt = threadIdx.x % (256 / cpb);
-    const long long cell = (long long)(blockIdx.x - nu) * cpb + grp;
+    const long long cell = (long long)idx * cpb + grp;
     const size_t per = (size_t)(3 * g.nb + g.n * g.n);
     cellop_body<D, double, double, double, double>(g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0, cell,
                                                    cell < g.Nc, lt, 256 / cpb,
@@ -1622,7 +1629,7 @@ __device__ __forceinline__ double sub_basis(const double* __restrict__ Vb, long 
 __global__ void __launch_bounds__(256)
     k_gm_update1(double* __restrict__ Vb, const int* __restrict__ jdev, long long N, const double* __restrict__ hsum,
                  int kmax, double* __restrict__ H, double* __restrict__ scal, int* __restrict__ reo,
-                 const int* __restrict__ iflag) {
+                 const int* __restrict__ force, const int* __restrict__ iflag) {
     __shared__ double h[kMaxKrylov + 2];
     if (iflag[0]) return;
     const int j = *jdev;
@@ -1631,7 +1638,7 @@ __global__ void __launch_bounds__(256)
         double q = 0.0;
         for (int i = 0; i <= j; ++i) q += h[i] * h[i];
         const double n1 = h[j + 1] - q;             // ||w1||^2
-        const int r = !(n1 > 0.5 * h[j + 1]);
+        const int r = (*force != 0) || !(n1 > 0.5 * h[j + 1]);
         if (blockIdx.x == 0) {
             *reo = r;
             scal[4] = n1;
@@ -1803,7 +1810,7 @@ cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s) {
     const dim3 gd(nch, gmres_dot_groups(G.kmax));
     k_gm_dots2<<<gd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, nullptr, G.hsum, G.counter);
     note_launch();
-    k_gm_update1<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.hsum, G.kmax, G.H, G.scal, G.reo, G.iflag);
+    k_gm_update1<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.hsum, G.kmax, G.H, G.scal, G.reo, G.force, G.iflag);
     note_launch();
     k_gm_dots2<<<gd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, G.reo, G.hsum, G.counter);
     note_launch();

@@ -262,10 +262,12 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     G.counter = dalloc<unsigned int>(D, gmres_dot_groups(G.kmax), ok);
     G.counter2 = dalloc<unsigned int>(D, 1, ok);
     G.reo = dalloc<int>(D, 1, ok);
+    G.force = dalloc<int>(D, 1, ok);
     G.y = dalloc<double>(D, G.kmax + 1, ok);
     if (!ok) { free_device(P, s); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
     cudaMemsetAsync(G.counter, 0, sizeof(unsigned int) * gmres_dot_groups(G.kmax), s);
     cudaMemsetAsync(G.counter2, 0, sizeof(unsigned int), s);
+    cudaMemsetAsync(G.force, 0, sizeof(int), s);
     cudaMemsetAsync(G.iflag, 0, 4 * sizeof(int), s);
     cudaMemsetAsync(G.jdev, 0, sizeof(int), s);
     static std::once_flag configured;
@@ -1097,7 +1099,10 @@ hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, in
         CK(ie);
         it = D.bench_graphs.emplace(key, std::make_pair(ex, nk)).first;
     }
+    // the timed Arnoldi step always takes both Gram-Schmidt passes
+    if (cls == HPG_K_ORTHO) CK(cudaMemsetAsync(D.gm.force, 1, sizeof(int), s));
     CK(cudaGraphLaunch(it->second.first, s));
+    if (cls == HPG_K_ORTHO) CK(cudaMemsetAsync(D.gm.force, 0, sizeof(int), s));
     add_kernel_launches(it->second.second);
     return HPG_OK;
 }
