@@ -230,7 +230,10 @@ def kernel_only(args, ctx, w, stream, hpg, torch):
     """Launch one kernel class `steps` times on a seeded synthetic Newton state of
     the workload (no solve), for ncu captures and per-kernel timing."""
     prec = hpg.HPG_MIXED if args.precision == "mixed" else hpg.HPG_FP64
-    P = hpg.from_workload(ctx, w, hpg.default_params(precision=prec))
+    kw = {}
+    if args.fdm_tile >= 0:
+        kw = {"fdm_tile_f32": args.fdm_tile} if prec == hpg.HPG_MIXED else {"fdm_tile_f64": args.fdm_tile}
+    P = hpg.from_workload(ctx, w, hpg.default_params(precision=prec, **kw))
     rng = np.random.default_rng(7)
     u = np.zeros(P.n_u_full)
     psi = 0.3 * rng.standard_normal(P.n_psi)
@@ -266,6 +269,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--kernel-workload", default=WORKLOAD,
                     help="workload of the kernel-only mode (radial32, torsion, sine3d, ...)")
+    ap.add_argument("--fdm-tile", type=int, default=-1,
+                    help="kernel-only mode: force this fast-diagonalisation pass variant (-1: autotuned)")
     ap.add_argument("--batch", type=int, default=16, help="independent solves in flight per step")
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests of the serving workload (0 = skip; 512 = the full stream)")

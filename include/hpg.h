@@ -103,6 +103,11 @@ typedef struct {
     int    graphs;        /* 1 (default): GMRES runs as a device-side loop in one CUDA graph;
                              0: host-driven launches (for profilers that cannot trace
                              conditional graph nodes)                                          */
+    int    fdm_tile_f32;  /* -1 (default): the FP32 fast-diagonalisation pass variant is picked
+                             by timing all of them at set-up; 0 .. hpg_fdm_tile_count(HPG_MIXED)-1
+                             forces one (the last two are the tcgen05 3xTF32 tensor-core
+                             kernels); changing it releases the problem's device state       */
+    int    fdm_tile_f64;  /* the same for the FP64 passes                                     */
 } hpg_params;
 
 #define HPG_MAX_ALPHA 128
@@ -241,6 +246,10 @@ hpg_status hpg_reset_kernel_times(hpg_ctx* ctx, int pid);
  * with both Gram-Schmidt passes (two dot passes, two update passes, Givens) at
  * j = krylov_max / 2 on the Krylov basis buffer, whose contents it overwrites. */
 hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precision, int reps);
+/* Number of fast-diagonalisation pass variants for `precision` (HPG_MIXED: FP32
+ * passes, HPG_FP64: FP64 passes); valid values of hpg_params.fdm_tile_f32/_f64
+ * are 0 .. count-1.  Returns 0 for an unknown precision. */
+int hpg_fdm_tile_count(int precision);
 
 /* ------------------------------------------------------------ request loop
  * Continuous batching of independent solves.  The client creates and fills

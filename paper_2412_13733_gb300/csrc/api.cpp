@@ -67,6 +67,8 @@ void hpg_default_params(hpg_params* p) {
     p->refine_max = 8;
     p->timing = 0;
     p->graphs = 1;
+    p->fdm_tile_f32 = -1;
+    p->fdm_tile_f64 = -1;
 }
 
 const char* hpg_status_str(hpg_status s) {
@@ -290,9 +292,13 @@ hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params) {
     NOT_BUSY(P);
     if (params->krylov_max < 1 || params->krylov_max > 1000 || params->newton_max < 0 ||
         !(params->newton_tol > 0.0) || !(params->krylov_rtol > 0.0) || params->beta < 0.0 ||
-        (params->precision != HPG_FP64 && params->precision != HPG_MIXED) || params->ls_max < 0)
+        (params->precision != HPG_FP64 && params->precision != HPG_MIXED) || params->ls_max < 0 ||
+        params->fdm_tile_f32 < -1 || params->fdm_tile_f32 >= hpg::fdm_tile_count(4) ||
+        params->fdm_tile_f64 < -1 || params->fdm_tile_f64 >= hpg::fdm_tile_count(8))
         return HPG_ERR_ARG;
-    const bool realloc = P->alloc_done && params->krylov_max != P->params.krylov_max;
+    const bool realloc = P->alloc_done && (params->krylov_max != P->params.krylov_max ||
+                                           params->fdm_tile_f32 != P->params.fdm_tile_f32 ||
+                                           params->fdm_tile_f64 != P->params.fdm_tile_f64);
     if (realloc) {
         hpg::free_device(*P, ctx->stream);
         P->data_dirty = P->phi_dirty = true;
@@ -404,6 +410,10 @@ hpg_status hpg_get_stats(hpg_ctx* ctx, int pid, hpg_stats* stats) {
     Problem* P = find(ctx, pid);
     if (!P || !stats) return HPG_ERR_ARG;
     *stats = P->stats;
+    if (P->alloc_done) {
+        stats->fdm_tile_f32 = P->D.gf.gemm_cfg;
+        stats->fdm_tile_f64 = P->D.gd.gemm_cfg;
+    }
     return HPG_OK;
 }
 
@@ -554,6 +564,12 @@ hpg_status hpg_newton_direction(hpg_ctx* ctx, int pid, int precision, double rto
     GUARD_BEGIN
     return hpg::op_newton_direction(ctx, *P, precision, rtol, delta, krylov_its);
     GUARD_END
+}
+
+int hpg_fdm_tile_count(int precision) {
+    if (precision == HPG_MIXED) return hpg::fdm_tile_count(4);
+    if (precision == HPG_FP64) return hpg::fdm_tile_count(8);
+    return 0;
 }
 
 hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precision, int reps) {

@@ -1126,6 +1126,277 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         }
 }
 
+// ---- tensor-core variant of the FP32 pass (tcgen05, 3xTF32) ------------------
+// C = A B on the 5th-generation tensor cores.  Each operand is split as x = hi + lo
+// with hi = x rounded to TF32 (10-bit mantissa) and lo = x - hi (exact in FP32);
+// C accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor memory (lo*lo is below
+// FP32 rounding), which keeps the FP32-level accuracy of the SIMT passes.  One CTA
+// of 4 warps computes a 128 x BN tile:
+//  1. the whole K extent of its A row-panel and B column-panel is staged raw in
+//     shared memory with 4-byte cp.async ([k][m] and [k][n]);
+//  2. per chunk of 32 along K, all threads split the panels into hi/lo tiles in
+//     the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
+//     matrix; 128 bytes between core matrices along K, BK/4 x 128 bytes between
+//     8-row groups), fence them to the tensor-core (async) proxy, and thread 0
+//     issues 3 x 4 tcgen05.mma (M = 128, N = BN, K = 8) and commits them to the
+//     buffer's mbarrier; with two buffers a chunk's split overlaps the previous
+//     chunk's MMAs;
+//  3. each warp reads its 32 TMEM lanes (tile rows) with tcgen05.ld and stores
+//     them, with the FDM eigenvalue scaling on the last forward pass.
+// Every mbarrier wait is bounded (about a second); on time-out the tile is
+// written as NaN, which the solver's finiteness checks report, after a second
+// bounded wait for the MMAs in flight, and TMEM is released in every case.
+constexpr int kTcBM = 128, kTcBK = 32;
+constexpr size_t kTcSmemMax = 225 * 1024;   // dynamic; the static mbarriers fit in the rest of 227 KB
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor (tcgen05 format): start, leading (K) and stride
+// (8-row group) byte offsets, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = __uint_as_float(h);
+    lo = x - hi;
+}
+
+template <int BN>
+__device__ __forceinline__ void tmem_ld_row(uint32_t taddr, uint32_t* v);
+template <>
+__device__ __forceinline__ void tmem_ld_row<16>(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+template <>
+__device__ __forceinline__ void tmem_ld_row<32>(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+// Raw panel layout in shared memory: when the operand is contiguous along k in
+// global memory the panel is kept as [row][Kp + 4] (coalesced loads), otherwise as
+// [k][rows + 8]; the pads make the core-matrix split below bank-conflict-free.
+struct TcPanel {
+    int kfast;    // 1: [row][ld], 0: [k][ld]
+    int ld;       // leading dimension (floats)
+};
+
+__host__ __device__ inline TcPanel tc_panel(bool kfast, int rows, int Kp) {
+    return kfast ? TcPanel{1, Kp + 4} : TcPanel{0, rows + 8};
+}
+
+__host__ __device__ inline size_t tc_panel_floats(const TcPanel& t, int rows, int Kp) {
+    return (size_t)(t.kfast ? rows : Kp) * t.ld;
+}
+
+// dynamic shared memory of k_gemm_tc: nbuf hi/lo stages + raw K-panels (+ the output
+// tile, which reuses the raw region)
+template <int BN>
+static size_t tc_smem_bytes(const GemmArgs& a, int nbuf) {
+    const int Kp = ((a.K + kTcBK - 1) / kTcBK) * kTcBK;
+    const size_t stage = 2 * (size_t)kTcBM * kTcBK + 2 * (size_t)BN * kTcBK;
+    const TcPanel pa = tc_panel(a.sAk == 1, kTcBM, Kp), pb = tc_panel(a.sBk == 1, BN, Kp);
+    const size_t raw = tc_panel_floats(pa, kTcBM, Kp) + tc_panel_floats(pb, BN, Kp);
+    const size_t out = (size_t)kTcBM * (BN + 1);
+    return (nbuf * stage + (raw > out ? raw : out)) * sizeof(float);
+}
+
+// stage rows x Kp of an operand (element (r, k) at G[r * sr + k * sk], zero outside
+// rows_valid x K) into the raw panel; consecutive threads take consecutive global
+// addresses along the contiguous direction
+__device__ __forceinline__ void tc_stage(float* P, const TcPanel& t, const float* G, long long sr, long long sk,
+                                         int rows, int rows_valid, int K, int Kp, int tid, int nthr) {
+    if (t.kfast) {
+        for (int e = tid; e < rows * Kp; e += nthr) {
+            const int r = e / Kp, k = e - r * Kp;
+            const bool ok = r < rows_valid && k < K;
+            cp_async_elem(&P[(size_t)r * t.ld + k], ok ? G + (long long)r * sr + (long long)k * sk : G, ok);
+        }
+    } else {
+        for (int e = tid; e < rows * Kp; e += nthr) {
+            const int k = e / rows, r = e - k * rows;
+            const bool ok = r < rows_valid && k < K;
+            cp_async_elem(&P[(size_t)k * t.ld + r], ok ? G + (long long)r * sr + (long long)k * sk : G, ok);
+        }
+    }
+}
+
+// split rows x 32 (k0 .. k0+31) of a raw panel into hi/lo core-matrix tiles: a warp
+// writes one whole core matrix (8 rows x 4 k) per instruction
+__device__ __forceinline__ void tc_split(const float* P, const TcPanel& t, int rows, int k0, float* Hi, float* Lo,
+                                         int tid, int nthr) {
+    for (int e = tid; e < rows * kTcBK; e += nthr) {
+        const int cm = e >> 5, w = e & 31;
+        const int g = cm / (kTcBK / 4), c = cm - g * (kTcBK / 4);
+        const int r = 8 * g + (w >> 2), k = k0 + 4 * c + (w & 3);
+        const float x = t.kfast ? P[(size_t)r * t.ld + k] : P[(size_t)k * t.ld + r];
+        float h, l;
+        tf32_split(x, h, l);
+        Hi[e] = h;
+        Lo[e] = l;
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(256, 1)
+    k_gemm_tc(GemmArgs a, const float* __restrict__ Ap, const float* __restrict__ Bp, float* __restrict__ Cp,
+              FdmScale sc, const float* __restrict__ l0, const float* __restrict__ l1, const float* __restrict__ l2,
+              const int* skip, int nbuf) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    if (skip && *skip) return;
+    constexpr int BM = kTcBM, BK = kTcBK, NT = 256;
+    constexpr int ATILE = BM * BK, BTILE = BN * BK, STAGE = 2 * ATILE + 2 * BTILE;
+    constexpr uint32_t SBO = (BK / 4) * 128;              // bytes between 8-row core-matrix groups
+    const int K = a.K;
+    const int nch = (K + BK - 1) / BK;
+    const int Kp = nch * BK;
+    const TcPanel pa = tc_panel(a.sAk == 1, BM, Kp), pb = tc_panel(a.sBk == 1, BN, Kp);
+    float* stage = reinterpret_cast<float*>(smraw);       // nbuf x [A_hi, A_lo, B_hi, B_lo]
+    float* As = stage + nbuf * STAGE;
+    float* Bs = As + tc_panel_floats(pa, BM, Kp);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, b = blockIdx.z;
+    const float* A = Ap + (long long)b * a.sAb + (long long)m0 * a.sAm;
+    const float* B = Bp + (long long)b * a.sBb + (long long)n0 * a.sBn;
+    float* C = Cp + (long long)b * a.sCb;
+    tc_stage(As, pa, A, a.sAm, a.sAk, BM, a.M - m0, K, Kp, tid, NT);
+    tc_stage(Bs, pb, B, a.sBn, a.sBk, BN, a.N - n0, K, Kp, tid, NT);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cp_async_wait_all();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    // kind::tf32 instruction descriptor: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9,
+    // 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+        const int buf = c % nbuf;
+        float* Ah = stage + buf * STAGE;
+        float* Al = Ah + ATILE;
+        float* Bh = Al + ATILE;
+        float* Bl = Bh + BTILE;
+        if (c >= nbuf) ok = mbar_wait(smem_addr(&mbar[buf]), (uint32_t)(((c - nbuf) / nbuf) & 1)) && ok;
+        tc_split(As, pa, BM, c * BK, Ah, Al, tid, NT);
+        tc_split(Bs, pb, BN, c * BK, Bh, Bl, tid, NT);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_addr(Ah), al = smem_addr(Al), bh = smem_addr(Bh), bl = smem_addr(Bl);
+            for (int st = 0; st < BK / 8; ++st) {
+                const uint32_t off = (uint32_t)st * 256;  // two core matrices (8 along K) per MMA
+                tc_mma_tf32(tmem, tc_desc(ah + off, 128, SBO), tc_desc(bh + off, 128, SBO), idesc,
+                            (c > 0 || st > 0) ? 1u : 0u);
+                tc_mma_tf32(tmem, tc_desc(ah + off, 128, SBO), tc_desc(bl + off, 128, SBO), idesc, 1u);
+                tc_mma_tf32(tmem, tc_desc(al + off, 128, SBO), tc_desc(bh + off, 128, SBO), idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&mbar[buf]))
+                         : "memory");
+        }
+    }
+    const uint32_t last_bar = smem_addr(&mbar[(nch - 1) % nbuf]);
+    const uint32_t last_par = (uint32_t)(((nch - 1) / nbuf) & 1);
+    ok = mbar_wait(last_bar, last_par) && ok;
+    if (!ok) mbar_wait(last_bar, last_par);               // drain the MMAs in flight before TMEM is read/freed
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // TMEM -> shared output tile [BM][BN + 1] (reuses the raw panels) -> global
+    float* Cs = As;
+    if (warp < 4) {
+        uint32_t v[BN];
+        tmem_ld_row<BN>(tmem + ((uint32_t)(warp * 32) << 16), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int r = warp * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < BN; ++j) Cs[r * (BN + 1) + j] = ok ? __uint_as_float(v[j]) : __int_as_float(0x7fc00000);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+    float ainv = 1.0f;
+    if (sc.on) ainv = (float)(1.0 / (sc.alpha_dev ? *sc.alpha_dev : sc.alpha_host));
+    const bool nfast = a.sCn == 1;
+    for (int e = tid; e < BM * BN; e += NT) {
+        const int r = nfast ? e / BN : e % BM, j = nfast ? e % BN : e / BM;
+        const int gm = m0 + r, gn = n0 + j;
+        if (gm < a.M && gn < a.N) {
+            const long long off = (long long)gm * a.sCm + (long long)gn * a.sCn;
+            float val = Cs[r * (BN + 1) + j];
+            if (sc.on) {
+                long long lin = off + (long long)b * a.sCb;
+                const int i0 = (int)(lin % sc.n1[0]);
+                lin /= sc.n1[0];
+                const int i1 = (int)(lin % sc.n1[1]);
+                float lsum = l0[i0] + l1[i1];
+                if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                val = val * ainv / lsum;
+            }
+            C[off] = val;
+        }
+    }
+}
+
+template <int BN>
+static cudaError_t launch_gemm_tc(const GemmArgs& a, const float* A, const float* B, float* Cp, const FdmScale& sc,
+                                  const float* l0, const float* l1, const float* l2, cudaStream_t s, const int* skip) {
+    int nbuf = 2;
+    if (tc_smem_bytes<BN>(a, nbuf) > kTcSmemMax) nbuf = 1;
+    const size_t smem = tc_smem_bytes<BN>(a, nbuf);
+    if (smem > kTcSmemMax) return cudaErrorInvalidValue;       // K too long for whole-K staging
+    dim3 grid((a.N + BN - 1) / BN, (a.M + kTcBM - 1) / kTcBM, a.batch);
+    k_gemm_tc<BN><<<grid, 256, smem, s>>>(a, A, B, Cp, sc, l0, l1, l2, skip, nbuf);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // Tile choice: FP32 uses 32x32 tiles (4x2 per thread) -- the pass is latency-
 // bound at these sizes; FP64 runs at a small fraction of the FP32 rate, so it
 // uses 16x16 tiles to spread the work over all SMs.
@@ -1165,7 +1436,11 @@ struct TileSet<float> { using type = F32Tiles; };
 template <>
 struct TileSet<double> { using type = F64Tiles; };
 
-int fdm_tile_count(int elem) { return elem == 4 ? (int)std::tuple_size<F32Tiles>::value : (int)std::tuple_size<F64Tiles>::value; }
+// FP32 variants: the SIMT tiles, then the tcgen05 3xTF32 kernel with BN = 16 and 32
+constexpr int kTcVariants = 2;
+int fdm_tile_count(int elem) {
+    return elem == 4 ? (int)std::tuple_size<F32Tiles>::value + kTcVariants : (int)std::tuple_size<F64Tiles>::value;
+}
 
 template <typename T, size_t I = 0>
 static cudaError_t launch_tile_idx(int idx, const GemmArgs& a, const T* A, const T* B, T* Cp, const FdmScale& sc,
@@ -1176,6 +1451,11 @@ static cudaError_t launch_tile_idx(int idx, const GemmArgs& a, const T* A, const
             return launch_tile<T, typename std::tuple_element<I, Set>::type>(a, A, B, Cp, sc, l0, l1, l2, s, skip);
         return launch_tile_idx<T, I + 1>(idx, a, A, B, Cp, sc, l0, l1, l2, s, skip);
     } else {
+        if constexpr (sizeof(T) == 4) {
+            const int t = idx - (int)std::tuple_size<Set>::value;
+            if (t == 0) return launch_gemm_tc<16>(a, A, B, Cp, sc, l0, l1, l2, s, skip);
+            if (t == 1) return launch_gemm_tc<32>(a, A, B, Cp, sc, l0, l1, l2, s, skip);
+        }
         return cudaErrorInvalidValue;
     }
 }
@@ -1848,6 +2128,8 @@ cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s) {
 void configure_kernels() {
     configure_tiles<float>();
     configure_tiles<double>();
+    cudaFuncSetAttribute(k_gemm_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
+    cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
     cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -323,8 +323,10 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
         g.Vq = D.Vq_f; g.wq = D.wq_f; g.detJ = (float)H.detJ; g.Mpsi = D.Mpsi_f; g.Kpsi = D.Kpsi_f; g.C = D.C_f;
     });
     CK(cudaStreamSynchronize(s));
-    CKS(autotune_fdm<double>(ctx, P, D.gd, D.tu_d, D.tu2_d, D.w1_d, D.w2_d));
-    CKS(autotune_fdm<float>(ctx, P, D.gf, D.tu_f, D.tu2_f, D.w1_f, D.w2_f));
+    if (P.params.fdm_tile_f64 >= 0) D.gd.gemm_cfg = P.params.fdm_tile_f64;
+    else CKS(autotune_fdm<double>(ctx, P, D.gd, D.tu_d, D.tu2_d, D.w1_d, D.w2_d));
+    if (P.params.fdm_tile_f32 >= 0) D.gf.gemm_cfg = P.params.fdm_tile_f32;
+    else CKS(autotune_fdm<float>(ctx, P, D.gf, D.tu_f, D.tu2_f, D.w1_f, D.w2_f));
     P.alloc_done = true;
     return HPG_OK;
 }

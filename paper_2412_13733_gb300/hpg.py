@@ -25,7 +25,8 @@ STATUS = ["HPG_OK", "HPG_ERR_ARG", "HPG_ERR_OOM", "HPG_ERR_CUDA", "HPG_ERR_NEWTO
 class hpg_params(C.Structure):
     _fields_ = [("beta", C.c_double), ("newton_tol", C.c_double), ("newton_max", C.c_int),
                 ("krylov_max", C.c_int), ("krylov_rtol", C.c_double), ("precision", C.c_int),
-                ("ls_max", C.c_int), ("refine_max", C.c_int), ("timing", C.c_int), ("graphs", C.c_int)]
+                ("ls_max", C.c_int), ("refine_max", C.c_int), ("timing", C.c_int), ("graphs", C.c_int),
+                ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int)]
 
 
 class hpg_stats(C.Structure):
@@ -82,6 +83,7 @@ SIGNATURES = {
     "hpg_apply_schur": ([_ctx, C.c_int, C.c_int, _pd, _pd, _sz], C.c_int),
     "hpg_newton_direction": ([_ctx, C.c_int, C.c_int, _d, _pd, _sz, _P(C.c_int)], C.c_int),
     "hpg_launch_kernel": ([_ctx, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
+    "hpg_fdm_tile_count": ([C.c_int], C.c_int),
     "hpg_apply_stiffness_inv_noalloc": ([_ctx, C.c_int, _d, C.c_void_p, C.c_void_p, _sz], C.c_int),
     "hpg_server_start": ([_ctx, C.c_int, _sz], C.c_int),
     "hpg_server_stop": ([_ctx], C.c_int),
@@ -204,6 +206,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def fdm_tile_count(precision):
+    """Number of fast-diagonalisation pass variants (valid hpg_params.fdm_tile_f32/_f64)."""
+    return int(lib().hpg_fdm_tile_count(int(precision)))
 
 
 def default_params(**kw):

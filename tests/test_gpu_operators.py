@@ -124,3 +124,39 @@ def test_newton_direction(ctx, name):
     assert rel(d64, want) < 1e-8
     dmx, its2 = P.newton_direction(hpg.HPG_MIXED, rtol=1e-10)
     assert rel(dmx, want) < 1e-7
+
+
+def _fdm_case(name):
+    from paper_2412_13733_gb300 import workloads as W
+    if name == "rect_30x20_p5":
+        # n1 = (149, 99): two 128-row tensor-core tiles with a ragged second one, ragged N tiles
+        return dict(name=name, kind="obstacle", lower=False, dim=2,
+                    breakpoints=[W.uniform(0.0, 1.5, 30), W.uniform(0.0, 1.0, 20)], p=5,
+                    f=W.const_field(10.0), f_const=10.0, phi=lambda X: 0.3 + 0.0 * X[:, 0], g=None,
+                    alphas=W.alpha_list(2.0 ** -7, 2.0 ** -3), beta=1e-4, tol=1e-10)
+    return case(name)
+
+
+@pytest.mark.parametrize("name", ["rect_30x20_p5", "radial_3x3_p5", "p2", "sine3d_3x2x2", "torsion_3x3_p3"])
+def test_stiffness_inverse_every_pass_variant(ctx, name):
+    """Every fast-diagonalisation pass variant (SIMT tiles and the tcgen05 3xTF32
+    kernels) against a sparse direct solve of alpha A."""
+    from paper_2412_13733_gb300 import hpg
+    w = _fdm_case(name)
+    o = oracle_for(w)
+    alpha = 0.05
+    x = np.random.default_rng(6).normal(size=len(o.interior))
+    ref = spla.spsolve((alpha * o.A00).tocsc(), x)
+    u, psi, psi_prev = random_state(o, 0)
+    for prec, count, tol in ((hpg.HPG_MIXED, hpg.fdm_tile_count(hpg.HPG_MIXED), 1e-4),
+                             (hpg.HPG_FP64, hpg.fdm_tile_count(hpg.HPG_FP64), 1e-10)):
+        assert count >= 1
+        for v in range(count):
+            kw = {"fdm_tile_f32": v} if prec == hpg.HPG_MIXED else {"fdm_tile_f64": v}
+            P = hpg.from_workload(ctx, w, hpg.default_params(**kw))
+            P.set_state(u, psi, psi_prev, alpha)
+            st = P.stats()
+            assert (st["fdm_tile_f32"] if prec == hpg.HPG_MIXED else st["fdm_tile_f64"]) == v
+            err = rel(P.apply_stiffness_inv(x, prec), ref)
+            assert err < tol, (prec, v, err)
+            P.free()
