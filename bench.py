@@ -276,6 +276,8 @@ def main():
                     help="requests of the serving workload (0 = skip; 512 = the full stream)")
     ap.add_argument("--serve-fp64", action="store_true", help="also serve with the FP64 path")
     ap.add_argument("--no-others", action="store_true", help="skip the 4x4, 3D and torsion workloads")
+    ap.add_argument("--no-strategies", action="store_true",
+                    help="skip the Section 6.5 solver-strategy comparison (Schur vs FGMRES + P_D / P_L P_D / P_F-(10))")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven GMRES launches (profilers cannot trace conditional graph nodes)")
     args = ap.parse_args()
@@ -502,6 +504,37 @@ def main():
                 P.free()
             others[wname] = entry
 
+    # Section 6.5: the 3D box under the four strategies of solving the Newton systems,
+    # in the format of the paper's strategy table (averages per Newton step), FP64
+    strategies = None
+    if not args.no_strategies:
+        strategies = {}
+        names = {hpg.HPG_SCHUR: "schur", hpg.HPG_FGMRES_PD: "P_D", hpg.HPG_FGMRES_PLPD: "P_L P_D",
+                 hpg.HPG_FGMRES_PF: "P_F-(10)"}
+        for p_deg, m_cells in ((2, 4), (2, 8), (6, 4)):
+            wb = W.workload(f"box3d_p{p_deg}_m{m_cells}")
+            entry = {}
+            for strat, label in names.items():
+                P = hpg.from_workload(ctx, wb, hpg.default_params(precision=hpg.HPG_FP64, strategy=strat,
+                                                                   inner_max=10))
+                P.solve()                                   # warm-up
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.solve()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                st = P.stats()
+                nn = max(1, st["newton_total"])
+                entry[label] = {"newton": st["newton_total"],
+                                "avg_fgmres": (st["fgmres_total"] / nn) if strat != hpg.HPG_SCHUR else None,
+                                "avg_gmres": (st["krylov_total"] / nn) if strat in (hpg.HPG_SCHUR,
+                                                                                   hpg.HPG_FGMRES_PF) else None,
+                                "avg_ainv": st["ainv_total"] / nn, "solve_ms": e0.elapsed_time(e1),
+                                "status": st["status"]}
+                P.free()
+            strategies[f"p={p_deg}, {m_cells}^3 cells"] = entry
+
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = {"requests": args.serve_requests, "workers": B,
@@ -551,7 +584,8 @@ def main():
                 "e2e": head["e2e"], "gpu_launches": int(head["launches"] * args.steps),
                 "roofline": roof, "newton_apply_roofline": newton_roof, "other_rooflines": bw_roofs,
                 "kernel_avg_us": {k: v[0] * 1000.0 for k, v in kt.items()},
-                "other_workloads": others, "serving": serving, "clocks": clocks, "cpu_baseline": cpu}
+                "other_workloads": others, "solver_strategies": strategies, "serving": serving, "clocks": clocks,
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

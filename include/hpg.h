@@ -85,6 +85,21 @@ typedef enum {
                                    refinement of each Newton system                           */
 } hpg_precision;
 
+/* How each Newton system G delta = F of eq. (pG-matrix) is solved (Section 4.3).
+ * HPG_SCHUR: the Schur-complement sequence of eq. (schur2) with S-hat-preconditioned
+ *   GMRES on S (the strategy the paper uses in 2D).
+ * HPG_FGMRES_PD / _PLPD / _PF: flexible GMRES on G, right-preconditioned by the block
+ *   preconditioner P_D = diag(A_alpha, S), P_L P_D, or P_F = P_L P_D P_R of eq. (schur4);
+ *   S^{-1} is S-hat^{-1} for P_D and P_L P_D, and at most hpg_params.inner_max iterations of
+ *   S-hat-preconditioned GMRES on S (relative tolerance 1e-5) for P_F ("P_F-(n)").
+ *   A_alpha^{-1} is the exact fast diagonalisation in every strategy.  FP64 only. */
+typedef enum {
+    HPG_SCHUR = 0,
+    HPG_FGMRES_PD = 1,
+    HPG_FGMRES_PLPD = 2,
+    HPG_FGMRES_PF = 3
+} hpg_strategy;
+
 /* Field callback: out[i] = field(x[i*dim], ..., x[i*dim+dim-1]) for i < npts. */
 typedef void (*hpg_field_fn)(int npts, int dim, const double* x, double* out, void* user);
 
@@ -108,6 +123,9 @@ typedef struct {
                              forces one (the last two are the tcgen05 3xTF32 tensor-core
                              kernels); changing it releases the problem's device state       */
     int    fdm_tile_f64;  /* the same for the FP64 passes                                     */
+    int    strategy;      /* hpg_strategy; default HPG_SCHUR; the FGMRES strategies need
+                             precision HPG_FP64 (HPG_ERR_ARG otherwise)                       */
+    int    inner_max;     /* HPG_FGMRES_PF: inner GMRES iterations per application; default 10 */
 } hpg_params;
 
 #define HPG_MAX_ALPHA 128
@@ -129,6 +147,8 @@ typedef struct {
     long long h2d_bytes;                   /* problem data copied host->device by it       */
     int    fdm_tile_f32;                   /* FDM GEMM tile variant picked by the autotuner */
     int    fdm_tile_f64;                   /*   (FP32 and FP64 passes)                      */
+    long long fgmres_total;                /* outer FGMRES iterations (FGMRES strategies)  */
+    long long ainv_total;                  /* applications of A_alpha^{-1} over the solve  */
 } hpg_stats;
 
 /* Kernel classes timed when hpg_params.timing = 1. */

@@ -69,6 +69,8 @@ void hpg_default_params(hpg_params* p) {
     p->graphs = 1;
     p->fdm_tile_f32 = -1;
     p->fdm_tile_f64 = -1;
+    p->strategy = HPG_SCHUR;
+    p->inner_max = 10;
 }
 
 const char* hpg_status_str(hpg_status s) {
@@ -294,7 +296,9 @@ hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params) {
         !(params->newton_tol > 0.0) || !(params->krylov_rtol > 0.0) || params->beta < 0.0 ||
         (params->precision != HPG_FP64 && params->precision != HPG_MIXED) || params->ls_max < 0 ||
         params->fdm_tile_f32 < -1 || params->fdm_tile_f32 >= hpg::fdm_tile_count(4) ||
-        params->fdm_tile_f64 < -1 || params->fdm_tile_f64 >= hpg::fdm_tile_count(8))
+        params->fdm_tile_f64 < -1 || params->fdm_tile_f64 >= hpg::fdm_tile_count(8) ||
+        params->strategy < HPG_SCHUR || params->strategy > HPG_FGMRES_PF ||
+        (params->strategy != HPG_SCHUR && params->precision != HPG_FP64) || params->inner_max < 1)
         return HPG_ERR_ARG;
     const bool realloc = P->alloc_done && (params->krylov_max != P->params.krylov_max ||
                                            params->fdm_tile_f32 != P->params.fdm_tile_f32 ||

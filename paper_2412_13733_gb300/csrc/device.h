@@ -140,7 +140,8 @@ struct GmresDev {
     double* part_dots;  // dot-product partials, gmres_dot_blocks(N) x (kmax+2)
     double* part_norm;  // norm partials, >= max(gmres_upd_blocks(N), 1024)
     double* scal;     // [0] beta0, [1] resid estimate, [2] tol*beta0, [3] h_{j+1,j}, [4] ||w1||^2
-    int* iflag;       // [0] stop flag, [1] completed iterations, [2] breakdown, [3] cap reached
+    int* iflag;       // [0] stop flag, [1] completed iterations, [2] breakdown, [3] cap reached,
+                      // [4] iteration cap of the current run (<= kmax)
     int* jdev;        // current iteration index
     double* hsum;     // final dot sums of the current pass, kmax+2
     unsigned int* counter;   // last-block counters of the dot kernel, one per vector group
@@ -152,10 +153,17 @@ struct GmresDev {
     long long N;
 };
 int gmres_dot_blocks(long long N);
+// Flexible GMRES on G: chunk partials of the dots V_v . w (v < nv, vectors ld apart),
+// part[v * fg_chunks(N) + c]; and w += sgn * sum_v h[v] V_v (h on the device).
+int fg_chunks(long long N);
+cudaError_t launch_mdot(const double* V, long long ld, int nv, const double* w, long long N, double* part,
+                        cudaStream_t s);
+cudaError_t launch_maxpy(double* w, const double* V, long long ld, const double* h, int nv, long long N, double sgn,
+                         cudaStream_t s);
 int gmres_dot_groups(int kmax);
 int gmres_upd_blocks(long long N);
 // r0 = b: beta0 = ||b||, V_0 = b / beta0, g = beta0 e_1, tol*beta0 stored, j = 0.
-cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s);
+cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s, int cap = 0);
 // After w (= S Shat^{-1} V_j) has been written into Vb[j+1]: CGS2 orthogonalise,
 // normalise, Givens update, convergence test, j += 1.  No-op once stopped.
 cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s);

@@ -1769,7 +1769,8 @@ cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts
 
 __global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b, long long N,
                            const double* __restrict__ part, int nparts, double rtol, double* __restrict__ scal,
-                           double* __restrict__ gv, int kmax, int* __restrict__ iflag, int* __restrict__ jdev) {
+                           double* __restrict__ gv, int kmax, int cap, int* __restrict__ iflag,
+                           int* __restrict__ jdev) {
     __shared__ double sh[32];
     double v = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
@@ -1791,6 +1792,7 @@ __global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b
         iflag[1] = 0;
         iflag[2] = 0;
         iflag[3] = 0;
+        iflag[4] = cap;
         *jdev = 0;
     }
 }
@@ -2006,7 +2008,7 @@ __global__ void __launch_bounds__(256)
         int stop = 0;
         if (!(res > scal[2])) stop = 1;                                   // converged
         if (!(hn > 1e-300) || !isfinite(res)) { stop = 1; iflag[2] = 1; }  // breakdown
-        if (j + 1 >= kmax) { stop = 1; iflag[3] = 1; }                    // cap
+        if (j + 1 >= kmax || j + 1 >= iflag[4]) { stop = 1; iflag[3] = 1; }  // cap
         if (stop) iflag[0] = 1;
         else *jdev = j + 1;
     }
@@ -2074,13 +2076,14 @@ int gmres_dot_blocks(long long N) { return (int)((N + kDotChunk - 1) / kDotChunk
 int gmres_dot_groups(int kmax) { return (kmax + 2 + kDotVec - 1) / kDotVec; }
 int gmres_upd_blocks(long long N) { return (int)((N + 255) / 256); }
 
-cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s) {
+cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s, int cap) {
     int np = 0;
     cudaError_t e = launch_sumsq(b, G.N, G.part_norm, &np, s);
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(G.H, 0, sizeof(double) * (size_t)(G.kmax + 1) * G.kmax, s);
     const int nb = gmres_upd_blocks(G.N) < 1024 ? gmres_upd_blocks(G.N) : 1024;
-    k_gm_start<<<nb, 256, 0, s>>>(G.Vb, b, G.N, G.part_norm, np, rtol, G.scal, G.gv, G.kmax, G.iflag, G.jdev);
+    const int c = (cap > 0 && cap < G.kmax) ? cap : G.kmax;
+    k_gm_start<<<nb, 256, 0, s>>>(G.Vb, b, G.N, G.part_norm, np, rtol, G.scal, G.gv, G.kmax, c, G.iflag, G.jdev);
     note_launch();
     return cudaGetLastError();
 }
@@ -2100,17 +2103,19 @@ cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-__global__ void k_gm_setj(int* __restrict__ jdev, int* __restrict__ iflag, unsigned int* __restrict__ counter, int j) {
+__global__ void k_gm_setj(int* __restrict__ jdev, int* __restrict__ iflag, unsigned int* __restrict__ counter, int j,
+                          int kmax) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         *jdev = j;
         iflag[0] = iflag[1] = iflag[2] = iflag[3] = 0;
+        iflag[4] = kmax;
         *counter = 0u;
     }
 }
 
 cudaError_t gmres_timed_step(GmresDev& G, int j, cudaStream_t s) {
     if (j < 0 || j >= G.kmax) return cudaErrorInvalidValue;
-    k_gm_setj<<<1, 32, 0, s>>>(G.jdev, G.iflag, G.counter2, j);
+    k_gm_setj<<<1, 32, 0, s>>>(G.jdev, G.iflag, G.counter2, j, G.kmax);
     note_launch();
     return gmres_arnoldi(G, s);
 }
@@ -2121,6 +2126,52 @@ cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s) {
     k_gm_backsolve<<<1, 256, use_smem ? tri : 0, s>>>(G.H, G.gv, G.iflag, G.kmax, G.y, use_smem);
     note_launch();
     k_gm_combine<<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(G.Vb, G.y, G.iflag, G.N, x);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---- vector blocks of the flexible GMRES on G (host-driven outer loop) ---------
+// part[v * nchunks + c] = sum over chunk c (kFgChunk elements) of V_v . w, v < nv
+constexpr int kFgChunk = 2048;
+
+__global__ void __launch_bounds__(256)
+    k_mdot(const double* __restrict__ V, long long ld, const double* __restrict__ w, long long N, double* __restrict__ part) {
+    __shared__ double sh[32];
+    const long long e0 = (long long)blockIdx.x * kFgChunk;
+    const double* v = V + (long long)blockIdx.y * ld;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < kFgChunk; t += blockDim.x) {
+        const long long e = e0 + t;
+        if (e < N) acc += v[e] * w[e];
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+// w += sgn * sum_{v < nv} h[v] V_v, in order of v
+__global__ void k_maxpy(double* __restrict__ w, const double* __restrict__ V, long long ld, const double* __restrict__ h,
+                        int nv, long long N, double sgn) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    double acc = 0.0;
+    for (int v = 0; v < nv; ++v) acc += h[v] * V[(long long)v * ld + e];
+    w[e] += sgn * acc;
+}
+
+int fg_chunks(long long N) { return (int)((N + kFgChunk - 1) / kFgChunk); }
+
+cudaError_t launch_mdot(const double* V, long long ld, int nv, const double* w, long long N, double* part,
+                        cudaStream_t s) {
+    if (nv <= 0) return cudaSuccess;
+    k_mdot<<<dim3((unsigned)fg_chunks(N), (unsigned)nv), 256, 0, s>>>(V, ld, w, N, part);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxpy(double* w, const double* V, long long ld, const double* h, int nv, long long N, double sgn,
+                         cudaStream_t s) {
+    if (nv <= 0) return cudaSuccess;
+    k_maxpy<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(w, V, ld, h, nv, N, sgn);
     note_launch();
     return cudaGetLastError();
 }

@@ -256,7 +256,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     G.part_dots = dalloc<double>(D, (size_t)gmres_dot_blocks(G.N) * (G.kmax + 2), ok);
     G.part_norm = dalloc<double>(D, std::max<size_t>(1024, (size_t)gmres_upd_blocks(G.N)), ok);
     G.scal = dalloc<double>(D, 8, ok);
-    G.iflag = dalloc<int>(D, 4, ok);
+    G.iflag = dalloc<int>(D, 8, ok);
     G.jdev = dalloc<int>(D, 1, ok);
     G.hsum = dalloc<double>(D, G.kmax + 2, ok);
     G.counter = dalloc<unsigned int>(D, gmres_dot_groups(G.kmax), ok);
@@ -268,7 +268,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     cudaMemsetAsync(G.counter, 0, sizeof(unsigned int) * gmres_dot_groups(G.kmax), s);
     cudaMemsetAsync(G.counter2, 0, sizeof(unsigned int), s);
     cudaMemsetAsync(G.force, 0, sizeof(int), s);
-    cudaMemsetAsync(G.iflag, 0, 4 * sizeof(int), s);
+    cudaMemsetAsync(G.iflag, 0, 8 * sizeof(int), s);
     cudaMemsetAsync(G.jdev, 0, sizeof(int), s);
     static std::once_flag configured;
     std::call_once(configured, configure_kernels);
@@ -652,7 +652,7 @@ static hpg_status gmres_run(hpg_ctx* ctx, Problem& P, int* its, bool* capped) {
 // S-hat); delta_u = A^{-1}(b_u - B delta_psi).  All vectors FP64, operators in T.
 template <typename T>
 static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const double* bu, const double* bp,
-                                double* du, double* dp, double rtol, int* its, bool* capped) {
+                                double* du, double* dp, double rtol, int* its, bool* capped, int cap = 0) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
     const Geo<T>& g = PV<T>::g(D);
@@ -670,9 +670,10 @@ static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const do
     }
     {
         Scope sc(P.timer, HPG_K_ORTHO, s);
-        CK(gmres_start(G, D.yp, rtol, s));
+        CK(gmres_start(G, D.yp, rtol, s, cap));
     }
     CKS(gmres_run<T>(ctx, P, its, capped));
+    P.stats.ainv_total += 2 + *its;
     {
         Scope sc(P.timer, HPG_K_ORTHO, s);
         CK(gmres_finish(G, D.xs, s));
@@ -692,6 +693,132 @@ static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const do
     }
     CKS(fdm_T<T>(ctx, P, alpha, tu, tu2));
     CK(from_T<T>(tu2, du, Nu0, s));
+    return HPG_OK;
+}
+
+// ---- flexible GMRES on G with a block preconditioner (Section 4.3) -------------
+// z = P^{-1} r for r = [r_u; r_psi] (G = [[A_alpha, B], [B^T, C]], S = C - B^T A_alpha^{-1} B):
+//   P_D:      z_u = A_alpha^{-1} r_u,  z_psi = S-hat^{-1} r_psi
+//   P_L P_D:  z_u = A_alpha^{-1} r_u,  z_psi = S-hat^{-1} (r_psi - B^T z_u)
+//   P_F:      eq. (schur2) with S^{-1} replaced by at most inner_max iterations of
+//             S-hat-preconditioned GMRES on S (relative tolerance 1e-5)
+static hpg_status fg_precond(hpg_ctx* ctx, Problem& P, double alpha, const double* r, double* z) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const Geo<double>& g = D.gd;
+    const long long Nu0 = (long long)P.H.Nu0, Npsi = (long long)P.H.Npsi;
+    if (P.params.strategy == HPG_FGMRES_PF) {
+        int its = 0;
+        bool capped = false;
+        CKS(schur_solve_T<double>(ctx, P, alpha, r, r + Nu0, z, z + Nu0, 1e-5, &its, &capped, P.params.inner_max));
+        P.stats.krylov_total += its;
+        return HPG_OK;
+    }
+    CK(launch_fdm<double>(g, nullptr, alpha, r, z, D.w1_d, D.w2_d, s));
+    P.stats.ainv_total += 1;
+    const double* rp = r + Nu0;
+    if (P.params.strategy == HPG_FGMRES_PLPD) {
+        CK(launch_btapply<double, double, double>(g, z, D.fP1, s));
+        CK(launch_sub_scaled<double>(r + Nu0, 1.0, D.fP1, D.fP1, Npsi, s));     // r_psi - B^T z_u
+        rp = D.fP1;
+    }
+    CK(launch_precond<double, double, double>(g, D.Sinv_d, rp, z + Nu0, s));
+    return HPG_OK;
+}
+
+// sum of the chunk partials of nv dot products (chunk order), on the host
+static hpg_status fg_dots(hpg_ctx* ctx, Problem& P, const double* V, int nv, const double* w, std::vector<double>& h) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long N = (long long)(P.H.Nu0 + P.H.Npsi);
+    const int nch = fg_chunks(N);
+    CK(launch_mdot(V, N, nv, w, N, D.fpart, s));
+    std::vector<double> part((size_t)nv * nch);
+    CK(cudaMemcpyAsync(part.data(), D.fpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h.assign(nv, 0.0);
+    for (int v = 0; v < nv; ++v)
+        for (int c = 0; c < nch; ++c) h[v] += part[(size_t)v * nch + c];
+    return HPG_OK;
+}
+
+// Right-preconditioned flexible GMRES (unrestarted, at most krylov_max iterations) on
+// G x = b, classical Gram-Schmidt with one re-orthogonalisation, Givens rotations on
+// the host.  Outer iterations are few (1-3 for P_F, tens for P_D), so the loop is
+// host-driven; every vector operation runs in libhpg kernels.
+static hpg_status fgmres_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* b, double rtol, double* x,
+                               int* its, bool* capped) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long Nu0 = (long long)P.H.Nu0, Npsi = (long long)P.H.Npsi, N = Nu0 + Npsi;
+    const int m = std::max(1, P.params.krylov_max);
+    if (!D.fV || D.fm != m) {
+        bool ok = true;
+        D.fV = dalloc<double>(D, (size_t)(m + 1) * N, ok);
+        D.fZ = dalloc<double>(D, (size_t)m * N, ok);
+        D.fpart = dalloc<double>(D, (size_t)(m + 1) * fg_chunks(N), ok);
+        D.fh = dalloc<double>(D, (size_t)m + 1, ok);
+        D.fP1 = dalloc<double>(D, (size_t)Npsi, ok);
+        if (!ok) { ctx->err = "device allocation failed (flexible GMRES)"; return HPG_ERR_OOM; }
+        D.fm = m;
+    }
+    *its = 0;
+    *capped = false;
+    CK(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+    double beta = 0.0;
+    CKS(norm_of(ctx, P, b, N, &beta));
+    if (!(beta > 0.0)) return HPG_OK;
+    CK(cudaMemsetAsync(D.fV, 0, N * sizeof(double), s));
+    CK(launch_axpby(1.0 / beta, b, 0.0, D.fV, N, s));
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gv(m + 1, 0.0), h, h2;
+    gv[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+        double* vj = D.fV + (long long)j * N;
+        double* zj = D.fZ + (long long)j * N;
+        double* w = D.fV + (long long)(j + 1) * N;
+        CKS(fg_precond(ctx, P, alpha, vj, zj));
+        CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, zj, w, s, D.aux, D.ev_fork, D.ev_join));
+        double* col = H.data() + (size_t)j * (m + 1);
+        for (int pass = 0; pass < 2; ++pass) {
+            CKS(fg_dots(ctx, P, D.fV, j + 1, w, h));
+            CK(cudaMemcpyAsync(D.fh, h.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+            CK(launch_maxpy(w, D.fV, N, D.fh, j + 1, N, -1.0, s));
+            for (int i = 0; i <= j; ++i) col[i] += h[i];
+        }
+        CKS(fg_dots(ctx, P, w, 1, w, h2));
+        const double hn = std::sqrt(std::max(h2[0], 0.0));
+        col[j + 1] = hn;
+        if (hn > 0.0) CK(launch_axpby(1.0 / hn, w, 0.0, w, N, s));
+        for (int i = 0; i < j; ++i) {
+            const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+            col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+            col[i] = t;
+        }
+        const double r = std::hypot(col[j], col[j + 1]);
+        cs[j] = r > 0.0 ? col[j] / r : 1.0;
+        sn[j] = r > 0.0 ? col[j + 1] / r : 0.0;
+        col[j] = r;
+        col[j + 1] = 0.0;
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        k = j + 1;
+        if (!(std::fabs(gv[j + 1]) > rtol * beta) || !(hn > 1e-300 * beta)) break;
+    }
+    *its = k;
+    P.stats.fgmres_total += k;
+    *capped = k == m && std::fabs(gv[k]) > rtol * beta;
+    // back substitution, then x = Z y
+    std::vector<double> y(k, 0.0);
+    for (int i = k - 1; i >= 0; --i) {
+        double t = gv[i];
+        for (int l = i + 1; l < k; ++l) t -= H[(size_t)l * (m + 1) + i] * y[l];
+        const double dgl = H[(size_t)i * (m + 1) + i];
+        y[i] = dgl != 0.0 ? t / dgl : 0.0;
+    }
+    CK(cudaMemcpyAsync(D.fh, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(launch_maxpy(x, D.fZ, N, D.fh, k, N, 1.0, s));
+    CK(cudaStreamSynchronize(s));
     return HPG_OK;
 }
 
@@ -718,8 +845,14 @@ static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
         // refinement sweep usually suffices
         const double need = eta * normF / std::max(rnorm, 1e-300);
         const double rt = f64 ? std::min(1.0, need) : std::min(1.0, std::max(0.1 * need, 1e-6));
-        if (f64) CKS(schur_solve_T<double>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, rt, &its, &capped));
-        else CKS(schur_solve_T<float>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, rt, &its, &capped));
+        if (f64 && P.params.strategy != HPG_SCHUR) {
+            int outer = 0;
+            CKS(fgmres_solve(ctx, P, alpha, D.r, rt, D.dcorr, &outer, &capped));
+        } else if (f64) {
+            CKS(schur_solve_T<double>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, rt, &its, &capped));
+        } else {
+            CKS(schur_solve_T<float>(ctx, P, alpha, D.r, D.r + Nu0, D.dcorr, D.dcorr + Nu0, rt, &its, &capped));
+        }
         *its_total += its;
         *sweeps = sw + 1;
         if (capped) P.stats.krylov_cap_hits++;

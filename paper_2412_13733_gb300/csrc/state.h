@@ -20,6 +20,11 @@ struct DevSten {
 };
 
 struct DevState {
+    // flexible GMRES on G (allocated on first use): basis, preconditioned directions,
+    // dot partials, coefficients, block scratch
+    double *fV = nullptr, *fZ = nullptr, *fpart = nullptr, *fh = nullptr;
+    double *fT1 = nullptr, *fT2 = nullptr, *fP1 = nullptr;
+    int fm = 0;
     // constant operators
     DevSten A[kMaxDim], M[kMaxDim], B[kMaxDim], BT[kMaxDim], Bd[kMaxDim], BdT[kMaxDim];
     double *Vq_d = nullptr, *wq_d = nullptr, *Mpsi_d = nullptr, *Kpsi_d = nullptr, *C_d = nullptr;

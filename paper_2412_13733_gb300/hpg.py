@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_PKG, "libhpg.so")
 
 HPG_OBSTACLE_UPPER, HPG_OBSTACLE_LOWER, HPG_GRADIENT = 0, 1, 2
 HPG_FP64, HPG_MIXED = 0, 1
+HPG_SCHUR, HPG_FGMRES_PD, HPG_FGMRES_PLPD, HPG_FGMRES_PF = 0, 1, 2, 3
 HPG_MAX_ALPHA = 128
 KERNEL_CLASSES = ["eval", "residual", "factor", "precond", "bapply", "fdm", "schur", "ortho", "newton_apply",
                   "update"]
@@ -26,7 +27,8 @@ class hpg_params(C.Structure):
     _fields_ = [("beta", C.c_double), ("newton_tol", C.c_double), ("newton_max", C.c_int),
                 ("krylov_max", C.c_int), ("krylov_rtol", C.c_double), ("precision", C.c_int),
                 ("ls_max", C.c_int), ("refine_max", C.c_int), ("timing", C.c_int), ("graphs", C.c_int),
-                ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int)]
+                ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int), ("strategy", C.c_int),
+                ("inner_max", C.c_int)]
 
 
 class hpg_stats(C.Structure):
@@ -35,7 +37,8 @@ class hpg_stats(C.Structure):
                 ("refine_total", C.c_int), ("ls_fail", C.c_int), ("krylov_cap_hits", C.c_int),
                 ("final_residual", C.c_double), ("solve_ms", C.c_double), ("n_u", C.c_longlong),
                 ("n_psi", C.c_longlong), ("kernel_launches", C.c_longlong), ("h2d_bytes", C.c_longlong),
-                ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int)]
+                ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int), ("fgmres_total", C.c_longlong),
+                ("ainv_total", C.c_longlong)]
 
 
 FIELD_FN = C.CFUNCTYPE(None, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)

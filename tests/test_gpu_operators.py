@@ -160,3 +160,17 @@ def test_stiffness_inverse_every_pass_variant(ctx, name):
             err = rel(P.apply_stiffness_inv(x, prec), ref)
             assert err < tol, (prec, v, err)
             P.free()
+
+
+@pytest.mark.parametrize("strategy", [1, 2, 3])
+@pytest.mark.parametrize("name", ["radial_3x3_p5", "sine3d_3x2x2", "torsion_3x3_p3"])
+def test_newton_direction_fgmres(ctx, name, strategy):
+    """The Newton direction by flexible GMRES on G with each block preconditioner
+    equals the sparse direct solve of eq. (pG-matrix)."""
+    from paper_2412_13733_gb300 import hpg
+    w, o, P, (u, psi, psi_prev, alpha) = _setup(ctx, name)
+    P.set_params(hpg.default_params(precision=0, strategy=strategy, beta=w["beta"]))
+    F = o.residual(u, psi, psi_prev, alpha)
+    want = spla.spsolve(o.jacobian(psi, alpha), F)
+    d, its = P.newton_direction(hpg.HPG_FP64, rtol=1e-12)
+    assert rel(d, want) < 1e-8

@@ -121,3 +121,27 @@ def test_box3d_paper_newton_counts(ctx, p, m, precision):
         assert abs(a - b) <= 1, (st["newton_per_step"], r["newton"])
     assert 16 <= st["newton_total"] <= 22, st["newton_total"]
     P.free()
+
+
+@pytest.mark.parametrize("strategy", [1, 2, 3])
+@pytest.mark.parametrize("name", ["radial_3x3_p5", "box3d_p2_m4", "torsion_3x3_p3"])
+def test_fgmres_block_preconditioners_match_oracle(ctx, name, strategy):
+    """Section 4.3: flexible GMRES on G with P_D, P_L P_D or P_F-(10) gives the
+    oracle's Newton counts (+-1 per proximal step) and solution (FP64 gates)."""
+    from paper_2412_13733_gb300 import hpg
+    o, r = oracle_solution(name)
+    P = hpg.from_workload(ctx, case(name), hpg.default_params(precision=0, strategy=strategy))
+    P.solve()
+    st = P.stats()
+    _check(o, r, P.u(), P.psi(), st, 1e-9, 1e-8)
+    assert st["fgmres_total"] >= st["newton_total"]
+    assert st["ainv_total"] >= st["fgmres_total"]
+    if strategy == 3:
+        assert st["krylov_total"] > 0
+    P.free()
+
+
+def test_fgmres_needs_fp64(ctx):
+    from paper_2412_13733_gb300 import hpg
+    with pytest.raises(hpg.HpgError):
+        hpg.from_workload(ctx, case("radial4"), hpg.default_params(precision=1, strategy=1))
