@@ -147,6 +147,22 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(value, dist, torch, device):
+    """The slowest rank's timed-region length (replicas run independent solves;
+    the whole-job throughput is the units of all ranks over this time)."""
+    if dist is None:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, total_ms):
+    """Whole-job units per second from the max-over-ranks time."""
+    return world * units_per_rank / (total_ms / 1000.0)
+
+
 # ------------------------------------------------------------------ GPU legs
 def algorithmic_work(P, w):
     """Per-launch algorithmic FLOPs / bytes of the kernel classes."""
@@ -270,7 +286,7 @@ def main():
     ap.add_argument("--kernel-workload", default=WORKLOAD,
                     help="workload of the kernel-only mode (radial32, torsion, sine3d, ...)")
     ap.add_argument("--fdm-tile", type=int, default=-1,
-                    help="kernel-only mode: force this fast-diagonalisation pass variant (-1: autotuned)")
+                    help="force this fast-diagonalisation pass variant of the timed precision (-1: autotuned)")
     ap.add_argument("--batch", type=int, default=16, help="independent solves in flight per step")
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests of the serving workload (0 = skip; 512 = the full stream)")
@@ -336,7 +352,10 @@ def main():
     B = args.batch
 
     def make(prec, count):
-        ps = [hpg.from_workload(ctx, w, hpg.default_params(precision=prec, graphs=0 if args.no_graphs else 1))
+        kw = {}
+        if args.fdm_tile >= 0:
+            kw = {"fdm_tile_f32": args.fdm_tile} if prec == hpg.HPG_MIXED else {"fdm_tile_f64": args.fdm_tile}
+        ps = [hpg.from_workload(ctx, w, hpg.default_params(precision=prec, graphs=0 if args.no_graphs else 1, **kw))
               for _ in range(count)]
         return ps
 
@@ -378,15 +397,11 @@ def main():
         torch.cuda.synchronize()
         barrier()
         clk = sampler.stop() if sampler else None
-        total_ms = sum(times)
-        if dist is not None:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(times), dist, torch, "cuda")
         st = ps[0].stats()
         dofs = ps[0].n_u + ps[0].n_psi
         kry = sum(P.stats()["krylov_total"] for P in ps)
-        res = dict(value=world * count * args.steps / (total_ms / 1000.0), ms_per_step=total_ms / args.steps,
+        res = dict(value=replica_throughput(count * args.steps, world, total_ms), ms_per_step=total_ms / args.steps,
                    batch=count, newton=st["newton_total"], krylov=st["krylov_total"], refine=st["refine_total"],
                    launches=sum(P.stats()["kernel_launches"] for P in ps),
                    dof_krylov_per_s=world * dofs * kry / (total_ms / args.steps / 1000.0), clocks=clk,

@@ -5,6 +5,7 @@
 // inverse of A_alpha, and GMRES.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <tuple>
 #include <cfloat>
 #include <cmath>
@@ -695,6 +696,10 @@ __global__ void k_factor(Geo<T> g, const T* __restrict__ gw, T alpha_inv, T beta
     }
 }
 
+// the factorisation workspace of a cell stays in shared memory up to this size
+// (227 KB per block on this GPU, less the kernel's static shared memory)
+constexpr size_t kFactorSmemMax = 225 * 1024;
+
 static size_t factor_ws_elems(int n, int d, int nb, int nc) {
     size_t nloc = 1, nbuf_b = 1;
     for (int t = 0; t < d; ++t) nloc *= n;
@@ -706,7 +711,7 @@ size_t factor_smem_bytes(int nb, int elem) { return (size_t)nb * nb * elem; }
 
 size_t factor_workspace_elems(int n, int d, int nb, int nc, long long Nc, int elem) {
     const size_t elems = factor_ws_elems(n, d, nb, nc);
-    return elems * elem <= 200 * 1024 ? 0 : elems * (size_t)Nc;
+    return elems * elem <= kFactorSmemMax ? 0 : elems * (size_t)Nc;
 }
 
 template <typename T>
@@ -714,7 +719,7 @@ cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double bet
                           int* flag, T* gwork, cudaStream_t s) {
     const size_t elems = factor_ws_elems(g.n, g.d, (int)g.nb, g.ncomp);
     const size_t bytes = elems * sizeof(T);
-    const int use_smem = bytes <= 200 * 1024;
+    const int use_smem = bytes <= kFactorSmemMax;
     if (!use_smem && !gwork) return cudaErrorInvalidValue;
     k_factor<T><<<(unsigned)g.Nc, 256, use_smem ? bytes : 0, s>>>(g, gw, (T)(1.0 / alpha), (T)beta, Sinv, dump,
                                                                  flag, gwork, use_smem);
@@ -1617,14 +1622,27 @@ __device__ __forceinline__ void cellop_body(const Geo<T>& g, const T* __restrict
     }
 }
 
+// Cells are processed by groups of gs threads, cpb cells per block (in the fused Newton
+// apply gs = min(nb, 256) and cpb = 256 / gs, so that few lanes idle when nb is not a
+// multiple of 32, 49 for n = 7); threads left over after cpb groups run on a scratch
+// slot, inactive.
+inline void cell_groups(long long nb, int* gs, int* cpb) {
+    *gs = (int)(nb < 256 ? (nb > 0 ? nb : 1) : 256);
+    *cpb = 256 / *gs;
+}
+
 template <int D, typename T, typename Tz, typename Tt, typename Tout>
-__global__ void k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* __restrict__ z,
-                         const Tt* __restrict__ t, T sB, T sD, Tout* __restrict__ out, IterCtl ctl) {
-    extern __shared__ unsigned char smraw[];
+__global__ void __launch_bounds__(256)
+    k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* __restrict__ z, const Tt* __restrict__ t, T sB,
+             T sD, Tout* __restrict__ out, IterCtl ctl, int gs, int cpb) {
+    extern __shared__ __align__(16) unsigned char smraw[];
     if (ctl.skip && *ctl.skip) return;
     Tout* outp = out + (ctl.jptr ? (long long)(*ctl.jptr + 1) * ctl.jstride : 0LL);
-    cellop_body<D, T, Tz, Tt, Tout>(g, gw, beta, z, t, sB, sD, outp, blockIdx.x, true, threadIdx.x, blockDim.x,
-                                    reinterpret_cast<T*>(smraw));
+    const int grp = threadIdx.x / gs, lt = threadIdx.x - grp * gs;
+    const long long cell = (long long)blockIdx.x * cpb + grp;
+    const size_t per = (size_t)(3 * g.nb + g.n * g.n);
+    cellop_body<D, T, Tz, Tt, Tout>(g, gw, beta, z, t, sB, sD, outp, cell, grp < cpb && cell < g.Nc, lt, gs,
+                                    reinterpret_cast<T*>(smraw) + (size_t)(grp < cpb ? grp : cpb) * per);
 }
 
 // One launch for G x: blocks [0, nu) are u-row tiles (alpha A x_u + B x_psi),
@@ -1633,7 +1651,7 @@ __global__ void k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* _
 template <int D>
 __global__ void __launch_bounds__(256)
     k_newton_fused(Geo<double> g, const double* __restrict__ gw, double alpha, double beta,
-                   const double* __restrict__ x, double* __restrict__ y, int nu, int cpb) {
+                   const double* __restrict__ x, double* __restrict__ y, int nu, int gs, int cpb) {
     extern __shared__ __align__(16) unsigned char smraw[];
     // u-row tiles and cell groups alternate in block order, so that the block
     // scheduler hands every SM a similar mix of the two kinds of work
@@ -1648,23 +1666,32 @@ __global__ void __launch_bounds__(256)
             g, alpha, x, 1.0, x + g.Nu0, nullptr, nullptr, nullptr, nullptr, nullptr, y, idx, smraw);
         return;
     }
-    const int grp = threadIdx.x / (256 / cpb), lt = threadIdx.x % (256 / cpb);
+    const int grp = threadIdx.x / gs, lt = threadIdx.x - grp * gs;
     const long long cell = (long long)idx * cpb + grp;
     const size_t per = (size_t)(3 * g.nb + g.n * g.n);
     cellop_body<D, double, double, double, double>(g, gw, beta, x + g.Nu0, x, 1.0, -1.0, y + g.Nu0, cell,
-                                                   cell < g.Nc, lt, 256 / cpb,
-                                                   reinterpret_cast<double*>(smraw) + grp * per);
+                                                   grp < cpb && cell < g.Nc, lt, gs,
+                                                   reinterpret_cast<double*>(smraw) +
+                                                       (size_t)(grp < cpb ? grp : cpb) * per);
 }
 
 template <typename T, typename Tout>
 cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T* z, const T* t, Tout* w,
                               cudaStream_t s, IterCtl ctl) {
-    const size_t smem = (size_t)(3 * g.nb + g.n * g.n) * sizeof(T);
-    const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
+    // one cell per block here (measured faster than several cells per block for the
+    // FP32 and FP64 Krylov-loop applies); the fused Newton apply groups cells
+    const int gs = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256), cpb = 1;
+    const size_t smem = (size_t)(cpb + 1) * (3 * g.nb + g.n * g.n) * sizeof(T);
+    const unsigned blocks = (unsigned)g.Nc;
+    static std::once_flag big_smem;
+    std::call_once(big_smem, [] {
+        cudaFuncSetAttribute(k_cellop<2, T, T, T, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_cellop<3, T, T, T, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
     if (g.d == 2)
-        k_cellop<2, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl);
+        k_cellop<2, T, T, T, Tout><<<blocks, gs, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb);
     else
-        k_cellop<3, T, T, T, Tout><<<(unsigned)g.Nc, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl);
+        k_cellop<3, T, T, T, Tout><<<blocks, gs, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb);
     note_launch();
     return cudaGetLastError();
 }
@@ -1684,13 +1711,14 @@ __global__ void k_newton_u(Geo<double> g, double alpha, const double* __restrict
 cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
                                 const double* x, double* y, cudaStream_t s, cudaStream_t, cudaEvent_t, cudaEvent_t) {
     const int nu = (int)utile_blocks(g.d, g.n1);
-    const int cpb = g.nb <= 64 ? 4 : 1;
+    int gs = 0, cpb = 0;
+    cell_groups(g.nb, &gs, &cpb);
     const int nc = (int)((g.Nc + cpb - 1) / cpb);
     const size_t per = (size_t)(3 * g.nb + g.n * g.n) * sizeof(double);
     const size_t st = g.d == 2 ? sizeof(StenTile<double, UTileMax<2>::v>) : sizeof(StenTile<double, UTileMax<3>::v>);
-    const size_t smem = std::max(st, cpb * per);
-    if (g.d == 2) k_newton_fused<2><<<nu + nc, 256, smem, s>>>(g, gw, alpha, beta, x, y, nu, cpb);
-    else k_newton_fused<3><<<nu + nc, 256, smem, s>>>(g, gw, alpha, beta, x, y, nu, cpb);
+    const size_t smem = std::max(st, (cpb + 1) * per);
+    if (g.d == 2) k_newton_fused<2><<<nu + nc, 256, smem, s>>>(g, gw, alpha, beta, x, y, nu, gs, cpb);
+    else k_newton_fused<3><<<nu + nc, 256, smem, s>>>(g, gw, alpha, beta, x, y, nu, gs, cpb);
     note_launch();
     return cudaGetLastError();
 }
@@ -2181,8 +2209,8 @@ void configure_kernels() {
     configure_tiles<double>();
     cudaFuncSetAttribute(k_gemm_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
     cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
-    cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_newton_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_newton_fused<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
