@@ -331,6 +331,7 @@ hpg_status hpg_solve(hpg_ctx* ctx, int pid) {
     hpg_status s = cuda_ok(ctx);
     if (s != HPG_OK) return s;
     GUARD_BEGIN
+    ctx->err.clear();
     s = ready(ctx, P);
     if (s != HPG_OK) return s;
     P->host_result = false;

@@ -919,8 +919,18 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
         int it = 0;
         while (true) {
             if (flag & 1) { status = HPG_ERR_NONFINITE; break; }
+            if (!std::isfinite(normF)) {
+                status = HPG_ERR_NONFINITE;
+                ctx->err = "non-finite Newton residual in proximal step " + std::to_string(k + 1);
+                break;
+            }
             if (normF <= P.params.newton_tol) break;
-            if (it >= P.params.newton_max) { status = HPG_ERR_NEWTON_CAP; break; }
+            if (it >= P.params.newton_max) {
+                status = HPG_ERR_NEWTON_CAP;
+                ctx->err = "Newton cap reached in proximal step " + std::to_string(k + 1) + " (||F|| = " +
+                           std::to_string(normF) + ")";
+                break;
+            }
             if (P.params.precision == HPG_FP64) CKS(factor_T<double>(ctx, P, alpha, nullptr));
             else CKS(factor_T<float>(ctx, P, alpha, nullptr));
             int its = 0, sweeps = 0;

@@ -228,6 +228,7 @@ class Problem:
     """One hpG problem in a Context (argument marshalling over the C ABI)."""
 
     def __init__(self, ctx, dim, lo, hi, cells, p, kind):
+        self.pid = None
         self.ctx, self.L = ctx, ctx.L
         pid = C.c_int()
         lo = _f64(lo)
