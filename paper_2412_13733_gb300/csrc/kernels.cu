@@ -651,24 +651,40 @@ __global__ void k_factor(Geo<T> g, const T* __restrict__ gw, T alpha_inv, T beta
     __syncthreads();
     if (dump)
         for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) dump[cell * nb * nb + o] = (double)A[o];
-    // Cholesky (right-looking), lower triangle
+    // Cholesky (right-looking), lower triangle; two barriers per column: every thread
+    // takes the pivot's square root itself (the pivot is final after the previous
+    // step) and scales its part of column k; the trailing update runs warps over rows
+    // and lanes over columns j <= i (no index division, no idle upper half)
     __shared__ int bad;
     if (threadIdx.x == 0) bad = 0;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
     __syncthreads();
+    __shared__ T piv;
     for (int k = 0; k < nb; ++k) {
-        if (threadIdx.x == 0) {
+        T lkk;
+        if constexpr (sizeof(T) == 8) {
+            // FP64 square roots are costly on this GPU's FP64 pipe: one thread takes it
+            if (threadIdx.x == 0) {
+                T pv = A[(size_t)k * nb + k];
+                if (!(pv > T(0))) { bad = 1; pv = T(1); }
+                piv = sqrt(pv);
+            }
+            __syncthreads();
+            lkk = piv;
+        } else {
             T pv = A[(size_t)k * nb + k];
-            if (!(pv > T(0))) { bad = 1; pv = T(1); }
-            A[(size_t)k * nb + k] = sqrt(pv);
+            if (!(pv > T(0))) {
+                if (threadIdx.x == 0) bad = 1;
+                pv = T(1);
+            }
+            lkk = sqrt(pv);
         }
-        __syncthreads();
-        const T lkk = A[(size_t)k * nb + k];
         for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) A[(size_t)i * nb + k] /= lkk;
         __syncthreads();
-        const int rem = nb - k - 1;
-        for (int o = threadIdx.x; o < rem * rem; o += blockDim.x) {
-            const int i = k + 1 + o / rem, j = k + 1 + o % rem;
-            if (j <= i) A[(size_t)i * nb + j] -= A[(size_t)i * nb + k] * A[(size_t)j * nb + k];
+        if (threadIdx.x == 0) A[(size_t)k * nb + k] = lkk;
+        for (int i = k + 1 + ty; i < nb; i += nty) {
+            const T lik = A[(size_t)i * nb + k];
+            for (int j = k + 1 + tx; j <= i; j += 32) A[(size_t)i * nb + j] -= lik * A[(size_t)j * nb + k];
         }
         __syncthreads();
     }
