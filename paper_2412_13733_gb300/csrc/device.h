@@ -108,13 +108,10 @@ template <typename T, typename Tout>
 cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T* z, const T* t, Tout* w,
                               cudaStream_t s, IterCtl ctl = IterCtl{});
 
-// FP64 matrix-free Newton apply y = G x (eq. pG-matrix) split in two kernels.
+// FP64 matrix-free Newton apply y = G x (eq. pG-matrix), one fused launch.
 cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
-                                const double* x, double* y, cudaStream_t s, cudaStream_t s2 = nullptr,
-                                cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
+                                const double* x, double* y, cudaStream_t s);
 
-// y = A x (interior), FP64 (used by tests of the stiffness inverse).
-cudaError_t launch_aapply(const Geo<double>& g, const double* x, double* y, cudaStream_t s);
 
 // ---- vector helpers (FP64 unless typed)
 template <typename Tin, typename Tout>

@@ -71,79 +71,6 @@ __device__ __forceinline__ T gather_u(const Sten<T>* const* S, const int* r, con
     return s;
 }
 
-// (A x)[r] with A = sum_k (x)_j (j == k ? A_j : M_j)
-template <int D, typename T, typename Tx>
-__device__ __forceinline__ T apply_A_row(const Geo<T>& g, const int* r, const Tx* x) {
-    T s = T(0);
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        const Sten<T>* S[kMaxDim];
-#pragma unroll
-        for (int j = 0; j < D; ++j) S[j] = (j == k) ? &g.A[j] : &g.M[j];
-        s += gather_u<D, T, Tx>(S, r, g.n1, x);
-    }
-    return s;
-}
-
-// (B z)[r] (psi -> interior u).  Column packing: (cell << 8) | k.
-// If z2 != nullptr the input is z - z2 (used for psi - psi_prev).
-template <int D, typename T, typename Tz>
-__device__ __forceinline__ T apply_B_row(const Geo<T>& g, const int* r, const Tz* z, const Tz* z2) {
-    T s = T(0);
-    const int n = g.n;
-    for (int comp = 0; comp < g.ncomp; ++comp) {
-        const Sten<T>* S[kMaxDim];
-#pragma unroll
-        for (int j = 0; j < D; ++j) S[j] = (g.kind == HPG_GRADIENT && j == comp) ? &g.Bd[j] : &g.B[j];
-        int cnt[kMaxDim];
-#pragma unroll
-        for (int j = 0; j < D; ++j) cnt[j] = S[j]->cnt[r[j]];
-        if (D == 2) {
-            for (int e1 = 0; e1 < cnt[1]; ++e1) {
-                const int p1 = S[1]->col[(size_t)r[1] * kEll + e1];
-                const T v1 = S[1]->val[(size_t)r[1] * kEll + e1];
-                const int c1 = p1 >> 8, k1 = p1 & 255;
-                T t = T(0);
-                for (int e0 = 0; e0 < cnt[0]; ++e0) {
-                    const int p0 = S[0]->col[(size_t)r[0] * kEll + e0];
-                    const int c0 = p0 >> 8, k0 = p0 & 255;
-                    const long long cell = c0 + (long long)g.m[0] * c1;
-                    const long long idx = (cell * g.ncomp + comp) * g.nloc + k0 + n * k1;
-                    T zv = (T)z[idx];
-                    if (z2) zv -= (T)z2[idx];
-                    t += S[0]->val[(size_t)r[0] * kEll + e0] * zv;
-                }
-                s += v1 * t;
-            }
-        } else {
-            for (int e2 = 0; e2 < cnt[2]; ++e2) {
-                const int p2 = S[2]->col[(size_t)r[2] * kEll + e2];
-                const T v2 = S[2]->val[(size_t)r[2] * kEll + e2];
-                const int c2 = p2 >> 8, k2 = p2 & 255;
-                T t2 = T(0);
-                for (int e1 = 0; e1 < cnt[1]; ++e1) {
-                    const int p1 = S[1]->col[(size_t)r[1] * kEll + e1];
-                    const T v1 = S[1]->val[(size_t)r[1] * kEll + e1];
-                    const int c1 = p1 >> 8, k1 = p1 & 255;
-                    T t = T(0);
-                    for (int e0 = 0; e0 < cnt[0]; ++e0) {
-                        const int p0 = S[0]->col[(size_t)r[0] * kEll + e0];
-                        const int c0 = p0 >> 8, k0 = p0 & 255;
-                        const long long cell = c0 + (long long)g.m[0] * (c1 + (long long)g.m[1] * c2);
-                        const long long idx = (cell * g.ncomp + comp) * g.nloc + k0 + n * (k1 + n * k2);
-                        T zv = (T)z[idx];
-                        if (z2) zv -= (T)z2[idx];
-                        t += S[0]->val[(size_t)r[0] * kEll + e0] * zv;
-                    }
-                    t2 += v1 * t;
-                }
-                s += v2 * t2;
-            }
-        }
-    }
-    return s;
-}
-
 // (B^T x)[cell, comp, k] (interior u -> psi)
 template <int D, typename T, typename Tx>
 __device__ __forceinline__ T apply_BT_entry(const Geo<T>& g, const int* cm, int comp, const int* km, const Tx* x) {
@@ -480,26 +407,6 @@ cudaError_t launch_project(const Geo<double>& g, const double* phiq, double* phi
 }
 
 // ================================================================== residual
-template <int D>
-__global__ void k_residual_u(Geo<double> g, const double* __restrict__ u, const double* __restrict__ psi,
-                             const double* __restrict__ psi_prev, const double* __restrict__ rA,
-                             const double* __restrict__ bf, double alpha, double* __restrict__ F,
-                             double* __restrict__ part) {
-    __shared__ double sh[32];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double v = 0.0;
-    if (i < g.Nu0) {
-        int r[kMaxDim];
-        decompose(i, D, g.n1, r);
-        const double Au = apply_A_row<D, double, double>(g, r, u);
-        const double Bp = apply_B_row<D, double, double>(g, r, psi, psi_prev);
-        v = alpha * (Au + rA[i] - bf[i]) + Bp;
-        F[i] = v;
-    }
-    v = block_sum(v * v, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
-}
-
 template <int D>
 __global__ void k_residual_psi(Geo<double> g, const double* __restrict__ u, const double* __restrict__ eg,
                                const double* __restrict__ rB, const double* __restrict__ phiz,
@@ -859,16 +766,6 @@ cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z
 }
 
 // ==================================================================== B, B^T
-template <int D, typename T, typename Tin, typename Tout>
-__global__ void k_bapply(Geo<T> g, const Tin* __restrict__ z, Tout* __restrict__ y, const int* skip) {
-    if (skip && *skip) return;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.Nu0) return;
-    int r[kMaxDim];
-    decompose(i, D, g.n1, r);
-    y[i] = (Tout)apply_B_row<D, T, Tin>(g, r, z, (const Tin*)nullptr);
-}
-
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s, const int* skip) {
     if (g.d == 2)
@@ -900,26 +797,6 @@ cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t 
     const unsigned b = (unsigned)((g.Npsi + 255) / 256);
     if (g.d == 2) k_btapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y);
     else k_btapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y);
-    note_launch();
-    return cudaGetLastError();
-}
-
-template <int D>
-__global__ void k_aapply(Geo<double> g, const double* __restrict__ x, double* __restrict__ y) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.Nu0) return;
-    int r[kMaxDim];
-    decompose(i, D, g.n1, r);
-    y[i] = apply_A_row<D, double, double>(g, r, x);
-}
-
-cudaError_t launch_aapply(const Geo<double>& g, const double* x, double* y, cudaStream_t s) {
-    if (g.d == 2)
-        k_urow<2, double, double, double, true, false, false><<<utile_grid<2>(g.n1), 256, 0, s>>>(
-            g, 1.0, x, 0.0, (const double*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, y, nullptr);
-    else
-        k_urow<3, double, double, double, true, false, false><<<utile_grid<3>(g.n1), 256, 0, s>>>(
-            g, 1.0, x, 0.0, (const double*)nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, y, nullptr);
     note_launch();
     return cudaGetLastError();
 }
@@ -1712,20 +1589,9 @@ cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T
     return cudaGetLastError();
 }
 
-// y_u = alpha A x_u + B x_psi (interior rows)
-template <int D>
-__global__ void k_newton_u(Geo<double> g, double alpha, const double* __restrict__ xu,
-                           const double* __restrict__ xp, double* __restrict__ yu) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.Nu0) return;
-    int r[kMaxDim];
-    decompose(i, D, g.n1, r);
-    yu[i] = alpha * apply_A_row<D, double, double>(g, r, xu) + apply_B_row<D, double, double>(g, r, xp, nullptr);
-}
-
 // G x (eq. pG-matrix) in one launch: u-row tiles and psi cells share the SMs.
 cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
-                                const double* x, double* y, cudaStream_t s, cudaStream_t, cudaEvent_t, cudaEvent_t) {
+                                const double* x, double* y, cudaStream_t s) {
     const int nu = (int)utile_blocks(g.d, g.n1);
     int gs = 0, cpb = 0;
     cell_groups(g.nb, &gs, &cpb);

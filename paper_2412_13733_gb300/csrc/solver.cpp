@@ -100,9 +100,6 @@ void free_device(Problem& P, cudaStream_t s) {
     P.D.bench_graphs.clear();
     for (void* p : P.D.allocs) cudaFreeAsync(p, s);
     P.D.allocs.clear();
-    if (P.D.aux) { cudaStreamSynchronize(P.D.aux); cudaStreamDestroy(P.D.aux); }
-    if (P.D.ev_fork) cudaEventDestroy(P.D.ev_fork);
-    if (P.D.ev_join) cudaEventDestroy(P.D.ev_join);
     for (auto e : P.timer.pool) cudaEventDestroy(e);
     P.timer.pool.clear();
     P.D = DevState{};
@@ -281,13 +278,6 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     }
     D.h_scal = P.pinned_scal;
     D.h_iflag = P.pinned_iflag;
-    if (cudaStreamCreateWithFlags(&D.aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&D.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&D.ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        free_device(P, s);
-        ctx->err = "stream/event creation failed";
-        return HPG_ERR_CUDA;
-    }
     // geometry views
     auto fill = [&](auto& g, auto sel) {
         g.d = d; g.n = H.n; g.ncomp = H.ncomp; g.kind = H.kind;
@@ -778,7 +768,7 @@ static hpg_status fgmres_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
         double* zj = D.fZ + (long long)j * N;
         double* w = D.fV + (long long)(j + 1) * N;
         CKS(fg_precond(ctx, P, alpha, vj, zj));
-        CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, zj, w, s, D.aux, D.ev_fork, D.ev_join));
+        CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, zj, w, s));
         double* col = H.data() + (size_t)j * (m + 1);
         for (int pass = 0; pass < 2; ++pass) {
             CKS(fg_dots(ctx, P, D.fV, j + 1, w, h));
@@ -863,7 +853,7 @@ static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
         if (f64 && !capped) break;      // FP64 GMRES residual is the true Newton-system residual
         {
             Scope sc(P.timer, HPG_K_NEWTON_APPLY, s);
-            CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, delta, D.r, s, D.aux, D.ev_fork, D.ev_join));
+            CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, delta, D.r, s));
         }
         {
             Scope sc(P.timer, HPG_K_UPDATE, s);
@@ -1069,8 +1059,7 @@ hpg_status op_apply_newton(hpg_ctx* ctx, Problem& P, const double* x, double* y)
     DevState& D = P.D;
     const size_t Nx = P.H.Nu0 + P.H.Npsi;
     CK(cudaMemcpy(D.r, x, Nx * sizeof(double), cudaMemcpyHostToDevice));
-    CK(launch_newton_apply(D.gd, D.gw, P.state_alpha, P.params.beta, D.r, D.dcorr, ctx->stream, D.aux, D.ev_fork,
-                           D.ev_join));
+    CK(launch_newton_apply(D.gd, D.gw, P.state_alpha, P.params.beta, D.r, D.dcorr, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(y, D.dcorr, Nx * sizeof(double), cudaMemcpyDeviceToHost));
     return HPG_OK;
@@ -1196,7 +1185,7 @@ static hpg_status enqueue_kernel(hpg_ctx* ctx, Problem& P, int cls, bool f32, do
             else CK(launch_schur_rest<double, double>(D.gd, D.gwl, P.params.beta, D.zp_d, D.tu2_d, D.xs, s));
             break;
         case HPG_K_NEWTON_APPLY:
-            CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, D.x, D.r, s, D.aux, D.ev_fork, D.ev_join));
+            CK(launch_newton_apply(D.gd, D.gw, alpha, P.params.beta, D.x, D.r, s));
             break;
         case HPG_K_FACTOR:
             if (f32) CK(launch_factor<float>(D.gf, D.gwf, alpha, P.params.beta, D.Sinv_f, nullptr, D.flag, D.fwork_f, s));

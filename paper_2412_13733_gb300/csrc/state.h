@@ -44,8 +44,6 @@ struct DevState {
     double* fwork_d = nullptr;                   // factor workspace when blocks exceed shared memory
     float* fwork_f = nullptr;
     double* alpha_dev = nullptr;                 // alpha of the current proximal step (device)
-    cudaStream_t aux = nullptr;                  // helper stream for concurrent halves of G x
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gmres_graph[2] = {nullptr, nullptr};   // captured GMRES chunk per precision
     long long graph_kernels[2] = {0, 0};                    // kernels in one loop body
     bool gmres_graph_failed[2] = {false, false};            // conditional graphs unsupported
