@@ -60,7 +60,8 @@ cudaError_t launch_eval(const Geo<double>& g, const double* psi, const double* p
 
 // phiz = (phi, zeta) from phi at the latent Gauss points (obstacle kinds).
 cudaError_t launch_project(const Geo<double>& g, const double* phiq, double* phiz, cudaStream_t s);
-// Number of kernels launched (or replayed in graphs) by this library since load.
+// Number of kernels launched (or replayed in graphs) by this library from the calling
+// host thread since it started.
 long long kernel_launch_count();
 void add_kernel_launches(long long n);
 

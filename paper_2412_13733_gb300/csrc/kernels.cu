@@ -16,8 +16,10 @@ namespace hpg {
 
 namespace {
 
-std::atomic<long long> g_launches{0};
-inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// kernels launched (or replayed from graphs) by the calling host thread: a solve
+// runs on one host thread, also when several solves are in flight on others
+thread_local long long t_launches = 0;
+inline void note_launch() { ++t_launches; }
 
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* sh) {
@@ -110,7 +112,7 @@ __device__ __forceinline__ void sf_pass(const T* in, T* out, const T* mat, bool 
 
 }  // namespace
 
-long long kernel_launch_count() { return g_launches.load(std::memory_order_relaxed); }
+long long kernel_launch_count() { return t_launches; }
 
 // ============================================================ tiled u-row applies
 // y[i] over interior u-dofs i of  cA * (A x)[i] + cB * (B z)[i]  (+ residual terms),
@@ -293,7 +295,7 @@ static long long utile_blocks(int d, const int* n1) {
 }
 
 
-void add_kernel_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void add_kernel_launches(long long n) { t_launches += n; }
 
 // ====================================================================== eval
 // Obstacle: g_q = w_q |J| exp(-psi(x_q)), eg = V^T g per cell (Section 5, Quadrature).
