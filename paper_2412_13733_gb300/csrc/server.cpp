@@ -75,6 +75,8 @@ size_t estimate_device_bytes(const Problem& P) {
     b += factor_workspace_elems(H.n, H.d, (int)H.nb, H.ncomp, (long long)H.Nc, 4) * 4;
     b += (kmax + 1) * Npsi * 8;                          // Krylov basis
     b += (kmax + 1) * kmax * 8 + (size_t)gmres_dot_blocks((long long)Npsi) * (kmax + 2) * 8 + (kmax + 2) * 8;
+    if (P.params.strategy != HPG_SCHUR)                   // flexible GMRES on G: V, Z, partials
+        b += (2 * kmax + 1) * Nx * 8 + (kmax + 1) * (size_t)fg_chunks((long long)Nx) * 8 + Npsi * 8;
     return b + (1u << 20);
 }
 
