@@ -14,7 +14,25 @@ struct Sten {
     const int* cnt;
     const int* col;
     const T* val;
+    const int* lcol;   // column as a position in the row tile's column list (TileCols), or null
 };
+
+// Columns referenced by the rows of each row tile of one axis (tiles of the tiled
+// u-row kernels): count[t] sorted entries at list[t * cap].  The u-row kernels stage
+// the values at these columns (a box per tile) in shared memory before the gathers.
+struct TileCols {
+    const int* list;
+    const int* count;
+    int cap;
+};
+
+// Row-tile extent of the tiled u-row kernels along axis `axis` for dimension d.
+int utile_extent(int d, int axis);
+template <typename T>
+struct Geo;
+// Whether the value boxes of the tiled u-row kernels fit their shared-memory budget.
+template <typename T>
+bool urow_boxes_fit(const Geo<T>& g);
 
 // Everything a kernel needs to know about one problem, for compute type T.
 template <typename T>
@@ -34,6 +52,9 @@ struct Geo {
     const T* V[kMaxDim];                      // n1 x n1 fast-diagonalisation eigenvectors
     const T* lam[kMaxDim];                    // n1 eigenvalues
     int gemm_cfg;                             // tile variant of the FDM passes (autotuned)
+    TileCols tu[kMaxDim];                     // u columns of the A, M stencils per row tile
+    TileCols tp[kMaxDim];                     // psi columns (packed) of the B, Bd stencils
+    int staged;                               // 1: the u-row kernels stage value boxes in shared memory
 };
 
 // Number of values stored per Gauss point by the evaluation kernel:

@@ -147,8 +147,27 @@ struct UTileMax {
     static constexpr int v = T0 > T1 ? (T0 > T2 ? T0 : T2) : (T1 > T2 ? T1 : T2);
 };
 
+// Value boxes of a u-row tile (staged path): the x values at the tile's u-column
+// lists (capX = prod cap of tu) and, per component, the psi values at its psi-column
+// lists (capZ = prod cap of tp), both converted to T.
+template <typename T>
+__host__ __device__ inline long long urow_box_x(const Geo<T>& g) {
+    long long c = 1;
+    for (int j = 0; j < g.d; ++j) c *= g.tu[j].cap;
+    return c;
+}
+template <typename T>
+__host__ __device__ inline long long urow_box_z(const Geo<T>& g) {
+    long long c = 1;
+    for (int j = 0; j < g.d; ++j) c *= g.tp[j].cap;
+    return c;
+}
+
 // Body of the tiled u-row apply for the tile with linear index `blin`
-// (x-tiles fastest); `stp` points to the block's shared StenTile.
+// (x-tiles fastest); `stp` points to the block's shared StenTile, followed (staged
+// path) by the tile's value boxes.  Staged: the x and psi values the tile's rows
+// touch are first copied into shared memory (all loads in flight together, one
+// barrier), and the gathers read the boxes through the stencils' tile-local columns.
 template <int D, typename T, typename Tx, typename Tz, bool HAS_A, bool HAS_B, bool RESID>
 __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __restrict__ x, T cB,
                                             const Tz* __restrict__ z, const Tz* __restrict__ z2,
@@ -158,27 +177,67 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
     constexpr int T0 = UTile<D>::T0, T1 = UTile<D>::T1, T2 = UTile<D>::T2;
     constexpr int TMAX = UTileMax<D>::v;
     StenTile<T, TMAX>& st = *reinterpret_cast<StenTile<T, TMAX>*>(stp);
+    T* xs = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(stp) + sizeof(StenTile<T, TMAX>));
+    T* zs = xs + (HAS_A ? urow_box_x(g) : 0);
+    const long long capZ = urow_box_z(g);
     __shared__ double sh[32];
     const int tile[kMaxDim] = {T0, T1, T2};
     const int gx = (g.n1[0] + T0 - 1) / T0, gy = (g.n1[1] + T1 - 1) / T1;
-    const int org[kMaxDim] = {(blin % gx) * T0, ((blin / gx) % gy) * T1, (blin / (gx * gy)) * T2};
+    const int tix[kMaxDim] = {blin % gx, (blin / gx) % gy, blin / (gx * gy)};
+    const int org[kMaxDim] = {tix[0] * T0, tix[1] * T1, tix[2] * T2};
     const bool grad = g.kind == HPG_GRADIENT;
-    // stage the stencil rows of this tile
+    const bool staged = g.staged != 0;
+    // stage the stencil rows of this tile (tile-local columns on the staged path)
     for (int op = 0; op < NOPS; ++op) {
         if ((op == OP_A || op == OP_M) && !HAS_A) continue;
         if (op == OP_B && !HAS_B) continue;
         if (op == OP_BD && !(HAS_B && grad)) continue;
         for (int j = 0; j < D; ++j) {
             const Sten<T>& S = op_of(g, op, j);
+            const int* cols = staged ? S.lcol : S.col;
             for (int e = threadIdx.x; e < tile[j] * kEll; e += blockDim.x) {
                 const int l = e / kEll, k = e % kEll, r = org[j] + l;
                 if (r < g.n1[j]) {
-                    st.col[op][j][l][k] = S.col[(size_t)r * kEll + k];
+                    st.col[op][j][l][k] = cols[(size_t)r * kEll + k];
                     st.val[op][j][l][k] = S.val[(size_t)r * kEll + k];
                     if (k == 0) st.cnt[op][j][l] = S.cnt[r];
                 } else if (k == 0) {
                     st.cnt[op][j][l] = 0;
                 }
+            }
+        }
+    }
+    int L[kMaxDim] = {1, 1, 1}, Pn[kMaxDim] = {1, 1, 1};
+    if (staged) {
+        const int n1x = g.n1[0], n1y = g.n1[1];
+        if (HAS_A) {
+            for (int j = 0; j < D; ++j) L[j] = g.tu[j].count[tix[j]];
+            const int* ux = g.tu[0].list + (size_t)tix[0] * g.tu[0].cap;
+            const int* uy = g.tu[1].list + (size_t)tix[1] * g.tu[1].cap;
+            const int* uz = D == 3 ? g.tu[2].list + (size_t)tix[2] * g.tu[2].cap : nullptr;
+            const int tot = L[0] * L[1] * L[2];
+            for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+                const int lx = e % L[0], ly = (e / L[0]) % L[1], lz = e / (L[0] * L[1]);
+                const long long zz = D == 3 ? uz[lz] : 0;
+                xs[e] = (T)x[(zz * n1y + uy[ly]) * n1x + ux[lx]];
+            }
+        }
+        if (HAS_B) {
+            for (int j = 0; j < D; ++j) Pn[j] = g.tp[j].count[tix[j]];
+            const int* px = g.tp[0].list + (size_t)tix[0] * g.tp[0].cap;
+            const int* py = g.tp[1].list + (size_t)tix[1] * g.tp[1].cap;
+            const int* pz = D == 3 ? g.tp[2].list + (size_t)tix[2] * g.tp[2].cap : nullptr;
+            const int tot = Pn[0] * Pn[1] * Pn[2];
+            const int n = g.n;
+            for (int e = threadIdx.x; e < tot * g.ncomp; e += blockDim.x) {
+                const int comp = e / tot, le = e - comp * tot;
+                const int lx = le % Pn[0], ly = (le / Pn[0]) % Pn[1], lz = le / (Pn[0] * Pn[1]);
+                const int p0 = px[lx], p1 = py[ly], p2 = D == 3 ? pz[lz] : 0;
+                const long long cell = (p0 >> 8) + (long long)g.m[0] * ((p1 >> 8) + (long long)g.m[1] * (p2 >> 8));
+                const long long idx = (cell * g.ncomp + comp) * g.nloc + (p0 & 255) + n * ((p1 & 255) + n * (p2 & 255));
+                T v = (T)z[idx];
+                if (z2) v -= (T)z2[idx];
+                zs[(long long)comp * capZ + le] = v;
             }
         }
     }
@@ -193,6 +252,8 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
         i = r0 + (long long)n1x * (r1 + (long long)n1y * r2);
         T acc = T(0);
         if (HAS_A) {
+            // x values: the staged box [lz][ly][lx] or the global vector
+            const long long sy = staged ? L[0] : n1x, sz = staged ? (long long)L[0] * L[1] : (long long)n1x * n1y;
             T sa = T(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -200,20 +261,29 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
                 const int c0 = st.cnt[o0][0][l0], c1 = st.cnt[o1][1][l1];
                 if (D == 2) {
                     for (int e1 = 0; e1 < c1; ++e1) {
-                        const long long base = (long long)st.col[o1][1][l1][e1] * n1x;
+                        const long long base = (long long)st.col[o1][1][l1][e1] * sy;
                         T t = T(0);
-                        for (int e0 = 0; e0 < c0; ++e0) t += st.val[o0][0][l0][e0] * (T)x[base + st.col[o0][0][l0][e0]];
+                        if (staged)
+                            for (int e0 = 0; e0 < c0; ++e0) t += st.val[o0][0][l0][e0] * xs[base + st.col[o0][0][l0][e0]];
+                        else
+                            for (int e0 = 0; e0 < c0; ++e0)
+                                t += st.val[o0][0][l0][e0] * (T)x[base + st.col[o0][0][l0][e0]];
                         sa += st.val[o1][1][l1][e1] * t;
                     }
                 } else {
                     const int c2 = st.cnt[o2][2][l2];
                     for (int e2 = 0; e2 < c2; ++e2) {
-                        const long long b2 = (long long)st.col[o2][2][l2][e2] * n1y;
+                        const long long b2 = (long long)st.col[o2][2][l2][e2] * sz;
                         T t2 = T(0);
                         for (int e1 = 0; e1 < c1; ++e1) {
-                            const long long base = (b2 + st.col[o1][1][l1][e1]) * n1x;
+                            const long long base = b2 + (long long)st.col[o1][1][l1][e1] * sy;
                             T t = T(0);
-                            for (int e0 = 0; e0 < c0; ++e0) t += st.val[o0][0][l0][e0] * (T)x[base + st.col[o0][0][l0][e0]];
+                            if (staged)
+                                for (int e0 = 0; e0 < c0; ++e0)
+                                    t += st.val[o0][0][l0][e0] * xs[base + st.col[o0][0][l0][e0]];
+                            else
+                                for (int e0 = 0; e0 < c0; ++e0)
+                                    t += st.val[o0][0][l0][e0] * (T)x[base + st.col[o0][0][l0][e0]];
                             t2 += st.val[o1][1][l1][e1] * t;
                         }
                         sa += st.val[o2][2][l2][e2] * t2;
@@ -230,6 +300,7 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
                           o2 = (grad && comp == 2) ? OP_BD : OP_B;
                 const int c0 = st.cnt[o0][0][l0], c1 = st.cnt[o1][1][l1];
                 const int c2 = (D == 3) ? st.cnt[o2][2][l2] : 1;
+                const T* zc = zs + (long long)comp * capZ;
                 for (int e2 = 0; e2 < c2; ++e2) {
                     int cz = 0, kz = 0;
                     T vz = T(1);
@@ -240,16 +311,22 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
                     T t2 = T(0);
                     for (int e1 = 0; e1 < c1; ++e1) {
                         const int p1 = st.col[o1][1][l1][e1];
-                        const int cy = p1 >> 8, ky = p1 & 255;
                         T t = T(0);
-                        for (int e0 = 0; e0 < c0; ++e0) {
-                            const int p0 = st.col[o0][0][l0][e0];
-                            const int cx = p0 >> 8, kx = p0 & 255;
-                            const long long cell = cx + (long long)g.m[0] * (cy + (long long)g.m[1] * cz);
-                            const long long idx = (cell * g.ncomp + comp) * g.nloc + kx + n * (ky + n * kz);
-                            T zv = (T)z[idx];
-                            if (z2) zv -= (T)z2[idx];
-                            t += st.val[o0][0][l0][e0] * zv;
+                        if (staged) {
+                            // tile-local columns: positions in the psi-column lists
+                            const long long base = ((long long)(D == 3 ? st.col[o2][2][l2][e2] : 0) * Pn[1] + p1) * Pn[0];
+                            for (int e0 = 0; e0 < c0; ++e0) t += st.val[o0][0][l0][e0] * zc[base + st.col[o0][0][l0][e0]];
+                        } else {
+                            const int cy = p1 >> 8, ky = p1 & 255;
+                            for (int e0 = 0; e0 < c0; ++e0) {
+                                const int p0 = st.col[o0][0][l0][e0];
+                                const int cx = p0 >> 8, kx = p0 & 255;
+                                const long long cell = cx + (long long)g.m[0] * (cy + (long long)g.m[1] * cz);
+                                const long long idx = (cell * g.ncomp + comp) * g.nloc + kx + n * (ky + n * kz);
+                                T zv = (T)z[idx];
+                                if (z2) zv -= (T)z2[idx];
+                                t += st.val[o0][0][l0][e0] * zv;
+                            }
                         }
                         t2 += st.val[o1][1][l1][e1] * t;
                     }
@@ -277,10 +354,35 @@ __global__ void __launch_bounds__(256)
     k_urow(Geo<T> g, T cA, const Tx* __restrict__ x, T cB, const Tz* __restrict__ z, const Tz* __restrict__ z2,
            const double* __restrict__ rA, const double* __restrict__ bf, double* __restrict__ yres,
            double* __restrict__ part, Tx* __restrict__ y, const int* skip) {
-    __shared__ StenTile<T, UTileMax<D>::v> st;
+    extern __shared__ __align__(16) unsigned char smraw[];
     if (skip && *skip) return;
     const int blin = (int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
-    k_urow_body<D, T, Tx, Tz, HAS_A, HAS_B, RESID>(g, cA, x, cB, z, z2, rA, bf, yres, part, y, blin, &st);
+    k_urow_body<D, T, Tx, Tz, HAS_A, HAS_B, RESID>(g, cA, x, cB, z, z2, rA, bf, yres, part, y, blin, smraw);
+}
+
+// dynamic shared memory of a tiled u-row launch: the stencil tile, then the value
+// boxes it stages (only on the staged path)
+template <int D, typename T>
+static size_t urow_smem(const Geo<T>& g, bool has_a, bool has_b) {
+    size_t b = sizeof(StenTile<T, UTileMax<D>::v>);
+    if (g.staged) b += (size_t)((has_a ? urow_box_x(g) : 0) + (has_b ? g.ncomp * urow_box_z(g) : 0)) * sizeof(T);
+    return b;
+}
+
+// the staged path is taken when the boxes of the heaviest launch (residual / Newton
+// apply: x box and psi boxes) fit this budget next to the stencil tile
+constexpr size_t kUrowBoxBudget = 96 * 1024;
+
+template <typename T>
+bool urow_boxes_fit(const Geo<T>& g) {
+    return (size_t)(urow_box_x(g) + g.ncomp * urow_box_z(g)) * sizeof(T) <= kUrowBoxBudget;
+}
+template bool urow_boxes_fit<float>(const Geo<float>&);
+template bool urow_boxes_fit<double>(const Geo<double>&);
+
+int utile_extent(int d, int axis) {
+    if (d == 2) return axis == 0 ? UTile<2>::T0 : (axis == 1 ? UTile<2>::T1 : 1);
+    return axis == 0 ? UTile<3>::T0 : (axis == 1 ? UTile<3>::T1 : UTile<3>::T2);
 }
 
 template <int D>
@@ -446,13 +548,15 @@ cudaError_t launch_residual(const Geo<double>& g, const double* u, const double*
                             const double* phiz, double alpha, double* F, double* part, cudaStream_t s) {
     const int bu = (int)utile_blocks(g.d, g.n1), bp = (int)((g.Npsi + 255) / 256);
     if (g.d == 2) {
-        k_urow<2, double, double, double, true, true, true><<<utile_grid<2>(g.n1), 256, 0, s>>>(
+        k_urow<2, double, double, double, true, true, true><<<utile_grid<2>(g.n1), 256,
+                                                                 urow_smem<2>(g, true, true), s>>>(
             g, alpha, u, 1.0, psi, psi_prev, rA, bf, F, part, nullptr, nullptr);
         note_launch();
         k_residual_psi<2><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
         note_launch();
     } else {
-        k_urow<3, double, double, double, true, true, true><<<utile_grid<3>(g.n1), 256, 0, s>>>(
+        k_urow<3, double, double, double, true, true, true><<<utile_grid<3>(g.n1), 256,
+                                                                 urow_smem<3>(g, true, true), s>>>(
             g, alpha, u, 1.0, psi, psi_prev, rA, bf, F, part, nullptr, nullptr);
         note_launch();
         k_residual_psi<3><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
@@ -771,10 +875,10 @@ cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s, const int* skip) {
     if (g.d == 2)
-        k_urow<2, T, Tout, Tin, false, true, false><<<utile_grid<2>(g.n1), 256, 0, s>>>(
+        k_urow<2, T, Tout, Tin, false, true, false><<<utile_grid<2>(g.n1), 256, urow_smem<2>(g, false, true), s>>>(
             g, T(0), (const Tout*)nullptr, T(1), z, (const Tin*)nullptr, nullptr, nullptr, nullptr, nullptr, y, skip);
     else
-        k_urow<3, T, Tout, Tin, false, true, false><<<utile_grid<3>(g.n1), 256, 0, s>>>(
+        k_urow<3, T, Tout, Tin, false, true, false><<<utile_grid<3>(g.n1), 256, urow_smem<3>(g, false, true), s>>>(
             g, T(0), (const Tout*)nullptr, T(1), z, (const Tin*)nullptr, nullptr, nullptr, nullptr, nullptr, y, skip);
     note_launch();
     return cudaGetLastError();
@@ -1578,11 +1682,6 @@ cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T
     const int gs = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256), cpb = 1;
     const size_t smem = (size_t)(cpb + 1) * (3 * g.nb + g.n * g.n) * sizeof(T);
     const unsigned blocks = (unsigned)g.Nc;
-    static std::once_flag big_smem;
-    std::call_once(big_smem, [] {
-        cudaFuncSetAttribute(k_cellop<2, T, T, T, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_cellop<3, T, T, T, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    });
     if (g.d == 2)
         k_cellop<2, T, T, T, Tout><<<blocks, gs, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb);
     else
@@ -1594,15 +1693,20 @@ cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T
 // G x (eq. pG-matrix) in one launch: u-row tiles and psi cells share the SMs.
 cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
                                 const double* x, double* y, cudaStream_t s) {
+    // 2D: the u rows gather straight from global memory (measured on radial 32x32 p=8:
+    // the staged boxes cut the blocks per SM of both halves more than they save,
+    // 19.3 vs 15.8 us); 3D: staged (sine 3D: 76 vs 98 us)
+    Geo<double> gu = g;
+    if (g.d == 2) gu.staged = 0;
     const int nu = (int)utile_blocks(g.d, g.n1);
     int gs = 0, cpb = 0;
     cell_groups(g.nb, &gs, &cpb);
     const int nc = (int)((g.Nc + cpb - 1) / cpb);
     const size_t per = (size_t)(3 * g.nb + g.n * g.n) * sizeof(double);
-    const size_t st = g.d == 2 ? sizeof(StenTile<double, UTileMax<2>::v>) : sizeof(StenTile<double, UTileMax<3>::v>);
+    const size_t st = g.d == 2 ? urow_smem<2>(gu, true, true) : urow_smem<3>(gu, true, true);
     const size_t smem = std::max(st, (cpb + 1) * per);
-    if (g.d == 2) k_newton_fused<2><<<nu + nc, 256, smem, s>>>(g, gw, alpha, beta, x, y, nu, gs, cpb);
-    else k_newton_fused<3><<<nu + nc, 256, smem, s>>>(g, gw, alpha, beta, x, y, nu, gs, cpb);
+    if (g.d == 2) k_newton_fused<2><<<nu + nc, 256, smem, s>>>(gu, gw, alpha, beta, x, y, nu, gs, cpb);
+    else k_newton_fused<3><<<nu + nc, 256, smem, s>>>(gu, gw, alpha, beta, x, y, nu, gs, cpb);
     note_launch();
     return cudaGetLastError();
 }
@@ -2088,9 +2192,27 @@ cudaError_t launch_maxpy(double* w, const double* V, long long ld, const double*
     return cudaGetLastError();
 }
 
+template <typename F>
+static void allow_big_smem(F* kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 void configure_kernels() {
     configure_tiles<float>();
     configure_tiles<double>();
+    // tiled u-row kernels (stencil tile + staged value boxes) and cell operators
+    allow_big_smem(k_urow<2, double, double, double, true, true, true>);
+    allow_big_smem(k_urow<3, double, double, double, true, true, true>);
+    allow_big_smem(k_urow<2, double, double, double, false, true, false>);
+    allow_big_smem(k_urow<3, double, double, double, false, true, false>);
+    allow_big_smem(k_urow<2, float, float, float, false, true, false>);
+    allow_big_smem(k_urow<3, float, float, float, false, true, false>);
+    allow_big_smem(k_urow<2, float, float, double, false, true, false>);
+    allow_big_smem(k_urow<3, float, float, double, false, true, false>);
+    allow_big_smem(k_cellop<2, double, double, double, double>);
+    allow_big_smem(k_cellop<3, double, double, double, double>);
+    allow_big_smem(k_cellop<2, float, float, float, double>);
+    allow_big_smem(k_cellop<3, float, float, float, double>);
     cudaFuncSetAttribute(k_gemm_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
     cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
     cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);

@@ -130,6 +130,52 @@ static bool upload_sten(DevState& D, const Ell& E, bool gram, int n, DevSten& S,
     return cudaStreamSynchronize(s) == cudaSuccess;
 }
 
+// Column lists of the row tiles (extent T) of one axis for the stencils `ops`, and
+// each stencil entry's column as a position in its row tile's list (lcol[op]).
+// Gram operators (psi columns) use the packed (cell << 8) | k form.
+static bool upload_tile_cols(DevState& D, int n1, int T, const std::vector<const Ell*>& ops, bool gram, int n,
+                             DevTileCols& tc, const std::vector<int**>& lcol, cudaStream_t s) {
+    const int nt = (n1 + T - 1) / T;
+    auto packed = [&](int c) { return gram ? (((c / n) << 8) | (c % n)) : c; };
+    std::vector<std::vector<int>> lists(nt);
+    for (int t = 0; t < nt; ++t) {
+        std::vector<int>& L = lists[t];
+        for (int r = t * T; r < std::min(n1, (t + 1) * T); ++r)
+            for (const Ell* E : ops)
+                for (int e = 0; e < E->cnt[r]; ++e) L.push_back(packed(E->col[(size_t)r * kEll + e]));
+        std::sort(L.begin(), L.end());
+        L.erase(std::unique(L.begin(), L.end()), L.end());
+    }
+    int cap = 1;
+    for (const auto& L : lists) cap = std::max(cap, (int)L.size());
+    std::vector<int> list((size_t)nt * cap, 0), count(nt, 0);
+    for (int t = 0; t < nt; ++t) {
+        count[t] = (int)lists[t].size();
+        std::copy(lists[t].begin(), lists[t].end(), list.begin() + (size_t)t * cap);
+    }
+    bool ok = true;
+    tc.cap = cap;
+    tc.list = dalloc<int>(D, list.size(), ok);
+    tc.count = dalloc<int>(D, count.size(), ok);
+    std::vector<std::vector<int>> lc(ops.size(), std::vector<int>((size_t)n1 * kEll, 0));
+    for (size_t o = 0; o < ops.size(); ++o) {
+        *lcol[o] = dalloc<int>(D, lc[o].size(), ok);
+        for (int r = 0; r < n1; ++r) {
+            const std::vector<int>& L = lists[r / T];
+            for (int e = 0; e < ops[o]->cnt[r]; ++e) {
+                const int c = packed(ops[o]->col[(size_t)r * kEll + e]);
+                lc[o][(size_t)r * kEll + e] = (int)(std::lower_bound(L.begin(), L.end(), c) - L.begin());
+            }
+        }
+    }
+    if (!ok) return false;
+    cudaMemcpyAsync(tc.list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(tc.count, count.data(), count.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    for (size_t o = 0; o < ops.size(); ++o)
+        cudaMemcpyAsync(*lcol[o], lc[o].data(), lc[o].size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    return cudaStreamSynchronize(s) == cudaSuccess;
+}
+
 template <typename T>
 static T* upload_vec(DevState& D, const std::vector<double>& v, bool& ok, cudaStream_t s) {
     T* p = dalloc<T>(D, v.size(), ok);
@@ -173,6 +219,13 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
             ok = ok && upload_sten(D, Dj.Bdi, true, H.n, D.Bd[j], s);
             ok = ok && upload_sten(D, Dj.BdTi, false, H.n, D.BdT[j], s);
         }
+        const int T = utile_extent(d, j);
+        ok = ok && upload_tile_cols(D, Dj.n1, T, {&Dj.Ai, &Dj.Mi}, false, H.n, D.tu[j], {&D.A[j].lcol, &D.M[j].lcol}, s);
+        if (grad)
+            ok = ok && upload_tile_cols(D, Dj.n1, T, {&Dj.Bi, &Dj.Bdi}, true, H.n, D.tp[j],
+                                        {&D.B[j].lcol, &D.Bd[j].lcol}, s);
+        else
+            ok = ok && upload_tile_cols(D, Dj.n1, T, {&Dj.Bi}, true, H.n, D.tp[j], {&D.B[j].lcol}, s);
         D.V_d[j] = upload_vec<double>(D, Dj.V, ok, s);
         D.V_f[j] = upload_vec<float>(D, Dj.V, ok, s);
         D.lam_d[j] = upload_vec<double>(D, Dj.lam, ok, s);
@@ -288,12 +341,14 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     };
     fill(D.gd, [&](Geo<double>& g) {
         for (int j = 0; j < d; ++j) {
-            g.A[j] = {D.A[j].cnt, D.A[j].col, D.A[j].vd};
-            g.M[j] = {D.M[j].cnt, D.M[j].col, D.M[j].vd};
-            g.B[j] = {D.B[j].cnt, D.B[j].col, D.B[j].vd};
-            g.BT[j] = {D.BT[j].cnt, D.BT[j].col, D.BT[j].vd};
-            g.Bd[j] = {D.Bd[j].cnt, D.Bd[j].col, D.Bd[j].vd};
-            g.BdT[j] = {D.BdT[j].cnt, D.BdT[j].col, D.BdT[j].vd};
+            g.A[j] = {D.A[j].cnt, D.A[j].col, D.A[j].vd, D.A[j].lcol};
+            g.M[j] = {D.M[j].cnt, D.M[j].col, D.M[j].vd, D.M[j].lcol};
+            g.B[j] = {D.B[j].cnt, D.B[j].col, D.B[j].vd, D.B[j].lcol};
+            g.BT[j] = {D.BT[j].cnt, D.BT[j].col, D.BT[j].vd, nullptr};
+            g.Bd[j] = {D.Bd[j].cnt, D.Bd[j].col, D.Bd[j].vd, D.Bd[j].lcol};
+            g.BdT[j] = {D.BdT[j].cnt, D.BdT[j].col, D.BdT[j].vd, nullptr};
+            g.tu[j] = {D.tu[j].list, D.tu[j].count, D.tu[j].cap};
+            g.tp[j] = {D.tp[j].list, D.tp[j].count, D.tp[j].cap};
             g.V[j] = D.V_d[j];
             g.lam[j] = D.lam_d[j];
         }
@@ -301,17 +356,27 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     });
     fill(D.gf, [&](Geo<float>& g) {
         for (int j = 0; j < d; ++j) {
-            g.A[j] = {D.A[j].cnt, D.A[j].col, D.A[j].vf};
-            g.M[j] = {D.M[j].cnt, D.M[j].col, D.M[j].vf};
-            g.B[j] = {D.B[j].cnt, D.B[j].col, D.B[j].vf};
-            g.BT[j] = {D.BT[j].cnt, D.BT[j].col, D.BT[j].vf};
-            g.Bd[j] = {D.Bd[j].cnt, D.Bd[j].col, D.Bd[j].vf};
-            g.BdT[j] = {D.BdT[j].cnt, D.BdT[j].col, D.BdT[j].vf};
+            g.A[j] = {D.A[j].cnt, D.A[j].col, D.A[j].vf, D.A[j].lcol};
+            g.M[j] = {D.M[j].cnt, D.M[j].col, D.M[j].vf, D.M[j].lcol};
+            g.B[j] = {D.B[j].cnt, D.B[j].col, D.B[j].vf, D.B[j].lcol};
+            g.BT[j] = {D.BT[j].cnt, D.BT[j].col, D.BT[j].vf, nullptr};
+            g.Bd[j] = {D.Bd[j].cnt, D.Bd[j].col, D.Bd[j].vf, D.Bd[j].lcol};
+            g.BdT[j] = {D.BdT[j].cnt, D.BdT[j].col, D.BdT[j].vf, nullptr};
+            g.tu[j] = {D.tu[j].list, D.tu[j].count, D.tu[j].cap};
+            g.tp[j] = {D.tp[j].list, D.tp[j].count, D.tp[j].cap};
             g.V[j] = D.V_f[j];
             g.lam[j] = D.lam_f[j];
         }
         g.Vq = D.Vq_f; g.wq = D.wq_f; g.detJ = (float)H.detJ; g.Mpsi = D.Mpsi_f; g.Kpsi = D.Kpsi_f; g.C = D.C_f;
     });
+    // The u-row kernels stage per-tile value boxes (when they fit the shared-memory
+    // budget) where a row gathers from many planes or psi components: 3D, or the
+    // gradient kind.  Measured: B apply on the 3D 8^3 p=6 obstacle 23 -> 12.8 us,
+    // torsion 16^2 p=10 solve -6 %; on the 2D obstacle (one component) the direct
+    // gathers stay faster (radial 32x32 p=8 B apply 4.8 vs 6.3 us).
+    const bool stage = d == 3 || grad;
+    D.gd.staged = stage && urow_boxes_fit(D.gd) ? 1 : 0;
+    D.gf.staged = stage && urow_boxes_fit(D.gf) ? 1 : 0;
     CK(cudaStreamSynchronize(s));
     if (P.params.fdm_tile_f64 >= 0) D.gd.gemm_cfg = P.params.fdm_tile_f64;
     else CKS(autotune_fdm<double>(ctx, P, D.gd, D.tu_d, D.tu2_d, D.w1_d, D.w2_d));

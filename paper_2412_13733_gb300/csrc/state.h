@@ -17,6 +17,13 @@ struct DevSten {
     int* col = nullptr;
     double* vd = nullptr;
     float* vf = nullptr;
+    int* lcol = nullptr;
+};
+
+struct DevTileCols {
+    int* list = nullptr;
+    int* count = nullptr;
+    int cap = 0;
 };
 
 struct DevState {
@@ -27,6 +34,7 @@ struct DevState {
     int fm = 0;
     // constant operators
     DevSten A[kMaxDim], M[kMaxDim], B[kMaxDim], BT[kMaxDim], Bd[kMaxDim], BdT[kMaxDim];
+    DevTileCols tu[kMaxDim], tp[kMaxDim];
     double *Vq_d = nullptr, *wq_d = nullptr, *Mpsi_d = nullptr, *Kpsi_d = nullptr, *C_d = nullptr;
     float *Vq_f = nullptr, *wq_f = nullptr, *Mpsi_f = nullptr, *Kpsi_f = nullptr, *C_f = nullptr;
     double *V_d[kMaxDim] = {}, *lam_d[kMaxDim] = {};
