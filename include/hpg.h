@@ -262,9 +262,11 @@ hpg_status hpg_reset_kernel_times(hpg_ctx* ctx, int pid);
  * captured into a CUDA graph on the first call for a given (class, precision,
  * reps) and replayed on later calls, so time the second call.  Needs a prior
  * hpg_solve or hpg_set_state (+ hpg_factor_precond for _PRECOND/_SCHUR);
- * the kernels write only scratch buffers.  _ORTHO is one FP64 Arnoldi step
- * with both Gram-Schmidt passes (two dot passes, two update passes, Givens) at
- * j = krylov_max / 2 on the Krylov basis buffer, whose contents it overwrites. */
+ * the kernels write only scratch buffers.  _ORTHO is one Arnoldi step (FP64
+ * basis for HPG_FP64, float basis for HPG_MIXED) with both Gram-Schmidt passes
+ * (two dot passes, two update passes, Givens) at j = krylov_max / 2 on the
+ * Krylov basis buffer, whose contents it overwrites; the HPG_MIXED _PRECOND and
+ * _SCHUR launches also read and write that buffer, as in the solver. */
 hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precision, int reps);
 /* Number of fast-diagonalisation pass variants for `precision` (HPG_MIXED: FP32
  * passes, HPG_FP64: FP64 passes); valid values of hpg_params.fdm_tile_f32/_f64

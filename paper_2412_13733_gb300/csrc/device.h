@@ -151,7 +151,8 @@ cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts
 // ---- GMRES (right-preconditioned, unrestarted), all state on the device.
 constexpr int kMaxKrylov = 1000;   // upper bound of hpg_params.krylov_max
 struct GmresDev {
-    double* Vb;       // (kmax+1) x N basis
+    double* Vb;       // (kmax+1) x N basis storage: doubles (FP64 solves) or, in the same
+                      // allocation, floats (FP32 inner solves); see gmres_basis
     double* H;        // kmax columns of (kmax+1)
     double* cs;       // kmax
     double* sn;       // kmax
@@ -171,6 +172,9 @@ struct GmresDev {
     int kmax;
     long long N;
 };
+// The basis viewed in its element type VT (double or float).
+template <typename VT>
+inline VT* gmres_basis(const GmresDev& G) { return reinterpret_cast<VT*>(G.Vb); }
 int gmres_dot_blocks(long long N);
 // Flexible GMRES on G: chunk partials of the dots V_v . w (v < nv, vectors ld apart),
 // part[v * fg_chunks(N) + c]; and w += sgn * sum_v h[v] V_v (h on the device).
@@ -181,16 +185,21 @@ cudaError_t launch_maxpy(double* w, const double* V, long long ld, const double*
                          cudaStream_t s);
 int gmres_dot_groups(int kmax);
 int gmres_upd_blocks(long long N);
+// The GMRES launchers take the basis element type VT (double or float).
 // r0 = b: beta0 = ||b||, V_0 = b / beta0, g = beta0 e_1, tol*beta0 stored, j = 0.
+template <typename VT>
 cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s, int cap = 0);
-// After w (= S Shat^{-1} V_j) has been written into Vb[j+1]: CGS2 orthogonalise,
+// After w (= S Shat^{-1} V_j) has been written into V_{j+1}: CGS2 orthogonalise,
 // normalise, Givens update, convergence test, j += 1.  No-op once stopped.
+template <typename VT>
 cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s);
 // Timing aid: set j (and clear the stop flags), then one Arnoldi step.
+template <typename VT>
 cudaError_t gmres_timed_step(GmresDev& G, int j, cudaStream_t s);
 // Set the WHILE condition of a device-side GMRES loop to "not stopped".
 cudaError_t launch_gm_setcond(cudaGraphConditionalHandle h, const int* iflag, cudaStream_t s);
-// Solve H y = g for the completed iterations and form x = sum_i y_i V_i.
+// Solve H y = g for the completed iterations and form x = sum_i y_i V_i (FP64 sums).
+template <typename VT>
 cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s);
 // Number of FDM GEMM tile variants for elements of `elem` bytes.
 int fdm_tile_count(int elem);

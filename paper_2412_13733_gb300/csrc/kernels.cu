@@ -1781,9 +1781,14 @@ cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts
 // the device (G.jdev) so that a chunk of iterations can be captured once in a
 // CUDA graph and replayed.  Every kernel returns immediately once the
 // converged/stop flag (G.iflag[0]) is set.  Classical Gram--Schmidt with one
-// re-orthogonalisation (CGS2), FP64, fixed-order (deterministic) reductions.
+// re-orthogonalisation (CGS2), fixed-order (deterministic) reductions.  The
+// basis is stored in VT: double for the FP64 solves, float for the FP32 inner
+// solves of the mixed path (their operator is FP32 as well; the FP64 refinement
+// around them corrects what either loses).  Dot products, Hessenberg column,
+// Givens rotations and residual estimate are FP64 for both.
 
-__global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b, long long N,
+template <typename VT>
+__global__ void k_gm_start(VT* __restrict__ Vb, const double* __restrict__ b, long long N,
                            const double* __restrict__ part, int nparts, double rtol, double* __restrict__ scal,
                            double* __restrict__ gv, int kmax, int cap, int* __restrict__ iflag,
                            int* __restrict__ jdev) {
@@ -1797,7 +1802,7 @@ __global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b
     const double bb = beta;
     const double inv = bb > 0.0 ? 1.0 / bb : 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        Vb[i] = b[i] * inv;
+        Vb[i] = (VT)(b[i] * inv);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         scal[0] = bb;
         scal[1] = bb;
@@ -1827,16 +1832,21 @@ __global__ void k_gm_start(double* __restrict__ Vb, const double* __restrict__ b
 // In FP64 on this GPU the passes are bound by the FP64 FMA rate (one FMA per
 // 8-byte basis word), so every kernel does (j+1) N FMAs and a few adds: a dot
 // work item is one (vector, 1024-element chunk) pair per warp, 32 FMAs per lane
-// before one shuffle reduction.  Chunk partials are summed in chunk order by the
-// last block of each vector group (deterministic).
+// before one shuffle reduction.  With a float basis the 32 per-lane products are
+// summed in FP32 (two chains of 16) and only the shuffle tree and the chunk sums
+// are FP64, so the passes are bound by memory instead.  Chunk partials are summed
+// in chunk order by the last block of each vector group (deterministic).
 constexpr int kDotChunk = 1024;      // elements per warp work item (32 per lane)
 constexpr int kDotVec = 8;           // vectors per dot block (one per warp)
 
+// VEC (float basis, N a multiple of 4): full chunks are read as float4, lane l
+// holding elements 4l + 128q .. 4l + 128q + 3.
+template <typename VT, bool VEC>
 __global__ void __launch_bounds__(256)
-    k_gm_dots2(const double* __restrict__ Vb, const int* __restrict__ jdev, long long N, double* __restrict__ part,
+    k_gm_dots2(const VT* __restrict__ Vb, const int* __restrict__ jdev, long long N, double* __restrict__ part,
                int kmax, const int* __restrict__ iflag, const int* __restrict__ reo, double* __restrict__ hsum,
                unsigned int* __restrict__ counter) {
-    __shared__ double ws[kDotChunk];
+    __shared__ __align__(16) VT ws[kDotChunk];
     __shared__ bool last;
     if (iflag[0]) return;
     if (reo && *reo == 0) return;                        // second pass not needed
@@ -1846,19 +1856,44 @@ __global__ void __launch_bounds__(256)
     if (i0 >= nvec) return;
     const long long e0 = (long long)blockIdx.x * kDotChunk;
     const int len = (N - e0 < kDotChunk) ? (int)(N - e0) : kDotChunk;
-    const double* w = Vb + (long long)(j + 1) * N + e0;
-    for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) ws[t] = (t < len) ? w[t] : 0.0;
+    const VT* w = Vb + (long long)(j + 1) * N + e0;
+    for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) ws[t] = (t < len) ? w[t] : VT(0);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int i = i0 + wid;
     const long long ld = kmax + 2;
     if (i < nvec) {
-        const double* vi = (i <= j) ? Vb + (long long)i * N + e0 : nullptr;
-        double s0 = 0.0, s1 = 0.0;
-        if (vi && len == kDotChunk) {
+        const VT* vi = (i <= j) ? Vb + (long long)i * N + e0 : nullptr;
+        VT s0 = VT(0), s1 = VT(0);
+        if (VEC && len == kDotChunk) {
+            const float4* w4 = reinterpret_cast<const float4*>(ws);
+            if (vi) {
+                const float4* v4 = reinterpret_cast<const float4*>(vi);
+                float4 a[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a[q] = v4[lane + 32 * q];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 b = w4[lane + 32 * q];
+                    s0 += a[q].x * b.x;
+                    s1 += a[q].y * b.y;
+                    s0 += a[q].z * b.z;
+                    s1 += a[q].w * b.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 b = w4[lane + 32 * q];
+                    s0 += b.x * b.x;
+                    s1 += b.y * b.y;
+                    s0 += b.z * b.z;
+                    s1 += b.w * b.w;
+                }
+            }
+        } else if (vi && len == kDotChunk) {
 #pragma unroll
             for (int q0 = 0; q0 < 32; q0 += 8) {
-                double a[8];
+                VT a[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) a[u] = vi[lane + 32 * (q0 + u)];
 #pragma unroll
@@ -1875,12 +1910,12 @@ __global__ void __launch_bounds__(256)
         } else {
 #pragma unroll 8
             for (int q = 0; q < 32; q += 2) {
-                const double x0 = ws[lane + 32 * q], x1 = ws[lane + 32 * (q + 1)];
+                const VT x0 = ws[lane + 32 * q], x1 = ws[lane + 32 * (q + 1)];
                 s0 += x0 * x0;
                 s1 += x1 * x1;
             }
         }
-        double t = s0 + s1;
+        double t = (double)s0 + (double)s1;
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
         if (lane == 0) {
             part[(long long)blockIdx.x * ld + i] = t;
@@ -1903,18 +1938,24 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x == 0) counter[blockIdx.y] = 0u;
 }
 
-// the final dot sums of the pass (written by the dot kernel's last blocks)
-__device__ __forceinline__ void load_sums(const double* __restrict__ hsum, int nvec, double* h) {
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) h[i] = hsum[i];
+// the final dot sums of the pass (written by the dot kernel's last blocks), and
+// their copy in the basis type for the update
+template <typename VT>
+__device__ __forceinline__ void load_sums(const double* __restrict__ hsum, int nvec, double* h, VT* hv) {
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+        h[i] = hsum[i];
+        hv[i] = (VT)h[i];
+    }
     __syncthreads();
 }
 
 // v - sum_{i < nv} h[i] V_i[e], in order of i, sixteen basis loads in flight
-__device__ __forceinline__ double sub_basis(const double* __restrict__ Vb, long long N, long long e,
-                                            const double* h, int nv, double v) {
+template <typename VT>
+__device__ __forceinline__ VT sub_basis(const VT* __restrict__ Vb, long long N, long long e, const VT* h, int nv,
+                                        VT v) {
     int i = 0;
     for (; i + 16 <= nv; i += 16) {
-        double a[16];
+        VT a[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) a[u] = Vb[(long long)(i + u) * N + e];
 #pragma unroll
@@ -1924,14 +1965,97 @@ __device__ __forceinline__ double sub_basis(const double* __restrict__ Vb, long 
     return v;
 }
 
+// Elements per block of the update kernels: FP64 one per thread; float 128.
+template <typename VT>
+constexpr int upd_elems() { return sizeof(VT) == 8 ? 256 : 128; }
+
+// four float elements of lane `lane` in the 128-element block at `base`:
+// VEC: the float4 at base + 4 lane (N a multiple of 4); else base + lane + 32 k
+template <bool VEC>
+__device__ __forceinline__ void load4(const float* __restrict__ v, long long base, int lane, long long N, float (&a)[4]) {
+    if (VEC) {
+        const long long e = base + 4 * lane;
+        if (e < N) {
+            const float4 t = *reinterpret_cast<const float4*>(v + e);
+            a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+        } else {
+            a[0] = a[1] = a[2] = a[3] = 0.f;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long e = base + lane + 32 * k;
+            a[k] = e < N ? v[e] : 0.f;
+        }
+    }
+}
+
+// w = (sub ? w - sum_{i <= j} hv[i] V_i : w) * scale on this block's elements,
+// w = V_{j+1}.  FP64: one element per thread, the vectors in order (sub_basis).
+// Float: 128 elements per block, four per lane; warp q sums the vectors
+// i = q, q + 8, q + 16, ... (four loads in flight) and the eight warp partials
+// are added in warp order, so the result is the same with and without VEC.
+// Every thread of the block must call it (it has a barrier on the float path).
+template <typename VT, bool VEC>
+__device__ __forceinline__ void block_update(VT* __restrict__ Vb, long long N, int j, const VT* hv, bool sub,
+                                             VT scale) {
+    VT* w = Vb + (long long)(j + 1) * N;
+    if constexpr (sizeof(VT) == 8) {
+        const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        if (e < N) w[e] = (sub ? sub_basis(Vb, N, e, hv, j + 1, w[e]) : w[e]) * scale;
+    } else {
+        __shared__ __align__(16) float red[8][128];
+        const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+        const long long base = (long long)blockIdx.x * 128;
+        if (sub) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            int i = q;
+            for (; i + 24 <= j; i += 32) {
+                float a[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) load4<VEC>(Vb + (long long)(i + 8 * u) * N, base, lane, N, a[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[k] += hv[i + 8 * u] * a[u][k];
+            }
+            for (; i <= j; i += 8) {
+                float a[4];
+                load4<VEC>(Vb + (long long)i * N, base, lane, N, a);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[k] += hv[i] * a[k];
+            }
+            if (VEC) {
+                reinterpret_cast<float4*>(red[q])[lane] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) red[q][lane + 32 * k] = acc[k];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 128) {
+            const long long e = base + threadIdx.x;
+            if (e < N) {
+                float t = 0.f;
+                if (sub)
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) t += red[r][threadIdx.x];
+                w[e] = (w[e] - t) * scale;
+            }
+        }
+    }
+}
+
+template <typename VT, bool VEC>
 __global__ void __launch_bounds__(256)
-    k_gm_update1(double* __restrict__ Vb, const int* __restrict__ jdev, long long N, const double* __restrict__ hsum,
+    k_gm_update1(VT* __restrict__ Vb, const int* __restrict__ jdev, long long N, const double* __restrict__ hsum,
                  int kmax, double* __restrict__ H, double* __restrict__ scal, int* __restrict__ reo,
                  const int* __restrict__ force, const int* __restrict__ iflag) {
     __shared__ double h[kMaxKrylov + 2];
+    __shared__ VT hv[kMaxKrylov + 2];
     if (iflag[0]) return;
     const int j = *jdev;
-    load_sums(hsum, j + 2, h);                      // h1[0..j], ||w||^2 in h[j+1]
+    load_sums(hsum, j + 2, h, hv);                  // h1[0..j], ||w||^2 in h[j+1]
     if (threadIdx.x == 0) {
         double q = 0.0;
         for (int i = 0; i <= j; ++i) q += h[i] * h[i];
@@ -1944,25 +2068,24 @@ __global__ void __launch_bounds__(256)
     }
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i <= j; i += blockDim.x) H[(long long)j * (kmax + 1) + i] = h[i];
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= N) return;
-    double* w = Vb + (long long)(j + 1) * N;
-    w[e] = sub_basis(Vb, N, e, h, j + 1, w[e]);
+    block_update<VT, VEC>(Vb, N, j, hv, true, VT(1));
 }
 
+template <typename VT, bool VEC>
 __global__ void __launch_bounds__(256)
-    k_gm_update2(double* __restrict__ Vb, const int* __restrict__ jdev_c, long long N, const double* __restrict__ hsum,
+    k_gm_update2(VT* __restrict__ Vb, const int* __restrict__ jdev_c, long long N, const double* __restrict__ hsum,
                  int kmax, double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
                  double* __restrict__ gv, double* __restrict__ scal, int* __restrict__ iflag,
                  const int* __restrict__ reo, unsigned int* __restrict__ counter, int* __restrict__ jdev) {
     __shared__ double h[kMaxKrylov + 2];
+    __shared__ VT hv[kMaxKrylov + 2];
     __shared__ double shn;
     __shared__ bool last;
     if (iflag[0]) return;
     const int j = *jdev_c;
     const bool second = *reo != 0;
     if (second) {
-        load_sums(hsum, j + 2, h);                      // h2[0..j], ||w1||^2 in h[j+1]
+        load_sums(hsum, j + 2, h, hv);                  // h2[0..j], ||w1||^2 in h[j+1]
     } else {
         for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = 0.0;
         __syncthreads();
@@ -1980,12 +2103,8 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const double hn = shn;
-    const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < N) {
-        double* w = Vb + (long long)(j + 1) * N;
-        w[e] = (second ? sub_basis(Vb, N, e, h, j + 1, w[e]) : w[e]) * inv;
-    }
+    const VT inv = (VT)(hn > 0.0 ? 1.0 / hn : 0.0);
+    block_update<VT, VEC>(Vb, N, j, hv, second, inv);
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(gridDim.x - 1));
     __syncthreads();
@@ -2059,7 +2178,8 @@ __global__ void k_gm_backsolve(const double* __restrict__ H, const double* __res
     }
 }
 
-__global__ void k_gm_combine(const double* __restrict__ Vb, const double* __restrict__ y,
+template <typename VT>
+__global__ void k_gm_combine(const VT* __restrict__ Vb, const double* __restrict__ y,
                              const int* __restrict__ iflag, long long N, double* __restrict__ x) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N) return;
@@ -2067,13 +2187,13 @@ __global__ void k_gm_combine(const double* __restrict__ Vb, const double* __rest
     double s = 0.0;
     int i = 0;
     for (; i + 8 <= k; i += 8) {
-        double a[8];
+        VT a[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) a[u] = Vb[(long long)(i + u) * N + e];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s += y[i + u] * a[u];
+        for (int u = 0; u < 8; ++u) s += y[i + u] * (double)a[u];
     }
-    for (; i < k; ++i) s += y[i] * Vb[(long long)i * N + e];
+    for (; i < k; ++i) s += y[i] * (double)Vb[(long long)i * N + e];
     x[e] = s;
 }
 
@@ -2092,6 +2212,7 @@ int gmres_dot_blocks(long long N) { return (int)((N + kDotChunk - 1) / kDotChunk
 int gmres_dot_groups(int kmax) { return (kmax + 2 + kDotVec - 1) / kDotVec; }
 int gmres_upd_blocks(long long N) { return (int)((N + 255) / 256); }
 
+template <typename VT>
 cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s, int cap) {
     int np = 0;
     cudaError_t e = launch_sumsq(b, G.N, G.part_norm, &np, s);
@@ -2099,25 +2220,38 @@ cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t 
     cudaMemsetAsync(G.H, 0, sizeof(double) * (size_t)(G.kmax + 1) * G.kmax, s);
     const int nb = gmres_upd_blocks(G.N) < 1024 ? gmres_upd_blocks(G.N) : 1024;
     const int c = (cap > 0 && cap < G.kmax) ? cap : G.kmax;
-    k_gm_start<<<nb, 256, 0, s>>>(G.Vb, b, G.N, G.part_norm, np, rtol, G.scal, G.gv, G.kmax, c, G.iflag, G.jdev);
+    k_gm_start<VT><<<nb, 256, 0, s>>>(gmres_basis<VT>(G), b, G.N, G.part_norm, np, rtol, G.scal, G.gv, G.kmax, c,
+                                      G.iflag, G.jdev);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s) {
-    const int nch = gmres_dot_blocks(G.N), bu = gmres_upd_blocks(G.N);
+template <typename VT, bool VEC>
+static void arnoldi_launch(GmresDev& G, cudaStream_t s) {
+    const int nch = gmres_dot_blocks(G.N);
+    const int bu = (int)((G.N + upd_elems<VT>() - 1) / upd_elems<VT>());
     const dim3 gd(nch, gmres_dot_groups(G.kmax));
-    k_gm_dots2<<<gd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, nullptr, G.hsum, G.counter);
+    VT* V = gmres_basis<VT>(G);
+    k_gm_dots2<VT, VEC><<<gd, 256, 0, s>>>(V, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, nullptr, G.hsum,
+                                             G.counter);
     note_launch();
-    k_gm_update1<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.hsum, G.kmax, G.H, G.scal, G.reo, G.force, G.iflag);
+    k_gm_update1<VT, VEC><<<bu, 256, 0, s>>>(V, G.jdev, G.N, G.hsum, G.kmax, G.H, G.scal, G.reo, G.force, G.iflag);
     note_launch();
-    k_gm_dots2<<<gd, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, G.reo, G.hsum, G.counter);
+    k_gm_dots2<VT, VEC><<<gd, 256, 0, s>>>(V, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, G.reo, G.hsum, G.counter);
     note_launch();
-    k_gm_update2<<<bu, 256, 0, s>>>(G.Vb, G.jdev, G.N, G.hsum, G.kmax, G.H, G.cs, G.sn, G.gv, G.scal, G.iflag, G.reo,
-                                    G.counter2, G.jdev);
+    k_gm_update2<VT, VEC><<<bu, 256, 0, s>>>(V, G.jdev, G.N, G.hsum, G.kmax, G.H, G.cs, G.sn, G.gv, G.scal,
+                                             G.iflag, G.reo, G.counter2, G.jdev);
     note_launch();
+}
+
+template <typename VT>
+cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s) {
+    // float4 access needs every basis vector 16-byte aligned: N a multiple of 4
+    if (sizeof(VT) == 4 && G.N % 4 == 0) arnoldi_launch<VT, true>(G, s);
+    else arnoldi_launch<VT, false>(G, s);
     return cudaGetLastError();
 }
+
 
 __global__ void k_gm_setj(int* __restrict__ jdev, int* __restrict__ iflag, unsigned int* __restrict__ counter, int j,
                           int kmax) {
@@ -2129,22 +2263,33 @@ __global__ void k_gm_setj(int* __restrict__ jdev, int* __restrict__ iflag, unsig
     }
 }
 
+template <typename VT>
 cudaError_t gmres_timed_step(GmresDev& G, int j, cudaStream_t s) {
     if (j < 0 || j >= G.kmax) return cudaErrorInvalidValue;
     k_gm_setj<<<1, 32, 0, s>>>(G.jdev, G.iflag, G.counter2, j, G.kmax);
     note_launch();
-    return gmres_arnoldi(G, s);
+    return gmres_arnoldi<VT>(G, s);
 }
 
+template <typename VT>
 cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s) {
     const size_t tri = (size_t)G.kmax * (G.kmax + 1) / 2 * sizeof(double);
     const int use_smem = tri <= 200 * 1024;
     k_gm_backsolve<<<1, 256, use_smem ? tri : 0, s>>>(G.H, G.gv, G.iflag, G.kmax, G.y, use_smem);
     note_launch();
-    k_gm_combine<<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(G.Vb, G.y, G.iflag, G.N, x);
+    k_gm_combine<VT><<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(gmres_basis<VT>(G), G.y, G.iflag, G.N, x);
     note_launch();
     return cudaGetLastError();
 }
+
+template cudaError_t gmres_start<double>(GmresDev&, const double*, double, cudaStream_t, int);
+template cudaError_t gmres_start<float>(GmresDev&, const double*, double, cudaStream_t, int);
+template cudaError_t gmres_arnoldi<double>(GmresDev&, cudaStream_t);
+template cudaError_t gmres_arnoldi<float>(GmresDev&, cudaStream_t);
+template cudaError_t gmres_timed_step<double>(GmresDev&, int, cudaStream_t);
+template cudaError_t gmres_timed_step<float>(GmresDev&, int, cudaStream_t);
+template cudaError_t gmres_finish<double>(GmresDev&, double*, cudaStream_t);
+template cudaError_t gmres_finish<float>(GmresDev&, double*, cudaStream_t);
 
 // ---- vector blocks of the flexible GMRES on G (host-driven outer loop) ---------
 // part[v * nchunks + c] = sum over chunk c (kFgChunk elements) of V_v . w, v < nv
@@ -2213,6 +2358,8 @@ void configure_kernels() {
     allow_big_smem(k_cellop<3, double, double, double, double>);
     allow_big_smem(k_cellop<2, float, float, float, double>);
     allow_big_smem(k_cellop<3, float, float, float, double>);
+    allow_big_smem(k_cellop<2, float, float, float, float>);
+    allow_big_smem(k_cellop<3, float, float, float, float>);
     cudaFuncSetAttribute(k_gemm_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
     cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
     cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
@@ -2229,6 +2376,8 @@ template cudaError_t launch_factor<float>(const Geo<float>&, const float*, doubl
                                           float*, cudaStream_t);
 template cudaError_t launch_precond<double, double, double>(const Geo<double>&, const double*, const double*,
                                                             double*, cudaStream_t, IterCtl);
+template cudaError_t launch_precond<float, float, float>(const Geo<float>&, const float*, const float*, float*,
+                                                         cudaStream_t, IterCtl);
 template cudaError_t launch_precond<float, double, float>(const Geo<float>&, const float*, const double*, float*,
                                                           cudaStream_t, IterCtl);
 template cudaError_t launch_precond<float, double, double>(const Geo<float>&, const float*, const double*,
@@ -2248,6 +2397,8 @@ template cudaError_t launch_fdm<float>(const Geo<float>&, const double*, double,
                                        float*, cudaStream_t, const int*);
 template cudaError_t launch_schur_rest<double, double>(const Geo<double>&, const double*, double, const double*,
                                                        const double*, double*, cudaStream_t, IterCtl);
+template cudaError_t launch_schur_rest<float, float>(const Geo<float>&, const float*, double, const float*,
+                                                    const float*, float*, cudaStream_t, IterCtl);
 template cudaError_t launch_schur_rest<float, double>(const Geo<float>&, const float*, double, const float*,
                                                       const float*, double*, cudaStream_t, IterCtl);
 template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);

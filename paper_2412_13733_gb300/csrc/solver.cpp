@@ -591,7 +591,7 @@ static hpg_status gmres_chunk(hpg_ctx* ctx, Problem& P, int chunk) {
     for (int c = 0; c < chunk; ++c) {
         {
             Scope sc(P.timer, HPG_K_PRECOND, s);
-            CK(launch_precond<T, double, T>(g, PV<T>::Sinv(D), G.Vb, PV<T>::zp(D), s, ctl));
+            CK(launch_precond<T, T, T>(g, PV<T>::Sinv(D), gmres_basis<T>(G), PV<T>::zp(D), s, ctl));
         }
         {
             Scope sc(P.timer, HPG_K_BAPPLY, s);
@@ -604,12 +604,12 @@ static hpg_status gmres_chunk(hpg_ctx* ctx, Problem& P, int chunk) {
         }
         {
             Scope sc(P.timer, HPG_K_SCHUR, s);
-            CK(launch_schur_rest<T, double>(g, PV<T>::gw(D), P.params.beta, PV<T>::zp(D), PV<T>::tu2(D), G.Vb, s,
-                                            ctl));
+            CK(launch_schur_rest<T, T>(g, PV<T>::gw(D), P.params.beta, PV<T>::zp(D), PV<T>::tu2(D),
+                                       gmres_basis<T>(G), s, ctl));
         }
         {
             Scope sc(P.timer, HPG_K_ORTHO, s);
-            CK(gmres_arnoldi(G, s));
+            CK(gmres_arnoldi<T>(G, s));
         }
     }
     return HPG_OK;
@@ -704,7 +704,8 @@ static hpg_status gmres_run(hpg_ctx* ctx, Problem& P, int* its, bool* capped) {
 }
 
 // eq. (schur2): y = b_psi - B^T A^{-1} b_u; GMRES on S (right-preconditioned by
-// S-hat); delta_u = A^{-1}(b_u - B delta_psi).  All vectors FP64, operators in T.
+// S-hat); delta_u = A^{-1}(b_u - B delta_psi).  Right-hand sides and results FP64,
+// operators and the GMRES basis in T.
 template <typename T>
 static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const double* bu, const double* bp,
                                 double* du, double* dp, double rtol, int* its, bool* capped, int cap = 0) {
@@ -725,13 +726,13 @@ static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const do
     }
     {
         Scope sc(P.timer, HPG_K_ORTHO, s);
-        CK(gmres_start(G, D.yp, rtol, s, cap));
+        CK(gmres_start<T>(G, D.yp, rtol, s, cap));
     }
     CKS(gmres_run<T>(ctx, P, its, capped));
     P.stats.ainv_total += 2 + *its;
     {
         Scope sc(P.timer, HPG_K_ORTHO, s);
-        CK(gmres_finish(G, D.xs, s));
+        CK(gmres_finish<T>(G, D.xs, s));
     }
     {
         Scope sc(P.timer, HPG_K_PRECOND, s);
@@ -1238,7 +1239,7 @@ static hpg_status enqueue_kernel(hpg_ctx* ctx, Problem& P, int cls, bool f32, do
             else CK(launch_fdm<double>(D.gd, nullptr, alpha, D.tu_d, D.tu2_d, D.w1_d, D.w2_d, s));
             break;
         case HPG_K_PRECOND:
-            if (f32) CK(launch_precond<float, double, float>(D.gf, D.Sinv_f, D.yp, D.zp_f, s));
+            if (f32) CK(launch_precond<float, float, float>(D.gf, D.Sinv_f, gmres_basis<float>(D.gm), D.zp_f, s));
             else CK(launch_precond<double, double, double>(D.gd, D.Sinv_d, D.yp, D.zp_d, s));
             break;
         case HPG_K_BAPPLY:
@@ -1246,7 +1247,9 @@ static hpg_status enqueue_kernel(hpg_ctx* ctx, Problem& P, int cls, bool f32, do
             else CK(launch_bapply<double, double, double>(D.gd, D.zp_d, D.tu_d, s));
             break;
         case HPG_K_SCHUR:
-            if (f32) CK(launch_schur_rest<float, double>(D.gf, D.gwf, P.params.beta, D.zp_f, D.tu2_f, D.xs, s));
+            if (f32)
+                CK(launch_schur_rest<float, float>(D.gf, D.gwf, P.params.beta, D.zp_f, D.tu2_f,
+                                                   gmres_basis<float>(D.gm) + D.gm.N, s));
             else CK(launch_schur_rest<double, double>(D.gd, D.gwl, P.params.beta, D.zp_d, D.tu2_d, D.xs, s));
             break;
         case HPG_K_NEWTON_APPLY:
@@ -1261,7 +1264,9 @@ static hpg_status enqueue_kernel(hpg_ctx* ctx, Problem& P, int cls, bool f32, do
             break;
         case HPG_K_ORTHO:
             // one CGS2 Arnoldi step at j = kmax / 2, the mean j of a full Krylov cycle
-            CK(gmres_timed_step(D.gm, D.gm.kmax / 2, s));
+            // (float basis for the FP32 inner solves)
+            if (f32) CK(gmres_timed_step<float>(D.gm, D.gm.kmax / 2, s));
+            else CK(gmres_timed_step<double>(D.gm, D.gm.kmax / 2, s));
             break;
         default:
             return HPG_ERR_ARG;
@@ -1281,6 +1286,8 @@ hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, in
         // operands of this linearisation: the weights of the current state
         CK(cudaMemcpyAsync(D.gwl, D.gw, gsz * sizeof(double), cudaMemcpyDeviceToDevice, s));
         CK(launch_convert<double, float>(D.gwl, D.gwf, gsz, s));
+        // FP32 Krylov-loop kernels read the float basis: V_0 = yp
+        if (f32) CK(launch_convert<double, float>(D.yp, gmres_basis<float>(D.gm), D.gm.N, s));
         CK(cudaStreamSynchronize(s));
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
