@@ -1857,16 +1857,21 @@ __global__ void __launch_bounds__(256)
     const long long e0 = (long long)blockIdx.x * kDotChunk;
     const int len = (N - e0 < kDotChunk) ? (int)(N - e0) : kDotChunk;
     const VT* w = Vb + (long long)(j + 1) * N + e0;
-    for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) ws[t] = (t < len) ? w[t] : VT(0);
-    __syncthreads();
+    // full chunks on the float4 path read w straight from global memory (L1 serves
+    // the other warps); otherwise w is staged in shared memory first
+    const bool direct = VEC && len == kDotChunk;
+    if (!direct) {
+        for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) ws[t] = (t < len) ? w[t] : VT(0);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int i = i0 + wid;
     const long long ld = kmax + 2;
     if (i < nvec) {
         const VT* vi = (i <= j) ? Vb + (long long)i * N + e0 : nullptr;
         VT s0 = VT(0), s1 = VT(0);
-        if (VEC && len == kDotChunk) {
-            const float4* w4 = reinterpret_cast<const float4*>(ws);
+        if (direct) {
+            const float4* w4 = reinterpret_cast<const float4*>(w);
             if (vi) {
                 const float4* v4 = reinterpret_cast<const float4*>(vi);
                 float4 a[8];
@@ -1965,6 +1970,16 @@ __device__ __forceinline__ VT sub_basis(const VT* __restrict__ Vb, long long N, 
     return v;
 }
 
+// sum_{i < n} h[i]^2 by warp 0 (lane-strided partials, then a fixed xor tree);
+// the result is returned to lane 0 of warp 0
+__device__ __forceinline__ double warp_sumsq(const double* h, int n) {
+    const int lane = threadIdx.x & 31;
+    double q = 0.0;
+    for (int i = lane; i < n; i += 32) q += h[i] * h[i];
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    return q;
+}
+
 // Elements per block of the update kernels: FP64 one per thread; float 128.
 template <typename VT>
 constexpr int upd_elems() { return sizeof(VT) == 8 ? 256 : 128; }
@@ -2056,12 +2071,11 @@ __global__ void __launch_bounds__(256)
     if (iflag[0]) return;
     const int j = *jdev;
     load_sums(hsum, j + 2, h, hv);                  // h1[0..j], ||w||^2 in h[j+1]
-    if (threadIdx.x == 0) {
-        double q = 0.0;
-        for (int i = 0; i <= j; ++i) q += h[i] * h[i];
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const double q = warp_sumsq(h, j + 1);
         const double n1 = h[j + 1] - q;             // ||w1||^2
         const int r = (*force != 0) || !(n1 > 0.5 * h[j + 1]);
-        if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
             *reo = r;
             scal[4] = n1;
         }
@@ -2090,16 +2104,9 @@ __global__ void __launch_bounds__(256)
         for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = 0.0;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        double n2;
-        if (second) {
-            double q = 0.0;
-            for (int i = 0; i <= j; ++i) q += h[i] * h[i];
-            n2 = h[j + 1] - q;
-        } else {
-            n2 = scal[4];
-        }
-        shn = n2 > 0.0 ? sqrt(n2) : 0.0;
+    if (threadIdx.x < 32) {
+        const double n2 = second ? h[j + 1] - warp_sumsq(h, j + 1) : scal[4];
+        if (threadIdx.x == 0) shn = n2 > 0.0 ? sqrt(n2) : 0.0;
     }
     __syncthreads();
     const double hn = shn;
@@ -2120,11 +2127,14 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x == 0) {
         *counter = 0u;
         scol[j + 1] = hn;
+        // previous rotations; the rotated entry i+1 is carried in a register
+        double cr = scol[0];
         for (int i = 0; i < j; ++i) {
-            const double t = scs[i] * scol[i] + ssn[i] * scol[i + 1];
-            scol[i + 1] = -ssn[i] * scol[i] + scs[i] * scol[i + 1];
-            scol[i] = t;
+            const double b = scol[i + 1];
+            scol[i] = scs[i] * cr + ssn[i] * b;
+            cr = -ssn[i] * cr + scs[i] * b;
         }
+        scol[j] = cr;
         const double a = scol[j], bq = scol[j + 1];
         const double r = hypot(a, bq);
         double c = 1.0, sgv = 0.0;
