@@ -249,6 +249,8 @@ def kernel_only(args, ctx, w, stream, hpg, torch):
     kw = {}
     if args.fdm_tile >= 0:
         kw = {"fdm_tile_f32": args.fdm_tile} if prec == hpg.HPG_MIXED else {"fdm_tile_f64": args.fdm_tile}
+    if args.krylov_f32:
+        kw["krylov_f32"] = 1
     P = hpg.from_workload(ctx, w, hpg.default_params(precision=prec, **kw))
     rng = np.random.default_rng(7)
     u = np.zeros(P.n_u_full)
@@ -287,6 +289,8 @@ def main():
                     help="workload of the kernel-only mode (radial32, torsion, sine3d, ...)")
     ap.add_argument("--fdm-tile", type=int, default=-1,
                     help="force this fast-diagonalisation pass variant of the timed precision (-1: autotuned)")
+    ap.add_argument("--krylov-f32", action="store_true",
+                    help="kernel-only mode: the opt-in float GMRES basis of the FP32 inner solves")
     ap.add_argument("--batch", type=int, default=16, help="independent solves in flight per step")
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests of the serving workload (0 = skip; 512 = the full stream)")
@@ -475,28 +479,18 @@ def main():
         bw_roofs["precond"] = {"bound": "hbm", "bytes_per_launch": byts, "achieved": ach, "peak": peaks["hbm_gbs"],
                                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "avg_launch_us": avg_ms * 1000.0}
     if "ortho" in kt:
-        # float basis (FP32 inner solves): 0.5 flop/B is far below the FP32 ridge, so memory bounds it
-        # (the basis of one solve is L2-resident: a fraction above 1 would mean L2 service)
+        # FP64 Gram-Schmidt (the mixed path keeps it FP64): 0.25 flop/B is above the FP64 ridge
+        # (1.25 TFLOP/s / HBM), so the FP64 FMA rate bounds it
         _, fl, _ = work["ortho"]
-        byts = work["ortho_bytes"] / 2.0
         avg_ms = kt["ortho"][0]
-        ach = byts / (avg_ms / 1000.0) / 1e9
-        bw_roofs["ortho"] = {"kernel": "Arnoldi step, float basis, j = 75, both passes", "bound": "hbm",
-                             "bytes_per_launch": byts, "flops_per_launch": fl, "achieved": ach,
-                             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
-                             "avg_launch_us": avg_ms * 1000.0}
-    if "fp64" in results and "ortho" in results["fp64"]["kernels"]:
-        # FP64 basis: 0.25 flop/B is above the FP64 ridge (1.25 TFLOP/s / HBM), so the FP64 FMA rate bounds it
-        _, fl, _ = results["fp64"]["work"]["ortho"]
-        avg_ms = results["fp64"]["kernels"]["ortho"][0]
         ach = fl / (avg_ms / 1000.0) / 1e12
         pk = alu_peak_tflops("fp64", peak_mhz)
-        bw_roofs["ortho_fp64"] = {"kernel": "Arnoldi step, FP64 basis, j = 75, both passes", "bound": "alu",
-                                  "flops_per_launch": fl, "bytes_per_launch": work["ortho_bytes"],
-                                  "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                                  "achieved_gbs": work["ortho_bytes"] / (avg_ms / 1000.0) / 1e9,
-                                  "avg_launch_us": avg_ms * 1000.0,
-                                  "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz"}
+        bw_roofs["ortho"] = {"kernel": "Arnoldi step, FP64 basis, j = 75, both passes", "bound": "alu",
+                             "flops_per_launch": fl, "bytes_per_launch": work["ortho_bytes"],
+                             "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                             "achieved_gbs": work["ortho_bytes"] / (avg_ms / 1000.0) / 1e9,
+                             "avg_launch_us": avg_ms * 1000.0, "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz"}
+
     fp64_fdm = None
     if "fp64" in results and "fdm" in results["fp64"]["kernels"]:
         _, flops, _ = results["fp64"]["work"]["fdm"]
@@ -512,8 +506,12 @@ def main():
         for wname in ("radial4", "sine3d", "torsion"):
             wo = W.workload(wname)
             entry = {}
-            for pname, prec in (("mixed", hpg.HPG_MIXED), ("fp64", hpg.HPG_FP64)):
-                P = hpg.from_workload(ctx, wo, hpg.default_params(precision=prec))
+            # mixed_f32_basis: the opt-in float GMRES basis of the FP32 inner solves (krylov_f32)
+            for pname, prec, kw in (("mixed", hpg.HPG_MIXED, {}), ("fp64", hpg.HPG_FP64, {}),
+                                    ("mixed_f32_basis", hpg.HPG_MIXED, {"krylov_f32": 1})):
+                if kw and wname == "radial4":
+                    continue
+                P = hpg.from_workload(ctx, wo, hpg.default_params(precision=prec, **kw))
                 P.solve()                                   # warm-up (set-up, graph capture)
                 ts = []
                 for _ in range(max(1, min(args.steps, 3))):

@@ -126,6 +126,13 @@ typedef struct {
     int    strategy;      /* hpg_strategy; default HPG_SCHUR; the FGMRES strategies need
                              precision HPG_FP64 (HPG_ERR_ARG otherwise)                       */
     int    inner_max;     /* HPG_FGMRES_PF: inner GMRES iterations per application; default 10 */
+    int    krylov_f32;    /* 0 (default): the GMRES basis and its Gram-Schmidt are FP64 in both
+                             precisions (the mixed form keeps Krylov orthogonalisation in FP64);
+                             1: with HPG_MIXED the FP32 inner solves store and orthogonalise
+                             their basis in FP32 (per-lane products and updates in FP32, lane and
+                             chunk sums, Hessenberg and Givens in FP64) -- faster, outside that
+                             rule; the FP64 refinement still sets the accuracy.  Ignored for
+                             HPG_FP64.                                                          */
 } hpg_params;
 
 #define HPG_MAX_ALPHA 128

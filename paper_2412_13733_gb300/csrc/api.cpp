@@ -71,6 +71,7 @@ void hpg_default_params(hpg_params* p) {
     p->fdm_tile_f64 = -1;
     p->strategy = HPG_SCHUR;
     p->inner_max = 10;
+    p->krylov_f32 = 0;
 }
 
 const char* hpg_status_str(hpg_status s) {
@@ -298,7 +299,8 @@ hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params) {
         params->fdm_tile_f32 < -1 || params->fdm_tile_f32 >= hpg::fdm_tile_count(4) ||
         params->fdm_tile_f64 < -1 || params->fdm_tile_f64 >= hpg::fdm_tile_count(8) ||
         params->strategy < HPG_SCHUR || params->strategy > HPG_FGMRES_PF ||
-        (params->strategy != HPG_SCHUR && params->precision != HPG_FP64) || params->inner_max < 1)
+        (params->strategy != HPG_SCHUR && params->precision != HPG_FP64) || params->inner_max < 1 ||
+        (params->krylov_f32 != 0 && params->krylov_f32 != 1))
         return HPG_ERR_ARG;
     const bool realloc = P->alloc_done && (params->krylov_max != P->params.krylov_max ||
                                            params->fdm_tile_f32 != P->params.fdm_tile_f32 ||

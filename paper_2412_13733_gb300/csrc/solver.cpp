@@ -581,7 +581,7 @@ static hpg_status schur_apply_T(hpg_ctx* ctx, Problem& P, double alpha, const T*
 // z = S-hat^{-1} V_j, w = S z written into V_{j+1}, Arnoldi/Givens update.
 // Iteration index, stop flag and alpha are read on the device, so the same
 // launches can be captured once into a CUDA graph and replayed.
-template <typename T>
+template <typename T, typename VT>
 static hpg_status gmres_chunk(hpg_ctx* ctx, Problem& P, int chunk) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
@@ -591,7 +591,7 @@ static hpg_status gmres_chunk(hpg_ctx* ctx, Problem& P, int chunk) {
     for (int c = 0; c < chunk; ++c) {
         {
             Scope sc(P.timer, HPG_K_PRECOND, s);
-            CK(launch_precond<T, T, T>(g, PV<T>::Sinv(D), gmres_basis<T>(G), PV<T>::zp(D), s, ctl));
+            CK(launch_precond<T, VT, T>(g, PV<T>::Sinv(D), gmres_basis<VT>(G), PV<T>::zp(D), s, ctl));
         }
         {
             Scope sc(P.timer, HPG_K_BAPPLY, s);
@@ -604,12 +604,12 @@ static hpg_status gmres_chunk(hpg_ctx* ctx, Problem& P, int chunk) {
         }
         {
             Scope sc(P.timer, HPG_K_SCHUR, s);
-            CK(launch_schur_rest<T, T>(g, PV<T>::gw(D), P.params.beta, PV<T>::zp(D), PV<T>::tu2(D),
-                                       gmres_basis<T>(G), s, ctl));
+            CK(launch_schur_rest<T, VT>(g, PV<T>::gw(D), P.params.beta, PV<T>::zp(D), PV<T>::tu2(D),
+                                        gmres_basis<VT>(G), s, ctl));
         }
         {
             Scope sc(P.timer, HPG_K_ORTHO, s);
-            CK(gmres_arnoldi<T>(G, s));
+            CK(gmres_arnoldi<VT>(G, s));
         }
     }
     return HPG_OK;
@@ -621,7 +621,7 @@ constexpr int kGraphChunk = 2;
 // node whose body is `kGraphChunk` iterations followed by a kernel that sets
 // the loop condition from the stop flag.  One launch runs GMRES to its stop
 // flag with no host round trip.  Returns false if the runtime lacks support.
-template <typename T>
+template <typename T, typename VT>
 static bool build_gmres_loop(hpg_ctx* ctx, Problem& P, cudaGraphExec_t* exec, long long* kernels_per_body) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
@@ -648,7 +648,7 @@ static bool build_gmres_loop(hpg_ctx* ctx, Problem& P, cudaGraphExec_t* exec, lo
         return false;
     }
     const long long before = kernel_launch_count();
-    hpg_status st = gmres_chunk<T>(ctx, P, kGraphChunk);
+    hpg_status st = gmres_chunk<T, VT>(ctx, P, kGraphChunk);
     if (st == HPG_OK && launch_gm_setcond(h, D.gm.iflag, s) != cudaSuccess) st = HPG_ERR_CUDA;
     *kernels_per_body = kernel_launch_count() - before;
     add_kernel_launches(-*kernels_per_body);
@@ -662,16 +662,16 @@ static bool build_gmres_loop(hpg_ctx* ctx, Problem& P, cudaGraphExec_t* exec, lo
 
 // Run GMRES to its stop flag: one launch of the device-side loop graph (or
 // eager launches when kernel timing is on), then one read of the flags.
-template <typename T>
+template <typename T, typename VT>
 static hpg_status gmres_run(hpg_ctx* ctx, Problem& P, int* its, bool* capped) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
     GmresDev& G = D.gm;
-    const int pi = sizeof(T) == sizeof(float) ? 1 : 0;
+    const int pi = sizeof(T) == sizeof(float) ? (sizeof(VT) == sizeof(float) ? 2 : 1) : 0;
     const bool use_graph = !P.timer.on && P.params.graphs != 0;
     if (use_graph && !D.gmres_graph[pi] && !D.gmres_graph_failed[pi]) {
         long long nk = 0;
-        if (!build_gmres_loop<T>(ctx, P, &D.gmres_graph[pi], &nk)) {
+        if (!build_gmres_loop<T, VT>(ctx, P, &D.gmres_graph[pi], &nk)) {
             D.gmres_graph[pi] = nullptr;
             D.gmres_graph_failed[pi] = true;
         } else {
@@ -686,7 +686,7 @@ static hpg_status gmres_run(hpg_ctx* ctx, Problem& P, int* its, bool* capped) {
         add_kernel_launches(D.graph_kernels[pi] * ((D.h_iflag[5] + kGraphChunk - 1) / kGraphChunk + 1));
     } else {
         for (int guard = 0; guard <= G.kmax; ++guard) {
-            CKS(gmres_chunk<T>(ctx, P, 1));
+            CKS(gmres_chunk<T, VT>(ctx, P, 1));
             CK(cudaMemcpyAsync(D.h_iflag + 4, G.iflag, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (D.h_iflag[4]) break;
@@ -705,10 +705,10 @@ static hpg_status gmres_run(hpg_ctx* ctx, Problem& P, int* its, bool* capped) {
 
 // eq. (schur2): y = b_psi - B^T A^{-1} b_u; GMRES on S (right-preconditioned by
 // S-hat); delta_u = A^{-1}(b_u - B delta_psi).  Right-hand sides and results FP64,
-// operators and the GMRES basis in T.
-template <typename T>
-static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const double* bu, const double* bp,
-                                double* du, double* dp, double rtol, int* its, bool* capped, int cap = 0) {
+// operators in T, the GMRES basis and its Gram-Schmidt in VT.
+template <typename T, typename VT>
+static hpg_status schur_solve_TV(hpg_ctx* ctx, Problem& P, double alpha, const double* bu, const double* bp,
+                                 double* du, double* dp, double rtol, int* its, bool* capped, int cap) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
     const Geo<T>& g = PV<T>::g(D);
@@ -726,13 +726,13 @@ static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const do
     }
     {
         Scope sc(P.timer, HPG_K_ORTHO, s);
-        CK(gmres_start<T>(G, D.yp, rtol, s, cap));
+        CK(gmres_start<VT>(G, D.yp, rtol, s, cap));
     }
-    CKS(gmres_run<T>(ctx, P, its, capped));
+    CKS(gmres_run<T, VT>(ctx, P, its, capped));
     P.stats.ainv_total += 2 + *its;
     {
         Scope sc(P.timer, HPG_K_ORTHO, s);
-        CK(gmres_finish<T>(G, D.xs, s));
+        CK(gmres_finish<VT>(G, D.xs, s));
     }
     {
         Scope sc(P.timer, HPG_K_PRECOND, s);
@@ -750,6 +750,15 @@ static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const do
     CKS(fdm_T<T>(ctx, P, alpha, tu, tu2));
     CK(from_T<T>(tu2, du, Nu0, s));
     return HPG_OK;
+}
+
+// FP64 basis unless the FP32 inner solves are asked for a float basis (krylov_f32)
+template <typename T>
+static hpg_status schur_solve_T(hpg_ctx* ctx, Problem& P, double alpha, const double* bu, const double* bp,
+                                double* du, double* dp, double rtol, int* its, bool* capped, int cap = 0) {
+    if constexpr (sizeof(T) == sizeof(float))
+        if (P.params.krylov_f32) return schur_solve_TV<T, float>(ctx, P, alpha, bu, bp, du, dp, rtol, its, capped, cap);
+    return schur_solve_TV<T, double>(ctx, P, alpha, bu, bp, du, dp, rtol, its, capped, cap);
 }
 
 // ---- flexible GMRES on G with a block preconditioner (Section 4.3) -------------
@@ -1233,13 +1242,15 @@ hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double r
 static hpg_status enqueue_kernel(hpg_ctx* ctx, Problem& P, int cls, bool f32, double alpha) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
+    const bool fb = f32 && P.params.krylov_f32 != 0;     // float GMRES basis
     switch (cls) {
         case HPG_K_FDM:
             if (f32) CK(launch_fdm<float>(D.gf, nullptr, alpha, D.tu_f, D.tu2_f, D.w1_f, D.w2_f, s));
             else CK(launch_fdm<double>(D.gd, nullptr, alpha, D.tu_d, D.tu2_d, D.w1_d, D.w2_d, s));
             break;
         case HPG_K_PRECOND:
-            if (f32) CK(launch_precond<float, float, float>(D.gf, D.Sinv_f, gmres_basis<float>(D.gm), D.zp_f, s));
+            if (fb) CK(launch_precond<float, float, float>(D.gf, D.Sinv_f, gmres_basis<float>(D.gm), D.zp_f, s));
+            else if (f32) CK(launch_precond<float, double, float>(D.gf, D.Sinv_f, D.yp, D.zp_f, s));
             else CK(launch_precond<double, double, double>(D.gd, D.Sinv_d, D.yp, D.zp_d, s));
             break;
         case HPG_K_BAPPLY:
@@ -1247,9 +1258,10 @@ static hpg_status enqueue_kernel(hpg_ctx* ctx, Problem& P, int cls, bool f32, do
             else CK(launch_bapply<double, double, double>(D.gd, D.zp_d, D.tu_d, s));
             break;
         case HPG_K_SCHUR:
-            if (f32)
+            if (fb)
                 CK(launch_schur_rest<float, float>(D.gf, D.gwf, P.params.beta, D.zp_f, D.tu2_f,
                                                    gmres_basis<float>(D.gm) + D.gm.N, s));
+            else if (f32) CK(launch_schur_rest<float, double>(D.gf, D.gwf, P.params.beta, D.zp_f, D.tu2_f, D.xs, s));
             else CK(launch_schur_rest<double, double>(D.gd, D.gwl, P.params.beta, D.zp_d, D.tu2_d, D.xs, s));
             break;
         case HPG_K_NEWTON_APPLY:
@@ -1264,8 +1276,8 @@ static hpg_status enqueue_kernel(hpg_ctx* ctx, Problem& P, int cls, bool f32, do
             break;
         case HPG_K_ORTHO:
             // one CGS2 Arnoldi step at j = kmax / 2, the mean j of a full Krylov cycle
-            // (float basis for the FP32 inner solves)
-            if (f32) CK(gmres_timed_step<float>(D.gm, D.gm.kmax / 2, s));
+            // (float basis for FP32 inner solves with krylov_f32)
+            if (fb) CK(gmres_timed_step<float>(D.gm, D.gm.kmax / 2, s));
             else CK(gmres_timed_step<double>(D.gm, D.gm.kmax / 2, s));
             break;
         default:
@@ -1280,14 +1292,14 @@ hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, in
     const long long gsz = (long long)(P.H.Nq * gauss_stride(P.H.kind, P.H.d));
     const bool f32 = precision == HPG_MIXED;
     const double alpha = P.state_alpha > 0.0 ? P.state_alpha : (P.H.alphas.empty() ? 1.0 : P.H.alphas.back());
-    const long long key = ((long long)cls * 4 + (f32 ? 1 : 0)) * 1000003LL + reps;
+    const long long key = ((long long)cls * 4 + (f32 ? 1 : 0) + (f32 && P.params.krylov_f32 ? 2 : 0)) * 1000003LL + reps;
     auto it = D.bench_graphs.find(key);
     if (it == D.bench_graphs.end()) {
         // operands of this linearisation: the weights of the current state
         CK(cudaMemcpyAsync(D.gwl, D.gw, gsz * sizeof(double), cudaMemcpyDeviceToDevice, s));
         CK(launch_convert<double, float>(D.gwl, D.gwf, gsz, s));
-        // FP32 Krylov-loop kernels read the float basis: V_0 = yp
-        if (f32) CK(launch_convert<double, float>(D.yp, gmres_basis<float>(D.gm), D.gm.N, s));
+        // FP32 Krylov-loop kernels with a float basis read it: V_0 = yp
+        if (f32 && P.params.krylov_f32) CK(launch_convert<double, float>(D.yp, gmres_basis<float>(D.gm), D.gm.N, s));
         CK(cudaStreamSynchronize(s));
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));

@@ -52,9 +52,10 @@ struct DevState {
     double* fwork_d = nullptr;                   // factor workspace when blocks exceed shared memory
     float* fwork_f = nullptr;
     double* alpha_dev = nullptr;                 // alpha of the current proximal step (device)
-    cudaGraphExec_t gmres_graph[2] = {nullptr, nullptr};   // captured GMRES chunk per precision
-    long long graph_kernels[2] = {0, 0};                    // kernels in one loop body
-    bool gmres_graph_failed[2] = {false, false};            // conditional graphs unsupported
+    // captured GMRES loop per (operator, basis) precision: FP64/FP64, FP32/FP64, FP32/FP32
+    cudaGraphExec_t gmres_graph[3] = {nullptr, nullptr, nullptr};
+    long long graph_kernels[3] = {0, 0, 0};                 // kernels in one loop body
+    bool gmres_graph_failed[3] = {false, false, false};     // conditional graphs unsupported
     std::map<long long, std::pair<cudaGraphExec_t, long long>> bench_graphs;   // hpg_launch_kernel replays
     double *eg = nullptr, *egt = nullptr;
     double *F = nullptr, *Ft = nullptr, *delta = nullptr, *r = nullptr, *dcorr = nullptr;

@@ -39,9 +39,9 @@ def oracle_solution(name):
     return _ORACLE_CACHE[name]
 
 
-def gpu_solve(ctx, w, precision):
+def gpu_solve(ctx, w, precision, **kw):
     from paper_2412_13733_gb300 import hpg
-    P = hpg.from_workload(ctx, w, hpg.default_params(precision=precision))
+    P = hpg.from_workload(ctx, w, hpg.default_params(precision=precision, **kw))
     P.solve()
     return P, P.u(), P.psi(), P.stats()
 
@@ -65,6 +65,44 @@ def test_full_solve_matches_oracle(ctx, name, precision):
     o, r = oracle_solution(name)
     P, u, psi, st = gpu_solve(ctx, case(name), precision)
     _check(o, r, u, psi, st, 1e-9 if precision == 0 else 1e-8, 1e-8 if precision == 0 else 1e-7)
+    P.free()
+
+
+@pytest.mark.parametrize("name", ["radial4", "p2", "sine3d_small", "torsion_small", "box3d_p3_m4"])
+def test_mixed_float_krylov_basis_matches_oracle(ctx, name):
+    """Opt-in float GMRES basis of the FP32 inner solves (krylov_f32 = 1): the FP64
+    refinement still brings the result to the mixed path's accuracy."""
+    o, r = oracle_solution(name)
+    P, u, psi, st = gpu_solve(ctx, case(name), 1, krylov_f32=1)
+    _check(o, r, u, psi, st, 1e-8, 1e-7)
+    P.free()
+
+
+def test_mixed_float_krylov_basis_full_size(ctx):
+    """The 32x32 p=8 radial obstacle with the float basis against the stored oracle run."""
+    from paper_2412_13733_gb300 import workloads as W
+    from oracle.space import TensorSpace
+    path = os.path.join(GOLDEN, "radial32_oracle.npz")
+    if not os.path.exists(path):
+        pytest.skip("stored oracle result missing")
+    g = np.load(path)
+    w = W.workload("radial32")
+    P, u, psi, st = gpu_solve(ctx, w, 1, krylov_f32=1)
+    assert st["status"] == 0
+    for a, b in zip(st["newton_per_step"], g["newton"]):
+        assert abs(a - b) <= 1
+    S = TensorSpace(w["breakpoints"], w["p"])
+    e = u - g["u"]
+    assert np.sqrt(e @ (S.M @ e)) / np.sqrt(g["u"] @ (S.M @ g["u"])) <= 1e-8
+    assert rel(psi, g["psi"]) <= 1e-7
+    P.free()
+
+
+def test_krylov_f32_flag_validated(ctx):
+    from paper_2412_13733_gb300 import hpg
+    P = hpg.from_workload(ctx, case("radial4"), hpg.default_params(precision=1))
+    with pytest.raises(hpg.HpgError):
+        P.set_params(hpg.default_params(precision=1, krylov_f32=2))
     P.free()
 
 
