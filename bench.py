@@ -403,13 +403,14 @@ def main():
         clk = sampler.stop() if sampler else None
         total_ms = max_over_ranks(sum(times), dist, torch, "cuda")
         st = ps[0].stats()
+        fdm_variant = st["fdm_tile_f32"] if prec == hpg.HPG_MIXED else st["fdm_tile_f64"]
         dofs = ps[0].n_u + ps[0].n_psi
         kry = sum(P.stats()["krylov_total"] for P in ps)
         res = dict(value=replica_throughput(count * args.steps, world, total_ms), ms_per_step=total_ms / args.steps,
                    batch=count, newton=st["newton_total"], krylov=st["krylov_total"], refine=st["refine_total"],
                    launches=sum(P.stats()["kernel_launches"] for P in ps),
                    dof_krylov_per_s=world * dofs * kry / (total_ms / args.steps / 1000.0), clocks=clk,
-                   h2d=int(sum(P.stats()["h2d_bytes"] for P in ps)))
+                   h2d=int(sum(P.stats()["h2d_bytes"] for P in ps)), fdm_variant=fdm_variant)
         res["e2e"] = None
         if with_e2e and not args.no_e2e:
             host_phi = np.ascontiguousarray(w["phi"](ps[0].quad_points()), dtype=np.float64)
@@ -610,6 +611,9 @@ def main():
                 "e2e": head["e2e"], "gpu_launches": int(head["launches"] * args.steps),
                 "roofline": roof, "newton_apply_roofline": newton_roof, "other_rooflines": bw_roofs,
                 "kernel_avg_us": {k: v[0] * 1000.0 for k, v in kt.items()},
+                # FDM pass variant picked by the set-up autotuner (hpg_fdm_tile_count; the last two FP32
+                # variants are the tcgen05 kernels); pass it to --fdm-tile to reproduce a run under ncu
+                "fdm_variant": {"mixed": head["fdm_variant"], "fp64": fp["fdm_variant"] if fp else None},
                 "other_workloads": others, "solver_strategies": strategies, "serving": serving, "clocks": clocks,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
