@@ -19,6 +19,10 @@ import os
 # the oracle baseline runs single-threaded (SuperLU is sequential; BLAS pinned to 1 thread)
 for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
+# the batched solves and the request loop run 16 streams: give them as many hardware
+# work queues (the default of 8 makes streams share queues and wait on each other);
+# read when the CUDA context is created, so set before torch touches the device
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import argparse
 import json
