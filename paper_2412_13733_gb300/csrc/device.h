@@ -55,6 +55,8 @@ struct Geo {
     TileCols tu[kMaxDim];                     // u columns of the A, M stencils per row tile
     TileCols tp[kMaxDim];                     // psi columns (packed) of the B, Bd stencils
     int staged;                               // 1: the u-row kernels stage value boxes in shared memory
+    const int* perm0;                         // n1[0] rows of axis 0 in the order the unstaged u-row
+                                              // tiles take them (sorted by stencil counts), or null
 };
 
 // Number of values stored per Gauss point by the evaluation kernel:

@@ -187,6 +187,10 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
     const int org[kMaxDim] = {tix[0] * T0, tix[1] * T1, tix[2] * T2};
     const bool grad = g.kind == HPG_GRADIENT;
     const bool staged = g.staged != 0;
+    // unstaged path: rows along axis 0 in the order perm0 (equal stencil counts side by
+    // side, so the lanes of a warp run loops of equal length); the staged path keeps
+    // the natural order its column lists were built for
+    const int* perm0 = staged ? nullptr : g.perm0;
     // stage the stencil rows of this tile (tile-local columns on the staged path)
     for (int op = 0; op < NOPS; ++op) {
         if ((op == OP_A || op == OP_M) && !HAS_A) continue;
@@ -196,8 +200,9 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
             const Sten<T>& S = op_of(g, op, j);
             const int* cols = staged ? S.lcol : S.col;
             for (int e = threadIdx.x; e < tile[j] * kEll; e += blockDim.x) {
-                const int l = e / kEll, k = e % kEll, r = org[j] + l;
-                if (r < g.n1[j]) {
+                const int l = e / kEll, k = e % kEll, pos = org[j] + l;
+                if (pos < g.n1[j]) {
+                    const int r = (j == 0 && perm0) ? perm0[pos] : pos;
                     st.col[op][j][l][k] = cols[(size_t)r * kEll + k];
                     st.val[op][j][l][k] = S.val[(size_t)r * kEll + k];
                     if (k == 0) st.cnt[op][j][l] = S.cnt[r];
@@ -243,8 +248,9 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
     }
     __syncthreads();
     const int l0 = threadIdx.x % T0, l1 = (threadIdx.x / T0) % T1, l2 = threadIdx.x / (T0 * T1);
-    const int r0 = org[0] + l0, r1 = org[1] + l1, r2 = (D == 3) ? org[2] + l2 : 0;
-    const bool inside = r0 < g.n1[0] && r1 < g.n1[1] && (D == 2 || r2 < g.n1[2]);
+    const int p0 = org[0] + l0, r1 = org[1] + l1, r2 = (D == 3) ? org[2] + l2 : 0;
+    const bool inside = p0 < g.n1[0] && r1 < g.n1[1] && (D == 2 || r2 < g.n1[2]);
+    const int r0 = (perm0 && inside) ? perm0[p0] : p0;
     const int n1x = g.n1[0], n1y = g.n1[1];
     double v = 0.0;
     long long i = 0;

@@ -209,6 +209,24 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     bool ok = true;
     const int d = H.d;
     const bool grad = H.kind == HPG_GRADIENT;
+    {
+        // axis-0 row order of the FP64 u-row tiles: rows grouped by their stencil counts
+        // (a hierarchical vertex row couples to more columns than a bubble row), so that
+        // the 32 lanes of a warp run equally long gather loops; stable, so rows of equal
+        // counts keep their natural order
+        const Dir1D& D0 = H.dir[0];
+        std::vector<int> perm(D0.n1);
+        for (int r = 0; r < D0.n1; ++r) perm[r] = r;
+        auto key = [&](int r) {
+            return std::make_tuple(D0.Ai.cnt[r], D0.Mi.cnt[r], D0.Bi.cnt[r], grad ? D0.Bdi.cnt[r] : 0);
+        };
+        std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return key(a) < key(b); });
+        D.perm0 = dalloc<int>(D, perm.size(), ok);
+        if (ok) {
+            cudaMemcpyAsync(D.perm0, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+            ok = cudaStreamSynchronize(s) == cudaSuccess;
+        }
+    }
     for (int j = 0; j < d; ++j) {
         const Dir1D& Dj = H.dir[j];
         ok = ok && upload_sten(D, Dj.Ai, false, H.n, D.A[j], s);
@@ -340,6 +358,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
         sel(g);
     };
     fill(D.gd, [&](Geo<double>& g) {
+        g.perm0 = D.perm0;
         for (int j = 0; j < d; ++j) {
             g.A[j] = {D.A[j].cnt, D.A[j].col, D.A[j].vd, D.A[j].lcol};
             g.M[j] = {D.M[j].cnt, D.M[j].col, D.M[j].vd, D.M[j].lcol};
@@ -355,6 +374,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
         g.Vq = D.Vq_d; g.wq = D.wq_d; g.detJ = H.detJ; g.Mpsi = D.Mpsi_d; g.Kpsi = D.Kpsi_d; g.C = D.C_d;
     });
     fill(D.gf, [&](Geo<float>& g) {
+        g.perm0 = nullptr;               // FP32 tiles keep the natural order (coalesced gathers)
         for (int j = 0; j < d; ++j) {
             g.A[j] = {D.A[j].cnt, D.A[j].col, D.A[j].vf, D.A[j].lcol};
             g.M[j] = {D.M[j].cnt, D.M[j].col, D.M[j].vf, D.M[j].lcol};

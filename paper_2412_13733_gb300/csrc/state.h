@@ -52,6 +52,7 @@ struct DevState {
     double* fwork_d = nullptr;                   // factor workspace when blocks exceed shared memory
     float* fwork_f = nullptr;
     double* alpha_dev = nullptr;                 // alpha of the current proximal step (device)
+    int* perm0 = nullptr;                        // axis-0 row order of the FP64 u-row tiles
     // captured GMRES loop per (operator, basis) precision: FP64/FP64, FP32/FP64, FP32/FP32
     cudaGraphExec_t gmres_graph[3] = {nullptr, nullptr, nullptr};
     long long graph_kernels[3] = {0, 0, 0};                 // kernels in one loop body
