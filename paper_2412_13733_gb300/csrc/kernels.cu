@@ -187,10 +187,11 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
     const int org[kMaxDim] = {tix[0] * T0, tix[1] * T1, tix[2] * T2};
     const bool grad = g.kind == HPG_GRADIENT;
     const bool staged = g.staged != 0;
-    // unstaged path: rows along axis 0 in the order perm0 (equal stencil counts side by
-    // side, so the lanes of a warp run loops of equal length); the staged path keeps
-    // the natural order its column lists were built for
-    const int* perm0 = staged ? nullptr : g.perm0;
+    // FP64, unstaged path: rows along axis 0 in the order perm0 (equal stencil counts side
+    // by side, so the lanes of a warp run loops of equal length); the staged path keeps the
+    // natural order its column lists were built for, and the FP32 kernels (bound by gather
+    // latency, not arithmetic) are compiled without it
+    const int* perm0 = (sizeof(T) == 8 && !staged) ? g.perm0 : nullptr;
     // stage the stencil rows of this tile (tile-local columns on the staged path)
     for (int op = 0; op < NOPS; ++op) {
         if ((op == OP_A || op == OP_M) && !HAS_A) continue;
