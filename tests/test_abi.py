@@ -53,3 +53,33 @@ def test_host_only_calls_without_gpu(libpath):
     assert p.newton_tol == 1e-10 and p.krylov_max == 150
     # a NULL output pointer is rejected, never dereferenced
     assert L.hpg_create(None, 0, None) == 1
+
+
+def struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/hpg.h, in order."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    bodies = dict((n, body) for body, n in re.findall(r"typedef struct\s*\{([^{}]*)\}\s*(\w+)\s*;", src))
+    assert name in bodies, name
+    fields = []
+    for decl in bodies[name].split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        head, *rest = [t.strip() for t in decl.split(",")]
+        fields.append(re.sub(r"\[.*\]", "", head.split()[-1]).lstrip("*"))
+        fields.extend(re.sub(r"\[.*\]", "", r).lstrip("*") for r in rest)
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("hpg_params", "hpg_params"), ("hpg_stats", "hpg_stats")])
+def test_binding_structs_mirror_header(cname, pyname):
+    """The ctypes structures lay out the same fields, in the same order, as the C header."""
+    from paper_2412_13733_gb300 import hpg
+    py = [f[0] for f in getattr(hpg, pyname)._fields_]
+    assert py == struct_fields(cname)
+
+
+def test_default_params_keep_fp64_orthogonalisation(libpath):
+    from paper_2412_13733_gb300 import hpg
+    p = hpg.default_params()
+    assert p.krylov_f32 == 0 and p.strategy == hpg.HPG_SCHUR and p.precision == hpg.HPG_FP64
