@@ -245,7 +245,11 @@ hpg_status hpg_solve(hpg_ctx* ctx, int pid);
  * distinct.  Blocking.  Returns HPG_OK if every problem converged, else the
  * first failure in id order; per-problem status in hpg_stats. */
 hpg_status hpg_solve_batch(hpg_ctx* ctx, const int* pids, int count);
-/* Number of concurrent workers/streams of hpg_solve_batch (1..64, default 8). */
+/* Number of concurrent workers/streams of hpg_solve_batch (1..64, default 8).
+ * With more than 8 streams, set the environment variable
+ * CUDA_DEVICE_MAX_CONNECTIONS (e.g. to 32) before the process creates its CUDA
+ * context: with the driver's default of 8 hardware work queues, streams share
+ * queues and their kernels wait on each other. */
 hpg_status hpg_set_concurrency(hpg_ctx* ctx, int streams);
 
 /* Results of the last solve (u in the caller's sign convention). */
