@@ -38,6 +38,11 @@ def case(name):
         w = W.workload("torsion_small")
         w.update(breakpoints=[W.uniform(0, 1, 3)] * 2, p=3)
         return w
+    if name == "grad3d_2x3x2_p3":
+        # gradient constraint in 3D: three psi components, derivative Grams on every axis
+        w = W.workload("torsion_small")
+        w.update(name=name, dim=3, breakpoints=[W.uniform(0, 1, 2), W.uniform(0, 1, 3), W.uniform(0, 1, 2)], p=3)
+        return w
     if name.startswith("box3d_"):
         w = W.workload(name)
         w["tol"] = 1e-10          # parity gates at the usual Newton tolerance

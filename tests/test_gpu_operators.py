@@ -19,7 +19,7 @@ from tests.gpu_helpers import case, oracle_for, random_state, rel
 pytestmark = pytest.mark.gpu
 
 OBSTACLE_CASES = ["radial_3x3_p5", "aniso_upper", "p2", "single_cell", "sine3d_small", "sine3d_3x2x2"]
-ALL_CASES = OBSTACLE_CASES + ["torsion_small", "torsion_3x3_p3"]
+ALL_CASES = OBSTACLE_CASES + ["torsion_small", "torsion_3x3_p3", "grad3d_2x3x2_p3"]
 
 
 @pytest.fixture(scope="module")

@@ -59,7 +59,7 @@ def _check(o, r, u, psi, st, u_tol, psi_tol):
 
 
 @pytest.mark.parametrize("name", ["radial4", "aniso_upper", "p2", "single_cell", "sine3d_small", "torsion_small",
-                                  "box3d_p3_m4"])
+                                  "box3d_p3_m4", "grad3d_2x3x2_p3"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_full_solve_matches_oracle(ctx, name, precision):
     o, r = oracle_solution(name)
@@ -68,7 +68,7 @@ def test_full_solve_matches_oracle(ctx, name, precision):
     P.free()
 
 
-@pytest.mark.parametrize("name", ["radial4", "p2", "sine3d_small", "torsion_small", "box3d_p3_m4"])
+@pytest.mark.parametrize("name", ["radial4", "p2", "sine3d_small", "torsion_small", "box3d_p3_m4", "grad3d_2x3x2_p3"])
 def test_mixed_float_krylov_basis_matches_oracle(ctx, name):
     """Opt-in float GMRES basis of the FP32 inner solves (krylov_f32 = 1): the FP64
     refinement still brings the result to the mixed path's accuracy."""
