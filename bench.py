@@ -38,6 +38,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "radial32"
+# dram__bytes_read.sum + dram__bytes_write.sum of the four k_gemm_fullk<float,32,16,4,2,4> passes of
+# one A_alpha^{-1} apply on the 32x32 p=8 workload (ncu, profiles/fdm_gemm_fp32_radial32.md)
+FDM_TRAFFIC_BYTES = (573952 + 575744 + 574720 + 573952)
 METRIC = "solves/s (complete hpG solve at 1e-8 rel err vs FP64 oracle), mixed vs FP64; DoF*Krylov-its/s"
 
 
@@ -463,8 +466,11 @@ def main():
         avg_ms = kt["fdm"][0]
         ach = flops / (avg_ms / 1000.0) / 1e12
         peak = alu_peak_tflops("fp32", peak_mhz)
+        # DRAM bytes of one apply (4 passes) from the ncu capture of FDM variant 0 on this
+        # workload (profiles/fdm_gemm_fp32_radial32.md); null if the autotuner picked another
+        traffic = FDM_TRAFFIC_BYTES if mixed["fdm_variant"] == 0 else None
         roof = {"kernel": "fdm (A_alpha^-1, FP32 SIMT GEMM passes)", "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": unit, "frac": ach / peak, "traffic": None, "avg_launch_us": avg_ms * 1000.0,
+                "unit": unit, "frac": ach / peak, "traffic": traffic, "avg_launch_us": avg_ms * 1000.0,
                 "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x {peak_mhz:.0f} MHz"}
     newton_roof = None
     if "newton_apply" in kt:
