@@ -41,9 +41,10 @@ def _taylor_slopes(F, J, x, h):
     return np.log(r[:-1] / r[1:]) / np.log(2.0)
 
 
-def test_taylor_obstacle():
-    o = ObstacleOracle([np.linspace(0, 1, 3), np.linspace(0, 1, 4)], 4, W.const_field(3.0),
-                       lambda X: 0.3 + 0.1 * X[:, 0], None, beta=0.0)
+@pytest.mark.parametrize("bps,p", [([np.linspace(0, 1, 3), np.linspace(0, 1, 4)], 4),
+                                   ([np.linspace(0, 1, 3), np.linspace(0, 1, 2), np.linspace(0, 1, 3)], 3)])
+def test_taylor_obstacle(bps, p):
+    o = ObstacleOracle(bps, p, W.const_field(3.0), lambda X: 0.3 + 0.1 * X[:, 0], None, beta=0.0)
     rng = np.random.default_rng(0)
     ni = len(o.interior)
     u0 = o.ulift.copy()
@@ -63,8 +64,11 @@ def test_taylor_obstacle():
     assert np.all(s > 1.9), s
 
 
-def test_taylor_gradient():
-    o = GradientOracle([np.linspace(0, 1, 3)] * 2, 3, W.const_field(8.0), W.torsion_phi, beta=0.0)
+@pytest.mark.parametrize("bps,p", [([np.linspace(0, 1, 3)] * 2, 3),
+                                   ([np.linspace(0, 1, 3), np.linspace(0, 1, 2), np.linspace(0, 1, 2)], 2)])
+def test_taylor_gradient(bps, p):
+    """2D and 3D (three psi components, the derivative Gram on each axis)."""
+    o = GradientOracle(bps, p, W.const_field(8.0), W.torsion_phi, beta=0.0)
     rng = np.random.default_rng(1)
     ni = len(o.interior)
     psi = 0.5 * rng.normal(size=o.sp.Npsi)
