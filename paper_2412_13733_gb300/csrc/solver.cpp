@@ -911,6 +911,12 @@ static hpg_status fgmres_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
 // if it stops at its cap the FP64 residual r = F - G delta is formed and the
 // solve is repeated on r (a restart).  Mixed: FP32 inner solves inside FP64
 // iterative refinement until ||F - G delta|| <= eta ||F||.
+// tolerance of the FP32 inner solve, relative to the reduction the refinement still needs:
+// half of it (measured against a tenth: 6 % fewer inner iterations on the 32x32 p=8 obstacle,
+// 5 % on torsion, 7 % on the 3D obstacle, same Newton counts, a few more second sweeps;
+// single solves 2.6 %, 5 % and 9 % faster)
+constexpr double kInnerMargin = 0.5;
+
 static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* F, double normF, double eta,
                                double* delta, int* its_total, int* sweeps) {
     DevState& D = P.D;
@@ -926,10 +932,10 @@ static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
         int its = 0;
         bool capped = false;
         // GMRES tolerance relative to the current residual r, aimed at ||r|| <= eta ||F||:
-        // FP64 exactly; FP32 a decade below, floored near the FP32 limit, so that one
-        // refinement sweep usually suffices
+        // FP64 exactly; FP32 with a margin below it (kInnerMargin), floored near the FP32
+        // limit, so that one refinement sweep usually suffices
         const double need = eta * normF / std::max(rnorm, 1e-300);
-        const double rt = f64 ? std::min(1.0, need) : std::min(1.0, std::max(0.1 * need, 1e-6));
+        const double rt = f64 ? std::min(1.0, need) : std::min(1.0, std::max(kInnerMargin * need, 1e-6));
         if (f64 && P.params.strategy != HPG_SCHUR) {
             int outer = 0;
             CKS(fgmres_solve(ctx, P, alpha, D.r, rt, D.dcorr, &outer, &capped));
