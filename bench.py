@@ -39,7 +39,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "radial32"
 # dram__bytes_read.sum + dram__bytes_write.sum of the four k_gemm_fullk<float,32,16,4,2,4> passes of
-# one A_alpha^{-1} apply on the 32x32 p=8 workload (ncu, profiles/fdm_gemm_fp32_radial32.md)
+# one A_alpha^{-1} apply on the 32x32 p=8 workload, from one ncu capture (`--kernel fdm
+# --precision mixed --fdm-tile 0`, cold caches)
 FDM_TRAFFIC_BYTES = (573952 + 575744 + 574720 + 573952)
 METRIC = "solves/s (complete hpG solve at 1e-8 rel err vs FP64 oracle), mixed vs FP64; DoF*Krylov-its/s"
 
@@ -172,7 +173,7 @@ def replica_throughput(units_per_rank, world, total_ms):
 
 # ------------------------------------------------------------------ GPU legs
 def algorithmic_work(P, w):
-    """Per-launch algorithmic FLOPs / bytes of the kernel classes (see DESIGN.md)."""
+    """Per-launch algorithmic FLOPs / bytes of the kernel classes."""
     d = len(w["breakpoints"])
     n1 = [len(b) - 1 for b in w["breakpoints"]]
     n1 = [m * w["p"] - 1 for m in n1]
@@ -467,7 +468,7 @@ def main():
         ach = flops / (avg_ms / 1000.0) / 1e12
         peak = alu_peak_tflops("fp32", peak_mhz)
         # DRAM bytes of one apply (4 passes) from the ncu capture of FDM variant 0 on this
-        # workload (profiles/fdm_gemm_fp32_radial32.md); null if the autotuner picked another
+        # workload; null if the autotuner picked another variant
         traffic = FDM_TRAFFIC_BYTES if mixed["fdm_variant"] == 0 else None
         roof = {"kernel": "fdm (A_alpha^-1, FP32 SIMT GEMM passes)", "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": unit, "frac": ach / peak, "traffic": traffic, "avg_launch_us": avg_ms * 1000.0,
