@@ -2,8 +2,8 @@
 
 * Taylor test: the sparse Newton matrix is the derivative of the residual
   (||F(x + eps h) - F(x) - eps J h|| = O(eps^2)), obstacle and gradient.
-* Brute force: the obstacle subproblem is the saddle point of a
-  convex-concave function; eliminating u gives a concave dual in psi whose
+* Brute force: the obstacle and gradient subproblems are saddle points of
+  convex-concave functions; eliminating u gives a concave dual in psi whose
   maximiser (L-BFGS, no Newton, no G) must equal the Newton fixed point.
 * eq. (schur2) with exact inner solves equals the direct solve of G.
 * Feasibility by construction (eq. pG: u = phi - exp(-psi)) and the discrete
@@ -115,6 +115,43 @@ def test_subproblem_matches_dual_maximisation():
     res = so.minimize(negdual, psi_prev.copy(), jac=True, method="L-BFGS-B",
                       options=dict(gtol=1e-13, ftol=1e-16, maxiter=20000, maxcor=50))
     assert np.max(np.abs(res.x - psi)) < 1e-6 * max(1.0, np.abs(psi).max())
+
+
+def test_gradient_subproblem_matches_dual_maximisation():
+    """Gradient kind: the subproblem is the saddle point of
+    alpha (a(u,u)/2 - (f,u)) + u^T B (psi - psi_prev) - H(psi), H(psi) = sum_q w_q |J| phi_q
+    sqrt(1 + |psi_q|^2), whose psi-gradient is the projection of G(psi) in F_psi.  Eliminating u
+    leaves the concave dual -r^T A^{-1} r / (2 alpha) - H(psi), r = alpha (f, v) - B (psi - psi_prev);
+    its maximiser (L-BFGS, no Newton, no G) must equal the Newton fixed point."""
+    o = GradientOracle([np.linspace(0, 1, 3)] * 2, 3, W.const_field(8.0), W.torsion_phi, beta=0.0)
+    S = o.sp
+    rng = np.random.default_rng(6)
+    psi_prev = 0.3 * rng.normal(size=S.Npsi)
+    alpha = 0.2
+    u0, _ = o.initial_state()
+    u, psi, it, info = o.newton(u0, psi_prev.copy(), psi_prev, alpha, tol=1e-13)
+    assert info["converged"]
+    I = o.interior
+    lu = spla.splu(o.A00.tocsc())
+    bf = o.bf[I]
+
+    def negdual(ps):
+        r = alpha * bf - o.B0 @ (ps - psi_prev)
+        z = lu.solve(r)
+        pq = o.gauss_values(ps)                              # (Nc, d, q)
+        sq = np.sqrt(1.0 + np.sum(pq * pq, axis=1))          # (Nc, q)
+        H = np.sum(S.wJ * o.phiq * sq)
+        val = -0.5 / alpha * r @ z - H
+        gH = np.einsum("cq,ckq,qj->ckj", S.wJ * o.phiq / sq, pq, S.Vd).ravel()
+        grad = o.B0.T @ z / alpha - gH
+        return -val, -grad
+
+    res = so.minimize(negdual, psi_prev.copy(), jac=True, method="L-BFGS-B",
+                      options=dict(gtol=1e-13, ftol=1e-16, maxiter=20000, maxcor=50))
+    assert np.max(np.abs(res.x - psi)) < 1e-6 * max(1.0, np.abs(psi).max())
+    # and u is the minimiser in u for that psi
+    uu = lu.solve(alpha * bf - o.B0 @ (psi - psi_prev)) / alpha
+    assert np.max(np.abs(uu - u[I])) < 1e-8 * max(1.0, np.abs(u[I]).max())
 
 
 def test_schur_sequence_equals_direct_solve():
