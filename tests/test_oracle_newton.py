@@ -86,8 +86,13 @@ def test_taylor_gradient(bps, p):
     assert np.all(s > 1.9), s
 
 
-def test_subproblem_matches_dual_maximisation():
-    o = _radial(2, 3, beta=1e-4)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_subproblem_matches_dual_maximisation(dim):
+    if dim == 2:
+        o = _radial(2, 3, beta=1e-4)
+    else:
+        o = ObstacleOracle([np.linspace(0, 1, 3), np.linspace(0, 1, 2), np.linspace(0, 1, 3)], 3,
+                           W.const_field(40.0), lambda X: 0.05 + 0.02 * X[:, 0], None, beta=1e-4)
     rng = np.random.default_rng(5)
     psi_prev = 0.3 * rng.normal(size=o.sp.Npsi)
     alpha = 0.05
