@@ -3,6 +3,12 @@
 Usage: python tests/golden/make_golden.py [radial32] [sine3d] [torsion]
 Each run stores u (full, caller sign), psi, Newton counts per proximal step and
 metadata in tests/golden/<name>_oracle.npz.
+
+The 3D workload (sine3d, 8^3 hexes, p = 6) solves each Newton system by exact
+block elimination of psi (``linear="eliminate_psi"``): the direct sparse LU of
+the whole Newton matrix needs more than the host's 62 GB, the eliminated system
+about 7 GB; both give the same delta up to rounding (pinned in
+tests/test_oracle_newton.py).
 """
 import os
 import platform
@@ -25,7 +31,9 @@ def run(name):
     if w["kind"] == "gradient":
         o = GradientOracle(w["breakpoints"], w["p"], w["f"], w["phi"], beta=w["beta"])
     else:
-        o = ObstacleOracle(w["breakpoints"], w["p"], w["f"], w["phi"], w["g"], beta=w["beta"], lower=w["lower"])
+        linear = "eliminate_psi" if w["dim"] == 3 else "direct"
+        o = ObstacleOracle(w["breakpoints"], w["p"], w["f"], w["phi"], w["g"], beta=w["beta"], lower=w["lower"],
+                           linear=linear)
     r = o.solve(w["alphas"], tol=w["tol"], log=lambda s: print(name, s, flush=True))
     dt = time.time() - t0
     out = os.path.join(HERE, f"{name}_oracle.npz")

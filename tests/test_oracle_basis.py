@@ -134,6 +134,55 @@ def test_spectral_galerkin_cell_matrices():
     assert set(np.abs(i - j).tolist()) == {0, 2}
 
 
+def _spectral_closed_forms(h, p):
+    """(Y_a', Y_b')_K, (Y_a, Y_b)_K, (Y_a, P_k)_K on a cell of width h, from
+    Y_a = P_a - P_{a+2} and (P_a, P_b) = 2 delta_ab / (2a+1) on (-1, 1), scaled
+    by dx = (h/2) dy and d/dx = (2/h) d/dy."""
+    nb = p - 1
+    KY = np.zeros((nb, nb))
+    MY = np.zeros((nb, nb))
+    BY = np.zeros((nb, nb))
+    for a in range(nb):
+        KY[a, a] = (2.0 / h) * 2.0 * (2 * a + 3)
+        MY[a, a] = (h / 2.0) * (2.0 / (2 * a + 1) + 2.0 / (2 * a + 5))
+        if a + 2 < nb:
+            MY[a, a + 2] = MY[a + 2, a] = -(h / 2.0) * 2.0 / (2 * a + 5)
+        BY[a, a] = (h / 2.0) * 2.0 / (2 * a + 1)
+        if a + 2 < nb:
+            BY[a, a + 2] = -(h / 2.0) * 2.0 / (2 * a + 5)
+    return KY, MY, BY
+
+
+def test_spectral_cell_matrices_closed_forms():
+    # every entry of the three 1D cell matrices, on cells of several widths
+    for h, p in [(0.3, 9), (1.7, 5), (2.0, 2)]:
+        got = osch.spectral_cell_matrices(h, p)
+        want = _spectral_closed_forms(h, p)
+        for g, w in zip(got, want):
+            assert np.allclose(g, w, atol=1e-12 * max(1.0, np.abs(w).max()), rtol=0)
+
+
+@pytest.mark.parametrize("hs,p", [([0.3, 0.7], 5), ([0.25, 0.5], 8), ([0.4, 0.2, 0.9], 4)])
+def test_shat_constant_block_against_closed_forms(hs, p):
+    # C_K = B-hat^T A-hat_1^{-1} B-hat of eq. (schur-preconditioner) on one cell, built
+    # entry by entry (x index fastest) from the closed forms, then one dense solve
+    d, nb = len(hs), p - 1
+    mats = [_spectral_closed_forms(h, p) for h in hs]
+    idx = np.array(np.unravel_index(np.arange(nb ** d), (nb,) * d, order="F")).T   # x fastest
+    N = nb ** d
+    Ahat = np.zeros((N, N))
+    Bhat = np.zeros((N, N))
+    for I in range(N):
+        for J in range(N):
+            a, b = idx[I], idx[J]
+            Bhat[I, J] = np.prod([mats[j][2][a[j], b[j]] for j in range(d)])
+            for k in range(d):
+                Ahat[I, J] += np.prod([mats[j][0 if j == k else 1][a[j], b[j]] for j in range(d)])
+    C_want = Bhat.T @ np.linalg.solve(Ahat, Bhat)
+    C_got, _, _ = osch.shat_constant_block(hs, p)
+    assert np.allclose(C_got, C_want, atol=1e-12 * np.abs(C_want).max(), rtol=0)
+
+
 def test_shat_parity_blocks_2d():
     # Section 4.5: A-hat has 4 blocks per 2D cell (parities of the two degrees)
     import scipy.sparse.csgraph as csg
