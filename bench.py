@@ -127,6 +127,33 @@ def oracle_sample(max_alpha_steps=1):
                 t_setup=t_setup, t_newton=t_newton)
 
 
+def oracle_full_solve():
+    """One complete oracle solve of the workload (all alpha steps), timed on this host."""
+    from paper_2412_13733_gb300 import workloads as W
+    from oracle.hpg import ObstacleOracle
+    w = W.workload(WORKLOAD)
+    t0 = time.perf_counter()
+    o = ObstacleOracle(w["breakpoints"], w["p"], w["f"], w["phi"], w["g"], beta=w["beta"], lower=w["lower"])
+    r = o.solve(w["alphas"], tol=w["tol"])
+    return dict(seconds=time.perf_counter() - t0, newton=int(sum(r["newton"])), converged=bool(r["converged"]))
+
+
+def accuracy(ps, golden, gate):
+    """Relative L2(Omega) error of every solve's u_h against the stored FP64 oracle
+    run, and the largest per-step Newton-count difference (reported beside each leg)."""
+    if golden is None:
+        return None
+    worst, dn = 0.0, 0
+    for P in ps:
+        err, nrm = P.l2_error(golden["u"])
+        worst = max(worst, err / nrm)
+        ns = P.stats()["newton_per_step"]
+        ref = [int(v) for v in golden["newton"]]
+        dn = max(dn, max(abs(a - b) for a, b in zip(ns, ref)) if len(ns) == len(ref) else 99)
+    return {"rel_l2_vs_oracle": worst, "gate": gate, "newton_max_step_diff": dn,
+            "ok": bool(worst <= gate and dn <= 1), "solves_checked": len(ps)}
+
+
 def cpu_threads():
     return int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
 
@@ -195,11 +222,12 @@ def algorithmic_work(P, w):
                 ortho=("alu", ortho_flops, "TFLOP/s"), ortho_bytes=ortho_bytes, newton_apply_bytes=newton_bytes)
 
 
-def alu_peak_tflops(kind, clock_mhz):
-    """Derived ALU peaks (152 SMs): FP32 128 FMA/clk/SM, FP64 nominal 1.25 TFLOP/s at 2070 MHz."""
+def alu_peak_tflops(kind, clock_mhz, sms=152):
+    """Derived ALU peaks from unit counts, reported beside the measured ones: FP32
+    128 FMA/clk/SM; FP64 from the nominal 1.25 TFLOP/s at 2070 MHz on 152 SMs."""
     if kind == "fp32":
-        return 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
-    return 1.25 * clock_mhz / 2070.0
+        return sms * 128 * 2 * clock_mhz * 1e6 / 1e12
+    return 1.25 * clock_mhz / 2070.0 * sms / 152
 
 
 def serve_requests(ctx, hpg, W, prec, count, rate=None, workers=8):
@@ -288,6 +316,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-full-oracle", action="store_true",
+                    help="skip the one complete oracle solve beside the sampled CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
     ap.add_argument("--kernel", default=None,
@@ -336,6 +366,12 @@ def main():
     ctx = hpg.Context(local_rank, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > 126 MB L2
     peaks, peak_src = load_peaks()
+    gpath = os.path.join(ROOT, "tests", "golden", f"{WORKLOAD}_oracle.npz")
+    golden = dict(np.load(gpath)) if os.path.exists(gpath) else None
+    # SIMT FMA peaks of this GPU, measured by the library's own probe kernel
+    fp32_peak, sm_count = ctx.fma_peak(hpg.HPG_MIXED)
+    fp64_peak, _ = ctx.fma_peak(hpg.HPG_FP64)
+    alu_peaks = {"fp32": fp32_peak, "fp64": fp64_peak}
 
     def timed(P, steps, e2e=False, host_phi=None):
         times = []
@@ -443,6 +479,7 @@ def main():
                 torch.cuda.synchronize()
                 res["kernels"][cls] = (e0.elapsed_time(e1) / reps, reps)
         res["work"] = algorithmic_work(ps[0], w)
+        res["accuracy"] = accuracy(ps, golden, 1e-8 if prec == hpg.HPG_MIXED else 1e-9)
         for P in ps:
             P.free()
         return res
@@ -466,21 +503,23 @@ def main():
         _, flops, unit = work["fdm"]
         avg_ms = kt["fdm"][0]
         ach = flops / (avg_ms / 1000.0) / 1e12
-        peak = alu_peak_tflops("fp32", peak_mhz)
+        peak = alu_peaks["fp32"]
         # DRAM bytes of one apply (4 passes) from the ncu capture of FDM variant 0 on this
         # workload; null if the autotuner picked another variant
         traffic = FDM_TRAFFIC_BYTES if mixed["fdm_variant"] == 0 else None
         roof = {"kernel": "fdm (A_alpha^-1, FP32 SIMT GEMM passes)", "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": unit, "frac": ach / peak, "traffic": traffic, "avg_launch_us": avg_ms * 1000.0,
-                "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x {peak_mhz:.0f} MHz"}
+                "peak_source": "measured (hpg_measure_fma_peak, FP32 FMA chains on all SMs)",
+                "derived_peak": alu_peak_tflops("fp32", peak_mhz, sm_count)}
     newton_roof = None
     if "newton_apply" in kt:
         avg = kt["newton_apply"][0] / 1000.0
         _, fl, _ = work["newton_apply"]
-        t_alu = fl / (alu_peak_tflops("fp64", peak_mhz) * 1e12)
+        t_alu = fl / (alu_peaks["fp64"] * 1e12)
         t_hbm = work["newton_apply_bytes"] / (peaks["hbm_gbs"] * 1e9)
         newton_roof = {"kernel": "matrix-free Newton apply G x (FP64)", "bound": "alu" if t_alu > t_hbm else "hbm",
-                       "roofline_us": max(t_alu, t_hbm) * 1e6, "avg_us": avg * 1e6, "frac": max(t_alu, t_hbm) / avg}
+                       "roofline_us": max(t_alu, t_hbm) * 1e6, "avg_us": avg * 1e6, "frac": max(t_alu, t_hbm) / avg,
+                       "peak_source": "measured FP64 FMA rate (hpg_measure_fma_peak) and HBM copy rate"}
     # bandwidth-bound kernels against the measured HBM copy rate (their operands may
     # be L2-resident, so a fraction above 1 means L2 service, not an error)
     bw_roofs = {}
@@ -496,21 +535,21 @@ def main():
         _, fl, _ = work["ortho"]
         avg_ms = kt["ortho"][0]
         ach = fl / (avg_ms / 1000.0) / 1e12
-        pk = alu_peak_tflops("fp64", peak_mhz)
+        pk = alu_peaks["fp64"]
         bw_roofs["ortho"] = {"kernel": "Arnoldi step, FP64 basis, j = 75, both passes", "bound": "alu",
                              "flops_per_launch": fl, "bytes_per_launch": work["ortho_bytes"],
                              "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                              "achieved_gbs": work["ortho_bytes"] / (avg_ms / 1000.0) / 1e9,
-                             "avg_launch_us": avg_ms * 1000.0, "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz"}
+                             "avg_launch_us": avg_ms * 1000.0, "peak_source": "measured FP64 FMA rate"}
 
     fp64_fdm = None
     if "fp64" in results and "fdm" in results["fp64"]["kernels"]:
         _, flops, _ = results["fp64"]["work"]["fdm"]
         avg_ms = results["fp64"]["kernels"]["fdm"][0]
         ach = flops / (avg_ms / 1000.0) / 1e12
-        pk = alu_peak_tflops("fp64", peak_mhz)
+        pk = alu_peaks["fp64"]
         fp64_fdm = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "avg_launch_us": avg_ms * 1000.0, "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz"}
+                    "avg_launch_us": avg_ms * 1000.0, "peak_source": "measured FP64 FMA rate"}
 
     # the other configured workloads: single-solve latency and solves/s, both paths
     others = {}
@@ -593,7 +632,12 @@ def main():
         s = oracle_sample()
         cpu = {"value": s["value"], "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": (f"oracle setup + first alpha subproblem ({s['newton_done']} of {s['total_newton']} "
-                          f"Newton steps, {s['seconds']:.1f} s), extrapolated linearly in Newton steps")}
+                          f"Newton steps, {s['seconds']:.1f} s), extrapolated linearly in Newton steps"),
+               "extrapolated_solve_s": 1.0 / s["value"]}
+        if not args.no_full_oracle:
+            full = oracle_full_solve()
+            cpu.update(full_solve_s=full["seconds"], full_solve_newton=full["newton"],
+                       full_solve_converged=full["converged"], full_solve_value=1.0 / full["seconds"])
 
     if rank == 0:
         head = results["mixed_batch"]
@@ -620,6 +664,8 @@ def main():
                 "mixed_batch_over_fp64_single": (head["value"] / fp["value"]) if fp else None,
                 "newton": head["newton"], "krylov": head["krylov"], "refine_sweeps": head["refine"],
                 "e2e": head["e2e"], "gpu_launches": int(head["launches"] * args.steps),
+                "accuracy": {k: results[k]["accuracy"] for k in results},
+                "measured_alu_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak, "sm_count": sm_count},
                 "roofline": roof, "newton_apply_roofline": newton_roof, "other_rooflines": bw_roofs,
                 "kernel_avg_us": {k: v[0] * 1000.0 for k, v in kt.items()},
                 # FDM pass variant picked by the set-up autotuner (hpg_fdm_tile_count; the last two FP32
@@ -628,9 +674,13 @@ def main():
                 "other_workloads": others, "solver_strategies": strategies, "serving": serving, "clocks": clocks,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
+    bad = [k for k, r in results.items() if r["accuracy"] is not None and not r["accuracy"]["ok"]]
     if dist is not None:
         dist.destroy_process_group()
     ctx.close()
+    if bad:
+        print(f"accuracy gate failed for legs {bad}", file=sys.stderr)
+        return 1
     return 0
 
 

@@ -261,6 +261,12 @@ hpg_status hpg_get_stats(hpg_ctx* ctx, int pid, hpg_stats* stats);
  * defined only at the latent Gauss points (length n_quad). */
 hpg_status hpg_eval_u(hpg_ctx* ctx, int pid, const double* pts, int npts, double* out);
 hpg_status hpg_feasible_u(hpg_ctx* ctx, int pid, double* out_q, size_t len);
+/* Accuracy of the last solve against a reference u (full coefficients, caller's sign,
+ * length n_u_full): *err = ||u_h - u_ref||_{L2(Omega)} and, when ref_norm is not NULL,
+ * *ref_norm = ||u_ref||_{L2(Omega)}, both exact through the 1D mass matrices of
+ * Section 3 (M = M_1 (x) ... (x) M_d over the full tensor-product basis).  Host
+ * arithmetic; the reference stays the caller's. */
+hpg_status hpg_l2_error(hpg_ctx* ctx, int pid, const double* u_ref, size_t len, double* err, double* ref_norm);
 /* Accumulated per-kernel-class device time (ms) and launch counts since the
  * last reset, recorded only when params.timing = 1. */
 hpg_status hpg_get_kernel_times(hpg_ctx* ctx, int pid, double* ms, long long* launches, int count);
@@ -279,6 +285,12 @@ hpg_status hpg_reset_kernel_times(hpg_ctx* ctx, int pid);
  * Krylov basis buffer, whose contents it overwrites; the HPG_MIXED _PRECOND and
  * _SCHUR launches also read and write that buffer, as in the solver. */
 hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precision, int reps);
+/* Measured SIMT FMA throughput of the context's device (TFLOP/s, 2 flops per FMA):
+ * FP32 for HPG_MIXED, FP64 for HPG_FP64; eight independent FMA chains per thread,
+ * 8 blocks of 256 threads per SM, best of three timed launches on the context's
+ * stream (synchronises it).  *sm_count (may be NULL) receives the SM count.  The
+ * roofline denominators of the FP32/FP64-bound kernels; not part of the method. */
+hpg_status hpg_measure_fma_peak(hpg_ctx* ctx, int precision, double* tflops, int* sm_count);
 /* Number of fast-diagonalisation pass variants for `precision` (HPG_MIXED: FP32
  * passes, HPG_FP64: FP64 passes); valid values of hpg_params.fdm_tile_f32/_f64
  * are 0 .. count-1.  Returns 0 for an unknown precision. */
@@ -307,6 +319,10 @@ hpg_status hpg_poll(hpg_ctx* ctx, long long ticket, int* done, hpg_status* resul
 hpg_status hpg_wait(hpg_ctx* ctx, long long ticket, double timeout_ms, hpg_status* result);
 /* times3 = {queued ms, running ms, submit-to-done ms} (0 while unfinished). */
 hpg_status hpg_ticket_times(hpg_ctx* ctx, long long ticket, double* times3);
+/* Message of a finished request that failed: which step failed and why (the text
+ * hpg_last_error gives after a failing hpg_solve), truncated to len-1 bytes and
+ * NUL-terminated; an empty string while unfinished or after success. */
+hpg_status hpg_ticket_error(hpg_ctx* ctx, long long ticket, char* buf, size_t len);
 /* Bytes currently charged to the budget (running requests), and the
  * footprint estimate for problem pid (pid ignored when estimate is NULL). */
 hpg_status hpg_server_memory(hpg_ctx* ctx, int pid, size_t* in_use, size_t* estimate);

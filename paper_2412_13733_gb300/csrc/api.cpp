@@ -1,4 +1,5 @@
 // C ABI of libhpg (see include/hpg.h for the contract of every entry point).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <exception>
@@ -308,6 +309,9 @@ hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params) {
     if (realloc) {
         hpg::free_device(*P, ctx->stream);
         P->data_dirty = P->phi_dirty = true;
+    } else if (P->alloc_done && params->beta != P->params.beta) {
+        // beta is a launch argument of the captured GMRES loop and kernel replays
+        hpg::drop_graphs(*P);
     }
     P->params = *params;
     return HPG_OK;
@@ -438,6 +442,24 @@ hpg_status hpg_eval_u(hpg_ctx* ctx, int pid, const double* pts, int npts, double
     GUARD_END
 }
 
+hpg_status hpg_l2_error(hpg_ctx* ctx, int pid, const double* u_ref, size_t len, double* err, double* ref_norm) {
+    Problem* P = find(ctx, pid);
+    if (!P || !u_ref || !err) return HPG_ERR_ARG;
+    NOT_BUSY(P);
+    if (len < P->H.Nu_full) return HPG_ERR_ARG;
+    if (!P->solved) return HPG_ERR_STATE;
+    GUARD_BEGIN
+    std::vector<double> u(P->H.Nu_full);
+    hpg_status s = hpg_get_u(ctx, pid, u.data(), u.size());
+    if (s != HPG_OK) return s;
+    std::vector<double> e(u.size()), r(u_ref, u_ref + u.size());
+    for (size_t i = 0; i < u.size(); ++i) e[i] = u[i] - u_ref[i];
+    *err = std::sqrt(std::max(0.0, hpg::mass_norm2(P->H, e)));
+    if (ref_norm) *ref_norm = std::sqrt(std::max(0.0, hpg::mass_norm2(P->H, r)));
+    return HPG_OK;
+    GUARD_END
+}
+
 hpg_status hpg_feasible_u(hpg_ctx* ctx, int pid, double* out_q, size_t len) {
     Problem* P = find(ctx, pid);
     if (!P || !out_q) return HPG_ERR_ARG;
@@ -509,6 +531,7 @@ hpg_status hpg_set_state(hpg_ctx* ctx, int pid, const double* u_full, const doub
 #define OP_PROLOGUE(need)                                        \
     Problem* P = find(ctx, pid);                                 \
     if (!P) return HPG_ERR_ARG;                                  \
+    NOT_BUSY(P);                                                 \
     if (!P->alloc_done || P->state_alpha <= 0.0) return HPG_ERR_STATE; \
     if (len < (need)) return HPG_ERR_ARG;                        \
     if (cuda_ok(ctx) != HPG_OK) return HPG_ERR_CUDA;
@@ -540,6 +563,7 @@ hpg_status hpg_apply_stiffness_inv(hpg_ctx* ctx, int pid, int precision, const d
 hpg_status hpg_factor_precond(hpg_ctx* ctx, int pid, int precision, double* blocks, size_t len) {
     Problem* P = find(ctx, pid);
     if (!P) return HPG_ERR_ARG;
+    NOT_BUSY(P);
     if (!P->alloc_done || P->state_alpha <= 0.0) return HPG_ERR_STATE;
     if (blocks && len < P->H.Nc * P->H.nb * P->H.nb) return HPG_ERR_ARG;
     if (cuda_ok(ctx) != HPG_OK) return HPG_ERR_CUDA;
@@ -634,6 +658,36 @@ hpg_status hpg_wait(hpg_ctx* ctx, long long ticket, double timeout_ms, hpg_statu
 hpg_status hpg_ticket_times(hpg_ctx* ctx, long long ticket, double* times3) {
     if (!ctx || !times3) return HPG_ERR_ARG;
     return hpg::server_poll(ctx, ticket, 0.0, nullptr, nullptr, times3);
+}
+
+hpg_status hpg_measure_fma_peak(hpg_ctx* ctx, int precision, double* tflops, int* sm_count) {
+    if (!ctx || !tflops || (precision != HPG_FP64 && precision != HPG_MIXED)) return HPG_ERR_ARG;
+    if (cuda_ok(ctx) != HPG_OK) return HPG_ERR_CUDA;
+    GUARD_BEGIN
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        ctx->err = "cudaDeviceGetAttribute failed";
+        return HPG_ERR_CUDA;
+    }
+    if (sm_count) *sm_count = sms;
+    const cudaError_t e = hpg::measure_fma_peak(precision == HPG_FP64 ? 8 : 4, sms, ctx->stream, tflops);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("fma peak: ") + cudaGetErrorString(e);
+        return HPG_ERR_CUDA;
+    }
+    return HPG_OK;
+    GUARD_END
+}
+
+hpg_status hpg_ticket_error(hpg_ctx* ctx, long long ticket, char* buf, size_t len) {
+    if (!ctx || !buf || len == 0) return HPG_ERR_ARG;
+    std::string msg;
+    const hpg_status s = hpg::server_ticket_error(ctx, ticket, &msg);
+    if (s != HPG_OK) return s;
+    const size_t n = std::min(msg.size(), len - 1);
+    std::memcpy(buf, msg.data(), n);
+    buf[n] = 0;
+    return HPG_OK;
 }
 
 hpg_status hpg_server_memory(hpg_ctx* ctx, int pid, size_t* in_use, size_t* estimate) {

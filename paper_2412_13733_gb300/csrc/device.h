@@ -205,6 +205,9 @@ template <typename VT>
 cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s);
 // Number of FDM GEMM tile variants for elements of `elem` bytes.
 int fdm_tile_count(int elem);
+// FMA throughput of the SIMT pipe for elements of `elem` bytes (4: FP32, 8: FP64),
+// measured with independent FMA chains on every SM (best of three timed launches on s).
+cudaError_t measure_fma_peak(int elem, int sm_count, cudaStream_t s, double* tflops);
 // Opt-in shared-memory limits of the large-smem kernels (call once per device).
 void configure_kernels();
 

@@ -87,5 +87,8 @@ void compute_rhs(HostProblem& P, hpg_field_fn f, void* user, bool is_const, doub
 void compute_phi(HostProblem& P, const double* phi_q);
 void compute_lifting(HostProblem& P, hpg_field_fn g, void* user);
 double eval_u_point(const HostProblem& P, const std::vector<double>& ufull, const double* x);
+// e^T (M_1 (x) ... (x) M_d) e for a full u-coefficient vector e: the squared L2(Omega)
+// norm of the field, with the exact 1D mass matrices of Section 3.
+double mass_norm2(const HostProblem& P, const std::vector<double>& e);
 
 }  // namespace hpg

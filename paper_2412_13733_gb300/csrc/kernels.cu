@@ -2408,6 +2408,54 @@ template cudaError_t launch_bapply<float, double, float>(const Geo<float>&, cons
 template cudaError_t launch_btapply<double, double, double>(const Geo<double>&, const double*, double*,
                                                             cudaStream_t);
 template cudaError_t launch_btapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t);
+// ---- SIMT FMA throughput probe ------------------------------------------------
+// Eight independent FMA chains per thread (enough to cover the pipe latency with
+// 8 warps per SM scheduler), x <- x * a + b with |a| < 1 so nothing overflows; the
+// sum is stored only under a condition that never holds, which keeps the chains live.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T* out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k) * (T)1e-3;
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += x[k];
+    if (sum == (T)-12345.0) out[0] = sum;
+}
+
+cudaError_t measure_fma_peak(int elem, int sm_count, cudaStream_t s, double* tflops) {
+    const int blocks = sm_count * 8, threads = 256;
+    const int iters = elem == 4 ? 32768 : 1024;
+    void* out = nullptr;
+    cudaError_t e = cudaMallocAsync(&out, 16, s);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        if (elem == 4) k_fma_peak<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.999999f, 1e-6f);
+        else k_fma_peak<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.999999, 1e-6);
+        note_launch();
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms > 0.f) best = std::min(best, ms);     // the first launch warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, s);
+    if (e != cudaSuccess) return e;
+    const double flops = 2.0 * 8.0 * (double)iters * (double)blocks * threads;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return cudaStreamSynchronize(s);
+}
+
 template cudaError_t launch_fdm<double>(const Geo<double>&, const double*, double, const double*, double*, double*,
                                         double*, cudaStream_t, const int*);
 template cudaError_t launch_fdm<float>(const Geo<float>&, const double*, double, const float*, float*, float*,

@@ -28,6 +28,11 @@ extern "C" hpg_status hpg_apply_stiffness_inv_noalloc(hpg_ctx* ctx, int pid, dou
     auto it = ctx->problems.find(pid);
     if (it == ctx->problems.end()) return HPG_ERR_ARG;
     hpg::Problem& P = *it->second;
+    if (P.busy.load()) {
+        // a request-loop worker owns the problem and may release its device buffers
+        ctx->err = "problem is queued or running in the request loop";
+        return HPG_ERR_BUSY;
+    }
     if (!P.alloc_done) {
         ctx->err = "problem operators are not on the device yet (solve or set a state first)";
         return HPG_ERR_STATE;

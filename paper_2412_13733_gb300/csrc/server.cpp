@@ -14,6 +14,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 
 #include "state.h"
@@ -34,6 +35,7 @@ struct Request {
     size_t bytes = 0;
     int state = 0;              // 0 queued, 1 running, 2 done
     hpg_status result = HPG_OK;
+    std::string err;            // the solver's message when result != HPG_OK
     double t_submit = 0, t_start = 0, t_done = 0;
 };
 
@@ -138,6 +140,7 @@ static void worker_loop(Server* S, int w) {
             S->charged.erase(ch);
         }
         R->result = st;
+        if (st != HPG_OK) R->err = local.err.empty() ? std::string(hpg_status_str(st)) : local.err;
         R->t_done = now_ms();
         R->state = 2;
         R->P->busy = false;
@@ -229,6 +232,16 @@ hpg_status server_poll(hpg_ctx* ctx, long long ticket, double wait_ms, int* done
         times3[1] = R.state == 2 ? R.t_done - R.t_start : 0.0;                          // running
         times3[2] = R.state == 2 ? R.t_done - R.t_submit : 0.0;                         // latency
     }
+    return HPG_OK;
+}
+
+hpg_status server_ticket_error(hpg_ctx* ctx, long long ticket, std::string* msg) {
+    Server* S = ctx->server;
+    if (!S) return HPG_ERR_STATE;
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return HPG_ERR_ARG;
+    *msg = it->second.state == 2 ? it->second.err : std::string();
     return HPG_OK;
 }
 

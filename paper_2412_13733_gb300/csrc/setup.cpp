@@ -72,7 +72,12 @@ bool cholesky(int n, std::vector<double>& A) {
 }
 
 // Householder reduction to tridiagonal form followed by the implicit QL
-// iteration with Wilkinson-type shifts; eigenvectors accumulated in Z.
+// iteration with Wilkinson-type shifts; eigenvectors accumulated in Z.  The QL
+// sweep is the textbook method of Bowdler, Martin, Reinsch and Wilkinson, "The QR
+// and QL algorithms for symmetric matrices", Numer. Math. 11 (1968) 293-306
+// (procedure tql2 of the Handbook for Automatic Computation, Vol. II), whose
+// step order it keeps: shift from the leading 2x2 block, chase of the bulge by
+// plane rotations, deflation when an off-diagonal entry falls below round-off.
 bool symmetric_eigen(int n, std::vector<double> A, std::vector<double>& w, std::vector<double>& Z) {
     Z.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
@@ -786,6 +791,35 @@ double eval_u_point(const HostProblem& P, const std::vector<double>& u, const do
         while (j < d) { if (++e[j] < p + 1) break; e[j] = 0; ++j; }
         if (j == d) break;
     }
+    return s;
+}
+
+}  // namespace hpg
+
+namespace hpg {
+
+double mass_norm2(const HostProblem& P, const std::vector<double>& e) {
+    // apply the 1D mass matrix along each axis in turn (full numbering, x fastest)
+    std::vector<double> cur(e), nxt(e.size());
+    size_t inner = 1;
+    for (int j = 0; j < P.d; ++j) {
+        const Dir1D& D = P.dir[j];
+        const size_t N1 = (size_t)D.N1, outer = e.size() / (inner * N1);
+        for (size_t o = 0; o < outer; ++o)
+            for (size_t r = 0; r < N1; ++r)
+                for (size_t i = 0; i < inner; ++i) {
+                    double acc = 0.0;
+                    for (int t = 0; t < D.M.cnt[r]; ++t) {
+                        const size_t c = (size_t)D.M.col[r * kEll + t];
+                        acc += D.M.val[r * kEll + t] * cur[(o * N1 + c) * inner + i];
+                    }
+                    nxt[(o * N1 + r) * inner + i] = acc;
+                }
+        std::swap(cur, nxt);
+        inner *= N1;
+    }
+    double s = 0.0;
+    for (size_t i = 0; i < e.size(); ++i) s += e[i] * cur[i];
     return s;
 }
 

@@ -93,11 +93,15 @@ Problem::~Problem() {
 
 // Stream-ordered release (cudaFreeAsync), so that finishing one problem does
 // not synchronise the device while other problems run on other streams.
-void free_device(Problem& P, cudaStream_t s) {
+void drop_graphs(Problem& P) {
     for (auto& gx : P.D.gmres_graph)
         if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
     for (auto& kv : P.D.bench_graphs) cudaGraphExecDestroy(kv.second.first);
     P.D.bench_graphs.clear();
+}
+
+void free_device(Problem& P, cudaStream_t s) {
+    drop_graphs(P);
     for (void* p : P.D.allocs) cudaFreeAsync(p, s);
     P.D.allocs.clear();
     for (auto e : P.timer.pool) cudaEventDestroy(e);
@@ -409,7 +413,10 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
 // ------------------------------------------------------------ autotuner
 // Pick the FDM GEMM tile variant for this (dim, n1, precision) by timing one
 // A_alpha^{-1} apply per variant on the device (after a warm-up apply); cached
-// per process, so each mesh shape is tuned once.
+// per process, so each mesh shape is tuned once.  Every variant is first run on a
+// seeded nonzero input and its output compared with that of variant 0 (the plain
+// SIMT tile): a variant whose output is non-finite or differs by more than the
+// precision's tolerance is not a candidate, however fast it returns.
 template <typename T>
 static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, T* w1, T* w2) {
     static std::mutex mu;
@@ -421,16 +428,37 @@ static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, 
         if (it != cache.end()) { g.gemm_cfg = it->second; return HPG_OK; }
     }
     cudaStream_t s = ctx->stream;
-    CK(cudaMemsetAsync(x, 0, (size_t)g.Nu0 * sizeof(T), s));
+    const size_t n = (size_t)g.Nu0;
+    std::vector<T> hx(n), ref(n), out(n);
+    for (size_t i = 0; i < n; ++i) hx[i] = (T)std::sin(0.37 * (double)i + 0.1);
+    CK(cudaMemcpyAsync(x, hx.data(), n * sizeof(T), cudaMemcpyHostToDevice, s));
+    const double tol = sizeof(T) == sizeof(float) ? 1e-4 : 1e-11;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    int best = 0;
+    int best = -1;
     float best_ms = 1e30f;
+    double ref_max = 0.0;
     const int ncfg = fdm_tile_count((int)sizeof(T));
     for (int c = 0; c < ncfg; ++c) {
         g.gemm_cfg = c;
         if (launch_fdm<T>(g, nullptr, 1.0, x, y, w1, w2, s) != cudaSuccess) { cudaGetLastError(); continue; }
+        if (cudaMemcpyAsync(out.data(), y, n * sizeof(T), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        bool finite = true;
+        for (size_t i = 0; i < n && finite; ++i) finite = std::isfinite((double)out[i]);
+        if (!finite) continue;
+        if (c == 0) {
+            ref = out;
+            for (size_t i = 0; i < n; ++i) ref_max = std::max(ref_max, std::fabs((double)ref[i]));
+        } else {
+            double dmax = 0.0;
+            for (size_t i = 0; i < n; ++i) dmax = std::max(dmax, std::fabs((double)out[i] - (double)ref[i]));
+            if (ref.empty() || dmax > tol * std::max(ref_max, 1e-300)) continue;
+        }
         cudaEventRecord(e0, s);
         for (int r = 0; r < 5; ++r) launch_fdm<T>(g, nullptr, 1.0, x, y, w1, w2, s);
         cudaEventRecord(e1, s);
@@ -441,6 +469,10 @@ static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (best < 0) {
+        ctx->err = "no fast-diagonalisation pass variant produced a valid result";
+        return HPG_ERR_CUDA;
+    }
     g.gemm_cfg = best;
     std::lock_guard<std::mutex> lock(mu);
     cache[key] = best;

@@ -131,6 +131,9 @@ namespace hpg {
 hpg_status alloc_device(hpg_ctx* ctx, Problem& P);
 // Release the problem's device buffers, stream-ordered on `s`.
 void free_device(Problem& P, cudaStream_t s);
+// Destroy the problem's captured CUDA graphs (they hold launch arguments such as beta);
+// they are re-captured on next use.
+void drop_graphs(Problem& P);
 hpg_status upload_data(hpg_ctx* ctx, Problem& P);
 hpg_status solve_problem(hpg_ctx* ctx, Problem& P);
 hpg_status solve_batch(hpg_ctx* ctx, std::vector<Problem*>& probs);
@@ -153,6 +156,7 @@ hpg_status server_submit(hpg_ctx* ctx, Problem& P, long long* ticket);
 hpg_status server_poll(hpg_ctx* ctx, long long ticket, double wait_ms, int* done, hpg_status* result,
                        double* times3);
 void server_release(hpg_ctx* ctx, Problem& P);
+hpg_status server_ticket_error(hpg_ctx* ctx, long long ticket, std::string* msg);
 size_t server_in_use(hpg_ctx* ctx);
 
 }  // namespace hpg

@@ -95,6 +95,9 @@ SIGNATURES = {
     "hpg_wait": ([_ctx, C.c_longlong, _d, _P(C.c_int)], C.c_int),
     "hpg_ticket_times": ([_ctx, C.c_longlong, _pd], C.c_int),
     "hpg_server_memory": ([_ctx, C.c_int, _P(_sz), _P(_sz)], C.c_int),
+    "hpg_ticket_error": ([_ctx, C.c_longlong, C.c_char_p, _sz], C.c_int),
+    "hpg_l2_error": ([_ctx, C.c_int, _pd, _sz, _pd, _pd], C.c_int),
+    "hpg_measure_fma_peak": ([_ctx, C.c_int, _pd, _P(C.c_int)], C.c_int),
 }
 
 _lib = None
@@ -190,11 +193,23 @@ class Context:
         self.check(self.L.hpg_ticket_times(self.h, C.c_longlong(ticket), t), "hpg_ticket_times")
         return tuple(t)
 
+    def ticket_error(self, ticket):
+        buf = C.create_string_buffer(512)
+        self.check(self.L.hpg_ticket_error(self.h, C.c_longlong(ticket), buf, 512), "hpg_ticket_error")
+        return buf.value.decode()
+
     def server_memory(self, problem=None):
         a, b = _sz(), _sz()
         self.check(self.L.hpg_server_memory(self.h, problem.pid if problem else 0, C.byref(a),
                                             C.byref(b) if problem else None))
         return a.value, (b.value if problem else None)
+
+    def fma_peak(self, precision):
+        """Measured SIMT FMA throughput (TFLOP/s) and SM count of the device."""
+        t, n = C.c_double(), C.c_int()
+        self.check(self.L.hpg_measure_fma_peak(self.h, int(precision), C.byref(t), C.byref(n)),
+                   "hpg_measure_fma_peak")
+        return t.value, n.value
 
     def set_concurrency(self, n):
         self.check(self.L.hpg_set_concurrency(self.h, int(n)), "hpg_set_concurrency")
@@ -314,6 +329,14 @@ class Problem:
         out = np.zeros(X.shape[0])
         self.ctx.check(self.L.hpg_eval_u(self.ctx.h, self.pid, _dptr(X), X.shape[0], _dptr(out)), "hpg_eval_u")
         return out
+
+    def l2_error(self, u_ref):
+        """(||u_h - u_ref||_L2, ||u_ref||_L2) of the last solve, u_ref full coefficients."""
+        r = _f64(u_ref)
+        e, n = C.c_double(), C.c_double()
+        self.ctx.check(self.L.hpg_l2_error(self.ctx.h, self.pid, _dptr(r), r.size, C.byref(e), C.byref(n)),
+                       "hpg_l2_error")
+        return e.value, n.value
 
     def feasible_u(self):
         out = np.zeros(self.n_quad)

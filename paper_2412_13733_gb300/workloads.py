@@ -78,6 +78,12 @@ def sine3d_phi(X):
     return 0.2 + 0.1 * np.sin(2 * np.pi * X[:, 0]) * np.sin(2 * np.pi * X[:, 1]) * np.sin(2 * np.pi * X[:, 2])
 
 
+def oscillatory_phi(X):
+    from scipy.special import j0
+    X = np.atleast_2d(X)
+    return (1.0 + j0(20.0 * X[:, 0])) * (1.0 + j0(20.0 * X[:, 1]))
+
+
 def torsion_phi(X):
     X = np.atleast_2d(X)
     return 0.5 + 0.25 * X[:, 0]
@@ -120,6 +126,15 @@ def workload(name):
                     breakpoints=[uniform(0.0, 1.0, m)] * 2, m=m, p=p,
                     f=const_field(8.0), f_const=8.0, phi=torsion_phi, g=None,
                     alphas=alpha_list(2.0 ** -7, 4.0), beta=1e-14, tol=1e-10, exact=None)
+    if name.startswith("oscillatory_p"):
+        # Section 6.2's 2D example: (0,1)^2, 10 x 10 cells, f = 100,
+        # phi = (1 + J_0(20 x)) (1 + J_0(20 y)), alpha_1 = 2^-7 growing by sqrt(2) to 2^-3,
+        # beta = 1e-4 (the value of its Krylov runs); name "oscillatory_p{p}" picks the degree
+        p = int(name[len("oscillatory_p"):])
+        return dict(name=name, kind="obstacle", lower=False, dim=2,
+                    breakpoints=[uniform(0.0, 1.0, 10)] * 2, m=10, p=p,
+                    f=const_field(100.0), f_const=100.0, phi=oscillatory_phi, g=None,
+                    alphas=alpha_list(2.0 ** -7, 2.0 ** -3), beta=1e-4, tol=1e-6, exact=None)
     if name.startswith("box3d_"):
         # Section 6.5's 3D solver study: (0,1)^3, f = 40, phi = 1, alpha_1 = 2^-2, cap 2,
         # beta = 1e-5; name "box3d_p{p}_m{m}" picks the degree and cells per side

@@ -84,3 +84,32 @@ def test_largest_request_size_residual_property(ctx):
     F = o.residual(P.u(), P.psi(), psi_prev, w["alphas"][-1])
     assert np.linalg.norm(F) <= 2e-10, np.linalg.norm(F)
     P.free()
+
+
+def test_l2_error_is_the_mass_norm(ctx):
+    """hpg_l2_error gives ||u_h - u_ref||_L2 through the exact 1D mass matrices: it
+    equals the oracle's assembled mass-matrix norm for an arbitrary reference."""
+    from paper_2412_13733_gb300 import hpg
+    from tests.gpu_helpers import case, oracle_for, mass_norm
+    for name in ("radial_3x3_p5", "sine3d_3x2x2"):
+        w = case(name)
+        o = oracle_for(w)
+        P = hpg.from_workload(ctx, w)
+        P.solve()
+        ref = np.random.default_rng(3).standard_normal(P.n_u_full)
+        err, nrm = P.l2_error(ref)
+        assert abs(err - mass_norm(o, P.u() - ref)) <= 1e-12 * err
+        assert abs(nrm - mass_norm(o, ref)) <= 1e-12 * nrm
+        P.free()
+
+
+def test_fma_peak_probe(ctx):
+    """The roofline denominators of the ALU-bound kernels: FP32 and FP64 FMA rates
+    measured on this device lie between a quarter of and just above the unit-count
+    figures (128 FP32 FMA per SM per clock; FP64 1.25 TFLOP/s nominal)."""
+    from paper_2412_13733_gb300 import hpg
+    f32, sms = ctx.fma_peak(hpg.HPG_MIXED)
+    f64, _ = ctx.fma_peak(hpg.HPG_FP64)
+    derived32 = sms * 128 * 2 * 2.07e9 / 1e12
+    assert 0.25 * derived32 <= f32 <= 1.1 * derived32, (f32, derived32)
+    assert 0.05 <= f64 <= 0.5 * f32, f64

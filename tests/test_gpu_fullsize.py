@@ -5,11 +5,13 @@
   oracle run written by tests/golden/make_golden.py: Newton counts within +-1
   per step, u_h relative L2 <= 1e-9 (FP64) / 1e-8 (mixed).
 * sine3d: 3D obstacle on (0,1)^3, 8^3 hexes, p = 6 (117,649 u-dofs, 64,000
-  psi-dofs).  The oracle's direct sparse factorisation of this Newton matrix
-  does not fit in host memory, so the check is a property that holds at any
-  size: the oracle's own residual of eq. (pG), evaluated at the GPU's final
-  (u_K, psi_K) with psi_{K-1} from a GPU run stopped one step earlier, is
-  below the Newton tolerance (up to the round-off of re-evaluating it).
+  psi-dofs, 8 proximal steps) against the stored oracle run (its Newton systems
+  solved exactly by block elimination of psi, see tests/golden/make_golden.py):
+  Newton counts within +-1 per step, u_h relative L2 <= 1e-9 (FP64) / 1e-8
+  (mixed).  Beside it, a property that holds at any size, checked at every
+  proximal step: the oracle's own residual of eq. (pG) at the GPU's (u_k, psi_k)
+  with psi_{k-1} from the GPU run one step shorter is below the Newton tolerance
+  (up to the round-off of re-evaluating it).
 """
 import os
 
@@ -54,22 +56,43 @@ def test_torsion_full_size_against_stored_oracle(ctx, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_sine3d_full_size_residual_property(ctx, precision):
+def test_sine3d_full_size_against_stored_oracle(ctx, precision):
+    from paper_2412_13733_gb300 import hpg, workloads as W
+    path = os.path.join(GOLDEN, "sine3d_oracle.npz")
+    if not os.path.exists(path):
+        pytest.skip("stored oracle result missing")
+    g = np.load(path)
+    w = W.workload("sine3d")
+    P = hpg.from_workload(ctx, w, hpg.default_params(precision=precision))
+    P.solve()
+    st = P.stats()
+    assert st["status"] == 0
+    assert st["alpha_steps"] == len(g["newton"])
+    for a, b in zip(st["newton_per_step"], g["newton"]):
+        assert abs(a - b) <= 1, (st["newton_per_step"], list(g["newton"]))
+    err, nrm = P.l2_error(g["u"])
+    assert err / nrm <= (1e-9 if precision == 0 else 1e-8), err / nrm
+    assert rel(P.psi(), g["psi"]) <= (1e-8 if precision == 0 else 1e-7)
+    P.free()
+
+
+def test_sine3d_full_size_residual_chain(ctx):
+    """Every proximal step k of the full-size 3D solve (mixed path): the oracle's
+    residual of eq. (pG) at the GPU's (u_k, psi_k; psi_{k-1}) is at the Newton
+    tolerance.  Runs the GPU solve with the schedule cut after k steps, k = 1..K."""
     from paper_2412_13733_gb300 import hpg, workloads as W
     from oracle.hpg import ObstacleOracle
     w = W.workload("sine3d")
-    prm = hpg.default_params(precision=precision)
-    P = hpg.from_workload(ctx, w, prm)
-    P.set_alphas(w["alphas"][:-1])
-    P.solve()
-    psi_prev = P.psi()
-    P.set_alphas(w["alphas"])
-    P.solve()
-    st = P.stats()
-    assert st["status"] == 0 and st["final_residual"] <= 1e-10
-    assert st["alpha_steps"] == len(w["alphas"])
-    u, psi = P.u(), P.psi()
     o = ObstacleOracle(w["breakpoints"], w["p"], w["f"], w["phi"], None, beta=w["beta"])
-    F = o.residual(u, psi, psi_prev, w["alphas"][-1])
-    assert np.linalg.norm(F) <= 2e-10, np.linalg.norm(F)
+    P = hpg.from_workload(ctx, w, hpg.default_params(precision=1))
+    psi_prev = np.zeros(P.n_psi)
+    for k in range(1, len(w["alphas"]) + 1):
+        P.set_alphas(w["alphas"][:k])
+        P.solve()
+        st = P.stats()
+        assert st["status"] == 0 and st["final_residual"] <= 1e-10
+        u, psi = P.u(), P.psi()
+        F = o.residual(u, psi, psi_prev, w["alphas"][k - 1])
+        assert np.linalg.norm(F) <= 2e-10, (k, np.linalg.norm(F))
+        psi_prev = psi
     P.free()

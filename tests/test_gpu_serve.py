@@ -109,3 +109,50 @@ def test_bounded_wait_times_out_without_faulting():
     slow.free()
     ctx.server_stop()
     ctx.close()
+
+
+def test_component_calls_refuse_a_problem_in_the_loop():
+    """While a request is queued or running, a worker owns the problem's device
+    buffers; the component operators and the allocation-free apply must refuse it
+    (HPG_ERR_BUSY) instead of launching on buffers the worker may release."""
+    from paper_2412_13733_gb300 import hpg
+    ctx = hpg.Context(0)
+    w = case("radial_3x3_p5")
+    slow = hpg.from_workload(ctx, w)
+    slow.solve()                                # device state exists before submission
+    slow.set_alphas(w["alphas"] * 6)
+    ctx.server_start(workers=1)
+    t = ctx.submit(slow)
+    torch = pytest.importorskip("torch")
+    x = np.zeros(slow.n_u)
+    xd = torch.zeros(slow.n_u, dtype=torch.float64, device="cuda")
+    yd = torch.zeros_like(xd)
+    calls = [lambda: slow.apply_stiffness_inv(x, hpg.HPG_FP64), lambda: slow.residual(),
+             lambda: slow.factor_precond(hpg.HPG_FP64)]
+    for call in calls:
+        with pytest.raises(hpg.HpgError) as ei:
+            call()
+        assert ei.value.code == 11, ei.value            # HPG_ERR_BUSY
+    assert slow.apply_stiffness_inv_noalloc(0.5, xd.data_ptr(), yd.data_ptr(), slow.n_u) == 11
+    assert ctx.wait(t, 120000.0) == 0
+    slow.free()
+    ctx.server_stop()
+    ctx.close()
+
+
+def test_failed_request_reports_its_message():
+    from paper_2412_13733_gb300 import hpg
+    ctx = hpg.Context(0)
+    ctx.server_start(workers=2)
+    P = hpg.from_workload(ctx, case("radial_3x3_p5"), hpg.default_params(newton_max=1))
+    ok = hpg.from_workload(ctx, case("p2"))
+    t_bad, t_ok = ctx.submit(P), ctx.submit(ok)
+    assert ctx.wait(t_bad, 120000.0) == 4               # HPG_ERR_NEWTON_CAP
+    assert ctx.wait(t_ok, 120000.0) == 0
+    msg = ctx.ticket_error(t_bad)
+    assert "Newton cap" in msg and "proximal step" in msg, msg
+    assert ctx.ticket_error(t_ok) == ""
+    P.free()
+    ok.free()
+    ctx.server_stop()
+    ctx.close()

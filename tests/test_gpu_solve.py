@@ -183,3 +183,53 @@ def test_fgmres_needs_fp64(ctx):
     from paper_2412_13733_gb300 import hpg
     with pytest.raises(hpg.HpgError):
         hpg.from_workload(ctx, case("radial4"), hpg.default_params(precision=1, strategy=1))
+
+
+_OSC = {}
+
+
+@pytest.mark.parametrize("p", [4, 6])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_oscillatory_obstacle_paper_newton_counts(ctx, p, precision):
+    """Section 6.2's 2D oscillatory obstacle (10 x 10 cells) at the oracle's pinned
+    Newton tolerance 1e-6: the GPU's Newton counts equal the oracle's within 1 per
+    proximal step, and the total lies in the window around the paper's printed 24
+    that the oracle pin uses.  u_h agrees with the oracle to the accuracy that
+    tolerance allows (1e-6 relative L2)."""
+    from paper_2412_13733_gb300 import workloads as W
+    from oracle.hpg import ObstacleOracle
+    w = W.workload(f"oscillatory_p{p}")
+    if p not in _OSC:
+        o = ObstacleOracle(w["breakpoints"], w["p"], w["f"], w["phi"], None, beta=w["beta"])
+        r = o.solve(w["alphas"], tol=w["tol"])
+        assert r["converged"]
+        _OSC[p] = (o, r)
+    o, r = _OSC[p]
+    P, u, psi, st = gpu_solve(ctx, w, precision, newton_tol=w["tol"])
+    assert st["status"] == 0
+    assert st["alpha_steps"] == len(r["newton"])
+    for a, b in zip(st["newton_per_step"], r["newton"]):
+        assert abs(a - b) <= 1, (st["newton_per_step"], r["newton"])
+    assert 24 <= st["newton_total"] <= 30, st["newton_total"]
+    assert mass_norm(o, u - r["u"]) / mass_norm(o, r["u"]) <= 1e-6
+    P.free()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_changing_beta_after_a_solve(ctx, precision):
+    """beta enters the captured GMRES loop as a launch argument; a solve after
+    hpg_set_params changed it must equal a fresh problem solved with the new beta."""
+    from paper_2412_13733_gb300 import hpg
+    w = case("radial_3x3_p5")
+    P = hpg.from_workload(ctx, w, hpg.default_params(precision=precision))
+    P.solve()
+    P.set_params(hpg.default_params(precision=precision, beta=0.5))
+    P.solve()
+    Q = hpg.from_workload(ctx, w)
+    Q.set_params(hpg.default_params(precision=precision, beta=0.5))
+    Q.solve()
+    assert P.stats()["newton_per_step"] == Q.stats()["newton_per_step"]
+    assert P.stats()["krylov_total"] == Q.stats()["krylov_total"]
+    assert np.array_equal(P.u(), Q.u())
+    P.free()
+    Q.free()
