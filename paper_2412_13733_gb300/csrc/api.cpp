@@ -173,6 +173,7 @@ hpg_status hpg_problem_free(hpg_ctx* ctx, int pid) {
     hpg::server_release(ctx, *P);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    hpg::drop_groups_with(ctx, pid);
     hpg::free_device(*P, ctx->stream);
     ctx->problems.erase(pid);
     return HPG_OK;

@@ -59,6 +59,39 @@ struct Geo {
                                               // tiles take them (sorted by stencil counts), or null
 };
 
+// Lockstep group of same-shape problems (identical mesh, degree, kind and operator
+// constants): one launch serves every problem of the group.  Each problem keeps its
+// per-problem buffers (state, data, Krylov basis, factors) in one slab laid out
+// identically for all of them, so problem pb's copy of a buffer is problem 0's
+// pointer moved by delta[pb] bytes; the constant operators (stencils, eigenvectors,
+// quadrature) are read from problem 0.  The launch gives the problem index its own
+// grid coordinate; `act` (device, np flags, may be null) masks problems out of a
+// launch.  Bat{} (np = 1, no delta) is a single problem: every kernel then does
+// exactly what it does without batching.
+struct Bat {
+    const long long* delta = nullptr;   // device, np byte offsets (delta[0] = 0)
+    const int* act = nullptr;           // device, np flags (1: problem takes part)
+    const double* par = nullptr;        // device, np x kBatPar per-problem scalars (see BatPar)
+    int np = 1;
+};
+// per-problem scalars a batched launch reads from Bat::par instead of an argument
+enum BatPar { kParLam = 0, kParRtol = 1, kParAlpha = 2, kBatPar = 4 };
+
+#ifdef __CUDACC__
+// problem index of this block (the launch's problem grid coordinate) -> byte offset;
+// returns false when the problem is masked out (the whole block returns)
+__device__ __forceinline__ bool bat_enter(const Bat& bt, int pb, long long* off) {
+    if (bt.act && !bt.act[pb]) return false;
+    *off = bt.delta ? bt.delta[pb] : 0LL;
+    return true;
+}
+template <typename P>
+__device__ __forceinline__ P* bsh(P* p, long long off) {
+    return p ? reinterpret_cast<P*>(reinterpret_cast<char*>(const_cast<void*>(static_cast<const void*>(p))) + off)
+             : p;
+}
+#endif
+
 // Number of values stored per Gauss point by the evaluation kernel:
 // obstacle: 1 (w |J| exp(-psi)); gradient: packed symmetric d x d Jacobian * w|J|.
 inline int gauss_stride(int kind, int d) { return kind == HPG_GRADIENT ? d * (d + 1) / 2 : 1; }
@@ -79,7 +112,7 @@ struct IterCtl {
 // copy, may be null), eg = projection onto zeta (FP64, Npsi), flag |= 1 on
 // psi < -700 (obstacle) or non-finite values.
 cudaError_t launch_eval(const Geo<double>& g, const double* psi, const double* phiq, double* gw, float* gwf,
-                        double* eg, int* flag, cudaStream_t s);
+                        double* eg, int* flag, cudaStream_t s, const Bat& bt = Bat{});
 
 // phiz = (phi, zeta) from phi at the latent Gauss points (obstacle kinds).
 cudaError_t launch_project(const Geo<double>& g, const double* phiq, double* phiz, cudaStream_t s);
@@ -92,63 +125,78 @@ void add_kernel_launches(long long n);
 // Writes F (Nu0 + Npsi) and block partial sums of squares into part (see n_res_partials).
 cudaError_t launch_residual(const Geo<double>& g, const double* u, const double* psi, const double* psi_prev,
                             const double* eg, const double* rA, const double* rB, const double* bf,
-                            const double* phiz, double alpha, double* F, double* part, cudaStream_t s);
+                            const double* phiz, double alpha, double* F, double* part, cudaStream_t s,
+                            const Bat& bt = Bat{});
 int n_res_partials(const Geo<double>& g);
 int n_res_partials_for(int d, const int* n1, long long Npsi);
 
 // Deterministic reduction of `count` partials into out[0] (one block).
-cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaStream_t s);
+cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaStream_t s, const Bat& bt = Bat{});
 
 // Assemble -S-hat cell blocks, Cholesky, invert: Sinv (Nc x nb x nb, precision T)
 // holds (-S-hat)^{-1}.  If `dump` is non-null the assembled -S-hat blocks are written there.
 // gwork: global workspace of factor_workspace_elems() elements (null when that is 0).
 template <typename T>
 cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double beta, T* Sinv, double* dump,
-                          int* flag, T* gwork, cudaStream_t s);
+                          int* flag, T* gwork, cudaStream_t s, const Bat& bt = Bat{});
 size_t factor_smem_bytes(int nb, int elem);
 size_t factor_workspace_elems(int n, int d, int nb, int nc, long long Nc, int elem);
 
 // z = -Sinv v (per cell), in/out precision mixing: v (Tin), z (Tout).
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s,
-                           IterCtl ctl = IterCtl{});
+                           IterCtl ctl = IterCtl{}, const Bat& bt = Bat{});
 
 // y = B z  (psi -> interior u);  Tin/Tout storage, T compute.
 template <typename T, typename Tin, typename Tout>
-cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s, const int* skip = nullptr);
+cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s, const int* skip = nullptr,
+                          const Bat& bt = Bat{});
 
 // y = B^T x (interior u -> psi).
 template <typename T, typename Tin, typename Tout>
-cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t s);
+cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t s, const Bat& bt = Bat{});
 
 // y = A_alpha^{-1} x (interior) by fast diagonalisation; work1/work2 scratch of Nu0.
 // alpha is read from alpha_dev when non-null (graph replay), else alpha.
 template <typename T>
 cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, const T* x, T* y, T* work1,
-                       T* work2, cudaStream_t s, const int* skip = nullptr);
+                       T* work2, cudaStream_t s, const int* skip = nullptr, const Bat& bt = Bat{});
 
 // w = -(D z + E z + B^T t)  (per cell), D from gw.  z, t in T; w in Tout.
 template <typename T, typename Tout>
 cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T* z, const T* t, Tout* w,
-                              cudaStream_t s, IterCtl ctl = IterCtl{});
+                              cudaStream_t s, IterCtl ctl = IterCtl{}, const Bat& bt = Bat{});
 
 // FP64 matrix-free Newton apply y = G x (eq. pG-matrix), one fused launch.
 cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
-                                const double* x, double* y, cudaStream_t s);
+                                const double* x, double* y, cudaStream_t s, const Bat& bt = Bat{});
 
 
 // ---- vector helpers (FP64 unless typed)
 template <typename Tin, typename Tout>
-cudaError_t launch_convert(const Tin* x, Tout* y, long long n, cudaStream_t s);
+cudaError_t launch_convert(const Tin* x, Tout* y, long long n, cudaStream_t s, const Bat& bt = Bat{});
 // y = a*x + b*y
-cudaError_t launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s);
+cudaError_t launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s,
+                         const Bat& bt = Bat{});
 // y = x - b*z  (elementwise, z of precision T)
 template <typename T>
-cudaError_t launch_sub_scaled(const double* x, double b, const T* z, double* y, long long n, cudaStream_t s);
-// trial state: xt = x - lam * dx
-cudaError_t launch_trial(const double* x, const double* dx, double lam, double* xt, long long n, cudaStream_t s);
+cudaError_t launch_sub_scaled(const double* x, double b, const T* z, double* y, long long n, cudaStream_t s,
+                              const Bat& bt = Bat{});
+// trial state: xt = x - lam * dx (lam per problem from Bat::par when given)
+cudaError_t launch_trial(const double* x, const double* dx, double lam, double* xt, long long n, cudaStream_t s,
+                         const Bat& bt = Bat{});
 // partial sums of squares of x into part (returns number of partials through nparts)
-cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts, cudaStream_t s);
+cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts, cudaStream_t s,
+                         const Bat& bt = Bat{});
+// y = x (x null: y = 0), n elements
+template <typename T>
+cudaError_t launch_copy(const T* x, T* y, long long n, cudaStream_t s, const Bat& bt = Bat{});
+// *dst = Bat::par[pb][slot] for every problem of the batch
+cudaError_t launch_scatter_par(double* dst, int slot, cudaStream_t s, const Bat& bt);
+// status words of every problem of the batch into out (device): out[pb*nd + k] = d[k],
+// out[np*nd + pb*ni + k] = iv[k] (as doubles)
+cudaError_t launch_gather_status(const double* d, int nd, const int* iv, int ni, double* out, cudaStream_t s,
+                                 const Bat& bt);
 
 // ---- GMRES (right-preconditioned, unrestarted), all state on the device.
 constexpr int kMaxKrylov = 1000;   // upper bound of hpg_params.krylov_max
@@ -190,19 +238,24 @@ int gmres_upd_blocks(long long N);
 // The GMRES launchers take the basis element type VT (double or float).
 // r0 = b: beta0 = ||b||, V_0 = b / beta0, g = beta0 e_1, tol*beta0 stored, j = 0.
 template <typename VT>
-cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s, int cap = 0);
+cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s, int cap = 0,
+                        const Bat& bt = Bat{});
 // After w (= S Shat^{-1} V_j) has been written into V_{j+1}: CGS2 orthogonalise,
 // normalise, Givens update, convergence test, j += 1.  No-op once stopped.
 template <typename VT>
-cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s);
+cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s, const Bat& bt = Bat{});
 // Timing aid: set j (and clear the stop flags), then one Arnoldi step.
 template <typename VT>
 cudaError_t gmres_timed_step(GmresDev& G, int j, cudaStream_t s);
 // Set the WHILE condition of a device-side GMRES loop to "not stopped".
 cudaError_t launch_gm_setcond(cudaGraphConditionalHandle h, const int* iflag, cudaStream_t s);
+// the same for a batch: loop while any problem of the batch has not stopped
+cudaError_t launch_gm_setcond_batch(cudaGraphConditionalHandle h, const int* iflag, cudaStream_t s, const Bat& bt);
+// set the stop flag of the GMRES of every problem the mask selects
+cudaError_t launch_gm_stop(int* iflag, cudaStream_t s, const Bat& bt);
 // Solve H y = g for the completed iterations and form x = sum_i y_i V_i (FP64 sums).
 template <typename VT>
-cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s);
+cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s, const Bat& bt = Bat{});
 // Number of FDM GEMM tile variants for elements of `elem` bytes.
 int fdm_tile_count(int elem);
 // FMA throughput of the SIMT pipe for elements of `elem` bytes (4: FP32, 8: FP64),

@@ -356,14 +356,25 @@ __device__ __forceinline__ void k_urow_body(const Geo<T>& g, T cA, const Tx* __r
     }
 }
 
+// Grid: x, y tiles along axes 0, 1; z = (tiles along axis 2) x (problems of the batch),
+// the problem index slowest.  cA is read per problem from Bat::par (kParAlpha) when
+// `ca_from_par` is set (the residual's alpha).
 template <int D, typename T, typename Tx, typename Tz, bool HAS_A, bool HAS_B, bool RESID>
 __global__ void __launch_bounds__(256)
     k_urow(Geo<T> g, T cA, const Tx* __restrict__ x, T cB, const Tz* __restrict__ z, const Tz* __restrict__ z2,
            const double* __restrict__ rA, const double* __restrict__ bf, double* __restrict__ yres,
-           double* __restrict__ part, Tx* __restrict__ y, const int* skip) {
+           double* __restrict__ part, Tx* __restrict__ y, const int* skip, Bat bt, int ca_from_par) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    const int tz = (int)gridDim.z / bt.np;
+    const int pb = (int)blockIdx.z / tz, bz = (int)blockIdx.z - pb * tz;
+    long long off;
+    if (!bat_enter(bt, pb, &off)) return;
+    skip = bsh(skip, off);
     if (skip && *skip) return;
-    const int blin = (int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z));
+    x = bsh(x, off); z = bsh(z, off); z2 = bsh(z2, off); rA = bsh(rA, off); bf = bsh(bf, off);
+    yres = bsh(yres, off); part = bsh(part, off); y = bsh(y, off);
+    if (ca_from_par) cA = (T)bt.par[pb * kBatPar + kParAlpha];
+    const int blin = (int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * bz));
     k_urow_body<D, T, Tx, Tz, HAS_A, HAS_B, RESID>(g, cA, x, cB, z, z2, rA, bf, yres, part, y, blin, smraw);
 }
 
@@ -393,9 +404,9 @@ int utile_extent(int d, int axis) {
 }
 
 template <int D>
-static dim3 utile_grid(const int* n1) {
+static dim3 utile_grid(const int* n1, int np = 1) {
     return dim3((n1[0] + UTile<D>::T0 - 1) / UTile<D>::T0, (n1[1] + UTile<D>::T1 - 1) / UTile<D>::T1,
-                D == 3 ? (n1[2] + UTile<D>::T2 - 1) / UTile<D>::T2 : 1);
+                (D == 3 ? (n1[2] + UTile<D>::T2 - 1) / UTile<D>::T2 : 1) * np);
 }
 
 static long long utile_blocks(int d, const int* n1) {
@@ -412,8 +423,12 @@ void add_kernel_launches(long long n) { t_launches += n; }
 // Jacobian J_ab = phi (s d_ab - psi_a psi_b) s^{-3/2} (times w|J|) packed into gw.
 __global__ void k_eval(Geo<double> g, const double* __restrict__ psi, const double* __restrict__ phiq,
                        double* __restrict__ gw, float* __restrict__ gwf, double* __restrict__ eg,
-                       int* __restrict__ flag) {
+                       int* __restrict__ flag, Bat bt) {
     extern __shared__ double sm[];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    psi = bsh(psi, off); phiq = bsh(phiq, off); gw = bsh(gw, off); gwf = bsh(gwf, off); eg = bsh(eg, off);
+    flag = bsh(flag, off);
     const int n = g.n, nloc = (int)g.nloc, nc = g.ncomp;
     double* a = sm;
     double* b = sm + nc * nloc;
@@ -475,10 +490,10 @@ __global__ void k_eval(Geo<double> g, const double* __restrict__ psi, const doub
 }
 
 cudaError_t launch_eval(const Geo<double>& g, const double* psi, const double* phiq, double* gw, float* gwf,
-                        double* eg, int* flag, cudaStream_t s) {
+                        double* eg, int* flag, cudaStream_t s, const Bat& bt) {
     const size_t smem = (size_t)(2 * g.ncomp * g.nloc + g.n * g.n) * sizeof(double);
     const int threads = g.nloc * g.ncomp >= 256 ? 256 : 128;
-    k_eval<<<(unsigned)g.Nc, threads, smem, s>>>(g, psi, phiq, gw, gwf, eg, flag);
+    k_eval<<<dim3((unsigned)g.Nc, bt.np), threads, smem, s>>>(g, psi, phiq, gw, gwf, eg, flag, bt);
     note_launch();
     return cudaGetLastError();
 }
@@ -521,8 +536,12 @@ cudaError_t launch_project(const Geo<double>& g, const double* phiq, double* phi
 template <int D>
 __global__ void k_residual_psi(Geo<double> g, const double* __restrict__ u, const double* __restrict__ eg,
                                const double* __restrict__ rB, const double* __restrict__ phiz,
-                               double* __restrict__ F, double* __restrict__ part) {
+                               double* __restrict__ F, double* __restrict__ part, Bat bt) {
     __shared__ double sh[32];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    u = bsh(u, off); eg = bsh(eg, off); rB = bsh(rB, off); phiz = bsh(phiz, off); F = bsh(F, off);
+    part = bsh(part, off);
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
     if (j < g.Npsi) {
@@ -533,9 +552,9 @@ __global__ void k_residual_psi(Geo<double> g, const double* __restrict__ u, cons
         int kk = rem - comp * (int)g.nloc;
         for (int t = 0; t < D; ++t) { km[t] = kk % g.n; kk /= g.n; }
         cell_multi(g, cell, cm);
-        const double bt = apply_BT_entry<D, double, double>(g, cm, comp, km, u);
-        if (g.kind == HPG_GRADIENT) v = bt + rB[j] - eg[j];
-        else v = bt + rB[j] + eg[j] - phiz[j];
+        const double bt_ = apply_BT_entry<D, double, double>(g, cm, comp, km, u);
+        if (g.kind == HPG_GRADIENT) v = bt_ + rB[j] - eg[j];
+        else v = bt_ + rB[j] + eg[j] - phiz[j];
         F[j] = v;
     }
     v = block_sum(v * v, sh);
@@ -552,36 +571,42 @@ int n_res_partials_for(int d, const int* n1, long long Npsi) {
 
 cudaError_t launch_residual(const Geo<double>& g, const double* u, const double* psi, const double* psi_prev,
                             const double* eg, const double* rA, const double* rB, const double* bf,
-                            const double* phiz, double alpha, double* F, double* part, cudaStream_t s) {
+                            const double* phiz, double alpha, double* F, double* part, cudaStream_t s,
+                            const Bat& bt) {
     const int bu = (int)utile_blocks(g.d, g.n1), bp = (int)((g.Npsi + 255) / 256);
+    const int from_par = bt.par ? 1 : 0;
     if (g.d == 2) {
-        k_urow<2, double, double, double, true, true, true><<<utile_grid<2>(g.n1), 256,
+        k_urow<2, double, double, double, true, true, true><<<utile_grid<2>(g.n1, bt.np), 256,
                                                                  urow_smem<2>(g, true, true), s>>>(
-            g, alpha, u, 1.0, psi, psi_prev, rA, bf, F, part, nullptr, nullptr);
+            g, alpha, u, 1.0, psi, psi_prev, rA, bf, F, part, nullptr, nullptr, bt, from_par);
         note_launch();
-        k_residual_psi<2><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
+        k_residual_psi<2><<<dim3(bp, bt.np), 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu, bt);
         note_launch();
     } else {
-        k_urow<3, double, double, double, true, true, true><<<utile_grid<3>(g.n1), 256,
+        k_urow<3, double, double, double, true, true, true><<<utile_grid<3>(g.n1, bt.np), 256,
                                                                  urow_smem<3>(g, true, true), s>>>(
-            g, alpha, u, 1.0, psi, psi_prev, rA, bf, F, part, nullptr, nullptr);
+            g, alpha, u, 1.0, psi, psi_prev, rA, bf, F, part, nullptr, nullptr, bt, from_par);
         note_launch();
-        k_residual_psi<3><<<bp, 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu);
+        k_residual_psi<3><<<dim3(bp, bt.np), 256, 0, s>>>(g, u, eg, rB, phiz, F + g.Nu0, part + bu, bt);
         note_launch();
     }
     return cudaGetLastError();
 }
 
-__global__ void k_reduce_sum(const double* __restrict__ part, int count, double* __restrict__ out) {
+__global__ void k_reduce_sum(const double* __restrict__ part, int count, double* __restrict__ out, Bat bt) {
     __shared__ double sh[32];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.x, &off)) return;
+    part = bsh(part, off);
+    out = bsh(out, off);
     double v = 0.0;
     for (int i = threadIdx.x; i < count; i += blockDim.x) v += part[i];
     v = block_sum(v, sh);
     if (threadIdx.x == 0) out[0] = v;
 }
 
-cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaStream_t s) {
-    k_reduce_sum<<<1, 1024, 0, s>>>(part, count, out);
+cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaStream_t s, const Bat& bt) {
+    k_reduce_sum<<<bt.np, 1024, 0, s>>>(part, count, out, bt);
     note_launch();
     return cudaGetLastError();
 }
@@ -628,8 +653,14 @@ __device__ void assemble_D_block(const Geo<T>& g, const T* __restrict__ gw, long
 
 template <typename T>
 __global__ void k_factor(Geo<T> g, const T* __restrict__ gw, T alpha_inv, T beta, T* __restrict__ Sinv,
-                         double* __restrict__ dump, int* __restrict__ flag, T* __restrict__ gwork, int use_smem) {
+                         double* __restrict__ dump, int* __restrict__ flag, T* __restrict__ gwork, int use_smem,
+                         Bat bt) {
     extern __shared__ unsigned char smraw[];
+    long long off;
+    const int pb = (int)blockIdx.y;
+    if (!bat_enter(bt, pb, &off)) return;
+    gw = bsh(gw, off); Sinv = bsh(Sinv, off); dump = bsh(dump, off); flag = bsh(flag, off); gwork = bsh(gwork, off);
+    if (bt.par) alpha_inv = (T)(1.0 / bt.par[pb * kBatPar + kParAlpha]);
     T* sm = reinterpret_cast<T*>(smraw);
     const int n = g.n, nloc = (int)g.nloc, nb = (int)g.nb, nc = g.ncomp;
     const long long cell = blockIdx.x;
@@ -708,7 +739,9 @@ __global__ void k_factor(Geo<T> g, const T* __restrict__ gw, T alpha_inv, T beta
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && bad) atomicOr(flag, 2);
+    // non-SPD pivot: bit 1 of flag[1] (flag[0] holds the evaluation's flags, which each
+    // line-search trial clears; this one stays set until the next solve)
+    if (threadIdx.x == 0 && bad) atomicOr(flag + 1, 2);
     for (int i = threadIdx.x; i < nb; i += blockDim.x) ldiag[i] = A[(size_t)i * nb + i];
     __syncthreads();
     // X = L^{-1}, column j per thread; X[i][j] stored at A[j][i] (i >= j)
@@ -752,13 +785,13 @@ size_t factor_workspace_elems(int n, int d, int nb, int nc, long long Nc, int el
 
 template <typename T>
 cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double beta, T* Sinv, double* dump,
-                          int* flag, T* gwork, cudaStream_t s) {
+                          int* flag, T* gwork, cudaStream_t s, const Bat& bt) {
     const size_t elems = factor_ws_elems(g.n, g.d, (int)g.nb, g.ncomp);
     const size_t bytes = elems * sizeof(T);
     const int use_smem = bytes <= kFactorSmemMax;
     if (!use_smem && !gwork) return cudaErrorInvalidValue;
-    k_factor<T><<<(unsigned)g.Nc, 256, use_smem ? bytes : 0, s>>>(g, gw, (T)(1.0 / alpha), (T)beta, Sinv, dump,
-                                                                 flag, gwork, use_smem);
+    k_factor<T><<<dim3((unsigned)g.Nc, bt.np), 256, use_smem ? bytes : 0, s>>>(
+        g, gw, (T)(1.0 / alpha), (T)beta, Sinv, dump, flag, gwork, use_smem, bt);
     note_launch();
     return cudaGetLastError();
 }
@@ -773,9 +806,14 @@ cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double bet
 template <typename T, typename Tin, typename Tout>
 __global__ void __launch_bounds__(256)
     k_precond(Geo<T> g, const T* __restrict__ Sinv, const Tin* __restrict__ v, Tout* __restrict__ z, IterCtl ctl,
-              int rsplit) {
+              int rsplit, Bat bt) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    ctl.skip = bsh(ctl.skip, off);
+    ctl.jptr = bsh(ctl.jptr, off);
     if (ctl.skip && *ctl.skip) return;
+    Sinv = bsh(Sinv, off); v = bsh(v, off); z = bsh(z, off);
     const int nb = (int)g.nb;
     T* vs = reinterpret_cast<T*>(smraw);      // nb
     const long long cell = blockIdx.x / rsplit;
@@ -832,9 +870,14 @@ __global__ void __launch_bounds__(256)
 // thread owns one row and walks k (exactly nb^2 FMAs per cell, no reduction).
 template <typename Tin, typename Tout>
 __global__ void k_precond_f64(Geo<double> g, const double* __restrict__ Sinv, const Tin* __restrict__ v,
-                              Tout* __restrict__ z, IterCtl ctl) {
+                              Tout* __restrict__ z, IterCtl ctl, Bat bt) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    ctl.skip = bsh(ctl.skip, off);
+    ctl.jptr = bsh(ctl.jptr, off);
     if (ctl.skip && *ctl.skip) return;
+    Sinv = bsh(Sinv, off); v = bsh(v, off); z = bsh(z, off);
     double* vs = reinterpret_cast<double*>(smraw);
     const int nb = (int)g.nb;
     const long long cell = blockIdx.x;
@@ -864,35 +907,44 @@ static int precond_rsplit(long long Nc, long long nb) {
 }
 
 template <typename T, typename Tin, typename Tout>
-cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s, IterCtl ctl) {
+cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z, cudaStream_t s, IterCtl ctl,
+                           const Bat& bt) {
     if constexpr (sizeof(T) == 8) {
         const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
-        k_precond_f64<Tin, Tout><<<(unsigned)g.Nc, threads, g.nb * sizeof(double), s>>>(g, Sinv, v, z, ctl);
+        k_precond_f64<Tin, Tout><<<dim3((unsigned)g.Nc, bt.np), threads, g.nb * sizeof(double), s>>>(g, Sinv, v, z,
+                                                                                                     ctl, bt);
         note_launch();
         return cudaGetLastError();
     }
-    const int rsplit = precond_rsplit(g.Nc, g.nb);
+    // the row split serves one problem with few cells; a batch already fills the GPU
+    const int rsplit = precond_rsplit(g.Nc * bt.np, g.nb);
     const size_t smem = (size_t)g.nb * sizeof(T);
-    k_precond<T, Tin, Tout><<<(unsigned)(g.Nc * rsplit), 256, smem, s>>>(g, Sinv, v, z, ctl, rsplit);
+    k_precond<T, Tin, Tout><<<dim3((unsigned)(g.Nc * rsplit), bt.np), 256, smem, s>>>(g, Sinv, v, z, ctl, rsplit, bt);
     note_launch();
     return cudaGetLastError();
 }
 
 // ==================================================================== B, B^T
 template <typename T, typename Tin, typename Tout>
-cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s, const int* skip) {
+cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s, const int* skip, const Bat& bt) {
     if (g.d == 2)
-        k_urow<2, T, Tout, Tin, false, true, false><<<utile_grid<2>(g.n1), 256, urow_smem<2>(g, false, true), s>>>(
-            g, T(0), (const Tout*)nullptr, T(1), z, (const Tin*)nullptr, nullptr, nullptr, nullptr, nullptr, y, skip);
+        k_urow<2, T, Tout, Tin, false, true, false><<<utile_grid<2>(g.n1, bt.np), 256, urow_smem<2>(g, false, true),
+                                                      s>>>(g, T(0), (const Tout*)nullptr, T(1), z, (const Tin*)nullptr,
+                                                           nullptr, nullptr, nullptr, nullptr, y, skip, bt, 0);
     else
-        k_urow<3, T, Tout, Tin, false, true, false><<<utile_grid<3>(g.n1), 256, urow_smem<3>(g, false, true), s>>>(
-            g, T(0), (const Tout*)nullptr, T(1), z, (const Tin*)nullptr, nullptr, nullptr, nullptr, nullptr, y, skip);
+        k_urow<3, T, Tout, Tin, false, true, false><<<utile_grid<3>(g.n1, bt.np), 256, urow_smem<3>(g, false, true),
+                                                      s>>>(g, T(0), (const Tout*)nullptr, T(1), z, (const Tin*)nullptr,
+                                                           nullptr, nullptr, nullptr, nullptr, y, skip, bt, 0);
     note_launch();
     return cudaGetLastError();
 }
 
 template <int D, typename T, typename Tin, typename Tout>
-__global__ void k_btapply(Geo<T> g, const Tin* __restrict__ x, Tout* __restrict__ y) {
+__global__ void k_btapply(Geo<T> g, const Tin* __restrict__ x, Tout* __restrict__ y, Bat bt) {
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    x = bsh(x, off);
+    y = bsh(y, off);
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= g.Npsi) return;
     const long long cell = j / g.nb;
@@ -906,10 +958,10 @@ __global__ void k_btapply(Geo<T> g, const Tin* __restrict__ x, Tout* __restrict_
 }
 
 template <typename T, typename Tin, typename Tout>
-cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t s) {
-    const unsigned b = (unsigned)((g.Npsi + 255) / 256);
-    if (g.d == 2) k_btapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y);
-    else k_btapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y);
+cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t s, const Bat& bt) {
+    const dim3 b((unsigned)((g.Npsi + 255) / 256), bt.np);
+    if (g.d == 2) k_btapply<2, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y, bt);
+    else k_btapply<3, T, Tin, Tout><<<b, 256, 0, s>>>(g, x, y, bt);
     note_launch();
     return cudaGetLastError();
 }
@@ -925,7 +977,22 @@ cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t 
 struct GemmArgs {
     int M, N, K, batch;
     long long sAm, sAk, sAb, sBk, sBn, sBb, sCm, sCn, sCb;
+    int dA, dB;   // 1: the operand is per-problem data (moved by the batch offset); 0: a shared constant
 };
+
+// GEMM launches stack the problems of a batch in blockIdx.z above the GEMM batch
+// index: z = problem * a.batch + b.  Moves the per-problem operands, the output,
+// the device alpha and the skip flag to the block's problem.
+#define GEMM_BATCH_ENTER()                                   \
+    const int prob_ = (int)blockIdx.z / a.batch;             \
+    long long boff_;                                         \
+    if (!bat_enter(bt, prob_, &boff_)) return;               \
+    skip = bsh(skip, boff_);                                 \
+    if (skip && *skip) return;                               \
+    if (a.dA) Ap = bsh(Ap, boff_);                           \
+    if (a.dB) Bp = bsh(Bp, boff_);                           \
+    Cp = bsh(Cp, boff_);                                     \
+    sc.alpha_dev = bsh(sc.alpha_dev, boff_);
 
 struct FdmScale {
     int on;
@@ -957,16 +1024,16 @@ template <typename T, int BM, int BN, int TM, int TN, int KS>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
     k_gemm_fullk(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp,
                  FdmScale sc, const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2,
-                 const int* skip) {
+                 const int* skip, Bat bt) {
     constexpr int NG = (BM / TM) * (BN / TN);     // threads per group
     constexpr int NT = NG * KS;
     extern __shared__ __align__(16) unsigned char smraw[];
-    if (skip && *skip) return;
+    GEMM_BATCH_ENTER()
     T* As = reinterpret_cast<T*>(smraw);          // [K][BM]
     T* Bs = As + (size_t)a.K * BM;                // [K][BN]
     const int tid = threadIdx.x;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int b = blockIdx.z;
+    const int b = (int)blockIdx.z - prob_ * a.batch;
     const T* A = Ap + (long long)b * a.sAb;
     const T* B = Bp + (long long)b * a.sBb;
     T* C = Cp + (long long)b * a.sCb;
@@ -1066,15 +1133,15 @@ template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     k_gemm_tiled(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp,
                  FdmScale sc, const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2,
-                 const int* skip) {
+                 const int* skip, Bat bt) {
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
-    if (skip && *skip) return;
+    GEMM_BATCH_ENTER()
     constexpr int NT = (BM / TM) * (BN / TN);
     const int tid = threadIdx.x;
     const int tx = tid % (BN / TN), ty = tid / (BN / TN);
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int b = blockIdx.z;
+    const int b = (int)blockIdx.z - prob_ * a.batch;
     const T* A = Ap + (long long)b * a.sAb;
     const T* B = Bp + (long long)b * a.sBb;
     T* C = Cp + (long long)b * a.sCb;
@@ -1286,11 +1353,11 @@ template <int BN>
 __global__ void __launch_bounds__(256, 1)
     k_gemm_tc(GemmArgs a, const float* __restrict__ Ap, const float* __restrict__ Bp, float* __restrict__ Cp,
               FdmScale sc, const float* __restrict__ l0, const float* __restrict__ l1, const float* __restrict__ l2,
-              const int* skip, int nbuf) {
+              const int* skip, int nbuf, Bat bt) {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
-    if (skip && *skip) return;
+    GEMM_BATCH_ENTER()
     constexpr int BM = kTcBM, BK = kTcBK, NT = 256;
     constexpr int ATILE = BM * BK, BTILE = BN * BK, STAGE = 2 * ATILE + 2 * BTILE;
     constexpr uint32_t SBO = (BK / 4) * 128;              // bytes between 8-row core-matrix groups
@@ -1302,7 +1369,7 @@ __global__ void __launch_bounds__(256, 1)
     float* As = stage + nbuf * STAGE;
     float* Bs = As + tc_panel_floats(pa, BM, Kp);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, b = blockIdx.z;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, b = (int)blockIdx.z - prob_ * a.batch;
     const float* A = Ap + (long long)b * a.sAb + (long long)m0 * a.sAm;
     const float* B = Bp + (long long)b * a.sBb + (long long)n0 * a.sBn;
     float* C = Cp + (long long)b * a.sCb;
@@ -1397,13 +1464,14 @@ __global__ void __launch_bounds__(256, 1)
 
 template <int BN>
 static cudaError_t launch_gemm_tc(const GemmArgs& a, const float* A, const float* B, float* Cp, const FdmScale& sc,
-                                  const float* l0, const float* l1, const float* l2, cudaStream_t s, const int* skip) {
+                                  const float* l0, const float* l1, const float* l2, cudaStream_t s, const int* skip,
+                                  const Bat& bt) {
     int nbuf = 2;
     if (tc_smem_bytes<BN>(a, nbuf) > kTcSmemMax) nbuf = 1;
     const size_t smem = tc_smem_bytes<BN>(a, nbuf);
     if (smem > kTcSmemMax) return cudaErrorInvalidValue;       // K too long for whole-K staging
-    dim3 grid((a.N + BN - 1) / BN, (a.M + kTcBM - 1) / kTcBM, a.batch);
-    k_gemm_tc<BN><<<grid, 256, smem, s>>>(a, A, B, Cp, sc, l0, l1, l2, skip, nbuf);
+    dim3 grid((a.N + BN - 1) / BN, (a.M + kTcBM - 1) / kTcBM, a.batch * bt.np);
+    k_gemm_tc<BN><<<grid, 256, smem, s>>>(a, A, B, Cp, sc, l0, l1, l2, skip, nbuf, bt);
     note_launch();
     return cudaGetLastError();
 }
@@ -1420,17 +1488,17 @@ struct Tile { static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, KS = 
 
 template <typename T, typename C>
 static cudaError_t launch_tile(const GemmArgs& a, const T* A, const T* B, T* Cp, const FdmScale& sc, const T* l0,
-                               const T* l1, const T* l2, cudaStream_t s, const int* skip) {
+                               const T* l1, const T* l2, cudaStream_t s, const int* skip, const Bat& bt) {
     constexpr int BM = C::BM, BN = C::BN, TM = C::TM, TN = C::TN, KS = C::KS;
     const size_t red = (size_t)(KS - 1) * (BM / TM) * (BN / TN) * TM * TN * sizeof(T);
     const size_t smem = std::max((size_t)a.K * (BM + BN) * sizeof(T), red);
     if (smem <= 200 * 1024) {
-        dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch);
+        dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch * bt.np);
         k_gemm_fullk<T, BM, BN, TM, TN, KS><<<grid, (BM / TM) * (BN / TN) * KS, smem, s>>>(a, A, B, Cp, sc, l0, l1,
-                                                                                        l2, skip);
+                                                                                        l2, skip, bt);
     } else {
-        dim3 grid((a.N + 31) / 32, (a.M + 31) / 32, a.batch);
-        k_gemm_tiled<T, 32, 32, 16, 2, 2><<<grid, 256, 0, s>>>(a, A, B, Cp, sc, l0, l1, l2, skip);
+        dim3 grid((a.N + 31) / 32, (a.M + 31) / 32, a.batch * bt.np);
+        k_gemm_tiled<T, 32, 32, 16, 2, 2><<<grid, 256, 0, s>>>(a, A, B, Cp, sc, l0, l1, l2, skip, bt);
     }
     note_launch();
     return cudaGetLastError();
@@ -1455,17 +1523,18 @@ int fdm_tile_count(int elem) {
 
 template <typename T, size_t I = 0>
 static cudaError_t launch_tile_idx(int idx, const GemmArgs& a, const T* A, const T* B, T* Cp, const FdmScale& sc,
-                                   const T* l0, const T* l1, const T* l2, cudaStream_t s, const int* skip) {
+                                   const T* l0, const T* l1, const T* l2, cudaStream_t s, const int* skip,
+                                   const Bat& bt) {
     using Set = typename TileSet<T>::type;
     if constexpr (I < std::tuple_size<Set>::value) {
         if (idx == (int)I)
-            return launch_tile<T, typename std::tuple_element<I, Set>::type>(a, A, B, Cp, sc, l0, l1, l2, s, skip);
-        return launch_tile_idx<T, I + 1>(idx, a, A, B, Cp, sc, l0, l1, l2, s, skip);
+            return launch_tile<T, typename std::tuple_element<I, Set>::type>(a, A, B, Cp, sc, l0, l1, l2, s, skip, bt);
+        return launch_tile_idx<T, I + 1>(idx, a, A, B, Cp, sc, l0, l1, l2, s, skip, bt);
     } else {
         if constexpr (sizeof(T) == 4) {
             const int t = idx - (int)std::tuple_size<Set>::value;
-            if (t == 0) return launch_gemm_tc<16>(a, A, B, Cp, sc, l0, l1, l2, s, skip);
-            if (t == 1) return launch_gemm_tc<32>(a, A, B, Cp, sc, l0, l1, l2, s, skip);
+            if (t == 0) return launch_gemm_tc<16>(a, A, B, Cp, sc, l0, l1, l2, s, skip, bt);
+            if (t == 1) return launch_gemm_tc<32>(a, A, B, Cp, sc, l0, l1, l2, s, skip, bt);
         }
         return cudaErrorInvalidValue;
     }
@@ -1484,17 +1553,17 @@ static void configure_tiles() {
 
 template <typename T>
 static cudaError_t gemm(const GemmArgs& a, const T* A, const T* B, T* C, const FdmScale& sc, const Geo<T>& g,
-                        cudaStream_t s, const int* skip) {
+                        cudaStream_t s, const int* skip, const Bat& bt) {
     const T* l0 = g.lam[0];
     const T* l1 = g.d > 1 ? g.lam[1] : g.lam[0];
     const T* l2 = g.d > 2 ? g.lam[2] : g.lam[0];
-    return launch_tile_idx<T>(g.gemm_cfg, a, A, B, C, sc, l0, l1, l2, s, skip);
+    return launch_tile_idx<T>(g.gemm_cfg, a, A, B, C, sc, l0, l1, l2, s, skip, bt);
 }
 
 // A_alpha^{-1} x = alpha^{-1} (V (x) V (x) V) diag(1 / sum lam) (V^T (x) V^T (x) V^T) x
 template <typename T>
 cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, const T* x, T* y, T* work1, T* work2,
-                       cudaStream_t s, const int* skip) {
+                       cudaStream_t s, const int* skip, const Bat& bt) {
     const int d = g.d;
     long long inner[kMaxDim], outer[kMaxDim];
     for (int ax = 0; ax < d; ++ax) {
@@ -1521,14 +1590,16 @@ cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, c
             if (fwd) { a.sBk = n1; a.sBn = 1; } else { a.sBk = 1; a.sBn = n1; }
             a.sBb = 0;
             a.sCm = n1; a.sCn = 1; a.sCb = 0;
-            return gemm<T>(a, in, V, out, sc, g, s, skip);
+            a.dA = 1; a.dB = 0;
+            return gemm<T>(a, in, V, out, sc, g, s, skip, bt);
         }
         a.M = n1; a.N = (int)inner[ax]; a.K = n1; a.batch = (int)outer[ax];
         if (fwd) { a.sAm = 1; a.sAk = n1; } else { a.sAm = n1; a.sAk = 1; }
         a.sAb = 0;
         a.sBk = inner[ax]; a.sBn = 1; a.sBb = (long long)n1 * inner[ax];
         a.sCm = inner[ax]; a.sCn = 1; a.sCb = (long long)n1 * inner[ax];
-        return gemm<T>(a, V, in, out, sc, g, s, skip);
+        a.dA = 0; a.dB = 1;
+        return gemm<T>(a, V, in, out, sc, g, s, skip, bt);
     };
     cudaError_t e;
     const T* cur = x;
@@ -1640,9 +1711,14 @@ inline void cell_groups(long long nb, int* gs, int* cpb) {
 template <int D, typename T, typename Tz, typename Tt, typename Tout>
 __global__ void __launch_bounds__(256)
     k_cellop(Geo<T> g, const T* __restrict__ gw, T beta, const Tz* __restrict__ z, const Tt* __restrict__ t, T sB,
-             T sD, Tout* __restrict__ out, IterCtl ctl, int gs, int cpb) {
+             T sD, Tout* __restrict__ out, IterCtl ctl, int gs, int cpb, Bat bt) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    ctl.skip = bsh(ctl.skip, off);
+    ctl.jptr = bsh(ctl.jptr, off);
     if (ctl.skip && *ctl.skip) return;
+    gw = bsh(gw, off); z = bsh(z, off); t = bsh(t, off); out = bsh(out, off);
     Tout* outp = out + (ctl.jptr ? (long long)(*ctl.jptr + 1) * ctl.jstride : 0LL);
     const int grp = threadIdx.x / gs, lt = threadIdx.x - grp * gs;
     const long long cell = (long long)blockIdx.x * cpb + grp;
@@ -1657,8 +1733,13 @@ __global__ void __launch_bounds__(256)
 template <int D>
 __global__ void __launch_bounds__(256)
     k_newton_fused(Geo<double> g, const double* __restrict__ gw, double alpha, double beta,
-                   const double* __restrict__ x, double* __restrict__ y, int nu, int gs, int cpb) {
+                   const double* __restrict__ x, double* __restrict__ y, int nu, int gs, int cpb, Bat bt) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    long long off;
+    const int pbi = (int)blockIdx.y;
+    if (!bat_enter(bt, pbi, &off)) return;
+    gw = bsh(gw, off); x = bsh(x, off); y = bsh(y, off);
+    if (bt.par) alpha = bt.par[pbi * kBatPar + kParAlpha];
     // u-row tiles and cell groups alternate in block order, so that the block
     // scheduler hands every SM a similar mix of the two kinds of work
     const int nc = (int)gridDim.x - nu;
@@ -1683,23 +1764,23 @@ __global__ void __launch_bounds__(256)
 
 template <typename T, typename Tout>
 cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T* z, const T* t, Tout* w,
-                              cudaStream_t s, IterCtl ctl) {
+                              cudaStream_t s, IterCtl ctl, const Bat& bt) {
     // one cell per block here (measured faster than several cells per block for the
     // FP32 and FP64 Krylov-loop applies); the fused Newton apply groups cells
     const int gs = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256), cpb = 1;
     const size_t smem = (size_t)(cpb + 1) * (3 * g.nb + g.n * g.n) * sizeof(T);
-    const unsigned blocks = (unsigned)g.Nc;
+    const dim3 blocks((unsigned)g.Nc, bt.np);
     if (g.d == 2)
-        k_cellop<2, T, T, T, Tout><<<blocks, gs, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb);
+        k_cellop<2, T, T, T, Tout><<<blocks, gs, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb, bt);
     else
-        k_cellop<3, T, T, T, Tout><<<blocks, gs, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb);
+        k_cellop<3, T, T, T, Tout><<<blocks, gs, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb, bt);
     note_launch();
     return cudaGetLastError();
 }
 
 // G x (eq. pG-matrix) in one launch: u-row tiles and psi cells share the SMs.
 cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double alpha, double beta,
-                                const double* x, double* y, cudaStream_t s) {
+                                const double* x, double* y, cudaStream_t s, const Bat& bt) {
     // 2D: the u rows gather straight from global memory (measured on radial 32x32 p=8:
     // the staged boxes cut the blocks per SM of both halves more than they save,
     // 19.3 vs 15.8 us); 3D: staged (sine 3D: 76 vs 98 us)
@@ -1712,74 +1793,157 @@ cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double a
     const size_t per = (size_t)(3 * g.nb + g.n * g.n) * sizeof(double);
     const size_t st = g.d == 2 ? urow_smem<2>(gu, true, true) : urow_smem<3>(gu, true, true);
     const size_t smem = std::max(st, (cpb + 1) * per);
-    if (g.d == 2) k_newton_fused<2><<<nu + nc, 256, smem, s>>>(gu, gw, alpha, beta, x, y, nu, gs, cpb);
-    else k_newton_fused<3><<<nu + nc, 256, smem, s>>>(gu, gw, alpha, beta, x, y, nu, gs, cpb);
+    const dim3 grid(nu + nc, bt.np);
+    if (g.d == 2) k_newton_fused<2><<<grid, 256, smem, s>>>(gu, gw, alpha, beta, x, y, nu, gs, cpb, bt);
+    else k_newton_fused<3><<<grid, 256, smem, s>>>(gu, gw, alpha, beta, x, y, nu, gs, cpb, bt);
     note_launch();
     return cudaGetLastError();
 }
 
 // ==================================================================== vectors
+// One-dimensional grids over n elements; blockIdx.y is the problem of a batch.
 template <typename Tin, typename Tout>
-__global__ void k_convert(const Tin* __restrict__ x, Tout* __restrict__ y, long long n) {
+__global__ void k_convert(const Tin* __restrict__ x, Tout* __restrict__ y, long long n, Bat bt) {
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    x = bsh(x, off);
+    y = bsh(y, off);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = (Tout)x[i];
 }
 template <typename Tin, typename Tout>
-cudaError_t launch_convert(const Tin* x, Tout* y, long long n, cudaStream_t s) {
-    k_convert<Tin, Tout><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
+cudaError_t launch_convert(const Tin* x, Tout* y, long long n, cudaStream_t s, const Bat& bt) {
+    k_convert<Tin, Tout><<<dim3((unsigned)((n + 255) / 256), bt.np), 256, 0, s>>>(x, y, n, bt);
     note_launch();
     return cudaGetLastError();
 }
 
-__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, long long n) {
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, long long n,
+                        Bat bt) {
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    x = bsh(x, off);
+    y = bsh(y, off);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = a * x[i] + b * y[i];
 }
-cudaError_t launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s) {
-    k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, x, b, y, n);
+cudaError_t launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s, const Bat& bt) {
+    k_axpby<<<dim3((unsigned)((n + 255) / 256), bt.np), 256, 0, s>>>(a, x, b, y, n, bt);
     note_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void k_sub_scaled(const double* __restrict__ x, double b, const T* __restrict__ z, double* __restrict__ y,
-                             long long n) {
+                             long long n, Bat bt) {
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    x = bsh(x, off);
+    z = bsh(z, off);
+    y = bsh(y, off);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = x[i] - b * (double)z[i];
 }
 template <typename T>
-cudaError_t launch_sub_scaled(const double* x, double b, const T* z, double* y, long long n, cudaStream_t s) {
-    k_sub_scaled<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, b, z, y, n);
+cudaError_t launch_sub_scaled(const double* x, double b, const T* z, double* y, long long n, cudaStream_t s,
+                              const Bat& bt) {
+    k_sub_scaled<T><<<dim3((unsigned)((n + 255) / 256), bt.np), 256, 0, s>>>(x, b, z, y, n, bt);
     note_launch();
     return cudaGetLastError();
 }
 
+// xt = x - lam dx; lam from Bat::par (kParLam) when given
 __global__ void k_trial(const double* __restrict__ x, const double* __restrict__ dx, double lam,
-                        double* __restrict__ xt, long long n) {
+                        double* __restrict__ xt, long long n, Bat bt) {
+    long long off;
+    const int pb = (int)blockIdx.y;
+    if (!bat_enter(bt, pb, &off)) return;
+    x = bsh(x, off);
+    dx = bsh(dx, off);
+    xt = bsh(xt, off);
+    if (bt.par) lam = bt.par[pb * kBatPar + kParLam];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) xt[i] = x[i] - lam * dx[i];
 }
-cudaError_t launch_trial(const double* x, const double* dx, double lam, double* xt, long long n, cudaStream_t s) {
-    k_trial<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, dx, lam, xt, n);
+cudaError_t launch_trial(const double* x, const double* dx, double lam, double* xt, long long n, cudaStream_t s,
+                         const Bat& bt) {
+    k_trial<<<dim3((unsigned)((n + 255) / 256), bt.np), 256, 0, s>>>(x, dx, lam, xt, n, bt);
     note_launch();
     return cudaGetLastError();
 }
 
-__global__ void k_sumsq(const double* __restrict__ x, long long n, double* __restrict__ part) {
+__global__ void k_sumsq(const double* __restrict__ x, long long n, double* __restrict__ part, Bat bt) {
     __shared__ double sh[32];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    x = bsh(x, off);
+    part = bsh(part, off);
     double v = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         v += x[i] * x[i];
     v = block_sum(v, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
-cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts, cudaStream_t s) {
+cudaError_t launch_sumsq(const double* x, long long n, double* part, int* nparts, cudaStream_t s, const Bat& bt) {
     int b = (int)((n + 255) / 256);
     if (b > 1024) b = 1024;
     if (b < 1) b = 1;
-    k_sumsq<<<b, 256, 0, s>>>(x, n, part);
+    k_sumsq<<<dim3(b, bt.np), 256, 0, s>>>(x, n, part, bt);
     note_launch();
     *nparts = b;
+    return cudaGetLastError();
+}
+
+// y = x (n elements of T) and y = 0, per problem of a batch
+template <typename T>
+__global__ void k_copy(const T* __restrict__ x, T* __restrict__ y, long long n, Bat bt) {
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    x = bsh(x, off);
+    y = bsh(y, off);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = x ? x[i] : T(0);
+}
+template <typename T>
+cudaError_t launch_copy(const T* x, T* y, long long n, cudaStream_t s, const Bat& bt) {
+    long long b = (n + 255) / 256;
+    if (b > 2048) b = 2048;
+    if (b < 1) b = 1;
+    k_copy<T><<<dim3((unsigned)b, bt.np), 256, 0, s>>>(x, y, n, bt);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// *dst = par[pb][slot] for every problem of the batch (per-problem scalars into the problems' slabs)
+__global__ void k_scatter_par(double* __restrict__ dst, int slot, Bat bt) {
+    const int pb = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (pb >= bt.np) return;
+    long long off;
+    if (!bat_enter(bt, pb, &off)) return;
+    *bsh(dst, off) = bt.par[pb * kBatPar + slot];
+}
+cudaError_t launch_scatter_par(double* dst, int slot, cudaStream_t s, const Bat& bt) {
+    k_scatter_par<<<(bt.np + 63) / 64, 64, 0, s>>>(dst, slot, bt);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// out[pb * nd + k] = d[k] of problem pb (k < nd), out[np * nd + pb * ni + k] = i[k]:
+// the status words the host reads after a batched step, in one copy
+__global__ void k_gather_status(const double* __restrict__ d, int nd, const int* __restrict__ iv, int ni,
+                                double* __restrict__ out, Bat bt) {
+    const int pb = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (pb >= bt.np) return;
+    const long long off = bt.delta ? bt.delta[pb] : 0LL;
+    const double* dp = bsh(d, off);
+    const int* ip = bsh(iv, off);
+    for (int k = 0; k < nd; ++k) out[pb * nd + k] = dp[k];
+    for (int k = 0; k < ni; ++k) out[bt.np * nd + pb * ni + k] = (double)ip[k];
+}
+cudaError_t launch_gather_status(const double* d, int nd, const int* iv, int ni, double* out, cudaStream_t s,
+                                 const Bat& bt) {
+    k_gather_status<<<(bt.np + 63) / 64, 64, 0, s>>>(d, nd, iv, ni, out, bt);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1798,8 +1962,18 @@ template <typename VT>
 __global__ void k_gm_start(VT* __restrict__ Vb, const double* __restrict__ b, long long N,
                            const double* __restrict__ part, int nparts, double rtol, double* __restrict__ scal,
                            double* __restrict__ gv, int kmax, int cap, int* __restrict__ iflag,
-                           int* __restrict__ jdev) {
+                           int* __restrict__ jdev, double* __restrict__ H, Bat bt) {
     __shared__ double sh[32];
+    long long off;
+    const int pb = (int)blockIdx.y;
+    if (!bat_enter(bt, pb, &off)) return;
+    Vb = bsh(Vb, off); b = bsh(b, off); part = bsh(part, off); scal = bsh(scal, off); gv = bsh(gv, off);
+    iflag = bsh(iflag, off); jdev = bsh(jdev, off); H = bsh(H, off);
+    if (bt.par) rtol = bt.par[pb * kBatPar + kParRtol];
+    // the Hessenberg matrix starts at zero
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)(kmax + 1) * kmax;
+         i += (long long)gridDim.x * blockDim.x)
+        H[i] = 0.0;
     double v = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
     v = block_sum(v, sh);
@@ -1852,9 +2026,13 @@ template <typename VT, bool VEC>
 __global__ void __launch_bounds__(256)
     k_gm_dots2(const VT* __restrict__ Vb, const int* __restrict__ jdev, long long N, double* __restrict__ part,
                int kmax, const int* __restrict__ iflag, const int* __restrict__ reo, double* __restrict__ hsum,
-               unsigned int* __restrict__ counter) {
+               unsigned int* __restrict__ counter, Bat bt) {
     __shared__ __align__(16) VT ws[kDotChunk];
     __shared__ bool last;
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.z, &off)) return;
+    Vb = bsh(Vb, off); jdev = bsh(jdev, off); part = bsh(part, off); iflag = bsh(iflag, off); reo = bsh(reo, off);
+    hsum = bsh(hsum, off); counter = bsh(counter, off);
     if (iflag[0]) return;
     if (reo && *reo == 0) return;                        // second pass not needed
     const int j = *jdev;
@@ -2072,9 +2250,13 @@ template <typename VT, bool VEC>
 __global__ void __launch_bounds__(256)
     k_gm_update1(VT* __restrict__ Vb, const int* __restrict__ jdev, long long N, const double* __restrict__ hsum,
                  int kmax, double* __restrict__ H, double* __restrict__ scal, int* __restrict__ reo,
-                 const int* __restrict__ force, const int* __restrict__ iflag) {
+                 const int* __restrict__ force, const int* __restrict__ iflag, Bat bt) {
     __shared__ double h[kMaxKrylov + 2];
     __shared__ VT hv[kMaxKrylov + 2];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    Vb = bsh(Vb, off); jdev = bsh(jdev, off); hsum = bsh(hsum, off); H = bsh(H, off); scal = bsh(scal, off);
+    reo = bsh(reo, off); force = bsh(force, off); iflag = bsh(iflag, off);
     if (iflag[0]) return;
     const int j = *jdev;
     load_sums(hsum, j + 2, h, hv);                  // h1[0..j], ||w||^2 in h[j+1]
@@ -2097,11 +2279,16 @@ __global__ void __launch_bounds__(256)
     k_gm_update2(VT* __restrict__ Vb, const int* __restrict__ jdev_c, long long N, const double* __restrict__ hsum,
                  int kmax, double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
                  double* __restrict__ gv, double* __restrict__ scal, int* __restrict__ iflag,
-                 const int* __restrict__ reo, unsigned int* __restrict__ counter, int* __restrict__ jdev) {
+                 const int* __restrict__ reo, unsigned int* __restrict__ counter, int* __restrict__ jdev, Bat bt) {
     __shared__ double h[kMaxKrylov + 2];
     __shared__ VT hv[kMaxKrylov + 2];
     __shared__ double shn;
     __shared__ bool last;
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    Vb = bsh(Vb, off); jdev_c = bsh(jdev_c, off); hsum = bsh(hsum, off); H = bsh(H, off); cs = bsh(cs, off);
+    sn = bsh(sn, off); gv = bsh(gv, off); scal = bsh(scal, off); iflag = bsh(iflag, off); reo = bsh(reo, off);
+    counter = bsh(counter, off); jdev = bsh(jdev, off);
     if (iflag[0]) return;
     const int j = *jdev_c;
     const bool second = *reo != 0;
@@ -2171,8 +2358,11 @@ __global__ void __launch_bounds__(256)
 // Back substitution H y = g on the k completed columns; the packed upper
 // triangle is staged in shared memory when it fits (use_smem), else read from H.
 __global__ void k_gm_backsolve(const double* __restrict__ H, const double* __restrict__ gv, const int* __restrict__ iflag,
-                               int kmax, double* __restrict__ y, int use_smem) {
+                               int kmax, double* __restrict__ y, int use_smem, Bat bt) {
     extern __shared__ double shH[];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.x, &off)) return;
+    H = bsh(H, off); gv = bsh(gv, off); iflag = bsh(iflag, off); y = bsh(y, off);
     const int k = iflag[1];
     if (use_smem) {
         for (int e = threadIdx.x; e < k * (k + 1) / 2; e += blockDim.x) {
@@ -2197,7 +2387,10 @@ __global__ void k_gm_backsolve(const double* __restrict__ H, const double* __res
 
 template <typename VT>
 __global__ void k_gm_combine(const VT* __restrict__ Vb, const double* __restrict__ y,
-                             const int* __restrict__ iflag, long long N, double* __restrict__ x) {
+                             const int* __restrict__ iflag, long long N, double* __restrict__ x, Bat bt) {
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    Vb = bsh(Vb, off); y = bsh(y, off); iflag = bsh(iflag, off); x = bsh(x, off);
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N) return;
     const int k = iflag[1];
@@ -2225,47 +2418,82 @@ cudaError_t launch_gm_setcond(cudaGraphConditionalHandle h, const int* iflag, cu
     return cudaGetLastError();
 }
 
+// Batched loop: keep looping while any problem of the batch has not stopped.
+__global__ void k_gm_setcond_batch(cudaGraphConditionalHandle h, const int* __restrict__ iflag, Bat bt) {
+    int running = 0;
+    for (int pb = threadIdx.x; pb < bt.np; pb += blockDim.x) {
+        const long long off = bt.delta ? bt.delta[pb] : 0LL;
+        if (bsh(iflag, off)[0] == 0) running = 1;
+    }
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, running ? 1u : 0u);
+}
+
+cudaError_t launch_gm_setcond_batch(cudaGraphConditionalHandle h, const int* iflag, cudaStream_t s, const Bat& bt) {
+    k_gm_setcond_batch<<<1, 128, 0, s>>>(h, iflag, bt);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Stop the GMRES of every problem the mask selects (problems that take no part in
+// a batched Krylov solve must not run in its device-side loop).
+__global__ void k_gm_stop(int* __restrict__ iflag, Bat bt) {
+    const int pb = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (pb >= bt.np) return;
+    long long off;
+    if (!bat_enter(bt, pb, &off)) return;
+    bsh(iflag, off)[0] = 1;
+}
+
+cudaError_t launch_gm_stop(int* iflag, cudaStream_t s, const Bat& bt) {
+    k_gm_stop<<<(bt.np + 63) / 64, 64, 0, s>>>(iflag, bt);
+    note_launch();
+    return cudaGetLastError();
+}
+
 int gmres_dot_blocks(long long N) { return (int)((N + kDotChunk - 1) / kDotChunk); }
 int gmres_dot_groups(int kmax) { return (kmax + 2 + kDotVec - 1) / kDotVec; }
 int gmres_upd_blocks(long long N) { return (int)((N + 255) / 256); }
 
 template <typename VT>
-cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s, int cap) {
+cudaError_t gmres_start(GmresDev& G, const double* b, double rtol, cudaStream_t s, int cap, const Bat& bt) {
     int np = 0;
-    cudaError_t e = launch_sumsq(b, G.N, G.part_norm, &np, s);
+    cudaError_t e = launch_sumsq(b, G.N, G.part_norm, &np, s, bt);
     if (e != cudaSuccess) return e;
-    cudaMemsetAsync(G.H, 0, sizeof(double) * (size_t)(G.kmax + 1) * G.kmax, s);
     const int nb = gmres_upd_blocks(G.N) < 1024 ? gmres_upd_blocks(G.N) : 1024;
     const int c = (cap > 0 && cap < G.kmax) ? cap : G.kmax;
-    k_gm_start<VT><<<nb, 256, 0, s>>>(gmres_basis<VT>(G), b, G.N, G.part_norm, np, rtol, G.scal, G.gv, G.kmax, c,
-                                      G.iflag, G.jdev);
+    k_gm_start<VT><<<dim3(nb, bt.np), 256, 0, s>>>(gmres_basis<VT>(G), b, G.N, G.part_norm, np, rtol, G.scal, G.gv,
+                                                   G.kmax, c, G.iflag, G.jdev, G.H, bt);
     note_launch();
     return cudaGetLastError();
 }
 
 template <typename VT, bool VEC>
-static void arnoldi_launch(GmresDev& G, cudaStream_t s) {
+static void arnoldi_launch(GmresDev& G, cudaStream_t s, const Bat& bt) {
     const int nch = gmres_dot_blocks(G.N);
     const int bu = (int)((G.N + upd_elems<VT>() - 1) / upd_elems<VT>());
-    const dim3 gd(nch, gmres_dot_groups(G.kmax));
+    const dim3 gd(nch, gmres_dot_groups(G.kmax), bt.np);
+    const dim3 gu(bu, bt.np);
     VT* V = gmres_basis<VT>(G);
     k_gm_dots2<VT, VEC><<<gd, 256, 0, s>>>(V, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, nullptr, G.hsum,
-                                             G.counter);
+                                             G.counter, bt);
     note_launch();
-    k_gm_update1<VT, VEC><<<bu, 256, 0, s>>>(V, G.jdev, G.N, G.hsum, G.kmax, G.H, G.scal, G.reo, G.force, G.iflag);
+    k_gm_update1<VT, VEC><<<gu, 256, 0, s>>>(V, G.jdev, G.N, G.hsum, G.kmax, G.H, G.scal, G.reo, G.force, G.iflag,
+                                             bt);
     note_launch();
-    k_gm_dots2<VT, VEC><<<gd, 256, 0, s>>>(V, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, G.reo, G.hsum, G.counter);
+    k_gm_dots2<VT, VEC><<<gd, 256, 0, s>>>(V, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, G.reo, G.hsum, G.counter,
+                                             bt);
     note_launch();
-    k_gm_update2<VT, VEC><<<bu, 256, 0, s>>>(V, G.jdev, G.N, G.hsum, G.kmax, G.H, G.cs, G.sn, G.gv, G.scal,
-                                             G.iflag, G.reo, G.counter2, G.jdev);
+    k_gm_update2<VT, VEC><<<gu, 256, 0, s>>>(V, G.jdev, G.N, G.hsum, G.kmax, G.H, G.cs, G.sn, G.gv, G.scal,
+                                             G.iflag, G.reo, G.counter2, G.jdev, bt);
     note_launch();
 }
 
 template <typename VT>
-cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s) {
+cudaError_t gmres_arnoldi(GmresDev& G, cudaStream_t s, const Bat& bt) {
     // float4 access needs every basis vector 16-byte aligned: N a multiple of 4
-    if (sizeof(VT) == 4 && G.N % 4 == 0) arnoldi_launch<VT, true>(G, s);
-    else arnoldi_launch<VT, false>(G, s);
+    if (sizeof(VT) == 4 && G.N % 4 == 0) arnoldi_launch<VT, true>(G, s, bt);
+    else arnoldi_launch<VT, false>(G, s, bt);
     return cudaGetLastError();
 }
 
@@ -2285,28 +2513,29 @@ cudaError_t gmres_timed_step(GmresDev& G, int j, cudaStream_t s) {
     if (j < 0 || j >= G.kmax) return cudaErrorInvalidValue;
     k_gm_setj<<<1, 32, 0, s>>>(G.jdev, G.iflag, G.counter2, j, G.kmax);
     note_launch();
-    return gmres_arnoldi<VT>(G, s);
+    return gmres_arnoldi<VT>(G, s, Bat{});
 }
 
 template <typename VT>
-cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s) {
+cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s, const Bat& bt) {
     const size_t tri = (size_t)G.kmax * (G.kmax + 1) / 2 * sizeof(double);
     const int use_smem = tri <= 200 * 1024;
-    k_gm_backsolve<<<1, 256, use_smem ? tri : 0, s>>>(G.H, G.gv, G.iflag, G.kmax, G.y, use_smem);
+    k_gm_backsolve<<<bt.np, 256, use_smem ? tri : 0, s>>>(G.H, G.gv, G.iflag, G.kmax, G.y, use_smem, bt);
     note_launch();
-    k_gm_combine<VT><<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(gmres_basis<VT>(G), G.y, G.iflag, G.N, x);
+    k_gm_combine<VT><<<dim3((unsigned)((G.N + 255) / 256), bt.np), 256, 0, s>>>(gmres_basis<VT>(G), G.y, G.iflag,
+                                                                               G.N, x, bt);
     note_launch();
     return cudaGetLastError();
 }
 
-template cudaError_t gmres_start<double>(GmresDev&, const double*, double, cudaStream_t, int);
-template cudaError_t gmres_start<float>(GmresDev&, const double*, double, cudaStream_t, int);
-template cudaError_t gmres_arnoldi<double>(GmresDev&, cudaStream_t);
-template cudaError_t gmres_arnoldi<float>(GmresDev&, cudaStream_t);
+template cudaError_t gmres_start<double>(GmresDev&, const double*, double, cudaStream_t, int, const Bat&);
+template cudaError_t gmres_start<float>(GmresDev&, const double*, double, cudaStream_t, int, const Bat&);
+template cudaError_t gmres_arnoldi<double>(GmresDev&, cudaStream_t, const Bat&);
+template cudaError_t gmres_arnoldi<float>(GmresDev&, cudaStream_t, const Bat&);
 template cudaError_t gmres_timed_step<double>(GmresDev&, int, cudaStream_t);
 template cudaError_t gmres_timed_step<float>(GmresDev&, int, cudaStream_t);
-template cudaError_t gmres_finish<double>(GmresDev&, double*, cudaStream_t);
-template cudaError_t gmres_finish<float>(GmresDev&, double*, cudaStream_t);
+template cudaError_t gmres_finish<double>(GmresDev&, double*, cudaStream_t, const Bat&);
+template cudaError_t gmres_finish<float>(GmresDev&, double*, cudaStream_t, const Bat&);
 
 // ---- vector blocks of the flexible GMRES on G (host-driven outer loop) ---------
 // part[v * nchunks + c] = sum over chunk c (kFgChunk elements) of V_v . w, v < nv
@@ -2386,28 +2615,6 @@ void configure_kernels() {
     cudaFuncSetAttribute(k_newton_fused<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-// ============================================================ instantiations
-template cudaError_t launch_factor<double>(const Geo<double>&, const double*, double, double, double*, double*,
-                                           int*, double*, cudaStream_t);
-template cudaError_t launch_factor<float>(const Geo<float>&, const float*, double, double, float*, double*, int*,
-                                          float*, cudaStream_t);
-template cudaError_t launch_precond<double, double, double>(const Geo<double>&, const double*, const double*,
-                                                            double*, cudaStream_t, IterCtl);
-template cudaError_t launch_precond<float, float, float>(const Geo<float>&, const float*, const float*, float*,
-                                                         cudaStream_t, IterCtl);
-template cudaError_t launch_precond<float, double, float>(const Geo<float>&, const float*, const double*, float*,
-                                                          cudaStream_t, IterCtl);
-template cudaError_t launch_precond<float, double, double>(const Geo<float>&, const float*, const double*,
-                                                           double*, cudaStream_t, IterCtl);
-template cudaError_t launch_bapply<double, double, double>(const Geo<double>&, const double*, double*, cudaStream_t,
-                                                           const int*);
-template cudaError_t launch_bapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t,
-                                                        const int*);
-template cudaError_t launch_bapply<float, double, float>(const Geo<float>&, const double*, float*, cudaStream_t,
-                                                         const int*);
-template cudaError_t launch_btapply<double, double, double>(const Geo<double>&, const double*, double*,
-                                                            cudaStream_t);
-template cudaError_t launch_btapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t);
 // ---- SIMT FMA throughput probe ------------------------------------------------
 // Eight independent FMA chains per thread (enough to cover the pipe latency with
 // 8 warps per SM scheduler), x <- x * a + b with |a| < 1 so nothing overflows; the
@@ -2456,21 +2663,47 @@ cudaError_t measure_fma_peak(int elem, int sm_count, cudaStream_t s, double* tfl
     return cudaStreamSynchronize(s);
 }
 
+// ============================================================ instantiations
+template cudaError_t launch_factor<double>(const Geo<double>&, const double*, double, double, double*, double*,
+                                           int*, double*, cudaStream_t, const Bat&);
+template cudaError_t launch_factor<float>(const Geo<float>&, const float*, double, double, float*, double*, int*,
+                                          float*, cudaStream_t, const Bat&);
+template cudaError_t launch_precond<double, double, double>(const Geo<double>&, const double*, const double*,
+                                                            double*, cudaStream_t, IterCtl, const Bat&);
+template cudaError_t launch_precond<float, float, float>(const Geo<float>&, const float*, const float*, float*,
+                                                         cudaStream_t, IterCtl, const Bat&);
+template cudaError_t launch_precond<float, double, float>(const Geo<float>&, const float*, const double*, float*,
+                                                          cudaStream_t, IterCtl, const Bat&);
+template cudaError_t launch_precond<float, double, double>(const Geo<float>&, const float*, const double*,
+                                                           double*, cudaStream_t, IterCtl, const Bat&);
+template cudaError_t launch_bapply<double, double, double>(const Geo<double>&, const double*, double*, cudaStream_t,
+                                                           const int*, const Bat&);
+template cudaError_t launch_bapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t,
+                                                        const int*, const Bat&);
+template cudaError_t launch_bapply<float, double, float>(const Geo<float>&, const double*, float*, cudaStream_t,
+                                                         const int*, const Bat&);
+template cudaError_t launch_btapply<double, double, double>(const Geo<double>&, const double*, double*,
+                                                            cudaStream_t, const Bat&);
+template cudaError_t launch_btapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t,
+                                                         const Bat&);
 template cudaError_t launch_fdm<double>(const Geo<double>&, const double*, double, const double*, double*, double*,
-                                        double*, cudaStream_t, const int*);
+                                        double*, cudaStream_t, const int*, const Bat&);
 template cudaError_t launch_fdm<float>(const Geo<float>&, const double*, double, const float*, float*, float*,
-                                       float*, cudaStream_t, const int*);
+                                       float*, cudaStream_t, const int*, const Bat&);
 template cudaError_t launch_schur_rest<double, double>(const Geo<double>&, const double*, double, const double*,
-                                                       const double*, double*, cudaStream_t, IterCtl);
+                                                       const double*, double*, cudaStream_t, IterCtl, const Bat&);
 template cudaError_t launch_schur_rest<float, float>(const Geo<float>&, const float*, double, const float*,
-                                                    const float*, float*, cudaStream_t, IterCtl);
+                                                    const float*, float*, cudaStream_t, IterCtl, const Bat&);
 template cudaError_t launch_schur_rest<float, double>(const Geo<float>&, const float*, double, const float*,
-                                                      const float*, double*, cudaStream_t, IterCtl);
-template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
-template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+                                                      const float*, double*, cudaStream_t, IterCtl, const Bat&);
+template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t, const Bat&);
+template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t, const Bat&);
 template cudaError_t launch_sub_scaled<double>(const double*, double, const double*, double*, long long,
-                                               cudaStream_t);
+                                               cudaStream_t, const Bat&);
 template cudaError_t launch_sub_scaled<float>(const double*, double, const float*, double*, long long,
-                                              cudaStream_t);
+                                              cudaStream_t, const Bat&);
+template cudaError_t launch_copy<double>(const double*, double*, long long, cudaStream_t, const Bat&);
+template cudaError_t launch_copy<float>(const float*, float*, long long, cudaStream_t, const Bat&);
+template cudaError_t launch_copy<int>(const int*, int*, long long, cudaStream_t, const Bat&);
 
 }  // namespace hpg

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <map>
 #include <tuple>
+#include <type_traits>
 #include <mutex>
 #include <thread>
 #include <chrono>
@@ -193,6 +194,8 @@ static T* upload_vec(DevState& D, const std::vector<double>& v, bool& ok, cudaSt
 template <typename T>
 static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, T* w1, T* w2);
 
+long long next_alloc_gen();
+
 hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     if (P.alloc_done) return HPG_OK;
     HostProblem& H = P.H;
@@ -269,73 +272,105 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     }
     const size_t Nu0 = H.Nu0, Npsi = H.Npsi, Nx = Nu0 + Npsi;
     const size_t gsz = H.Nq * gauss_stride(H.kind, d);
-    D.rA = dalloc<double>(D, Nu0, ok);
-    D.rB = dalloc<double>(D, Npsi, ok);
-    D.bf = dalloc<double>(D, Nu0, ok);
-    D.phiz = dalloc<double>(D, Npsi, ok);
-    D.phiq = dalloc<double>(D, H.Nq, ok);
-    D.x = dalloc<double>(D, Nx, ok);
-    D.xt = dalloc<double>(D, Nx, ok);
-    D.psi_prev = dalloc<double>(D, Npsi, ok);
-    D.gw = dalloc<double>(D, gsz, ok);
-    D.gwt = dalloc<double>(D, gsz, ok);
-    D.gwl = dalloc<double>(D, gsz, ok);
-    D.gwf = dalloc<float>(D, gsz, ok);
-    D.alpha_dev = dalloc<double>(D, 1, ok);
-    {
-        const size_t fw_d = factor_workspace_elems(H.n, d, (int)H.nb, H.ncomp, (long long)H.Nc, 8);
-        const size_t fw_f = factor_workspace_elems(H.n, d, (int)H.nb, H.ncomp, (long long)H.Nc, 4);
-        if (fw_d) D.fwork_d = dalloc<double>(D, fw_d, ok);
-        if (fw_f) D.fwork_f = dalloc<float>(D, fw_f, ok);
+    // Per-problem state (data, Newton state, factors, Krylov basis) lives in one
+    // slab: every problem of a shape lays it out identically, so a batched launch
+    // reaches problem b's copy of a buffer at a fixed byte offset from problem 0's.
+    GmresDev& Gk = D.gm;
+    Gk.kmax = std::max(1, P.params.krylov_max);
+    Gk.N = (long long)Npsi;
+    char* slab = nullptr;
+    size_t slab_need = 0, slab_off = 0;
+    bool measuring = true;
+    auto sa = [&](auto*& ptr, size_t n) {
+        using E = std::remove_reference_t<decltype(*ptr)>;
+        const size_t bytes = ((std::max<size_t>(n, 1) * sizeof(E)) + 255) & ~(size_t)255;
+        if (measuring) {
+            slab_need += bytes;
+        } else {
+            ptr = reinterpret_cast<E*>(slab + slab_off);
+            slab_off += bytes;
+        }
+    };
+    auto state_buffers = [&]() {
+        sa(D.rA, Nu0);
+        sa(D.rB, Npsi);
+        sa(D.bf, Nu0);
+        sa(D.phiz, Npsi);
+        sa(D.phiq, H.Nq);
+        sa(D.x, Nx);
+        sa(D.xt, Nx);
+        sa(D.psi_prev, Npsi);
+        sa(D.gw, gsz);
+        sa(D.gwt, gsz);
+        sa(D.gwl, gsz);
+        sa(D.gwf, gsz);
+        sa(D.alpha_dev, 1);
+        {
+            const size_t fw_d = factor_workspace_elems(H.n, d, (int)H.nb, H.ncomp, (long long)H.Nc, 8);
+            const size_t fw_f = factor_workspace_elems(H.n, d, (int)H.nb, H.ncomp, (long long)H.Nc, 4);
+            if (fw_d) sa(D.fwork_d, fw_d);
+            if (fw_f) sa(D.fwork_f, fw_f);
+        }
+        sa(D.eg, Npsi);
+        sa(D.egt, Npsi);
+        sa(D.F, Nx);
+        sa(D.Ft, Nx);
+        sa(D.delta, Nx);
+        sa(D.r, Nx);
+        sa(D.dcorr, Nx);
+        const size_t sblk = (size_t)H.Nc * H.nb * H.nb;
+        sa(D.Sinv_d, sblk);
+        sa(D.Sinv_f, sblk);
+        sa(D.tu_d, Nu0);
+        sa(D.tu2_d, Nu0);
+        sa(D.w1_d, Nu0);
+        sa(D.w2_d, Nu0);
+        sa(D.tu_f, Nu0);
+        sa(D.tu2_f, Nu0);
+        sa(D.w1_f, Nu0);
+        sa(D.w2_f, Nu0);
+        sa(D.zp_d, Npsi);
+        sa(D.zp_f, Npsi);
+        sa(D.yp, Npsi);
+        sa(D.xs, Npsi);
+        int n1v[kMaxDim] = {1, 1, 1};
+        for (int j = 0; j < d; ++j) n1v[j] = H.dir[j].n1;
+        const int nres = n_res_partials_for(d, n1v, (long long)Npsi);
+        sa(D.part, std::max(nres, 1024));
+        sa(D.scal, 16);
+        sa(D.flag, 4);
+        // GMRES
+        GmresDev& G = D.gm;
+        sa(G.Vb, (size_t)(G.kmax + 1) * Npsi);
+        sa(G.H, (size_t)(G.kmax + 1) * G.kmax);
+        sa(G.cs, G.kmax);
+        sa(G.sn, G.kmax);
+        sa(G.gv, G.kmax + 1);
+        sa(G.part_dots, (size_t)gmres_dot_blocks(G.N) * (G.kmax + 2));
+        sa(G.part_norm, std::max<size_t>(1024, (size_t)gmres_upd_blocks(G.N)));
+        sa(G.scal, 8);
+        sa(G.iflag, 8);
+        sa(G.jdev, 1);
+        sa(G.hsum, G.kmax + 2);
+        sa(G.counter, gmres_dot_groups(G.kmax));
+        sa(G.counter2, 1);
+        sa(G.reo, 1);
+        sa(G.force, 1);
+        sa(G.y, G.kmax + 1);
+    };
+    state_buffers();
+    measuring = false;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&slab), slab_need, D.alloc_stream) != cudaSuccess) {
+        free_device(P, s);
+        ctx->err = "device allocation failed";
+        return HPG_ERR_OOM;
     }
-    D.eg = dalloc<double>(D, Npsi, ok);
-    D.egt = dalloc<double>(D, Npsi, ok);
-    D.F = dalloc<double>(D, Nx, ok);
-    D.Ft = dalloc<double>(D, Nx, ok);
-    D.delta = dalloc<double>(D, Nx, ok);
-    D.r = dalloc<double>(D, Nx, ok);
-    D.dcorr = dalloc<double>(D, Nx, ok);
-    const size_t sblk = (size_t)H.Nc * H.nb * H.nb;
-    D.Sinv_d = dalloc<double>(D, sblk, ok);
-    D.Sinv_f = dalloc<float>(D, sblk, ok);
-    D.tu_d = dalloc<double>(D, Nu0, ok);
-    D.tu2_d = dalloc<double>(D, Nu0, ok);
-    D.w1_d = dalloc<double>(D, Nu0, ok);
-    D.w2_d = dalloc<double>(D, Nu0, ok);
-    D.tu_f = dalloc<float>(D, Nu0, ok);
-    D.tu2_f = dalloc<float>(D, Nu0, ok);
-    D.w1_f = dalloc<float>(D, Nu0, ok);
-    D.w2_f = dalloc<float>(D, Nu0, ok);
-    D.zp_d = dalloc<double>(D, Npsi, ok);
-    D.zp_f = dalloc<float>(D, Npsi, ok);
-    D.yp = dalloc<double>(D, Npsi, ok);
-    D.xs = dalloc<double>(D, Npsi, ok);
-    int n1v[kMaxDim] = {1, 1, 1};
-    for (int j = 0; j < d; ++j) n1v[j] = H.dir[j].n1;
-    const int nres = n_res_partials_for(d, n1v, (long long)Npsi);
-    D.part = dalloc<double>(D, std::max(nres, 1024), ok);
-    D.scal = dalloc<double>(D, 16, ok);
-    D.flag = dalloc<int>(D, 4, ok);
-    // GMRES
+    D.allocs.push_back(slab);
+    D.bytes += slab_need;
+    D.slab = slab;
+    D.slab_bytes = slab_need;
+    state_buffers();
     GmresDev& G = D.gm;
-    G.kmax = std::max(1, P.params.krylov_max);
-    G.N = (long long)Npsi;
-    G.Vb = dalloc<double>(D, (size_t)(G.kmax + 1) * Npsi, ok);
-    G.H = dalloc<double>(D, (size_t)(G.kmax + 1) * G.kmax, ok);
-    G.cs = dalloc<double>(D, G.kmax, ok);
-    G.sn = dalloc<double>(D, G.kmax, ok);
-    G.gv = dalloc<double>(D, G.kmax + 1, ok);
-    G.part_dots = dalloc<double>(D, (size_t)gmres_dot_blocks(G.N) * (G.kmax + 2), ok);
-    G.part_norm = dalloc<double>(D, std::max<size_t>(1024, (size_t)gmres_upd_blocks(G.N)), ok);
-    G.scal = dalloc<double>(D, 8, ok);
-    G.iflag = dalloc<int>(D, 8, ok);
-    G.jdev = dalloc<int>(D, 1, ok);
-    G.hsum = dalloc<double>(D, G.kmax + 2, ok);
-    G.counter = dalloc<unsigned int>(D, gmres_dot_groups(G.kmax), ok);
-    G.counter2 = dalloc<unsigned int>(D, 1, ok);
-    G.reo = dalloc<int>(D, 1, ok);
-    G.force = dalloc<int>(D, 1, ok);
-    G.y = dalloc<double>(D, G.kmax + 1, ok);
     if (!ok) { free_device(P, s); ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
     cudaMemsetAsync(G.counter, 0, sizeof(unsigned int) * gmres_dot_groups(G.kmax), s);
     cudaMemsetAsync(G.counter2, 0, sizeof(unsigned int), s);
@@ -407,6 +442,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     if (P.params.fdm_tile_f32 >= 0) D.gf.gemm_cfg = P.params.fdm_tile_f32;
     else CKS(autotune_fdm<float>(ctx, P, D.gf, D.tu_f, D.tu2_f, D.w1_f, D.w2_f));
     P.alloc_done = true;
+    P.alloc_gen = next_alloc_gen();
     return HPG_OK;
 }
 
@@ -1077,8 +1113,8 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
                 if (h == P.params.ls_max) { st.ls_fail++; break; }
                 lam *= 0.5;
             }
-            // factorisation flag (non-SPD block) is sticky in bit 1
-            CK(cudaMemcpyAsync(D.h_iflag, D.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            // factorisation flag (non-SPD block): bit 1 of flag[1], sticky for the solve
+            CK(cudaMemcpyAsync(D.h_iflag, D.flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (D.h_iflag[0] & 2) { status = HPG_ERR_NOT_SPD; break; }
             swap_state(D);
@@ -1103,6 +1139,594 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
     return status;
 }
 
+// ====================================================== lockstep groups (batched launches)
+// Problems of one shape are solved together: every launch of a Newton step or of a
+// Krylov iteration serves all problems of the group at once (Bat), so a batch of
+// small solves fills the GPU with few, large launches instead of many small ones.
+// Each problem keeps the arithmetic it has alone -- the same kernels, launch shapes,
+// operands and reduction orders -- and the host keeps each problem's Newton,
+// line-search and refinement decisions apart, masking problems out of the launches
+// they take no part in.  Results are therefore those of hpg_solve, bit for bit.
+namespace {
+enum { kMaskStart = 0, kMaskNewton = 1, kMaskSolve = 2, kMaskTrial = 3, kMaskIdle = 4, kMaskPrev = 5,
+       kMaskCount = 6 };
+constexpr int kStatD = 4;   // gathered doubles per problem (scal[0..3] or GMRES scal[0..3])
+constexpr int kStatI = 4;   // gathered ints per problem (flag[0..3] or GMRES iflag[0..3])
+std::atomic<long long> g_alloc_gen{0};
+}  // namespace
+
+long long next_alloc_gen() { return ++g_alloc_gen; }
+
+struct Group {
+    int np = 0;
+    std::vector<int> ids;
+    std::vector<long long> gens;
+    std::vector<Problem*> ps;
+    long long* delta_d = nullptr;
+    int* mask_d = nullptr;       // kMaskCount x np
+    double* par_d = nullptr;     // np x kBatPar
+    double* stat_d = nullptr;    // np x (kStatD + kStatI)
+    long long* h_delta = nullptr;
+    int* h_mask = nullptr;
+    double* h_par = nullptr;
+    double* h_stat = nullptr;
+    cudaGraphExec_t loop[3] = {nullptr, nullptr, nullptr};
+    long long loop_kernels[3] = {0, 0, 0};
+    bool loop_failed[3] = {false, false, false};
+    ~Group() {
+        for (auto& gx : loop)
+            if (gx) cudaGraphExecDestroy(gx);
+        if (delta_d) cudaFree(delta_d);
+        if (mask_d) cudaFree(mask_d);
+        if (par_d) cudaFree(par_d);
+        if (stat_d) cudaFree(stat_d);
+        if (h_delta) cudaFreeHost(h_delta);
+        if (h_mask) cudaFreeHost(h_mask);
+        if (h_par) cudaFreeHost(h_par);
+        if (h_stat) cudaFreeHost(h_stat);
+    }
+    Bat bat(int slot) const {
+        Bat b;
+        b.delta = delta_d;
+        b.act = slot < 0 ? nullptr : mask_d + (size_t)slot * np;
+        b.par = par_d;
+        b.np = np;
+        return b;
+    }
+    int* mask(int slot) { return h_mask + (size_t)slot * np; }
+};
+
+// Problems that may share a group: same shape (so the same operator constants and
+// the same slab layout) and the same solver parameters that launches depend on.
+static std::string group_key(const Problem& P) {
+    const HostProblem& H = P.H;
+    const hpg_params& q = P.params;
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "%d|%d|%d,%d,%d|%d|%a,%a,%a|%a,%a,%a|%d|%d|%d|%a|%d|%d|%d|%d|%d", H.d, H.kind,
+                  H.m[0], H.m[1], H.m[2], H.p, H.lo[0], H.lo[1], H.lo[2], H.hi[0], H.hi[1], H.hi[2], q.precision,
+                  q.krylov_max, q.krylov_f32, q.beta, q.fdm_tile_f32, q.fdm_tile_f64, q.strategy, q.ls_max,
+                  q.refine_max);
+    return buf;
+}
+
+// Whether a problem can run in a lockstep group at all (the flexible-GMRES strategies,
+// per-kernel timing and host-driven launches stay on the single-problem path).
+static bool groupable(const Problem& P) {
+    return P.params.strategy == HPG_SCHUR && P.params.timing == 0 && P.params.graphs != 0;
+}
+
+static hpg_status group_build(hpg_ctx* ctx, std::vector<Problem*>& ps, std::shared_ptr<Group>& out) {
+    auto Gp = std::make_shared<Group>();
+    const int np = (int)ps.size();
+    Gp->np = np;
+    Gp->ps = ps;
+    for (Problem* P : ps) {
+        Gp->ids.push_back(P->id);
+        Gp->gens.push_back(P->alloc_gen);
+        if (P->D.slab_bytes != ps[0]->D.slab_bytes) {
+            ctx->err = "problems of a group differ in layout";
+            return HPG_ERR_STATE;
+        }
+    }
+    if (cudaMalloc(&Gp->delta_d, sizeof(long long) * np) != cudaSuccess ||
+        cudaMalloc(&Gp->mask_d, sizeof(int) * np * kMaskCount) != cudaSuccess ||
+        cudaMalloc(&Gp->par_d, sizeof(double) * np * kBatPar) != cudaSuccess ||
+        cudaMalloc(&Gp->stat_d, sizeof(double) * np * (kStatD + kStatI)) != cudaSuccess ||
+        cudaMallocHost(&Gp->h_delta, sizeof(long long) * np) != cudaSuccess ||
+        cudaMallocHost(&Gp->h_mask, sizeof(int) * np * kMaskCount) != cudaSuccess ||
+        cudaMallocHost(&Gp->h_par, sizeof(double) * np * kBatPar) != cudaSuccess ||
+        cudaMallocHost(&Gp->h_stat, sizeof(double) * np * (kStatD + kStatI)) != cudaSuccess) {
+        ctx->err = "group allocation failed";
+        return HPG_ERR_OOM;
+    }
+    for (int i = 0; i < np; ++i) Gp->h_delta[i] = (long long)(ps[i]->D.slab - ps[0]->D.slab);
+    std::memset(Gp->h_mask, 0, sizeof(int) * np * kMaskCount);
+    std::memset(Gp->h_par, 0, sizeof(double) * np * kBatPar);
+    CK(cudaMemcpy(Gp->delta_d, Gp->h_delta, sizeof(long long) * np, cudaMemcpyHostToDevice));
+    out = Gp;
+    return HPG_OK;
+}
+
+// The group of these problems: reused while every problem keeps the device state it
+// had when the group was built (same allocation generation), else rebuilt.
+static hpg_status group_for(hpg_ctx* home, hpg_ctx* ctx, std::vector<Problem*>& ps, std::shared_ptr<Group>& out) {
+    std::vector<int> key;
+    for (Problem* P : ps) key.push_back(P->id);
+    std::lock_guard<std::mutex> lock(home->groups_mu);
+    auto it = home->groups.find(key);
+    if (it != home->groups.end()) {
+        bool same = true;
+        for (size_t i = 0; i < ps.size() && same; ++i)
+            same = it->second->ps[i] == ps[i] && it->second->gens[i] == ps[i]->alloc_gen;
+        if (same) {
+            out = it->second;
+            return HPG_OK;
+        }
+        home->groups.erase(it);
+    }
+    CKS(group_build(ctx, ps, out));
+    home->groups[key] = out;
+    return HPG_OK;
+}
+
+void drop_groups_with(hpg_ctx* ctx, int pid) {
+    std::lock_guard<std::mutex> lock(ctx->groups_mu);
+    for (auto it = ctx->groups.begin(); it != ctx->groups.end();) {
+        if (std::find(it->first.begin(), it->first.end(), pid) != it->first.end()) it = ctx->groups.erase(it);
+        else ++it;
+    }
+}
+
+static hpg_status group_upload(hpg_ctx* ctx, Group& Gp, bool masks, bool par) {
+    cudaStream_t s = ctx->stream;
+    if (masks)
+        CK(cudaMemcpyAsync(Gp.mask_d, Gp.h_mask, sizeof(int) * Gp.np * kMaskCount, cudaMemcpyHostToDevice, s));
+    if (par) CK(cudaMemcpyAsync(Gp.par_d, Gp.h_par, sizeof(double) * Gp.np * kBatPar, cudaMemcpyHostToDevice, s));
+    return HPG_OK;
+}
+
+// Read kStatD doubles at d and kStatI ints at iv of every problem (one copy, synchronises).
+static hpg_status group_gather(hpg_ctx* ctx, Group& Gp, const double* d, const int* iv) {
+    cudaStream_t s = ctx->stream;
+    CK(launch_gather_status(d, kStatD, iv, kStatI, Gp.stat_d, s, Gp.bat(-1)));
+    CK(cudaMemcpyAsync(Gp.h_stat, Gp.stat_d, sizeof(double) * Gp.np * (kStatD + kStatI), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return HPG_OK;
+}
+static double gd_(const Group& Gp, int i, int k) { return Gp.h_stat[i * kStatD + k]; }
+static int gi_(const Group& Gp, int i, int k) { return (int)Gp.h_stat[Gp.np * kStatD + i * kStatI + k]; }
+
+// `chunk` GMRES iterations of every problem of the group, enqueued without host
+// synchronisation (problems whose GMRES has stopped skip every launch).
+template <typename T, typename VT>
+static hpg_status group_gmres_chunk(hpg_ctx* ctx, Group& Gp, int chunk) {
+    Problem& P0 = *Gp.ps[0];
+    DevState& D = P0.D;
+    cudaStream_t s = ctx->stream;
+    GmresDev& G = D.gm;
+    const Geo<T>& g = PV<T>::g(D);
+    const IterCtl ctl{G.iflag, G.jdev, G.N};
+    const Bat all = Gp.bat(-1);
+    for (int c = 0; c < chunk; ++c) {
+        CK(launch_precond<T, VT, T>(g, PV<T>::Sinv(D), gmres_basis<VT>(G), PV<T>::zp(D), s, ctl, all));
+        CK(launch_bapply<T, T, T>(g, PV<T>::zp(D), PV<T>::tu(D), s, G.iflag, all));
+        CK(launch_fdm<T>(g, D.alpha_dev, 0.0, PV<T>::tu(D), PV<T>::tu2(D), PV<T>::w1(D), PV<T>::w2(D), s, G.iflag,
+                         all));
+        CK(launch_schur_rest<T, VT>(g, PV<T>::gw(D), P0.params.beta, PV<T>::zp(D), PV<T>::tu2(D),
+                                    gmres_basis<VT>(G), s, ctl, all));
+        CK(gmres_arnoldi<VT>(G, s, all));
+    }
+    return HPG_OK;
+}
+
+template <typename T, typename VT>
+static bool group_build_loop(hpg_ctx* ctx, Group& Gp, cudaGraphExec_t* exec, long long* kernels_per_body) {
+    DevState& D = Gp.ps[0]->D;
+    cudaStream_t s = ctx->stream;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return false;
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return false;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return false;
+    }
+    const long long before = kernel_launch_count();
+    hpg_status st = group_gmres_chunk<T, VT>(ctx, Gp, kGraphChunk);
+    if (st == HPG_OK && launch_gm_setcond_batch(h, D.gm.iflag, s, Gp.bat(-1)) != cudaSuccess) st = HPG_ERR_CUDA;
+    *kernels_per_body = kernel_launch_count() - before;
+    add_kernel_launches(-*kernels_per_body);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &captured);
+    bool ok = st == HPG_OK && ce == cudaSuccess && cudaGraphInstantiate(exec, g, 0) == cudaSuccess;
+    cudaGraphDestroy(g);
+    if (!ok) cudaGetLastError();
+    return ok;
+}
+
+// GMRES of the problems in mask slot kMaskSolve (the others' stop flags are set from
+// slot kMaskIdle) to their stop flags: one launch of the group's device-side loop.
+// its[i], capped[i] per problem.
+template <typename T, typename VT>
+static hpg_status group_gmres_run(hpg_ctx* ctx, Group& Gp, std::vector<int>& its, std::vector<char>& capped) {
+    DevState& D = Gp.ps[0]->D;
+    cudaStream_t s = ctx->stream;
+    GmresDev& G = D.gm;
+    const int pi = sizeof(T) == sizeof(float) ? (sizeof(VT) == sizeof(float) ? 2 : 1) : 0;
+    CK(launch_gm_stop(G.iflag, s, Gp.bat(kMaskIdle)));
+    if (!Gp.loop[pi] && !Gp.loop_failed[pi]) {
+        long long nk = 0;
+        if (!group_build_loop<T, VT>(ctx, Gp, &Gp.loop[pi], &nk)) {
+            Gp.loop[pi] = nullptr;
+            Gp.loop_failed[pi] = true;
+        } else {
+            Gp.loop_kernels[pi] = nk;
+        }
+    }
+    if (Gp.loop[pi]) {
+        CK(cudaGraphLaunch(Gp.loop[pi], s));
+        CKS(group_gather(ctx, Gp, G.scal, G.iflag));
+        int maxits = 0;
+        for (int i = 0; i < Gp.np; ++i) maxits = std::max(maxits, gi_(Gp, i, 1));
+        add_kernel_launches(Gp.loop_kernels[pi] * ((maxits + kGraphChunk - 1) / kGraphChunk + 1));
+    } else {
+        for (int guard = 0; guard <= G.kmax; ++guard) {
+            CKS(group_gmres_chunk<T, VT>(ctx, Gp, 1));
+            CKS(group_gather(ctx, Gp, G.scal, G.iflag));
+            bool all = true;
+            for (int i = 0; i < Gp.np && all; ++i) all = gi_(Gp, i, 0) != 0;
+            if (all) break;
+        }
+    }
+    for (int i = 0; i < Gp.np; ++i) {
+        its[i] = gi_(Gp, i, 1);
+        // the cap flag is also set when the last allowed iteration converged: check the residual
+        capped[i] = gi_(Gp, i, 3) != 0 && gi_(Gp, i, 0) != 0 && gi_(Gp, i, 2) == 0 && gd_(Gp, i, 1) > gd_(Gp, i, 2);
+    }
+    return HPG_OK;
+}
+
+// eq. (schur2) for the problems of mask slot kMaskSolve: y = b_psi - B^T A^{-1} b_u,
+// GMRES on S, delta_u = A^{-1}(b_u - B delta_psi); b = D.r, result in D.dcorr,
+// relative tolerance per problem in Bat::par (kParRtol).
+template <typename T, typename VT>
+static hpg_status group_schur_solve(hpg_ctx* ctx, Group& Gp, std::vector<int>& its, std::vector<char>& capped) {
+    Problem& P0 = *Gp.ps[0];
+    DevState& D = P0.D;
+    cudaStream_t s = ctx->stream;
+    const Geo<T>& g = PV<T>::g(D);
+    const long long Nu0 = (long long)P0.H.Nu0, Npsi = (long long)P0.H.Npsi;
+    GmresDev& G = D.gm;
+    const Bat b = Gp.bat(kMaskSolve);
+    T* tu = PV<T>::tu(D);
+    T* tu2 = PV<T>::tu2(D);
+    T* zp = PV<T>::zp(D);
+    const double* bu = D.r;
+    const double* bp = D.r + Nu0;
+    double* du = D.dcorr;
+    double* dp = D.dcorr + Nu0;
+    if constexpr (sizeof(T) == sizeof(double)) CK(launch_copy<double>(bu, tu, Nu0, s, b));
+    else CK(launch_convert<double, float>(bu, tu, Nu0, s, b));
+    CK(launch_fdm<T>(g, D.alpha_dev, 0.0, tu, tu2, PV<T>::w1(D), PV<T>::w2(D), s, nullptr, b));
+    CK(launch_btapply<T, T, T>(g, tu2, zp, s, b));
+    CK(launch_sub_scaled<T>(bp, 1.0, zp, D.yp, Npsi, s, b));
+    CK(gmres_start<VT>(G, D.yp, 0.0, s, 0, b));
+    CKS(group_gmres_run<T, VT>(ctx, Gp, its, capped));
+    CK(gmres_finish<VT>(G, D.xs, s, b));
+    CK(launch_precond<T, double, double>(g, PV<T>::Sinv(D), D.xs, dp, s, IterCtl{}, b));
+    CK(launch_bapply<T, double, T>(g, dp, tu, s, nullptr, b));
+    CK(launch_sub_scaled<T>(bu, 1.0, tu, D.tu_d, Nu0, s, b));
+    if constexpr (sizeof(T) == sizeof(float)) CK(launch_convert<double, float>(D.tu_d, tu, Nu0, s, b));
+    CK(launch_fdm<T>(g, D.alpha_dev, 0.0, tu, tu2, PV<T>::w1(D), PV<T>::w2(D), s, nullptr, b));
+    if constexpr (sizeof(T) == sizeof(double)) CK(launch_copy<double>(tu2, du, Nu0, s, b));
+    else CK(launch_convert<float, double>(tu2, du, Nu0, s, b));
+    return HPG_OK;
+}
+
+template <typename T>
+static hpg_status group_schur_solve_T(hpg_ctx* ctx, Group& Gp, std::vector<int>& its, std::vector<char>& capped) {
+    if constexpr (sizeof(T) == sizeof(float))
+        if (Gp.ps[0]->params.krylov_f32) return group_schur_solve<T, float>(ctx, Gp, its, capped);
+    return group_schur_solve<T, double>(ctx, Gp, its, capped);
+}
+
+// Newton systems of the problems in mask slot kMaskNewton: the refinement loop of
+// linear_solve, problem by problem in its decisions, batched in its launches.
+static hpg_status group_linear_solve(hpg_ctx* ctx, Group& Gp, const std::vector<char>& inN,
+                                     const std::vector<double>& normF, const std::vector<double>& eta) {
+    Problem& P0 = *Gp.ps[0];
+    DevState& D = P0.D;
+    cudaStream_t s = ctx->stream;
+    const int np = Gp.np;
+    const long long Nu0 = (long long)P0.H.Nu0, Npsi = (long long)P0.H.Npsi, Nx = Nu0 + Npsi;
+    const bool f64 = P0.params.precision == HPG_FP64;
+    const Bat bN = Gp.bat(kMaskNewton);
+    CK(launch_copy<double>(nullptr, D.delta, Nx, s, bN));
+    CK(launch_copy<double>(D.F, D.r, Nx, s, bN));
+    std::vector<double> rnorm(normF);
+    std::vector<char> on(inN);
+    std::vector<int> its(np, 0);
+    std::vector<char> capped(np, 0);
+    for (int sw = 0; sw < std::max(1, P0.params.refine_max); ++sw) {
+        bool any = false;
+        for (int i = 0; i < np; ++i) {
+            Gp.mask(kMaskSolve)[i] = on[i];
+            Gp.mask(kMaskIdle)[i] = !on[i];
+            any = any || on[i];
+            if (!on[i]) continue;
+            const double need = eta[i] * normF[i] / std::max(rnorm[i], 1e-300);
+            Gp.h_par[i * kBatPar + kParRtol] =
+                f64 ? std::min(1.0, need) : std::min(1.0, std::max(kInnerMargin * need, 1e-6));
+        }
+        if (!any) break;
+        CKS(group_upload(ctx, Gp, true, true));
+        if (f64) CKS(group_schur_solve_T<double>(ctx, Gp, its, capped));
+        else CKS(group_schur_solve_T<float>(ctx, Gp, its, capped));
+        bool more = false;
+        for (int i = 0; i < np; ++i) {
+            if (!on[i]) continue;
+            hpg_stats& st = Gp.ps[i]->stats;
+            st.krylov_total += its[i];
+            st.refine_total += 1;
+            st.ainv_total += 2 + its[i];
+            if (capped[i]) st.krylov_cap_hits++;
+        }
+        CK(launch_axpby(1.0, D.dcorr, 1.0, D.delta, Nx, s, Gp.bat(kMaskSolve)));
+        for (int i = 0; i < np; ++i) {
+            if (on[i] && f64 && !capped[i]) on[i] = 0;     // the FP64 GMRES residual is the true one
+            Gp.mask(kMaskPrev)[i] = on[i];
+            more = more || on[i];
+        }
+        if (!more) break;
+        CKS(group_upload(ctx, Gp, true, false));
+        const Bat bR = Gp.bat(kMaskPrev);
+        CK(launch_newton_apply(D.gd, D.gw, 0.0, P0.params.beta, D.delta, D.r, s, bR));
+        CK(launch_axpby(1.0, D.F, -1.0, D.r, Nx, s, bR));
+        int nparts = 0;
+        CK(launch_sumsq(D.r, Nx, D.part, &nparts, s, bR));
+        CK(launch_reduce_sum(D.part, nparts, D.scal + 1, s, bR));
+        CKS(group_gather(ctx, Gp, D.scal, D.flag));
+        for (int i = 0; i < np; ++i) {
+            if (!on[i]) continue;
+            rnorm[i] = std::sqrt(gd_(Gp, i, 1));
+            if (rnorm[i] <= eta[i] * normF[i]) on[i] = 0;
+        }
+    }
+    return HPG_OK;
+}
+
+// Evaluation + residual + norm of the state at `x` (the current or the trial state)
+// for the problems of mask slot `slot`; alpha from Bat::par.  Synchronises; the
+// squared norms and flags are in the group's gathered status.
+static hpg_status group_residual(hpg_ctx* ctx, Group& Gp, int slot, bool trial) {
+    Problem& P0 = *Gp.ps[0];
+    DevState& D = P0.D;
+    cudaStream_t s = ctx->stream;
+    const long long Nu0 = (long long)P0.H.Nu0;
+    const Bat b = Gp.bat(slot);
+    const double* x = trial ? D.xt : D.x;
+    double* gw = trial ? D.gwt : D.gw;
+    double* eg = trial ? D.egt : D.eg;
+    double* F = trial ? D.Ft : D.F;
+    CK(launch_eval(D.gd, x + Nu0, D.phiq, gw, nullptr, eg, D.flag, s, b));
+    CK(launch_residual(D.gd, x, x + Nu0, D.psi_prev, eg, D.rA, D.rB, D.bf, D.phiz, 0.0, F, D.part, s, b));
+    CK(launch_reduce_sum(D.part, n_res_partials(D.gd), D.scal, s, b));
+    return group_gather(ctx, Gp, D.scal, D.flag);
+}
+
+// The proximal loop of solve_problem for every problem of the group at once, on
+// ctx's stream; `home` owns the cache of groups (the caller's context).
+hpg_status solve_group(hpg_ctx* home, hpg_ctx* ctx, std::vector<Problem*>& ps, std::vector<std::string>* errs) {
+    auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = kernel_launch_count();
+    const int np = (int)ps.size();
+    for (Problem* P : ps) {
+        CKS(alloc_device(ctx, *P));
+        // every problem of a group keeps its current state in the first buffer of each pair
+        if (P->D.x > P->D.xt) swap_state(P->D);
+    }
+    std::shared_ptr<Group> gref;
+    CKS(group_for(home, ctx, ps, gref));
+    Group& Gp = *gref;
+    Problem& P0 = *ps[0];
+    DevState& D = P0.D;
+    cudaStream_t s = ctx->stream;
+    const long long Nu0 = (long long)P0.H.Nu0, Npsi = (long long)P0.H.Npsi, Nx = Nu0 + Npsi;
+    const long long gsz = (long long)(P0.H.Nq * gauss_stride(P0.H.kind, P0.H.d));
+    for (Problem* P : ps) {
+        P->stats = hpg_stats{};
+        P->stats.n_u = Nu0;
+        P->stats.n_psi = Npsi;
+        P->timer.on = false;
+    }
+    const Bat all = Gp.bat(-1);
+    CK(launch_copy<double>(nullptr, D.x, Nx, s, all));
+    CK(launch_copy<double>(nullptr, D.psi_prev, Npsi, s, all));
+    CK(launch_copy<int>(nullptr, D.flag, 4, s, all));
+    // per-problem host state
+    std::vector<int> k(np, 0), it(np, 0), flag(np, 0), status(np, HPG_OK);
+    std::vector<char> done(np, 0), start(np, 1);
+    std::vector<double> normF(np, 0.0), eta(np, 0.0), lam(np, 1.0), nFt(np, 0.0);
+    std::vector<int> tflag(np, 0), nsteps(np);
+    std::vector<std::string> msg(np);
+    for (int i = 0; i < np; ++i) nsteps[i] = (int)std::min<size_t>(ps[i]->H.alphas.size(), HPG_MAX_ALPHA);
+    auto finish_step = [&](int i) {
+        hpg_stats& st = ps[i]->stats;
+        st.newton_per_step[k[i]] = it[i];
+        st.newton_total += it[i];
+        st.alpha_steps = k[i] + 1;
+    };
+    while (true) {
+        // ---- subproblem starts: alpha_k, psi_{k-1} <- psi, residual at the warm start
+        bool anyS = false, anyPrev = false;
+        for (int i = 0; i < np; ++i) {
+            const bool st_ = !done[i] && start[i];
+            Gp.mask(kMaskStart)[i] = st_;
+            Gp.mask(kMaskPrev)[i] = st_ && k[i] > 0;
+            anyS = anyS || st_;
+            anyPrev = anyPrev || (st_ && k[i] > 0);
+            if (st_) Gp.h_par[i * kBatPar + kParAlpha] = ps[i]->H.alphas[k[i]];
+        }
+        if (anyS) {
+            CKS(group_upload(ctx, Gp, true, true));
+            CK(launch_scatter_par(D.alpha_dev, kParAlpha, s, Gp.bat(kMaskStart)));
+            if (anyPrev) CK(launch_copy<double>(D.x + Nu0, D.psi_prev, Npsi, s, Gp.bat(kMaskPrev)));
+            CKS(group_residual(ctx, Gp, kMaskStart, false));
+            for (int i = 0; i < np; ++i) {
+                if (!Gp.mask(kMaskStart)[i]) continue;
+                normF[i] = std::sqrt(gd_(Gp, i, 0));
+                flag[i] = gi_(Gp, i, 0);
+                if (!std::isfinite(normF[i])) flag[i] |= 1;
+                start[i] = 0;
+            }
+        }
+        // ---- per-problem decisions
+        bool anyN = false, live = false;
+        for (int i = 0; i < np; ++i) {
+            Gp.mask(kMaskNewton)[i] = 0;
+            if (done[i] || start[i]) {
+                live = live || !done[i];
+                continue;
+            }
+            const hpg_params& q = ps[i]->params;
+            if (flag[i] & 1) {
+                status[i] = HPG_ERR_NONFINITE;
+            } else if (!std::isfinite(normF[i])) {
+                status[i] = HPG_ERR_NONFINITE;
+                msg[i] = "non-finite Newton residual in proximal step " + std::to_string(k[i] + 1);
+            } else if (normF[i] <= q.newton_tol) {
+                finish_step(i);
+                ++k[i];
+                it[i] = 0;
+                if (k[i] >= nsteps[i]) done[i] = 1;
+                else start[i] = 1;
+                live = live || !done[i];
+                continue;
+            } else if (it[i] >= q.newton_max) {
+                status[i] = HPG_ERR_NEWTON_CAP;
+                msg[i] = "Newton cap reached in proximal step " + std::to_string(k[i] + 1) + " (||F|| = " +
+                         std::to_string(normF[i]) + ")";
+            } else {
+                Gp.mask(kMaskNewton)[i] = 1;
+                eta[i] = std::min(q.krylov_rtol, std::max(normF[i], 1e-12));
+                anyN = true;
+                live = true;
+                continue;
+            }
+            finish_step(i);
+            done[i] = 1;
+        }
+        if (!live) break;
+        if (!anyN) continue;
+        // ---- one Newton step of every problem in the Newton mask
+        CKS(group_upload(ctx, Gp, true, false));
+        const Bat bN = Gp.bat(kMaskNewton);
+        CK(launch_copy<double>(D.gw, D.gwl, gsz, s, bN));
+        if (P0.params.precision == HPG_FP64) {
+            CK(launch_factor<double>(D.gd, D.gwl, 1.0, P0.params.beta, D.Sinv_d, nullptr, D.flag, D.fwork_d, s, bN));
+        } else {
+            CK(launch_convert<double, float>(D.gwl, D.gwf, gsz, s, bN));
+            CK(launch_factor<float>(D.gf, D.gwf, 1.0, P0.params.beta, D.Sinv_f, nullptr, D.flag, D.fwork_f, s, bN));
+        }
+        std::vector<char> inN(np);
+        for (int i = 0; i < np; ++i) inN[i] = (char)Gp.mask(kMaskNewton)[i];
+        CKS(group_linear_solve(ctx, Gp, inN, normF, eta));
+        // backtracking on ||F||, each problem with its own step length
+        std::vector<char> ls(inN);
+        for (int i = 0; i < np; ++i) lam[i] = 1.0;
+        for (int h = 0; h <= P0.params.ls_max; ++h) {
+            bool any = false;
+            for (int i = 0; i < np; ++i) {
+                Gp.mask(kMaskTrial)[i] = ls[i];
+                any = any || ls[i];
+                if (ls[i]) Gp.h_par[i * kBatPar + kParLam] = lam[i];
+            }
+            if (!any) break;
+            CKS(group_upload(ctx, Gp, true, true));
+            const Bat bL = Gp.bat(kMaskTrial);
+            CK(launch_trial(D.x, D.delta, 1.0, D.xt, Nx, s, bL));
+            CK(launch_copy<int>(nullptr, D.flag, 1, s, bL));
+            CKS(group_residual(ctx, Gp, kMaskTrial, true));
+            for (int i = 0; i < np; ++i) {
+                if (!ls[i]) continue;
+                nFt[i] = std::sqrt(gd_(Gp, i, 0));
+                tflag[i] = gi_(Gp, i, 0);
+                if (!std::isfinite(nFt[i])) tflag[i] |= 1;
+                if (!(tflag[i] & 1) && nFt[i] <= (1.0 - 1e-4 * lam[i]) * normF[i]) {
+                    ls[i] = 0;
+                } else if (h == ps[i]->params.ls_max) {
+                    ps[i]->stats.ls_fail++;
+                    ls[i] = 0;
+                } else {
+                    lam[i] *= 0.5;
+                }
+            }
+        }
+        // factorisation flag (non-SPD block): bit 1 of flag[1]
+        CKS(group_gather(ctx, Gp, D.scal, D.flag));
+        bool anyAcc = false;
+        for (int i = 0; i < np; ++i) {
+            Gp.mask(kMaskTrial)[i] = 0;
+            if (!inN[i]) continue;
+            if (gi_(Gp, i, 1) & 2) {
+                status[i] = HPG_ERR_NOT_SPD;
+                finish_step(i);
+                done[i] = 1;
+                continue;
+            }
+            Gp.mask(kMaskTrial)[i] = 1;
+            anyAcc = true;
+            normF[i] = nFt[i];
+            flag[i] = tflag[i];
+            ++it[i];
+        }
+        if (anyAcc) {
+            // accept: the trial state becomes the current one
+            CKS(group_upload(ctx, Gp, true, false));
+            const Bat bA = Gp.bat(kMaskTrial);
+            CK(launch_copy<double>(D.xt, D.x, Nx, s, bA));
+            CK(launch_copy<double>(D.gwt, D.gw, gsz, s, bA));
+            CK(launch_copy<double>(D.egt, D.eg, Npsi, s, bA));
+            CK(launch_copy<double>(D.Ft, D.F, Nx, s, bA));
+        }
+    }
+    CK(cudaStreamSynchronize(s));
+    const long long launches = kernel_launch_count() - launches0;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    hpg_status first = HPG_OK;
+    for (int i = 0; i < np; ++i) {
+        hpg_stats& st = ps[i]->stats;
+        st.final_residual = normF[i];
+        st.status = status[i];
+        st.kernel_launches = launches / np + (i < launches % np ? 1 : 0);   // the group's launches, shared out
+        st.fdm_tile_f32 = ps[i]->D.gf.gemm_cfg;
+        st.fdm_tile_f64 = ps[i]->D.gd.gemm_cfg;
+        st.h2d_bytes = ps[i]->h2d_bytes;
+        st.solve_ms = ms;
+        ps[i]->solved = true;
+        if (errs) (*errs)[i] = msg[i];
+        if (status[i] != HPG_OK && first == HPG_OK) {
+            first = (hpg_status)status[i];
+            ctx->err = msg[i].empty() ? std::string(hpg_status_str(first)) : msg[i];
+        }
+    }
+    return first;
+}
+
 // Several independent solves in flight at once: up to ctx->concurrency host
 // workers, each driving its own CUDA stream (forked from and joined back to the
 // context's stream), pull problems from a shared queue.  Kernels of different
@@ -1110,7 +1734,28 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
 // order is exactly that of hpg_solve, so results do not depend on the mix.
 hpg_status solve_batch(hpg_ctx* ctx, std::vector<Problem*>& probs) {
     const int n = (int)probs.size();
-    const int W = std::max(1, std::min(ctx->concurrency, n));
+    // units of work: lockstep groups of same-shape problems (at most kGroupMax each), and
+    // single problems that cannot share launches
+    constexpr int kGroupMax = 64;
+    std::vector<std::vector<int>> units;
+    {
+        std::map<std::string, std::vector<int>> by_key;
+        std::vector<std::string> order;
+        for (int i = 0; i < n; ++i) {
+            if (!groupable(*probs[i])) { units.push_back({i}); continue; }
+            const std::string key = group_key(*probs[i]);
+            auto& v = by_key[key];
+            if (v.empty()) order.push_back(key);
+            v.push_back(i);
+        }
+        for (const auto& key : order) {
+            const auto& v = by_key[key];
+            for (size_t a = 0; a < v.size(); a += kGroupMax)
+                units.emplace_back(v.begin() + a, v.begin() + std::min(v.size(), a + kGroupMax));
+        }
+    }
+    const int nu = (int)units.size();
+    const int W = std::max(1, std::min(ctx->concurrency, nu));
     while ((int)ctx->side_streams.size() < W) {
         cudaStream_t st;
         cudaEvent_t ev;
@@ -1129,9 +1774,26 @@ hpg_status solve_batch(hpg_ctx* ctx, std::vector<Problem*>& probs) {
         hpg_ctx local;
         local.device = ctx->device;
         local.stream = ctx->side_streams[w];
-        for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
-            status[i] = solve_problem(&local, *probs[i]);
-            if (status[i] != HPG_OK) errs[i] = local.err;
+        for (int u = next.fetch_add(1); u < nu; u = next.fetch_add(1)) {
+            const std::vector<int>& idx = units[u];
+            if (idx.size() == 1) {
+                status[idx[0]] = solve_problem(&local, *probs[idx[0]]);
+                if (status[idx[0]] != HPG_OK) errs[idx[0]] = local.err;
+                continue;
+            }
+            std::vector<Problem*> ps;
+            for (int i : idx) ps.push_back(probs[i]);
+            std::vector<std::string> e(ps.size());
+            // the group cache belongs to the caller's context
+            const hpg_status gs = solve_group(ctx, &local, ps, &e);
+            // a failure of the solver itself is per problem (in its stats); any other stops the group
+            const bool per_problem = gs == HPG_OK || gs == HPG_ERR_NEWTON_CAP || gs == HPG_ERR_KRYLOV_CAP ||
+                                     gs == HPG_ERR_NONFINITE || gs == HPG_ERR_NOT_SPD;
+            for (size_t j = 0; j < idx.size(); ++j) {
+                status[idx[j]] = per_problem ? (hpg_status)ps[j]->stats.status : gs;
+                if (!per_problem) errs[idx[j]] = local.err;
+                else if (status[idx[j]] != HPG_OK) errs[idx[j]] = e[j].empty() ? hpg_status_str(status[idx[j]]) : e[j];
+            }
         }
     };
     std::vector<std::thread> threads;
@@ -1233,7 +1895,7 @@ hpg_status op_factor(hpg_ctx* ctx, Problem& P, int precision, double* blocks) {
     }
     if (dump) cudaFree(dump);
     int flag = 0;
-    cudaMemcpy(&flag, D.flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&flag, D.flag + 1, sizeof(int), cudaMemcpyDeviceToHost);
     if (st == HPG_OK && (flag & 2)) st = HPG_ERR_NOT_SPD;
     return st;
 }

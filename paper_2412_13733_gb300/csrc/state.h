@@ -4,6 +4,7 @@
 #include <atomic>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -74,10 +75,14 @@ struct DevState {
     // pinned host mirror for scalars (owned by the Problem, kept across re-allocation)
     double* h_scal = nullptr;
     int* h_iflag = nullptr;
+    char* slab = nullptr;                  // one allocation holding every per-problem buffer (layout fixed
+    size_t slab_bytes = 0;                 // by the problem's shape), see alloc_device
     cudaStream_t alloc_stream = nullptr;   // stream the stream-ordered allocations were made on
     std::vector<void*> allocs;
     size_t bytes = 0;
 };
+
+struct Group;
 
 struct KernelTimer {
     bool on = false;
@@ -97,6 +102,7 @@ struct Problem {
     HostProblem H;
     hpg_params params{};
     bool alloc_done = false;
+    long long alloc_gen = 0;     // changes whenever the device state is (re)allocated
     bool dirichlet_set = false;
     bool data_dirty = true;      // f load / lifting terms changed since the last upload
     bool phi_dirty = true;       // constraint values changed since the last upload
@@ -124,6 +130,9 @@ struct hpg_ctx {
     std::vector<cudaStream_t> side_streams;    // owned; forked from / joined to `stream`
     std::vector<cudaEvent_t> side_events;
     hpg::Server* server = nullptr;             // request loop (hpg_server_start)
+    // lockstep groups of hpg_solve_batch, by problem ids (their launch tables and loop graphs)
+    std::map<std::vector<int>, std::shared_ptr<hpg::Group>> groups;
+    std::mutex groups_mu;
 };
 
 namespace hpg {
@@ -137,6 +146,11 @@ void drop_graphs(Problem& P);
 hpg_status upload_data(hpg_ctx* ctx, Problem& P);
 hpg_status solve_problem(hpg_ctx* ctx, Problem& P);
 hpg_status solve_batch(hpg_ctx* ctx, std::vector<Problem*>& probs);
+// Same-shape problems in lockstep (every launch serves all of them); `home` owns the
+// group cache, ctx gives the stream.  Per-problem status in each problem's stats.
+hpg_status solve_group(hpg_ctx* home, hpg_ctx* ctx, std::vector<Problem*>& ps, std::vector<std::string>* errs);
+// Forget the cached groups that contain problem pid.
+void drop_groups_with(hpg_ctx* ctx, int pid);
 // component operators
 hpg_status op_set_state(hpg_ctx* ctx, Problem& P, const double* u_full, const double* psi, const double* psi_prev,
                         double alpha);

@@ -120,13 +120,14 @@ def test_component_calls_refuse_a_problem_in_the_loop():
     w = case("radial_3x3_p5")
     slow = hpg.from_workload(ctx, w)
     slow.solve()                                # device state exists before submission
-    slow.set_alphas(w["alphas"] * 6)
-    ctx.server_start(workers=1)
-    t = ctx.submit(slow)
     torch = pytest.importorskip("torch")
     x = np.zeros(slow.n_u)
     xd = torch.zeros(slow.n_u, dtype=torch.float64, device="cuda")
     yd = torch.zeros_like(xd)
+    torch.cuda.synchronize()
+    slow.set_alphas(w["alphas"] * 12)          # a request that outlives the calls below (120 steps)
+    ctx.server_start(workers=1)
+    t = ctx.submit(slow)
     calls = [lambda: slow.apply_stiffness_inv(x, hpg.HPG_FP64), lambda: slow.residual(),
              lambda: slow.factor_precond(hpg.HPG_FP64)]
     for call in calls:
