@@ -1167,8 +1167,11 @@ struct Group {
     double* par_d = nullptr;     // np x kBatPar
     double* stat_d = nullptr;    // np x (kStatD + kStatI)
     long long* h_delta = nullptr;
-    int* h_mask = nullptr;
-    double* h_par = nullptr;
+    // masks and per-problem scalars are staged in pageable host memory on purpose: an
+    // asynchronous copy from pageable memory takes its snapshot before it returns, so
+    // the host may change them for the next phase while earlier copies are queued
+    std::vector<int> h_mask;
+    std::vector<double> h_par;
     double* h_stat = nullptr;
     cudaGraphExec_t loop[3] = {nullptr, nullptr, nullptr};
     long long loop_kernels[3] = {0, 0, 0};
@@ -1181,8 +1184,6 @@ struct Group {
         if (par_d) cudaFree(par_d);
         if (stat_d) cudaFree(stat_d);
         if (h_delta) cudaFreeHost(h_delta);
-        if (h_mask) cudaFreeHost(h_mask);
-        if (h_par) cudaFreeHost(h_par);
         if (h_stat) cudaFreeHost(h_stat);
     }
     Bat bat(int slot) const {
@@ -1193,7 +1194,7 @@ struct Group {
         b.np = np;
         return b;
     }
-    int* mask(int slot) { return h_mask + (size_t)slot * np; }
+    int* mask(int slot) { return h_mask.data() + (size_t)slot * np; }
 };
 
 // Problems that may share a group: same shape (so the same operator constants and
@@ -1233,15 +1234,13 @@ static hpg_status group_build(hpg_ctx* ctx, std::vector<Problem*>& ps, std::shar
         cudaMalloc(&Gp->par_d, sizeof(double) * np * kBatPar) != cudaSuccess ||
         cudaMalloc(&Gp->stat_d, sizeof(double) * np * (kStatD + kStatI)) != cudaSuccess ||
         cudaMallocHost(&Gp->h_delta, sizeof(long long) * np) != cudaSuccess ||
-        cudaMallocHost(&Gp->h_mask, sizeof(int) * np * kMaskCount) != cudaSuccess ||
-        cudaMallocHost(&Gp->h_par, sizeof(double) * np * kBatPar) != cudaSuccess ||
         cudaMallocHost(&Gp->h_stat, sizeof(double) * np * (kStatD + kStatI)) != cudaSuccess) {
         ctx->err = "group allocation failed";
         return HPG_ERR_OOM;
     }
     for (int i = 0; i < np; ++i) Gp->h_delta[i] = (long long)(ps[i]->D.slab - ps[0]->D.slab);
-    std::memset(Gp->h_mask, 0, sizeof(int) * np * kMaskCount);
-    std::memset(Gp->h_par, 0, sizeof(double) * np * kBatPar);
+    Gp->h_mask.assign((size_t)np * kMaskCount, 0);
+    Gp->h_par.assign((size_t)np * kBatPar, 0.0);
     CK(cudaMemcpy(Gp->delta_d, Gp->h_delta, sizeof(long long) * np, cudaMemcpyHostToDevice));
     out = Gp;
     return HPG_OK;
@@ -1280,8 +1279,9 @@ void drop_groups_with(hpg_ctx* ctx, int pid) {
 static hpg_status group_upload(hpg_ctx* ctx, Group& Gp, bool masks, bool par) {
     cudaStream_t s = ctx->stream;
     if (masks)
-        CK(cudaMemcpyAsync(Gp.mask_d, Gp.h_mask, sizeof(int) * Gp.np * kMaskCount, cudaMemcpyHostToDevice, s));
-    if (par) CK(cudaMemcpyAsync(Gp.par_d, Gp.h_par, sizeof(double) * Gp.np * kBatPar, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(Gp.mask_d, Gp.h_mask.data(), sizeof(int) * Gp.np * kMaskCount, cudaMemcpyHostToDevice, s));
+    if (par)
+        CK(cudaMemcpyAsync(Gp.par_d, Gp.h_par.data(), sizeof(double) * Gp.np * kBatPar, cudaMemcpyHostToDevice, s));
     return HPG_OK;
 }
 
