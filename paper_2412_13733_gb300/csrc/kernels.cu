@@ -615,14 +615,17 @@ cudaError_t launch_reduce_sum(const double* part, int count, double* out, cudaSt
 // Assemble -S-hat_K = D_K + beta M_K + C/alpha (obstacle) or D_K + beta K_K (gradient)
 // by sum factorisation over the Gauss points, factor it (Cholesky, L L^T), invert
 // L (X = L^{-1}, kept transposed in the upper triangle), and write (-S-hat_K)^{-1} = X^T X.
-template <typename T>
+// The thread group is the whole block (WARP false: lt = threadIdx.x, nthr = blockDim.x,
+// block barriers) or one warp (WARP true: lt = lane, nthr = 32, warp barriers).
+template <typename T, bool WARP = false>
 __device__ void assemble_D_block(const Geo<T>& g, const T* __restrict__ gw, long long cell, int gs, int ge,
-                                 const T* Vq, T* bufA, T* bufB) {
+                                 const T* Vq, T* bufA, T* bufB, int lt = -1, int nthr = 0) {
+    if (lt < 0) { lt = threadIdx.x; nthr = blockDim.x; }
     // stage 0: X0[q] = gw[q]; stage s contracts q_{d-s-1}; final X_d = D (nloc x nloc) in bufA
     const int n = g.n, d = g.d, nloc = (int)g.nloc;
     T* cur = ((d % 2) == 0) ? bufA : bufB;
-    for (int q = threadIdx.x; q < nloc; q += blockDim.x) cur[q] = gw[(cell * nloc + q) * gs + ge];
-    __syncthreads();
+    for (int q = lt; q < nloc; q += nthr) cur[q] = gw[(cell * nloc + q) * gs + ge];
+    if (WARP) __syncwarp(); else __syncthreads();
     int nq_out = nloc;      // n^{d-s}
     int ns = 1;             // n^s
     for (int st = 0; st < d; ++st) {
@@ -630,7 +633,7 @@ __device__ void assemble_D_block(const Geo<T>& g, const T* __restrict__ gw, long
         const int nq_new = nq_out / n;          // n^{d-s-1}
         const int ns_new = ns * n;
         const int total = nq_new * ns_new * ns_new;
-        for (int o = threadIdx.x; o < total; o += blockDim.x) {
+        for (int o = lt; o < total; o += nthr) {
             const int J = o % ns_new;
             const int rest = o / ns_new;
             const int I = rest % ns_new;
@@ -644,7 +647,7 @@ __device__ void assemble_D_block(const Geo<T>& g, const T* __restrict__ gw, long
             }
             nxt[o] = s;
         }
-        __syncthreads();
+        if (WARP) __syncwarp(); else __syncthreads();
         cur = nxt;
         nq_out = nq_new;
         ns = ns_new;
@@ -765,6 +768,105 @@ __global__ void k_factor(Geo<T> g, const T* __restrict__ gw, T alpha_inv, T beta
     }
 }
 
+// ---- one warp per cell (blocks of at most kFactorWarpMaxNb) ----------------------
+// The block kernel above runs one cell per 256-thread block and spends its time in
+// block barriers (two per Cholesky column) and in a triangular inverse with one busy
+// thread per column.  Here each warp owns one cell: it assembles -S-hat_K in shared
+// memory (the same sum factorisation) and inverts it in place by Gauss-Jordan
+// elimination without pivoting -- the block is SPD, so every pivot is positive; a
+// non-positive one is flagged as for the Cholesky.  Lane l owns columns l, l + 32 and
+// l + 64 of the block; step k first copies column k (the elimination multipliers) to a
+// per-warp buffer, so the lanes only ever write their own columns and synchronise with
+// __syncwarp.  Work per cell: nb^3 multiply-adds, all 32 lanes busy at every step.
+constexpr int kFactorWarpMaxNb = 96;
+
+__host__ __device__ inline size_t factor_warp_elems(int n, int d, int nb, int nc) {
+    size_t nloc = 1, nbuf_b = 1;
+    for (int t = 0; t < d; ++t) nloc *= n;
+    for (int t = 0; t < 2 * d - 1; ++t) nbuf_b *= n;
+    // A (nb^2) | bufA (nloc^2, gradient only) | bufB (n^{2d-1}) | Vq (n^2) | column k (nb)
+    return (size_t)nb * nb + (nc > 1 ? nloc * nloc : 0) + nbuf_b + (size_t)n * n + nb;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_factor_warp(Geo<T> g, const T* __restrict__ gw, T alpha_inv, T beta, T* __restrict__ Sinv,
+                  double* __restrict__ dump, int* __restrict__ flag, int wpb, Bat bt) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    long long off;
+    const int pb = (int)blockIdx.y;
+    if (!bat_enter(bt, pb, &off)) return;
+    gw = bsh(gw, off); Sinv = bsh(Sinv, off); dump = bsh(dump, off); flag = bsh(flag, off);
+    if (bt.par) alpha_inv = (T)(1.0 / bt.par[pb * kBatPar + kParAlpha]);
+    const int n = g.n, nloc = (int)g.nloc, nb = (int)g.nb, nc = g.ncomp;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long cell = (long long)blockIdx.x * wpb + warp;
+    if (cell >= g.Nc) return;                    // whole warps only; no block barrier below
+    const size_t per = factor_warp_elems(n, g.d, nb, nc);
+    T* A = reinterpret_cast<T*>(smraw) + (size_t)warp * per;
+    T* bufA = (nc > 1) ? A + (size_t)nb * nb : A;
+    T* bufB = bufA + (nc > 1 ? (size_t)nloc * nloc : (size_t)nb * nb);
+    T* Vq = bufB;
+    {
+        size_t nbuf_b = 1;
+        for (int t = 0; t < 2 * g.d - 1; ++t) nbuf_b *= n;
+        Vq = bufB + nbuf_b;
+    }
+    T* colk = Vq + n * n;
+    for (int i = lane; i < n * n; i += 32) Vq[i] = g.Vq[i];
+    __syncwarp();
+    const int gs = (g.kind == HPG_GRADIENT) ? g.d * (g.d + 1) / 2 : 1;
+    if (nc == 1) {
+        assemble_D_block<T, true>(g, gw, cell, 1, 0, Vq, A, bufB, lane, 32);
+        for (int o = lane; o < nloc * nloc; o += 32) {
+            const int I = o / nloc, J = o % nloc;
+            T v = A[o] + g.C[o] * alpha_inv;
+            if (I == J) v += beta * g.Mpsi[I];
+            A[o] = v;
+        }
+    } else {
+        int e = 0;
+        for (int ca = 0; ca < nc; ++ca)
+            for (int cb = ca; cb < nc; ++cb, ++e) {
+                assemble_D_block<T, true>(g, gw, cell, gs, e, Vq, bufA, bufB, lane, 32);
+                for (int o = lane; o < nloc * nloc; o += 32) {
+                    const int I = o / nloc, J = o % nloc;
+                    T v = bufA[o];
+                    if (ca == cb) v += beta * g.Kpsi[o];
+                    A[(size_t)(ca * nloc + I) * nb + cb * nloc + J] = v;
+                    A[(size_t)(cb * nloc + J) * nb + ca * nloc + I] = v;
+                }
+                __syncwarp();
+            }
+    }
+    __syncwarp();
+    if (dump)
+        for (int o = lane; o < nb * nb; o += 32) dump[cell * nb * nb + o] = (double)A[o];
+    bool bad = false;
+    for (int k = 0; k < nb; ++k) {
+        for (int i = lane; i < nb; i += 32) colk[i] = A[(size_t)i * nb + k];
+        __syncwarp();
+        T p = colk[k];
+        if (!(p > T(0))) { bad = true; p = T(1); }
+        const T inv = T(1) / p;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int j = lane + 32 * c;
+            if (j >= nb) break;
+            const T rk = (j == k) ? inv : A[(size_t)k * nb + j] * inv;
+            for (int i = 0; i < nb; ++i) {
+                T* a = &A[(size_t)i * nb + j];
+                if (i == k) *a = rk;
+                else *a = ((j == k) ? T(0) : *a) - colk[i] * rk;
+            }
+        }
+        __syncwarp();
+    }
+    if (bad && lane == 0) atomicOr(flag + 1, 2);
+    T* out = Sinv + cell * (long long)nb * nb;
+    for (int o = lane; o < nb * nb; o += 32) out[o] = A[o];
+}
+
 // the factorisation workspace of a cell stays in shared memory up to this size
 // (227 KB per block on this GPU, less the kernel's static shared memory)
 constexpr size_t kFactorSmemMax = 225 * 1024;
@@ -789,6 +891,15 @@ cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double bet
     const size_t elems = factor_ws_elems(g.n, g.d, (int)g.nb, g.ncomp);
     const size_t bytes = elems * sizeof(T);
     const int use_smem = bytes <= kFactorSmemMax;
+    if (g.nb <= kFactorWarpMaxNb) {
+        const size_t per = factor_warp_elems(g.n, g.d, (int)g.nb, g.ncomp) * sizeof(T);
+        const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, kFactorSmemMax / per));
+        const unsigned blocks = (unsigned)((g.Nc + wpb - 1) / wpb);
+        k_factor_warp<T><<<dim3(blocks, bt.np), 32 * wpb, per * wpb, s>>>(g, gw, (T)(1.0 / alpha), (T)beta, Sinv,
+                                                                           dump, flag, wpb, bt);
+        note_launch();
+        return cudaGetLastError();
+    }
     if (!use_smem && !gwork) return cudaErrorInvalidValue;
     k_factor<T><<<dim3((unsigned)g.Nc, bt.np), 256, use_smem ? bytes : 0, s>>>(
         g, gw, (T)(1.0 / alpha), (T)beta, Sinv, dump, flag, gwork, use_smem, bt);
@@ -2610,6 +2721,8 @@ void configure_kernels() {
     cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
     cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_newton_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_newton_fused<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

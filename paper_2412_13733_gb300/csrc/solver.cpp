@@ -1206,15 +1206,13 @@ static std::string group_key(const Problem& P) {
     std::snprintf(buf, sizeof buf, "%d|%d|%d,%d,%d|%d|%a,%a,%a|%a,%a,%a|%d|%d|%d|%a|%d|%d|%d|%d|%d", H.d, H.kind,
                   H.m[0], H.m[1], H.m[2], H.p, H.lo[0], H.lo[1], H.lo[2], H.hi[0], H.hi[1], H.hi[2], q.precision,
                   q.krylov_max, q.krylov_f32, q.beta, q.fdm_tile_f32, q.fdm_tile_f64, q.strategy, q.ls_max,
-                  q.refine_max);
+                  q.refine_max * 2 + (q.graphs != 0));
     return buf;
 }
 
-// Whether a problem can run in a lockstep group at all (the flexible-GMRES strategies,
-// per-kernel timing and host-driven launches stay on the single-problem path).
-static bool groupable(const Problem& P) {
-    return P.params.strategy == HPG_SCHUR && P.params.timing == 0 && P.params.graphs != 0;
-}
+// Whether a problem can run in a lockstep group at all (the flexible-GMRES strategies
+// and per-kernel timing stay on the single-problem path).
+static bool groupable(const Problem& P) { return P.params.strategy == HPG_SCHUR && P.params.timing == 0; }
 
 static hpg_status group_build(hpg_ctx* ctx, std::vector<Problem*>& ps, std::shared_ptr<Group>& out) {
     auto Gp = std::make_shared<Group>();
@@ -1368,6 +1366,8 @@ static hpg_status group_gmres_run(hpg_ctx* ctx, Group& Gp, std::vector<int>& its
     GmresDev& G = D.gm;
     const int pi = sizeof(T) == sizeof(float) ? (sizeof(VT) == sizeof(float) ? 2 : 1) : 0;
     CK(launch_gm_stop(G.iflag, s, Gp.bat(kMaskIdle)));
+    // host-driven iterations when graphs are off (profilers cannot trace conditional nodes)
+    if (Gp.ps[0]->params.graphs == 0) Gp.loop_failed[pi] = true;
     if (!Gp.loop[pi] && !Gp.loop_failed[pi]) {
         long long nk = 0;
         if (!group_build_loop<T, VT>(ctx, Gp, &Gp.loop[pi], &nk)) {
