@@ -42,6 +42,8 @@ WORKLOAD = "radial32"
 # one A_alpha^{-1} apply on the 32x32 p=8 workload, from one ncu capture (`--kernel fdm
 # --precision mixed --fdm-tile 0`, cold caches)
 FDM_TRAFFIC_BYTES = (573952 + 575744 + 574720 + 573952)
+# the same for one batched apply (16 problems per launch); None until captured for the current kernels
+FDM_BATCH_TRAFFIC_BYTES = None
 METRIC = "solves/s (complete hpG solve at 1e-8 rel err vs FP64 oracle), mixed vs FP64; DoF*Krylov-its/s"
 
 
@@ -465,7 +467,20 @@ def main():
                               h2d_bytes_per_step=int(sum(P.stats()["h2d_bytes"] for P in ps)),
                               d2h_bytes_per_step=int(d2h))
         res["kernels"] = {}
-        if with_kernels and not args.no_kernel_timing:
+        if with_kernels and count > 1 and not args.no_kernel_timing:
+            # the kernels as the batched step runs them: one launch serves the whole group
+            for cls, reps in (("fdm", 20), ("precond", 20), ("bapply", 20), ("schur", 20), ("newton_apply", 20),
+                              ("factor", 5), ("eval", 20)):
+                ctx.launch_kernel_batch(ps, cls, prec, reps)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.launch_kernel_batch(ps, cls, prec, reps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res["kernels"][cls] = (e0.elapsed_time(e1) / reps, reps)
+        elif with_kernels and not args.no_kernel_timing:
             P = ps[0]
             for cls, reps in (("fdm", 50), ("precond", 50), ("bapply", 50), ("schur", 50),
                               ("newton_apply", 50), ("ortho", 50), ("factor", 5), ("eval", 20)):
@@ -486,7 +501,7 @@ def main():
 
     ctx.set_concurrency(B)
     results = {}
-    results["mixed_batch"] = leg("mixed_batch", hpg.HPG_MIXED, B, True, False, ClockSampler(local_rank))
+    results["mixed_batch"] = leg("mixed_batch", hpg.HPG_MIXED, B, True, True, ClockSampler(local_rank))
     clocks = results["mixed_batch"]["clocks"]
     results["mixed"] = leg("mixed", hpg.HPG_MIXED, 1, False, True)
     if not args.no_fp64:
@@ -498,8 +513,25 @@ def main():
     work = mixed["work"]
     kt = mixed["kernels"]
     roof = None
+    kb = results["mixed_batch"]["kernels"]
+    if "fdm" in kb:
+        # the dominant kernel of the timed step: the fast-diagonalisation A_alpha^{-1} apply
+        # (2d GEMM passes, FP32) as the batched step launches it, every problem of the
+        # group in one launch; algorithmic work = B x 4 d n1 N_u0 flops per launch
+        _, flops, unit = work["fdm"]
+        flops_b = flops * B
+        avg_ms = kb["fdm"][0]
+        ach = flops_b / (avg_ms / 1000.0) / 1e12
+        peak = alu_peaks["fp32"]
+        roof = {"kernel": f"fdm (A_alpha^-1, FP32 SIMT GEMM passes, {B} problems per launch as in the batched step)",
+                "bound": "alu", "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "traffic": FDM_BATCH_TRAFFIC_BYTES, "avg_launch_us": avg_ms * 1000.0, "problems_per_launch": B,
+                "flops_per_launch": flops_b,
+                "peak_source": "measured (hpg_measure_fma_peak, FP32 FMA chains on all SMs)",
+                "derived_peak": alu_peak_tflops("fp32", peak_mhz, sm_count)}
+    single_fdm = None
     if "fdm" in kt:
-        # the fast-diagonalisation A_alpha^{-1} apply (2d GEMM passes, FP32 in the mixed path)
+        # the same apply for one problem alone (latency-bound: few CTAs per pass)
         _, flops, unit = work["fdm"]
         avg_ms = kt["fdm"][0]
         ach = flops / (avg_ms / 1000.0) / 1e12
@@ -507,7 +539,8 @@ def main():
         # DRAM bytes of one apply (4 passes) from the ncu capture of FDM variant 0 on this
         # workload; null if the autotuner picked another variant
         traffic = FDM_TRAFFIC_BYTES if mixed["fdm_variant"] == 0 else None
-        roof = {"kernel": "fdm (A_alpha^-1, FP32 SIMT GEMM passes)", "bound": "alu", "achieved": ach, "peak": peak,
+        single_fdm = {"kernel": "fdm (A_alpha^-1, FP32 SIMT GEMM passes), one problem", "bound": "alu",
+                      "achieved": ach, "peak": peak,
                 "unit": unit, "frac": ach / peak, "traffic": traffic, "avg_launch_us": avg_ms * 1000.0,
                 "peak_source": "measured (hpg_measure_fma_peak, FP32 FMA chains on all SMs)",
                 "derived_peak": alu_peak_tflops("fp32", peak_mhz, sm_count)}
@@ -666,8 +699,10 @@ def main():
                 "e2e": head["e2e"], "gpu_launches": int(head["launches"] * args.steps),
                 "accuracy": {k: results[k]["accuracy"] for k in results},
                 "measured_alu_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak, "sm_count": sm_count},
-                "roofline": roof, "newton_apply_roofline": newton_roof, "other_rooflines": bw_roofs,
+                "roofline": roof, "single_problem_fdm_roofline": single_fdm, "newton_apply_roofline": newton_roof,
+                "other_rooflines": bw_roofs,
                 "kernel_avg_us": {k: v[0] * 1000.0 for k, v in kt.items()},
+                "batch_kernel_avg_us": {k: v[0] * 1000.0 for k, v in kb.items()},
                 # FDM pass variant picked by the set-up autotuner (hpg_fdm_tile_count; the last two FP32
                 # variants are the tcgen05 kernels); pass it to --fdm-tile to reproduce a run under ncu
                 "fdm_variant": {"mixed": head["fdm_variant"], "fp64": fp["fdm_variant"] if fp else None},

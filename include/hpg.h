@@ -291,6 +291,14 @@ hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precis
  * stream (synchronises it).  *sm_count (may be NULL) receives the SM count.  The
  * roofline denominators of the FP32/FP64-bound kernels; not part of the method. */
 hpg_status hpg_measure_fma_peak(hpg_ctx* ctx, int precision, double* tflops, int* sm_count);
+/* The same for a batch: `reps` back-to-back launches of one kernel class, each serving
+ * every problem of pids[0..count-1] in the lockstep configuration hpg_solve_batch uses
+ * for them (one launch per step for the whole group).  The problems must have been
+ * solved and share shape and parameters (HPG_ERR_STATE otherwise).  Classes HPG_K_FDM,
+ * _PRECOND, _BAPPLY, _SCHUR, _FACTOR, _NEWTON_APPLY, _EVAL; captured once per (class,
+ * precision, reps) and replayed; writes only scratch buffers. */
+hpg_status hpg_launch_kernel_batch(hpg_ctx* ctx, const int* pids, int count, int kernel_class, int precision,
+                                   int reps);
 /* Number of fast-diagonalisation pass variants for `precision` (HPG_MIXED: FP32
  * passes, HPG_FP64: FP64 passes); valid values of hpg_params.fdm_tile_f32/_f64
  * are 0 .. count-1.  Returns 0 for an unknown precision. */

@@ -615,6 +615,26 @@ hpg_status hpg_launch_kernel(hpg_ctx* ctx, int pid, int kernel_class, int precis
     GUARD_END
 }
 
+hpg_status hpg_launch_kernel_batch(hpg_ctx* ctx, const int* pids, int count, int kernel_class, int precision,
+                                   int reps) {
+    if (!ctx || !pids || count < 1 || reps < 0 || kernel_class < 0 || kernel_class >= HPG_K_COUNT ||
+        (precision != HPG_FP64 && precision != HPG_MIXED))
+        return HPG_ERR_ARG;
+    if (cuda_ok(ctx) != HPG_OK) return HPG_ERR_CUDA;
+    std::vector<Problem*> ps;
+    for (int i = 0; i < count; ++i) {
+        Problem* P = find(ctx, pids[i]);
+        if (!P) return HPG_ERR_ARG;
+        NOT_BUSY(P);
+        for (Problem* Q : ps)
+            if (Q == P) return HPG_ERR_ARG;
+        ps.push_back(P);
+    }
+    GUARD_BEGIN
+    return hpg::op_launch_kernel_group(ctx, ps, kernel_class, precision, reps);
+    GUARD_END
+}
+
 // ------------------------------------------------------------ request loop
 hpg_status hpg_server_start(hpg_ctx* ctx, int workers, size_t device_budget_bytes) {
     if (!ctx || workers < 1 || workers > 64) return HPG_ERR_ARG;

@@ -258,6 +258,8 @@ template <typename VT>
 cudaError_t gmres_finish(GmresDev& G, double* x, cudaStream_t s, const Bat& bt = Bat{});
 // Number of FDM GEMM tile variants for elements of `elem` bytes.
 int fdm_tile_count(int elem);
+// K split of variant idx (variants with the same split give the same bits); 0: tensor cores
+int fdm_tile_ks(int elem, int idx);
 // FMA throughput of the SIMT pipe for elements of `elem` bytes (4: FP32, 8: FP64),
 // measured with independent FMA chains on every SM (best of three timed launches on s).
 cudaError_t measure_fma_peak(int elem, int sm_count, cudaStream_t s, double* tflops);

@@ -784,11 +784,19 @@ __host__ __device__ inline size_t factor_warp_elems(int n, int d, int nb, int nc
     size_t nloc = 1, nbuf_b = 1;
     for (int t = 0; t < d; ++t) nloc *= n;
     for (int t = 0; t < 2 * d - 1; ++t) nbuf_b *= n;
-    // A (nb^2) | bufA (nloc^2, gradient only) | bufB (n^{2d-1}) | Vq (n^2) | column k (nb)
-    return (size_t)nb * nb + (nc > 1 ? nloc * nloc : 0) + nbuf_b + (size_t)n * n + nb;
+    // A (nb^2) | bufA (nloc^2, gradient only) | bufB (n^{2d-1}) | Vq (n^2) | column k (nb) or
+    // the two row buffers of the register variant (2 x 64), 16-byte aligned
+    size_t e = (size_t)nb * nb + (nc > 1 ? nloc * nloc : 0) + nbuf_b + (size_t)n * n;
+    e = (e + 3) & ~(size_t)3;
+    return e + (nb > 128 ? (size_t)nb : 128);
 }
 
-template <typename T>
+// R > 0: the register variant for nb <= 32 R.  Lane l keeps rows l + 32 r (r < R) of
+// the block in registers, padded to 32 R columns (and with identity rows past nb);
+// step k has the owner of row k publish it through a double-buffered shared row, and
+// every lane eliminates with one multiply-add per register -- no shared-memory
+// traffic per element, so the elimination runs at the FMA rate.
+template <typename T, int R>
 __global__ void __launch_bounds__(128)
     k_factor_warp(Geo<T> g, const T* __restrict__ gw, T alpha_inv, T beta, T* __restrict__ Sinv,
                   double* __restrict__ dump, int* __restrict__ flag, int wpb, Bat bt) {
@@ -812,7 +820,7 @@ __global__ void __launch_bounds__(128)
         for (int t = 0; t < 2 * g.d - 1; ++t) nbuf_b *= n;
         Vq = bufB + nbuf_b;
     }
-    T* colk = Vq + n * n;
+    T* colk = reinterpret_cast<T*>(smraw) + (size_t)warp * per + (per - (nb > 128 ? nb : 128));
     for (int i = lane; i < n * n; i += 32) Vq[i] = g.Vq[i];
     __syncwarp();
     const int gs = (g.kind == HPG_GRADIENT) ? g.d * (g.d + 1) / 2 : 1;
@@ -843,6 +851,51 @@ __global__ void __launch_bounds__(128)
     if (dump)
         for (int o = lane; o < nb * nb; o += 32) dump[cell * nb * nb + o] = (double)A[o];
     bool bad = false;
+    if constexpr (R > 0) {
+        constexpr int NM = 32 * R;
+        T a[R][NM];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = lane + 32 * r;
+#pragma unroll
+            for (int j = 0; j < NM; ++j) a[r][j] = (i < nb && j < nb) ? A[(size_t)i * nb + j] : T(i == j ? 1 : 0);
+        }
+        T* rb0 = colk;
+        T* rb1 = colk + 64;
+#pragma unroll
+        for (int k = 0; k < NM; ++k) {
+            if (k >= nb) break;
+            T* rb = (k & 1) ? rb1 : rb0;
+            if (lane == (k & 31)) {
+#pragma unroll
+                for (int j = 0; j < NM; ++j) rb[j] = a[k >> 5][j];
+            }
+            __syncwarp();
+            T p = rb[k];
+            if (!(p > T(0))) { bad = true; p = T(1); }
+            const T inv = T(1) / p;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const bool is_k = lane + 32 * r == k;
+                const T f = a[r][k];
+                const T fp = is_k ? T(1) - inv : f * inv;
+#pragma unroll
+                for (int j = 0; j < NM; ++j)
+                    if (j != k) a[r][j] -= fp * rb[j];
+                a[r][k] = is_k ? inv : -fp;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = lane + 32 * r;
+            if (i < nb)
+#pragma unroll
+                for (int j = 0; j < NM; ++j)
+                    if (j < nb) A[(size_t)i * nb + j] = a[r][j];
+        }
+        __syncwarp();
+    } else {
     for (int k = 0; k < nb; ++k) {
         for (int i = lane; i < nb; i += 32) colk[i] = A[(size_t)i * nb + k];
         __syncwarp();
@@ -861,6 +914,7 @@ __global__ void __launch_bounds__(128)
             }
         }
         __syncwarp();
+    }
     }
     if (bad && lane == 0) atomicOr(flag + 1, 2);
     T* out = Sinv + cell * (long long)nb * nb;
@@ -895,8 +949,20 @@ cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double bet
         const size_t per = factor_warp_elems(g.n, g.d, (int)g.nb, g.ncomp) * sizeof(T);
         const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, kFactorSmemMax / per));
         const unsigned blocks = (unsigned)((g.Nc + wpb - 1) / wpb);
-        k_factor_warp<T><<<dim3(blocks, bt.np), 32 * wpb, per * wpb, s>>>(g, gw, (T)(1.0 / alpha), (T)beta, Sinv,
-                                                                           dump, flag, wpb, bt);
+        const dim3 grid(blocks, bt.np);
+        const T ai = (T)(1.0 / alpha), be = (T)beta;
+        // registers hold 32 R columns per row: R = 2 for FP32 up to 64, R = 1 up to 32
+        bool done = false;
+        if (g.nb <= 32) {
+            k_factor_warp<T, 1><<<grid, 32 * wpb, per * wpb, s>>>(g, gw, ai, be, Sinv, dump, flag, wpb, bt);
+            done = true;
+        }
+        if constexpr (sizeof(T) == 4)
+            if (!done && g.nb <= 64) {
+                k_factor_warp<T, 2><<<grid, 32 * wpb, per * wpb, s>>>(g, gw, ai, be, Sinv, dump, flag, wpb, bt);
+                done = true;
+            }
+        if (!done) k_factor_warp<T, 0><<<grid, 32 * wpb, per * wpb, s>>>(g, gw, ai, be, Sinv, dump, flag, wpb, bt);
         note_launch();
         return cudaGetLastError();
     }
@@ -1176,7 +1242,18 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
     for (int k = kb; k < ke; ++k) {
         T av[TM], bv[TN];
         // vector shared loads (the panel rows are 16-byte aligned)
-        if (sizeof(T) == 4 && TM == 4 && TN == 2) {
+        if (sizeof(T) == 4 && TM % 4 == 0 && TN % 4 == 0) {
+#pragma unroll
+            for (int q = 0; q < TM / 4; ++q) {
+                const float4 va = *reinterpret_cast<const float4*>(ap + (size_t)k * BM + 4 * q);
+                av[4 * q] = (T)va.x; av[4 * q + 1] = (T)va.y; av[4 * q + 2] = (T)va.z; av[4 * q + 3] = (T)va.w;
+            }
+#pragma unroll
+            for (int q = 0; q < TN / 4; ++q) {
+                const float4 vb = *reinterpret_cast<const float4*>(bp + (size_t)k * BN + 4 * q);
+                bv[4 * q] = (T)vb.x; bv[4 * q + 1] = (T)vb.y; bv[4 * q + 2] = (T)vb.z; bv[4 * q + 3] = (T)vb.w;
+            }
+        } else if (sizeof(T) == 4 && TM == 4 && TN == 2) {
             const float4 va = *reinterpret_cast<const float4*>(ap + (size_t)k * BM);
             const float2 vb = *reinterpret_cast<const float2*>(bp + (size_t)k * BN);
             av[0] = (T)va.x; av[1] = (T)va.y; av[2] = (T)va.z; av[3] = (T)va.w;
@@ -1615,8 +1692,12 @@ static cudaError_t launch_tile(const GemmArgs& a, const T* A, const T* B, T* Cp,
     return cudaGetLastError();
 }
 
+// The last FP32 SIMT tiles (8 x 4 outputs per thread) serve batches: more multiply-adds
+// per shared load, for launches that fill the GPU many times over.  Tiles with the same
+// KS add the same products in the same order, so they give the same bits.
 using F32Tiles = std::tuple<Tile<float, 32, 16, 4, 2, 4>, Tile<float, 32, 32, 4, 2, 2>, Tile<float, 32, 16, 4, 2, 2>,
-                            Tile<float, 16, 16, 2, 2, 4>, Tile<float, 32, 32, 4, 2, 4>>;
+                            Tile<float, 16, 16, 2, 2, 4>, Tile<float, 32, 32, 4, 2, 4>, Tile<float, 64, 32, 8, 4, 4>,
+                            Tile<float, 64, 32, 8, 4, 2>, Tile<float, 64, 64, 8, 8, 4>>;
 using F64Tiles = std::tuple<Tile<double, 16, 16, 2, 2, 1>, Tile<double, 16, 16, 2, 2, 2>,
                             Tile<double, 32, 16, 4, 2, 1>, Tile<double, 16, 8, 2, 2, 2>>;
 template <typename T>
@@ -1630,6 +1711,21 @@ struct TileSet<double> { using type = F64Tiles; };
 constexpr int kTcVariants = 2;
 int fdm_tile_count(int elem) {
     return elem == 4 ? (int)std::tuple_size<F32Tiles>::value + kTcVariants : (int)std::tuple_size<F64Tiles>::value;
+}
+
+template <typename Set, size_t I = 0>
+static int tile_ks_of(int idx) {
+    if constexpr (I < std::tuple_size<Set>::value) {
+        if (idx == (int)I) return std::tuple_element<I, Set>::type::KS;
+        return tile_ks_of<Set, I + 1>(idx);
+    } else {
+        return 0;
+    }
+}
+
+// K split of a variant (its summation order); 0 for the tensor-core variants
+int fdm_tile_ks(int elem, int idx) {
+    return elem == 4 ? tile_ks_of<F32Tiles>(idx) : tile_ks_of<F64Tiles>(idx);
 }
 
 template <typename T, size_t I = 0>
@@ -2721,8 +2817,12 @@ void configure_kernels() {
     cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
     cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
-    cudaFuncSetAttribute(k_factor_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
-    cudaFuncSetAttribute(k_factor_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor_warp<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor_warp<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor_warp<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor_warp<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor_warp<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+
     cudaFuncSetAttribute(k_gm_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_newton_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_newton_fused<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -1176,7 +1176,13 @@ struct Group {
     cudaGraphExec_t loop[3] = {nullptr, nullptr, nullptr};
     long long loop_kernels[3] = {0, 0, 0};
     bool loop_failed[3] = {false, false, false};
+    // problem 0's operator views with the FDM pass variant tuned for the group's size
+    Geo<float> gf{};
+    Geo<double> gd{};
+    bool tuned_f = false, tuned_d = false;
+    std::map<long long, std::pair<cudaGraphExec_t, long long>> bench_graphs;   // kernel-class replays
     ~Group() {
+        for (auto& kv : bench_graphs) cudaGraphExecDestroy(kv.second.first);
         for (auto& gx : loop)
             if (gx) cudaGraphExecDestroy(gx);
         if (delta_d) cudaFree(delta_d);
@@ -1291,6 +1297,73 @@ static hpg_status group_gather(hpg_ctx* ctx, Group& Gp, const double* d, const i
     CK(cudaStreamSynchronize(s));
     return HPG_OK;
 }
+template <typename T>
+struct GG;
+template <>
+struct GG<float> {
+    static Geo<float>& g(Group& G) { return G.gf; }
+    static bool& tuned(Group& G) { return G.tuned_f; }
+};
+template <>
+struct GG<double> {
+    static Geo<double>& g(Group& G) { return G.gd; }
+    static bool& tuned(Group& G) { return G.tuned_d; }
+};
+
+// The FDM pass variant of a group: among the variants with the K split of the one
+// the problems use alone (the same products summed in the same order, so the same
+// bits), the fastest at the group's size; cached per (shape, precision, size).
+template <typename T>
+static hpg_status group_tune_fdm(hpg_ctx* ctx, Group& Gp) {
+    Geo<T>& gg = GG<T>::g(Gp);
+    DevState& D = Gp.ps[0]->D;
+    gg = PV<T>::g(D);
+    GG<T>::tuned(Gp) = true;
+    const int forced = sizeof(T) == 4 ? Gp.ps[0]->params.fdm_tile_f32 : Gp.ps[0]->params.fdm_tile_f64;
+    const int ks = fdm_tile_ks((int)sizeof(T), gg.gemm_cfg);
+    if (forced >= 0 || ks == 0 || Gp.np == 1) return HPG_OK;
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int, int>, int> cache;
+    const auto key = std::make_tuple(gg.d, gg.n1[0], gg.n1[1], gg.d > 2 ? gg.n1[2] : 1, (int)sizeof(T), Gp.np);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) { gg.gemm_cfg = it->second; return HPG_OK; }
+    }
+    cudaStream_t s = ctx->stream;
+    const Bat all = Gp.bat(-1);
+    T* x = PV<T>::tu(D);
+    T* y = PV<T>::tu2(D);
+    CK(launch_copy<T>(nullptr, x, gg.Nu0, s, all));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int base = gg.gemm_cfg;
+    int best = base;
+    float best_ms = 1e30f;
+    for (int c = 0; c < fdm_tile_count((int)sizeof(T)); ++c) {
+        if (fdm_tile_ks((int)sizeof(T), c) != ks) continue;
+        gg.gemm_cfg = c;
+        if (launch_fdm<T>(gg, nullptr, 1.0, x, y, PV<T>::w1(D), PV<T>::w2(D), s, nullptr, all) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch_fdm<T>(gg, nullptr, 1.0, x, y, PV<T>::w1(D), PV<T>::w2(D), s, nullptr, all);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    gg.gemm_cfg = best;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best;
+    return HPG_OK;
+}
+
 static double gd_(const Group& Gp, int i, int k) { return Gp.h_stat[i * kStatD + k]; }
 static int gi_(const Group& Gp, int i, int k) { return (int)Gp.h_stat[Gp.np * kStatD + i * kStatI + k]; }
 
@@ -1302,7 +1375,7 @@ static hpg_status group_gmres_chunk(hpg_ctx* ctx, Group& Gp, int chunk) {
     DevState& D = P0.D;
     cudaStream_t s = ctx->stream;
     GmresDev& G = D.gm;
-    const Geo<T>& g = PV<T>::g(D);
+    const Geo<T>& g = GG<T>::g(Gp);
     const IterCtl ctl{G.iflag, G.jdev, G.N};
     const Bat all = Gp.bat(-1);
     for (int c = 0; c < chunk; ++c) {
@@ -1408,7 +1481,7 @@ static hpg_status group_schur_solve(hpg_ctx* ctx, Group& Gp, std::vector<int>& i
     Problem& P0 = *Gp.ps[0];
     DevState& D = P0.D;
     cudaStream_t s = ctx->stream;
-    const Geo<T>& g = PV<T>::g(D);
+    const Geo<T>& g = GG<T>::g(Gp);
     const long long Nu0 = (long long)P0.H.Nu0, Npsi = (long long)P0.H.Npsi;
     GmresDev& G = D.gm;
     const Bat b = Gp.bat(kMaskSolve);
@@ -1554,6 +1627,8 @@ hpg_status solve_group(hpg_ctx* home, hpg_ctx* ctx, std::vector<Problem*>& ps, s
         P->timer.on = false;
     }
     const Bat all = Gp.bat(-1);
+    if (P0.params.precision == HPG_FP64 && !Gp.tuned_d) CKS(group_tune_fdm<double>(ctx, Gp));
+    if (P0.params.precision != HPG_FP64 && !Gp.tuned_f) CKS(group_tune_fdm<float>(ctx, Gp));
     CK(launch_copy<double>(nullptr, D.x, Nx, s, all));
     CK(launch_copy<double>(nullptr, D.psi_prev, Npsi, s, all));
     CK(launch_copy<int>(nullptr, D.flag, 4, s, all));
@@ -2041,6 +2116,95 @@ hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, in
     if (cls == HPG_K_ORTHO) CK(cudaMemsetAsync(D.gm.force, 1, sizeof(int), s));
     CK(cudaGraphLaunch(it->second.first, s));
     if (cls == HPG_K_ORTHO) CK(cudaMemsetAsync(D.gm.force, 0, sizeof(int), s));
+    add_kernel_launches(it->second.second);
+    return HPG_OK;
+}
+
+
+// ---- kernel-class replays over a whole group (timing in the batched configuration)
+template <typename T>
+static hpg_status group_enqueue(hpg_ctx* ctx, Group& Gp, int cls, double alpha) {
+    Problem& P0 = *Gp.ps[0];
+    DevState& D = P0.D;
+    cudaStream_t s = ctx->stream;
+    Bat all = Gp.bat(-1);
+    all.par = nullptr;                     // scalar arguments, as in the single-problem replays
+    const Geo<T>& g = GG<T>::g(Gp);
+    constexpr bool f32 = sizeof(T) == sizeof(float);
+    switch (cls) {
+        case HPG_K_FDM:
+            CK(launch_fdm<T>(g, nullptr, alpha, PV<T>::tu(D), PV<T>::tu2(D), PV<T>::w1(D), PV<T>::w2(D), s, nullptr,
+                             all));
+            break;
+        case HPG_K_PRECOND:
+            CK((launch_precond<T, double, T>(g, PV<T>::Sinv(D), D.yp, PV<T>::zp(D), s, IterCtl{}, all)));
+            break;
+        case HPG_K_BAPPLY:
+            CK((launch_bapply<T, T, T>(g, PV<T>::zp(D), PV<T>::tu(D), s, nullptr, all)));
+            break;
+        case HPG_K_SCHUR:
+            CK((launch_schur_rest<T, double>(g, PV<T>::gw(D), P0.params.beta, PV<T>::zp(D), PV<T>::tu2(D), D.xs, s,
+                                             IterCtl{}, all)));
+            break;
+        case HPG_K_FACTOR:
+            CK(launch_factor<T>(g, PV<T>::gw(D), alpha, P0.params.beta, PV<T>::Sinv(D), nullptr, D.flag,
+                                PV<T>::fwork(D), s, all));
+            break;
+        case HPG_K_NEWTON_APPLY:
+            CK(launch_newton_apply(D.gd, D.gw, alpha, P0.params.beta, D.x, D.r, s, all));
+            break;
+        case HPG_K_EVAL:
+            CK(launch_eval(D.gd, D.x + P0.H.Nu0, D.phiq, D.gwt, nullptr, D.egt, D.flag, s, all));
+            break;
+        default:
+            (void)f32;
+            return HPG_ERR_ARG;
+    }
+    return HPG_OK;
+}
+
+hpg_status op_launch_kernel_group(hpg_ctx* ctx, std::vector<Problem*>& ps, int cls, int precision, int reps) {
+    for (Problem* P : ps)
+        if (!P->alloc_done || !P->solved || !groupable(*P) || group_key(*P) != group_key(*ps[0])) {
+            ctx->err = "hpg_launch_kernel_batch: every problem must be solved, of one shape and parameter set";
+            return HPG_ERR_STATE;
+        }
+    std::shared_ptr<Group> gref;
+    CKS(group_for(ctx, ctx, ps, gref));
+    Group& Gp = *gref;
+    const bool f32 = precision == HPG_MIXED;
+    if (f32 && !Gp.tuned_f) CKS(group_tune_fdm<float>(ctx, Gp));
+    if (!f32 && !Gp.tuned_d) CKS(group_tune_fdm<double>(ctx, Gp));
+    Problem& P0 = *ps[0];
+    DevState& D = P0.D;
+    cudaStream_t s = ctx->stream;
+    const double alpha = P0.H.alphas.empty() ? 1.0 : P0.H.alphas.back();
+    const long long key = ((long long)cls * 2 + (f32 ? 1 : 0)) * 1000003LL + reps;
+    auto it = Gp.bench_graphs.find(key);
+    if (it == Gp.bench_graphs.end()) {
+        const long long gsz = (long long)(P0.H.Nq * gauss_stride(P0.H.kind, P0.H.d));
+        const Bat all = Gp.bat(-1);
+        CK(launch_copy<double>(D.gw, D.gwl, gsz, s, all));
+        CK(launch_convert<double, float>(D.gwl, D.gwf, gsz, s, all));
+        CK(cudaStreamSynchronize(s));
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        hpg_status st = HPG_OK;
+        const long long before = kernel_launch_count();
+        for (int r = 0; r < reps && st == HPG_OK; ++r)
+            st = f32 ? group_enqueue<float>(ctx, Gp, cls, alpha) : group_enqueue<double>(ctx, Gp, cls, alpha);
+        const long long nk = kernel_launch_count() - before;
+        add_kernel_launches(-nk);
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st != HPG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        CK(ce);
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+        it = Gp.bench_graphs.emplace(key, std::make_pair(ex, nk)).first;
+    }
+    CK(cudaGraphLaunch(it->second.first, s));
     add_kernel_launches(it->second.second);
     return HPG_OK;
 }

@@ -162,6 +162,7 @@ hpg_status op_precond_inv(hpg_ctx* ctx, Problem& P, int precision, const double*
 hpg_status op_schur(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y);
 hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double rtol, double* delta, int* its);
 hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, int reps);
+hpg_status op_launch_kernel_group(hpg_ctx* ctx, std::vector<Problem*>& ps, int cls, int precision, int reps);
 // request loop
 size_t estimate_device_bytes(const Problem& P);
 hpg_status server_start(hpg_ctx* ctx, int workers, size_t budget);

@@ -87,6 +87,7 @@ SIGNATURES = {
     "hpg_newton_direction": ([_ctx, C.c_int, C.c_int, _d, _pd, _sz, _P(C.c_int)], C.c_int),
     "hpg_launch_kernel": ([_ctx, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "hpg_fdm_tile_count": ([C.c_int], C.c_int),
+    "hpg_launch_kernel_batch": ([_ctx, _P(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "hpg_apply_stiffness_inv_noalloc": ([_ctx, C.c_int, _d, C.c_void_p, C.c_void_p, _sz], C.c_int),
     "hpg_server_start": ([_ctx, C.c_int, _sz], C.c_int),
     "hpg_server_stop": ([_ctx], C.c_int),
@@ -203,6 +204,13 @@ class Context:
         self.check(self.L.hpg_server_memory(self.h, problem.pid if problem else 0, C.byref(a),
                                             C.byref(b) if problem else None))
         return a.value, (b.value if problem else None)
+
+    def launch_kernel_batch(self, problems, name, precision=HPG_FP64, reps=1):
+        """Replay `reps` launches of one kernel class over a lockstep group of solved problems."""
+        cls = KERNEL_CLASSES.index(name) if isinstance(name, str) else int(name)
+        ids = (C.c_int * len(problems))(*[p.pid for p in problems])
+        self.check(self.L.hpg_launch_kernel_batch(self.h, ids, len(problems), cls, int(precision), int(reps)),
+                   "hpg_launch_kernel_batch")
 
     def fma_peak(self, precision):
         """Measured SIMT FMA throughput (TFLOP/s) and SM count of the device."""
