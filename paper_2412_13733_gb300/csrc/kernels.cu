@@ -7,6 +7,7 @@
 #include <atomic>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <cfloat>
 #include <cmath>
 
@@ -862,16 +863,33 @@ __global__ void __launch_bounds__(128)
         }
         T* rb0 = colk;
         T* rb1 = colk + 64;
+        // the published row moves in 16-byte words: 4 floats (2 doubles) per load
+        constexpr int VW = 16 / (int)sizeof(T);
+        using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
             if (k >= nb) break;
             T* rb = (k & 1) ? rb1 : rb0;
             if (lane == (k & 31)) {
 #pragma unroll
-                for (int j = 0; j < NM; ++j) rb[j] = a[k >> 5][j];
+                for (int q = 0; q < NM / VW; ++q) {
+                    V16 v;
+                    T* vt = reinterpret_cast<T*>(&v);
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) vt[u] = a[k >> 5][VW * q + u];
+                    reinterpret_cast<V16*>(rb)[q] = v;
+                }
             }
             __syncwarp();
-            T p = rb[k];
+            T row[NM];
+#pragma unroll
+            for (int q = 0; q < NM / VW; ++q) {
+                const V16 v = reinterpret_cast<const V16*>(rb)[q];
+                const T* vt = reinterpret_cast<const T*>(&v);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) row[VW * q + u] = vt[u];
+            }
+            T p = row[k];
             if (!(p > T(0))) { bad = true; p = T(1); }
             const T inv = T(1) / p;
 #pragma unroll
@@ -881,7 +899,7 @@ __global__ void __launch_bounds__(128)
                 const T fp = is_k ? T(1) - inv : f * inv;
 #pragma unroll
                 for (int j = 0; j < NM; ++j)
-                    if (j != k) a[r][j] -= fp * rb[j];
+                    if (j != k) a[r][j] -= fp * row[j];
                 a[r][k] = is_k ? inv : -fp;
             }
         }
@@ -1392,6 +1410,138 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         }
 }
 
+// ---- pipelined variant for batches --------------------------------------------
+// The whole-K tiles above stage a CTA's entire K panels before computing and rely on
+// several CTAs per SM to hide that.  For batched launches (many CTAs of identical
+// shape) this variant streams K in chunks of 16 through double-buffered shared
+// memory (cp.async groups: chunk c + 1 loads while chunk c computes) with a 4 x 4
+// register tile per thread.  It keeps KS separate accumulators -- K split into the
+// same KS contiguous ranges as the whole-K tile with that KS, each summed in k order,
+// then added in range order -- so it gives the same bits as those tiles.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <typename T, int BM, int BN, int TM, int TN, int KS>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_gemm_pipe(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp, FdmScale sc,
+                const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2, const int* skip,
+                Bat bt) {
+    constexpr int BK = 16, NT = (BM / TM) * (BN / TN);
+    __shared__ __align__(16) T As[2][BK][BM];
+    __shared__ __align__(16) T Bs[2][BK][BN];
+    GEMM_BATCH_ENTER()
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int b = (int)blockIdx.z - prob_ * a.batch;
+    const T* A = Ap + (long long)b * a.sAb;
+    const T* B = Bp + (long long)b * a.sBb;
+    T* C = Cp + (long long)b * a.sCb;
+    const int K = a.K;
+    const int kchunk = (K + KS - 1) / KS;
+    // stage K indices [k0, min(k0 + BK, kend)) into buffer buf (zero outside)
+    auto stage = [&](int buf, int k0, int kend) {
+        for (int e = tid; e < BM * BK; e += NT) {
+            const int mm = e % BM, kk = e / BM, gm = m0 + mm, k = k0 + kk;
+            const bool ok = gm < a.M && k < kend;
+            cp_async_elem(&As[buf][kk][mm], ok ? A + (long long)gm * a.sAm + (long long)k * a.sAk : A, ok);
+        }
+        for (int e = tid; e < BN * BK; e += NT) {
+            const int nn = e % BN, kk = e / BN, gn = n0 + nn, k = k0 + kk;
+            const bool ok = gn < a.N && k < kend;
+            cp_async_elem(&Bs[buf][kk][nn], ok ? B + (long long)k * a.sBk + (long long)gn * a.sBn : B, ok);
+        }
+    };
+    T acc[KS][TM][TN];
+#pragma unroll
+    for (int g = 0; g < KS; ++g)
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int jj = 0; jj < TN; ++jj) acc[g][i][jj] = T(0);
+    // the first chunk of the first non-empty range
+    int first_g = 0;
+    while (first_g < KS && first_g * kchunk >= K) ++first_g;
+    int t = 0;
+    if (first_g < KS) {
+        stage(0, first_g * kchunk, min(K, (first_g + 1) * kchunk));
+        cp_async_commit();
+    }
+#pragma unroll
+    for (int g = 0; g < KS; ++g) {
+        const int gb = g * kchunk, ge = min(K, gb + kchunk);
+        for (int k0 = gb; k0 < ge; k0 += BK) {
+            // next chunk: the rest of this range, else the start of the next non-empty one
+            int nk0 = -1, nke = 0;
+            if (k0 + BK < ge) {
+                nk0 = k0 + BK;
+                nke = ge;
+            } else {
+                for (int h = g + 1; h < KS; ++h)
+                    if (h * kchunk < K) { nk0 = h * kchunk; nke = min(K, (h + 1) * kchunk); break; }
+            }
+            if (nk0 >= 0) {
+                stage((t + 1) & 1, nk0, nke);
+                cp_async_commit();
+                cp_async_wait_group<1>();
+            } else {
+                cp_async_wait_group<0>();
+            }
+            __syncthreads();
+            const int buf = t & 1, kn = min(BK, ge - k0);
+            for (int kk = 0; kk < kn; ++kk) {
+                T av[TM], bv[TN];
+                if constexpr (sizeof(T) == 4 && TM == 4 && TN == 4) {
+                    const float4 va = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM]);
+                    const float4 vb = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * TN]);
+                    av[0] = va.x; av[1] = va.y; av[2] = va.z; av[3] = va.w;
+                    bv[0] = vb.x; bv[1] = vb.y; bv[2] = vb.z; bv[3] = vb.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < TM; ++i) av[i] = As[buf][kk][ty * TM + i];
+#pragma unroll
+                    for (int jj = 0; jj < TN; ++jj) bv[jj] = Bs[buf][kk][tx * TN + jj];
+                }
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < TN; ++jj) acc[g][i][jj] += av[i] * bv[jj];
+            }
+            __syncthreads();
+            ++t;
+        }
+    }
+#pragma unroll
+    for (int g = 1; g < KS; ++g)
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int jj = 0; jj < TN; ++jj) acc[0][i][jj] += acc[g][i][jj];
+    T ainv = T(1);
+    if (sc.on) ainv = (T)(1.0 / (sc.alpha_dev ? *sc.alpha_dev : sc.alpha_host));
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) {
+            const int gm = m0 + ty * TM + i, gn = n0 + tx * TN + jj;
+            if (gm < a.M && gn < a.N) {
+                const long long off = (long long)gm * a.sCm + (long long)gn * a.sCn;
+                T v = acc[0][i][jj];
+                if (sc.on) {
+                    long long lin = off + (long long)b * a.sCb;
+                    const int i0 = (int)(lin % sc.n1[0]);
+                    lin /= sc.n1[0];
+                    const int i1 = (int)(lin % sc.n1[1]);
+                    T lsum = l0[i0] + l1[i1];
+                    if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                    v = v * ainv / lsum;
+                }
+                C[off] = v;
+            }
+        }
+}
+
 // ---- tensor-core variant of the FP32 pass (tcgen05, 3xTF32) ------------------
 // C = A B on the 5th-generation tensor cores.  Each operand is split as x = hi + lo
 // with hi = x rounded to TF32 (10-bit mantissa) and lo = x - hi (exact in FP32);
@@ -1612,17 +1762,24 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t last_bar = smem_addr(&mbar[(nch - 1) % nbuf]);
     const uint32_t last_par = (uint32_t)(((nch - 1) / nbuf) & 1);
     ok = mbar_wait(last_bar, last_par) && ok;
-    if (!ok) mbar_wait(last_bar, last_par);               // drain the MMAs in flight before TMEM is read/freed
+    if (!ok) mbar_wait(last_bar, last_par);               // one more bounded wait for the MMAs in flight
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // TMEM -> shared output tile [BM][BN + 1] (reuses the raw panels) -> global
+    // TMEM -> shared output tile [BM][BN + 1] (reuses the raw panels) -> global.  After a
+    // timed-out wait the accumulator is not read at all: the tile is written as NaN, which
+    // the solver's finiteness checks report as a failed solve.
     float* Cs = As;
     if (warp < 4) {
-        uint32_t v[BN];
-        tmem_ld_row<BN>(tmem + ((uint32_t)(warp * 32) << 16), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int r = warp * 32 + lane;
+        if (__all_sync(0xffffffffu, ok)) {        // warp-uniform: tcgen05.ld is a warp-wide instruction
+            uint32_t v[BN];
+            tmem_ld_row<BN>(tmem + ((uint32_t)(warp * 32) << 16), v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < BN; ++j) Cs[r * (BN + 1) + j] = ok ? __uint_as_float(v[j]) : __int_as_float(0x7fc00000);
+            for (int j = 0; j < BN; ++j) Cs[r * (BN + 1) + j] = __uint_as_float(v[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < BN; ++j) Cs[r * (BN + 1) + j] = __int_as_float(0x7fc00000);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1672,12 +1829,22 @@ static cudaError_t launch_gemm_tc(const GemmArgs& a, const float* A, const float
 // (autotune_fdm).  FP32 passes are latency-bound (few, short K loops), FP64
 // passes are FP64-ALU-bound (~1/64 of the FP32 rate), so the candidates differ.
 template <typename T, int BM_, int BN_, int TM_, int TN_, int KS_>
-struct Tile { static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, KS = KS_; };
+struct Tile { static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, KS = KS_, PIPE = 0; };
+// the pipelined K-chunked kernel (k_gemm_pipe) with the same parameters
+template <typename T, int BM_, int BN_, int TM_, int TN_, int KS_>
+struct PTile { static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, KS = KS_, PIPE = 1; };
 
 template <typename T, typename C>
 static cudaError_t launch_tile(const GemmArgs& a, const T* A, const T* B, T* Cp, const FdmScale& sc, const T* l0,
                                const T* l1, const T* l2, cudaStream_t s, const int* skip, const Bat& bt) {
     constexpr int BM = C::BM, BN = C::BN, TM = C::TM, TN = C::TN, KS = C::KS;
+    if constexpr (C::PIPE) {
+        dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch * bt.np);
+        k_gemm_pipe<T, BM, BN, TM, TN, KS><<<grid, (BM / TM) * (BN / TN), 0, s>>>(a, A, B, Cp, sc, l0, l1, l2, skip,
+                                                                                bt);
+        note_launch();
+        return cudaGetLastError();
+    }
     const size_t red = (size_t)(KS - 1) * (BM / TM) * (BN / TN) * TM * TN * sizeof(T);
     const size_t smem = std::max((size_t)a.K * (BM + BN) * sizeof(T), red);
     if (smem <= 200 * 1024) {
@@ -1697,7 +1864,8 @@ static cudaError_t launch_tile(const GemmArgs& a, const T* A, const T* B, T* Cp,
 // KS add the same products in the same order, so they give the same bits.
 using F32Tiles = std::tuple<Tile<float, 32, 16, 4, 2, 4>, Tile<float, 32, 32, 4, 2, 2>, Tile<float, 32, 16, 4, 2, 2>,
                             Tile<float, 16, 16, 2, 2, 4>, Tile<float, 32, 32, 4, 2, 4>, Tile<float, 64, 32, 8, 4, 4>,
-                            Tile<float, 64, 32, 8, 4, 2>, Tile<float, 64, 64, 8, 8, 4>>;
+                            Tile<float, 64, 32, 8, 4, 2>, Tile<float, 64, 64, 8, 8, 4>, PTile<float, 64, 64, 4, 4, 4>,
+                            PTile<float, 32, 64, 4, 4, 4>, PTile<float, 64, 64, 4, 4, 2>, PTile<float, 32, 64, 4, 4, 2>>;
 using F64Tiles = std::tuple<Tile<double, 16, 16, 2, 2, 1>, Tile<double, 16, 16, 2, 2, 2>,
                             Tile<double, 32, 16, 4, 2, 1>, Tile<double, 16, 8, 2, 2, 2>>;
 template <typename T>
@@ -1752,8 +1920,9 @@ static void configure_tiles() {
     using Set = typename TileSet<T>::type;
     if constexpr (I < std::tuple_size<Set>::value) {
         using C = typename std::tuple_element<I, Set>::type;
-        cudaFuncSetAttribute(k_gemm_fullk<T, C::BM, C::BN, C::TM, C::TN, C::KS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if constexpr (!C::PIPE)
+            cudaFuncSetAttribute(k_gemm_fullk<T, C::BM, C::BN, C::TM, C::TN, C::KS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         configure_tiles<T, I + 1>();
     }
 }

@@ -1788,8 +1788,9 @@ hpg_status solve_group(hpg_ctx* home, hpg_ctx* ctx, std::vector<Problem*>& ps, s
         st.final_residual = normF[i];
         st.status = status[i];
         st.kernel_launches = launches / np + (i < launches % np ? 1 : 0);   // the group's launches, shared out
-        st.fdm_tile_f32 = ps[i]->D.gf.gemm_cfg;
-        st.fdm_tile_f64 = ps[i]->D.gd.gemm_cfg;
+        // the FDM pass variant the group ran (same summation order as the problem's own)
+        st.fdm_tile_f32 = Gp.tuned_f ? Gp.gf.gemm_cfg : ps[i]->D.gf.gemm_cfg;
+        st.fdm_tile_f64 = Gp.tuned_d ? Gp.gd.gemm_cfg : ps[i]->D.gd.gemm_cfg;
         st.h2d_bytes = ps[i]->h2d_bytes;
         st.solve_ms = ms;
         ps[i]->solved = true;
