@@ -192,7 +192,10 @@ void hpg_default_params(hpg_params* p);
 
 /* Uniform tensor-product mesh of (lo[j], hi[j]) with cells[j] cells in
  * direction j < dim (dim 2 or 3), partial degree p for u, constraint kind.
- * Obstacle kinds need 2 <= p <= 11; gradient needs 1 <= p <= 10.  The psi
+ * Obstacle kinds need 2 <= p <= 33; gradient needs 1 <= p <= 32, and one cell's
+ * latent coefficients and Gauss values must fit the per-cell kernels' shared memory
+ * (200 KB: 2 n^d + n^2 doubles, and 6 nb + 2 n^2 for the cell operators), which caps
+ * p near 15 for 3D obstacles and 10 for 3D gradient constraints.  The psi
  * pairing is the paper's (Section 4.1: degree p-2; Section 4.2: degree p-1).
  * Returns a problem id in *pid (valid until hpg_problem_free/hpg_destroy). */
 hpg_status hpg_problem_create(hpg_ctx* ctx, int dim, const double* lo, const double* hi,

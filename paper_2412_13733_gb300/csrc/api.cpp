@@ -143,7 +143,23 @@ hpg_status hpg_problem_create(hpg_ctx* ctx, int dim, const double* lo, const dou
     if (dim != 2 && dim != 3) { ctx->err = "dim must be 2 or 3"; return HPG_ERR_ARG; }
     if (kind != HPG_OBSTACLE_UPPER && kind != HPG_OBSTACLE_LOWER && kind != HPG_GRADIENT) return HPG_ERR_ARG;
     const bool grad = kind == HPG_GRADIENT;
-    if (grad ? (p < 1 || p > 10) : (p < 2 || p > 11)) { ctx->err = "degree out of range"; return HPG_ERR_ARG; }
+    if (grad ? (p < 1 || p > hpg::kMaxN) : (p < 2 || p > hpg::kMaxN + 1)) {
+        ctx->err = "degree out of range";
+        return HPG_ERR_ARG;
+    }
+    {
+        // the per-cell kernels hold one cell's latent coefficients (all components) and
+        // Gauss values in shared memory: eval 2 nc n^d + n^2 doubles, the cell operators
+        // two groups of 3 nb + n^2 values
+        const long long n = grad ? p : p - 1, nc = grad ? dim : 1;
+        long long nloc = 1;
+        for (int j = 0; j < dim; ++j) nloc *= n;
+        const long long need = std::max((2 * nc * nloc + n * n) * 8, 2 * (3 * nc * nloc + n * n) * 8);
+        if (need > (long long)hpg::kCellSmemMax) {
+            ctx->err = "degree too high for this dimension (per-cell shared memory)";
+            return HPG_ERR_ARG;
+        }
+    }
     for (int j = 0; j < dim; ++j) {
         if (cells[j] < 1 || cells[j] > 4096 || !(hi[j] > lo[j])) { ctx->err = "bad mesh"; return HPG_ERR_ARG; }
         if (cells[j] * p - 1 < 1) { ctx->err = "no interior dofs"; return HPG_ERR_ARG; }

@@ -13,7 +13,9 @@
 namespace hpg {
 
 constexpr int kMaxDim = 3;
-constexpr int kMaxN = 11;       // coefficients per direction per cell (n = p-1 or p)
+constexpr int kMaxN = 32;       // coefficients per direction per cell (n = p-1 or p)
+// largest dynamic shared memory a per-cell kernel of the path may ask for (bytes)
+constexpr size_t kCellSmemMax = 200 * 1024;
 constexpr int kEll = 8;         // padded width of the 1D stencils
 
 // ---------------------------------------------------------------- host math

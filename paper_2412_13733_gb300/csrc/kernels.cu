@@ -2967,6 +2967,9 @@ static void allow_big_smem(F* kernel) {
 void configure_kernels() {
     configure_tiles<float>();
     configure_tiles<double>();
+    // per-cell kernels of high degrees (one cell's coefficients and Gauss values)
+    allow_big_smem(k_eval);
+    allow_big_smem(k_project);
     // tiled u-row kernels (stencil tile + staged value boxes) and cell operators
     allow_big_smem(k_urow<2, double, double, double, true, true, true>);
     allow_big_smem(k_urow<3, double, double, double, true, true, true>);

@@ -43,6 +43,19 @@ def case(name):
         w = W.workload("torsion_small")
         w.update(name=name, dim=3, breakpoints=[W.uniform(0, 1, 2), W.uniform(0, 1, 3), W.uniform(0, 1, 2)], p=3)
         return w
+    if name == "radial_2x2_p16":
+        # high degree: 15 x 15 latent coefficients per cell (nb = 225, block factorisation)
+        w = W.workload("radial4")
+        w.update(name=name, breakpoints=[W.uniform(-2, 2, 2)] * 2, p=16, m=2)
+        return w
+    if name == "torsion_2x2_p12":
+        w = W.workload("torsion_small")
+        w.update(name=name, breakpoints=[W.uniform(0, 1, 2)] * 2, p=12)
+        return w
+    if name == "sine3d_1x1x2_p9":
+        w = W.workload("sine3d_small")
+        w.update(name=name, breakpoints=[W.uniform(0, 1, 1), W.uniform(0, 1, 1), W.uniform(0, 1, 2)], p=9)
+        return w
     if name.startswith("box3d_"):
         w = W.workload(name)
         w["tol"] = 1e-10          # parity gates at the usual Newton tolerance

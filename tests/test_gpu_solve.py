@@ -233,3 +233,24 @@ def test_changing_beta_after_a_solve(ctx, precision):
     assert np.array_equal(P.u(), Q.u())
     P.free()
     Q.free()
+
+
+@pytest.mark.parametrize("name", ["radial_2x2_p16", "torsion_2x2_p12", "sine3d_1x1x2_p9"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_high_degree_matches_oracle(ctx, name, precision):
+    """Degrees beyond the configured workloads (2D p = 16, gradient p = 12, 3D p = 9):
+    the same dense sum-factorised kernels and block factorisations, the same gates."""
+    o, r = oracle_solution(name)
+    P, u, psi, st = gpu_solve(ctx, case(name), precision)
+    _check(o, r, u, psi, st, 1e-9 if precision == 0 else 1e-8, 1e-8 if precision == 0 else 1e-7)
+    P.free()
+
+
+def test_degree_limits_are_checked(ctx):
+    from paper_2412_13733_gb300 import hpg
+    with pytest.raises(hpg.HpgError):
+        hpg.Problem(ctx, 2, [0, 0], [1, 1], [2, 2], 34, hpg.HPG_OBSTACLE_UPPER)
+    with pytest.raises(hpg.HpgError):             # one 3D cell's coefficients exceed shared memory
+        hpg.Problem(ctx, 3, [0, 0, 0], [1, 1, 1], [1, 1, 1], 20, hpg.HPG_OBSTACLE_UPPER)
+    P = hpg.Problem(ctx, 2, [0, 0], [1, 1], [1, 1], 33, hpg.HPG_OBSTACLE_UPPER)
+    P.free()
