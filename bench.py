@@ -645,6 +645,36 @@ def main():
                 P.free()
             strategies[f"p={p_deg}, {m_cells}^3 cells"] = entry
 
+    # Section 6.5's study of inverting A_alpha iteratively: A x = 1 on the 3D box by CG
+    # preconditioned with the block Jacobi of hpg_stiffness_solve_pcg, absolute and
+    # relative tolerance 1e-6 (the paper: Ruge-Stueben AMG-CG and a Cholesky factorisation);
+    # beside it one exact fast-diagonalisation apply of the same A
+    ainv_table = None
+    if not args.no_strategies:
+        ainv_table = {}
+        for m_cells in (4, 8):
+            for p_deg in range(2, 8):
+                wb = W.workload(f"box3d_p{p_deg}_m{m_cells}")
+                P = hpg.from_workload(ctx, wb)
+                P.set_state(np.zeros(P.n_u_full), np.zeros(P.n_psi), np.zeros(P.n_psi), 1.0)
+                ones = np.ones(P.n_u)
+                P.stiffness_solve_pcg(ones, 1.0, rtol=1e-6, atol=1e-6)       # set-up and warm-up
+                t0 = time.perf_counter()
+                _, its = P.stiffness_solve_pcg(ones, 1.0, rtol=1e-6, atol=1e-6)
+                t_cg = time.perf_counter() - t0
+                P.launch_kernel("fdm", hpg.HPG_FP64, 10)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.launch_kernel("fdm", hpg.HPG_FP64, 10)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ainv_table[f"p={p_deg}, {m_cells}^3 cells"] = {"pcg_iterations": its, "pcg_s": t_cg,
+                                                               "fdm_apply_s": e0.elapsed_time(e1) / 10 / 1000.0,
+                                                               "n_u": P.n_u}
+                P.free()
+
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = {"requests": args.serve_requests, "workers": B,
@@ -706,7 +736,8 @@ def main():
                 # FDM pass variant picked by the set-up autotuner (hpg_fdm_tile_count; the last two FP32
                 # variants are the tcgen05 kernels); pass it to --fdm-tile to reproduce a run under ncu
                 "fdm_variant": {"mixed": head["fdm_variant"], "fp64": fp["fdm_variant"] if fp else None},
-                "other_workloads": others, "solver_strategies": strategies, "serving": serving, "clocks": clocks,
+                "other_workloads": others, "solver_strategies": strategies, "ainv_pcg_table": ainv_table,
+                "serving": serving, "clocks": clocks,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     bad = [k for k, r in results.items() if r["accuracy"] is not None and not r["accuracy"]["ok"]]

@@ -172,6 +172,28 @@ cudaError_t launch_newton_apply(const Geo<double>& g, const double* gw, double a
                                 const double* x, double* y, cudaStream_t s, const Bat& bt = Bat{});
 
 
+// ---- iterative A_alpha^{-1}: preconditioned CG on the stiffness matrix
+// Block-Jacobi preconditioner over the entities of the hierarchical basis (see
+// AinvPrecond): geometry of the blocks as the kernels need it.
+struct PcgGeo {
+    int d, nbub;
+    int m[kMaxDim], n1[kMaxDim], nv[kMaxDim];
+    int bsize[8];
+    long long eoff[9];       // first entity of type t (types 1 .. 2^d - 1); eoff[2^d] = all
+    long long boff[8];
+    int bmax;
+    const double* Binv;
+};
+// z = alpha^{-1} B_e^{-1} r on the dofs of every edge/face/interior entity e
+cudaError_t launch_ainv_blocks(const PcgGeo& pg, double alpha, const double* r, double* z, cudaStream_t s);
+// rc = r at the vertex (all-hat) dofs; z at the vertex dofs = zc
+cudaError_t launch_vertex_gather(const PcgGeo& pg, const double* r, double* rc, long long nc, cudaStream_t s);
+cudaError_t launch_vertex_scatter(const PcgGeo& pg, const double* zc, double* z, long long nc, cudaStream_t s);
+// y = alpha A x (interior u, FP64, matrix-free)
+cudaError_t launch_aapply(const Geo<double>& g, double alpha, const double* x, double* y, cudaStream_t s);
+// partial dot products of a and b into part (count through nparts)
+cudaError_t launch_dot(const double* a, const double* b, long long n, double* part, int* nparts, cudaStream_t s);
+
 // ---- vector helpers (FP64 unless typed)
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin* x, Tout* y, long long n, cudaStream_t s, const Bat& bt = Bat{});

@@ -55,6 +55,22 @@ struct Dir1D {
     int int_of_glob(int g) const;   // global -> interior (-1 for boundary)
 };
 
+// Preconditioner of the stiffness matrix A for the iterative (inexact) A_alpha^{-1}:
+// block Jacobi over the hierarchical basis split by entity -- the vertex (all-hat)
+// functions form one block, the coarse Q1 stiffness, solved exactly by fast
+// diagonalisation of the 1D hat pencils; every edge, face and cell interior carries the
+// block of its bubble functions, solved with a dense inverse.  On a uniform mesh all
+// entities of one type (which axes carry bubbles) share one block.
+struct AinvPrecond {
+    bool built = false;
+    int nv[kMaxDim] = {1, 1, 1};                 // interior vertices per axis (m_j - 1)
+    std::vector<double> Vc[kMaxDim], lamc[kMaxDim];
+    int bsize[8] = {};                           // block size of type t (bubble-axis mask t)
+    long long nent[8] = {};                      // entities of type t
+    long long boff[8] = {};                      // offset of type t's inverse block in Binv
+    std::vector<double> Binv;                    // the inverse blocks, row-major, by type
+};
+
 // Everything the device path needs, computed on the host at setup.
 struct HostProblem {
     int d = 2, p = 2, n = 1, kind = 0, ncomp = 1;
@@ -79,9 +95,12 @@ struct HostProblem {
     std::vector<double> rB;              // B_g^T u_g (psi rows)
     bool has_phi = false;
     std::vector<double> alphas;
+    AinvPrecond ap;
 };
 
 void build_dir1d(Dir1D& D, int m, int p, int n, double lo, double hi);
+void pencil_eigen(int N, const std::vector<double>& Ad, const std::vector<double>& Md, std::vector<double>& V,
+                  std::vector<double>& lam);
 void build_problem_constants(HostProblem& P);
 // Quadrature points of the latent rule, Nq x d, cell-major, x fastest.
 void latent_points(const HostProblem& P, std::vector<double>& pts);
@@ -89,6 +108,8 @@ void compute_rhs(HostProblem& P, hpg_field_fn f, void* user, bool is_const, doub
 void compute_phi(HostProblem& P, const double* phi_q);
 void compute_lifting(HostProblem& P, hpg_field_fn g, void* user);
 double eval_u_point(const HostProblem& P, const std::vector<double>& ufull, const double* x);
+// Build P.ap (coarse pencils and entity blocks of the stiffness preconditioner).
+void build_ainv_precond(HostProblem& P);
 // e^T (M_1 (x) ... (x) M_d) e for a full u-coefficient vector e: the squared L2(Omega)
 // norm of the field, with the exact 1D mass matrices of Section 3.
 double mass_norm2(const HostProblem& P, const std::vector<double>& e);

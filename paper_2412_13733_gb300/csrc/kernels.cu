@@ -2959,6 +2959,131 @@ cudaError_t launch_maxpy(double* w, const double* V, long long ld, const double*
     return cudaGetLastError();
 }
 
+// ---- iterative A_alpha^{-1}: block-Jacobi preconditioner and helpers -----------
+__device__ __forceinline__ long long pcg_dof(const PcgGeo& pg, int t, const int* coord, int l) {
+    // 1D interior index per axis: vertex v -> v; bubble b of cell c -> (m - 1) + c nbub + b
+    long long I = 0, stride = 1;
+    int rl = l;
+    for (int j = 0; j < pg.d; ++j) {
+        int i1;
+        if ((t >> j) & 1) {
+            const int b = rl % pg.nbub;
+            rl /= pg.nbub;
+            i1 = pg.m[j] - 1 + coord[j] * pg.nbub + b;
+        } else {
+            i1 = coord[j];
+        }
+        I += (long long)i1 * stride;
+        stride *= pg.n1[j];
+    }
+    return I;
+}
+
+// one block per entity: gather its residual entries, multiply by the type's inverse block
+__global__ void __launch_bounds__(128) k_ainv_blocks(PcgGeo pg, double ainv, const double* __restrict__ r,
+                                                     double* __restrict__ z) {
+    extern __shared__ double smp[];
+    const long long ent = blockIdx.x;
+    const int ntyp = 1 << pg.d;
+    int t = 1;
+    while (t + 1 < ntyp && ent >= pg.eoff[t + 1]) ++t;
+    long long e = ent - pg.eoff[t];
+    int coord[kMaxDim] = {0, 0, 0};
+    for (int j = 0; j < pg.d; ++j) {
+        const long long ext = ((t >> j) & 1) ? pg.m[j] : pg.nv[j];
+        coord[j] = (int)(e % ext);
+        e /= ext;
+    }
+    const int nb = pg.bsize[t];
+    double* rs = smp;
+    long long* idx = reinterpret_cast<long long*>(smp + pg.bmax);
+    for (int l = threadIdx.x; l < nb; l += blockDim.x) {
+        const long long I = pcg_dof(pg, t, coord, l);
+        idx[l] = I;
+        rs[l] = r[I];
+    }
+    __syncthreads();
+    const double* Bi = pg.Binv + pg.boff[t];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < nb; ++k) acc += Bi[(size_t)i * nb + k] * rs[k];
+        z[idx[i]] = ainv * acc;
+    }
+}
+
+cudaError_t launch_ainv_blocks(const PcgGeo& pg, double alpha, const double* r, double* z, cudaStream_t s) {
+    const long long ne = pg.eoff[1 << pg.d] - pg.eoff[1];
+    if (ne <= 0) return cudaSuccess;
+    const size_t smem = (size_t)pg.bmax * (sizeof(double) + sizeof(long long));
+    k_ainv_blocks<<<(unsigned)ne, 128, smem, s>>>(pg, 1.0 / alpha, r, z);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_vertex_move(PcgGeo pg, const double* __restrict__ src, double* __restrict__ dst, long long nc,
+                              int gather) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int coord[kMaxDim] = {0, 0, 0};
+    long long e = c;
+    for (int j = 0; j < pg.d; ++j) {
+        coord[j] = (int)(e % pg.nv[j]);
+        e /= pg.nv[j];
+    }
+    const long long I = pcg_dof(pg, 0, coord, 0);
+    if (gather) dst[c] = src[I];
+    else dst[I] = src[c];
+}
+
+cudaError_t launch_vertex_gather(const PcgGeo& pg, const double* r, double* rc, long long nc, cudaStream_t s) {
+    if (nc <= 0) return cudaSuccess;
+    k_vertex_move<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(pg, r, rc, nc, 1);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vertex_scatter(const PcgGeo& pg, const double* zc, double* z, long long nc, cudaStream_t s) {
+    if (nc <= 0) return cudaSuccess;
+    k_vertex_move<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(pg, zc, z, nc, 0);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aapply(const Geo<double>& g, double alpha, const double* x, double* y, cudaStream_t s) {
+    if (g.d == 2)
+        k_urow<2, double, double, double, true, false, false><<<utile_grid<2>(g.n1), 256,
+                                                                urow_smem<2>(g, true, false), s>>>(
+            g, alpha, x, 0.0, (const double*)nullptr, (const double*)nullptr, nullptr, nullptr, nullptr, nullptr, y,
+            nullptr, Bat{}, 0);
+    else
+        k_urow<3, double, double, double, true, false, false><<<utile_grid<3>(g.n1), 256,
+                                                                urow_smem<3>(g, true, false), s>>>(
+            g, alpha, x, 0.0, (const double*)nullptr, (const double*)nullptr, nullptr, nullptr, nullptr, nullptr, y,
+            nullptr, Bat{}, 0);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                      double* __restrict__ part) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v += a[i] * b[i];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+cudaError_t launch_dot(const double* a, const double* b, long long n, double* part, int* nparts, cudaStream_t s) {
+    int nb = (int)((n + 255) / 256);
+    if (nb > 1024) nb = 1024;
+    if (nb < 1) nb = 1;
+    k_dot<<<nb, 256, 0, s>>>(a, b, n, part);
+    note_launch();
+    *nparts = nb;
+    return cudaGetLastError();
+}
+
 template <typename F>
 static void allow_big_smem(F* kernel) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -2975,6 +3100,9 @@ void configure_kernels() {
     allow_big_smem(k_urow<3, double, double, double, true, true, true>);
     allow_big_smem(k_urow<2, double, double, double, false, true, false>);
     allow_big_smem(k_urow<3, double, double, double, false, true, false>);
+    allow_big_smem(k_urow<2, double, double, double, true, false, false>);
+    allow_big_smem(k_urow<3, double, double, double, true, false, false>);
+    allow_big_smem(k_ainv_blocks);
     allow_big_smem(k_urow<2, float, float, float, false, true, false>);
     allow_big_smem(k_urow<3, float, float, float, false, true, false>);
     allow_big_smem(k_urow<2, float, float, double, false, true, false>);

@@ -206,6 +206,45 @@ static void build_dir1d_uncached(Dir1D& D, int m, int p, int n, double lo, doubl
 
 // The 1D operators (and their fast-diagonalisation eigenpairs, the costly part)
 // depend only on (m, p, n, lo, hi); many problems share them, so keep a cache.
+// Generalised symmetric eigenpairs of a 1D pencil (A, M), M SPD, dense row-major N x N:
+// M = L L^T, L^{-1} A L^{-T} = Q diag(lam) Q^T, V = L^{-T} Q, so V^T M V = I and
+// V^T A V = diag(lam) (V row-major, column j = vector j).
+void pencil_eigen(int N, const std::vector<double>& Ad, const std::vector<double>& Md, std::vector<double>& V,
+                  std::vector<double>& lam) {
+    std::vector<double> L = Md;
+    if (!cholesky(N, L)) throw std::runtime_error("1D mass matrix not SPD");
+    // C = L^{-1} A L^{-T}: first X = L^{-1} A (forward substitution on columns), then C = X L^{-T}
+    std::vector<double> X = Ad;
+    for (int col = 0; col < N; ++col)
+        for (int i = 0; i < N; ++i) {
+            double s = X[(size_t)i * N + col];
+            for (int k = 0; k < i; ++k) s -= L[(size_t)i * N + k] * X[(size_t)k * N + col];
+            X[(size_t)i * N + col] = s / L[(size_t)i * N + i];
+        }
+    std::vector<double> C((size_t)N * N);
+    for (int row = 0; row < N; ++row)
+        for (int i = 0; i < N; ++i) {
+            double s = X[(size_t)row * N + i];
+            for (int k = 0; k < i; ++k) s -= L[(size_t)i * N + k] * C[(size_t)row * N + k];
+            C[(size_t)row * N + i] = s / L[(size_t)i * N + i];
+        }
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < i; ++j) {
+            double s = 0.5 * (C[(size_t)i * N + j] + C[(size_t)j * N + i]);
+            C[(size_t)i * N + j] = C[(size_t)j * N + i] = s;
+        }
+    std::vector<double> Q;
+    if (!symmetric_eigen(N, C, lam, Q)) throw std::runtime_error("eigen-decomposition failed");
+    // V = L^{-T} Q: back substitution per column
+    V.assign((size_t)N * N, 0.0);
+    for (int col = 0; col < N; ++col)
+        for (int i = N - 1; i >= 0; --i) {
+            double s = Q[(size_t)i * N + col];
+            for (int k = i + 1; k < N; ++k) s -= L[(size_t)k * N + i] * V[(size_t)k * N + col];
+            V[(size_t)i * N + col] = s / L[(size_t)i * N + i];
+        }
+}
+
 void build_dir1d(Dir1D& D, int m, int p, int n, double lo, double hi) {
     static std::mutex mu;
     static std::map<std::tuple<int, int, int, double, double>, Dir1D> cache;
@@ -298,38 +337,7 @@ static void build_dir1d_uncached(Dir1D& D, int m, int p, int n, double lo, doubl
         for (int e = 0; e < D.Mi.cnt[i]; ++e) Md[(size_t)i * N + D.Mi.col[(size_t)i * kEll + e]] += D.Mi.val[(size_t)i * kEll + e];
         for (int e = 0; e < D.Ai.cnt[i]; ++e) Ad[(size_t)i * N + D.Ai.col[(size_t)i * kEll + e]] += D.Ai.val[(size_t)i * kEll + e];
     }
-    std::vector<double> L = Md;
-    if (!cholesky(N, L)) throw std::runtime_error("1D mass matrix not SPD");
-    // C = L^{-1} A L^{-T}: first X = L^{-1} A (forward substitution on columns), then C = X L^{-T}
-    std::vector<double> X = Ad;
-    for (int col = 0; col < N; ++col)
-        for (int i = 0; i < N; ++i) {
-            double s = X[(size_t)i * N + col];
-            for (int k = 0; k < i; ++k) s -= L[(size_t)i * N + k] * X[(size_t)k * N + col];
-            X[(size_t)i * N + col] = s / L[(size_t)i * N + i];
-        }
-    std::vector<double> C((size_t)N * N);
-    for (int row = 0; row < N; ++row)
-        for (int i = 0; i < N; ++i) {
-            double s = X[(size_t)row * N + i];
-            for (int k = 0; k < i; ++k) s -= L[(size_t)i * N + k] * C[(size_t)row * N + k];
-            C[(size_t)row * N + i] = s / L[(size_t)i * N + i];
-        }
-    for (int i = 0; i < N; ++i)
-        for (int j = 0; j < i; ++j) {
-            double s = 0.5 * (C[(size_t)i * N + j] + C[(size_t)j * N + i]);
-            C[(size_t)i * N + j] = C[(size_t)j * N + i] = s;
-        }
-    std::vector<double> Q;
-    if (!symmetric_eigen(N, C, D.lam, Q)) throw std::runtime_error("eigen-decomposition failed");
-    // V = L^{-T} Q: back substitution per column
-    D.V.assign((size_t)N * N, 0.0);
-    for (int col = 0; col < N; ++col)
-        for (int i = N - 1; i >= 0; --i) {
-            double s = Q[(size_t)i * N + col];
-            for (int k = i + 1; k < N; ++k) s -= L[(size_t)k * N + i] * D.V[(size_t)k * N + col];
-            D.V[(size_t)i * N + col] = s / L[(size_t)i * N + i];
-        }
+    pencil_eigen(N, Ad, Md, D.V, D.lam);
     // self-check: V^T A V = diag(lam), V^T M V = I
     double err = 0.0, scale = 1.0;
     for (double l : D.lam) scale = std::max(scale, std::fabs(l));
@@ -821,6 +829,100 @@ double mass_norm2(const HostProblem& P, const std::vector<double>& e) {
     double s = 0.0;
     for (size_t i = 0; i < e.size(); ++i) s += e[i] * cur[i];
     return s;
+}
+
+}  // namespace hpg
+
+namespace hpg {
+
+namespace {
+// entry (r, c) of a padded-ELL operator (0 if absent)
+double ell_at(const Ell& E, int r, int c) {
+    double v = 0.0;
+    for (int e = 0; e < E.cnt[r]; ++e)
+        if (E.col[(size_t)r * kEll + e] == c) v += E.val[(size_t)r * kEll + e];
+    return v;
+}
+}  // namespace
+
+void build_ainv_precond(HostProblem& P) {
+    AinvPrecond& ap = P.ap;
+    if (ap.built) return;
+    const int d = P.d, nbub = P.p - 1;
+    // coarse space: the interior vertex hats of each axis, interior 1D indices 0 .. m-2
+    for (int j = 0; j < d; ++j) {
+        const Dir1D& D = P.dir[j];
+        const int nv = D.m - 1;
+        ap.nv[j] = nv;
+        if (nv < 1) continue;
+        std::vector<double> Ad((size_t)nv * nv, 0.0), Md((size_t)nv * nv, 0.0);
+        for (int a = 0; a < nv; ++a)
+            for (int b = 0; b < nv; ++b) {
+                Ad[(size_t)a * nv + b] = ell_at(D.Ai, a, b);
+                Md[(size_t)a * nv + b] = ell_at(D.Mi, a, b);
+            }
+        pencil_eigen(nv, Ad, Md, ap.Vc[j], ap.lamc[j]);
+    }
+    // entity blocks: type t = mask of the axes that carry bubbles (t = 0 is the coarse space)
+    size_t off = 0;
+    for (int t = 1; t < (1 << d); ++t) {
+        int nb = 1;
+        long long ne = 1;
+        for (int j = 0; j < d; ++j) {
+            const bool bub = (t >> j) & 1;
+            if (bub) nb *= nbub;
+            ne *= bub ? P.dir[j].m : P.dir[j].m - 1;
+        }
+        ap.bsize[t] = nb;
+        ap.nent[t] = (nbub > 0) ? ne : 0;
+        ap.boff[t] = (long long)off;
+        if (ap.nent[t] == 0) continue;
+        // B[l][l'] = sum_k prod_j (k == j ? A_j : M_j)(e_j(l), e_j(l')): hat axes take the
+        // diagonal entry of an interior vertex, bubble axes the bubble block of cell 0
+        // (identical for every vertex and cell of a uniform mesh)
+        std::vector<double> B((size_t)nb * nb, 0.0);
+        for (int l = 0; l < nb; ++l)
+            for (int lp = 0; lp < nb; ++lp) {
+                int bl[kMaxDim], blp[kMaxDim];
+                int rl = l, rlp = lp;
+                for (int j = 0; j < d; ++j) {
+                    if ((t >> j) & 1) { bl[j] = rl % nbub; rl /= nbub; blp[j] = rlp % nbub; rlp /= nbub; }
+                    else { bl[j] = blp[j] = -1; }
+                }
+                double sum = 0.0;
+                for (int k = 0; k < d; ++k) {
+                    double prod = 1.0;
+                    for (int j = 0; j < d; ++j) {
+                        const Dir1D& D = P.dir[j];
+                        const Ell& E = (k == j) ? D.Ai : D.Mi;
+                        const int r = bl[j] < 0 ? 0 : D.m - 1 + bl[j];
+                        const int c = blp[j] < 0 ? 0 : D.m - 1 + blp[j];
+                        prod *= ell_at(E, r, c);
+                    }
+                    sum += prod;
+                }
+                B[(size_t)l * nb + lp] = sum;
+            }
+        // inverse through the Cholesky factor: B^{-1} = L^{-T} L^{-1}
+        std::vector<double> L = B;
+        if (!cholesky(nb, L)) throw std::runtime_error("stiffness entity block not SPD");
+        std::vector<double> X((size_t)nb * nb, 0.0);   // X = L^{-1}
+        for (int c = 0; c < nb; ++c)
+            for (int i = 0; i < nb; ++i) {
+                double v = (i == c) ? 1.0 : 0.0;
+                for (int k = 0; k < i; ++k) v -= L[(size_t)i * nb + k] * X[(size_t)k * nb + c];
+                X[(size_t)i * nb + c] = v / L[(size_t)i * nb + i];
+            }
+        ap.Binv.resize(off + (size_t)nb * nb);
+        for (int i = 0; i < nb; ++i)
+            for (int c = 0; c < nb; ++c) {
+                double v = 0.0;
+                for (int k = std::max(i, c); k < nb; ++k) v += X[(size_t)k * nb + i] * X[(size_t)k * nb + c];
+                ap.Binv[off + (size_t)i * nb + c] = v;
+            }
+        off += (size_t)nb * nb;
+    }
+    ap.built = true;
 }
 
 }  // namespace hpg

@@ -336,7 +336,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
         int n1v[kMaxDim] = {1, 1, 1};
         for (int j = 0; j < d; ++j) n1v[j] = H.dir[j].n1;
         const int nres = n_res_partials_for(d, n1v, (long long)Npsi);
-        sa(D.part, std::max(nres, 1024));
+        sa(D.part, std::max(nres, 2048));
         sa(D.scal, 16);
         sa(D.flag, 4);
         // GMRES
@@ -867,7 +867,14 @@ static hpg_status fg_precond(hpg_ctx* ctx, Problem& P, double alpha, const doubl
         P.stats.krylov_total += its;
         return HPG_OK;
     }
-    CK(launch_fdm<double>(g, nullptr, alpha, r, z, D.w1_d, D.w2_d, s));
+    if (P.params.ainv_pcg) {
+        int its = 0;
+        double res = 0.0;
+        CKS(pcg_solve(ctx, P, alpha, r, z, P.params.ainv_rtol, 0.0, 1000, &its, &res));
+        P.stats.ainv_iters += its;
+    } else {
+        CK(launch_fdm<double>(g, nullptr, alpha, r, z, D.w1_d, D.w2_d, s));
+    }
     P.stats.ainv_total += 1;
     const double* rp = r + Nu0;
     if (P.params.strategy == HPG_FGMRES_PLPD) {
@@ -2207,6 +2214,160 @@ hpg_status op_launch_kernel_group(hpg_ctx* ctx, std::vector<Problem*>& ps, int c
     }
     CK(cudaGraphLaunch(it->second.first, s));
     add_kernel_launches(it->second.second);
+    return HPG_OK;
+}
+
+
+// ---- iterative A_alpha^{-1}: preconditioned CG (Section 6.5 compares AMG-preconditioned
+// CG with the Cholesky factorisation of A; here the preconditioner is the block Jacobi of
+// AinvPrecond, every block solved exactly: the vertex block by fast diagonalisation of
+// the Q1 pencils, the edge/face/interior bubble blocks by their dense inverses)
+static hpg_status pcg_setup(hpg_ctx* ctx, Problem& P) {
+    DevState& D = P.D;
+    if (D.pcg_ready) return HPG_OK;
+    HostProblem& H = P.H;
+    build_ainv_precond(H);
+    const AinvPrecond& ap = H.ap;
+    cudaStream_t s = ctx->stream;
+    bool ok = true;
+    const size_t Nu0 = H.Nu0;
+    long long nc0 = 1;
+    for (int j = 0; j < H.d; ++j) nc0 *= ap.nv[j];
+    D.nc0 = nc0;
+    D.pr = dalloc<double>(D, Nu0, ok);
+    D.pz = dalloc<double>(D, Nu0, ok);
+    D.pp = dalloc<double>(D, Nu0, ok);
+    D.pq = dalloc<double>(D, Nu0, ok);
+    D.pxb = dalloc<double>(D, Nu0, ok);
+    D.pbb = dalloc<double>(D, Nu0, ok);
+    D.prc = dalloc<double>(D, (size_t)std::max(nc0, 1LL), ok);
+    D.pzc = dalloc<double>(D, (size_t)std::max(nc0, 1LL), ok);
+    D.pw1 = dalloc<double>(D, (size_t)std::max(nc0, 1LL), ok);
+    D.pw2 = dalloc<double>(D, (size_t)std::max(nc0, 1LL), ok);
+    if (!ok) { ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
+    D.pBinv = upload_vec<double>(D, ap.Binv.empty() ? std::vector<double>(1, 0.0) : ap.Binv, ok, s);
+    PcgGeo& pg = D.pg;
+    pg = PcgGeo{};
+    pg.d = H.d;
+    pg.nbub = H.p - 1;
+    pg.bmax = 1;
+    for (int j = 0; j < kMaxDim; ++j) {
+        pg.m[j] = j < H.d ? H.m[j] : 1;
+        pg.n1[j] = j < H.d ? H.dir[j].n1 : 1;
+        pg.nv[j] = j < H.d ? ap.nv[j] : 1;
+    }
+    const int ntyp = 1 << H.d;
+    pg.eoff[1] = 0;
+    for (int t = 1; t < ntyp; ++t) {
+        pg.bsize[t] = ap.bsize[t];
+        pg.boff[t] = ap.boff[t];
+        pg.eoff[t + 1] = pg.eoff[t] + ap.nent[t];
+        if (ap.nent[t] > 0) pg.bmax = std::max(pg.bmax, ap.bsize[t]);
+    }
+    pg.Binv = D.pBinv;
+    D.gc = D.gd;
+    if (nc0 > 0) {
+        for (int j = 0; j < H.d; ++j) {
+            D.pVc[j] = upload_vec<double>(D, ap.Vc[j], ok, s);
+            D.plamc[j] = upload_vec<double>(D, ap.lamc[j], ok, s);
+            D.gc.n1[j] = ap.nv[j];
+            D.gc.V[j] = D.pVc[j];
+            D.gc.lam[j] = D.plamc[j];
+        }
+        D.gc.Nu0 = nc0;
+        D.gc.gemm_cfg = 0;
+    }
+    if (!ok) { ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
+    CK(cudaStreamSynchronize(s));
+    D.pcg_ready = true;
+    return HPG_OK;
+}
+
+// z = M_alpha^{-1} r for the block-Jacobi preconditioner of A_alpha
+static hpg_status pcg_precond(hpg_ctx* ctx, Problem& P, double alpha, const double* r, double* z) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    CK(launch_ainv_blocks(D.pg, alpha, r, z, s));
+    if (D.nc0 > 0) {
+        CK(launch_vertex_gather(D.pg, r, D.prc, D.nc0, s));
+        CK(launch_fdm<double>(D.gc, nullptr, alpha, D.prc, D.pzc, D.pw1, D.pw2, s));
+        CK(launch_vertex_scatter(D.pg, D.pzc, z, D.nc0, s));
+    }
+    return HPG_OK;
+}
+
+// a . b and, when c is not null, c . c: one synchronisation for both
+static hpg_status pcg_dots(hpg_ctx* ctx, Problem& P, const double* a, const double* b, const double* c, double* ab,
+                           double* cc) {
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long n = (long long)P.H.Nu0;
+    int np = 0;
+    CK(launch_dot(a, b, n, D.part, &np, s));
+    CK(launch_reduce_sum(D.part, np, D.scal + 10, s));
+    if (c) {
+        CK(launch_dot(c, c, n, D.part + 1024, &np, s));
+        CK(launch_reduce_sum(D.part + 1024, np, D.scal + 11, s));
+    }
+    CK(cudaMemcpyAsync(D.h_scal + 10, D.scal + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *ab = D.h_scal[10];
+    if (cc) *cc = D.h_scal[11];
+    return HPG_OK;
+}
+
+hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* b, double* x, double rtol, double atol,
+                     int maxit, int* its, double* res) {
+    CKS(pcg_setup(ctx, P));
+    DevState& D = P.D;
+    cudaStream_t s = ctx->stream;
+    const long long n = (long long)P.H.Nu0;
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    CK(cudaMemcpyAsync(D.pr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double bb = 0.0;
+    CKS(pcg_dots(ctx, P, D.pr, D.pr, nullptr, &bb, nullptr));
+    const double bn = std::sqrt(bb);
+    *its = 0;
+    *res = bn;
+    if (!(bn > 0.0)) return HPG_OK;
+    const double tol = std::max(atol, rtol * bn);
+    CKS(pcg_precond(ctx, P, alpha, D.pr, D.pz));
+    CK(cudaMemcpyAsync(D.pp, D.pz, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double rz = 0.0;
+    CKS(pcg_dots(ctx, P, D.pr, D.pz, nullptr, &rz, nullptr));
+    for (int it = 1; it <= maxit; ++it) {
+        CK(launch_aapply(D.gd, alpha, D.pp, D.pq, s));
+        double pq = 0.0;
+        CKS(pcg_dots(ctx, P, D.pp, D.pq, nullptr, &pq, nullptr));
+        if (!(pq > 0.0)) { ctx->err = "CG breakdown (A_alpha not positive on the search direction)"; return HPG_ERR_NONFINITE; }
+        const double a = rz / pq;
+        CK(launch_axpby(a, D.pp, 1.0, x, n, s));
+        CK(launch_axpby(-a, D.pq, 1.0, D.pr, n, s));
+        CKS(pcg_precond(ctx, P, alpha, D.pr, D.pz));
+        double rz1 = 0.0, rr = 0.0;
+        CKS(pcg_dots(ctx, P, D.pr, D.pz, D.pr, &rz1, &rr));
+        *its = it;
+        *res = std::sqrt(rr);
+        if (!std::isfinite(*res)) { ctx->err = "non-finite CG residual"; return HPG_ERR_NONFINITE; }
+        if (*res <= tol) break;
+        const double beta = rz1 / rz;
+        rz = rz1;
+        CK(launch_axpby(1.0, D.pz, beta, D.pp, n, s));
+    }
+    return HPG_OK;
+}
+
+hpg_status op_stiffness_pcg(hpg_ctx* ctx, Problem& P, double alpha, const double* b, double* x, double rtol,
+                            double atol, int maxit, int* its) {
+    DevState& D = P.D;
+    CKS(pcg_setup(ctx, P));
+    cudaStream_t s = ctx->stream;
+    const long long n = (long long)P.H.Nu0;
+    CK(cudaMemcpyAsync(D.pbb, b, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    double res = 0.0;
+    CKS(pcg_solve(ctx, P, alpha, D.pbb, D.pxb, rtol, atol, maxit, its, &res));
+    CK(cudaMemcpyAsync(x, D.pxb, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     return HPG_OK;
 }
 

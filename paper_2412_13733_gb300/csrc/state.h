@@ -75,6 +75,15 @@ struct DevState {
     // pinned host mirror for scalars (owned by the Problem, kept across re-allocation)
     double* h_scal = nullptr;
     int* h_iflag = nullptr;
+    // iterative A_alpha^{-1} (preconditioned CG, allocated on first use)
+    double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr, *pxb = nullptr, *pbb = nullptr;
+    double *prc = nullptr, *pzc = nullptr, *pw1 = nullptr, *pw2 = nullptr, *pBinv = nullptr;
+    double* pVc[kMaxDim] = {};
+    double* plamc[kMaxDim] = {};
+    PcgGeo pg{};
+    Geo<double> gc{};
+    long long nc0 = 0;
+    bool pcg_ready = false;
     char* slab = nullptr;                  // one allocation holding every per-problem buffer (layout fixed
     size_t slab_bytes = 0;                 // by the problem's shape), see alloc_device
     cudaStream_t alloc_stream = nullptr;   // stream the stream-ordered allocations were made on
@@ -162,6 +171,12 @@ hpg_status op_precond_inv(hpg_ctx* ctx, Problem& P, int precision, const double*
 hpg_status op_schur(hpg_ctx* ctx, Problem& P, int precision, const double* x, double* y);
 hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double rtol, double* delta, int* its);
 hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, int reps);
+// Preconditioned CG on A_alpha x = b (device vectors of n_u interior entries), stopping at
+// ||r|| <= max(atol, rtol ||b||) or maxit; *its iterations, *res the final ||r||.
+hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* b, double* x, double rtol, double atol,
+                     int maxit, int* its, double* res);
+hpg_status op_stiffness_pcg(hpg_ctx* ctx, Problem& P, double alpha, const double* b, double* x, double rtol,
+                            double atol, int maxit, int* its);
 hpg_status op_launch_kernel_group(hpg_ctx* ctx, std::vector<Problem*>& ps, int cls, int precision, int reps);
 // request loop
 size_t estimate_device_bytes(const Problem& P);

@@ -28,7 +28,7 @@ class hpg_params(C.Structure):
                 ("krylov_max", C.c_int), ("krylov_rtol", C.c_double), ("precision", C.c_int),
                 ("ls_max", C.c_int), ("refine_max", C.c_int), ("timing", C.c_int), ("graphs", C.c_int),
                 ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int), ("strategy", C.c_int),
-                ("inner_max", C.c_int), ("krylov_f32", C.c_int)]
+                ("inner_max", C.c_int), ("krylov_f32", C.c_int), ("ainv_pcg", C.c_int), ("ainv_rtol", C.c_double)]
 
 
 class hpg_stats(C.Structure):
@@ -38,7 +38,7 @@ class hpg_stats(C.Structure):
                 ("final_residual", C.c_double), ("solve_ms", C.c_double), ("n_u", C.c_longlong),
                 ("n_psi", C.c_longlong), ("kernel_launches", C.c_longlong), ("h2d_bytes", C.c_longlong),
                 ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int), ("fgmres_total", C.c_longlong),
-                ("ainv_total", C.c_longlong)]
+                ("ainv_total", C.c_longlong), ("ainv_iters", C.c_longlong)]
 
 
 FIELD_FN = C.CFUNCTYPE(None, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
@@ -87,6 +87,7 @@ SIGNATURES = {
     "hpg_newton_direction": ([_ctx, C.c_int, C.c_int, _d, _pd, _sz, _P(C.c_int)], C.c_int),
     "hpg_launch_kernel": ([_ctx, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "hpg_fdm_tile_count": ([C.c_int], C.c_int),
+    "hpg_stiffness_solve_pcg": ([_ctx, C.c_int, _d, _pd, _pd, _sz, _d, _d, C.c_int, _P(C.c_int)], C.c_int),
     "hpg_launch_kernel_batch": ([_ctx, _P(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "hpg_apply_stiffness_inv_noalloc": ([_ctx, C.c_int, _d, C.c_void_p, C.c_void_p, _sz], C.c_int),
     "hpg_server_start": ([_ctx, C.c_int, _sz], C.c_int),
@@ -393,6 +394,16 @@ class Problem:
         """A_alpha^{-1} on device pointers without any allocation (see hpg.h)."""
         return self.L.hpg_apply_stiffness_inv_noalloc(self.ctx.h, self.pid, float(alpha), C.c_void_p(x_dev_ptr),
                                                        C.c_void_p(y_dev_ptr), int(length))
+
+    def stiffness_solve_pcg(self, b, alpha, rtol=1e-6, atol=1e-6, maxit=2000):
+        """x = A_alpha^{-1} b by block-Jacobi preconditioned CG; returns (x, iterations)."""
+        b = _f64(b)
+        x = np.zeros(self.n_u)
+        its = C.c_int()
+        self.ctx.check(self.L.hpg_stiffness_solve_pcg(self.ctx.h, self.pid, float(alpha), _dptr(b), _dptr(x), x.size,
+                                                      float(rtol), float(atol), int(maxit), C.byref(its)),
+                       "hpg_stiffness_solve_pcg")
+        return x, its.value
 
     def factor_precond(self, precision=HPG_FP64, dump=False):
         if dump:
