@@ -134,9 +134,9 @@ typedef struct {
                              rule; the FP64 refinement still sets the accuracy.  Ignored for
                              HPG_FP64.                                                          */
     int    ainv_pcg;      /* 0 (default): A_alpha^{-1} is the exact fast diagonalisation;
-                             1: in the FGMRES strategies HPG_FGMRES_PD and _PLPD, A_alpha^{-1}
-                             is preconditioned CG (the inexact inverse of Section 6.5) with the
-                             block-Jacobi preconditioner of hpg_stiffness_solve_pcg, to relative
+                             1 or 2: in the FGMRES strategies HPG_FGMRES_PD and _PLPD, A_alpha^{-1}
+                             is preconditioned CG (the inexact inverse of Section 6.5) with
+                             preconditioner 1 or 2 of hpg_stiffness_solve_pcg, to relative
                              tolerance ainv_rtol.  Ignored by HPG_SCHUR and HPG_FGMRES_PF, whose
                              A_alpha^{-1} runs inside the device-side GMRES loop               */
     double ainv_rtol;     /* relative tolerance of that CG; default 1e-10                       */
@@ -393,14 +393,16 @@ hpg_status hpg_apply_stiffness_inv_noalloc(hpg_ctx* ctx, int pid, double alpha, 
                                            size_t len);
 /* x = A_alpha^{-1} b by preconditioned CG (host vectors of n_u interior entries), to
  * ||b - A_alpha x|| <= max(atol, rtol ||b||) or maxit iterations; *its = iterations.
- * The preconditioner is block Jacobi over the entities of the hierarchical basis: the
- * vertex (all-hat) functions form one block -- the Q1 stiffness of the mesh, solved
- * exactly by fast diagonalisation -- and the bubble functions of every edge, face and
- * cell interior form dense blocks, solved with their inverses (a non-overlapping
- * additive Schwarz method of the p-version; Section 6.5 uses algebraic multigrid).
+ * Both preconditioners are additive Schwarz methods of the p-version whose coarse space
+ * is the vertex (all-hat) functions -- the Q1 stiffness of the mesh, solved exactly by
+ * fast diagonalisation (Section 6.5 uses algebraic multigrid instead):
+ *   precond 1: block Jacobi over the entities of the hierarchical basis, the bubble
+ *              functions of every edge, face and cell interior forming dense blocks;
+ *   precond 2: overlapping, one block per cell holding all its interior dofs (the
+ *              principal submatrix of A), the cells' corrections summed per dof.
  * Needs the problem's operators on the device (after hpg_solve or hpg_set_state). */
-hpg_status hpg_stiffness_solve_pcg(hpg_ctx* ctx, int pid, double alpha, const double* b, double* x, size_t len,
-                                   double rtol, double atol, int maxit, int* its);
+hpg_status hpg_stiffness_solve_pcg(hpg_ctx* ctx, int pid, int precond, double alpha, const double* b, double* x,
+                                   size_t len, double rtol, double atol, int maxit, int* its);
 /* Solve G delta = F(state) by eq. (schur2) + GMRES (relative tolerance rtol);
  * returns delta and the GMRES iteration count. */
 hpg_status hpg_newton_direction(hpg_ctx* ctx, int pid, int precision, double rtol, double* delta,

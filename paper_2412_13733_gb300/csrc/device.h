@@ -183,9 +183,20 @@ struct PcgGeo {
     long long boff[8];
     int bmax;
     const double* Binv;
+    // overlapping two-level variant (one block per cell, classes by boundary ends)
+    int cmax;
+    int csize[64];
+    long long coff[64];
+    const double* Cinv;
+    double* Y;               // per-cell block solutions, cmax per cell
 };
 // z = alpha^{-1} B_e^{-1} r on the dofs of every edge/face/interior entity e
 cudaError_t launch_ainv_blocks(const PcgGeo& pg, double alpha, const double* r, double* z, cudaStream_t s);
+// overlapping cell patches: Y_c = B_c^{-1} r|_c per cell, then z = alpha^{-1} sum_c R_c^T Y_c
+// (+ zc at the vertex dofs), each dof summing its cells in a fixed order
+cudaError_t launch_cells_solve(const PcgGeo& pg, long long ncells, const double* r, cudaStream_t s);
+cudaError_t launch_cells_gather(const PcgGeo& pg, double alpha, const double* zc, double* z, long long n,
+                                cudaStream_t s);
 // rc = r at the vertex (all-hat) dofs; z at the vertex dofs = zc
 cudaError_t launch_vertex_gather(const PcgGeo& pg, const double* r, double* rc, long long nc, cudaStream_t s);
 cudaError_t launch_vertex_scatter(const PcgGeo& pg, const double* zc, double* z, long long nc, cudaStream_t s);

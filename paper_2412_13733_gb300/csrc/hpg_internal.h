@@ -69,6 +69,14 @@ struct AinvPrecond {
     long long nent[8] = {};                      // entities of type t
     long long boff[8] = {};                      // offset of type t's inverse block in Binv
     std::vector<double> Binv;                    // the inverse blocks, row-major, by type
+    // two-level overlapping variant: one block per cell holding all the cell's interior
+    // dofs (principal submatrix of A); cells fall in classes by which of their ends are
+    // on the boundary along each axis (code 0: both, 1: left, 2: right, 3: none)
+    bool cells_built = false;
+    int cmax = 0;                                // largest cell block
+    int csize[64] = {};                          // block size of class k (-1: class absent)
+    long long coff[64] = {};                     // offset of class k's inverse block in Cinv
+    std::vector<double> Cinv;
 };
 
 // Everything the device path needs, computed on the host at setup.
@@ -110,6 +118,8 @@ void compute_lifting(HostProblem& P, hpg_field_fn g, void* user);
 double eval_u_point(const HostProblem& P, const std::vector<double>& ufull, const double* x);
 // Build P.ap (coarse pencils and entity blocks of the stiffness preconditioner).
 void build_ainv_precond(HostProblem& P);
+// Build the cell-patch blocks of P.ap (the overlapping two-level variant).
+void build_ainv_cells(HostProblem& P);
 // e^T (M_1 (x) ... (x) M_d) e for a full u-coefficient vector e: the squared L2(Omega)
 // norm of the field, with the exact 1D mass matrices of Section 3.
 double mass_norm2(const HostProblem& P, const std::vector<double>& e);

@@ -1413,8 +1413,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // ---- pipelined variant for batches --------------------------------------------
 // The whole-K tiles above stage a CTA's entire K panels before computing and rely on
 // several CTAs per SM to hide that.  For batched launches (many CTAs of identical
-// shape) this variant streams K in chunks of 16 through double-buffered shared
-// memory (cp.async groups: chunk c + 1 loads while chunk c computes) with a 4 x 4
+// shape) this variant streams K in chunks of 16 through a four-deep ring of shared
+// buffers (cp.async groups: chunks c + 1 .. c + 3 load while chunk c computes) with a 4 x 4
 // register tile per thread.  It keeps KS separate accumulators -- K split into the
 // same KS contiguous ranges as the whole-K tile with that KS, each summed in k order,
 // then added in range order -- so it gives the same bits as those tiles.
@@ -1427,9 +1427,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     k_gemm_pipe(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp, FdmScale sc,
                 const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2, const int* skip,
                 Bat bt) {
-    constexpr int BK = 16, NT = (BM / TM) * (BN / TN);
-    __shared__ __align__(16) T As[2][BK][BM];
-    __shared__ __align__(16) T Bs[2][BK][BN];
+    constexpr int BK = 16, NT = (BM / TM) * (BN / TN), NS = 4;   // NS chunks in flight
+    __shared__ __align__(16) T As[NS][BK][BM];
+    __shared__ __align__(16) T Bs[NS][BK][BN];
     GEMM_BATCH_ENTER()
     const int tid = threadIdx.x;
     const int tx = tid % (BN / TN), ty = tid / (BN / TN);
@@ -1453,6 +1453,17 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
             cp_async_elem(&Bs[buf][kk][nn], ok ? B + (long long)k * a.sBk + (long long)gn * a.sBn : B, ok);
         }
     };
+    // the t-th chunk in summation order: ranges in order, chunks of BK inside each
+    auto chunk_of = [&](int t, int& k0, int& kend) -> bool {
+        for (int g = 0; g < KS; ++g) {
+            const int gb = g * kchunk, ge = min(K, gb + kchunk);
+            if (gb >= ge) continue;
+            const int nc = (ge - gb + BK - 1) / BK;
+            if (t < nc) { k0 = gb + t * BK; kend = ge; return true; }
+            t -= nc;
+        }
+        return false;
+    };
     T acc[KS][TM][TN];
 #pragma unroll
     for (int g = 0; g < KS; ++g)
@@ -1460,36 +1471,25 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         for (int i = 0; i < TM; ++i)
 #pragma unroll
             for (int jj = 0; jj < TN; ++jj) acc[g][i][jj] = T(0);
-    // the first chunk of the first non-empty range
-    int first_g = 0;
-    while (first_g < KS && first_g * kchunk >= K) ++first_g;
-    int t = 0;
-    if (first_g < KS) {
-        stage(0, first_g * kchunk, min(K, (first_g + 1) * kchunk));
-        cp_async_commit();
+#pragma unroll
+    for (int st = 0; st < NS - 1; ++st) {
+        int k0, ke;
+        if (chunk_of(st, k0, ke)) stage(st, k0, ke);
+        cp_async_commit();                            // (an empty group when there is no chunk)
     }
+    int t = 0;
 #pragma unroll
     for (int g = 0; g < KS; ++g) {
         const int gb = g * kchunk, ge = min(K, gb + kchunk);
         for (int k0 = gb; k0 < ge; k0 += BK) {
-            // next chunk: the rest of this range, else the start of the next non-empty one
-            int nk0 = -1, nke = 0;
-            if (k0 + BK < ge) {
-                nk0 = k0 + BK;
-                nke = ge;
-            } else {
-                for (int h = g + 1; h < KS; ++h)
-                    if (h * kchunk < K) { nk0 = h * kchunk; nke = min(K, (h + 1) * kchunk); break; }
-            }
-            if (nk0 >= 0) {
-                stage((t + 1) & 1, nk0, nke);
+            {
+                int nk0, nke;
+                if (chunk_of(t + NS - 1, nk0, nke)) stage((t + NS - 1) % NS, nk0, nke);
                 cp_async_commit();
-                cp_async_wait_group<1>();
-            } else {
-                cp_async_wait_group<0>();
             }
+            cp_async_wait_group<NS - 1>();           // chunk t has landed
             __syncthreads();
-            const int buf = t & 1, kn = min(BK, ge - k0);
+            const int buf = t % NS, kn = min(BK, ge - k0);
             for (int kk = 0; kk < kn; ++kk) {
                 T av[TM], bv[TN];
                 if constexpr (sizeof(T) == 4 && TM == 4 && TN == 4) {
@@ -1512,6 +1512,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
             ++t;
         }
     }
+    cp_async_wait_group<0>();
 #pragma unroll
     for (int g = 1; g < KS; ++g)
 #pragma unroll
@@ -3049,6 +3050,114 @@ cudaError_t launch_vertex_scatter(const PcgGeo& pg, const double* zc, double* z,
     return cudaGetLastError();
 }
 
+// ---- overlapping cell patches (two-level additive Schwarz) -----------------------
+// local dof list of cell c along one axis: [left hat if c >= 1, right hat if c + 1 <= m - 1,
+// bubbles]; returns the count and the number of hats
+__device__ __forceinline__ int cell_nh(int m, int c) { return (c >= 1 ? 1 : 0) + (c + 1 <= m - 1 ? 1 : 0); }
+__device__ __forceinline__ int cell_dof_1d(int m, int nbub, int c, int pos) {
+    const int nh = cell_nh(m, c);
+    if (pos < nh) return (pos == 0 && c >= 1) ? c - 1 : c;     // left hat: vertex c; right hat: vertex c + 1
+    return m - 1 + c * nbub + (pos - nh);
+}
+
+__global__ void __launch_bounds__(128) k_cells_solve(PcgGeo pg, const double* __restrict__ r) {
+    extern __shared__ double smc[];
+    const long long cell = blockIdx.x;
+    int c[kMaxDim] = {0, 0, 0}, n1d[kMaxDim] = {1, 1, 1};
+    long long e = cell;
+    int cls = 0, nb = 1;
+    for (int j = 0; j < pg.d; ++j) {
+        c[j] = (int)(e % pg.m[j]);
+        e /= pg.m[j];
+        const int code = (c[j] >= 1 ? 1 : 0) | (c[j] + 1 <= pg.m[j] - 1 ? 2 : 0);
+        cls |= code << (2 * j);
+        n1d[j] = cell_nh(pg.m[j], c[j]) + pg.nbub;
+        nb *= n1d[j];
+    }
+    double* rs = smc;
+    for (int l = threadIdx.x; l < nb; l += blockDim.x) {
+        long long I = 0, stride = 1;
+        int rl = l;
+        for (int j = 0; j < pg.d; ++j) {
+            const int pos = rl % n1d[j];
+            rl /= n1d[j];
+            I += (long long)cell_dof_1d(pg.m[j], pg.nbub, c[j], pos) * stride;
+            stride *= pg.n1[j];
+        }
+        rs[l] = r[I];
+    }
+    __syncthreads();
+    const double* Bi = pg.Cinv + pg.coff[cls];
+    double* Y = pg.Y + cell * (long long)pg.cmax;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < nb; ++k) acc += Bi[(size_t)i * nb + k] * rs[k];
+        Y[i] = acc;
+    }
+}
+
+cudaError_t launch_cells_solve(const PcgGeo& pg, long long ncells, const double* r, cudaStream_t s) {
+    k_cells_solve<<<(unsigned)ncells, 128, (size_t)pg.cmax * sizeof(double), s>>>(pg, r);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// every interior dof sums the block solutions of the (up to 2^d) cells that hold it, in
+// the binary order of the choices per axis, plus the coarse correction at vertex dofs
+__global__ void k_cells_gather(PcgGeo pg, double ainv, const double* __restrict__ zc, double* __restrict__ z,
+                               long long n) {
+    const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= n) return;
+    int cc[kMaxDim][2], pp[kMaxDim][2], nch[kMaxDim];
+    long long e = I;
+    bool vertex = true;
+    long long vidx = 0, vstride = 1;
+    for (int j = 0; j < pg.d; ++j) {
+        const int i1 = (int)(e % pg.n1[j]);
+        e /= pg.n1[j];
+        const int m = pg.m[j];
+        if (i1 < m - 1) {
+            const int v = i1 + 1;                         // interior vertex v: right hat of cell v-1, left of v
+            cc[j][0] = v - 1; pp[j][0] = (v - 1 >= 1) ? 1 : 0;
+            cc[j][1] = v;     pp[j][1] = 0;
+            nch[j] = 2;
+            vidx += (long long)i1 * vstride;
+            vstride *= pg.nv[j];
+        } else {
+            const int q = i1 - (m - 1), cell = q / pg.nbub;
+            cc[j][0] = cell;
+            pp[j][0] = cell_nh(m, cell) + q % pg.nbub;
+            nch[j] = 1;
+            vertex = false;
+        }
+    }
+    double acc = 0.0;
+    const int ncomb = 1 << pg.d;
+    for (int sel = 0; sel < ncomb; ++sel) {
+        bool ok = true;
+        long long cell = 0, cstride = 1, l = 0, lstride = 1;
+        for (int j = 0; j < pg.d; ++j) {
+            const int bj = (sel >> j) & 1;
+            if (bj >= nch[j]) { ok = false; break; }
+            cell += (long long)cc[j][bj] * cstride;
+            cstride *= pg.m[j];
+            l += (long long)pp[j][bj] * lstride;
+            lstride *= cell_nh(pg.m[j], cc[j][bj]) + pg.nbub;
+        }
+        if (ok) acc += pg.Y[cell * (long long)pg.cmax + l];
+    }
+    double v = ainv * acc;
+    if (vertex && zc) v += zc[vidx];
+    z[I] = v;
+}
+
+cudaError_t launch_cells_gather(const PcgGeo& pg, double alpha, const double* zc, double* z, long long n,
+                                cudaStream_t s) {
+    k_cells_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pg, 1.0 / alpha, zc, z, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_aapply(const Geo<double>& g, double alpha, const double* x, double* y, cudaStream_t s) {
     if (g.d == 2)
         k_urow<2, double, double, double, true, false, false><<<utile_grid<2>(g.n1), 256,
@@ -3103,6 +3212,7 @@ void configure_kernels() {
     allow_big_smem(k_urow<2, double, double, double, true, false, false>);
     allow_big_smem(k_urow<3, double, double, double, true, false, false>);
     allow_big_smem(k_ainv_blocks);
+    allow_big_smem(k_cells_solve);
     allow_big_smem(k_urow<2, float, float, float, false, true, false>);
     allow_big_smem(k_urow<3, float, float, float, false, true, false>);
     allow_big_smem(k_urow<2, float, float, double, false, true, false>);

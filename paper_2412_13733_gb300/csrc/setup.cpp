@@ -926,3 +926,87 @@ void build_ainv_precond(HostProblem& P) {
 }
 
 }  // namespace hpg
+
+namespace hpg {
+
+namespace {
+// the interior 1D indices of the local dofs of cell c (left hat, right hat when interior,
+// then the bubbles), in the order the cell-patch blocks use
+void cell_dofs_1d(const Dir1D& D, int c, std::vector<int>& L) {
+    L.clear();
+    if (c >= 1) L.push_back(c - 1);                  // vertex c (interior index c - 1)
+    if (c + 1 <= D.m - 1) L.push_back(c);            // vertex c + 1
+    for (int b = 0; b < D.p - 1; ++b) L.push_back(D.m - 1 + c * (D.p - 1) + b);
+}
+}  // namespace
+
+void build_ainv_cells(HostProblem& P) {
+    AinvPrecond& ap = P.ap;
+    if (ap.cells_built) return;
+    const int d = P.d;
+    for (int k = 0; k < 64; ++k) ap.csize[k] = -1;
+    size_t off = 0;
+    // one representative cell per class: code per axis from (left end interior, right end interior)
+    for (int k = 0; k < (1 << (2 * d)); ++k) {
+        int cell[kMaxDim] = {0, 0, 0};
+        bool present = true;
+        for (int j = 0; j < d; ++j) {
+            const int code = (k >> (2 * j)) & 3, m = P.dir[j].m;
+            // code bit 0: a left interior vertex, bit 1: a right interior vertex
+            if (code == 0) { present = present && m == 1; cell[j] = 0; }
+            else if (code == 1) { present = present && m >= 2; cell[j] = m - 1; }
+            else if (code == 2) { present = present && m >= 2; cell[j] = 0; }
+            else { present = present && m >= 3; cell[j] = 1; }
+        }
+        if (!present) continue;
+        std::vector<int> L[kMaxDim];
+        int nb = 1, n1d[kMaxDim] = {1, 1, 1};
+        for (int j = 0; j < d; ++j) {
+            cell_dofs_1d(P.dir[j], cell[j], L[j]);
+            n1d[j] = (int)L[j].size();
+            nb *= n1d[j];
+        }
+        std::vector<double> B((size_t)nb * nb, 0.0);
+        for (int l = 0; l < nb; ++l)
+            for (int lp = 0; lp < nb; ++lp) {
+                int il[kMaxDim], ilp[kMaxDim];
+                int rl = l, rlp = lp;
+                for (int j = 0; j < d; ++j) {
+                    il[j] = L[j][rl % n1d[j]];
+                    rl /= n1d[j];
+                    ilp[j] = L[j][rlp % n1d[j]];
+                    rlp /= n1d[j];
+                }
+                double sum = 0.0;
+                for (int q = 0; q < d; ++q) {
+                    double prod = 1.0;
+                    for (int j = 0; j < d; ++j) prod *= ell_at(q == j ? P.dir[j].Ai : P.dir[j].Mi, il[j], ilp[j]);
+                    sum += prod;
+                }
+                B[(size_t)l * nb + lp] = sum;
+            }
+        std::vector<double> Lf = B;
+        if (!cholesky(nb, Lf)) throw std::runtime_error("stiffness cell block not SPD");
+        std::vector<double> X((size_t)nb * nb, 0.0);
+        for (int c = 0; c < nb; ++c)
+            for (int i = 0; i < nb; ++i) {
+                double v = (i == c) ? 1.0 : 0.0;
+                for (int q = 0; q < i; ++q) v -= Lf[(size_t)i * nb + q] * X[(size_t)q * nb + c];
+                X[(size_t)i * nb + c] = v / Lf[(size_t)i * nb + i];
+            }
+        ap.Cinv.resize(off + (size_t)nb * nb);
+        for (int i = 0; i < nb; ++i)
+            for (int c = 0; c < nb; ++c) {
+                double v = 0.0;
+                for (int q = std::max(i, c); q < nb; ++q) v += X[(size_t)q * nb + i] * X[(size_t)q * nb + c];
+                ap.Cinv[off + (size_t)i * nb + c] = v;
+            }
+        ap.csize[k] = nb;
+        ap.coff[k] = (long long)off;
+        ap.cmax = std::max(ap.cmax, nb);
+        off += (size_t)nb * nb;
+    }
+    ap.cells_built = true;
+}
+
+}  // namespace hpg

@@ -870,7 +870,7 @@ static hpg_status fg_precond(hpg_ctx* ctx, Problem& P, double alpha, const doubl
     if (P.params.ainv_pcg) {
         int its = 0;
         double res = 0.0;
-        CKS(pcg_solve(ctx, P, alpha, r, z, P.params.ainv_rtol, 0.0, 1000, &its, &res));
+        CKS(pcg_solve(ctx, P, P.params.ainv_pcg, alpha, r, z, P.params.ainv_rtol, 0.0, 1000, &its, &res));
         P.stats.ainv_iters += its;
     } else {
         CK(launch_fdm<double>(g, nullptr, alpha, r, z, D.w1_d, D.w2_d, s));
@@ -2222,8 +2222,21 @@ hpg_status op_launch_kernel_group(hpg_ctx* ctx, std::vector<Problem*>& ps, int c
 // CG with the Cholesky factorisation of A; here the preconditioner is the block Jacobi of
 // AinvPrecond, every block solved exactly: the vertex block by fast diagonalisation of
 // the Q1 pencils, the edge/face/interior bubble blocks by their dense inverses)
-static hpg_status pcg_setup(hpg_ctx* ctx, Problem& P) {
+static hpg_status pcg_setup(hpg_ctx* ctx, Problem& P, int kind) {
     DevState& D = P.D;
+    if (kind == 2 && D.pcg_ready && !D.pg.Cinv) {
+        // the cell-patch blocks on top of an existing set-up
+        build_ainv_cells(P.H);
+        bool ok = true;
+        const AinvPrecond& ap = P.H.ap;
+        D.pg.Cinv = upload_vec<double>(D, ap.Cinv, ok, ctx->stream);
+        D.pg.Y = dalloc<double>(D, (size_t)P.H.Nc * ap.cmax, ok);
+        D.pg.cmax = ap.cmax;
+        for (int k = 0; k < 64; ++k) { D.pg.csize[k] = ap.csize[k]; D.pg.coff[k] = ap.coff[k]; }
+        if (!ok) { ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
+        CK(cudaStreamSynchronize(ctx->stream));
+        return HPG_OK;
+    }
     if (D.pcg_ready) return HPG_OK;
     HostProblem& H = P.H;
     build_ainv_precond(H);
@@ -2280,13 +2293,25 @@ static hpg_status pcg_setup(hpg_ctx* ctx, Problem& P) {
     if (!ok) { ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
     CK(cudaStreamSynchronize(s));
     D.pcg_ready = true;
+    if (kind == 2) return pcg_setup(ctx, P, 2);
     return HPG_OK;
 }
 
-// z = M_alpha^{-1} r for the block-Jacobi preconditioner of A_alpha
-static hpg_status pcg_precond(hpg_ctx* ctx, Problem& P, double alpha, const double* r, double* z) {
+// z = M_alpha^{-1} r: kind 1, block Jacobi over the entities; kind 2, the two-level
+// overlapping Schwarz method with one patch per cell (Pavarino's additive Schwarz for the
+// p-version) and the same coarse vertex space
+static hpg_status pcg_precond(hpg_ctx* ctx, Problem& P, int kind, double alpha, const double* r, double* z) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
+    if (kind == 2) {
+        if (D.nc0 > 0) {
+            CK(launch_vertex_gather(D.pg, r, D.prc, D.nc0, s));
+            CK(launch_fdm<double>(D.gc, nullptr, alpha, D.prc, D.pzc, D.pw1, D.pw2, s));
+        }
+        CK(launch_cells_solve(D.pg, (long long)P.H.Nc, r, s));
+        CK(launch_cells_gather(D.pg, alpha, D.nc0 > 0 ? D.pzc : nullptr, z, (long long)P.H.Nu0, s));
+        return HPG_OK;
+    }
     CK(launch_ainv_blocks(D.pg, alpha, r, z, s));
     if (D.nc0 > 0) {
         CK(launch_vertex_gather(D.pg, r, D.prc, D.nc0, s));
@@ -2316,9 +2341,9 @@ static hpg_status pcg_dots(hpg_ctx* ctx, Problem& P, const double* a, const doub
     return HPG_OK;
 }
 
-hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* b, double* x, double rtol, double atol,
-                     int maxit, int* its, double* res) {
-    CKS(pcg_setup(ctx, P));
+hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, int kind, double alpha, const double* b, double* x, double rtol,
+                     double atol, int maxit, int* its, double* res) {
+    CKS(pcg_setup(ctx, P, kind));
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
     const long long n = (long long)P.H.Nu0;
@@ -2331,7 +2356,7 @@ hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* b, do
     *res = bn;
     if (!(bn > 0.0)) return HPG_OK;
     const double tol = std::max(atol, rtol * bn);
-    CKS(pcg_precond(ctx, P, alpha, D.pr, D.pz));
+    CKS(pcg_precond(ctx, P, kind, alpha, D.pr, D.pz));
     CK(cudaMemcpyAsync(D.pp, D.pz, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     double rz = 0.0;
     CKS(pcg_dots(ctx, P, D.pr, D.pz, nullptr, &rz, nullptr));
@@ -2343,7 +2368,7 @@ hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* b, do
         const double a = rz / pq;
         CK(launch_axpby(a, D.pp, 1.0, x, n, s));
         CK(launch_axpby(-a, D.pq, 1.0, D.pr, n, s));
-        CKS(pcg_precond(ctx, P, alpha, D.pr, D.pz));
+        CKS(pcg_precond(ctx, P, kind, alpha, D.pr, D.pz));
         double rz1 = 0.0, rr = 0.0;
         CKS(pcg_dots(ctx, P, D.pr, D.pz, D.pr, &rz1, &rr));
         *its = it;
@@ -2357,15 +2382,15 @@ hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* b, do
     return HPG_OK;
 }
 
-hpg_status op_stiffness_pcg(hpg_ctx* ctx, Problem& P, double alpha, const double* b, double* x, double rtol,
+hpg_status op_stiffness_pcg(hpg_ctx* ctx, Problem& P, int kind, double alpha, const double* b, double* x, double rtol,
                             double atol, int maxit, int* its) {
     DevState& D = P.D;
-    CKS(pcg_setup(ctx, P));
+    CKS(pcg_setup(ctx, P, kind));
     cudaStream_t s = ctx->stream;
     const long long n = (long long)P.H.Nu0;
     CK(cudaMemcpyAsync(D.pbb, b, n * sizeof(double), cudaMemcpyHostToDevice, s));
     double res = 0.0;
-    CKS(pcg_solve(ctx, P, alpha, D.pbb, D.pxb, rtol, atol, maxit, its, &res));
+    CKS(pcg_solve(ctx, P, kind, alpha, D.pbb, D.pxb, rtol, atol, maxit, its, &res));
     CK(cudaMemcpyAsync(x, D.pxb, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return HPG_OK;

@@ -173,9 +173,10 @@ hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double r
 hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, int reps);
 // Preconditioned CG on A_alpha x = b (device vectors of n_u interior entries), stopping at
 // ||r|| <= max(atol, rtol ||b||) or maxit; *its iterations, *res the final ||r||.
-hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* b, double* x, double rtol, double atol,
-                     int maxit, int* its, double* res);
-hpg_status op_stiffness_pcg(hpg_ctx* ctx, Problem& P, double alpha, const double* b, double* x, double rtol,
+// kind 1: block Jacobi over the basis entities; 2: overlapping cell patches (two-level).
+hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, int kind, double alpha, const double* b, double* x, double rtol,
+                     double atol, int maxit, int* its, double* res);
+hpg_status op_stiffness_pcg(hpg_ctx* ctx, Problem& P, int kind, double alpha, const double* b, double* x, double rtol,
                             double atol, int maxit, int* its);
 hpg_status op_launch_kernel_group(hpg_ctx* ctx, std::vector<Problem*>& ps, int cls, int precision, int reps);
 // request loop

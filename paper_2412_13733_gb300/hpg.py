@@ -87,7 +87,7 @@ SIGNATURES = {
     "hpg_newton_direction": ([_ctx, C.c_int, C.c_int, _d, _pd, _sz, _P(C.c_int)], C.c_int),
     "hpg_launch_kernel": ([_ctx, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "hpg_fdm_tile_count": ([C.c_int], C.c_int),
-    "hpg_stiffness_solve_pcg": ([_ctx, C.c_int, _d, _pd, _pd, _sz, _d, _d, C.c_int, _P(C.c_int)], C.c_int),
+    "hpg_stiffness_solve_pcg": ([_ctx, C.c_int, C.c_int, _d, _pd, _pd, _sz, _d, _d, C.c_int, _P(C.c_int)], C.c_int),
     "hpg_launch_kernel_batch": ([_ctx, _P(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "hpg_apply_stiffness_inv_noalloc": ([_ctx, C.c_int, _d, C.c_void_p, C.c_void_p, _sz], C.c_int),
     "hpg_server_start": ([_ctx, C.c_int, _sz], C.c_int),
@@ -395,12 +395,14 @@ class Problem:
         return self.L.hpg_apply_stiffness_inv_noalloc(self.ctx.h, self.pid, float(alpha), C.c_void_p(x_dev_ptr),
                                                        C.c_void_p(y_dev_ptr), int(length))
 
-    def stiffness_solve_pcg(self, b, alpha, rtol=1e-6, atol=1e-6, maxit=2000):
-        """x = A_alpha^{-1} b by block-Jacobi preconditioned CG; returns (x, iterations)."""
+    def stiffness_solve_pcg(self, b, alpha, rtol=1e-6, atol=1e-6, maxit=2000, precond=2):
+        """x = A_alpha^{-1} b by preconditioned CG (precond 1: entity blocks, 2: cell
+        patches); returns (x, iterations)."""
         b = _f64(b)
         x = np.zeros(self.n_u)
         its = C.c_int()
-        self.ctx.check(self.L.hpg_stiffness_solve_pcg(self.ctx.h, self.pid, float(alpha), _dptr(b), _dptr(x), x.size,
+        self.ctx.check(self.L.hpg_stiffness_solve_pcg(self.ctx.h, self.pid, int(precond), float(alpha), _dptr(b),
+                                                      _dptr(x), x.size,
                                                       float(rtol), float(atol), int(maxit), C.byref(its)),
                        "hpg_stiffness_solve_pcg")
         return x, its.value
