@@ -61,7 +61,7 @@ def sparse_direct_solve(G, F):
     return lu.solve(F)
 
 
-def eliminated_direct_solve(alphaA00, B0, C_blocks, F):
+def eliminated_direct_solve(alphaA00, B0, C_blocks, F, G=None, refine=8):
     """The same linear system G delta = F, by exact block elimination of psi.
 
     G = [[alpha A_00, B_0], [B_0^T, -C]] with C = D_psi + E_beta block-diagonal
@@ -73,15 +73,33 @@ def eliminated_direct_solve(alphaA00, B0, C_blocks, F):
     that of ``sparse_direct_solve(G, F)``; the elimination order only moves the
     fill-in to where it fits in host memory for the 3D workloads (the direct
     factorisation of G for 8^3 hexes at p = 6 does not fit in 62 GB).
+
+    Where the constraint is active exp(-psi) is tiny, C^{-1} is huge and the
+    eliminated matrix is badly scaled, so the solve alone can lose digits; with G
+    given, the result is refined against G itself (r = F - G delta, delta += the
+    same solve of r) until ||r|| <= 1e-14 ||F|| or `refine` passes -- iterative
+    refinement in FP64 of a direct method, which converges to the solution of
+    G delta = F whenever the factorisation is a contraction for G.
     """
     nu = B0.shape[0]
     Cinv = block_diagonal(np.linalg.inv(C_blocks))
     K = sp.csc_matrix(alphaA00 + B0 @ Cinv @ B0.T)
     lu = spla.splu(K, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0, options=dict(SymmetricMode=True))
-    Fu, Fpsi = F[:nu], F[nu:]
-    du = lu.solve(Fu + B0 @ (Cinv @ Fpsi))
-    dpsi = Cinv @ (B0.T @ du - Fpsi)
-    return np.concatenate([du, dpsi])
+    def once(R):
+        Ru, Rpsi = R[:nu], R[nu:]
+        du = lu.solve(Ru + B0 @ (Cinv @ Rpsi))
+        dpsi = Cinv @ (B0.T @ du - Rpsi)
+        return np.concatenate([du, dpsi])
+
+    delta = once(F)
+    if G is not None:
+        nF = np.linalg.norm(F)
+        for _ in range(refine):
+            R = F - G @ delta
+            if np.linalg.norm(R) <= 1e-14 * nF:
+                break
+            delta = delta + once(R)
+    return delta
 
 
 def alpha_schedule(alpha1, cap, growth_log2=0.5, max_steps=1000):
@@ -175,7 +193,7 @@ class ObstacleOracle:
         S = self.sp
         mloc = self.Mpsi.diagonal().reshape(S.Nc, S.nloc)
         C = self.D_blocks(psi) + self.beta * np.einsum("ci,ij->cij", mloc, np.eye(S.nloc))
-        return eliminated_direct_solve(alpha * self.A00, self.B0, C, F)
+        return eliminated_direct_solve(alpha * self.A00, self.B0, C, F, G=self.jacobian(psi, alpha))
 
     def split(self, x):
         ni = len(self.interior)
