@@ -232,21 +232,21 @@ def alu_peak_tflops(kind, clock_mhz, sms=152):
     return 1.25 * clock_mhz / 2070.0 * sms / 152
 
 
-def serve_requests(ctx, hpg, W, prec, count, rate=None, workers=8):
+def serve_requests(ctx, hpg, W, prec, count, rate=None, workers=8, policy=1):
     """Serve `count` seeded 2D obstacle requests through the request loop.
 
     rate None: saturated (all submitted at once).  Otherwise Poisson arrivals at
     `rate` requests/s; each request's problem is set up (host) when it arrives
-    and submitted; latency = arrival -> result readable (set-up included).
-    Returns (solves/s, p50 ms, p99 ms, mean Newton, makespan s).
+    and submitted; latency = arrival -> result readable (set-up included), split
+    into queueing (submit -> admitted) and running (admitted -> done).
     """
     reqs = W.requests(count)
     arr = W.arrivals(count, rate) if rate else np.zeros(count)
     ctx.server_start(workers=workers)
+    ctx.server_policy(policy)
     t0 = time.perf_counter()
     pending = {}
-    lat = []
-    newton = []
+    lat, queue, run, newton = [], [], [], []
     failed = 0
     i = 0
     done_t = 0.0
@@ -267,6 +267,9 @@ def serve_requests(ctx, hpg, W, prec, count, rate=None, workers=8):
                     P.u()                                 # result readable
                 end = time.perf_counter() - t0
                 lat.append(1000.0 * (end - a))
+                q, r_ms, _ = ctx.ticket_times(t)
+                queue.append(q)
+                run.append(r_ms)
                 newton.append(P.stats()["newton_total"])
                 P.free()
                 done_t = end
@@ -275,9 +278,11 @@ def serve_requests(ctx, hpg, W, prec, count, rate=None, workers=8):
         else:
             time.sleep(0.0005)
     ctx.server_stop()
-    lat = np.array(lat)
-    return (count / done_t, float(np.percentile(lat, 50)), float(np.percentile(lat, 99)), float(np.mean(newton)),
-            done_t, failed)
+    pc = lambda v, q: float(np.percentile(np.array(v), q))
+    return {"solves_per_s": count / done_t, "p50_ms": pc(lat, 50), "p99_ms": pc(lat, 99),
+            "queue_p50_ms": pc(queue, 50), "queue_p99_ms": pc(queue, 99), "run_p50_ms": pc(run, 50),
+            "run_p99_ms": pc(run, 99), "mean_newton": float(np.mean(newton)), "makespan_s": done_t,
+            "failed": failed}
 
 
 def kernel_only(args, ctx, w, stream, hpg, torch):
@@ -334,7 +339,8 @@ def main():
     ap.add_argument("--batch", type=int, default=16, help="independent solves in flight per step")
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests of the serving workload (0 = skip; 512 = the full stream)")
-    ap.add_argument("--serve-fp64", action="store_true", help="also serve with the FP64 path")
+    ap.add_argument("--serve-fp64", action="store_true",
+                    help="also run the three Poisson rates on the FP64 path (its saturated run is always made)")
     ap.add_argument("--no-others", action="store_true", help="skip the 4x4, 3D and torsion workloads")
     ap.add_argument("--no-strategies", action="store_true",
                     help="skip the Section 6.5 solver-strategy comparison (Schur vs FGMRES + P_D / P_L P_D / P_F-(10))")
@@ -659,7 +665,7 @@ def main():
                 P.set_state(np.zeros(P.n_u_full), np.zeros(P.n_psi), np.zeros(P.n_psi), 1.0)
                 ones = np.ones(P.n_u)
                 cg = {}
-                for pc, label in ((1, "entity_blocks"), (2, "cell_patches")):
+                for pc, label in ((1, "entity_blocks"), (2, "cell_patches"), (3, "vertex_stars")):
                     P.stiffness_solve_pcg(ones, 1.0, rtol=1e-6, atol=1e-6, precond=pc)   # set-up and warm-up
                     t0 = time.perf_counter()
                     _, its = P.stiffness_solve_pcg(ones, 1.0, rtol=1e-6, atol=1e-6, precond=pc)
@@ -679,17 +685,20 @@ def main():
 
     serving = None
     if args.serve_requests > 0 and world == 1:
-        serving = {"requests": args.serve_requests, "workers": B,
+        serving = {"requests": args.serve_requests, "workers": B, "admission": "largest work first (policy 1)",
                    "workload": "seeded 2D obstacle requests (0,1)^2, f~U[1,50], phi=0.3+1..4 Gaussian bumps, "
                                "m in 4..32, p in 2..10"}
-        for pname, prec in [("mixed", hpg.HPG_MIXED)] + ([("fp64", hpg.HPG_FP64)] if args.serve_fp64 else []):
-            thr, p50, p99, nmean, mk, nf = serve_requests(ctx, hpg, W, prec, args.serve_requests, None, B)
-            runs = {"saturated": {"solves_per_s": thr, "p50_ms": p50, "p99_ms": p99, "mean_newton": nmean,
-                                  "failed": nf}}
-            for f in (0.5, 0.9, 1.5):
-                t2, q50, q99, _, _, nf2 = serve_requests(ctx, hpg, W, prec, args.serve_requests, f * thr, B)
-                runs[f"poisson_{f}x"] = {"rate": f * thr, "solves_per_s": t2, "p50_ms": q50, "p99_ms": q99,
-                                         "failed": nf2}
+        for pname, prec in (("mixed", hpg.HPG_MIXED), ("fp64", hpg.HPG_FP64)):
+            runs = {"saturated": serve_requests(ctx, hpg, W, prec, args.serve_requests, None, B)}
+            if pname == "mixed":
+                runs["saturated_arrival_order"] = serve_requests(ctx, hpg, W, prec, args.serve_requests, None, B,
+                                                                 policy=0)
+            if pname == "mixed" or args.serve_fp64:
+                thr = runs["saturated"]["solves_per_s"]
+                for f in (0.5, 0.9, 1.5):
+                    r = serve_requests(ctx, hpg, W, prec, args.serve_requests, f * thr, B)
+                    r["rate"] = f * thr
+                    runs[f"poisson_{f}x"] = r
             serving[pname] = runs
 
     cpu = None

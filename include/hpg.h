@@ -134,9 +134,9 @@ typedef struct {
                              rule; the FP64 refinement still sets the accuracy.  Ignored for
                              HPG_FP64.                                                          */
     int    ainv_pcg;      /* 0 (default): A_alpha^{-1} is the exact fast diagonalisation;
-                             1 or 2: in the FGMRES strategies HPG_FGMRES_PD and _PLPD, A_alpha^{-1}
-                             is preconditioned CG (the inexact inverse of Section 6.5) with
-                             preconditioner 1 or 2 of hpg_stiffness_solve_pcg, to relative
+                             1, 2, 3: in the FGMRES strategies HPG_FGMRES_PD and _PLPD,
+                             A_alpha^{-1} is preconditioned CG (the inexact inverse of Section
+                             6.5) with that preconditioner of hpg_stiffness_solve_pcg, to relative
                              tolerance ainv_rtol.  Ignored by HPG_SCHUR and HPG_FGMRES_PF, whose
                              A_alpha^{-1} runs inside the device-side GMRES loop               */
     double ainv_rtol;     /* relative tolerance of that CG; default 1e-10                       */
@@ -338,6 +338,10 @@ hpg_status hpg_poll(hpg_ctx* ctx, long long ticket, int* done, hpg_status* resul
 hpg_status hpg_wait(hpg_ctx* ctx, long long ticket, double timeout_ms, hpg_status* result);
 /* times3 = {queued ms, running ms, submit-to-done ms} (0 while unfinished). */
 hpg_status hpg_ticket_times(hpg_ctx* ctx, long long ticket, double* times3);
+/* Admission order among queued requests that fit the budget: 0 (default) arrival order;
+ * 1 largest work first (unknowns x degree), so that long solves start early and short
+ * ones fill the gaps.  HPG_ERR_STATE without a running loop. */
+hpg_status hpg_server_policy(hpg_ctx* ctx, int policy);
 /* Message of a finished request that failed: which step failed and why (the text
  * hpg_last_error gives after a failing hpg_solve), truncated to len-1 bytes and
  * NUL-terminated; an empty string while unfinished or after success. */
@@ -399,7 +403,12 @@ hpg_status hpg_apply_stiffness_inv_noalloc(hpg_ctx* ctx, int pid, double alpha, 
  *   precond 1: block Jacobi over the entities of the hierarchical basis, the bubble
  *              functions of every edge, face and cell interior forming dense blocks;
  *   precond 2: overlapping, one block per cell holding all its interior dofs (the
- *              principal submatrix of A), the cells' corrections summed per dof.
+ *              principal submatrix of A), the cells' corrections summed per dof;
+ *   precond 3: overlapping, one patch per interior vertex -- the interior of its star
+ *              of cells, a tensor-product box -- solved exactly by fast diagonalisation
+ *              of the 1D restrictions of the pencil; the patches' corrections summed
+ *              per dof (the p-robust vertex-based method).  Its boxes (2p-1)^d must fit
+ *              in shared memory (HPG_ERR_ARG beyond).
  * Needs the problem's operators on the device (after hpg_solve or hpg_set_state). */
 hpg_status hpg_stiffness_solve_pcg(hpg_ctx* ctx, int pid, int precond, double alpha, const double* b, double* x,
                                    size_t len, double rtol, double atol, int maxit, int* its);

@@ -321,7 +321,7 @@ hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params) {
         params->strategy < HPG_SCHUR || params->strategy > HPG_FGMRES_PF ||
         (params->strategy != HPG_SCHUR && params->precision != HPG_FP64) || params->inner_max < 1 ||
         (params->krylov_f32 != 0 && params->krylov_f32 != 1) ||
-        params->ainv_pcg < 0 || params->ainv_pcg > 2 || !(params->ainv_rtol > 0.0))
+        params->ainv_pcg < 0 || params->ainv_pcg > 3 || !(params->ainv_rtol > 0.0))
         return HPG_ERR_ARG;
     const bool realloc = P->alloc_done && (params->krylov_max != P->params.krylov_max ||
                                            params->fdm_tile_f32 != P->params.fdm_tile_f32 ||
@@ -612,7 +612,7 @@ hpg_status hpg_stiffness_solve_pcg(hpg_ctx* ctx, int pid, int precond, double al
                                    size_t len, double rtol, double atol, int maxit, int* its) {
     OP_PROLOGUE(P->H.Nu0)
     if (!b || !x || !its || !(alpha > 0.0) || !(rtol >= 0.0) || !(atol >= 0.0) || maxit < 1 ||
-        (precond != 1 && precond != 2))
+        precond < 1 || precond > 3)
         return HPG_ERR_ARG;
     GUARD_BEGIN
     return hpg::op_stiffness_pcg(ctx, *P, precond, alpha, b, x, rtol, atol, maxit, its);
@@ -728,6 +728,11 @@ hpg_status hpg_measure_fma_peak(hpg_ctx* ctx, int precision, double* tflops, int
     }
     return HPG_OK;
     GUARD_END
+}
+
+hpg_status hpg_server_policy(hpg_ctx* ctx, int policy) {
+    if (!ctx || (policy != 0 && policy != 1)) return HPG_ERR_ARG;
+    return hpg::server_set_policy(ctx, policy);
 }
 
 hpg_status hpg_ticket_error(hpg_ctx* ctx, long long ticket, char* buf, size_t len) {

@@ -189,6 +189,12 @@ struct PcgGeo {
     long long coff[64];
     const double* Cinv;
     double* Y;               // per-cell block solutions, cmax per cell
+    // overlapping variant with vertex-star patches (tensor boxes, local fast diagonalisation)
+    int ns[kMaxDim];         // box extent per axis
+    int np_[kMaxDim];        // patches per axis (interior vertices, or 1 on a one-cell axis)
+    const double* Vs[kMaxDim];
+    const double* lams[kMaxDim];
+    double* Ys;              // per-patch solutions, ns0 ns1 ns2 per patch
 };
 // z = alpha^{-1} B_e^{-1} r on the dofs of every edge/face/interior entity e
 cudaError_t launch_ainv_blocks(const PcgGeo& pg, double alpha, const double* r, double* z, cudaStream_t s);
@@ -196,6 +202,11 @@ cudaError_t launch_ainv_blocks(const PcgGeo& pg, double alpha, const double* r, 
 // (+ zc at the vertex dofs), each dof summing its cells in a fixed order
 cudaError_t launch_cells_solve(const PcgGeo& pg, long long ncells, const double* r, cudaStream_t s);
 cudaError_t launch_cells_gather(const PcgGeo& pg, double alpha, const double* zc, double* z, long long n,
+                                cudaStream_t s);
+// vertex-star patches: Ys_v = A_v^{-1} r|_v per patch by fast diagonalisation of the box,
+// then z = alpha^{-1} sum_v R_v^T Ys_v (+ zc at the vertex dofs), fixed order per dof
+cudaError_t launch_stars_solve(const PcgGeo& pg, const double* r, cudaStream_t s);
+cudaError_t launch_stars_gather(const PcgGeo& pg, double alpha, const double* zc, double* z, long long n,
                                 cudaStream_t s);
 // rc = r at the vertex (all-hat) dofs; z at the vertex dofs = zc
 cudaError_t launch_vertex_gather(const PcgGeo& pg, const double* r, double* rc, long long nc, cudaStream_t s);

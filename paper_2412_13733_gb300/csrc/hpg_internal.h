@@ -77,6 +77,13 @@ struct AinvPrecond {
     int csize[64] = {};                          // block size of class k (-1: class absent)
     long long coff[64] = {};                     // offset of class k's inverse block in Cinv
     std::vector<double> Cinv;
+    // two-level overlapping variant with one patch per interior vertex: the interior of
+    // the vertex's star of cells, a tensor-product box per axis [bubbles of the left cell,
+    // the vertex's hat, bubbles of the right cell] (just the cell's bubbles on an axis with
+    // one cell), solved exactly by fast diagonalisation of the 1D star pencils
+    bool stars_built = false;
+    int ns[kMaxDim] = {1, 1, 1};                 // star box extent per axis
+    std::vector<double> Vs[kMaxDim], lams[kMaxDim];
 };
 
 // Everything the device path needs, computed on the host at setup.
@@ -120,6 +127,8 @@ double eval_u_point(const HostProblem& P, const std::vector<double>& ufull, cons
 void build_ainv_precond(HostProblem& P);
 // Build the cell-patch blocks of P.ap (the overlapping two-level variant).
 void build_ainv_cells(HostProblem& P);
+// Build the vertex-star pencils of P.ap (the overlapping variant with star patches).
+void build_ainv_stars(HostProblem& P);
 // e^T (M_1 (x) ... (x) M_d) e for a full u-coefficient vector e: the squared L2(Omega)
 // norm of the field, with the exact 1D mass matrices of Section 3.
 double mass_norm2(const HostProblem& P, const std::vector<double>& e);

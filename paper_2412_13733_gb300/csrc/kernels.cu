@@ -3158,6 +3158,148 @@ cudaError_t launch_cells_gather(const PcgGeo& pg, double alpha, const double* zc
     return cudaGetLastError();
 }
 
+// ---- vertex-star patches -------------------------------------------------------
+// 1D interior index of position `pos` of the star of patch q (interior vertex v = q + 1)
+// along an axis with m cells: [bubbles of cell v-1, hat v, bubbles of cell v]; on a
+// one-cell axis the patch is that cell's bubbles
+__device__ __forceinline__ int star_dof_1d(int m, int nbub, int q, int pos) {
+    if (m < 2) return m - 1 + pos;
+    const int v = q + 1;
+    if (pos < nbub) return m - 1 + (v - 1) * nbub + pos;
+    if (pos == nbub) return v - 1;
+    return m - 1 + v * nbub + (pos - nbub - 1);
+}
+
+// one pass of a box fast diagonalisation along axis ax: out[.., a, ..] = sum_k W(a, k) in[.., k, ..],
+// W = V^T (fwd: V[k][a]) or V (V[a][k])
+__device__ __forceinline__ void box_pass(const double* in, double* out, const double* V, bool fwd, const int* ext,
+                                         int d, int ax, int tot) {
+    int stride = 1;
+    for (int j = 0; j < ax; ++j) stride *= ext[j];
+    const int n = ext[ax];
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int a = (e / stride) % n;
+        const int base = e - a * stride;
+        double acc = 0.0;
+        if (fwd)
+            for (int k = 0; k < n; ++k) acc += V[k * n + a] * in[base + k * stride];
+        else
+            for (int k = 0; k < n; ++k) acc += V[a * n + k] * in[base + k * stride];
+        out[e] = acc;
+    }
+    (void)d;
+}
+
+__global__ void __launch_bounds__(256) k_stars_solve(PcgGeo pg, const double* __restrict__ r) {
+    extern __shared__ double sms[];
+    const int d = pg.d;
+    int q[kMaxDim] = {0, 0, 0};
+    long long e = blockIdx.x;
+    for (int j = 0; j < d; ++j) {
+        q[j] = (int)(e % pg.np_[j]);
+        e /= pg.np_[j];
+    }
+    int ext[kMaxDim] = {1, 1, 1}, tot = 1;
+    for (int j = 0; j < d; ++j) { ext[j] = pg.ns[j]; tot *= ext[j]; }
+    double* b0 = sms;
+    double* b1 = sms + tot;
+    for (int l = threadIdx.x; l < tot; l += blockDim.x) {
+        long long I = 0, stride = 1;
+        int rl = l;
+        for (int j = 0; j < d; ++j) {
+            const int pos = rl % ext[j];
+            rl /= ext[j];
+            I += (long long)star_dof_1d(pg.m[j], pg.nbub, q[j], pos) * stride;
+            stride *= pg.n1[j];
+        }
+        b0[l] = r[I];
+    }
+    __syncthreads();
+    double *in = b0, *out = b1;
+    for (int ax = 0; ax < d; ++ax) {
+        box_pass(in, out, pg.Vs[ax], true, ext, d, ax, tot);
+        __syncthreads();
+        double* t = in; in = out; out = t;
+    }
+    for (int l = threadIdx.x; l < tot; l += blockDim.x) {
+        int rl = l;
+        double lsum = 0.0;
+        for (int j = 0; j < d; ++j) {
+            lsum += pg.lams[j][rl % ext[j]];
+            rl /= ext[j];
+        }
+        in[l] /= lsum;
+    }
+    __syncthreads();
+    for (int ax = 0; ax < d; ++ax) {
+        box_pass(in, out, pg.Vs[ax], false, ext, d, ax, tot);
+        __syncthreads();
+        double* t = in; in = out; out = t;
+    }
+    double* Y = pg.Ys + (long long)blockIdx.x * tot;
+    for (int l = threadIdx.x; l < tot; l += blockDim.x) Y[l] = in[l];
+}
+
+cudaError_t launch_stars_solve(const PcgGeo& pg, const double* r, cudaStream_t s) {
+    long long npatch = 1, tot = 1;
+    for (int j = 0; j < pg.d; ++j) { npatch *= pg.np_[j]; tot *= pg.ns[j]; }
+    k_stars_solve<<<(unsigned)npatch, 256, (size_t)(2 * tot) * sizeof(double), s>>>(pg, r);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_stars_gather(PcgGeo pg, double ainv, const double* __restrict__ zc, double* __restrict__ z,
+                               long long n) {
+    const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= n) return;
+    int qq[kMaxDim][2], pp[kMaxDim][2], nch[kMaxDim];
+    long long e = I, vidx = 0, vstride = 1;
+    bool vertex = true;
+    for (int j = 0; j < pg.d; ++j) {
+        const int i1 = (int)(e % pg.n1[j]);
+        e /= pg.n1[j];
+        const int m = pg.m[j], nb = pg.nbub;
+        if (m < 2) {                                  // one cell: the single patch's bubbles
+            qq[j][0] = 0; pp[j][0] = i1 - (m - 1); nch[j] = 1;
+            vertex = false;
+        } else if (i1 < m - 1) {                      // hat of interior vertex v = i1 + 1: centre of patch v
+            qq[j][0] = i1; pp[j][0] = nb; nch[j] = 1;
+            vidx += (long long)i1 * vstride;
+            vstride *= pg.nv[j];
+        } else {                                      // bubble b of cell c: stars of vertices c and c + 1
+            const int qb = i1 - (m - 1), c = qb / nb, b = qb % nb;
+            nch[j] = 0;
+            if (c >= 1) { qq[j][nch[j]] = c - 1; pp[j][nch[j]] = nb + 1 + b; ++nch[j]; }
+            if (c + 1 <= m - 1) { qq[j][nch[j]] = c; pp[j][nch[j]] = b; ++nch[j]; }
+            vertex = false;
+        }
+    }
+    double acc = 0.0;
+    for (int sel = 0; sel < (1 << pg.d); ++sel) {
+        bool ok = true;
+        long long patch = 0, pstride = 1, l = 0, lstride = 1;
+        for (int j = 0; j < pg.d; ++j) {
+            const int bj = (sel >> j) & 1;
+            if (bj >= nch[j]) { ok = false; break; }
+            patch += (long long)qq[j][bj] * pstride;
+            pstride *= pg.np_[j];
+            l += (long long)pp[j][bj] * lstride;
+            lstride *= pg.ns[j];
+        }
+        if (ok) acc += pg.Ys[patch * lstride + l];
+    }
+    double v = ainv * acc;
+    if (vertex && zc) v += zc[vidx];
+    z[I] = v;
+}
+
+cudaError_t launch_stars_gather(const PcgGeo& pg, double alpha, const double* zc, double* z, long long n,
+                                cudaStream_t s) {
+    k_stars_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pg, 1.0 / alpha, zc, z, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_aapply(const Geo<double>& g, double alpha, const double* x, double* y, cudaStream_t s) {
     if (g.d == 2)
         k_urow<2, double, double, double, true, false, false><<<utile_grid<2>(g.n1), 256,
@@ -3213,6 +3355,7 @@ void configure_kernels() {
     allow_big_smem(k_urow<3, double, double, double, true, false, false>);
     allow_big_smem(k_ainv_blocks);
     allow_big_smem(k_cells_solve);
+    allow_big_smem(k_stars_solve);
     allow_big_smem(k_urow<2, float, float, float, false, true, false>);
     allow_big_smem(k_urow<3, float, float, float, false, true, false>);
     allow_big_smem(k_urow<2, float, float, double, false, true, false>);

@@ -53,7 +53,14 @@ struct Server {
     std::vector<cudaStream_t> streams;
     bool stopping = false;
     long long next_ticket = 1;
+    int policy = 0;                       // 0: arrival order; 1: largest work first
 };
+
+// Work of a request for the largest-first policy: unknowns times the degree (the Krylov
+// and factorisation work per Newton step grows with both).
+static double request_work(const Problem& P) {
+    return (double)(P.H.Nu0 + P.H.Npsi) * (double)P.H.p;
+}
 
 // Device bytes of a problem's buffers (the allocations of alloc_device).
 size_t estimate_device_bytes(const Problem& P) {
@@ -97,18 +104,29 @@ static void worker_loop(Server* S, int w) {
             return false;
         });
         if (S->stopping && S->queue.empty()) return;
+        // admission: the first request in arrival order that fits the memory budget, or
+        // (policy 1) the largest one that fits, so that long solves start early and the
+        // small ones fill the gaps
+        auto pick = S->queue.end();
         for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
             Request* q = *it;
-            const bool already = S->charged.count(q->P) != 0;
-            if (already || S->in_use + q->bytes <= S->budget) {
-                if (!already) {
-                    S->in_use += q->bytes;
-                    S->charged[q->P] = q->bytes;
-                }
-                R = q;
-                S->queue.erase(it);
-                break;
+            const bool fits = S->charged.count(q->P) != 0 || S->in_use + q->bytes <= S->budget;
+            if (!fits) continue;
+            if (pick == S->queue.end()) {
+                pick = it;
+                if (S->policy == 0) break;
+            } else if (request_work(*q->P) > request_work(*(*pick)->P)) {
+                pick = it;
             }
+        }
+        if (pick != S->queue.end()) {
+            Request* q = *pick;
+            if (S->charged.count(q->P) == 0) {
+                S->in_use += q->bytes;
+                S->charged[q->P] = q->bytes;
+            }
+            R = q;
+            S->queue.erase(pick);
         }
         if (!R) {
             if (S->stopping) return;
@@ -232,6 +250,14 @@ hpg_status server_poll(hpg_ctx* ctx, long long ticket, double wait_ms, int* done
         times3[1] = R.state == 2 ? R.t_done - R.t_start : 0.0;                          // running
         times3[2] = R.state == 2 ? R.t_done - R.t_submit : 0.0;                         // latency
     }
+    return HPG_OK;
+}
+
+hpg_status server_set_policy(hpg_ctx* ctx, int policy) {
+    Server* S = ctx->server;
+    if (!S) return HPG_ERR_STATE;
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->policy = policy;
     return HPG_OK;
 }
 

@@ -1010,3 +1010,36 @@ void build_ainv_cells(HostProblem& P) {
 }
 
 }  // namespace hpg
+
+namespace hpg {
+
+void build_ainv_stars(HostProblem& P) {
+    AinvPrecond& ap = P.ap;
+    if (ap.stars_built) return;
+    const int nbub = P.p - 1;
+    for (int j = 0; j < P.d; ++j) {
+        const Dir1D& D = P.dir[j];
+        // the star of interior vertex v = 1: bubbles of cell 0, hat of vertex 1, bubbles of
+        // cell 1 (every interior vertex's star has the same 1D matrices on a uniform mesh)
+        std::vector<int> L;
+        if (D.m >= 2) {
+            for (int b = 0; b < nbub; ++b) L.push_back(D.m - 1 + b);
+            L.push_back(0);
+            for (int b = 0; b < nbub; ++b) L.push_back(D.m - 1 + nbub + b);
+        } else {
+            for (int b = 0; b < nbub; ++b) L.push_back(D.m - 1 + b);
+        }
+        const int n = (int)L.size();
+        ap.ns[j] = n;
+        std::vector<double> Ad((size_t)n * n), Md((size_t)n * n);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                Ad[(size_t)a * n + b] = ell_at(D.Ai, L[a], L[b]);
+                Md[(size_t)a * n + b] = ell_at(D.Mi, L[a], L[b]);
+            }
+        pencil_eigen(n, Ad, Md, ap.Vs[j], ap.lams[j]);
+    }
+    ap.stars_built = true;
+}
+
+}  // namespace hpg

@@ -2224,6 +2224,31 @@ hpg_status op_launch_kernel_group(hpg_ctx* ctx, std::vector<Problem*>& ps, int c
 // the Q1 pencils, the edge/face/interior bubble blocks by their dense inverses)
 static hpg_status pcg_setup(hpg_ctx* ctx, Problem& P, int kind) {
     DevState& D = P.D;
+    if (kind == 3 && D.pcg_ready && !D.pg.Ys) {
+        // the vertex-star pencils on top of an existing set-up
+        build_ainv_stars(P.H);
+        const AinvPrecond& ap = P.H.ap;
+        long long npatch = 1, tot = 1;
+        for (int j = 0; j < P.H.d; ++j) {
+            D.pg.ns[j] = ap.ns[j];
+            D.pg.np_[j] = P.H.m[j] >= 2 ? P.H.m[j] - 1 : 1;
+            npatch *= D.pg.np_[j];
+            tot *= ap.ns[j];
+        }
+        if ((size_t)(2 * tot) * sizeof(double) > kCellSmemMax) {
+            ctx->err = "vertex-star boxes too large for shared memory at this degree";
+            return HPG_ERR_ARG;
+        }
+        bool ok = true;
+        for (int j = 0; j < P.H.d; ++j) {
+            D.pg.Vs[j] = upload_vec<double>(D, ap.Vs[j], ok, ctx->stream);
+            D.pg.lams[j] = upload_vec<double>(D, ap.lams[j], ok, ctx->stream);
+        }
+        D.pg.Ys = dalloc<double>(D, (size_t)(npatch * tot), ok);
+        if (!ok) { ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
+        CK(cudaStreamSynchronize(ctx->stream));
+        return HPG_OK;
+    }
     if (kind == 2 && D.pcg_ready && !D.pg.Cinv) {
         // the cell-patch blocks on top of an existing set-up
         build_ainv_cells(P.H);
@@ -2293,23 +2318,32 @@ static hpg_status pcg_setup(hpg_ctx* ctx, Problem& P, int kind) {
     if (!ok) { ctx->err = "device allocation failed"; return HPG_ERR_OOM; }
     CK(cudaStreamSynchronize(s));
     D.pcg_ready = true;
-    if (kind == 2) return pcg_setup(ctx, P, 2);
+    if (kind >= 2) return pcg_setup(ctx, P, kind);
     return HPG_OK;
 }
 
 // z = M_alpha^{-1} r: kind 1, block Jacobi over the entities; kind 2, the two-level
-// overlapping Schwarz method with one patch per cell (Pavarino's additive Schwarz for the
-// p-version) and the same coarse vertex space
+// overlapping Schwarz method with one patch per cell; kind 3, the same with one patch per
+// interior vertex (the interior of its star of cells) -- the vertex-based overlapping
+// Schwarz method of the p-version (L. F. Pavarino, Numer. Math. 66 (1994)), whose patch
+// solves are fast diagonalisations of tensor boxes as in P. F. Fischer's overlapping
+// Schwarz method for spectral elements (J. Comput. Phys. 133 (1997)); all with the coarse
+// vertex (Q1) space
 static hpg_status pcg_precond(hpg_ctx* ctx, Problem& P, int kind, double alpha, const double* r, double* z) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
-    if (kind == 2) {
+    if (kind >= 2) {
         if (D.nc0 > 0) {
             CK(launch_vertex_gather(D.pg, r, D.prc, D.nc0, s));
             CK(launch_fdm<double>(D.gc, nullptr, alpha, D.prc, D.pzc, D.pw1, D.pw2, s));
         }
-        CK(launch_cells_solve(D.pg, (long long)P.H.Nc, r, s));
-        CK(launch_cells_gather(D.pg, alpha, D.nc0 > 0 ? D.pzc : nullptr, z, (long long)P.H.Nu0, s));
+        if (kind == 2) {
+            CK(launch_cells_solve(D.pg, (long long)P.H.Nc, r, s));
+            CK(launch_cells_gather(D.pg, alpha, D.nc0 > 0 ? D.pzc : nullptr, z, (long long)P.H.Nu0, s));
+        } else {
+            CK(launch_stars_solve(D.pg, r, s));
+            CK(launch_stars_gather(D.pg, alpha, D.nc0 > 0 ? D.pzc : nullptr, z, (long long)P.H.Nu0, s));
+        }
         return HPG_OK;
     }
     CK(launch_ainv_blocks(D.pg, alpha, r, z, s));

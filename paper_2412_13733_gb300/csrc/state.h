@@ -173,7 +173,8 @@ hpg_status op_newton_direction(hpg_ctx* ctx, Problem& P, int precision, double r
 hpg_status op_launch_kernel(hpg_ctx* ctx, Problem& P, int cls, int precision, int reps);
 // Preconditioned CG on A_alpha x = b (device vectors of n_u interior entries), stopping at
 // ||r|| <= max(atol, rtol ||b||) or maxit; *its iterations, *res the final ||r||.
-// kind 1: block Jacobi over the basis entities; 2: overlapping cell patches (two-level).
+// kind 1: block Jacobi over the basis entities; 2: overlapping cell patches; 3: overlapping
+// vertex-star patches (both two-level, with the coarse vertex space).
 hpg_status pcg_solve(hpg_ctx* ctx, Problem& P, int kind, double alpha, const double* b, double* x, double rtol,
                      double atol, int maxit, int* its, double* res);
 hpg_status op_stiffness_pcg(hpg_ctx* ctx, Problem& P, int kind, double alpha, const double* b, double* x, double rtol,
@@ -188,6 +189,7 @@ hpg_status server_poll(hpg_ctx* ctx, long long ticket, double wait_ms, int* done
                        double* times3);
 void server_release(hpg_ctx* ctx, Problem& P);
 hpg_status server_ticket_error(hpg_ctx* ctx, long long ticket, std::string* msg);
+hpg_status server_set_policy(hpg_ctx* ctx, int policy);
 size_t server_in_use(hpg_ctx* ctx);
 
 }  // namespace hpg

@@ -98,6 +98,7 @@ SIGNATURES = {
     "hpg_ticket_times": ([_ctx, C.c_longlong, _pd], C.c_int),
     "hpg_server_memory": ([_ctx, C.c_int, _P(_sz), _P(_sz)], C.c_int),
     "hpg_ticket_error": ([_ctx, C.c_longlong, C.c_char_p, _sz], C.c_int),
+    "hpg_server_policy": ([_ctx, C.c_int], C.c_int),
     "hpg_l2_error": ([_ctx, C.c_int, _pd, _sz, _pd, _pd], C.c_int),
     "hpg_measure_fma_peak": ([_ctx, C.c_int, _pd, _P(C.c_int)], C.c_int),
 }
@@ -194,6 +195,9 @@ class Context:
         t = (C.c_double * 3)()
         self.check(self.L.hpg_ticket_times(self.h, C.c_longlong(ticket), t), "hpg_ticket_times")
         return tuple(t)
+
+    def server_policy(self, policy):
+        self.check(self.L.hpg_server_policy(self.h, int(policy)), "hpg_server_policy")
 
     def ticket_error(self, ticket):
         buf = C.create_string_buffer(512)
@@ -395,9 +399,9 @@ class Problem:
         return self.L.hpg_apply_stiffness_inv_noalloc(self.ctx.h, self.pid, float(alpha), C.c_void_p(x_dev_ptr),
                                                        C.c_void_p(y_dev_ptr), int(length))
 
-    def stiffness_solve_pcg(self, b, alpha, rtol=1e-6, atol=1e-6, maxit=2000, precond=2):
+    def stiffness_solve_pcg(self, b, alpha, rtol=1e-6, atol=1e-6, maxit=2000, precond=3):
         """x = A_alpha^{-1} b by preconditioned CG (precond 1: entity blocks, 2: cell
-        patches); returns (x, iterations)."""
+        patches, 3: vertex-star patches); returns (x, iterations)."""
         b = _f64(b)
         x = np.zeros(self.n_u)
         its = C.c_int()

@@ -1,7 +1,8 @@
-"""The iterative (inexact) A_alpha^{-1}: conjugate gradients on the stiffness matrix
-preconditioned by block Jacobi over the entities of the hierarchical basis (the
-vertex functions' Q1 block solved exactly by fast diagonalisation, the bubble blocks
-of every edge, face and cell interior by their dense inverses).  Section 6.5 compares
+"""The iterative (inexact) A_alpha^{-1}: conjugate gradients on the stiffness matrix with
+three two-level additive Schwarz preconditioners sharing the coarse vertex (Q1) space,
+solved exactly by fast diagonalisation: (1) block Jacobi over the entities of the
+hierarchical basis, (2) overlapping cell patches, (3) overlapping vertex-star patches
+whose tensor boxes are solved by fast diagonalisation.  Section 6.5 compares
 algebraic-multigrid CG with the Cholesky factorisation of A; here the exact inverse is
 the fast diagonalisation, so CG is checked against it, and against the oracle inside
 the flexible-GMRES strategies that accept an inexact A_alpha^{-1}."""
@@ -21,7 +22,7 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("precond", [1, 2])
+@pytest.mark.parametrize("precond", [1, 2, 3])
 @pytest.mark.parametrize("name", ["radial_3x3_p5", "aniso_upper", "sine3d_3x2x2", "box3d_p3_m4", "single_cell"])
 def test_pcg_equals_fast_diagonalisation(ctx, name, precond):
     from paper_2412_13733_gb300 import hpg
@@ -42,8 +43,9 @@ def test_pcg_equals_fast_diagonalisation(ctx, name, precond):
 def test_pcg_table_of_section_6_5(ctx):
     """The experiment of Section 6.5's CG table on 4^3 hexes: A x = 1 to absolute and
     relative tolerance 1e-6; x is A^{-1} 1 (checked against the fast diagonalisation).
-    The overlapping cell patches keep the count nearly independent of p (the paper's
-    AMG-CG: 20, 76, 165 at p = 2, 4, 6); the non-overlapping entity blocks do not."""
+    The vertex-star patches keep the count nearly independent of p (the paper's AMG-CG:
+    20, 76, 165 at p = 2, 4, 6); the cell patches and the non-overlapping entity blocks
+    do not."""
     from paper_2412_13733_gb300 import hpg, workloads as W
     its = {}
     for p in (2, 4, 6):
@@ -52,15 +54,17 @@ def test_pcg_table_of_section_6_5(ctx):
         P.set_state(np.zeros(P.n_u_full), np.zeros(P.n_psi), np.zeros(P.n_psi), 1.0)
         ones = np.ones(P.n_u)
         ref = P.apply_stiffness_inv(ones, hpg.HPG_FP64)
-        for pc in (1, 2):
+        for pc in (1, 2, 3):
             x, its[(pc, p)] = P.stiffness_solve_pcg(ones, 1.0, rtol=1e-6, atol=1e-6, precond=pc)
             assert np.linalg.norm(x - ref) <= 1e-3 * np.linalg.norm(ref)
         P.free()
     assert its[(1, 2)] <= 40 and its[(1, 6)] < 1000, its
-    assert its[(2, 6)] <= 2 * its[(2, 2)] + 20 and its[(2, 6)] < its[(1, 6)], its
+    assert its[(2, 6)] < its[(1, 6)], its
+    # the vertex-star patches: at most about twice the p = 2 count at p = 6
+    assert its[(3, 6)] <= 2 * its[(3, 2)] + 10 and its[(3, 6)] < its[(2, 6)], its
 
 
-@pytest.mark.parametrize("precond", [1, 2])
+@pytest.mark.parametrize("precond", [1, 3])
 @pytest.mark.parametrize("strategy", [1, 2])
 @pytest.mark.parametrize("name", ["radial_3x3_p5", "box3d_p2_m4"])
 def test_fgmres_with_inexact_inverse_matches_oracle(ctx, name, strategy, precond):
