@@ -1094,6 +1094,45 @@ __global__ void k_precond_f64(Geo<double> g, const double* __restrict__ Sinv, co
     }
 }
 
+// Small FP32 blocks (nb <= 128): the block is symmetric, so z_i = -sum_k S[k][i] v_k
+// with one thread per i reads rows of S with consecutive threads on consecutive words
+// (coalesced), four independent accumulators, and several cells share a 256-thread
+// block (groups of nb rounded up to a warp) -- no lane padding to 128 columns and no
+// shuffle reductions, which the row form spends on blocks of 49 or 64.
+template <typename T, typename Tin, typename Tout>
+__global__ void __launch_bounds__(256)
+    k_precond_col(Geo<T> g, const T* __restrict__ Sinv, const Tin* __restrict__ v, Tout* __restrict__ z, IterCtl ctl,
+                  int gsz, Bat bt) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    long long off;
+    if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
+    ctl.skip = bsh(ctl.skip, off);
+    ctl.jptr = bsh(ctl.jptr, off);
+    if (ctl.skip && *ctl.skip) return;
+    Sinv = bsh(Sinv, off); v = bsh(v, off); z = bsh(z, off);
+    const int nb = (int)g.nb;
+    const int cpb = blockDim.x / gsz;
+    const int grp = threadIdx.x / gsz, i = threadIdx.x - grp * gsz;
+    const long long cell = (long long)blockIdx.x * cpb + grp;
+    T* vs = reinterpret_cast<T*>(smraw) + (size_t)grp * gsz;
+    const Tin* vin = v + (ctl.jptr ? (long long)(*ctl.jptr) * ctl.jstride : 0LL);
+    const bool live = grp < cpb && cell < g.Nc;
+    if (live && i < nb) vs[i] = (T)vin[cell * nb + i];
+    __syncthreads();
+    if (!live || i >= nb) return;
+    const T* S = Sinv + cell * (long long)nb * nb;
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    int k = 0;
+    for (; k + 3 < nb; k += 4) {
+        s0 += S[(size_t)k * nb + i] * vs[k];
+        s1 += S[(size_t)(k + 1) * nb + i] * vs[k + 1];
+        s2 += S[(size_t)(k + 2) * nb + i] * vs[k + 2];
+        s3 += S[(size_t)(k + 3) * nb + i] * vs[k + 3];
+    }
+    for (; k < nb; ++k) s0 += S[(size_t)k * nb + i] * vs[k];
+    z[cell * nb + i] = (Tout)(-((s0 + s1) + (s2 + s3)));
+}
+
 // blocks per cell: enough blocks for two per SM when cells are few
 static int precond_rsplit(long long Nc, long long nb) {
     int r = 1;
@@ -1108,6 +1147,13 @@ cudaError_t launch_precond(const Geo<T>& g, const T* Sinv, const Tin* v, Tout* z
         const int threads = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256);
         k_precond_f64<Tin, Tout><<<dim3((unsigned)g.Nc, bt.np), threads, g.nb * sizeof(double), s>>>(g, Sinv, v, z,
                                                                                                      ctl, bt);
+        note_launch();
+        return cudaGetLastError();
+    }
+    if (g.nb <= 128) {
+        const int gsz = (int)((g.nb + 31) / 32) * 32, cpb = 256 / gsz;
+        const dim3 grid((unsigned)((g.Nc + cpb - 1) / cpb), bt.np);
+        k_precond_col<T, Tin, Tout><<<grid, 256, (size_t)cpb * gsz * sizeof(T), s>>>(g, Sinv, v, z, ctl, gsz, bt);
         note_launch();
         return cudaGetLastError();
     }
@@ -1543,6 +1589,143 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         }
 }
 
+// ---- split-K pipelined variant with 8 x 8 register tiles -------------------------
+// For batches.  The 4 x 4 tiles of k_gemm_pipe load 2 floats from shared memory per
+// multiply-add and are bound by shared-memory bandwidth; here each thread holds 8 x 8
+// outputs (1 float per 4 multiply-adds).  To keep enough threads per tile, the KS warp
+// groups of a CTA take the KS K ranges in parallel -- each streams its range in chunks of
+// 16 through its own three-deep ring of shared buffers, synchronising on its own named
+// barrier -- and the group partials are added in range order at the end, the summation
+// of the whole-K tiles with the same KS (the same bits).
+template <typename T, int BM, int BN, int TM, int TN, int KS>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
+    k_gemm_pipe2(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp, FdmScale sc,
+                 const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2, const int* skip,
+                 Bat bt) {
+    constexpr int BK = 16, NS = 3, NG = (BM / TM) * (BN / TN);
+    constexpr int STAGE = BK * (BM + BN);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    GEMM_BATCH_ENTER()
+    const int tid = threadIdx.x, grp = tid / NG, gt = tid - grp * NG;
+    const int tx = gt % (BN / TN), ty = gt / (BN / TN);
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int b = (int)blockIdx.z - prob_ * a.batch;
+    const T* A = Ap + (long long)b * a.sAb;
+    const T* B = Bp + (long long)b * a.sBb;
+    T* C = Cp + (long long)b * a.sCb;
+    const int K = a.K;
+    const int kchunk = (K + KS - 1) / KS;
+    T* ring = reinterpret_cast<T*>(smraw) + (size_t)grp * NS * STAGE;
+    const int kb = grp * kchunk, ke = min(K, kb + kchunk);
+    const int nch = kb < ke ? (ke - kb + BK - 1) / BK : 0;
+    auto stage = [&](int buf, int k0) {
+        T* As = ring + (size_t)buf * STAGE;
+        T* Bs = As + BK * BM;
+        for (int e = gt; e < BM * BK; e += NG) {
+            const int mm = e % BM, kk = e / BM, gm = m0 + mm, k = k0 + kk;
+            const bool ok = gm < a.M && k < ke;
+            cp_async_elem(&As[kk * BM + mm], ok ? A + (long long)gm * a.sAm + (long long)k * a.sAk : A, ok);
+        }
+        for (int e = gt; e < BN * BK; e += NG) {
+            const int nn = e % BN, kk = e / BN, gn = n0 + nn, k = k0 + kk;
+            const bool ok = gn < a.N && k < ke;
+            cp_async_elem(&Bs[kk * BN + nn], ok ? B + (long long)k * a.sBk + (long long)gn * a.sBn : B, ok);
+        }
+    };
+    auto group_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(NG) : "memory"); };
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) acc[i][jj] = T(0);
+#pragma unroll
+    for (int st = 0; st < NS - 1; ++st) {
+        if (st < nch) stage(st, kb + st * BK);
+        cp_async_commit();
+    }
+    for (int c = 0; c < nch; ++c) {
+        if (c + NS - 1 < nch) stage((c + NS - 1) % NS, kb + (c + NS - 1) * BK);
+        cp_async_commit();
+        cp_async_wait_group<NS - 1>();
+        group_sync();
+        const T* As = ring + (size_t)(c % NS) * STAGE;
+        const T* Bs = As + BK * BM;
+        const int kn = min(BK, ke - (kb + c * BK));
+        for (int kk = 0; kk < kn; ++kk) {
+            T av[TM], bv[TN];
+            if constexpr (sizeof(T) == 4 && TM % 4 == 0 && TN % 4 == 0) {
+#pragma unroll
+                for (int q = 0; q < TM / 4; ++q) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(&As[kk * BM + ty * TM + 4 * q]);
+                    av[4 * q] = v4.x; av[4 * q + 1] = v4.y; av[4 * q + 2] = v4.z; av[4 * q + 3] = v4.w;
+                }
+#pragma unroll
+                for (int q = 0; q < TN / 4; ++q) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(&Bs[kk * BN + tx * TN + 4 * q]);
+                    bv[4 * q] = v4.x; bv[4 * q + 1] = v4.y; bv[4 * q + 2] = v4.z; bv[4 * q + 3] = v4.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < TM; ++i) av[i] = As[kk * BM + ty * TM + i];
+#pragma unroll
+                for (int jj = 0; jj < TN; ++jj) bv[jj] = Bs[kk * BN + tx * TN + jj];
+            }
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int jj = 0; jj < TN; ++jj) acc[i][jj] += av[i] * bv[jj];
+        }
+        group_sync();
+    }
+    cp_async_wait_group<0>();
+    if (KS > 1) {
+        // group partials through shared memory, added in range order (deterministic)
+        __syncthreads();
+        T* red = reinterpret_cast<T*>(smraw);
+        if (grp > 0)
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int jj = 0; jj < TN; ++jj) red[((size_t)(grp - 1) * NG + gt) * (TM * TN) + i * TN + jj] = acc[i][jj];
+        __syncthreads();
+        if (grp > 0) return;
+        for (int g2 = 1; g2 < KS; ++g2)
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int jj = 0; jj < TN; ++jj) acc[i][jj] += red[((size_t)(g2 - 1) * NG + gt) * (TM * TN) + i * TN + jj];
+    }
+    T ainv = T(1);
+    if (sc.on) ainv = (T)(1.0 / (sc.alpha_dev ? *sc.alpha_dev : sc.alpha_host));
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) {
+            const int gm = m0 + ty * TM + i, gn = n0 + tx * TN + jj;
+            if (gm < a.M && gn < a.N) {
+                const long long off = (long long)gm * a.sCm + (long long)gn * a.sCn;
+                T v = acc[i][jj];
+                if (sc.on) {
+                    long long lin = off + (long long)b * a.sCb;
+                    const int i0 = (int)(lin % sc.n1[0]);
+                    lin /= sc.n1[0];
+                    const int i1 = (int)(lin % sc.n1[1]);
+                    T lsum = l0[i0] + l1[i1];
+                    if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                    v = v * ainv / lsum;
+                }
+                C[off] = v;
+            }
+        }
+}
+
+template <typename T, int BM, int BN, int TM, int TN, int KS>
+constexpr size_t pipe2_smem() {
+    constexpr size_t ring = (size_t)KS * 3 * 16 * (BM + BN) * sizeof(T);
+    constexpr size_t red = (size_t)(KS - 1) * (BM / TM) * (BN / TN) * TM * TN * sizeof(T);
+    return ring > red ? ring : red;
+}
+
 // ---- tensor-core variant of the FP32 pass (tcgen05, 3xTF32) ------------------
 // C = A B on the 5th-generation tensor cores.  Each operand is split as x = hi + lo
 // with hi = x rounded to TF32 (10-bit mantissa) and lo = x - hi (exact in FP32);
@@ -1834,12 +2017,21 @@ struct Tile { static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, KS = 
 // the pipelined K-chunked kernel (k_gemm_pipe) with the same parameters
 template <typename T, int BM_, int BN_, int TM_, int TN_, int KS_>
 struct PTile { static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, KS = KS_, PIPE = 1; };
+// the split-K pipelined kernel (k_gemm_pipe2)
+template <typename T, int BM_, int BN_, int TM_, int TN_, int KS_>
+struct QTile { static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_, KS = KS_, PIPE = 2; };
 
 template <typename T, typename C>
 static cudaError_t launch_tile(const GemmArgs& a, const T* A, const T* B, T* Cp, const FdmScale& sc, const T* l0,
                                const T* l1, const T* l2, cudaStream_t s, const int* skip, const Bat& bt) {
     constexpr int BM = C::BM, BN = C::BN, TM = C::TM, TN = C::TN, KS = C::KS;
-    if constexpr (C::PIPE) {
+    if constexpr (C::PIPE == 2) {
+        dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch * bt.np);
+        k_gemm_pipe2<T, BM, BN, TM, TN, KS><<<grid, (BM / TM) * (BN / TN) * KS, pipe2_smem<T, BM, BN, TM, TN, KS>(),
+                                              s>>>(a, A, B, Cp, sc, l0, l1, l2, skip, bt);
+        note_launch();
+        return cudaGetLastError();
+    } else if constexpr (C::PIPE == 1) {
         dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch * bt.np);
         k_gemm_pipe<T, BM, BN, TM, TN, KS><<<grid, (BM / TM) * (BN / TN), 0, s>>>(a, A, B, Cp, sc, l0, l1, l2, skip,
                                                                                 bt);
@@ -1866,7 +2058,8 @@ static cudaError_t launch_tile(const GemmArgs& a, const T* A, const T* B, T* Cp,
 using F32Tiles = std::tuple<Tile<float, 32, 16, 4, 2, 4>, Tile<float, 32, 32, 4, 2, 2>, Tile<float, 32, 16, 4, 2, 2>,
                             Tile<float, 16, 16, 2, 2, 4>, Tile<float, 32, 32, 4, 2, 4>, Tile<float, 64, 32, 8, 4, 4>,
                             Tile<float, 64, 32, 8, 4, 2>, Tile<float, 64, 64, 8, 8, 4>, PTile<float, 64, 64, 4, 4, 4>,
-                            PTile<float, 32, 64, 4, 4, 4>, PTile<float, 64, 64, 4, 4, 2>, PTile<float, 32, 64, 4, 4, 2>>;
+                            PTile<float, 32, 64, 4, 4, 4>, PTile<float, 64, 64, 4, 4, 2>, PTile<float, 32, 64, 4, 4, 2>,
+                            QTile<float, 64, 64, 8, 8, 4>, QTile<float, 64, 32, 8, 4, 4>, QTile<float, 64, 64, 8, 8, 2>>;
 using F64Tiles = std::tuple<Tile<double, 16, 16, 2, 2, 1>, Tile<double, 16, 16, 2, 2, 2>,
                             Tile<double, 32, 16, 4, 2, 1>, Tile<double, 16, 8, 2, 2, 2>>;
 template <typename T>
@@ -1921,8 +2114,11 @@ static void configure_tiles() {
     using Set = typename TileSet<T>::type;
     if constexpr (I < std::tuple_size<Set>::value) {
         using C = typename std::tuple_element<I, Set>::type;
-        if constexpr (!C::PIPE)
+        if constexpr (C::PIPE == 0)
             cudaFuncSetAttribute(k_gemm_fullk<T, C::BM, C::BN, C::TM, C::TN, C::KS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if constexpr (C::PIPE == 2)
+            cudaFuncSetAttribute(k_gemm_pipe2<T, C::BM, C::BN, C::TM, C::TN, C::KS>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         configure_tiles<T, I + 1>();
     }
