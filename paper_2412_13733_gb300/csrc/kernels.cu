@@ -1598,12 +1598,17 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // barrier -- and the group partials are added in range order at the end, the summation
 // of the whole-K tiles with the same KS (the same bits).
 template <typename T, int BM, int BN, int TM, int TN, int KS>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
+__global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS, 2)
     k_gemm_pipe2(GemmArgs a, const T* __restrict__ Ap, const T* __restrict__ Bp, T* __restrict__ Cp, FdmScale sc,
                  const T* __restrict__ l0, const T* __restrict__ l1, const T* __restrict__ l2, const int* skip,
                  Bat bt) {
     constexpr int BK = 16, NS = 3, NG = (BM / TM) * (BN / TN);
-    constexpr int STAGE = BK * (BM + BN);
+    // panel rows padded by 4 floats: the k-contiguous staging writes 16 k's of one row,
+    // which would otherwise all fall in one bank
+    constexpr int BMP = BM + 4, BNP = BN + 4;
+    constexpr int STAGE = BK * (BMP + BNP);
+    static_assert(NG % BM == 0 && NG % BN == 0 && NG % BK == 0, "staging map");
+    constexpr int EA = BM * BK / NG, EB = BN * BK / NG;
     extern __shared__ __align__(16) unsigned char smraw[];
     GEMM_BATCH_ENTER()
     const int tid = threadIdx.x, grp = tid / NG, gt = tid - grp * NG;
@@ -1618,18 +1623,27 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
     T* ring = reinterpret_cast<T*>(smraw) + (size_t)grp * NS * STAGE;
     const int kb = grp * kchunk, ke = min(K, kb + kchunk);
     const int nch = kb < ke ? (ke - kb + BK - 1) / BK : 0;
+    // staging map of each operand, fixed per thread: consecutive threads take consecutive
+    // global words (along k when the operand is k-contiguous, else along m / n)
+    const bool ak = a.sAk == 1, bk = a.sBk == 1;
+    const int a_mm = ak ? gt / BK : gt % BM, a_kk = ak ? gt % BK : gt / BM;
+    const int a_dm = ak ? NG / BK : 0, a_dk = ak ? 0 : NG / BM;
+    const int b_nn = bk ? gt / BK : gt % BN, b_kk = bk ? gt % BK : gt / BN;
+    const int b_dn = bk ? NG / BK : 0, b_dk = bk ? 0 : NG / BN;
     auto stage = [&](int buf, int k0) {
         T* As = ring + (size_t)buf * STAGE;
-        T* Bs = As + BK * BM;
-        for (int e = gt; e < BM * BK; e += NG) {
-            const int mm = e % BM, kk = e / BM, gm = m0 + mm, k = k0 + kk;
+        T* Bs = As + BK * BMP;
+#pragma unroll
+        for (int q = 0; q < EA; ++q) {
+            const int mm = a_mm + q * a_dm, kk = a_kk + q * a_dk, gm = m0 + mm, k = k0 + kk;
             const bool ok = gm < a.M && k < ke;
-            cp_async_elem(&As[kk * BM + mm], ok ? A + (long long)gm * a.sAm + (long long)k * a.sAk : A, ok);
+            cp_async_elem(&As[kk * BMP + mm], ok ? A + (long long)gm * a.sAm + (long long)k * a.sAk : A, ok);
         }
-        for (int e = gt; e < BN * BK; e += NG) {
-            const int nn = e % BN, kk = e / BN, gn = n0 + nn, k = k0 + kk;
+#pragma unroll
+        for (int q = 0; q < EB; ++q) {
+            const int nn = b_nn + q * b_dn, kk = b_kk + q * b_dk, gn = n0 + nn, k = k0 + kk;
             const bool ok = gn < a.N && k < ke;
-            cp_async_elem(&Bs[kk * BN + nn], ok ? B + (long long)k * a.sBk + (long long)gn * a.sBn : B, ok);
+            cp_async_elem(&Bs[kk * BNP + nn], ok ? B + (long long)k * a.sBk + (long long)gn * a.sBn : B, ok);
         }
     };
     auto group_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(NG) : "memory"); };
@@ -1649,31 +1663,37 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
         cp_async_wait_group<NS - 1>();
         group_sync();
         const T* As = ring + (size_t)(c % NS) * STAGE;
-        const T* Bs = As + BK * BM;
+        const T* Bs = As + BK * BMP;
         const int kn = min(BK, ke - (kb + c * BK));
-        for (int kk = 0; kk < kn; ++kk) {
+        auto step = [&](int kk) {
             T av[TM], bv[TN];
             if constexpr (sizeof(T) == 4 && TM % 4 == 0 && TN % 4 == 0) {
 #pragma unroll
                 for (int q = 0; q < TM / 4; ++q) {
-                    const float4 v4 = *reinterpret_cast<const float4*>(&As[kk * BM + ty * TM + 4 * q]);
+                    const float4 v4 = *reinterpret_cast<const float4*>(&As[kk * BMP + ty * TM + 4 * q]);
                     av[4 * q] = v4.x; av[4 * q + 1] = v4.y; av[4 * q + 2] = v4.z; av[4 * q + 3] = v4.w;
                 }
 #pragma unroll
                 for (int q = 0; q < TN / 4; ++q) {
-                    const float4 v4 = *reinterpret_cast<const float4*>(&Bs[kk * BN + tx * TN + 4 * q]);
+                    const float4 v4 = *reinterpret_cast<const float4*>(&Bs[kk * BNP + tx * TN + 4 * q]);
                     bv[4 * q] = v4.x; bv[4 * q + 1] = v4.y; bv[4 * q + 2] = v4.z; bv[4 * q + 3] = v4.w;
                 }
             } else {
 #pragma unroll
-                for (int i = 0; i < TM; ++i) av[i] = As[kk * BM + ty * TM + i];
+                for (int i = 0; i < TM; ++i) av[i] = As[kk * BMP + ty * TM + i];
 #pragma unroll
-                for (int jj = 0; jj < TN; ++jj) bv[jj] = Bs[kk * BN + tx * TN + jj];
+                for (int jj = 0; jj < TN; ++jj) bv[jj] = Bs[kk * BNP + tx * TN + jj];
             }
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
                 for (int jj = 0; jj < TN; ++jj) acc[i][jj] += av[i] * bv[jj];
+        };
+        if (kn == BK) {
+#pragma unroll 4
+            for (int kk = 0; kk < BK; ++kk) step(kk);
+        } else {
+            for (int kk = 0; kk < kn; ++kk) step(kk);
         }
         group_sync();
     }
@@ -1721,7 +1741,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
 
 template <typename T, int BM, int BN, int TM, int TN, int KS>
 constexpr size_t pipe2_smem() {
-    constexpr size_t ring = (size_t)KS * 3 * 16 * (BM + BN) * sizeof(T);
+    constexpr size_t ring = (size_t)KS * 3 * 16 * (BM + 4 + BN + 4) * sizeof(T);
     constexpr size_t red = (size_t)(KS - 1) * (BM / TM) * (BN / TN) * TM * TN * sizeof(T);
     return ring > red ? ring : red;
 }
