@@ -556,9 +556,16 @@ def main():
         _, fl, _ = work["newton_apply"]
         t_alu = fl / (alu_peaks["fp64"] * 1e12)
         t_hbm = work["newton_apply_bytes"] / (peaks["hbm_gbs"] * 1e9)
-        newton_roof = {"kernel": "matrix-free Newton apply G x (FP64)", "bound": "alu" if t_alu > t_hbm else "hbm",
+        newton_roof = {"kernel": "matrix-free Newton apply G x (FP64), one problem",
+                       "bound": "alu" if t_alu > t_hbm else "hbm",
                        "roofline_us": max(t_alu, t_hbm) * 1e6, "avg_us": avg * 1e6, "frac": max(t_alu, t_hbm) / avg,
                        "peak_source": "measured FP64 FMA rate (hpg_measure_fma_peak) and HBM copy rate"}
+        if "newton_apply" in kb:
+            # as the batched step launches it: every problem of the group in one launch
+            avg_b = kb["newton_apply"][0] / 1000.0
+            t_b = max(t_alu, t_hbm) * B
+            newton_roof["batched"] = {"problems_per_launch": B, "roofline_us": t_b * 1e6, "avg_us": avg_b * 1e6,
+                                      "frac": t_b / avg_b, "achieved_tflops": fl * B / avg_b / 1e12}
     # bandwidth-bound kernels against the measured HBM copy rate (their operands may
     # be L2-resident, so a fraction above 1 means L2 service, not an error)
     bw_roofs = {}
