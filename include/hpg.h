@@ -412,6 +412,70 @@ hpg_status hpg_apply_stiffness_inv_noalloc(hpg_ctx* ctx, int pid, double alpha, 
  * Needs the problem's operators on the device (after hpg_solve or hpg_set_state). */
 hpg_status hpg_stiffness_solve_pcg(hpg_ctx* ctx, int pid, int precond, double alpha, const double* b, double* x,
                                    size_t len, double rtol, double atol, int maxit, int* its);
+/* ---------------------------------------------------------------- thermoforming QVI */
+/* The quasi-variational inequality of Section 6.4 (thermoforming): the membrane u of
+ * an upper-obstacle problem (this problem: HPG_OBSTACLE_UPPER, its rhs, Dirichlet data
+ * and alpha schedule as set) under the obstacle Phi_0 + xi T, where the mould
+ * temperature T in U_{h,p} (all dofs, no boundary condition) solves
+ *     (grad T, grad q) + gamma (T, q) = (g(Phi_0 + xi T - u), q)   for all q,
+ *     g(s) = g0 for s <= 0, g0 (1 - s) for 0 < s < 1, 0 for s >= 1.
+ * Fixed point from T_0 = 0: (I) the obstacle problem with phi = Phi_0 + xi T_i at the
+ * latent Gauss points (a full hpG solve, psi_0 = 0); (II) T_{i+1} by Newton on the T
+ * equation from T_i, each Newton system by GMRES right-preconditioned with
+ * (A + gamma M)^{-1} (fast diagonalisation of the full-space 1D pencils), until
+ * ||R(T)||_2 <= t_tol; stop once ||u_{i+1} - u_i||_{H^1} <= tol (i >= 1).  The nonsmooth
+ * integral (g(.), q) uses nq Gauss points per direction per cell. */
+typedef struct {
+    double gamma;         /* > 0; default 1                                            */
+    double g0;            /* >= 0; default 0.2                                         */
+    double tol;           /* H^1 stopping tolerance of the fixed point; default 3e-3   */
+    double t_tol;         /* absolute ||R(T)||_2 of the T Newton; default 1e-10        */
+    int    max_fp;        /* fixed-point cap (<= HPG_QVI_MAX_FP); default 30           */
+    int    nq;            /* Gauss points per direction per cell of the T equation;
+                             p + 2 by default (0)                                       */
+    int    t_newton_max;  /* Newton cap of one T solve; default 50                     */
+    int    t_krylov_max;  /* GMRES cap of one T Newton system; default 200             */
+    double t_krylov_rtol; /* GMRES relative tolerance; default 1.5e-8 (Section 6.4)    */
+} hpg_qvi_params;
+
+#define HPG_QVI_MAX_FP 64
+
+typedef struct {
+    int    status;                      /* hpg_status of the QVI solve                  */
+    int    iterations;                  /* fixed-point iterations taken                 */
+    int    converged;                   /* 1 when the H^1 test was met                  */
+    int    newton_total;                /* Newton steps of the obstacle solves          */
+    int    t_newton_total;              /* Newton steps of the T solves                 */
+    long long t_krylov_total;           /* GMRES iterations of the T Newton systems     */
+    double du_h1[HPG_QVI_MAX_FP];       /* ||u_i - u_{i-1}||_{H^1} per iteration (entry 0: 0) */
+    int    newton_per_fp[HPG_QVI_MAX_FP];   /* obstacle Newton steps per iteration       */
+    int    t_newton_per_fp[HPG_QVI_MAX_FP]; /* T Newton steps per iteration              */
+    double t_residual;                  /* ||R(T)||_2 at the end                        */
+    double solve_ms;                    /* wall time (host clock)                       */
+    long long kernel_launches;          /* libhpg kernels launched by the QVI solve     */
+} hpg_qvi_stats;
+
+/* Defaults of hpg_qvi_params. */
+hpg_status hpg_qvi_default_params(hpg_qvi_params* out);
+/* The T-equation Gauss points of problem pid (nq per direction per cell; 0: p + 2):
+ * Nc nq^d points, cell-major (cells as psi), x index fastest inside a cell; pts holds
+ * len >= Nc nq^d dim doubles. */
+hpg_status hpg_qvi_points(hpg_ctx* ctx, int pid, int nq, double* pts, size_t len);
+/* Solve the QVI.  phi0_lat, xi_lat: Phi_0 and xi at the latent Gauss points
+ * (hpg_quad_points order, n_lat = Nq values each); phi0_q, xi_q: at the T-equation
+ * points of hpg_qvi_points for params->nq (n_q values each).  Afterwards hpg_get_u and
+ * hpg_get_psi give the last obstacle solve, hpg_qvi_get_T the temperature, and the
+ * problem's constraint is the last obstacle Phi_0 + xi T_i.  Errors: HPG_ERR_ARG for a
+ * kind other than HPG_OBSTACLE_UPPER, wrong lengths or parameters, or cells too large
+ * for shared memory ((max(p+1, nq))^d doubles twice); the obstacle solve's status when
+ * it fails (hpg_last_error names the iteration); HPG_ERR_NEWTON_CAP when a T Newton
+ * or the fixed point runs out. */
+hpg_status hpg_qvi_solve(hpg_ctx* ctx, int pid, const hpg_qvi_params* params, const double* phi0_lat,
+                         const double* xi_lat, size_t n_lat, const double* phi0_q, const double* xi_q, size_t n_q,
+                         hpg_qvi_stats* stats);
+/* The temperature T of the last hpg_qvi_solve (full U_{h,p} coefficients, len >= the
+ * full u length). */
+hpg_status hpg_qvi_get_T(hpg_ctx* ctx, int pid, double* T_full, size_t len);
 /* Solve G delta = F(state) by eq. (schur2) + GMRES (relative tolerance rtol);
  * returns delta and the GMRES iteration count. */
 hpg_status hpg_newton_direction(hpg_ctx* ctx, int pid, int precision, double rtol, double* delta,

@@ -757,4 +757,83 @@ hpg_status hpg_server_memory(hpg_ctx* ctx, int pid, size_t* in_use, size_t* esti
     return HPG_OK;
 }
 
+hpg_status hpg_qvi_default_params(hpg_qvi_params* out) {
+    if (!out) return HPG_ERR_ARG;
+    *out = hpg_qvi_params{};
+    out->gamma = 1.0;
+    out->g0 = 0.2;
+    out->tol = 3e-3;
+    out->t_tol = 1e-10;
+    out->max_fp = 30;
+    out->nq = 0;
+    out->t_newton_max = 50;
+    out->t_krylov_max = 200;
+    out->t_krylov_rtol = 1.5e-8;
+    return HPG_OK;
+}
+
+static size_t qvi_npts(const hpg::HostProblem& H, int nq) {
+    size_t per = 1;
+    for (int j = 0; j < H.d; ++j) per *= (size_t)nq;
+    return H.Nc * per;
+}
+
+hpg_status hpg_qvi_points(hpg_ctx* ctx, int pid, int nq, double* pts, size_t len) {
+    Problem* P = find(ctx, pid);
+    if (!P || !pts || nq < 0 || nq > 64) return HPG_ERR_ARG;
+    const int q = nq > 0 ? nq : P->H.p + 2;
+    if (len < qvi_npts(P->H, q) * P->H.d) return HPG_ERR_ARG;
+    GUARD_BEGIN
+    std::vector<double> v;
+    hpg::qvi_points(P->H, q, v);
+    std::memcpy(pts, v.data(), v.size() * sizeof(double));
+    return HPG_OK;
+    GUARD_END
+}
+
+hpg_status hpg_qvi_solve(hpg_ctx* ctx, int pid, const hpg_qvi_params* params, const double* phi0_lat,
+                         const double* xi_lat, size_t n_lat, const double* phi0_q, const double* xi_q, size_t n_q,
+                         hpg_qvi_stats* stats) {
+    Problem* P = find(ctx, pid);
+    if (!P || !params || !phi0_lat || !xi_lat || !phi0_q || !xi_q) return HPG_ERR_ARG;
+    NOT_BUSY(P);
+    const hpg::HostProblem& H = P->H;
+    const hpg_qvi_params& q = *params;
+    const int nq = q.nq > 0 ? q.nq : H.p + 2;
+    if (H.kind != HPG_OBSTACLE_UPPER) { ctx->err = "QVI needs an HPG_OBSTACLE_UPPER problem"; return HPG_ERR_ARG; }
+    if (!(q.gamma > 0.0) || !(q.g0 >= 0.0) || !(q.tol > 0.0) || !(q.t_tol > 0.0) || q.max_fp < 1 ||
+        q.max_fp > HPG_QVI_MAX_FP || q.nq < 0 || q.nq > 64 || q.t_newton_max < 1 || q.t_krylov_max < 1 ||
+        q.t_krylov_max > hpg::kMaxKrylov || !(q.t_krylov_rtol > 0.0)) {
+        ctx->err = "invalid QVI parameters";
+        return HPG_ERR_ARG;
+    }
+    if (n_lat < H.Nq || n_q < qvi_npts(H, nq)) { ctx->err = "QVI data arrays too short"; return HPG_ERR_ARG; }
+    size_t capq = 1, capl = 1;
+    for (int j = 0; j < H.d; ++j) {
+        capq *= (size_t)std::max(H.p + 1, nq);
+        capl *= (size_t)std::max(H.p + 1, H.n);
+    }
+    if (2 * std::max(capq, capl) * sizeof(double) > hpg::kCellSmemMax) {
+        ctx->err = "QVI cell tables exceed shared memory";
+        return HPG_ERR_ARG;
+    }
+    if (P->H.alphas.empty()) { ctx->err = "alpha schedule not set"; return HPG_ERR_STATE; }
+    hpg_status s = cuda_ok(ctx);
+    if (s != HPG_OK) return s;
+    GUARD_BEGIN
+    ctx->err.clear();
+    P->host_result = false;
+    return hpg::qvi_solve(ctx, *P, q, phi0_lat, xi_lat, phi0_q, xi_q, stats);
+    GUARD_END
+}
+
+hpg_status hpg_qvi_get_T(hpg_ctx* ctx, int pid, double* T_full, size_t len) {
+    Problem* P = find(ctx, pid);
+    if (!P || !T_full) return HPG_ERR_ARG;
+    if (len < P->H.Nu_full) return HPG_ERR_ARG;
+    if (P->qvi_T.size() != P->H.Nu_full) { ctx->err = "no QVI solve on this problem"; return HPG_ERR_STATE; }
+    std::memcpy(T_full, P->qvi_T.data(), P->H.Nu_full * sizeof(double));
+    return HPG_OK;
+}
+
 }  // extern "C"

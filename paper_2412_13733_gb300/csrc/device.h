@@ -119,6 +119,8 @@ cudaError_t launch_project(const Geo<double>& g, const double* phiq, double* phi
 // Number of kernels launched (or replayed in graphs) by this library from the calling
 // host thread since it started.
 long long kernel_launch_count();
+// Add n kernels launched by another translation unit of the library to that count.
+void note_kernel_launches(long long n);
 void add_kernel_launches(long long n);
 
 // F_u = alpha A u + alpha rA + B (psi - psi_prev) - alpha bf;  F_psi = B^T u + rB + sgn*eg - phiz.
@@ -156,11 +158,12 @@ cudaError_t launch_bapply(const Geo<T>& g, const Tin* z, Tout* y, cudaStream_t s
 template <typename T, typename Tin, typename Tout>
 cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t s, const Bat& bt = Bat{});
 
-// y = A_alpha^{-1} x (interior) by fast diagonalisation; work1/work2 scratch of Nu0.
+// y = A_alpha^{-1} x (interior) by fast diagonalisation; work1/work2 scratch of Nu0.  With
+// shift s > 0 (and alpha 1): y = (A + s M)^{-1} x for the pencil of g's eigenpairs.
 // alpha is read from alpha_dev when non-null (graph replay), else alpha.
 template <typename T>
 cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, const T* x, T* y, T* work1,
-                       T* work2, cudaStream_t s, const int* skip = nullptr, const Bat& bt = Bat{});
+                       T* work2, cudaStream_t s, const int* skip = nullptr, const Bat& bt = Bat{}, double shift = 0.0);
 
 // w = -(D z + E z + B^T t)  (per cell), D from gw.  z, t in T; w in Tout.
 template <typename T, typename Tout>

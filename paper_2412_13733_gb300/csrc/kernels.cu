@@ -114,6 +114,7 @@ __device__ __forceinline__ void sf_pass(const T* in, T* out, const T* mat, bool 
 }  // namespace
 
 long long kernel_launch_count() { return t_launches; }
+void note_kernel_launches(long long n) { t_launches += n; }
 
 // ============================================================ tiled u-row applies
 // y[i] over interior u-dofs i of  cA * (A x)[i] + cB * (B z)[i]  (+ residual terms),
@@ -1241,6 +1242,7 @@ struct FdmScale {
     int n1[kMaxDim];
     const double* alpha_dev;   // alpha on the device (graph-friendly); null: use alpha_host
     double alpha_host;
+    double shift;              // added to the eigenvalue sums: (A + shift M)^{-1} (0 for A_alpha^{-1})
 };
 
 // Asynchronous 4/8-byte global->shared copy (LDGSTS); `valid` false zero-fills.
@@ -1373,6 +1375,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS)
                     const int i1 = (int)(lin % sc.n1[1]);
                     T lsum = l0[i0] + l1[i1];
                     if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                    lsum += (decltype(lsum))sc.shift;
                     v = v * ainv / lsum;
                 }
                 C[off] = v;
@@ -1449,6 +1452,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
                     const int i1 = (int)(lin % sc.n1[1]);
                     T lsum = l0[i0] + l1[i1];
                     if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                    lsum += (decltype(lsum))sc.shift;
                     v = v * ainv / lsum;
                 }
                 C[off] = v;
@@ -1582,6 +1586,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
                     const int i1 = (int)(lin % sc.n1[1]);
                     T lsum = l0[i0] + l1[i1];
                     if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                    lsum += (decltype(lsum))sc.shift;
                     v = v * ainv / lsum;
                 }
                 C[off] = v;
@@ -1732,6 +1737,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN) * KS, 2)
                     const int i1 = (int)(lin % sc.n1[1]);
                     T lsum = l0[i0] + l1[i1];
                     if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                    lsum += (decltype(lsum))sc.shift;
                     v = v * ainv / lsum;
                 }
                 C[off] = v;
@@ -2004,6 +2010,7 @@ __global__ void __launch_bounds__(256, 1)
                 const int i1 = (int)(lin % sc.n1[1]);
                 float lsum = l0[i0] + l1[i1];
                 if (sc.d == 3) lsum += l2[(int)(lin / sc.n1[1])];
+                    lsum += (decltype(lsum))sc.shift;
                 val = val * ainv / lsum;
             }
             C[off] = val;
@@ -2156,7 +2163,7 @@ static cudaError_t gemm(const GemmArgs& a, const T* A, const T* B, T* C, const F
 // A_alpha^{-1} x = alpha^{-1} (V (x) V (x) V) diag(1 / sum lam) (V^T (x) V^T (x) V^T) x
 template <typename T>
 cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, const T* x, T* y, T* work1, T* work2,
-                       cudaStream_t s, const int* skip, const Bat& bt) {
+                       cudaStream_t s, const int* skip, const Bat& bt, double shift) {
     const int d = g.d;
     long long inner[kMaxDim], outer[kMaxDim];
     for (int ax = 0; ax < d; ++ax) {
@@ -2172,6 +2179,7 @@ cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, c
     for (int j = 0; j < kMaxDim; ++j) on.n1[j] = g.n1[j];
     on.alpha_dev = alpha_dev;
     on.alpha_host = alpha;
+    on.shift = shift;
     // pass along axis ax: out[o][a][i] = sum_k W(a,k) in[o][k][i]; W = V^T (fwd) or V (bwd)
     auto pass = [&](int ax, bool fwd, const T* in, T* out, const FdmScale& sc) -> cudaError_t {
         const int n1 = g.n1[ax];
@@ -3669,9 +3677,9 @@ template cudaError_t launch_btapply<double, double, double>(const Geo<double>&, 
 template cudaError_t launch_btapply<float, float, float>(const Geo<float>&, const float*, float*, cudaStream_t,
                                                          const Bat&);
 template cudaError_t launch_fdm<double>(const Geo<double>&, const double*, double, const double*, double*, double*,
-                                        double*, cudaStream_t, const int*, const Bat&);
+                                        double*, cudaStream_t, const int*, const Bat&, double);
 template cudaError_t launch_fdm<float>(const Geo<float>&, const double*, double, const float*, float*, float*,
-                                       float*, cudaStream_t, const int*, const Bat&);
+                                       float*, cudaStream_t, const int*, const Bat&, double);
 template cudaError_t launch_schur_rest<double, double>(const Geo<double>&, const double*, double, const double*,
                                                        const double*, double*, cudaStream_t, IterCtl, const Bat&);
 template cudaError_t launch_schur_rest<float, float>(const Geo<float>&, const float*, double, const float*,

@@ -123,6 +123,7 @@ struct Problem {
     KernelTimer timer;
     double* pinned_scal = nullptr;   // 16 doubles + 8 ints of pinned host memory, lazily allocated
     int* pinned_iflag = nullptr;
+    std::vector<double> qvi_T;       // temperature of the last QVI solve (full u numbering)
     ~Problem();
 };
 
@@ -191,5 +192,10 @@ void server_release(hpg_ctx* ctx, Problem& P);
 hpg_status server_ticket_error(hpg_ctx* ctx, long long ticket, std::string* msg);
 hpg_status server_set_policy(hpg_ctx* ctx, int policy);
 size_t server_in_use(hpg_ctx* ctx);
+// thermoforming QVI (Section 6.4): T-equation Gauss points (Nc nq^d x d, cell-major,
+// x fastest) and the fixed point of obstacle and temperature solves
+void qvi_points(const HostProblem& H, int nq, std::vector<double>& pts);
+hpg_status qvi_solve(hpg_ctx* ctx, Problem& P, const hpg_qvi_params& q, const double* phi0_lat, const double* xi_lat,
+                     const double* phi0_q, const double* xi_q, hpg_qvi_stats* st);
 
 }  // namespace hpg

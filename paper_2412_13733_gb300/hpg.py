@@ -41,6 +41,23 @@ class hpg_stats(C.Structure):
                 ("ainv_total", C.c_longlong), ("ainv_iters", C.c_longlong)]
 
 
+HPG_QVI_MAX_FP = 64
+
+
+class hpg_qvi_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("g0", C.c_double), ("tol", C.c_double), ("t_tol", C.c_double),
+                ("max_fp", C.c_int), ("nq", C.c_int), ("t_newton_max", C.c_int), ("t_krylov_max", C.c_int),
+                ("t_krylov_rtol", C.c_double)]
+
+
+class hpg_qvi_stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("converged", C.c_int), ("newton_total", C.c_int),
+                ("t_newton_total", C.c_int), ("t_krylov_total", C.c_longlong),
+                ("du_h1", C.c_double * HPG_QVI_MAX_FP), ("newton_per_fp", C.c_int * HPG_QVI_MAX_FP),
+                ("t_newton_per_fp", C.c_int * HPG_QVI_MAX_FP), ("t_residual", C.c_double),
+                ("solve_ms", C.c_double), ("kernel_launches", C.c_longlong)]
+
+
 FIELD_FN = C.CFUNCTYPE(None, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
 
 _P = C.POINTER
@@ -101,6 +118,11 @@ SIGNATURES = {
     "hpg_server_policy": ([_ctx, C.c_int], C.c_int),
     "hpg_l2_error": ([_ctx, C.c_int, _pd, _sz, _pd, _pd], C.c_int),
     "hpg_measure_fma_peak": ([_ctx, C.c_int, _pd, _P(C.c_int)], C.c_int),
+    "hpg_qvi_default_params": ([_P(hpg_qvi_params)], C.c_int),
+    "hpg_qvi_points": ([_ctx, C.c_int, C.c_int, _pd, _sz], C.c_int),
+    "hpg_qvi_solve": ([_ctx, C.c_int, _P(hpg_qvi_params), _pd, _pd, _sz, _pd, _pd, _sz, _P(hpg_qvi_stats)],
+                      C.c_int),
+    "hpg_qvi_get_T": ([_ctx, C.c_int, _pd, _sz], C.c_int),
 }
 
 _lib = None
@@ -267,6 +289,7 @@ class Problem:
                   "hpg_problem_create")
         self.pid = pid.value
         self.dim = dim
+        self._p = int(p)
         self.cells = int(np.prod(cells))
         a, b, c, d = (_sz() for _ in range(4))
         ctx.check(self.L.hpg_problem_sizes(ctx.h, self.pid, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
@@ -443,10 +466,54 @@ class Problem:
                                                    d.size, C.byref(its)), "hpg_newton_direction")
         return d, its.value
 
+    # thermoforming QVI (Section 6.4)
+    def qvi_points(self, nq=0):
+        """Gauss points of the T equation (nq per direction per cell; 0: p + 2)."""
+        q = int(nq) if nq else None
+        L = self.L
+        # the count follows from the cells and nq
+        n = self.cells * (q or (self._p + 2)) ** self.dim
+        out = np.zeros(n * self.dim)
+        self.ctx.check(L.hpg_qvi_points(self.ctx.h, self.pid, int(nq), _dptr(out), out.size), "hpg_qvi_points")
+        return out.reshape(n, self.dim)
+
+    def qvi_solve(self, phi0_lat, xi_lat, phi0_q, xi_q, check=True, **kw):
+        """Fixed point of the thermoforming QVI; kw sets hpg_qvi_params fields.  Returns
+        (status, stats dict)."""
+        prm = qvi_default_params(**kw)
+        a, b, c, d = (_f64(v) for v in (phi0_lat, xi_lat, phi0_q, xi_q))
+        st = hpg_qvi_stats()
+        rc = self.L.hpg_qvi_solve(self.ctx.h, self.pid, C.byref(prm), _dptr(a), _dptr(b), min(a.size, b.size),
+                                  _dptr(c), _dptr(d), min(c.size, d.size), C.byref(st))
+        if check:
+            self.ctx.check(rc, "hpg_qvi_solve")
+        n = st.iterations
+        out = {k: getattr(st, k) for k, _ in hpg_qvi_stats._fields_
+               if k not in ("du_h1", "newton_per_fp", "t_newton_per_fp")}
+        out["du_h1"] = list(st.du_h1[:n])
+        out["newton_per_fp"] = list(st.newton_per_fp[:n])
+        out["t_newton_per_fp"] = list(st.t_newton_per_fp[:n])
+        return rc, out
+
+    def qvi_T(self):
+        out = np.zeros(self.n_u_full)
+        self.ctx.check(self.L.hpg_qvi_get_T(self.ctx.h, self.pid, _dptr(out), out.size), "hpg_qvi_get_T")
+        return out
+
     def free(self):
         if self.pid is not None:
             self.L.hpg_problem_free(self.ctx.h, self.pid)
             self.pid = None
+
+
+def qvi_default_params(**kw):
+    prm = hpg_qvi_params()
+    lib().hpg_qvi_default_params(C.byref(prm))
+    for k, v in kw.items():
+        if not hasattr(prm, k):
+            raise AttributeError(f"hpg_qvi_params has no field {k}")
+        setattr(prm, k, v)
+    return prm
 
 
 def from_workload(ctx, w, params=None):

@@ -89,6 +89,18 @@ def torsion_phi(X):
     return 0.5 + 0.25 * X[:, 0]
 
 
+def thermoforming_phi0(X):
+    """Original mould of Section 6.4 on (0,1)^d: 11/10 - 2 max_j |x_j - 1/2| + prod_j cos(8 pi x_j) / 10."""
+    X = np.atleast_2d(X)
+    return 1.1 - 2.0 * np.max(np.abs(X - 0.5), axis=1) + np.prod(np.cos(8 * np.pi * X), axis=1) / 10.0
+
+
+def thermoforming_xi(X):
+    """xi = prod_j sin(pi x_j) (Section 6.4)."""
+    X = np.atleast_2d(X)
+    return np.prod(np.sin(np.pi * X), axis=1)
+
+
 def alpha_list(alpha1, cap):
     """alpha_1, sqrt(2) growth, capped; stops once alpha repeats (Sections 6.1, 6.3, 6.5)."""
     out = []
@@ -135,6 +147,18 @@ def workload(name):
                     breakpoints=[uniform(0.0, 1.0, 10)] * 2, m=10, p=p,
                     f=const_field(100.0), f_const=100.0, phi=oscillatory_phi, g=None,
                     alphas=alpha_list(2.0 ** -7, 2.0 ** -3), beta=1e-4, tol=1e-6, exact=None)
+    if name.startswith("thermoforming_p"):
+        # Section 6.4's QVI: (0,1)^2, 4 x 4 cells, f = 100, gamma = 1, g0 = 1/5,
+        # alpha_1 = 2^-6 growing by 4 until alpha = 1, beta = 1e-6, H^1 tolerance 3e-3;
+        # name "thermoforming_p{p}" picks the degree ("..._m{m}" the cells per side)
+        parts = name[len("thermoforming_p"):].split("_m")
+        p = int(parts[0])
+        m = int(parts[1]) if len(parts) > 1 else 4
+        return dict(name=name, kind="obstacle", lower=False, dim=2,
+                    breakpoints=[uniform(0.0, 1.0, m)] * 2, m=m, p=p,
+                    f=const_field(100.0), f_const=100.0, phi=thermoforming_phi0, g=None,
+                    Phi0=thermoforming_phi0, xi=thermoforming_xi, gamma=1.0, g0=0.2,
+                    alphas=[2.0 ** -6, 2.0 ** -4, 2.0 ** -2, 1.0], beta=1e-6, tol=1e-10, qvi_tol=3e-3, exact=None)
     if name.startswith("box3d_"):
         # Section 6.5's 3D solver study: (0,1)^3, f = 40, phi = 1, alpha_1 = 2^-2, cap 2,
         # beta = 1e-5; name "box3d_p{p}_m{m}" picks the degree and cells per side

@@ -57,3 +57,16 @@ def test_fixed_point_converges_on_a_small_mesh():
     assert np.linalg.norm(q.T_residual(r["T"], r["u"])) < 1e-10
     d = [x["du_h1"] for x in h[1:]]
     assert all(b < a for a, b in zip(d, d[1:])), d
+
+
+def test_fixed_point_count_of_table_3():
+    """Section 6.4's setup on the 4 x 4 mesh at p = 6: the fixed point stops after 4
+    iterations (Table 3), each T solve taking one or two Newton steps (Table 3's average
+    1.5 at p = 6)."""
+    w = W.workload("thermoforming_p6")
+    q = QVIOracle(w["breakpoints"], w["p"], w["f"], w["Phi0"], w["xi"], gamma=w["gamma"], g0=w["g0"],
+                  beta=w["beta"])
+    r = q.solve(w["alphas"], tol=w["qvi_tol"])
+    assert r["iterations"] == 4
+    assert all(1 <= h["t_newton"] <= 3 for h in r["history"])
+    assert r["history"][-1]["du_h1"] <= 3e-3 < r["history"][-2]["du_h1"]
