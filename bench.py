@@ -294,6 +294,28 @@ def kernel_only(args, ctx, w, stream, hpg, torch):
         kw = {"fdm_tile_f32": args.fdm_tile} if prec == hpg.HPG_MIXED else {"fdm_tile_f64": args.fdm_tile}
     if args.krylov_f32:
         kw["krylov_f32"] = 1
+    if args.kernel_batch > 1:
+        # a lockstep group: one proximal step solved in lockstep sets every member's
+        # state, then the kernel class is replayed over the whole group
+        wb = dict(w)
+        wb["alphas"] = w["alphas"][:1]
+        ps = [hpg.from_workload(ctx, wb, hpg.default_params(precision=prec, **kw)) for _ in range(args.kernel_batch)]
+        ctx.set_concurrency(16)
+        ctx.solve_batch(ps)
+        ctx.launch_kernel_batch(ps, args.kernel, prec, args.steps)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.launch_kernel_batch(ps, args.kernel, prec, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel": args.kernel, "precision": args.precision, "batch": args.kernel_batch,
+                          "launches": args.steps, "avg_us": 1000.0 * e0.elapsed_time(e1) / args.steps}), flush=True)
+        for P in ps:
+            P.free()
+        ctx.close()
+        return 0
     P = hpg.from_workload(ctx, w, hpg.default_params(precision=prec, **kw))
     rng = np.random.default_rng(7)
     u = np.zeros(P.n_u_full)
@@ -334,6 +356,8 @@ def main():
                     help="workload of the kernel-only mode (radial32, torsion, sine3d, ...)")
     ap.add_argument("--fdm-tile", type=int, default=-1,
                     help="force this fast-diagonalisation pass variant of the timed precision (-1: autotuned)")
+    ap.add_argument("--kernel-batch", type=int, default=1,
+                    help="kernel-only mode: replay the kernel class over a lockstep group of this many solves")
     ap.add_argument("--krylov-f32", action="store_true",
                     help="kernel-only mode: the opt-in float GMRES basis of the FP32 inner solves")
     ap.add_argument("--batch", type=int, default=16, help="independent solves in flight per step")
@@ -344,6 +368,7 @@ def main():
     ap.add_argument("--no-others", action="store_true", help="skip the 4x4, 3D and torsion workloads")
     ap.add_argument("--no-strategies", action="store_true",
                     help="skip the Section 6.5 solver-strategy comparison (Schur vs FGMRES + P_D / P_L P_D / P_F-(10))")
+    ap.add_argument("--no-qvi", action="store_true", help="skip the Section 6.4 thermoforming QVI table")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven GMRES launches (profilers cannot trace conditional graph nodes)")
     args = ap.parse_args()
@@ -690,6 +715,43 @@ def main():
                                                                "n_u": P.n_u}
                 P.free()
 
+    # Section 6.4: the thermoforming QVI on the 4 x 4 mesh (Table 3's columns), FP64 + mixed
+    # obstacle solves on the device; the oracle's fixed point timed beside it at p = 6
+    qvi = None
+    if not args.no_qvi:
+        qvi = {}
+        for p_deg in (6, 12, 22, 32):
+            wq = W.workload(f"thermoforming_p{p_deg}")
+            P = hpg.Problem(ctx, 2, [0.0, 0.0], [1.0, 1.0], [4, 4], p_deg, hpg.HPG_OBSTACLE_UPPER)
+            P.set_rhs(wq["f_const"])
+            P.set_alphas(wq["alphas"])
+            P.set_params(hpg.default_params(beta=wq["beta"], precision=hpg.HPG_MIXED))
+            Xl, Xq = P.quad_points(), P.qvi_points()
+            data = (wq["Phi0"](Xl), wq["xi"](Xl), wq["Phi0"](Xq), wq["xi"](Xq))
+            P.qvi_solve(*data, gamma=wq["gamma"], g0=wq["g0"], tol=wq["qvi_tol"])     # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st = P.qvi_solve(*data, gamma=wq["gamma"], g0=wq["g0"], tol=wq["qvi_tol"], check=False)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            nfp = max(1, st["iterations"])
+            qvi[f"p={p_deg}"] = {"status": rc, "fixed_point": st["iterations"], "seconds": sec,
+                                 "avg_newton_I": st["newton_total"] / nfp,
+                                 "avg_gmres_I": st["krylov_total"] / max(1, st["newton_total"]),
+                                 "avg_newton_II": st["t_newton_total"] / nfp,
+                                 "avg_gmres_II": st["t_krylov_total"] / max(1, st["t_newton_total"]),
+                                 "kernel_launches": st["kernel_launches"], "n_u_full": P.n_u_full}
+            P.free()
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            from oracle.qvi import QVIOracle
+            wq = W.workload("thermoforming_p6")
+            t0 = time.perf_counter()
+            qo = QVIOracle(wq["breakpoints"], wq["p"], wq["f"], wq["Phi0"], wq["xi"], gamma=wq["gamma"],
+                           g0=wq["g0"], beta=wq["beta"])
+            ro = qo.solve(wq["alphas"], tol=wq["qvi_tol"])
+            qvi["oracle_p=6"] = {"seconds": time.perf_counter() - t0, "fixed_point": ro["iterations"],
+                                 "cores": cpu_threads()}
+
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = {"requests": args.serve_requests, "workers": B, "admission": "largest work first (policy 1)",
@@ -755,6 +817,7 @@ def main():
                 # variants are the tcgen05 kernels); pass it to --fdm-tile to reproduce a run under ncu
                 "fdm_variant": {"mixed": head["fdm_variant"], "fp64": fp["fdm_variant"] if fp else None},
                 "other_workloads": others, "solver_strategies": strategies, "ainv_pcg_table": ainv_table,
+                "thermoforming_qvi": qvi,
                 "serving": serving, "clocks": clocks,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -453,6 +453,7 @@ typedef struct {
     double t_residual;                  /* ||R(T)||_2 at the end                        */
     double solve_ms;                    /* wall time (host clock)                       */
     long long kernel_launches;          /* libhpg kernels launched by the QVI solve     */
+    long long krylov_total;             /* GMRES iterations of the obstacle Newton systems */
 } hpg_qvi_stats;
 
 /* Defaults of hpg_qvi_params. */

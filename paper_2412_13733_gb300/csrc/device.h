@@ -50,6 +50,8 @@ struct Geo {
     const T* Kpsi;                            // nloc x nloc (gradient E_beta)
     const T* C;                               // nloc x nloc (obstacle S-hat constant part)
     const T* V[kMaxDim];                      // n1 x n1 fast-diagonalisation eigenvectors
+    const T* VT[kMaxDim];                     // their transposes VT[a][k] = V[k][a] (or null): the
+                                              // forward passes along the outer axes read V^T K-contiguous
     const T* lam[kMaxDim];                    // n1 eigenvalues
     int gemm_cfg;                             // tile variant of the FDM passes (autotuned)
     TileCols tu[kMaxDim];                     // u columns of the A, M stencils per row tile

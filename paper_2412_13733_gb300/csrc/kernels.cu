@@ -2195,12 +2195,16 @@ cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, c
             return gemm<T>(a, in, V, out, sc, g, s, skip, bt);
         }
         a.M = n1; a.N = (int)inner[ax]; a.K = n1; a.batch = (int)outer[ax];
-        if (fwd) { a.sAm = 1; a.sAk = n1; } else { a.sAm = n1; a.sAk = 1; }
+        // W = V^T (forward) read K-contiguous from the stored transpose when there is one
+        const T* Wm = V;
+        if (fwd && g.VT[ax]) { Wm = g.VT[ax]; a.sAm = n1; a.sAk = 1; }
+        else if (fwd) { a.sAm = 1; a.sAk = n1; }
+        else { a.sAm = n1; a.sAk = 1; }
         a.sAb = 0;
         a.sBk = inner[ax]; a.sBn = 1; a.sBb = (long long)n1 * inner[ax];
         a.sCm = inner[ax]; a.sCn = 1; a.sCb = (long long)n1 * inner[ax];
         a.dA = 0; a.dB = 1;
-        return gemm<T>(a, V, in, out, sc, g, s, skip, bt);
+        return gemm<T>(a, Wm, in, out, sc, g, s, skip, bt);
     };
     cudaError_t e;
     const T* cur = x;

@@ -594,6 +594,7 @@ hpg_status qvi_solve(hpg_ctx* ctx, Problem& P, const hpg_qvi_params& q, const do
         pencil_eigen(N1, Ad, Md, Vj[j], lamj[j]);
         r.gfdm.n1[j] = N1;
         r.gfdm.V[j] = ar.up(Vj[j].data(), Vj[j].size());
+        r.gfdm.VT[j] = nullptr;
         r.gfdm.lam[j] = ar.up(lamj[j].data(), lamj[j].size());
     }
     // data and state
@@ -629,6 +630,7 @@ hpg_status qvi_solve(hpg_ctx* ctx, Problem& P, const hpg_qvi_params& q, const do
         QCK(launch_project(D.gd, D.phiq, D.phiz, s));
         hpg_status os = solve_problem(ctx, P);
         st.newton_total += P.stats.newton_total;
+        st.krylov_total += P.stats.krylov_total;
         st.newton_per_fp[it] = P.stats.newton_total;
         if (os != HPG_OK) {
             ctx->err = "QVI iteration " + std::to_string(it + 1) + ", obstacle step: " + ctx->err;

@@ -71,7 +71,7 @@ size_t estimate_device_bytes(const Problem& P) {
     size_t b = 0;
     for (int j = 0; j < H.d; ++j) {
         const size_t n1 = H.dir[j].n1;
-        b += n1 * n1 * 12 + n1 * 12;                      // V, lam (FP64 + FP32)
+        b += n1 * n1 * 24 + n1 * 12;                      // V, V^T, lam (FP64 + FP32)
         b += (size_t)kEll * 20 * (4 * n1 + 2 * H.m[j] * H.n);   // stencils
     }
     b += Nu0 * (8 * 8 + 4 * 4);                          // rA, bf, tu/w buffers

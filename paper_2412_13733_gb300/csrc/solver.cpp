@@ -253,6 +253,13 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
             ok = ok && upload_tile_cols(D, Dj.n1, T, {&Dj.Bi}, true, H.n, D.tp[j], {&D.B[j].lcol}, s);
         D.V_d[j] = upload_vec<double>(D, Dj.V, ok, s);
         D.V_f[j] = upload_vec<float>(D, Dj.V, ok, s);
+        {
+            std::vector<double> Vt((size_t)Dj.n1 * Dj.n1);
+            for (int k = 0; k < Dj.n1; ++k)
+                for (int a = 0; a < Dj.n1; ++a) Vt[(size_t)a * Dj.n1 + k] = Dj.V[(size_t)k * Dj.n1 + a];
+            D.VT_d[j] = upload_vec<double>(D, Vt, ok, s);
+            D.VT_f[j] = upload_vec<float>(D, Vt, ok, s);
+        }
         D.lam_d[j] = upload_vec<double>(D, Dj.lam, ok, s);
         D.lam_f[j] = upload_vec<float>(D, Dj.lam, ok, s);
     }
@@ -408,6 +415,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
             g.tu[j] = {D.tu[j].list, D.tu[j].count, D.tu[j].cap};
             g.tp[j] = {D.tp[j].list, D.tp[j].count, D.tp[j].cap};
             g.V[j] = D.V_d[j];
+            g.VT[j] = D.VT_d[j];
             g.lam[j] = D.lam_d[j];
         }
         g.Vq = D.Vq_d; g.wq = D.wq_d; g.detJ = H.detJ; g.Mpsi = D.Mpsi_d; g.Kpsi = D.Kpsi_d; g.C = D.C_d;
@@ -424,6 +432,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
             g.tu[j] = {D.tu[j].list, D.tu[j].count, D.tu[j].cap};
             g.tp[j] = {D.tp[j].list, D.tp[j].count, D.tp[j].cap};
             g.V[j] = D.V_f[j];
+            g.VT[j] = D.VT_f[j];
             g.lam[j] = D.lam_f[j];
         }
         g.Vq = D.Vq_f; g.wq = D.wq_f; g.detJ = (float)H.detJ; g.Mpsi = D.Mpsi_f; g.Kpsi = D.Kpsi_f; g.C = D.C_f;
@@ -2310,6 +2319,7 @@ static hpg_status pcg_setup(hpg_ctx* ctx, Problem& P, int kind) {
             D.plamc[j] = upload_vec<double>(D, ap.lamc[j], ok, s);
             D.gc.n1[j] = ap.nv[j];
             D.gc.V[j] = D.pVc[j];
+            D.gc.VT[j] = nullptr;        // the coarse pencils keep the strided forward passes
             D.gc.lam[j] = D.plamc[j];
         }
         D.gc.Nu0 = nc0;

@@ -40,6 +40,8 @@ struct DevState {
     float *Vq_f = nullptr, *wq_f = nullptr, *Mpsi_f = nullptr, *Kpsi_f = nullptr, *C_f = nullptr;
     double *V_d[kMaxDim] = {}, *lam_d[kMaxDim] = {};
     float *V_f[kMaxDim] = {}, *lam_f[kMaxDim] = {};
+    double* VT_d[kMaxDim] = {};
+    float* VT_f[kMaxDim] = {};
     Geo<double> gd{};
     Geo<float> gf{};
     // data

@@ -55,7 +55,7 @@ class hpg_qvi_stats(C.Structure):
                 ("t_newton_total", C.c_int), ("t_krylov_total", C.c_longlong),
                 ("du_h1", C.c_double * HPG_QVI_MAX_FP), ("newton_per_fp", C.c_int * HPG_QVI_MAX_FP),
                 ("t_newton_per_fp", C.c_int * HPG_QVI_MAX_FP), ("t_residual", C.c_double),
-                ("solve_ms", C.c_double), ("kernel_launches", C.c_longlong)]
+                ("solve_ms", C.c_double), ("kernel_launches", C.c_longlong), ("krylov_total", C.c_longlong)]
 
 
 FIELD_FN = C.CFUNCTYPE(None, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
