@@ -429,7 +429,7 @@ typedef struct {
     double gamma;         /* > 0; default 1                                            */
     double g0;            /* >= 0; default 0.2                                         */
     double tol;           /* H^1 stopping tolerance of the fixed point; default 3e-3   */
-    double t_tol;         /* absolute ||R(T)||_2 of the T Newton; default 1e-10        */
+    double t_tol;         /* absolute ||R(T)||_2 of the T Newton; default 1e-11        */
     int    max_fp;        /* fixed-point cap (<= HPG_QVI_MAX_FP); default 30           */
     int    nq;            /* Gauss points per direction per cell of the T equation;
                              p + 2 by default (0)                                       */

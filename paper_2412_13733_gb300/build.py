@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libhpg.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "setup.cpp", "solver.cpp", "api.cpp", "server.cpp", "noalloc.cu", "qvi.cu"]
+SOURCES = ["kernels.cu", "setup.cpp", "solver.cpp", "api.cpp", "server.cpp", "noalloc.cu", "qvi.cu", "fdm_tma.cu"]
 
 
 def nvcc():

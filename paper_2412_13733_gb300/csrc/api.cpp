@@ -763,7 +763,7 @@ hpg_status hpg_qvi_default_params(hpg_qvi_params* out) {
     out->gamma = 1.0;
     out->g0 = 0.2;
     out->tol = 3e-3;
-    out->t_tol = 1e-10;
+    out->t_tol = 1e-11;
     out->max_fp = 30;
     out->nq = 0;
     out->t_newton_max = 50;

@@ -3,6 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
+#include <string>
+
 #include "hpg_internal.h"
 
 namespace hpg {
@@ -34,6 +37,8 @@ struct Geo;
 template <typename T>
 bool urow_boxes_fit(const Geo<T>& g);
 
+struct FdmTma;
+
 // Everything a kernel needs to know about one problem, for compute type T.
 template <typename T>
 struct Geo {
@@ -59,6 +64,7 @@ struct Geo {
     int staged;                               // 1: the u-row kernels stage value boxes in shared memory
     const int* perm0;                         // n1[0] rows of axis 0 in the order the unstaged u-row
                                               // tiles take them (sorted by stencil counts), or null
+    const FdmTma* tma;                        // host view of the TMA/tcgen05 fast diagonalisation (FP32), or null
 };
 
 // Lockstep group of same-shape problems (identical mesh, degree, kind and operator
@@ -166,6 +172,35 @@ cudaError_t launch_btapply(const Geo<T>& g, const Tin* x, Tout* y, cudaStream_t 
 template <typename T>
 cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, const T* x, T* y, T* work1,
                        T* work2, cudaStream_t s, const int* skip = nullptr, const Bat& bt = Bat{}, double shift = 0.0);
+
+// The fast diagonalisation on TMA-fed tcgen05 passes (FP32 in, 3xTF32 products, FP32
+// accumulation): the tensors between passes live in a workspace in sliced form
+// [k/4][rows][k%4], rows padded to the 128-row tile and slices to the 4-slice stage, as
+// TF32-exact high parts and FP32 remainders; np problems (a lockstep group) share the
+// pass matrices.  Host view: device pointers and sizes.
+struct FdmTma {
+    bool ready = false;
+    int d = 0, np = 0;
+    int n1[kMaxDim] = {1, 1, 1};
+    long long R[kMaxDim] = {}, Rp[kMaxDim] = {};   // rows of the pass along axis j, padded
+    int C[kMaxDim] = {}, Cp[kMaxDim] = {};         // 4-float slices of axis j, padded
+    long long wsz = 0;                             // floats per workspace buffer
+    float* ws = nullptr;                           // np x [buffer 0 hi, lo, buffer 1 hi, lo]
+    const void* mA = nullptr;                      // device CUtensorMap [np][d][2 buffers][hi, lo]
+    const void* mB = nullptr;                      // device CUtensorMap [variant][d][fwd, bwd][hi, lo]
+    const float* lam[kMaxDim] = {};
+};
+// Number of TMA variants (N tiles of 64, 128, 256 columns).
+int fdm_tma_variants();
+// y = A_alpha^{-1} x (or (A + shift M)^{-1} x) for every problem of bt; x, y natural FP32.
+cudaError_t launch_fdm_tma(const FdmTma& t, int variant, const double* alpha_dev, double alpha, const float* x,
+                           float* y, cudaStream_t s, const int* skip, const Bat& bt, double shift);
+// Build t for np problems of H's shape: workspace and maps through `alloc` (device bytes),
+// the pass matrices from `consts` when given (a group reuses problem 0's), else uploaded.
+// False (with the reason) when a tensor map cannot be made.
+bool fdm_tma_setup(FdmTma& t, const HostProblem& H, const float* const* lam, int np,
+                   const std::function<void*(size_t)>& alloc, cudaStream_t s, const FdmTma* consts,
+                   std::string* why);
 
 // w = -(D z + E z + B^T t)  (per cell), D from gw.  z, t in T; w in Tout.
 template <typename T, typename Tout>

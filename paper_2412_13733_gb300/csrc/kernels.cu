@@ -2098,8 +2098,10 @@ struct TileSet<double> { using type = F64Tiles; };
 
 // FP32 variants: the SIMT tiles, then the tcgen05 3xTF32 kernel with BN = 16 and 32
 constexpr int kTcVariants = 2;
+// ... then the TMA-fed tcgen05 passes (fdm_tma.cu) with N tiles of 64, 128 and 256
 int fdm_tile_count(int elem) {
-    return elem == 4 ? (int)std::tuple_size<F32Tiles>::value + kTcVariants : (int)std::tuple_size<F64Tiles>::value;
+    return elem == 4 ? (int)std::tuple_size<F32Tiles>::value + kTcVariants + fdm_tma_variants()
+                     : (int)std::tuple_size<F64Tiles>::value;
 }
 
 template <typename Set, size_t I = 0>
@@ -2112,9 +2114,15 @@ static int tile_ks_of(int idx) {
     }
 }
 
-// K split of a variant (its summation order); 0 for the tensor-core variants
+// K split of a variant (its summation order); 0 for the tensor-core variants that split
+// in shared memory, -1 - v for TMA variant v (each its own order: groups keep it)
 int fdm_tile_ks(int elem, int idx) {
-    return elem == 4 ? tile_ks_of<F32Tiles>(idx) : tile_ks_of<F64Tiles>(idx);
+    if (elem == 4) {
+        const int tv = idx - (int)std::tuple_size<F32Tiles>::value - kTcVariants;
+        if (tv >= 0) return -1 - tv;
+        return tile_ks_of<F32Tiles>(idx);
+    }
+    return tile_ks_of<F64Tiles>(idx);
 }
 
 template <typename T, size_t I = 0>
@@ -2164,6 +2172,13 @@ static cudaError_t gemm(const GemmArgs& a, const T* A, const T* B, T* C, const F
 template <typename T>
 cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, const T* x, T* y, T* work1, T* work2,
                        cudaStream_t s, const int* skip, const Bat& bt, double shift) {
+    if constexpr (sizeof(T) == 4) {
+        const int tv = g.gemm_cfg - (int)std::tuple_size<F32Tiles>::value - kTcVariants;
+        if (tv >= 0) {
+            if (!g.tma || !g.tma->ready) return cudaErrorInvalidValue;
+            return launch_fdm_tma(*g.tma, tv, alpha_dev, alpha, x, y, s, skip, bt, shift);
+        }
+    }
     const int d = g.d;
     long long inner[kMaxDim], outer[kMaxDim];
     for (int ax = 0; ax < d; ++ax) {

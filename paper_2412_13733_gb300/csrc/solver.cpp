@@ -442,6 +442,18 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
     // gradient kind.  Measured: B apply on the 3D 8^3 p=6 obstacle 23 -> 12.8 us,
     // torsion 16^2 p=10 solve -6 %; on the 2D obstacle (one component) the direct
     // gathers stay faster (radial 32x32 p=8 B apply 4.8 vs 6.3 us).
+    // the TMA-fed tcgen05 fast diagonalisation (FP32): workspace, sliced pass matrices and
+    // tensor maps; when a map cannot be made its variants are simply not candidates
+    {
+        bool okt = true;
+        auto al = [&](size_t bytes) -> void* { return dalloc<char>(D, bytes, okt); };
+        const float* lamf[kMaxDim] = {D.lam_f[0], D.lam_f[1], D.lam_f[2]};
+        std::string why;
+        D.tma_ok = fdm_tma_setup(D.tma, H, lamf, 1, al, s, nullptr, &why) && okt;
+        D.gf.tma = D.tma_ok ? &D.tma : nullptr;
+        D.gd.tma = nullptr;
+        cudaGetLastError();
+    }
     const bool stage = d == 3 || grad;
     D.gd.staged = stage && urow_boxes_fit(D.gd) ? 1 : 0;
     D.gf.staged = stage && urow_boxes_fit(D.gf) ? 1 : 0;
@@ -1132,7 +1144,12 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
             // factorisation flag (non-SPD block): bit 1 of flag[1], sticky for the solve
             CK(cudaMemcpyAsync(D.h_iflag, D.flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            if (D.h_iflag[0] & 2) { status = HPG_ERR_NOT_SPD; break; }
+            if (D.h_iflag[0] & 2) {
+                status = HPG_ERR_NOT_SPD;
+                ctx->err = std::string("non-positive pivot in a ") + (P.params.precision == HPG_FP64 ? "FP64" : "FP32") +
+                           " S-hat block factorisation in proximal step " + std::to_string(k + 1);
+                break;
+            }
             swap_state(D);
             normF = nFt;
             flag = tflag;
@@ -1196,6 +1213,9 @@ struct Group {
     Geo<float> gf{};
     Geo<double> gd{};
     bool tuned_f = false, tuned_d = false;
+    // the TMA fast diagonalisation over all np problems (its own workspace and maps)
+    FdmTma tma{};
+    std::vector<void*> tma_allocs;
     std::map<long long, std::pair<cudaGraphExec_t, long long>> bench_graphs;   // kernel-class replays
     ~Group() {
         for (auto& kv : bench_graphs) cudaGraphExecDestroy(kv.second.first);
@@ -1207,6 +1227,7 @@ struct Group {
         if (stat_d) cudaFree(stat_d);
         if (h_delta) cudaFreeHost(h_delta);
         if (h_stat) cudaFreeHost(h_stat);
+        for (void* p : tma_allocs) cudaFree(p);
     }
     Bat bat(int slot) const {
         Bat b;
@@ -1337,6 +1358,27 @@ static hpg_status group_tune_fdm(hpg_ctx* ctx, Group& Gp) {
     GG<T>::tuned(Gp) = true;
     const int forced = sizeof(T) == 4 ? Gp.ps[0]->params.fdm_tile_f32 : Gp.ps[0]->params.fdm_tile_f64;
     const int ks = fdm_tile_ks((int)sizeof(T), gg.gemm_cfg);
+    if (ks < 0) {
+        // a TMA variant: the group gets its own workspace and tensor maps over its np
+        // problems; the pass matrices are problem 0's.  The variant stays the problems'
+        // own (each TMA variant has its own summation order).
+        if (!Gp.tma.ready) {
+            std::string why;
+            auto al = [&](size_t bytes) -> void* {
+                void* p = nullptr;
+                if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+                Gp.tma_allocs.push_back(p);
+                return p;
+            };
+            const float* lamf[kMaxDim] = {D.lam_f[0], D.lam_f[1], D.lam_f[2]};
+            if (!D.tma_ok || !fdm_tma_setup(Gp.tma, Gp.ps[0]->H, lamf, Gp.np, al, ctx->stream, &D.tma, &why)) {
+                ctx->err = "lockstep group: TMA fast diagonalisation set-up failed (" + why + ")";
+                return HPG_ERR_CUDA;
+            }
+        }
+        gg.tma = &Gp.tma;
+        return HPG_OK;
+    }
     if (forced >= 0 || ks == 0 || Gp.np == 1) return HPG_OK;
     static std::mutex mu;
     static std::map<std::tuple<int, int, int, int, int, int>, int> cache;

@@ -42,6 +42,8 @@ struct DevState {
     float *V_f[kMaxDim] = {}, *lam_f[kMaxDim] = {};
     double* VT_d[kMaxDim] = {};
     float* VT_f[kMaxDim] = {};
+    FdmTma tma{};                 // TMA/tcgen05 fast diagonalisation of this problem (FP32)
+    bool tma_ok = false;
     Geo<double> gd{};
     Geo<float> gf{};
     // data
