@@ -296,6 +296,8 @@ def kernel_only(args, ctx, w, stream, hpg, torch):
         kw["krylov_f32"] = 1
     if args.no_graphs:
         kw["graphs"] = 0
+    if args.kernel_batch > 1:
+        kw["fdm_tune_batch"] = min(args.kernel_batch, 64)
     if args.kernel == "solve":
         # whole solves (every alpha step) of a lockstep group of --kernel-batch problems:
         # one untimed warm-up solve, then --steps timed ones (launch lists of the batched step)
@@ -460,7 +462,10 @@ def main():
         kw = {}
         if args.fdm_tile >= 0:
             kw = {"fdm_tile_f32": args.fdm_tile} if prec == hpg.HPG_MIXED else {"fdm_tile_f64": args.fdm_tile}
-        ps = [hpg.from_workload(ctx, w, hpg.default_params(precision=prec, graphs=0 if args.no_graphs else 1, **kw))
+        # batched legs tune the fast-diagonalisation variant for the time per problem at
+        # their group size (hpg_params.fdm_tune_batch); one solve alone tunes for itself
+        ps = [hpg.from_workload(ctx, w, hpg.default_params(precision=prec, graphs=0 if args.no_graphs else 1,
+                                                           fdm_tune_batch=min(count, 64), **kw))
               for _ in range(count)]
         return ps
 

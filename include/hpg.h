@@ -140,6 +140,12 @@ typedef struct {
                              tolerance ainv_rtol.  Ignored by HPG_SCHUR and HPG_FGMRES_PF, whose
                              A_alpha^{-1} runs inside the device-side GMRES loop               */
     double ainv_rtol;     /* relative tolerance of that CG; default 1e-10                       */
+    int    fdm_tune_batch;/* 1 (default): the set-up autotuner picks the fast-diagonalisation
+                             variant that is fastest for this problem alone; B in 2..64: the
+                             variant with the least time per problem when B same-shape problems
+                             run in one lockstep launch (hpg_solve_batch).  A group runs its
+                             members' variant, so solving alone and in a batch give the same
+                             bits either way; changing it releases the device state            */
 } hpg_params;
 
 #define HPG_MAX_ALPHA 128

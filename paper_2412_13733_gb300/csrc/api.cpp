@@ -75,6 +75,7 @@ void hpg_default_params(hpg_params* p) {
     p->krylov_f32 = 0;
     p->ainv_pcg = 0;
     p->ainv_rtol = 1e-10;
+    p->fdm_tune_batch = 1;
 }
 
 const char* hpg_status_str(hpg_status s) {
@@ -321,11 +322,13 @@ hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params) {
         params->strategy < HPG_SCHUR || params->strategy > HPG_FGMRES_PF ||
         (params->strategy != HPG_SCHUR && params->precision != HPG_FP64) || params->inner_max < 1 ||
         (params->krylov_f32 != 0 && params->krylov_f32 != 1) ||
-        params->ainv_pcg < 0 || params->ainv_pcg > 3 || !(params->ainv_rtol > 0.0))
+        params->ainv_pcg < 0 || params->ainv_pcg > 3 || !(params->ainv_rtol > 0.0) ||
+        params->fdm_tune_batch < 1 || params->fdm_tune_batch > 64)
         return HPG_ERR_ARG;
     const bool realloc = P->alloc_done && (params->krylov_max != P->params.krylov_max ||
                                            params->fdm_tile_f32 != P->params.fdm_tile_f32 ||
-                                           params->fdm_tile_f64 != P->params.fdm_tile_f64);
+                                           params->fdm_tile_f64 != P->params.fdm_tile_f64 ||
+                                           params->fdm_tune_batch != P->params.fdm_tune_batch);
     if (realloc) {
         hpg::free_device(*P, ctx->stream);
         P->data_dirty = P->phi_dirty = true;

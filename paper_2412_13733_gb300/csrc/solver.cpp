@@ -477,8 +477,9 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
 template <typename T>
 static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, T* w1, T* w2) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int>, int> cache;
-    const auto key = std::make_tuple(g.d, g.n1[0], g.n1[1], g.d > 2 ? g.n1[2] : 1, (int)sizeof(T));
+    static std::map<std::tuple<int, int, int, int, int, int>, int> cache;
+    const int B = std::max(1, P.params.fdm_tune_batch);
+    const auto key = std::make_tuple(g.d, g.n1[0], g.n1[1], g.d > 2 ? g.n1[2] : 1, (int)sizeof(T), B);
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
@@ -496,6 +497,38 @@ static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, 
     int best = -1;
     float best_ms = 1e30f;
     double ref_max = 0.0;
+    // Timing at batch B (fdm_tune_batch): one launch per pass serves B copies that all read
+    // x and write y (the same values at the same addresses), as a lockstep group of B
+    // would; the TMA variants get a temporary workspace and tensor maps for B problems.
+    Bat bb{};
+    long long* dz = nullptr;
+    FdmTma tb{};
+    std::vector<void*> tallocs;
+    if (B > 1) {
+        if (cudaMalloc(&dz, (size_t)B * sizeof(long long)) == cudaSuccess &&
+            cudaMemset(dz, 0, (size_t)B * sizeof(long long)) == cudaSuccess) {
+            bb.delta = dz;
+            bb.np = B;
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (P.D.tma_ok && bb.np == B) {
+                auto al = [&](size_t bytes) -> void* {
+                    void* q = nullptr;
+                    if (cudaMalloc(&q, bytes) != cudaSuccess) return nullptr;
+                    tallocs.push_back(q);
+                    return q;
+                };
+                const float* lamf[kMaxDim] = {P.D.lam_f[0], P.D.lam_f[1], P.D.lam_f[2]};
+                std::string why;
+                if (!fdm_tma_setup(tb, P.H, lamf, B, al, s, &P.D.tma, &why)) tb = FdmTma{};
+            }
+        }
+        cudaGetLastError();
+    }
+    auto release = [&]() {
+        if (dz) cudaFree(dz);
+        for (void* q : tallocs) cudaFree(q);
+    };
     const int ncfg = fdm_tile_count((int)sizeof(T));
     for (int c = 0; c < ncfg; ++c) {
         g.gemm_cfg = c;
@@ -516,8 +549,19 @@ static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, 
             for (size_t i = 0; i < n; ++i) dmax = std::max(dmax, std::fabs((double)out[i] - (double)ref[i]));
             if (ref.empty() || dmax > tol * std::max(ref_max, 1e-300)) continue;
         }
+        Geo<T> gt = g;
+        Bat bt{};
+        if (B > 1) {
+            if (bb.np != B) continue;
+            bt = bb;
+            if (gt.tma) gt.tma = tb.ready ? &tb : nullptr;
+        }
+        if (launch_fdm<T>(gt, nullptr, 1.0, x, y, w1, w2, s, nullptr, bt) != cudaSuccess) {   // warm-up
+            cudaGetLastError();
+            continue;
+        }
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 5; ++r) launch_fdm<T>(g, nullptr, 1.0, x, y, w1, w2, s);
+        for (int r = 0; r < 5; ++r) launch_fdm<T>(gt, nullptr, 1.0, x, y, w1, w2, s, nullptr, bt);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
         float ms = 0.f;
@@ -526,6 +570,8 @@ static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    CK(cudaStreamSynchronize(s));
+    release();
     if (best < 0) {
         ctx->err = "no fast-diagonalisation pass variant produced a valid result";
         return HPG_ERR_CUDA;
@@ -1248,8 +1294,8 @@ static std::string group_key(const Problem& P) {
     char buf[512];
     std::snprintf(buf, sizeof buf, "%d|%d|%d,%d,%d|%d|%a,%a,%a|%a,%a,%a|%d|%d|%d|%a|%d|%d|%d|%d|%d", H.d, H.kind,
                   H.m[0], H.m[1], H.m[2], H.p, H.lo[0], H.lo[1], H.lo[2], H.hi[0], H.hi[1], H.hi[2], q.precision,
-                  q.krylov_max, q.krylov_f32, q.beta, q.fdm_tile_f32, q.fdm_tile_f64, q.strategy, q.ls_max,
-                  q.refine_max * 2 + (q.graphs != 0));
+                  q.krylov_max, q.krylov_f32, q.beta, q.fdm_tile_f32, q.fdm_tile_f64 * 128 + q.fdm_tune_batch,
+                  q.strategy, q.ls_max, q.refine_max * 2 + (q.graphs != 0));
     return buf;
 }
 

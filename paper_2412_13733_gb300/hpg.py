@@ -28,7 +28,8 @@ class hpg_params(C.Structure):
                 ("krylov_max", C.c_int), ("krylov_rtol", C.c_double), ("precision", C.c_int),
                 ("ls_max", C.c_int), ("refine_max", C.c_int), ("timing", C.c_int), ("graphs", C.c_int),
                 ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int), ("strategy", C.c_int),
-                ("inner_max", C.c_int), ("krylov_f32", C.c_int), ("ainv_pcg", C.c_int), ("ainv_rtol", C.c_double)]
+                ("inner_max", C.c_int), ("krylov_f32", C.c_int), ("ainv_pcg", C.c_int), ("ainv_rtol", C.c_double),
+                ("fdm_tune_batch", C.c_int)]
 
 
 class hpg_stats(C.Structure):

@@ -123,3 +123,31 @@ def test_tma_lockstep_group_equals_alone(ctx):
                 assert np.array_equal(P.u(), u)
         for P in probs:
             P.free()
+
+
+def test_tune_batch_group_equals_alone(ctx):
+    """hpg_params.fdm_tune_batch tunes the variant for the time per problem in a lockstep
+    group; the group then runs that variant, so alone and batched results stay equal bit
+    for bit whichever variant wins."""
+    from paper_2412_13733_gb300 import hpg
+    base = case("radial_3x3_p5")
+    ws = []
+    for i in range(4):
+        w = dict(base)
+        w["phi"] = (lambda f0, c: (lambda X: f0(X) + c))(base["phi"], 0.02 * i)
+        ws.append(w)
+    prm = lambda: hpg.default_params(precision=hpg.HPG_MIXED, fdm_tune_batch=4)
+    alone = []
+    for w in ws:
+        P = hpg.from_workload(ctx, w, prm())
+        P.solve()
+        alone.append((P.u(), P.stats()["fdm_tile_f32"]))
+        P.free()
+    probs = [hpg.from_workload(ctx, w, prm()) for w in ws]
+    ctx.solve_batch(probs)
+    for P, (u, v) in zip(probs, alone):
+        st = P.stats()
+        assert st["status"] == 0 and st["fdm_tile_f32"] == v
+        assert np.array_equal(P.u(), u)
+    for P in probs:
+        P.free()
