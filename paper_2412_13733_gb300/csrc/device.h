@@ -174,9 +174,10 @@ cudaError_t launch_fdm(const Geo<T>& g, const double* alpha_dev, double alpha, c
                        T* work2, cudaStream_t s, const int* skip = nullptr, const Bat& bt = Bat{}, double shift = 0.0);
 
 // The fast diagonalisation on TMA-fed tcgen05 passes (FP32 in, 3xTF32 products, FP32
-// accumulation): the tensors between passes live in an FP32 workspace in sliced form
-// [k/4][rows][k%4], rows padded to the 128-row tile and slices to the 4-slice stage; np
-// problems (a lockstep group) share the pass matrices.  Host view: device pointers and sizes.
+// accumulation): the tensors between passes live in a workspace in sliced form
+// [k/4][rows][k%4], rows padded to the 128-row tile and slices to the 4-slice stage, as
+// TF32-exact high parts and FP32 remainders; np problems (a lockstep group) share the
+// pass matrices.  Host view: device pointers and sizes.
 struct FdmTma {
     bool ready = false;
     int d = 0, np = 0;
@@ -184,9 +185,9 @@ struct FdmTma {
     long long R[kMaxDim] = {}, Rp[kMaxDim] = {};   // rows of the pass along axis j, padded
     int C[kMaxDim] = {}, Cp[kMaxDim] = {};         // 4-float slices of axis j, padded
     long long wsz = 0;                             // floats per workspace buffer
-    float* ws = nullptr;                           // np x [buffer 0, buffer 1]
-    const void* mA = nullptr;                      // device CUtensorMap [np][d][2 buffers]
-    const void* mB = nullptr;                      // device CUtensorMap [variant][d][fwd, bwd]
+    float* ws = nullptr;                           // np x [buffer 0 hi, lo, buffer 1 hi, lo]
+    const void* mA = nullptr;                      // device CUtensorMap [np][d][2 buffers][hi, lo]
+    const void* mB = nullptr;                      // device CUtensorMap [variant][d][fwd, bwd][hi, lo]
     const float* lam[kMaxDim] = {};
 };
 // Number of TMA variants (N tiles of 64, 128, 256 columns).

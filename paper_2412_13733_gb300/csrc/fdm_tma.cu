@@ -7,23 +7,23 @@
 // the contracted axis (the fastest of the pass's input layout) and r over the others.
 // The output is written with a as its slowest index, so the next axis becomes the
 // fastest: after d passes the axes are back in their natural order (2D: [i1][i0] ->
-// [a0][i1] -> [a1][a0]).  Between passes the tensors live in an FP32 workspace in
-// "sliced" form, [k / 4][r][k % 4] (16-byte slices of four consecutive k, zero-padded,
-// rows padded to the 128-row tile).  That layout is a plain 3D tensor for TMA whose box
-// lands in shared memory as the no-swizzle K-major core-matrix layout of tcgen05.mma,
-// so every operand tile is one bulk tensor copy (runs of 1 KB).
+// [a0][i1] -> [a1][a0]).  Between passes the tensors live in a workspace in "sliced"
+// form, [k / 4][r][k % 4] (16-byte slices of four consecutive k, zero-padded, rows padded
+// to the 128-row tile), split into a TF32-exact high part (the FP32 value with its 13 low
+// mantissa bits cleared) and the FP32 remainder.  That layout is a plain 3D tensor for
+// TMA whose box lands in shared memory as the no-swizzle K-major core-matrix layout of
+// tcgen05.mma, so every operand tile is one bulk tensor copy (runs of 1 KB).
 //
-// Per CTA (128 threads): warp 0 issues the TMA loads of a ring of stages (A: 128 rows,
-// B: the pass's matrix, 16 k each); warps 2-3 split every staged value into its
-// TF32-exact high part (13 low mantissa bits cleared, in place) and the FP32 remainder;
-// warp 1 issues the MMAs (kind::tf32, M = 128, N = BN, K = 8; three products per step:
-// hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM) and commits each stage back to the
-// producer; then all four warps read the accumulator with tcgen05.ld and write the next
-// pass's sliced input (the last forward pass scales by 1 / (alpha (sum of eigenvalues +
-// shift)); the last backward pass writes the natural FP32 output).  Every mbarrier wait
-// is a bounded spin; on time-out the tile is written as NaN (which the solver's
-// finiteness checks report), in-flight copies and products are waited for once more
-// (bounded) and TMEM is released.
+// Per CTA (128 threads): warp 0 issues the TMA loads of a ring of stages (A high and
+// remainder: 128 rows, B high and remainder: the pass's matrix; 16 k each), warp 1 issues
+// the MMAs (kind::tf32, M = 128, N = BN, K = 8; three products per step: hi*hi + hi*lo +
+// lo*hi, FP32 accumulation in TMEM) and commits each stage back to the producer; then
+// all four warps read the accumulator with tcgen05.ld and write the next pass's sliced
+// parts (the last forward pass scales by 1 / (alpha (sum of eigenvalues + shift)); the
+// last backward pass writes the natural FP32 output).  Every
+// mbarrier wait is a bounded spin; on time-out the tile is written as NaN (which the
+// solver's finiteness checks report), in-flight copies and products are waited for once
+// more (bounded) and TMEM is released.
 #include <cuda.h>
 
 #include <algorithm>
@@ -46,16 +46,18 @@ constexpr int kTSl = kTBK / 4; // slices per stage
 constexpr int kTRbA = 64;      // rows per innermost TMA run of the A operand (1 KB runs)
 
 struct TmaPassArgs {
-    const CUtensorMap* mA;     // input map of problem 0; problem pb at + pb * mA_stride
+    const CUtensorMap* mA;     // input maps of problem 0 (high at +0, remainder at +1); problem pb at + pb * mA_stride
     int mA_stride;
-    const CUtensorMap* mB;     // the pass's matrix
+    const CUtensorMap* mBh;    // the pass's matrix, high and remainder parts
+    const CUtensorMap* mBl;
     int M, N, nch;             // rows, columns (n1 of the axis), stages of k
     int BN, tcols;             // N tile (= the B box's rows), TMEM columns
     int rb;                    // rows per innermost TMA run of the B tile
     int ns;                    // stages in the ring (<= kTNS)
     int lbo_a, lbo_b;          // bytes between k-adjacent core matrices in shared memory
-    int mode;                  // 0: sliced out, 1: the same scaled by the eigenvalues, 2: natural out
-    float* out;                // sliced output buffer of problem 0 (problem pb at + pb * ws_stride floats)
+    int mode;                  // 0: sliced out, 1: the same scaled by the eigenvalues, 2: natural FP32 out
+    float* ohi;                // sliced output parts of problem 0 (problem pb at + pb * ws_stride floats)
+    float* olo;
     long long ws_stride;
     int F;                     // fastest extent of the output layout
     long long Rn;              // rows of the output layout (padded to a multiple of the M tile)
@@ -132,7 +134,6 @@ __device__ __forceinline__ void split_hl(float x, float& hi, float& lo) {
 __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* skip, Bat bt) {
     extern __shared__ unsigned char tsm_raw[];
     __shared__ __align__(8) uint64_t full[kTNS];
-    __shared__ __align__(8) uint64_t conv[kTNS];
     __shared__ __align__(8) uint64_t empty[kTNS];
     __shared__ __align__(8) uint64_t done;
     __shared__ uint32_t tbase;
@@ -145,11 +146,10 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
     const double* adev = bsh(p.alpha_dev, off);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int BN = p.BN, NS = p.ns;
-    // stage: [A (TMA, then its TF32 high part)][A remainder][B (TMA, then high)][B remainder]
+    // stage: [A high][A remainder][B high][B remainder], each a TMA box
     const uint32_t a_bytes = kTBM * kTBK * 4, b_bytes = (uint32_t)BN * kTBK * 4;
     const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
     const uint32_t st0 = (saddr(tsm_raw) + 1023u) & ~1023u;
-    unsigned char* st0p = tsm_raw + (st0 - saddr(tsm_raw));
     const int m0 = (int)blockIdx.y * kTBM, n0 = (int)blockIdx.x * BN;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tbase)),
@@ -159,7 +159,6 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 64;" ::"r"(saddr(&conv[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&done)));
@@ -172,11 +171,14 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tbase;
-    const CUtensorMap* mA = p.mA + (size_t)pb * p.mA_stride;
+    const CUtensorMap* mAh = p.mA + (size_t)pb * p.mA_stride;
+    const CUtensorMap* mAl = mAh + 1;
     if (warp == 0 && lane == 0) {
-        // producer: one bulk tensor copy per operand and stage
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mA)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(p.mB)) : "memory");
+        // producer: one bulk tensor copy per operand part and stage
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mAh)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mAl)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(p.mBh)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(p.mBl)) : "memory");
         int c = 0;
         for (; c < p.nch; ++c) {
             const int s = c % NS;
@@ -186,9 +188,11 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
             }
             const uint32_t sb = st0 + (uint32_t)s * stage_bytes;
             const uint32_t fb = saddr(&full[s]);
-            bar_expect_tx(fb, a_bytes + b_bytes);
-            tma_load3(sb, mA, 0, m0 / kTRbA, c * kTSl, fb);
-            tma_load3(sb + 2 * a_bytes, p.mB, 0, n0 / p.rb, c * kTSl, fb);
+            bar_expect_tx(fb, stage_bytes);
+            tma_load3(sb, mAh, 0, m0 / kTRbA, c * kTSl, fb);
+            tma_load3(sb + a_bytes, mAl, 0, m0 / kTRbA, c * kTSl, fb);
+            tma_load3(sb + 2 * a_bytes, p.mBh, 0, n0 / p.rb, c * kTSl, fb);
+            tma_load3(sb + 2 * a_bytes + b_bytes, p.mBl, 0, n0 / p.rb, c * kTSl, fb);
         }
         atomicExch(&s_issued, c);
     } else if (warp == 1 && lane == 0) {
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
         int c = 0;
         for (; c < p.nch; ++c) {
             const int s = c % NS;
-            if (!bar_wait(saddr(&conv[s]), (uint32_t)((c / NS) & 1))) {
+            if (!bar_wait(saddr(&full[s]), (uint32_t)((c / NS) & 1))) {
                 atomicExch(&s_fail, 1);
                 break;
             }
@@ -218,42 +222,6 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
         }
         atomicExch(&s_consumed, c);
         mma_commit(saddr(&done));   // completes when every product issued above has landed
-    } else if (warp >= 2) {
-        // converters (64 threads): each staged operand -> TF32 high part in place + remainder
-        const int ct = tid - 64;
-        const int na4 = (int)(a_bytes / 16), nb4 = (int)(b_bytes / 16);
-        for (int c = 0; c < p.nch; ++c) {
-            const int s = c % NS;
-            if (!bar_wait(saddr(&full[s]), (uint32_t)((c / NS) & 1))) {
-                atomicExch(&s_fail, 1);
-                break;
-            }
-            float4* A = reinterpret_cast<float4*>(st0p + (size_t)s * stage_bytes);
-            float4* Al = A + na4;
-            float4* B = Al + na4;
-            float4* Bl = B + nb4;
-            for (int i = ct; i < na4; i += 64) {
-                float4 v = A[i], h, l;
-                split_hl(v.x, h.x, l.x);
-                split_hl(v.y, h.y, l.y);
-                split_hl(v.z, h.z, l.z);
-                split_hl(v.w, h.w, l.w);
-                A[i] = h;
-                Al[i] = l;
-            }
-            for (int i = ct; i < nb4; i += 64) {
-                float4 v = B[i], h, l;
-                split_hl(v.x, h.x, l.x);
-                split_hl(v.y, h.y, l.y);
-                split_hl(v.z, h.z, l.z);
-                split_hl(v.w, h.w, l.w);
-                B[i] = h;
-                Bl[i] = l;
-            }
-            // make the generic-proxy writes visible to the tensor cores, then arrive
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&conv[s])) : "memory");
-        }
     }
     __syncwarp();
     bool ok = bar_wait(saddr(&done), 0);
@@ -264,8 +232,6 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
     const int r = m0 + warp * 32 + lane;
     const bool rok = r < p.M;
     float ainv = 1.0f, part = 0.0f;
-    int rf = 0;
-    long long rq = 0;
     if (p.mode == 1) {
         ainv = (float)(1.0 / (adev ? *adev : p.alpha_host));
         // the rows of the last forward pass are (a_{d-2}, ..., a_0), a_0 fastest
@@ -276,13 +242,15 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
         }
         part += (float)p.shift;
     }
-    if (p.mode != 2) {
-        rf = rok ? r % p.F : 0;
-        rq = rok ? r / p.F : 0;
-    }
-    float* o = p.out + (size_t)pb * p.ws_stride;
+    float* ohi = p.ohi + (size_t)pb * p.ws_stride;
+    float* olo = p.olo + (size_t)pb * p.ws_stride;
     float* y = bsh(p.y, off);
+    // the next pass's sliced parts (or, on the last pass, the natural output): consecutive
+    // lanes write consecutive rows of one column; after a timed-out wait every row of the
+    // tile is written as NaN (no TMEM read)
     const long long MF = p.mode != 2 ? (long long)p.M / p.F : 0;
+    const int rf = (p.mode != 2 && rok) ? r % p.F : 0;
+    const long long rq = (p.mode != 2 && rok) ? r / p.F : 0;
     for (int j0 = 0; j0 < BN; j0 += 16) {
         uint32_t v[16];
         if (good) {
@@ -303,8 +271,11 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
                 continue;
             }
             if (p.mode == 1) val = val * ainv / (part + p.lam[p.d - 1][n]);
-            const long long q = (long long)n * MF + rq;
-            o[((long long)(rf >> 2) * p.Rn + q) * 4 + (rf & 3)] = val;
+            const long long addr = ((long long)(rf >> 2) * p.Rn + (long long)n * MF + rq) * 4 + (rf & 3);
+            float h, l;
+            split_hl(val, h, l);
+            ohi[addr] = h;
+            olo[addr] = l;
         }
     }
     if (!good && tid == 0) {
@@ -318,21 +289,26 @@ __global__ void __launch_bounds__(128, 1) k_fdm_tma(TmaPassArgs p, const int* sk
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tcols));
 }
 
-// natural FP32 input -> sliced workspace buffer 0 (layout of the pass along axis 0)
-__global__ void k_fdm_tma_slice(const float* __restrict__ x, float* ws, long long ws_stride, int n10, long long Rp0,
-                                long long total, const int* skip, Bat bt) {
+// natural FP32 input -> sliced hi/lo parts of workspace buffer 0 (layout of the pass along axis 0)
+__global__ void k_fdm_tma_split(const float* __restrict__ x, float* ws, long long ws_stride, long long wsz, int n10,
+                                long long Rp0, long long total, const int* skip, Bat bt) {
     const int pb = (int)blockIdx.y;
     long long off;
     if (!bat_enter(bt, pb, &off)) return;
     skip = bsh(skip, off);
     if (skip && *skip) return;
     x = bsh(x, off);
-    float* o = ws + (size_t)pb * ws_stride;
+    float* hi = ws + (size_t)pb * ws_stride;
+    float* lo = hi + wsz;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const int f = (int)(i % n10);
         const long long q = i / n10;
-        o[((long long)(f >> 2) * Rp0 + q) * 4 + (f & 3)] = x[i];
+        const long long addr = ((long long)(f >> 2) * Rp0 + q) * 4 + (f & 3);
+        float h, l;
+        split_hl(x[i], h, l);
+        hi[addr] = h;
+        lo[addr] = l;
     }
 }
 
@@ -354,8 +330,10 @@ int pow2_cols(int bn) {
 }
 
 size_t tma_stage_bytes(int bn) { return 2 * (size_t)kTBM * kTBK * 4 + 2 * (size_t)bn * kTBK * 4; }
-// stages that fit 192 KB (at most kTNS)
-int tma_stages(int bn) { return (int)std::min<size_t>(kTNS, (192 * 1024) / tma_stage_bytes(bn)); }
+// stages in about 96 KB (two CTAs per SM), at least 2 and at most kTNS
+int tma_stages(int bn) {
+    return (int)std::max<size_t>(2, std::min<size_t>(kTNS, (96 * 1024) / tma_stage_bytes(bn)));
+}
 size_t tma_smem(int bn) { return 1024 + (size_t)tma_stages(bn) * tma_stage_bytes(bn); }
 
 }  // namespace
@@ -369,8 +347,8 @@ cudaError_t launch_fdm_tma(const FdmTma& t, int variant, const double* alpha_dev
     {
         const long long total = t.R[0] * t.n1[0];
         const unsigned gx = (unsigned)std::min<long long>((total + 255) / 256, 2048);
-        k_fdm_tma_slice<<<dim3(gx, (unsigned)bt.np), 256, 0, s>>>(x, t.ws, 2 * t.wsz, t.n1[0], t.Rp[0], total, skip,
-                                                                  bt);
+        k_fdm_tma_split<<<dim3(gx, (unsigned)bt.np), 256, 0, s>>>(x, t.ws, 4 * t.wsz, t.wsz, t.n1[0], t.Rp[0], total,
+                                                                  skip, bt);
         note_kernel_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -380,9 +358,10 @@ cudaError_t launch_fdm_tma(const FdmTma& t, int variant, const double* alpha_dev
     for (int pass = 0; pass < 2 * d; ++pass) {
         const int ax = pass % d, fb = pass < d ? 0 : 1, in = pass % 2, out = 1 - in;
         TmaPassArgs a{};
-        a.mA = mA + (size_t)(ax * 2 + in);
-        a.mA_stride = 2 * d;
-        a.mB = mB + (size_t)((variant * d + ax) * 2 + fb);
+        a.mA = mA + (size_t)((ax * 2 + in) * 2);
+        a.mA_stride = 4 * d;
+        a.mBh = mB + (size_t)(((variant * d + ax) * 2 + fb) * 2);
+        a.mBl = a.mBh + 1;
         a.M = (int)t.R[ax];
         a.N = t.n1[ax];
         a.nch = t.Cp[ax] / kTSl;
@@ -393,8 +372,9 @@ cudaError_t launch_fdm_tma(const FdmTma& t, int variant, const double* alpha_dev
         a.lbo_a = kTBM * 16;
         a.lbo_b = a.BN * 16;
         a.mode = pass == 2 * d - 1 ? 2 : (pass == d - 1 ? 1 : 0);
-        a.out = t.ws + (size_t)out * t.wsz;
-        a.ws_stride = 2 * t.wsz;
+        a.ohi = t.ws + (size_t)out * 2 * t.wsz;
+        a.olo = a.ohi + t.wsz;
+        a.ws_stride = 4 * t.wsz;
         a.F = t.n1[(ax + 1) % d];
         a.Rn = t.Rp[(ax + 1) % d];
         a.y = y;
@@ -484,33 +464,45 @@ bool fdm_tma_setup(FdmTma& t, const HostProblem& H, const float* const* lam, int
         if (why) *why = "cuTensorMapEncodeTiled unavailable";
         return false;
     }
-    // the pass matrices: sliced FP32 V^T (forward) and V (backward), rows padded so that
-    // every variant's N tile is one in-bounds box; shared by a group
+    // the pass matrices: sliced high parts and remainders of V^T (forward) and V (backward),
+    // rows padded so that every variant's N tile is one in-bounds box; shared by a group
     if (consts) {
         t.mB = consts->mB;
     } else {
         const int nv = fdm_tma_variants();
-        std::vector<CUtensorMap> mb((size_t)nv * d * 2);
+        std::vector<CUtensorMap> mb((size_t)nv * d * 4);
         for (int j = 0; j < d; ++j) {
             const int n = t.n1[j], Cp = t.Cp[j];
             const int np_rows = n <= 64 ? (n + 15) / 16 * 16 : (n + 255) / 256 * 256;
             const std::vector<double>& V = H.dir[j].V;   // row-major V[k][a]
             for (int fb = 0; fb < 2; ++fb) {
-                std::vector<float> w((size_t)Cp * np_rows * 4, 0.0f);
+                std::vector<float> hi((size_t)Cp * np_rows * 4, 0.0f), lo((size_t)Cp * np_rows * 4, 0.0f);
                 for (int row = 0; row < n; ++row)
-                    for (int k = 0; k < n; ++k)   // forward W[a][k] = V[k][a]; backward W[a][k] = V[a][k]
-                        w[((size_t)(k >> 2) * np_rows + row) * 4 + (k & 3)] =
-                            (float)(fb == 0 ? V[(size_t)k * n + row] : V[(size_t)row * n + k]);
-                float* dw = static_cast<float*>(alloc(w.size() * sizeof(float)));
-                if (!dw) {
+                    for (int k = 0; k < n; ++k) {
+                        // forward W[a][k] = V[k][a]; backward W[a][k] = V[a][k]
+                        const float x = (float)(fb == 0 ? V[(size_t)k * n + row] : V[(size_t)row * n + k]);
+                        uint32_t bits;
+                        std::memcpy(&bits, &x, 4);
+                        bits &= 0xFFFFE000u;
+                        float h;
+                        std::memcpy(&h, &bits, 4);
+                        const size_t at = ((size_t)(k >> 2) * np_rows + row) * 4 + (k & 3);
+                        hi[at] = h;
+                        lo[at] = x - h;
+                    }
+                float* dh = static_cast<float*>(alloc(hi.size() * sizeof(float)));
+                float* dl = static_cast<float*>(alloc(lo.size() * sizeof(float)));
+                if (!dh || !dl) {
                     if (why) *why = "device allocation failed";
                     return false;
                 }
-                cudaMemcpyAsync(dw, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+                cudaMemcpyAsync(dh, hi.data(), hi.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+                cudaMemcpyAsync(dl, lo.data(), lo.size() * sizeof(float), cudaMemcpyHostToDevice, s);
                 cudaStreamSynchronize(s);
                 for (int v = 0; v < nv; ++v) {
-                    const int bn = tma_bn(v, n);
-                    if (!encode_sliced(&mb[(size_t)((v * d + j) * 2 + fb)], dw, np_rows, Cp, bn, tma_rb(bn))) {
+                    const int bn = tma_bn(v, n), rb = tma_rb(bn);
+                    if (!encode_sliced(&mb[(size_t)(((v * d + j) * 2 + fb) * 2) + 0], dh, np_rows, Cp, bn, rb) ||
+                        !encode_sliced(&mb[(size_t)(((v * d + j) * 2 + fb) * 2) + 1], dl, np_rows, Cp, bn, rb)) {
                         if (why) *why = "tensor map of a pass matrix rejected";
                         return false;
                     }
@@ -525,25 +517,26 @@ bool fdm_tma_setup(FdmTma& t, const HostProblem& H, const float* const* lam, int
         cudaMemcpyAsync(dmb, mb.data(), mb.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
         t.mB = dmb;
     }
-    // workspace: np x [buffer 0, buffer 1] (FP32, sliced), zeroed once (the padding of the
-    // last slice of every row is never written)
-    t.ws = static_cast<float*>(alloc((size_t)np * 2 * t.wsz * sizeof(float)));
+    // workspace: np x [buffer 0 high, remainder, buffer 1 high, remainder], zeroed once (the
+    // padding of the last slice of every row is never written)
+    t.ws = static_cast<float*>(alloc((size_t)np * 4 * t.wsz * sizeof(float)));
     if (!t.ws) {
         if (why) *why = "device allocation failed";
         return false;
     }
-    cudaMemsetAsync(t.ws, 0, (size_t)np * 2 * t.wsz * sizeof(float), s);
-    std::vector<CUtensorMap> ma((size_t)np * d * 2);
+    cudaMemsetAsync(t.ws, 0, (size_t)np * 4 * t.wsz * sizeof(float), s);
+    std::vector<CUtensorMap> ma((size_t)np * d * 4);
     for (int pb = 0; pb < np; ++pb)
         for (int j = 0; j < d; ++j)
-            for (int b = 0; b < 2; ++b) {
-                const float* base = t.ws + ((size_t)pb * 2 + (size_t)b) * t.wsz;
-                if (!encode_sliced(&ma[(size_t)pb * d * 2 + (size_t)(j * 2 + b)], base, t.Rp[j], t.Cp[j], kTBM,
-                                   kTRbA)) {
-                    if (why) *why = "tensor map of the workspace rejected";
-                    return false;
+            for (int b = 0; b < 2; ++b)
+                for (int hl = 0; hl < 2; ++hl) {
+                    const float* base = t.ws + ((size_t)pb * 4 + (size_t)b * 2 + hl) * t.wsz;
+                    if (!encode_sliced(&ma[(size_t)pb * d * 4 + (size_t)(j * 2 + b) * 2 + hl], base, t.Rp[j],
+                                       t.Cp[j], kTBM, kTRbA)) {
+                        if (why) *why = "tensor map of the workspace rejected";
+                        return false;
+                    }
                 }
-            }
     void* dma = alloc(ma.size() * sizeof(CUtensorMap));
     if (!dma) {
         if (why) *why = "device allocation failed";

@@ -88,9 +88,9 @@ size_t estimate_device_bytes(const Problem& P) {
         for (int j = 0; j < H.d; ++j) {
             const size_t n1 = H.dir[j].n1, R = Nu0 / n1;
             ws = std::max(ws, ((n1 + 15) / 16 * 16) * ((R + 127) / 128 * 128));
-            b += 2 * ((n1 + 15) / 16 * 16) * ((n1 + 255) / 256 * 256) * 4 + 4096;
+            b += 4 * ((n1 + 15) / 16 * 16) * ((n1 + 255) / 256 * 256) * 4 + 4096;
         }
-        b += 2 * ws * 4;
+        b += 4 * ws * 4;
     }
     b += (kmax + 1) * Npsi * 8;                          // Krylov basis
     b += (kmax + 1) * kmax * 8 + (size_t)gmres_dot_blocks((long long)Npsi) * (kmax + 2) * 8 + (kmax + 2) * 8;
