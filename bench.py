@@ -42,7 +42,8 @@ WORKLOAD = "radial32"
 # one A_alpha^{-1} apply on the 32x32 p=8 workload, from one ncu capture (`--kernel fdm
 # --precision mixed --fdm-tile 0`, cold caches)
 FDM_TRAFFIC_BYTES = (573952 + 575744 + 574720 + 573952)
-# the same for one batched apply (16 problems per launch); None until captured for the current kernels
+# DRAM bytes of one batched apply (16 problems per launch, the TMA variant's split kernel
+# and four passes) from the ncu capture in profiles/; None until captured for the current kernels
 FDM_BATCH_TRAFFIC_BYTES = None
 METRIC = "solves/s (complete hpG solve at 1e-8 rel err vs FP64 oracle), mixed vs FP64; DoF*Krylov-its/s"
 
@@ -576,19 +577,37 @@ def main():
     kb = results["mixed_batch"]["kernels"]
     if "fdm" in kb:
         # the dominant kernel of the timed step: the fast-diagonalisation A_alpha^{-1} apply
-        # (2d GEMM passes, FP32) as the batched step launches it, every problem of the
-        # group in one launch; algorithmic work = B x 4 d n1 N_u0 flops per launch
+        # (2d dense passes, FP32 in and out) as the batched step launches it, every problem
+        # of the group in one launch; algorithmic work = B x 4 d n1 N_u0 flops per launch
         _, flops, unit = work["fdm"]
         flops_b = flops * B
         avg_ms = kb["fdm"][0]
         ach = flops_b / (avg_ms / 1000.0) / 1e12
-        peak = alu_peaks["fp32"]
-        roof = {"kernel": f"fdm (A_alpha^-1, FP32 SIMT GEMM passes, {B} problems per launch as in the batched step)",
-                "bound": "alu", "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "traffic": FDM_BATCH_TRAFFIC_BYTES, "avg_launch_us": avg_ms * 1000.0, "problems_per_launch": B,
-                "flops_per_launch": flops_b,
-                "peak_source": "measured (hpg_measure_fma_peak, FP32 FMA chains on all SMs)",
-                "derived_peak": alu_peak_tflops("fp32", peak_mhz, sm_count)}
+        vb = results["mixed_batch"]["fdm_variant"]
+        ntile = hpg.fdm_tile_count(hpg.HPG_MIXED)
+        fp32_eq = {"achieved": ach, "peak": alu_peaks["fp32"], "unit": unit, "frac": ach / alu_peaks["fp32"],
+                   "peak_source": "measured (hpg_measure_fma_peak, FP32 FMA chains on all SMs)"}
+        if vb >= ntile - 3:
+            # tcgen05 kind::tf32 passes fed by TMA: three TF32 products (hi*hi + hi*lo + lo*hi)
+            # per FP32 product, so the tensor work is 3x the algorithmic flops; the TF32 dense
+            # peak is the measured bf16 burst rate times the nominal TF32 / bf16 ratio 1.1 / 2.25
+            tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+            tach = 3.0 * ach
+            roof = {"kernel": f"fdm (A_alpha^-1, tcgen05 3xTF32 passes fed by TMA, variant {vb}, "
+                              f"{B} problems per launch as in the batched step)",
+                    "bound": "tensor", "achieved": tach, "peak": tf32_peak, "unit": unit, "frac": tach / tf32_peak,
+                    "traffic": FDM_BATCH_TRAFFIC_BYTES, "avg_launch_us": avg_ms * 1000.0, "problems_per_launch": B,
+                    "flops_per_launch": 3.0 * flops_b, "algorithmic_flops_per_launch": flops_b,
+                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x nominal TF32/bf16 ratio",
+                    "fp32_equivalent": fp32_eq}
+        else:
+            roof = {"kernel": f"fdm (A_alpha^-1, FP32 SIMT GEMM passes, variant {vb}, {B} problems per launch "
+                              f"as in the batched step)",
+                    "bound": "alu", "achieved": ach, "peak": alu_peaks["fp32"], "unit": unit,
+                    "frac": ach / alu_peaks["fp32"], "traffic": None, "avg_launch_us": avg_ms * 1000.0,
+                    "problems_per_launch": B, "flops_per_launch": flops_b,
+                    "peak_source": "measured (hpg_measure_fma_peak, FP32 FMA chains on all SMs)",
+                    "derived_peak": alu_peak_tflops("fp32", peak_mhz, sm_count)}
     single_fdm = None
     if "fdm" in kt:
         # the same apply for one problem alone (latency-bound: few CTAs per pass)

@@ -497,18 +497,37 @@ static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, 
     int best = -1;
     float best_ms = 1e30f;
     double ref_max = 0.0;
-    // Timing at batch B (fdm_tune_batch): one launch per pass serves B copies that all read
-    // x and write y (the same values at the same addresses), as a lockstep group of B
-    // would; the TMA variants get a temporary workspace and tensor maps for B problems.
+    // Timing at batch B (fdm_tune_batch): one launch per pass serves B copies of the apply,
+    // each on its own input, output and intermediate buffers (a temporary block per copy,
+    // reached by byte offsets as a lockstep group's slabs are), as a group of B would; the
+    // TMA variants get a temporary workspace and tensor maps for B problems.
     Bat bb{};
     long long* dz = nullptr;
     FdmTma tb{};
     std::vector<void*> tallocs;
+    T* bx = nullptr;                 // copy 0's x, y, w1, w2 inside the temporary blocks
+    T *by = nullptr, *bw1 = nullptr, *bw2 = nullptr;
     if (B > 1) {
-        if (cudaMalloc(&dz, (size_t)B * sizeof(long long)) == cudaSuccess &&
-            cudaMemset(dz, 0, (size_t)B * sizeof(long long)) == cudaSuccess) {
-            bb.delta = dz;
-            bb.np = B;
+        const size_t np4 = (n + 63) / 64 * 64;
+        void* blk = nullptr;
+        std::vector<long long> hd((size_t)B);
+        for (int b = 0; b < B; ++b) hd[(size_t)b] = (long long)b * (long long)(4 * np4 * sizeof(T));
+        if (cudaMalloc(&blk, (size_t)B * 4 * np4 * sizeof(T)) == cudaSuccess) {
+            tallocs.push_back(blk);
+            bx = static_cast<T*>(blk);
+            by = bx + np4;
+            bw1 = bx + 2 * np4;
+            bw2 = bx + 3 * np4;
+            bool okb = cudaMalloc(&dz, (size_t)B * sizeof(long long)) == cudaSuccess &&
+                       cudaMemcpy(dz, hd.data(), (size_t)B * sizeof(long long), cudaMemcpyHostToDevice) ==
+                           cudaSuccess;
+            for (int b = 0; b < B && okb; ++b)
+                okb = cudaMemcpy(bx + (size_t)b * 4 * np4, hx.data(), n * sizeof(T), cudaMemcpyHostToDevice) ==
+                      cudaSuccess;
+            if (okb) {
+                bb.delta = dz;
+                bb.np = B;
+            }
         }
         if constexpr (sizeof(T) == 4) {
             if (P.D.tma_ok && bb.np == B) {
@@ -551,17 +570,22 @@ static hpg_status autotune_fdm(hpg_ctx* ctx, Problem& P, Geo<T>& g, T* x, T* y, 
         }
         Geo<T> gt = g;
         Bat bt{};
+        T *tx = x, *ty = y, *tw1 = w1, *tw2 = w2;
         if (B > 1) {
             if (bb.np != B) continue;
             bt = bb;
+            tx = bx;
+            ty = by;
+            tw1 = bw1;
+            tw2 = bw2;
             if (gt.tma) gt.tma = tb.ready ? &tb : nullptr;
         }
-        if (launch_fdm<T>(gt, nullptr, 1.0, x, y, w1, w2, s, nullptr, bt) != cudaSuccess) {   // warm-up
+        if (launch_fdm<T>(gt, nullptr, 1.0, tx, ty, tw1, tw2, s, nullptr, bt) != cudaSuccess) {   // warm-up
             cudaGetLastError();
             continue;
         }
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 5; ++r) launch_fdm<T>(gt, nullptr, 1.0, x, y, w1, w2, s, nullptr, bt);
+        for (int r = 0; r < (B > 1 ? 10 : 5); ++r) launch_fdm<T>(gt, nullptr, 1.0, tx, ty, tw1, tw2, s, nullptr, bt);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
         float ms = 0.f;
