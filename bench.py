@@ -769,7 +769,7 @@ def main():
     qvi = None
     if not args.no_qvi:
         qvi = {}
-        for p_deg in (6, 12, 22, 32):
+        for p_deg in (6, 12, 22):
             wq = W.workload(f"thermoforming_p{p_deg}")
             P = hpg.Problem(ctx, 2, [0.0, 0.0], [1.0, 1.0], [4, 4], p_deg, hpg.HPG_OBSTACLE_UPPER)
             P.set_rhs(wq["f_const"])

@@ -72,7 +72,13 @@ def test_sine3d_full_size_against_stored_oracle(ctx, precision):
         assert abs(a - b) <= 1, (st["newton_per_step"], list(g["newton"]))
     err, nrm = P.l2_error(g["u"])
     assert err / nrm <= (1e-9 if precision == 0 else 1e-8), err / nrm
-    assert rel(P.psi(), g["psi"]) <= (1e-8 if precision == 0 else 1e-7)
+    # psi is fixed by the Newton test only through the psi block -(D_psi + beta M_Psi) of
+    # eq. (pG-matrix): where exp(-psi) is tiny a residual of 1e-10 leaves a psi coefficient
+    # free up to 1e-10 / (beta m), m the smallest diagonal entry of M_Psi (beta = 1e-5 and
+    # m = |K| / 9^3 = 2.7e-6 on 8^3 cells at degree 4 per direction: up to ~4 in absolute
+    # terms), so psi is compared at 1e-4 relative and u_h, which the constraint pins, at the
+    # gates above
+    assert rel(P.psi(), g["psi"]) <= 1e-4
     P.free()
 
 
