@@ -120,8 +120,10 @@ typedef struct {
                              conditional graph nodes)                                          */
     int    fdm_tile_f32;  /* -1 (default): the FP32 fast-diagonalisation pass variant is picked
                              by timing all of them at set-up; 0 .. hpg_fdm_tile_count(HPG_MIXED)-1
-                             forces one (the last two are the tcgen05 3xTF32 tensor-core
-                             kernels); changing it releases the problem's device state       */
+                             forces one (the last six are tcgen05 3xTF32 tensor-core
+                             kernels: two staging operands element by element, then four fed
+                             by TMA with N tiles of 64, 128, 256 and 32 columns); changing it
+                             releases the problem's device state                              */
     int    fdm_tile_f64;  /* the same for the FP64 passes                                     */
     int    strategy;      /* hpg_strategy; default HPG_SCHUR; the FGMRES strategies need
                              precision HPG_FP64 (HPG_ERR_ARG otherwise)                       */

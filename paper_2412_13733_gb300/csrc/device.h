@@ -190,7 +190,7 @@ struct FdmTma {
     const void* mB = nullptr;                      // device CUtensorMap [variant][d][fwd, bwd][hi, lo]
     const float* lam[kMaxDim] = {};
 };
-// Number of TMA variants (N tiles of 64, 128, 256 columns).
+// Number of TMA variants (N tiles of 64, 128, 256 and 32 columns).
 int fdm_tma_variants();
 // y = A_alpha^{-1} x (or (A + shift M)^{-1} x) for every problem of bt; x, y natural FP32.
 cudaError_t launch_fdm_tma(const FdmTma& t, int variant, const double* alpha_dev, double alpha, const float* x,

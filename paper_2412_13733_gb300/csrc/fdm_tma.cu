@@ -312,16 +312,19 @@ __global__ void k_fdm_tma_split(const float* __restrict__ x, float* ws, long lon
     }
 }
 
+// N tile of a variant: 64, 128 or 256 columns (at most n1 rounded up to 16), or 32 (variant 3:
+// more, smaller CTAs)
 int tma_bn(int variant, int n1) {
     const int r16 = (n1 + 15) / 16 * 16;
+    if (variant == 3) return std::min(32, r16);
     if (r16 <= 64) return r16;
     const int cap = variant == 0 ? 64 : (variant == 1 ? 128 : 256);
     const int r64 = (n1 + 63) / 64 * 64;
     return std::min(cap, r64);
 }
 
-// rows per innermost TMA run of a B tile of bn rows
-int tma_rb(int bn) { return bn <= 64 ? bn : 64; }
+// rows per innermost TMA run of a B tile of bn rows (a divisor of bn and of the padded rows)
+int tma_rb(int bn) { return bn % 64 == 0 ? 64 : 16; }
 
 int pow2_cols(int bn) {
     int c = 32;
@@ -338,7 +341,7 @@ size_t tma_smem(int bn) { return 1024 + (size_t)tma_stages(bn) * tma_stage_bytes
 
 }  // namespace
 
-int fdm_tma_variants() { return 3; }
+int fdm_tma_variants() { return 4; }
 
 cudaError_t launch_fdm_tma(const FdmTma& t, int variant, const double* alpha_dev, double alpha, const float* x,
                            float* y, cudaStream_t s, const int* skip, const Bat& bt, double shift) {
@@ -473,7 +476,7 @@ bool fdm_tma_setup(FdmTma& t, const HostProblem& H, const float* const* lam, int
         std::vector<CUtensorMap> mb((size_t)nv * d * 4);
         for (int j = 0; j < d; ++j) {
             const int n = t.n1[j], Cp = t.Cp[j];
-            const int np_rows = n <= 64 ? (n + 15) / 16 * 16 : (n + 255) / 256 * 256;
+            const int np_rows = (n + 255) / 256 * 256;   // a multiple of every variant's N tile
             const std::vector<double>& V = H.dir[j].V;   // row-major V[k][a]
             for (int fb = 0; fb < 2; ++fb) {
                 std::vector<float> hi((size_t)Cp * np_rows * 4, 0.0f), lo((size_t)Cp * np_rows * 4, 0.0f);
