@@ -246,6 +246,13 @@ hpg_status hpg_set_dirichlet(hpg_ctx* ctx, int pid, hpg_field_fn g, void* user);
  * (Sections 6.1-6.5), or an explicit list (count <= HPG_MAX_ALPHA). */
 hpg_status hpg_set_alpha_schedule(hpg_ctx* ctx, int pid, double a1, double cap);
 hpg_status hpg_set_alpha_list(hpg_ctx* ctx, int pid, const double* alphas, int count);
+/* alpha_k = min(a1 growth^{k-1}, cap) for k = 1 .. max_steps (growth >= 1, max_steps <=
+ * HPG_MAX_ALPHA); the schedule ends at the first step that reaches cap (cap_twice = 0:
+ * "terminate once alpha_k = cap", as for the QVI of Section 6.4: a1 = 2^-6, growth 4, cap 1
+ * gives 2^-6, 2^-4, 2^-2, 1) or after cap has been repeated once (cap_twice = 1, the rule of
+ * hpg_set_alpha_schedule with growth sqrt(2)). */
+hpg_status hpg_set_alpha_growth(hpg_ctx* ctx, int pid, double a1, double growth, double cap, int max_steps,
+                                int cap_twice);
 
 hpg_status hpg_set_params(hpg_ctx* ctx, int pid, const hpg_params* params);
 

@@ -300,6 +300,24 @@ hpg_status hpg_set_alpha_schedule(hpg_ctx* ctx, int pid, double a1, double cap) 
     return HPG_OK;
 }
 
+hpg_status hpg_set_alpha_growth(hpg_ctx* ctx, int pid, double a1, double growth, double cap, int max_steps,
+                                int cap_twice) {
+    Problem* P = find(ctx, pid);
+    if (!P || !(a1 > 0.0) || !(growth >= 1.0) || !std::isfinite(growth) || !(cap > 0.0) || max_steps < 1 ||
+        max_steps > HPG_MAX_ALPHA || (cap_twice != 0 && cap_twice != 1))
+        return HPG_ERR_ARG;
+    NOT_BUSY(P);
+    std::vector<double> al;
+    for (int k = 1; k <= max_steps; ++k) {
+        const double a = std::min(a1 * std::pow(growth, (double)(k - 1)), cap);
+        if (!cap_twice && !al.empty() && al.back() == a) break;
+        al.push_back(a);
+        if (cap_twice && al.size() >= 2 && al[al.size() - 1] == al[al.size() - 2]) break;
+    }
+    P->H.alphas = al;
+    return HPG_OK;
+}
+
 hpg_status hpg_set_alpha_list(hpg_ctx* ctx, int pid, const double* alphas, int count) {
     Problem* P = find(ctx, pid);
     if (!P || !alphas || count < 1 || count > HPG_MAX_ALPHA) return HPG_ERR_ARG;

@@ -84,6 +84,7 @@ SIGNATURES = {
     "hpg_set_dirichlet": ([_ctx, C.c_int, FIELD_FN, C.c_void_p], C.c_int),
     "hpg_set_alpha_schedule": ([_ctx, C.c_int, _d, _d], C.c_int),
     "hpg_set_alpha_list": ([_ctx, C.c_int, _pd, C.c_int], C.c_int),
+    "hpg_set_alpha_growth": ([_ctx, C.c_int, _d, _d, _d, C.c_int, C.c_int], C.c_int),
     "hpg_set_params": ([_ctx, C.c_int, _P(hpg_params)], C.c_int),
     "hpg_solve": ([_ctx, C.c_int], C.c_int),
     "hpg_solve_batch": ([_ctx, _P(C.c_int), C.c_int], C.c_int),
@@ -330,6 +331,10 @@ class Problem:
     def set_alphas(self, alphas):
         a = _f64(alphas)
         self.ctx.check(self.L.hpg_set_alpha_list(self.ctx.h, self.pid, _dptr(a), a.size), "hpg_set_alpha_list")
+
+    def set_alpha_growth(self, a1, growth, cap, max_steps=HPG_MAX_ALPHA, cap_twice=False):
+        self.ctx.check(self.L.hpg_set_alpha_growth(self.ctx.h, self.pid, float(a1), float(growth), float(cap),
+                                                   int(max_steps), int(bool(cap_twice))), "hpg_set_alpha_growth")
 
     def set_alpha_schedule(self, a1, cap):
         self.ctx.check(self.L.hpg_set_alpha_schedule(self.ctx.h, self.pid, float(a1), float(cap)))

@@ -32,7 +32,9 @@ def _setup(ctx, w):
                     hpg.HPG_OBSTACLE_UPPER)
     P.set_rhs(w["f_const"])
     P.set_dirichlet(None)
-    P.set_alphas(w["alphas"])
+    # Section 6.4's rule: alpha_1 = 2^-6, alpha_{k+1} = 4 alpha_k, stop once alpha_k = 1 (the
+    # oracle takes the same four values as a list)
+    P.set_alpha_growth(2.0 ** -6, 4.0, 1.0)
     prm = hpg.default_params()
     prm.beta = w["beta"]
     prm.newton_tol = 1e-10
@@ -65,6 +67,7 @@ def test_qvi_matches_oracle(ctx, name):
                   beta=w["beta"])
     r = q.solve(w["alphas"], tol=w["qvi_tol"], newton_tol=1e-10)
     assert rc == 0 and st["converged"] == 1
+    assert P.stats()["alpha_steps"] == len(w["alphas"])     # the growth rule gives the oracle's list
     assert st["iterations"] == r["iterations"], (st, [h["du_h1"] for h in r["history"]])
     # per-iteration H^1 differences (the fixed point's contraction), then u and T
     want = [h["du_h1"] for h in r["history"][1:]]
@@ -83,9 +86,8 @@ def test_qvi_matches_oracle(ctx, name):
 
 @pytest.mark.parametrize("p", [12, 22])
 def test_qvi_fixed_point_count_at_high_degree(ctx, p):
-    """Table 3: four fixed-point iterations at every degree on the 4 x 4 mesh; the device
-    (u, T) satisfies the oracle's T equation; the final mould lies above the membrane at
-    the latent points up to the proximal tolerance."""
+    """Table 3: four fixed-point iterations at every degree on the 4 x 4 mesh, one to three
+    temperature Newton steps each; the device (u, T) satisfies the oracle's T equation."""
     w = W.workload(f"thermoforming_p{p}")
     P, data = _setup(ctx, w)
     rc, st = P.qvi_solve(*data, gamma=w["gamma"], g0=w["g0"], tol=w["qvi_tol"])
@@ -104,6 +106,12 @@ def test_qvi_argument_errors(ctx):
     from paper_2412_13733_gb300 import hpg
     w = W.workload("thermoforming_p3")
     P, data = _setup(ctx, w)
+    for bad in ((0.0, 4.0, 1.0), (1.0, 0.5, 1.0), (1.0, 2.0, -1.0)):
+        with pytest.raises(hpg.HpgError):
+            P.set_alpha_growth(*bad)
+    with pytest.raises(hpg.HpgError):
+        P.set_alpha_growth(1.0, 2.0, 4.0, max_steps=hpg.HPG_MAX_ALPHA + 1)
+    P.set_alpha_growth(2.0 ** -6, 4.0, 1.0)
     with pytest.raises(hpg.HpgError):
         P.qvi_T()                                     # no QVI solve yet
     rc, _ = P.qvi_solve(data[0][:-1], data[1], data[2], data[3], check=False)
