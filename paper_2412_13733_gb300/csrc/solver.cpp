@@ -1451,8 +1451,9 @@ static hpg_status group_tune_fdm(hpg_ctx* ctx, Group& Gp) {
     }
     if (forced >= 0 || ks == 0 || Gp.np == 1) return HPG_OK;
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int, int>, int> cache;
-    const auto key = std::make_tuple(gg.d, gg.n1[0], gg.n1[1], gg.d > 2 ? gg.n1[2] : 1, (int)sizeof(T), Gp.np);
+    static std::map<std::tuple<int, int, int, int, int, int, int>, int> cache;
+    const auto key =
+        std::make_tuple(gg.d, gg.n1[0], gg.n1[1], gg.d > 2 ? gg.n1[2] : 1, (int)sizeof(T), Gp.np, ks);
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);

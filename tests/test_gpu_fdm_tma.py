@@ -148,7 +148,7 @@ def test_tune_batch_group_equals_alone(ctx):
     ctx.solve_batch(probs)
     for P, (u, v) in zip(probs, alone):
         st = P.stats()
-        assert st["status"] == 0 and st["fdm_tile_f32"] == v
-        assert np.array_equal(P.u(), u)
+        assert st["status"] == 0 and st["fdm_tile_f32"] == v, (st["fdm_tile_f32"], v)
+        assert np.array_equal(P.u(), u), (v, float(np.max(np.abs(P.u() - u))))
     for P in probs:
         P.free()
