@@ -2386,15 +2386,24 @@ __global__ void __launch_bounds__(256)
 template <typename T, typename Tout>
 cudaError_t launch_schur_rest(const Geo<T>& g, const T* gw, double beta, const T* z, const T* t, Tout* w,
                               cudaStream_t s, IterCtl ctl, const Bat& bt) {
-    // one cell per block here (measured faster than several cells per block for the
-    // FP32 and FP64 Krylov-loop applies); the fused Newton apply groups cells
-    const int gs = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256), cpb = 1;
+    // one cell per block for a single problem (measured faster than several cells per block
+    // for the FP32 and FP64 Krylov-loop applies, which are latency-bound); a lockstep launch
+    // over several problems packs floor(256 / nb) cells into 256-thread blocks, as the fused
+    // Newton apply does.  Each cell's arithmetic is the same either way.
+    int gs = g.nb <= 64 ? 64 : (g.nb <= 128 ? 128 : 256), cpb = 1, threads = gs;
+    if (bt.np > 1 && g.nb <= 128) {
+        gs = (int)g.nb;
+        cpb = std::max(1, 256 / gs);
+        threads = 256;
+    }
     const size_t smem = (size_t)(cpb + 1) * (3 * g.nb + g.n * g.n) * sizeof(T);
-    const dim3 blocks((unsigned)g.Nc, bt.np);
+    const dim3 blocks((unsigned)((g.Nc + cpb - 1) / cpb), bt.np);
     if (g.d == 2)
-        k_cellop<2, T, T, T, Tout><<<blocks, gs, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb, bt);
+        k_cellop<2, T, T, T, Tout><<<blocks, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb,
+                                                                bt);
     else
-        k_cellop<3, T, T, T, Tout><<<blocks, gs, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb, bt);
+        k_cellop<3, T, T, T, Tout><<<blocks, threads, smem, s>>>(g, gw, (T)beta, z, t, T(-1), T(-1), w, ctl, gs, cpb,
+                                                                bt);
     note_launch();
     return cudaGetLastError();
 }
