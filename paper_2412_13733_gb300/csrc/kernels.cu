@@ -940,6 +940,105 @@ __global__ void __launch_bounds__(128)
     for (int o = lane; o < nb * nb; o += 32) out[o] = A[o];
 }
 
+// FP32 blocks of 33 .. 64 rows: one cell per block of 64 threads, thread t keeping row t of
+// the block in registers (64 columns, identity rows past nb).  The same assembly and the same
+// Gauss-Jordan updates as k_factor_warp<float, 2> (hence the same bits), with half the
+// registers per thread: more cells resident per SM.  The pivot row moves through shared
+// memory (double-buffered, one block barrier per step) and is read as 16-byte words.
+__global__ void __launch_bounds__(64)
+    k_factor_rows(Geo<float> g, const float* __restrict__ gw, float alpha_inv, float beta, float* __restrict__ Sinv,
+                  double* __restrict__ dump, int* __restrict__ flag, Bat bt) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    long long off;
+    const int pb = (int)blockIdx.y;
+    if (!bat_enter(bt, pb, &off)) return;
+    gw = bsh(gw, off); Sinv = bsh(Sinv, off); dump = bsh(dump, off); flag = bsh(flag, off);
+    if (bt.par) alpha_inv = (float)(1.0 / bt.par[pb * kBatPar + kParAlpha]);
+    const int n = g.n, nloc = (int)g.nloc, nb = (int)g.nb, nc = g.ncomp;
+    const int t = threadIdx.x;
+    const long long cell = blockIdx.x;
+    const size_t per = factor_warp_elems(n, g.d, nb, nc);
+    float* A = reinterpret_cast<float*>(smraw);
+    float* bufA = (nc > 1) ? A + (size_t)nb * nb : A;
+    float* bufB = bufA + (nc > 1 ? (size_t)nloc * nloc : (size_t)nb * nb);
+    float* Vq = bufB;
+    {
+        size_t nbuf_b = 1;
+        for (int q = 0; q < 2 * g.d - 1; ++q) nbuf_b *= n;
+        Vq = bufB + nbuf_b;
+    }
+    float* rbuf = A + (per - (nb > 128 ? nb : 128));
+    for (int i = t; i < n * n; i += 64) Vq[i] = g.Vq[i];
+    __syncthreads();
+    const int gs = (g.kind == HPG_GRADIENT) ? g.d * (g.d + 1) / 2 : 1;
+    if (nc == 1) {
+        assemble_D_block<float, false>(g, gw, cell, 1, 0, Vq, A, bufB, t, 64);
+        for (int o = t; o < nloc * nloc; o += 64) {
+            const int I = o / nloc, J = o % nloc;
+            float v = A[o] + g.C[o] * alpha_inv;
+            if (I == J) v += beta * g.Mpsi[I];
+            A[o] = v;
+        }
+    } else {
+        int e = 0;
+        for (int ca = 0; ca < nc; ++ca)
+            for (int cb = ca; cb < nc; ++cb, ++e) {
+                assemble_D_block<float, false>(g, gw, cell, gs, e, Vq, bufA, bufB, t, 64);
+                for (int o = t; o < nloc * nloc; o += 64) {
+                    const int I = o / nloc, J = o % nloc;
+                    float v = bufA[o];
+                    if (ca == cb) v += beta * g.Kpsi[o];
+                    A[(size_t)(ca * nloc + I) * nb + cb * nloc + J] = v;
+                    A[(size_t)(cb * nloc + J) * nb + ca * nloc + I] = v;
+                }
+                __syncthreads();
+            }
+    }
+    __syncthreads();
+    if (dump)
+        for (int o = t; o < nb * nb; o += 64) dump[cell * nb * nb + o] = (double)A[o];
+    constexpr int NM = 64;
+    float a[NM];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) a[j] = (t < nb && j < nb) ? A[(size_t)t * nb + j] : (t == j ? 1.f : 0.f);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+        if (k >= nb) break;
+        float* rb = rbuf + (k & 1) * 64;
+        if (t == k) {
+#pragma unroll
+            for (int q = 0; q < NM / 4; ++q)
+                reinterpret_cast<float4*>(rb)[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+        }
+        __syncthreads();
+        float p = rb[k];
+        if (!(p > 0.f)) { bad = true; p = 1.f; }
+        const float inv = 1.f / p;
+        const bool is_k = t == k;
+        const float f = a[k];
+        const float fp = is_k ? 1.f - inv : f * inv;
+#pragma unroll
+        for (int q = 0; q < NM / 4; ++q) {
+            const float4 r4 = reinterpret_cast<const float4*>(rb)[q];
+            const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (4 * q + u != k) a[4 * q + u] -= fp * rr[u];
+        }
+        a[k] = is_k ? inv : -fp;
+    }
+    __syncthreads();
+    if (t < nb)
+#pragma unroll
+        for (int j = 0; j < NM; ++j)
+            if (j < nb) A[(size_t)t * nb + j] = a[j];
+    __syncthreads();
+    if (bad && t == 0) atomicOr(flag + 1, 2);
+    float* out = Sinv + cell * (long long)nb * nb;
+    for (int o = t; o < nb * nb; o += 64) out[o] = A[o];
+}
+
 // the factorisation workspace of a cell stays in shared memory up to this size
 // (227 KB per block on this GPU, less the kernel's static shared memory)
 constexpr size_t kFactorSmemMax = 225 * 1024;
@@ -978,7 +1077,8 @@ cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double bet
         }
         if constexpr (sizeof(T) == 4)
             if (!done && g.nb <= 64) {
-                k_factor_warp<T, 2><<<grid, 32 * wpb, per * wpb, s>>>(g, gw, ai, be, Sinv, dump, flag, wpb, bt);
+                // one cell per 64-thread block, a row per thread (k_factor_rows)
+                k_factor_rows<<<dim3((unsigned)g.Nc, bt.np), 64, per, s>>>(g, gw, ai, be, Sinv, dump, flag, bt);
                 done = true;
             }
         if (!done) k_factor_warp<T, 0><<<grid, 32 * wpb, per * wpb, s>>>(g, gw, ai, be, Sinv, dump, flag, wpb, bt);
@@ -3626,6 +3726,7 @@ void configure_kernels() {
     cudaFuncSetAttribute(k_factor_warp<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor_warp<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor_warp<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor_warp<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor_warp<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
 
