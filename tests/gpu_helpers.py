@@ -89,3 +89,13 @@ def mass_norm(o, v):
 
 def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def rel_entry(a, b):
+    """The larger of the relative l2 error and the largest entry error over the largest
+    entry: an error that sits in a few entries (a boundary row, a ragged tile) must also stay
+    below the tolerance."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    mx = float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)) if b.size else 0.0
+    return max(rel(a, b), mx)

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from tests.gpu_helpers import case, oracle_for, random_state, rel
+from tests.gpu_helpers import case, oracle_for, random_state, rel_entry as rel
 
 pytestmark = pytest.mark.gpu
 
