@@ -940,42 +940,44 @@ __global__ void __launch_bounds__(128)
     for (int o = lane; o < nb * nb; o += 32) out[o] = A[o];
 }
 
-// FP32 blocks of 33 .. 64 rows: one cell per block of 64 threads, thread t keeping row t of
-// the block in registers (64 columns, identity rows past nb).  The same assembly and the same
-// Gauss-Jordan updates as k_factor_warp<float, 2> (hence the same bits), with half the
-// registers per thread: more cells resident per SM.  The pivot row moves through shared
+// Blocks of 33 .. 64 rows: one cell per block of 64 threads, thread t keeping row t of the
+// block in registers (64 columns, identity rows past nb).  In FP32 the same assembly and the
+// same Gauss-Jordan updates as k_factor_warp<float, 2> (hence the same bits) with half the
+// registers per thread, so more cells are resident per SM (FP32 only: in FP64 the
+// shared-memory elimination of k_factor_warp<double, 0> is faster).  The pivot row moves through shared
 // memory (double-buffered, one block barrier per step) and is read as 16-byte words.
+template <typename T>
 __global__ void __launch_bounds__(64)
-    k_factor_rows(Geo<float> g, const float* __restrict__ gw, float alpha_inv, float beta, float* __restrict__ Sinv,
+    k_factor_rows(Geo<T> g, const T* __restrict__ gw, T alpha_inv, T beta, T* __restrict__ Sinv,
                   double* __restrict__ dump, int* __restrict__ flag, Bat bt) {
     extern __shared__ __align__(16) unsigned char smraw[];
     long long off;
     const int pb = (int)blockIdx.y;
     if (!bat_enter(bt, pb, &off)) return;
     gw = bsh(gw, off); Sinv = bsh(Sinv, off); dump = bsh(dump, off); flag = bsh(flag, off);
-    if (bt.par) alpha_inv = (float)(1.0 / bt.par[pb * kBatPar + kParAlpha]);
+    if (bt.par) alpha_inv = (T)(1.0 / bt.par[pb * kBatPar + kParAlpha]);
     const int n = g.n, nloc = (int)g.nloc, nb = (int)g.nb, nc = g.ncomp;
     const int t = threadIdx.x;
     const long long cell = blockIdx.x;
     const size_t per = factor_warp_elems(n, g.d, nb, nc);
-    float* A = reinterpret_cast<float*>(smraw);
-    float* bufA = (nc > 1) ? A + (size_t)nb * nb : A;
-    float* bufB = bufA + (nc > 1 ? (size_t)nloc * nloc : (size_t)nb * nb);
-    float* Vq = bufB;
+    T* A = reinterpret_cast<T*>(smraw);
+    T* bufA = (nc > 1) ? A + (size_t)nb * nb : A;
+    T* bufB = bufA + (nc > 1 ? (size_t)nloc * nloc : (size_t)nb * nb);
+    T* Vq = bufB;
     {
         size_t nbuf_b = 1;
         for (int q = 0; q < 2 * g.d - 1; ++q) nbuf_b *= n;
         Vq = bufB + nbuf_b;
     }
-    float* rbuf = A + (per - (nb > 128 ? nb : 128));
+    T* rbuf = A + (per - (nb > 128 ? nb : 128));
     for (int i = t; i < n * n; i += 64) Vq[i] = g.Vq[i];
     __syncthreads();
     const int gs = (g.kind == HPG_GRADIENT) ? g.d * (g.d + 1) / 2 : 1;
     if (nc == 1) {
-        assemble_D_block<float, false>(g, gw, cell, 1, 0, Vq, A, bufB, t, 64);
+        assemble_D_block<T, false>(g, gw, cell, 1, 0, Vq, A, bufB, t, 64);
         for (int o = t; o < nloc * nloc; o += 64) {
             const int I = o / nloc, J = o % nloc;
-            float v = A[o] + g.C[o] * alpha_inv;
+            T v = A[o] + g.C[o] * alpha_inv;
             if (I == J) v += beta * g.Mpsi[I];
             A[o] = v;
         }
@@ -983,10 +985,10 @@ __global__ void __launch_bounds__(64)
         int e = 0;
         for (int ca = 0; ca < nc; ++ca)
             for (int cb = ca; cb < nc; ++cb, ++e) {
-                assemble_D_block<float, false>(g, gw, cell, gs, e, Vq, bufA, bufB, t, 64);
+                assemble_D_block<T, false>(g, gw, cell, gs, e, Vq, bufA, bufB, t, 64);
                 for (int o = t; o < nloc * nloc; o += 64) {
                     const int I = o / nloc, J = o % nloc;
-                    float v = bufA[o];
+                    T v = bufA[o];
                     if (ca == cb) v += beta * g.Kpsi[o];
                     A[(size_t)(ca * nloc + I) * nb + cb * nloc + J] = v;
                     A[(size_t)(cb * nloc + J) * nb + ca * nloc + I] = v;
@@ -998,33 +1000,40 @@ __global__ void __launch_bounds__(64)
     if (dump)
         for (int o = t; o < nb * nb; o += 64) dump[cell * nb * nb + o] = (double)A[o];
     constexpr int NM = 64;
-    float a[NM];
+    constexpr int VW = 16 / (int)sizeof(T);
+    using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    T a[NM];
 #pragma unroll
-    for (int j = 0; j < NM; ++j) a[j] = (t < nb && j < nb) ? A[(size_t)t * nb + j] : (t == j ? 1.f : 0.f);
+    for (int j = 0; j < NM; ++j) a[j] = (t < nb && j < nb) ? A[(size_t)t * nb + j] : T(t == j ? 1 : 0);
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < NM; ++k) {
         if (k >= nb) break;
-        float* rb = rbuf + (k & 1) * 64;
+        T* rb = rbuf + (k & 1) * 64;
         if (t == k) {
 #pragma unroll
-            for (int q = 0; q < NM / 4; ++q)
-                reinterpret_cast<float4*>(rb)[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+            for (int q = 0; q < NM / VW; ++q) {
+                V16 v;
+                T* vt = reinterpret_cast<T*>(&v);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) vt[u] = a[VW * q + u];
+                reinterpret_cast<V16*>(rb)[q] = v;
+            }
         }
         __syncthreads();
-        float p = rb[k];
-        if (!(p > 0.f)) { bad = true; p = 1.f; }
-        const float inv = 1.f / p;
+        T p = rb[k];
+        if (!(p > T(0))) { bad = true; p = T(1); }
+        const T inv = T(1) / p;
         const bool is_k = t == k;
-        const float f = a[k];
-        const float fp = is_k ? 1.f - inv : f * inv;
+        const T f = a[k];
+        const T fp = is_k ? T(1) - inv : f * inv;
 #pragma unroll
-        for (int q = 0; q < NM / 4; ++q) {
-            const float4 r4 = reinterpret_cast<const float4*>(rb)[q];
-            const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+        for (int q = 0; q < NM / VW; ++q) {
+            const V16 r = reinterpret_cast<const V16*>(rb)[q];
+            const T* rr = reinterpret_cast<const T*>(&r);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (4 * q + u != k) a[4 * q + u] -= fp * rr[u];
+            for (int u = 0; u < VW; ++u)
+                if (VW * q + u != k) a[VW * q + u] -= fp * rr[u];
         }
         a[k] = is_k ? inv : -fp;
     }
@@ -1035,7 +1044,7 @@ __global__ void __launch_bounds__(64)
             if (j < nb) A[(size_t)t * nb + j] = a[j];
     __syncthreads();
     if (bad && t == 0) atomicOr(flag + 1, 2);
-    float* out = Sinv + cell * (long long)nb * nb;
+    T* out = Sinv + cell * (long long)nb * nb;
     for (int o = t; o < nb * nb; o += 64) out[o] = A[o];
 }
 
@@ -1075,10 +1084,12 @@ cudaError_t launch_factor(const Geo<T>& g, const T* gw, double alpha, double bet
             k_factor_warp<T, 1><<<grid, 32 * wpb, per * wpb, s>>>(g, gw, ai, be, Sinv, dump, flag, wpb, bt);
             done = true;
         }
+        // FP32: one cell per 64-thread block, a row per thread (k_factor_rows); in FP64 that form
+        // measured slower than the shared-memory elimination (589 against 476 us on 1024 cells
+        // of 49 rows)
         if constexpr (sizeof(T) == 4)
             if (!done && g.nb <= 64) {
-                // one cell per 64-thread block, a row per thread (k_factor_rows)
-                k_factor_rows<<<dim3((unsigned)g.Nc, bt.np), 64, per, s>>>(g, gw, ai, be, Sinv, dump, flag, bt);
+                k_factor_rows<T><<<dim3((unsigned)g.Nc, bt.np), 64, per, s>>>(g, gw, ai, be, Sinv, dump, flag, bt);
                 done = true;
             }
         if (!done) k_factor_warp<T, 0><<<grid, 32 * wpb, per * wpb, s>>>(g, gw, ai, be, Sinv, dump, flag, wpb, bt);
@@ -3726,7 +3737,7 @@ void configure_kernels() {
     cudaFuncSetAttribute(k_factor_warp<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor_warp<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor_warp<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
-    cudaFuncSetAttribute(k_factor_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
+    cudaFuncSetAttribute(k_factor_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor_warp<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
     cudaFuncSetAttribute(k_factor_warp<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmemMax);
 
