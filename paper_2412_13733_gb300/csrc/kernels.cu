@@ -2718,11 +2718,14 @@ __global__ void k_gm_start(VT* __restrict__ Vb, const double* __restrict__ b, lo
     double v = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
     v = block_sum(v, sh);
-    __shared__ double beta;
-    if (threadIdx.x == 0) beta = sqrt(v);
+    __shared__ double beta, binv;
+    if (threadIdx.x == 0) {
+        beta = sqrt(v);
+        binv = beta > 0.0 ? 1.0 / beta : 0.0;
+    }
     __syncthreads();
     const double bb = beta;
-    const double inv = bb > 0.0 ? 1.0 / bb : 0.0;
+    const double inv = binv;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
         Vb[i] = (VT)(b[i] * inv);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -3021,9 +3024,15 @@ __global__ void __launch_bounds__(256)
                  int kmax, double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
                  double* __restrict__ gv, double* __restrict__ scal, int* __restrict__ iflag,
                  const int* __restrict__ reo, unsigned int* __restrict__ counter, int* __restrict__ jdev, Bat bt) {
-    __shared__ double h[kMaxKrylov + 2];
-    __shared__ VT hv[kMaxKrylov + 2];
-    __shared__ double shn;
+    // dynamic shared memory sized for kmax: h, scol (kmax + 2), scs, ssn
+    // (kmax) doubles, then hv (kmax + 2) in the basis type
+    extern __shared__ __align__(16) double dsh[];
+    double* h = dsh;
+    double* scol = h + (kmax + 2);
+    double* scs = scol + (kmax + 2);
+    double* ssn = scs + kmax;
+    VT* hv = reinterpret_cast<VT*>(ssn + kmax);
+    __shared__ double shn, sinv;
     __shared__ bool last;
     long long off;
     if (!bat_enter(bt, (int)blockIdx.y, &off)) return;
@@ -3041,18 +3050,21 @@ __global__ void __launch_bounds__(256)
     }
     if (threadIdx.x < 32) {
         const double n2 = second ? h[j + 1] - warp_sumsq(h, j + 1) : scal[4];
-        if (threadIdx.x == 0) shn = n2 > 0.0 ? sqrt(n2) : 0.0;
+        if (threadIdx.x == 0) {
+            const double r = n2 > 0.0 ? sqrt(n2) : 0.0;
+            shn = r;
+            sinv = r > 0.0 ? 1.0 / r : 0.0;          // one FP64 division per block
+        }
     }
     __syncthreads();
     const double hn = shn;
-    const VT inv = (VT)(hn > 0.0 ? 1.0 / hn : 0.0);
+    const VT inv = (VT)sinv;
     block_update<VT, VEC>(Vb, N, j, hv, second, inv);
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(gridDim.x - 1));
     __syncthreads();
     if (!last) return;
     // the last block: every block has read j; H column, Givens, convergence, j += 1
-    __shared__ double scol[kMaxKrylov + 2], scs[kMaxKrylov], ssn[kMaxKrylov];
     double* col = H + (long long)j * (kmax + 1);
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         scol[i] = col[i] + h[i];
@@ -3225,8 +3237,9 @@ static void arnoldi_launch(GmresDev& G, cudaStream_t s, const Bat& bt) {
     k_gm_dots2<VT, VEC><<<gd, 256, 0, s>>>(V, G.jdev, G.N, G.part_dots, G.kmax, G.iflag, G.reo, G.hsum, G.counter,
                                              bt);
     note_launch();
-    k_gm_update2<VT, VEC><<<gu, 256, 0, s>>>(V, G.jdev, G.N, G.hsum, G.kmax, G.H, G.cs, G.sn, G.gv, G.scal,
-                                             G.iflag, G.reo, G.counter2, G.jdev, bt);
+    const size_t upd2_smem = (size_t)(4 * G.kmax + 4) * sizeof(double) + (size_t)(G.kmax + 2) * sizeof(VT);
+    k_gm_update2<VT, VEC><<<gu, 256, upd2_smem, s>>>(V, G.jdev, G.N, G.hsum, G.kmax, G.H, G.cs, G.sn, G.gv,
+                                                     G.scal, G.iflag, G.reo, G.counter2, G.jdev, bt);
     note_launch();
 }
 
