@@ -394,9 +394,11 @@ hpg_status hpg_apply_schur(hpg_ctx* ctx, int pid, int precision, const double* x
                            size_t len);
 /* y_dev = A_alpha^{-1} x_dev, the same FP64 fast-diagonalisation apply as
  * hpg_apply_stiffness_inv, for callers that cannot allocate device memory at
- * call time: code running while a CUDA stream is being captured into a graph
- * (where cudaMalloc is not allowed), or real-time loops that forbid allocation
- * after start-up.  The paper has no counterpart; this is a library service.
+ * call time: real-time loops that forbid allocation after start-up (cudaMalloc
+ * may synchronise the device and takes unbounded time), and applications that
+ * hand all device memory to their own pool or budget up front, so that an
+ * extra cudaMalloc would fail or fragment it.  The paper has no counterpart;
+ * this is a library service.
  * x_dev, y_dev: device pointers of length n_u_interior (len >= that); they may
  * alias.  Its intermediate tensors live in one fixed device array of the
  * library (4 MiB, held by every GPU that loads libhpg until exit), so it

@@ -2,9 +2,9 @@
 hpg_apply_stiffness_inv.
 
 hpg_apply_stiffness_inv_noalloc serves callers that cannot allocate device
-memory at call time (work enqueued during CUDA stream capture, real-time loops
-that forbid allocation after start-up): its scratch is a fixed device array of
-the library.  This file is collected last so that, if it fails, a run that
+memory at call time (real-time loops that forbid allocation after start-up,
+applications that give all device memory to their own pool up front): its
+scratch is a fixed device array of the library.  This file is collected last so that, if it fails, a run that
 stops at the first failure has run every other test already.
 """
 import numpy as np
