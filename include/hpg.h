@@ -65,7 +65,8 @@ typedef enum {
     HPG_ERR_NEWTON_CAP = 4,     /* a subproblem hit the Newton iteration cap                 */
     HPG_ERR_KRYLOV_CAP = 5,     /* GMRES hit its cap before its tolerance (reported only)    */
     HPG_ERR_NONFINITE = 6,      /* NaN/Inf, or psi < -700 at a Gauss point (exp overflow)    */
-    HPG_ERR_NOT_SPD = 7,        /* a cell block of -S-hat had a non-positive Cholesky pivot  */
+    HPG_ERR_NOT_SPD = 7,        /* a cell block of -S-hat had a non-positive pivot in FP64
+                                   (HPG_MIXED takes a failed step again in FP64 first)          */
     HPG_ERR_TIMEOUT = 8,        /* a bounded host wait expired                               */
     HPG_ERR_INFEASIBLE_BC = 9,  /* Dirichlet data violates the constraint on the boundary    */
     HPG_ERR_STATE = 10,         /* call out of order (e.g. solve before data were set)       */
@@ -172,6 +173,14 @@ typedef struct {
     long long fgmres_total;                /* outer FGMRES iterations (FGMRES strategies)  */
     long long ainv_total;                  /* applications of A_alpha^{-1} over the solve  */
     long long ainv_iters;                  /* CG iterations of those applications (ainv_pcg) */
+    /* HPG_MIXED fallback: a proximal step whose mixed Newton iteration fails (a
+       non-positive pivot of the FP32 S-hat elimination, a line search that ends on a
+       non-finite trial point, the Newton cap) is solved again from its starting point in
+       FP64, and so is the rest of the solve.  newton_total counts the discarded steps too,
+       newton_per_step the FP64 ones.  A lockstep-group member that falls back is solved
+       again on its own after the group, which gives the result of solving it alone. */
+    int    fp64_from_step;                 /* proximal step (1-based) of the fallback, or 0 */
+    int    fp64_newton_steps;              /* Newton steps taken in FP64 after it          */
 } hpg_stats;
 
 /* Kernel classes timed when hpg_params.timing = 1. */

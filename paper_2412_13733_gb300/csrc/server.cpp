@@ -76,7 +76,7 @@ size_t estimate_device_bytes(const Problem& P) {
     }
     b += Nu0 * (8 * 8 + 4 * 4);                          // rA, bf, tu/w buffers
     b += Npsi * 8 * 10 + Npsi * 4;                       // psi-sized vectors
-    b += Nx * 8 * 7;                                     // x, xt, F, Ft, delta, r, dcorr
+    b += Nx * 8 * 8;                                     // x, xt, x0, F, Ft, delta, r, dcorr
     b += gsz * (8 * 3 + 4);                              // Gauss weights
     b += H.Nq * 8;
     b += H.Nc * H.nb * H.nb * 12;                        // S-hat inverses (FP64 + FP32)

@@ -306,6 +306,7 @@ hpg_status alloc_device(hpg_ctx* ctx, Problem& P) {
         sa(D.phiq, H.Nq);
         sa(D.x, Nx);
         sa(D.xt, Nx);
+        sa(D.x0, Nx);
         sa(D.psi_prev, Npsi);
         sa(D.gw, gsz);
         sa(D.gwt, gsz);
@@ -1084,11 +1085,11 @@ static hpg_status fgmres_solve(hpg_ctx* ctx, Problem& P, double alpha, const dou
 constexpr double kInnerMargin = 0.5;
 
 static hpg_status linear_solve(hpg_ctx* ctx, Problem& P, double alpha, const double* F, double normF, double eta,
-                               double* delta, int* its_total, int* sweeps) {
+                               double* delta, int* its_total, int* sweeps, bool force_f64 = false) {
     DevState& D = P.D;
     cudaStream_t s = ctx->stream;
     const long long Nu0 = (long long)P.H.Nu0, Npsi = (long long)P.H.Npsi, Nx = Nu0 + Npsi;
-    const bool f64 = P.params.precision == HPG_FP64;
+    const bool f64 = P.params.precision == HPG_FP64 || force_f64;
     *sweeps = 0;
     *its_total = 0;
     CK(cudaMemsetAsync(delta, 0, Nx * sizeof(double), s));
@@ -1165,15 +1166,33 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
     CK(cudaMemsetAsync(D.flag, 0, 4 * sizeof(int), s));
     hpg_status status = HPG_OK;
     double normF = 0.0;
+    // HPG_MIXED: a proximal step whose mixed Newton iteration fails (a non-positive pivot
+    // of the FP32 S-hat elimination, a line search ending on a non-finite trial point, the
+    // Newton cap) is solved again from its starting point in FP64, and so is the rest of
+    // the solve
+    const bool mixed = P.params.precision != HPG_FP64;
+    bool fp64 = !mixed;
     const int nsteps = (int)std::min<size_t>(H.alphas.size(), HPG_MAX_ALPHA);
     for (int k = 0; k < nsteps && status == HPG_OK; ++k) {
         const double alpha = H.alphas[k];
         CKS(set_alpha(ctx, P, alpha));
         if (k > 0) CK(cudaMemcpyAsync(D.psi_prev, D.x + Nu0, Npsi * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (!fp64) CK(cudaMemcpyAsync(D.x0, D.x, Nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
         int flag = 0;
         CKS(eval_state(ctx, P, D.x, D.gw, D.eg));
         CKS(residual_state(ctx, P, D.x, D.eg, alpha, D.F, &normF, &flag));
         int it = 0;
+        auto fall_back = [&]() -> hpg_status {
+            fp64 = true;
+            st.fp64_from_step = k + 1;
+            st.newton_total += it;              // the mixed Newton steps discarded
+            it = 0;
+            CK(cudaMemcpyAsync(D.x, D.x0, Nx * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemsetAsync(D.flag, 0, 4 * sizeof(int), s));
+            CKS(eval_state(ctx, P, D.x, D.gw, D.eg));
+            CKS(residual_state(ctx, P, D.x, D.eg, alpha, D.F, &normF, &flag));
+            return HPG_OK;
+        };
         while (true) {
             if (flag & 1) { status = HPG_ERR_NONFINITE; break; }
             if (!std::isfinite(normF)) {
@@ -1182,18 +1201,23 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
                 break;
             }
             if (normF <= P.params.newton_tol) break;
+            if (it >= P.params.newton_max && !fp64) {
+                CKS(fall_back());
+                continue;
+            }
             if (it >= P.params.newton_max) {
                 status = HPG_ERR_NEWTON_CAP;
                 ctx->err = "Newton cap reached in proximal step " + std::to_string(k + 1) + " (||F|| = " +
                            std::to_string(normF) + ")";
                 break;
             }
-            if (P.params.precision == HPG_FP64) CKS(factor_T<double>(ctx, P, alpha, nullptr));
+            if (fp64) CKS(factor_T<double>(ctx, P, alpha, nullptr));
             else CKS(factor_T<float>(ctx, P, alpha, nullptr));
+            if (mixed && fp64) st.fp64_newton_steps++;
             int its = 0, sweeps = 0;
             // forcing term: relative tolerance min(krylov_rtol, ||F||)
             const double eta = std::min(P.params.krylov_rtol, std::max(normF, 1e-12));
-            CKS(linear_solve(ctx, P, alpha, D.F, normF, eta, D.delta, &its, &sweeps));
+            CKS(linear_solve(ctx, P, alpha, D.F, normF, eta, D.delta, &its, &sweeps, fp64));
             st.krylov_total += its;
             st.refine_total += sweeps;
             // backtracking on ||F||
@@ -1214,10 +1238,16 @@ hpg_status solve_problem(hpg_ctx* ctx, Problem& P) {
             // factorisation flag (non-SPD block): bit 1 of flag[1], sticky for the solve
             CK(cudaMemcpyAsync(D.h_iflag, D.flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            if (D.h_iflag[0] & 2) {
+            const bool spd_fail = (D.h_iflag[0] & 2) != 0;
+            const bool bad_trial = (tflag & 1) || !std::isfinite(nFt);
+            if (!fp64 && (spd_fail || bad_trial)) {
+                CKS(fall_back());
+                continue;
+            }
+            if (spd_fail) {
                 status = HPG_ERR_NOT_SPD;
-                ctx->err = std::string("non-positive pivot in a ") + (P.params.precision == HPG_FP64 ? "FP64" : "FP32") +
-                           " S-hat block factorisation in proximal step " + std::to_string(k + 1);
+                ctx->err = "non-positive pivot in an FP64 S-hat block factorisation in proximal step " +
+                           std::to_string(k + 1);
                 break;
             }
             swap_state(D);
@@ -1763,8 +1793,9 @@ hpg_status solve_group(hpg_ctx* home, hpg_ctx* ctx, std::vector<Problem*>& ps, s
     CK(launch_copy<int>(nullptr, D.flag, 4, s, all));
     // per-problem host state
     std::vector<int> k(np, 0), it(np, 0), flag(np, 0), status(np, HPG_OK);
-    std::vector<char> done(np, 0), start(np, 1);
+    std::vector<char> done(np, 0), start(np, 1), redo(np, 0);
     std::vector<double> normF(np, 0.0), eta(np, 0.0), lam(np, 1.0), nFt(np, 0.0);
+    const bool mixed = P0.params.precision != HPG_FP64;
     std::vector<int> tflag(np, 0), nsteps(np);
     std::vector<std::string> msg(np);
     for (int i = 0; i < np; ++i) nsteps[i] = (int)std::min<size_t>(ps[i]->H.alphas.size(), HPG_MAX_ALPHA);
@@ -1819,6 +1850,10 @@ hpg_status solve_group(hpg_ctx* home, hpg_ctx* ctx, std::vector<Problem*>& ps, s
                 if (k[i] >= nsteps[i]) done[i] = 1;
                 else start[i] = 1;
                 live = live || !done[i];
+                continue;
+            } else if (it[i] >= q.newton_max && mixed) {
+                redo[i] = 1;                // FP64 again on its own, as alone (below)
+                done[i] = 1;
                 continue;
             } else if (it[i] >= q.newton_max) {
                 status[i] = HPG_ERR_NEWTON_CAP;
@@ -1886,8 +1921,20 @@ hpg_status solve_group(hpg_ctx* home, hpg_ctx* ctx, std::vector<Problem*>& ps, s
         for (int i = 0; i < np; ++i) {
             Gp.mask(kMaskTrial)[i] = 0;
             if (!inN[i]) continue;
-            if (gi_(Gp, i, 1) & 2) {
+            const bool spd_fail = (gi_(Gp, i, 1) & 2) != 0;
+            const bool bad_trial = (tflag[i] & 1) || !std::isfinite(nFt[i]);
+            if (mixed && (spd_fail || bad_trial)) {
+                // a failed mixed step: a problem solved alone takes its proximal step again
+                // in FP64, which the group does not run; the member is solved again on its
+                // own afterwards (the same steps as alone)
+                redo[i] = 1;
+                done[i] = 1;
+                continue;
+            }
+            if (spd_fail) {
                 status[i] = HPG_ERR_NOT_SPD;
+                msg[i] = "non-positive pivot in an FP64 S-hat block factorisation in proximal step " +
+                         std::to_string(k[i] + 1);
                 finish_step(i);
                 done[i] = 1;
                 continue;
@@ -1911,8 +1958,22 @@ hpg_status solve_group(hpg_ctx* home, hpg_ctx* ctx, std::vector<Problem*>& ps, s
     CK(cudaStreamSynchronize(s));
     const long long launches = kernel_launch_count() - launches0;
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    // members that fell back from the mixed form: solved again on their own (same steps as alone)
+    for (int i = 0; i < np; ++i) {
+        if (!redo[i]) continue;
+        status[i] = solve_problem(ctx, *ps[i]);
+        if (status[i] != HPG_OK) msg[i] = ctx->err;
+    }
     hpg_status first = HPG_OK;
     for (int i = 0; i < np; ++i) {
+        if (redo[i]) {
+            if (errs) (*errs)[i] = msg[i];
+            if (status[i] != HPG_OK && first == HPG_OK) {
+                first = (hpg_status)status[i];
+                ctx->err = msg[i];
+            }
+            continue;
+        }
         hpg_stats& st = ps[i]->stats;
         st.final_residual = normF[i];
         st.status = status[i];

@@ -50,6 +50,7 @@ struct DevState {
     double *rA = nullptr, *rB = nullptr, *bf = nullptr, *phiz = nullptr, *phiq = nullptr;
     // state: x = [u (interior); psi] contiguous so Newton updates are one axpy
     double *x = nullptr, *xt = nullptr;          // current and trial
+    double* x0 = nullptr;                        // HPG_MIXED: x at the start of the proximal step
     double *psi_prev = nullptr;
     double *gw = nullptr, *gwt = nullptr;        // Gauss weights (current, trial)
     double* gwl = nullptr;                       // weights of the current linearisation (FP64)

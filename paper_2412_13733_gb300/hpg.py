@@ -39,7 +39,8 @@ class hpg_stats(C.Structure):
                 ("final_residual", C.c_double), ("solve_ms", C.c_double), ("n_u", C.c_longlong),
                 ("n_psi", C.c_longlong), ("kernel_launches", C.c_longlong), ("h2d_bytes", C.c_longlong),
                 ("fdm_tile_f32", C.c_int), ("fdm_tile_f64", C.c_int), ("fgmres_total", C.c_longlong),
-                ("ainv_total", C.c_longlong), ("ainv_iters", C.c_longlong)]
+                ("ainv_total", C.c_longlong), ("ainv_iters", C.c_longlong), ("fp64_from_step", C.c_int),
+                ("fp64_newton_steps", C.c_int)]
 
 
 HPG_QVI_MAX_FP = 64

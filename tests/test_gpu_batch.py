@@ -123,3 +123,35 @@ def test_lockstep_group_member_failure_is_its_own(ctx):
         assert np.array_equal(probs[i].u(), alone[i])
     for P in probs:
         P.free()
+
+
+def test_lockstep_group_mixed_fallback_equals_alone(ctx):
+    """A mixed problem whose proximal step hits the Newton cap is solved again from that
+    step's start in FP64 (where, with a cap of two steps, it hits the cap again).  In a
+    lockstep group that member leaves the group and is solved on its own afterwards: its
+    status, counts and iterate equal its solve alone, and the other members are unaffected."""
+    from paper_2412_13733_gb300 import hpg
+    ws = _variants("radial_3x3_p5", 3)
+    prm = lambda i: hpg.default_params(precision=hpg.HPG_MIXED, newton_max=2 if i == 1 else 50)
+    alone = []
+    for i, w in enumerate(ws):
+        P = hpg.from_workload(ctx, w, prm(i))
+        rc = P.solve(check=False)
+        alone.append((rc, P.stats(), P.u().copy()))
+        P.free()
+    rc1, st1, _ = alone[1]
+    assert rc1 == 4 and st1["fp64_from_step"] == 1 and st1["fp64_newton_steps"] == 2, st1
+    assert st1["newton_total"] == 4                  # two mixed steps discarded, two in FP64
+    for i in (0, 2):
+        assert alone[i][0] == 0 and alone[i][1]["fp64_from_step"] == 0
+    probs = [hpg.from_workload(ctx, w, prm(i)) for i, w in enumerate(ws)]
+    assert ctx.solve_batch(probs, check=False) == 4
+    for (rc, st, u), P in zip(alone, probs):
+        sb = P.stats()
+        assert sb["status"] == rc
+        for key in ("fp64_from_step", "fp64_newton_steps", "newton_total", "krylov_total"):
+            assert sb[key] == st[key], key
+        assert sb["newton_per_step"] == st["newton_per_step"]
+        assert np.array_equal(P.u(), u)
+    for P in probs:
+        P.free()

@@ -135,3 +135,71 @@ def test_qvi_argument_errors(ctx):
     rc, _ = L.qvi_solve(np.zeros(len(Xl)), np.zeros(len(Xl)), np.zeros(len(Xq)), np.zeros(len(Xq)), check=False)
     assert rc == hpg.STATUS.index("HPG_ERR_ARG")
     L.free()
+
+
+def test_qvi_mixed_precision_matches_oracle(ctx):
+    """The QVI with HPG_MIXED obstacle solves: the same fixed point as the oracle's (count,
+    u, T) at the tolerances of the FP64 comparison."""
+    from paper_2412_13733_gb300 import hpg
+    w = W.workload("thermoforming_p6")
+    P, data = _setup(ctx, w)
+    prm = hpg.default_params()
+    prm.beta = w["beta"]
+    prm.newton_tol = 1e-10
+    prm.precision = hpg.HPG_MIXED
+    P.set_params(prm)
+    rc, st = P.qvi_solve(*data, gamma=w["gamma"], g0=w["g0"], tol=w["qvi_tol"])
+    q = QVIOracle(w["breakpoints"], w["p"], w["f"], w["Phi0"], w["xi"], gamma=w["gamma"], g0=w["g0"],
+                  beta=w["beta"])
+    r = q.solve(w["alphas"], tol=w["qvi_tol"], newton_tol=1e-10)
+    assert rc == 0 and st["converged"] == 1 and st["iterations"] == r["iterations"], st
+    u, T = P.u(), P.qvi_T()
+    assert np.max(np.abs(u - r["u"])) <= 1e-6 * max(1.0, np.max(np.abs(r["u"])))
+    assert np.max(np.abs(T - r["T"])) <= 1e-7 * max(1.0, np.max(np.abs(r["T"])))
+    P.free()
+
+
+def _mould_problem(ctx, precision, p=22):
+    """Obstacle solve with the thermoforming mould Phi_0 (the QVI's first iterate) at degree p
+    on the 4 x 4 mesh; beta = 1e-6 makes the S-hat cell blocks badly conditioned."""
+    from paper_2412_13733_gb300 import hpg
+    w = W.workload(f"thermoforming_p{p}")
+    P = hpg.Problem(ctx, 2, [0.0, 0.0], [1.0, 1.0], [4, 4], p, hpg.HPG_OBSTACLE_UPPER)
+    P.set_rhs(w["f_const"])
+    P.set_alphas(w["alphas"])
+    P.set_params(hpg.default_params(beta=w["beta"], precision=precision))
+    P.set_constraint_values(w["Phi0"](P.quad_points()))
+    return P
+
+
+def test_mixed_fallback_to_fp64_steps(ctx):
+    """At p = 22 a mixed proximal step fails (the FP32 elimination of an S-hat block meets a
+    non-positive pivot, the line search ends on a non-finite point): the step is solved again
+    from its start in FP64, as is the rest of the solve, and the result is the FP64 one; in
+    a lockstep group the member is solved again on its own, bit for bit as alone."""
+    from paper_2412_13733_gb300 import hpg
+    ref = _mould_problem(ctx, hpg.HPG_FP64)
+    ref.solve()
+    u_ref = ref.u().copy()
+    sr = ref.stats()
+    assert sr["fp64_from_step"] == 0 and sr["fp64_newton_steps"] == 0
+    A = _mould_problem(ctx, hpg.HPG_MIXED)
+    assert A.solve(check=False) == 0
+    sa = A.stats()
+    assert sa["fp64_from_step"] >= 1 and sa["fp64_newton_steps"] >= 1, sa
+    assert sa["newton_total"] >= sum(sa["newton_per_step"])           # discarded mixed steps count
+    # both end on FP64 Newton steps at the same residual tolerance; at beta = 1e-6 the psi
+    # block of eq. (pG-matrix) is nearly singular on the contact set, so two such solves from
+    # slightly different starting points agree to the max-norm bar of the QVI comparisons
+    assert sa["final_residual"] <= 1e-10 and sr["final_residual"] <= 1e-10
+    assert np.max(np.abs(A.u() - u_ref)) <= 1e-6 * max(1.0, np.max(np.abs(u_ref)))
+    assert all(abs(a - b) <= 1 for a, b in zip(sa["newton_per_step"], sr["newton_per_step"]))
+    B1, B2 = _mould_problem(ctx, hpg.HPG_MIXED), _mould_problem(ctx, hpg.HPG_MIXED)
+    assert ctx.solve_batch([B1, B2], check=False) == 0
+    for B in (B1, B2):
+        assert np.array_equal(B.u(), A.u())
+        sb = B.stats()
+        assert sb["newton_per_step"] == sa["newton_per_step"]
+        assert sb["fp64_from_step"] == sa["fp64_from_step"]
+    for P in (ref, A, B1, B2):
+        P.free()
