@@ -763,34 +763,45 @@ def main():
                                                                "n_u": P.n_u}
                 P.free()
 
-    # Section 6.4: the thermoforming QVI on the 4 x 4 mesh (Table 3's columns), FP64 obstacle
-    # solves on the device (with beta = 1e-6 an FP32 S-hat factorisation meets a non-positive
-    # pivot); the oracle's fixed point timed beside it at p = 6
+    # Section 6.4: the thermoforming QVI on the 4 x 4 mesh (Table 3's columns), obstacle solves
+    # in FP64 and in the mixed form (where a failed mixed proximal step is solved again in
+    # FP64: fp64_from_step); the oracle's fixed point timed beside it at p = 6
     qvi = None
     if not args.no_qvi:
         qvi = {}
         for p_deg in (6, 12, 22):
             wq = W.workload(f"thermoforming_p{p_deg}")
-            P = hpg.Problem(ctx, 2, [0.0, 0.0], [1.0, 1.0], [4, 4], p_deg, hpg.HPG_OBSTACLE_UPPER)
-            P.set_rhs(wq["f_const"])
-            P.set_alphas(wq["alphas"])
-            P.set_params(hpg.default_params(beta=wq["beta"], precision=hpg.HPG_FP64))
-            Xl, Xq = P.quad_points(), P.qvi_points()
-            data = (wq["Phi0"](Xl), wq["xi"](Xl), wq["Phi0"](Xq), wq["xi"](Xq))
-            P.qvi_solve(*data, gamma=wq["gamma"], g0=wq["g0"], tol=wq["qvi_tol"])     # warm-up
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rc, st = P.qvi_solve(*data, gamma=wq["gamma"], g0=wq["g0"], tol=wq["qvi_tol"], check=False)
-            torch.cuda.synchronize()
-            sec = time.perf_counter() - t0
-            nfp = max(1, st["iterations"])
-            qvi[f"p={p_deg}"] = {"status": rc, "fixed_point": st["iterations"], "seconds": sec,
-                                 "avg_newton_I": st["newton_total"] / nfp,
-                                 "avg_gmres_I": st["krylov_total"] / max(1, st["newton_total"]),
-                                 "avg_newton_II": st["t_newton_total"] / nfp,
-                                 "avg_gmres_II": st["t_krylov_total"] / max(1, st["t_newton_total"]),
-                                 "kernel_launches": st["kernel_launches"], "n_u_full": P.n_u_full}
-            P.free()
+            row = {}
+            for tag, prec in (("fp64", hpg.HPG_FP64), ("mixed", hpg.HPG_MIXED)):
+                P = hpg.Problem(ctx, 2, [0.0, 0.0], [1.0, 1.0], [4, 4], p_deg, hpg.HPG_OBSTACLE_UPPER)
+                P.set_rhs(wq["f_const"])
+                P.set_alphas(wq["alphas"])
+                P.set_params(hpg.default_params(beta=wq["beta"], precision=prec))
+                Xl, Xq = P.quad_points(), P.qvi_points()
+                data = (wq["Phi0"](Xl), wq["xi"](Xl), wq["Phi0"](Xq), wq["xi"](Xq))
+                P.qvi_solve(*data, gamma=wq["gamma"], g0=wq["g0"], tol=wq["qvi_tol"], check=False)   # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, st = P.qvi_solve(*data, gamma=wq["gamma"], g0=wq["g0"], tol=wq["qvi_tol"], check=False)
+                torch.cuda.synchronize()
+                sec = time.perf_counter() - t0
+                nfp = max(1, st["iterations"])
+                if tag == "fp64":
+                    row.update({"status": rc, "fixed_point": st["iterations"], "seconds": sec,
+                                "avg_newton_I": st["newton_total"] / nfp,
+                                "avg_gmres_I": st["krylov_total"] / max(1, st["newton_total"]),
+                                "avg_newton_II": st["t_newton_total"] / nfp,
+                                "avg_gmres_II": st["t_krylov_total"] / max(1, st["t_newton_total"]),
+                                "kernel_launches": st["kernel_launches"], "n_u_full": P.n_u_full})
+                    u64 = P.u().copy()
+                else:
+                    ps_ = P.stats()        # the last obstacle solve of the fixed point
+                    row["mixed"] = {"status": rc, "fixed_point": st["iterations"], "seconds": sec,
+                                    "avg_newton_I": st["newton_total"] / nfp,
+                                    "last_solve_fp64_from_step": ps_["fp64_from_step"],
+                                    "u_max_diff_vs_fp64": float(np.max(np.abs(P.u() - u64))) if rc == 0 else None}
+                P.free()
+            qvi[f"p={p_deg}"] = row
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             from oracle.qvi import QVIOracle
             wq = W.workload("thermoforming_p6")
