@@ -42,9 +42,9 @@ WORKLOAD = "radial32"
 # one A_alpha^{-1} apply on the 32x32 p=8 workload, from one ncu capture (`--kernel fdm
 # --precision mixed --fdm-tile 0`, cold caches)
 FDM_TRAFFIC_BYTES = (573952 + 575744 + 574720 + 573952)
-# DRAM bytes of one batched apply (16 problems per launch, the TMA variant's split kernel
-# and four passes) from the ncu capture in profiles/; None until captured for the current kernels
-FDM_BATCH_TRAFFIC_BYTES = None
+# DRAM bytes of one batched apply (16 problems per launch, the TMA variant with 32-column tiles:
+# four passes of 9.0 MB each and the split kernel's 0.27 MB, cold-cache ncu captures)
+FDM_BATCH_TRAFFIC_BYTES = 4 * 9.0e6 + 0.27e6
 METRIC = "solves/s (complete hpG solve at 1e-8 rel err vs FP64 oracle), mixed vs FP64; DoF*Krylov-its/s"
 
 
@@ -596,7 +596,8 @@ def main():
             roof = {"kernel": f"fdm (A_alpha^-1, tcgen05 3xTF32 passes fed by TMA, variant {vb}, "
                               f"{B} problems per launch as in the batched step)",
                     "bound": "tensor", "achieved": tach, "peak": tf32_peak, "unit": unit, "frac": tach / tf32_peak,
-                    "traffic": FDM_BATCH_TRAFFIC_BYTES, "avg_launch_us": avg_ms * 1000.0, "problems_per_launch": B,
+                    "traffic": FDM_BATCH_TRAFFIC_BYTES if vb == 20 and B == 16 else None,
+                    "avg_launch_us": avg_ms * 1000.0, "problems_per_launch": B,
                     "flops_per_launch": 3.0 * flops_b, "algorithmic_flops_per_launch": flops_b,
                     "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x nominal TF32/bf16 ratio",
                     "fp32_equivalent": fp32_eq}
