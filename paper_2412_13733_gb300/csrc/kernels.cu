@@ -2789,7 +2789,11 @@ __global__ void __launch_bounds__(256)
     // full chunks on the float4 path read w straight from global memory (L1 serves
     // the other warps); otherwise w is staged in shared memory first
     const bool direct = VEC && len == kDotChunk;
-    if (!direct) {
+    // FP64 basis, full chunk: every warp reads w from global memory too (L1 serves the
+    // other warps), so the basis loads do not wait behind a staging pass and a barrier;
+    // the same products in the same order as from shared memory
+    const bool wdir = sizeof(VT) == 8 && len == kDotChunk;
+    if (!direct && !wdir) {
         for (int t = threadIdx.x; t < kDotChunk; t += blockDim.x) ws[t] = (t < len) ? w[t] : VT(0);
         __syncthreads();
     }
@@ -2823,6 +2827,28 @@ __global__ void __launch_bounds__(256)
                     s0 += b.z * b.z;
                     s1 += b.w * b.w;
                 }
+            }
+        } else if (vi && wdir) {
+#pragma unroll
+            for (int q0 = 0; q0 < 32; q0 += 8) {
+                VT a[8], b[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    a[u] = vi[lane + 32 * (q0 + u)];
+                    b[u] = w[lane + 32 * (q0 + u)];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u += 2) {
+                    s0 += a[u] * b[u];
+                    s1 += a[u + 1] * b[u + 1];
+                }
+            }
+        } else if (wdir) {
+#pragma unroll 8
+            for (int q = 0; q < 32; q += 2) {
+                const VT x0 = w[lane + 32 * q], x1 = w[lane + 32 * (q + 1)];
+                s0 += x0 * x0;
+                s1 += x1 * x1;
             }
         } else if (vi && len == kDotChunk) {
 #pragma unroll
@@ -3056,10 +3082,21 @@ __global__ void __launch_bounds__(256)
             sinv = r > 0.0 ? 1.0 / r : 0.0;          // one FP64 division per block
         }
     }
-    __syncthreads();
-    const double hn = shn;
-    const VT inv = (VT)sinv;
-    block_update<VT, VEC>(Vb, N, j, hv, second, inv);
+    double hn;
+    if constexpr (sizeof(VT) == 8) {
+        // FP64: the subtraction does not wait for warp 0's norm; only the scaling does
+        const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        VT* w = Vb + (long long)(j + 1) * N;
+        VT v = VT(0);
+        if (e < N) v = second ? sub_basis(Vb, N, e, hv, j + 1, w[e]) : w[e];
+        __syncthreads();
+        hn = shn;
+        if (e < N) w[e] = v * (VT)sinv;
+    } else {
+        __syncthreads();
+        hn = shn;
+        block_update<VT, VEC>(Vb, N, j, hv, second, (VT)sinv);
+    }
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)(gridDim.x - 1));
     __syncthreads();
